@@ -1,0 +1,292 @@
+"""FP64 CPU oracle of the SANS Monte Carlo trace.
+
+TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` are the only users. Nothing in the CUDA
+library imports, links or calls this package, and this package imports
+nothing from the CUDA library.
+
+The C part (``sas_oracle.c``) traces neutrons in double precision; this
+module builds it with gcc, loads it with ctypes and computes the quadrature
+nodes it consumes:
+
+* Schulz polydispersity: the Schulz density of mean rbar and relative width
+  p, f(r) ~ r^z exp(-(z+1) r / rbar) with z = 1/p^2 - 1, becomes the
+  generalised Laguerre weight x^z e^-x under x = (z+1) r / rbar, so an
+  n-point generalised Gauss-Laguerre rule (alpha = z) gives nodes
+  r_i = rbar x_i / (z+1); it is exact for <r^k> with k <= 2n-1.
+  (The paper samples a Gaussian per event, Sec. II.B; the Schulz rule with a
+  fixed node count is the reading used here for the polydisperse workloads.)
+* Orientation: the particle axis is spread about a mean axis n with density
+  proportional to exp(-gamma^2 / (2 sigma^2)) on the unit sphere (gamma is the
+  angle from n, psi the azimuth about n), truncated at gamma = min(3 sigma, pi),
+  integrated by Gauss-Legendre in gamma (with the sin(gamma) area element)
+  and Gauss-Legendre in psi over [0, 2 pi). The axis of node (gamma, psi) is
+  cos(gamma) n + sin(gamma) (cos(psi) e_theta + sin(psi) e_phi), with e_theta,
+  e_phi the spherical unit vectors at n. Isotropic: gamma over [0, pi], flat.
+  Orientation angles theta, phi of the axis follow Sec. II.A (Eq. 7).
+
+Both rules use the Golub-Welsch construction (eigen-decomposition of the
+Jacobi matrix of the orthogonal polynomials) with numpy's symmetric
+eigensolver.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sas_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libsas_oracle.so")
+_lib = None
+_lock = threading.Lock()
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle (gcc, FP64, OpenMP). Returns the library path."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+           "-fno-fast-math", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Instrument(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in (
+        "lambda0", "dlambda_rel", "ap1_radius", "ap1_z", "ap2_radius", "ap2_z",
+        "sample_half_x", "sample_half_y", "sample_thickness", "mu", "det_distance",
+        "pixel_x", "pixel_y")] + [("nx", ctypes.c_int64), ("ny", ctypes.c_int64)]
+
+
+_DP = ctypes.POINTER(ctypes.c_double)
+
+
+class _Model(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int64), ("sq_kind", ctypes.c_int64),
+                ("n_poly", ctypes.c_int64), ("n_orient", ctypes.c_int64)] + \
+               [(n, ctypes.c_double) for n in (
+                   "radius", "thickness", "length", "radius_polar", "sld", "sld_shell",
+                   "sld_solvent", "volume_fraction", "sq_radius", "sq_fraction")] + \
+               [("poly_r", _DP), ("poly_w", _DP), ("orient_c", _DP), ("orient_w", _DP)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build()
+            L = ctypes.CDLL(path)
+            u32p = ctypes.POINTER(ctypes.c_uint32)
+            L.oracle_philox4x32_10.argtypes = [u32p, u32p, u32p]
+            for f in ("oracle_sphere_f", "oracle_cyl_a", "oracle_sinc"):
+                getattr(L, f).argtypes = [ctypes.c_double]
+                getattr(L, f).restype = ctypes.c_double
+            L.oracle_sq_py.argtypes = [ctypes.c_double] * 3
+            L.oracle_sq_py.restype = ctypes.c_double
+            L.oracle_dsigma.argtypes = [ctypes.POINTER(_Model), _DP]
+            L.oracle_dsigma.restype = ctypes.c_double
+            L.oracle_dsigma_many.argtypes = [ctypes.POINTER(_Model), _DP, ctypes.c_int64, _DP]
+            L.oracle_trace.argtypes = [ctypes.POINTER(_Instrument), ctypes.POINTER(_Model),
+                                       ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64,
+                                       ctypes.c_uint64, _DP, _DP,
+                                       ctypes.POINTER(ctypes.c_uint64), _DP, ctypes.c_int]
+            L.oracle_records.argtypes = [ctypes.POINTER(_Instrument), ctypes.POINTER(_Model),
+                                         ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64,
+                                         ctypes.c_uint64, ctypes.POINTER(ctypes.c_int64), _DP]
+            L.oracle_num_threads.restype = ctypes.c_int
+            L.oracle_sample_lambda.argtypes = [ctypes.c_double] * 3
+            L.oracle_sample_lambda.restype = ctypes.c_double
+            _lib = L
+    return _lib
+
+
+# ------------------------------------------------------------- quadrature
+
+def gauss_legendre(n: int):
+    """n-point Gauss-Legendre rule on [-1, 1] by Golub-Welsch."""
+    if n == 1:
+        return np.array([0.0]), np.array([2.0])
+    k = np.arange(1, n, dtype=np.float64)
+    off = k / np.sqrt(4.0 * k * k - 1.0)
+    J = np.diag(off, 1) + np.diag(off, -1)
+    x, V = np.linalg.eigh(J)
+    w = 2.0 * V[0, :] ** 2
+    return x, w
+
+
+def gauss_laguerre_gen(n: int, alpha: float):
+    """n-point generalised Gauss-Laguerre rule for x^alpha e^-x on (0, inf),
+    weights normalised to sum 1, by Golub-Welsch."""
+    k = np.arange(n, dtype=np.float64)
+    diag = 2.0 * k + alpha + 1.0
+    kk = np.arange(1, n, dtype=np.float64)
+    off = np.sqrt(kk * (kk + alpha))
+    J = np.diag(diag) + np.diag(off, 1) + np.diag(off, -1)
+    x, V = np.linalg.eigh(J)
+    w = V[0, :] ** 2
+    return x, w / w.sum()
+
+
+def schulz_nodes(mean: float, p: float, n: int):
+    """Nodes and normalised weights of the Schulz distribution of mean `mean`
+    and relative standard deviation p; p == 0 or n == 1 gives the mean."""
+    if p <= 0.0 or n <= 1:
+        return np.array([float(mean)]), np.array([1.0])
+    z = 1.0 / (p * p) - 1.0
+    x, w = gauss_laguerre_gen(n, z)
+    return mean * x / (z + 1.0), w
+
+
+def axis_from_angles(theta: float, phi: float):
+    n = np.array([math.sin(theta) * math.cos(phi), math.sin(theta) * math.sin(phi),
+                  math.cos(theta)])
+    e_t = np.array([math.cos(theta) * math.cos(phi), math.cos(theta) * math.sin(phi),
+                    -math.sin(theta)])
+    e_p = np.array([-math.sin(phi), math.cos(phi), 0.0])
+    return n, e_t, e_p
+
+
+def orientation_nodes(theta, phi, sigma, n_gamma, n_psi, isotropic=False):
+    """Axis unit vectors [n,3] and normalised weights [n] of the orientation
+    distribution (see the module docstring)."""
+    n, e_t, e_p = axis_from_angles(theta, phi)
+    if not isotropic and (sigma <= 0.0 or n_gamma * n_psi <= 1):
+        return n[None, :].copy(), np.array([1.0])
+    gmax = math.pi if isotropic else min(3.0 * sigma, math.pi)
+    xg, wg = gauss_legendre(n_gamma)
+    xp, wp = gauss_legendre(n_psi)
+    gam = 0.5 * gmax * (xg + 1.0)
+    wgam = 0.5 * gmax * wg * np.sin(gam)
+    if not isotropic:
+        wgam = wgam * np.exp(-gam * gam / (2.0 * sigma * sigma))
+    psi = math.pi * (xp + 1.0)
+    wpsi = math.pi * wp
+    G, P = np.meshgrid(gam, psi, indexing="ij")
+    W = np.outer(wgam, wpsi)
+    c = (np.cos(G)[..., None] * n + np.sin(G)[..., None] *
+         (np.cos(P)[..., None] * e_t + np.sin(P)[..., None] * e_p))
+    W = W.reshape(-1)
+    return c.reshape(-1, 3), W / W.sum()
+
+
+# ----------------------------------------------------------- marshalling
+
+class Prepared:
+    """A model bound to its quadrature tables (keeps the arrays alive)."""
+
+    def __init__(self, model):
+        m = model if isinstance(model, dict) else model.as_dict()
+        self.m = m
+        kind = int(m["kind"])
+        self.poly_r, self.poly_w = schulz_nodes(m["radius"], m["poly"], int(m["n_poly"]))
+        if kind in (2, 3):
+            self.orient_c, self.orient_w = orientation_nodes(
+                m["axis_theta"], m["axis_phi"], m["sigma_orient"], int(m["n_gamma"]),
+                int(m["n_psi"]), bool(m["isotropic"]))
+        else:
+            self.orient_c, self.orient_w = np.zeros((1, 3)), np.ones(1)
+        self.poly_r = np.ascontiguousarray(self.poly_r, dtype=np.float64)
+        self.poly_w = np.ascontiguousarray(self.poly_w, dtype=np.float64)
+        self.orient_c = np.ascontiguousarray(self.orient_c, dtype=np.float64)
+        self.orient_w = np.ascontiguousarray(self.orient_w, dtype=np.float64)
+        self.c = _Model(kind=kind, sq_kind=int(m["sq_kind"]), n_poly=len(self.poly_r),
+                        n_orient=len(self.orient_w), radius=m["radius"],
+                        thickness=m["thickness"], length=m["length"],
+                        radius_polar=m["radius_polar"], sld=m["sld"],
+                        sld_shell=m["sld_shell"], sld_solvent=m["sld_solvent"],
+                        volume_fraction=m["volume_fraction"], sq_radius=m["sq_radius"],
+                        sq_fraction=m["sq_fraction"],
+                        poly_r=self.poly_r.ctypes.data_as(_DP),
+                        poly_w=self.poly_w.ctypes.data_as(_DP),
+                        orient_c=self.orient_c.ctypes.data_as(_DP),
+                        orient_w=self.orient_w.ctypes.data_as(_DP))
+
+
+def _inst(instrument):
+    d = instrument if isinstance(instrument, dict) else instrument.as_dict()
+    return _Instrument(**{k: (int(v) if k in ("nx", "ny") else float(v)) for k, v in d.items()})
+
+
+# ------------------------------------------------------------- public API
+
+def philox4x32_10(ctr, key):
+    c = (ctypes.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
+    k = (ctypes.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+    o = (ctypes.c_uint32 * 4)()
+    lib().oracle_philox4x32_10(c, k, o)
+    return list(o)
+
+
+def sphere_f(x):
+    return lib().oracle_sphere_f(float(x))
+
+
+def cyl_a(x):
+    return lib().oracle_cyl_a(float(x))
+
+
+def sinc(x):
+    return lib().oracle_sinc(float(x))
+
+
+def sq_py(q, radius, phi):
+    return lib().oracle_sq_py(float(q), float(radius), float(phi))
+
+
+def dsigma(model, q_xyz):
+    """dSigma/dOmega in 1/angstrom at scattering vectors q_xyz [n,3] (1/angstrom)."""
+    prep = model if isinstance(model, Prepared) else Prepared(model)
+    q = np.ascontiguousarray(np.asarray(q_xyz, dtype=np.float64).reshape(-1, 3))
+    out = np.empty(q.shape[0], dtype=np.float64)
+    lib().oracle_dsigma_many(ctypes.byref(prep.c), q.ctypes.data_as(_DP), q.shape[0],
+                             out.ctypes.data_as(_DP))
+    return out
+
+
+def trace(instrument, model, n, seed, first=0, exp_id=0, threads=0):
+    """Trace neutrons [first, first+n). Returns dict(sum_w, sum_w2, count, trans)
+    with detector arrays of shape (ny, nx)."""
+    inst = _inst(instrument)
+    prep = model if isinstance(model, Prepared) else Prepared(model)
+    npix = inst.nx * inst.ny
+    sw = np.zeros(npix)
+    sw2 = np.zeros(npix)
+    cnt = np.zeros(npix, dtype=np.uint64)
+    tr = ctypes.c_double(0.0)
+    lib().oracle_trace(ctypes.byref(inst), ctypes.byref(prep.c), int(seed), int(exp_id),
+                       int(first), int(n), sw.ctypes.data_as(_DP), sw2.ctypes.data_as(_DP),
+                       cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), ctypes.byref(tr),
+                       int(threads))
+    shp = (inst.ny, inst.nx)
+    return dict(sum_w=sw.reshape(shp), sum_w2=sw2.reshape(shp), count=cnt.reshape(shp),
+                trans=tr.value)
+
+
+def records(instrument, model, n, seed, first=0, exp_id=0):
+    """Per-neutron (pixel, weight); pixel -1 marks a history that missed."""
+    inst = _inst(instrument)
+    prep = model if isinstance(model, Prepared) else Prepared(model)
+    pix = np.empty(n, dtype=np.int64)
+    w = np.empty(n, dtype=np.float64)
+    lib().oracle_records(ctypes.byref(inst), ctypes.byref(prep.c), int(seed), int(exp_id),
+                         int(first), int(n), pix.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                         w.ctypes.data_as(_DP))
+    return pix, w
+
+
+def sample_lambda(lambda0, drel, u):
+    return lib().oracle_sample_lambda(float(lambda0), float(drel), float(u))
+
+
+def num_threads():
+    return lib().oracle_num_threads()

@@ -1,0 +1,422 @@
+/*
+ * FP64 CPU oracle of the SANS Monte Carlo trace.
+ *
+ * TEST INFRASTRUCTURE ONLY. Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg use this file. It shares no code, header,
+ * table or constant with the CUDA library and must never be linked into it.
+ *
+ * It follows the method step by step in double precision, in the order the
+ * paper describes one neutron history (Sec. II.A, instrument chain: source,
+ * collimation, sample, 2D position-sensitive detector; single scattering,
+ * Sec. I), and evaluates the averaged model by its plain definition:
+ *
+ *   amplitude A(Q) = integral of drho exp(-i Q.r) dV          (Eq. 1)
+ *   intensity  I = (Phi / V) A A*                             (Eq. 2)
+ *   dilute isotropic I = n drho^2 V^2 P(Q) S(Q)               (Eq. 3)
+ *   model M = A* A / V                                        (Eq. 4)
+ *   uniaxial particles A(Q_AB, Q_C)                           (Eq. 7)
+ *   cylinder amplitude, volume pi r^2 L                       (Eq. 8)
+ *
+ * The quadrature nodes (Schulz polydispersity, orientation distribution) are
+ * computed by the Python side of the oracle and passed in as arrays.
+ * Special functions come from the C library (sin, cos, j1, exp, sqrt).
+ *
+ * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror and Shaw, SC'11),
+ * key = (seed low 32 bits, seed high 32 bits), counter = (draw block,
+ * experiment id, neutron index low 32 bits, neutron index high 32 bits).
+ * With draw block 0 and experiment 0, neutron i reads the same four words as
+ * block i of cuRAND's host Philox4x32-10 generator seeded with the same seed.
+ */
+#define _DEFAULT_SOURCE
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define PI 3.14159265358979323846
+
+/* ---------------------------------------------------------------- Philox */
+
+void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* uniform on (0,1): 23 random bits plus one half, exact in float and double */
+static double u01(uint32_t x) { return ((double)(x >> 9) + 0.5) * (1.0 / 8388608.0); }
+
+/* ------------------------------------------------------------ structures */
+
+typedef struct {
+    double lambda0, dlambda_rel;
+    double ap1_radius, ap1_z, ap2_radius, ap2_z;
+    double sample_half_x, sample_half_y, sample_thickness;
+    double mu;
+    double det_distance, pixel_x, pixel_y;
+    int64_t nx, ny;
+} oracle_instrument;
+
+typedef struct {
+    int64_t kind;          /* 0 sphere, 1 core-shell, 2 cylinder, 3 ellipsoid */
+    int64_t sq_kind;       /* 0 none, 1 Percus-Yevick hard spheres */
+    int64_t n_poly;        /* polydispersity nodes */
+    int64_t n_orient;      /* orientation nodes */
+    double radius, thickness, length, radius_polar;
+    double sld, sld_shell, sld_solvent;
+    double volume_fraction;
+    double sq_radius, sq_fraction;
+    const double *poly_r;  /* [n_poly] radii of the polydisperse radius */
+    const double *poly_w;  /* [n_poly] normalised weights */
+    const double *orient_c;/* [n_orient][3] particle axis unit vectors */
+    const double *orient_w;/* [n_orient] normalised weights */
+} oracle_model;
+
+/* --------------------------------------------------------- model pieces */
+
+/* normalised sphere amplitude 3 (sin x - x cos x) / x^3, f(0) = 1 */
+double oracle_sphere_f(double x)
+{
+    x = fabs(x);
+    if (x < 0.1) {
+        /* Taylor series: sum_m (-1)^m 6 (m+1) x^(2m) / (2m+3)! */
+        double t = x * x;
+        return 1.0 - t / 10.0 * (1.0 - t / 28.0 * (1.0 - t / 54.0 * (1.0 - t / 88.0
+                                                        * (1.0 - t / 130.0))));
+    }
+    return 3.0 * (sin(x) - x * cos(x)) / (x * x * x);
+}
+
+/* 2 J1(x) / x, value 1 at x = 0 */
+double oracle_cyl_a(double x)
+{
+    x = fabs(x);
+    if (x < 1e-6) return 1.0 - x * x / 8.0;
+    return 2.0 * j1(x) / x;
+}
+
+/* sin(y) / y */
+double oracle_sinc(double y)
+{
+    y = fabs(y);
+    if (y < 1e-8) return 1.0;
+    return sin(y) / y;
+}
+
+/* Taylor coefficient (of A^(2m)) of each bracket of the Percus-Yevick G(A).
+ * b1 = sin A - A cos A
+ * b2 = 2 A sin A + (2 - A^2) cos A - 2
+ * b3 = -A^4 cos A + 4 [ (3 A^2 - 6) cos A + (A^3 - 6 A) sin A + 6 ]
+ * sin A = sum (-1)^n A^(2n+1)/(2n+1)!,  cos A = sum (-1)^n A^(2n)/(2n)!    */
+static double fact(int n) { double f = 1.0; for (int i = 2; i <= n; ++i) f *= i; return f; }
+static double sgn(int n) { return (n % 2 == 0) ? 1.0 : -1.0; }
+/* coefficient of A^k in sin A and cos A */
+static double sin_c(int k) { return (k % 2 == 1) ? sgn((k - 1) / 2) / fact(k) : 0.0; }
+static double cos_c(int k) { return (k % 2 == 0) ? sgn(k / 2) / fact(k) : 0.0; }
+static double b1_c(int k) { return sin_c(k) - (k >= 1 ? cos_c(k - 1) : 0.0); }
+static double b2_c(int k)
+{
+    double c = (k >= 1 ? 2.0 * sin_c(k - 1) : 0.0) + 2.0 * cos_c(k)
+             - (k >= 2 ? cos_c(k - 2) : 0.0) - (k == 0 ? 2.0 : 0.0);
+    return c;
+}
+static double b3_c(int k)
+{
+    double c = -(k >= 4 ? cos_c(k - 4) : 0.0);
+    double in = (k >= 2 ? 3.0 * cos_c(k - 2) : 0.0) - 6.0 * cos_c(k)
+              + (k >= 3 ? sin_c(k - 3) : 0.0) - (k >= 1 ? 6.0 * sin_c(k - 1) : 0.0)
+              + (k == 0 ? 6.0 : 0.0);
+    return c + 4.0 * in;
+}
+
+/* Percus-Yevick hard-sphere structure factor (Wertheim / Thiele closed form).
+ * S(q) = 1 / (1 + 24 phi G(A) / A), A = 2 q R, with
+ * G(A) = alpha b1/A^2 + beta b2/A^3 + gamma b3/A^5,
+ * alpha = (1+2phi)^2/(1-phi)^4, beta = -6 phi (1+phi/2)^2/(1-phi)^4,
+ * gamma = phi alpha / 2.                                                    */
+double oracle_sq_py(double q, double radius, double phi)
+{
+    double A = 2.0 * fabs(q) * radius;
+    double d = pow(1.0 - phi, 4);
+    double alpha = (1.0 + 2.0 * phi) * (1.0 + 2.0 * phi) / d;
+    double beta = -6.0 * phi * (1.0 + 0.5 * phi) * (1.0 + 0.5 * phi) / d;
+    double gamma = 0.5 * phi * alpha;
+    double GA; /* G(A)/A */
+    if (A < 0.5) {
+        /* series of each bracket: b1 ~ A^3, b2 ~ A^4, b3 ~ A^6 */
+        double s1 = 0.0, s2 = 0.0, s3 = 0.0, Ak;
+        Ak = 1.0; for (int k = 3; k <= 3 + 30; ++k) { s1 += b1_c(k) * Ak; Ak *= A; }
+        Ak = 1.0; for (int k = 4; k <= 4 + 30; ++k) { s2 += b2_c(k) * Ak; Ak *= A; }
+        Ak = 1.0; for (int k = 6; k <= 6 + 30; ++k) { s3 += b3_c(k) * Ak; Ak *= A; }
+        /* b1/A^3 = s1, b2/A^4 = s2, b3/A^6 = s3 */
+        GA = alpha * s1 + beta * s2 + gamma * s3;
+    } else {
+        double sA = sin(A), cA = cos(A);
+        double b1 = sA - A * cA;
+        double b2 = 2.0 * A * sA + (2.0 - A * A) * cA - 2.0;
+        double b3 = -A * A * A * A * cA
+                  + 4.0 * ((3.0 * A * A - 6.0) * cA + (A * A * A - 6.0 * A) * sA + 6.0);
+        GA = alpha * b1 / (A * A * A) + beta * b2 / (A * A * A * A)
+           + gamma * b3 / (A * A * A * A * A * A);
+    }
+    return 1.0 / (1.0 + 24.0 * phi * GA);
+}
+
+static double sphere_volume(double r) { return 4.0 / 3.0 * PI * r * r * r; }
+
+/* Scattering cross section per unit volume dSigma/dOmega(Q) in 1/angstrom:
+ * (phi / <V>) <|F|^2> S(Q), F = drho V f, averages over the polydispersity
+ * nodes (and, for the uniaxial models, over the orientation nodes).      */
+double oracle_dsigma(const oracle_model *m, const double q[3])
+{
+    double qq = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
+    double sum = 0.0, vmean = 0.0;
+    int64_t np = m->n_poly;
+    if (m->kind == 0) {              /* sphere */
+        double drho = m->sld - m->sld_solvent;
+        for (int64_t i = 0; i < np; ++i) {
+            double r = m->poly_r[i], V = sphere_volume(r);
+            double F = drho * V * oracle_sphere_f(qq * r);
+            sum += m->poly_w[i] * F * F;
+            vmean += m->poly_w[i] * V;
+        }
+    } else if (m->kind == 1) {       /* core-shell sphere: core radius polydisperse */
+        for (int64_t i = 0; i < np; ++i) {
+            double rc = m->poly_r[i], ro = rc + m->thickness;
+            double Vc = sphere_volume(rc), Vo = sphere_volume(ro);
+            double F = (m->sld - m->sld_shell) * Vc * oracle_sphere_f(qq * rc)
+                     + (m->sld_shell - m->sld_solvent) * Vo * oracle_sphere_f(qq * ro);
+            sum += m->poly_w[i] * F * F;
+            vmean += m->poly_w[i] * Vo;
+        }
+    } else if (m->kind == 2) {       /* cylinder: radius polydisperse, length fixed */
+        double drho = m->sld - m->sld_solvent;
+        for (int64_t i = 0; i < np; ++i)
+            vmean += m->poly_w[i] * PI * m->poly_r[i] * m->poly_r[i] * m->length;
+        for (int64_t o = 0; o < m->n_orient; ++o) {
+            const double *c = m->orient_c + 3 * o;
+            double qc = q[0] * c[0] + q[1] * c[1] + q[2] * c[2];
+            double x0 = q[1] * c[2] - q[2] * c[1];
+            double x1 = q[2] * c[0] - q[0] * c[2];
+            double x2 = q[0] * c[1] - q[1] * c[0];
+            double qab = sqrt(x0 * x0 + x1 * x1 + x2 * x2);
+            double s = oracle_sinc(0.5 * qc * m->length);
+            double inner = 0.0;
+            for (int64_t i = 0; i < np; ++i) {
+                double r = m->poly_r[i];
+                double V = PI * r * r * m->length;
+                double F = drho * V * s * oracle_cyl_a(qab * r);
+                inner += m->poly_w[i] * F * F;
+            }
+            sum += m->orient_w[o] * inner;
+        }
+    } else {                         /* ellipsoid of revolution: equatorial radius polydisperse */
+        double drho = m->sld - m->sld_solvent;
+        double rp = m->radius_polar;
+        for (int64_t i = 0; i < np; ++i)
+            vmean += m->poly_w[i] * 4.0 / 3.0 * PI * rp * m->poly_r[i] * m->poly_r[i];
+        for (int64_t o = 0; o < m->n_orient; ++o) {
+            const double *c = m->orient_c + 3 * o;
+            double qc = q[0] * c[0] + q[1] * c[1] + q[2] * c[2];
+            double x0 = q[1] * c[2] - q[2] * c[1];
+            double x1 = q[2] * c[0] - q[0] * c[2];
+            double x2 = q[0] * c[1] - q[1] * c[0];
+            double qab2 = x0 * x0 + x1 * x1 + x2 * x2;
+            double inner = 0.0;
+            for (int64_t i = 0; i < np; ++i) {
+                double re = m->poly_r[i];
+                double V = 4.0 / 3.0 * PI * rp * re * re;
+                double x = sqrt(re * re * qab2 + rp * rp * qc * qc);
+                double F = drho * V * oracle_sphere_f(x);
+                inner += m->poly_w[i] * F * F;
+            }
+            sum += m->orient_w[o] * inner;
+        }
+    }
+    double S = 1.0;
+    if (m->sq_kind == 1) S = oracle_sq_py(qq, m->sq_radius, m->sq_fraction);
+    return m->volume_fraction / vmean * sum * S;
+}
+
+void oracle_dsigma_many(const oracle_model *m, const double *q, int64_t n, double *out)
+{
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) out[i] = oracle_dsigma(m, q + 3 * i);
+}
+
+/* ------------------------------------------------------------- geometry */
+
+/* source wavelength from one uniform: triangular on [l0 (1-d), l0 (1+d)],
+ * mode l0, by inverse cumulative distribution */
+double oracle_sample_lambda(double lambda0, double drel, double u)
+{
+    double T = (u < 0.5) ? sqrt(2.0 * u) - 1.0 : 1.0 - sqrt(2.0 * (1.0 - u));
+    return lambda0 * (1.0 + drel * T);
+}
+
+/* entry and exit ray parameters of the sample box |x|<=hx, |y|<=hy, 0<=z<=t.
+ * Returns 0 on a miss. */
+static int slab(const oracle_instrument *in, const double o[3], const double d[3],
+                double *t_in, double *t_out)
+{
+    double lo[3] = {-in->sample_half_x, -in->sample_half_y, 0.0};
+    double hi[3] = {in->sample_half_x, in->sample_half_y, in->sample_thickness};
+    double a = -INFINITY, b = INFINITY;
+    for (int k = 0; k < 3; ++k) {
+        if (d[k] == 0.0) {
+            if (o[k] < lo[k] || o[k] > hi[k]) return 0;
+            continue;
+        }
+        double t1 = (lo[k] - o[k]) / d[k], t2 = (hi[k] - o[k]) / d[k];
+        if (t1 > t2) { double s = t1; t1 = t2; t2 = s; }
+        if (t1 > a) a = t1;
+        if (t2 < b) b = t2;
+    }
+    if (a < 0.0) a = 0.0;
+    if (b <= a) return 0;
+    *t_in = a; *t_out = b;
+    return 1;
+}
+
+/* One neutron history. Returns 1 if it scattered onto the detector, with
+ * its pixel and weight; *w_trans gets the unscattered (transmitted) weight. */
+int oracle_history(const oracle_instrument *in, const oracle_model *m, uint64_t seed,
+                   uint32_t exp_id, uint64_t index, int64_t *pixel, double *w,
+                   double *w_trans)
+{
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t c0[4] = {0u, exp_id, (uint32_t)index, (uint32_t)(index >> 32)};
+    uint32_t c1[4] = {1u, exp_id, (uint32_t)index, (uint32_t)(index >> 32)};
+    uint32_t x[8];
+    oracle_philox4x32_10(c0, key, x);
+    oracle_philox4x32_10(c1, key, x + 4);
+
+    /* source: triangular wavelength spread by inverse CDF */
+    double lambda = oracle_sample_lambda(in->lambda0, in->dlambda_rel, u01(x[0]));
+    /* collimation: uniform points on the two pinhole discs */
+    double r1 = in->ap1_radius * sqrt(u01(x[1])), f1 = 2.0 * PI * u01(x[2]);
+    double r2 = in->ap2_radius * sqrt(u01(x[3])), f2 = 2.0 * PI * u01(x[4]);
+    double p1[3] = {r1 * cos(f1), r1 * sin(f1), in->ap1_z};
+    double p2[3] = {r2 * cos(f2), r2 * sin(f2), in->ap2_z};
+    double d[3] = {p2[0] - p1[0], p2[1] - p1[1], p2[2] - p1[2]};
+    double dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    double k_in[3] = {d[0] / dn, d[1] / dn, d[2] / dn};
+    /* sample */
+    double t_in, t_out;
+    if (!slab(in, p2, k_in, &t_in, &t_out)) { *w_trans = 1.0; return 0; }
+    double l = t_out - t_in;
+    *w_trans = exp(-in->mu * l);
+    double s = u01(x[5]) * l;
+    double ps[3] = {p2[0] + (t_in + s) * k_in[0], p2[1] + (t_in + s) * k_in[1],
+                    p2[2] + (t_in + s) * k_in[2]};
+    /* detector point: pixel from the integer draw, position inside it from the remainder */
+    uint64_t mx = (uint64_t)(x[6] >> 9) * (uint64_t)in->nx;
+    uint64_t my = (uint64_t)(x[7] >> 9) * (uint64_t)in->ny;
+    int64_t ix = (int64_t)(mx >> 23), iy = (int64_t)(my >> 23);
+    double fx = ((double)(mx & 0x7FFFFF) + 0.5) / 8388608.0;
+    double fy = ((double)(my & 0x7FFFFF) + 0.5) / 8388608.0;
+    double pd[3] = {((double)ix + fx) * in->pixel_x - 0.5 * (double)in->nx * in->pixel_x,
+                    ((double)iy + fy) * in->pixel_y - 0.5 * (double)in->ny * in->pixel_y,
+                    in->det_distance};
+    double v[3] = {pd[0] - ps[0], pd[1] - ps[1], pd[2] - ps[2]};
+    double rr = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    double k_out[3] = {v[0] / rr, v[1] / rr, v[2] / rr};
+    /* solid-angle factor of the area-uniform detector point */
+    double area = (double)in->nx * in->pixel_x * (double)in->ny * in->pixel_y;
+    double domega = area * k_out[2] / (rr * rr);
+    /* scattering vector Q = k_f - k_i in 1/angstrom */
+    double k = 2.0 * PI / lambda;
+    double q[3] = {k * (k_out[0] - k_in[0]), k * (k_out[1] - k_in[1]), k * (k_out[2] - k_in[2])};
+    double ds = oracle_dsigma(m, q) * 1e10; /* 1/angstrom -> 1/m */
+    /* path to the exit of the sample along the scattered direction */
+    double e_in, e_out, l_out = 0.0;
+    if (slab(in, ps, k_out, &e_in, &e_out)) l_out = e_out - e_in;
+    double att = exp(-in->mu * (s + l_out));
+    *w = l * ds * domega * att;
+    *pixel = iy * in->nx + ix;
+    return 1;
+}
+
+/* Trace neutrons [first, first+n) and accumulate the detector in place.
+ * sum_w, sum_w2: [ny*nx] doubles; count: [ny*nx] uint64; trans: scalar. */
+void oracle_trace(const oracle_instrument *in, const oracle_model *m, uint64_t seed,
+                  uint32_t exp_id, uint64_t first, uint64_t n, double *sum_w,
+                  double *sum_w2, uint64_t *count, double *trans, int threads)
+{
+    int64_t npix = in->nx * in->ny;
+    int nt = 1;
+#ifdef _OPENMP
+    nt = threads > 0 ? threads : omp_get_max_threads();
+#endif
+    double *pw = calloc((size_t)nt * npix, sizeof(double));
+    double *pw2 = calloc((size_t)nt * npix, sizeof(double));
+    uint64_t *pc = calloc((size_t)nt * npix, sizeof(uint64_t));
+    double *pt = calloc((size_t)nt, sizeof(double));
+#pragma omp parallel num_threads(nt)
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        double *w1 = pw + (size_t)tid * npix, *w2 = pw2 + (size_t)tid * npix;
+        uint64_t *c = pc + (size_t)tid * npix;
+        double tr = 0.0;
+#pragma omp for schedule(static)
+        for (int64_t j = 0; j < (int64_t)n; ++j) {
+            int64_t pix; double w, wt;
+            if (oracle_history(in, m, seed, exp_id, first + (uint64_t)j, &pix, &w, &wt)) {
+                w1[pix] += w; w2[pix] += w * w; c[pix] += 1;
+            }
+            tr += wt;
+        }
+        pt[tid] = tr;
+    }
+    for (int t = 0; t < nt; ++t) {
+        for (int64_t p = 0; p < npix; ++p) {
+            sum_w[p] += pw[(size_t)t * npix + p];
+            sum_w2[p] += pw2[(size_t)t * npix + p];
+            count[p] += pc[(size_t)t * npix + p];
+        }
+        *trans += pt[t];
+    }
+    free(pw); free(pw2); free(pc); free(pt);
+}
+
+/* Per-neutron records for brute-force comparisons: pixel (-1 on a miss), weight. */
+void oracle_records(const oracle_instrument *in, const oracle_model *m, uint64_t seed,
+                    uint32_t exp_id, uint64_t first, uint64_t n, int64_t *pixel, double *w)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t j = 0; j < (int64_t)n; ++j) {
+        int64_t pix; double ww, wt;
+        if (oracle_history(in, m, seed, exp_id, first + (uint64_t)j, &pix, &ww, &wt)) {
+            pixel[j] = pix; w[j] = ww;
+        } else {
+            pixel[j] = -1; w[j] = 0.0;
+        }
+    }
+}
+
+int oracle_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

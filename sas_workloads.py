@@ -1,0 +1,179 @@
+"""Seeded synthetic workloads for the SANS Monte Carlo trace.
+
+This module holds only input descriptions and seeded parameter draws. It
+contains none of the method's arithmetic (no RNG stream of the trace, no
+geometry, no form factor), so both the FP64 oracle and the CUDA path may use
+it as their common source of inputs.
+
+Units: instrument lengths in metres, wavelength and particle sizes in
+angstrom, scattering-length densities in 1/angstrom^2, angles in radians.
+The beam runs along +z; the sample front face sits at z = 0.
+
+Workloads (the paper's KWS-1 instrument description and its measured data
+set are not available, so these synthetic set-ups stand in for them; the
+instrument chain follows Sec. II.A: source, collimation, sample, 2D PSD):
+
+* ``sphere``      monodisperse sphere R=50, contrast 2e-6, phi=0.01, no S(Q),
+                  128x128 detector, 1e6 neutrons, traced in FP64.
+* ``core_shell``  core 40 + shell 10, SLDs (1, 3, 6)e-6 (core, shell, solvent),
+                  Schulz sigma/R = 0.1 on the core radius with 40 nodes,
+                  Percus-Yevick hard spheres at phi = 0.2, R_hs = 50,
+                  128x128 detector, 1e9 neutrons, FP32.
+* ``cylinder``    R=20, L=400, axis Gaussian (sigma 15 deg) about x (normal to
+                  the beam), Schulz 0.1 on R with 40 nodes, 76x76 orientation
+                  nodes, 256x256 detector, 1e9 neutrons, FP32.
+* ``batched``     4096 experiments, model kind uniform over the four kinds,
+                  sizes uniform in [10, 200], polydispersity uniform in
+                  [0, 0.3], neutron counts log-uniform in [1e5, 1e8], 128x128
+                  detector each.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field, asdict
+
+import numpy as np
+
+SPHERE, CORE_SHELL, CYLINDER, ELLIPSOID = 0, 1, 2, 3
+MODEL_NAMES = {SPHERE: "sphere", CORE_SHELL: "core_shell", CYLINDER: "cylinder",
+               ELLIPSOID: "ellipsoid"}
+SQ_NONE, SQ_HARD_SPHERE_PY = 0, 1
+FP32, FP64 = 0, 1
+
+
+@dataclass
+class Instrument:
+    lambda0: float = 6.0            # angstrom
+    dlambda_rel: float = 0.10       # half width of the triangular spread (fraction of lambda0)
+    ap1_radius: float = 4.0e-3      # m (8 mm diameter)
+    ap1_z: float = -2.0             # m
+    ap2_radius: float = 2.0e-3      # m (4 mm diameter)
+    ap2_z: float = 0.0              # m, immediately in front of the sample
+    sample_half_x: float = 5.0e-3   # m (10 mm wide)
+    sample_half_y: float = 5.0e-3   # m (10 mm high)
+    sample_thickness: float = 1.0e-3  # m
+    mu: float = 0.0                 # 1/m, attenuation inside the sample
+    det_distance: float = 5.0       # m from the sample front face
+    pixel_x: float = 5.0e-3         # m
+    pixel_y: float = 5.0e-3         # m
+    nx: int = 128
+    ny: int = 128
+
+    def as_dict(self):
+        return asdict(self)
+
+
+@dataclass
+class Model:
+    kind: int = SPHERE
+    sq_kind: int = SQ_NONE
+    precision: int = FP32
+    n_poly: int = 1
+    n_gamma: int = 1
+    n_psi: int = 1
+    isotropic: int = 0
+    radius: float = 50.0            # sphere R, core radius, cylinder R, ellipsoid equatorial R
+    thickness: float = 0.0          # core-shell shell thickness
+    length: float = 0.0             # cylinder length
+    radius_polar: float = 0.0       # ellipsoid polar radius (along the axis)
+    sld: float = 2.0e-6             # particle (core) SLD
+    sld_shell: float = 0.0
+    sld_solvent: float = 0.0
+    volume_fraction: float = 0.01
+    poly: float = 0.0               # Schulz relative width of the polydisperse radius
+    sigma_orient: float = 0.0       # rad, Gaussian width of the axis distribution
+    axis_theta: float = 0.5 * math.pi  # rad, polar angle of the mean axis from +z
+    axis_phi: float = 0.0           # rad, azimuth of the mean axis
+    sq_radius: float = 0.0
+    sq_fraction: float = 0.0
+
+    def as_dict(self):
+        return asdict(self)
+
+
+def instrument(nx=128, ny=128, **kw) -> Instrument:
+    return Instrument(nx=nx, ny=ny, **kw)
+
+
+def sphere_config():
+    """Monodisperse sphere, FP64 trace, 1e6 neutrons, seed 1."""
+    m = Model(kind=SPHERE, precision=FP64, radius=50.0, sld=2.0e-6, sld_solvent=0.0,
+              volume_fraction=0.01, n_poly=1)
+    return dict(name="sphere", instrument=instrument(), model=m, n_neutrons=10**6, seed=1)
+
+
+def core_shell_config():
+    """Core-shell sphere + Schulz(40) + Percus-Yevick, FP32, 1e9 neutrons, seed 1."""
+    m = Model(kind=CORE_SHELL, sq_kind=SQ_HARD_SPHERE_PY, precision=FP32, radius=40.0,
+              thickness=10.0, sld=1.0e-6, sld_shell=3.0e-6, sld_solvent=6.0e-6,
+              volume_fraction=0.2, poly=0.1, n_poly=40, sq_radius=50.0, sq_fraction=0.2)
+    return dict(name="core_shell", instrument=instrument(), model=m, n_neutrons=10**9, seed=1)
+
+
+def cylinder_config():
+    """Oriented polydisperse cylinder, 76x76 orientation nodes, 256x256, FP32."""
+    m = Model(kind=CYLINDER, precision=FP32, radius=20.0, length=400.0, sld=2.0e-6,
+              sld_solvent=0.0, volume_fraction=0.01, poly=0.1, n_poly=40,
+              sigma_orient=math.radians(15.0), axis_theta=0.5 * math.pi, axis_phi=0.0,
+              n_gamma=76, n_psi=76)
+    return dict(name="cylinder", instrument=instrument(nx=256, ny=256), model=m,
+                n_neutrons=10**9, seed=1)
+
+
+CONFIGS = {"sphere": sphere_config, "core_shell": core_shell_config,
+           "cylinder": cylinder_config}
+
+
+def batched_models(n_exp=4096, seed=1, n_poly=40, n_gamma=76, n_psi=76,
+                   count_range=(1e5, 1e8)):
+    """Draw the batched set of experiments (numpy PCG64, seeded).
+
+    Model kind uniform over {sphere, core-shell, cylinder, ellipsoid}; every
+    size parameter uniform in [10, 200] angstrom; polydispersity uniform in
+    [0, 0.3]; anisotropic particles get a Gaussian axis spread uniform in
+    [0, 30] degrees about an axis uniform on the sphere; no structure factor;
+    neutron counts log-uniform in ``count_range``.
+    Returns (list[Model], np.ndarray[uint64] counts).
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    kinds = rng.integers(0, 4, size=n_exp)
+    sizes = rng.uniform(10.0, 200.0, size=(n_exp, 3))
+    polys = rng.uniform(0.0, 0.3, size=n_exp)
+    sig = np.radians(rng.uniform(0.0, 30.0, size=n_exp))
+    cos_t = rng.uniform(-1.0, 1.0, size=n_exp)
+    phis = rng.uniform(0.0, 2.0 * math.pi, size=n_exp)
+    slds = rng.uniform(0.5e-6, 6.0e-6, size=(n_exp, 2))
+    lo, hi = math.log(count_range[0]), math.log(count_range[1])
+    counts = np.exp(rng.uniform(lo, hi, size=n_exp)).astype(np.uint64)
+    models = []
+    for e in range(n_exp):
+        k = int(kinds[e])
+        p = float(polys[e])
+        npoly = n_poly if p > 0.0 else 1
+        m = Model(kind=k, precision=FP32, radius=float(sizes[e, 0]), sld=float(slds[e, 0]),
+                  sld_solvent=0.0, volume_fraction=0.01, poly=p, n_poly=npoly)
+        if k == CORE_SHELL:
+            m.thickness = float(sizes[e, 1])
+            m.sld_shell = float(slds[e, 1])
+            m.sld_solvent = 0.0
+        if k in (CYLINDER, ELLIPSOID):
+            if k == CYLINDER:
+                m.length = float(sizes[e, 1])
+            else:
+                m.radius_polar = float(sizes[e, 1])
+            m.sigma_orient = float(sig[e])
+            m.axis_theta = float(math.acos(cos_t[e]))
+            m.axis_phi = float(phis[e])
+            if m.sigma_orient > 0.0:
+                m.n_gamma, m.n_psi = n_gamma, n_psi
+        models.append(m)
+    return models, counts
+
+
+def random_q(n, qmax, seed):
+    """Uniform random scattering vectors in a ball of radius qmax (1/angstrom)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    v = rng.normal(size=(n, 3))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    r = qmax * rng.uniform(0.0, 1.0, size=n) ** (1.0 / 3.0)
+    return v * r[:, None]

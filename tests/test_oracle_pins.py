@@ -1,0 +1,520 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Every check compares the oracle with something other than itself: a library
+routine (cuRAND's host Philox generator, scipy special functions and
+quadrature, numpy's Gauss-Legendre rule), a closed form, a limit or an
+identity, or an independent numpy Monte Carlo of the same estimator.
+"""
+import ctypes
+import math
+
+import numpy as np
+import pytest
+import scipy.integrate as si
+import scipy.special as sp
+
+import oracle
+import sas_workloads as W
+
+pytestmark = pytest.mark.filterwarnings("ignore::scipy.integrate.IntegrationWarning")
+
+
+# ------------------------------------------------------------------ Philox
+
+def _curand():
+    for name in ("libcurand.so", "libcurand.so.10", "/usr/local/cuda/lib64/libcurand.so"):
+        try:
+            return ctypes.CDLL(name)
+        except OSError:
+            continue
+    pytest.skip("libcurand not available")
+
+
+def _curand_blocks(lib, seed, first_block, n):
+    gen = ctypes.c_void_p()
+    assert lib.curandCreateGeneratorHost(ctypes.byref(gen), 161) == 0  # PHILOX4_32_10
+    try:
+        assert lib.curandSetPseudoRandomGeneratorSeed(gen, ctypes.c_ulonglong(seed)) == 0
+        assert lib.curandSetGeneratorOffset(gen, ctypes.c_ulonglong(4 * first_block)) == 0
+        buf = (ctypes.c_uint32 * (4 * n))()
+        assert lib.curandGenerate(gen, buf, ctypes.c_size_t(4 * n)) == 0
+    finally:
+        lib.curandDestroyGenerator(gen)
+    return np.array(buf, dtype=np.uint32).reshape(n, 4)
+
+
+@pytest.mark.parametrize("seed,first", [(0, 0), (1, 0), (0xFFFFFFFFFFFFFFFF, 7),
+                                        (0x123456789ABCDEF0, 65533), (12345, 987654)])
+def test_philox_matches_curand_host_generator(seed, first):
+    """Philox4x32-10 (Salmon et al., SC'11) against cuRAND's host generator.
+    That generator's block b is Philox at counter (b >> 16, 0, b & 0xFFFF, 0)
+    with key (seed_lo, seed_hi) (its output layout, observed by running it);
+    for b < 65536 this is the oracle's draw block 0, experiment 0, neutron b."""
+    lib = _curand()
+    n = 6
+    ref = _curand_blocks(lib, seed, first, n)
+    for j in range(n):
+        b = first + j
+        got = oracle.philox4x32_10([b >> 16, 0, b & 0xFFFF, 0],
+                                   [seed & 0xFFFFFFFF, seed >> 32])
+        assert list(ref[j]) == got
+
+
+def test_philox_streams_differ_by_block_and_experiment():
+    a = oracle.philox4x32_10([0, 0, 5, 0], [1, 0])
+    b = oracle.philox4x32_10([1, 0, 5, 0], [1, 0])
+    c = oracle.philox4x32_10([0, 1, 5, 0], [1, 0])
+    assert a != b and a != c and b != c
+
+
+# --------------------------------------------------------- special functions
+
+def test_sphere_amplitude_closed_form_and_limits():
+    """f(x) = 3 j1(x)/x (spherical Bessel), f(0) = 1, first zero tan x = x."""
+    xs = np.concatenate([np.linspace(1e-4, 2e-3, 7), np.linspace(0.01, 300.0, 2001)])
+    ref = 3.0 * sp.spherical_jn(1, xs) / xs
+    got = np.array([oracle.sphere_f(x) for x in xs])
+    assert np.max(np.abs(got - ref)) < 1e-12
+    assert oracle.sphere_f(0.0) == 1.0
+    import scipy.optimize as so
+    x0 = so.brentq(lambda x: math.tan(x) - x, 4.0, 4.6)
+    assert abs(oracle.sphere_f(x0)) < 1e-12
+    assert abs(x0 - 4.4934094579) < 1e-9
+
+
+def test_cylinder_radial_factor_and_first_zero():
+    """2 J1(x)/x vs scipy; first zero = first zero of J1 (3.8317; the paper's
+    R = 3.78/Q_min rule, Sec. III.A, is its rounded form)."""
+    xs = np.concatenate([np.linspace(1e-8, 1e-5, 5), np.linspace(1e-3, 400.0, 3001)])
+    ref = 2.0 * sp.j1(xs) / xs
+    got = np.array([oracle.cyl_a(x) for x in xs])
+    assert np.max(np.abs(got - ref)) < 1e-13
+    z = sp.jn_zeros(1, 1)[0]
+    assert abs(oracle.cyl_a(z)) < 1e-13
+    assert oracle.cyl_a(0.0) == 1.0
+
+
+def test_sinc():
+    ys = np.linspace(-50, 50, 1001)
+    got = np.array([oracle.sinc(y) for y in ys])
+    assert np.max(np.abs(got - np.sinc(ys / np.pi))) < 1e-14
+
+
+def _py_from_direct_correlation(q, R, phi):
+    """S(q) = 1/(1 - n c^(q)) from the Percus-Yevick direct correlation
+    function of hard spheres of diameter s = 2R (Wertheim 1963):
+    c(r) = -l1 - 6 phi l2 (r/s) - (phi/2) l1 (r/s)^3 for r < s, zero beyond,
+    l1 = (1+2phi)^2/(1-phi)^4, l2 = -(1+phi/2)^2/(1-phi)^4.
+    The 3D Fourier transform is done by adaptive quadrature."""
+    s = 2.0 * R
+    l1 = (1 + 2 * phi) ** 2 / (1 - phi) ** 4
+    l2 = -(1 + 0.5 * phi) ** 2 / (1 - phi) ** 4
+    n = phi / (math.pi * s ** 3 / 6.0)
+
+    def c(r):
+        x = r / s
+        return -l1 - 6 * phi * l2 * x - 0.5 * phi * l1 * x ** 3
+
+    if q == 0.0:
+        val = si.quad(lambda r: 4 * math.pi * r * r * c(r), 0, s, epsabs=0, epsrel=1e-13)[0]
+    else:
+        val = si.quad(lambda r: 4 * math.pi * r * r * c(r) * math.sin(q * r) / (q * r), 0, s,
+                      epsabs=0, epsrel=1e-13, limit=200)[0]
+    return 1.0 / (1.0 - n * val)
+
+
+@pytest.mark.parametrize("phi", [0.05, 0.2, 0.4])
+def test_percus_yevick_against_direct_correlation_transform(phi):
+    R = 50.0
+    for q in [0.0, 1e-4, 2e-3, 4.9e-3, 5.1e-3, 0.02, 0.05, 0.1, 0.3]:
+        got = oracle.sq_py(q, R, phi)
+        ref = _py_from_direct_correlation(q, R, phi)
+        assert abs(got - ref) < 1e-9 * max(1.0, abs(ref)), (q, got, ref)
+
+
+def test_percus_yevick_limits():
+    phi = 0.2
+    s0 = (1 - phi) ** 4 / (1 + 2 * phi) ** 2   # PY compressibility route
+    assert abs(oracle.sq_py(0.0, 50.0, phi) - s0) < 1e-14
+    assert abs(oracle.sq_py(50.0, 50.0, phi) - 1.0) < 2e-3
+    # continuity across the switch between the series and the closed form (A = 0.5)
+    qa = 0.5 / (2 * 50.0)
+    lo, hi = oracle.sq_py(qa * (1 - 1e-12), 50.0, phi), oracle.sq_py(qa * (1 + 1e-12), 50.0, phi)
+    assert abs(lo - hi) < 1e-12
+
+
+# ---------------------------------------------------------------- quadrature
+
+@pytest.mark.parametrize("n", [1, 2, 5, 40, 76])
+def test_gauss_legendre_matches_numpy(n):
+    x, w = oracle.gauss_legendre(n)
+    xr, wr = np.polynomial.legendre.leggauss(n)
+    assert np.max(np.abs(np.sort(x) - xr)) < 1e-13
+    assert np.max(np.abs(w[np.argsort(x)] - wr)) < 1e-13
+
+
+@pytest.mark.parametrize("p,n", [(0.1, 40), (0.3, 40), (0.05, 10), (0.01, 40)])
+def test_schulz_nodes_moments_and_scipy(p, n):
+    rbar = 40.0
+    r, w = oracle.schulz_nodes(rbar, p, n)
+    z = 1.0 / p ** 2 - 1.0
+    assert abs(w.sum() - 1.0) < 1e-13
+    for k in range(1, 7):
+        ref = rbar ** k * math.exp(sp.gammaln(z + 1 + k) - sp.gammaln(z + 1)) / (z + 1) ** k
+        assert abs(np.dot(w, r ** k) / ref - 1.0) < 1e-10, k
+    # relative width is p
+    var = np.dot(w, r * r) - np.dot(w, r) ** 2
+    assert abs(math.sqrt(var) / rbar - p) < 1e-10
+    if z < 200:
+        xr, wr = sp.roots_genlaguerre(n, z)
+        assert np.max(np.abs(np.sort(r) - rbar * xr / (z + 1))) < 1e-9 * rbar
+        wr = wr / wr.sum()
+        assert np.max(np.abs(w[np.argsort(r)] - wr)) < 1e-12
+
+
+def test_schulz_monodisperse():
+    r, w = oracle.schulz_nodes(20.0, 0.0, 40)
+    assert list(r) == [20.0] and list(w) == [1.0]
+
+
+def test_orientation_weights_gaussian_cap():
+    """<cos gamma> of the truncated Gaussian cap equals its integral."""
+    sig = math.radians(15.0)
+    c, wt = oracle.orientation_nodes(0.5 * math.pi, 0.0, sig, 76, 76)
+    assert abs(wt.sum() - 1.0) < 1e-13
+    assert np.max(np.abs(np.linalg.norm(c, axis=1) - 1.0)) < 1e-14
+    n = np.array([1.0, 0.0, 0.0])
+    g = lambda x: math.exp(-x * x / (2 * sig * sig)) * math.sin(x)
+    Z = si.quad(g, 0, 3 * sig, epsrel=1e-13)[0]
+    m1 = si.quad(lambda x: g(x) * math.cos(x), 0, 3 * sig, epsrel=1e-13)[0] / Z
+    assert abs(np.dot(wt, c @ n) - m1) < 1e-12
+    # the mean axis is n: transverse components average to zero
+    assert np.max(np.abs(wt @ c - m1 * n)) < 1e-12
+    # sigma = 0: a single node on the mean axis (theta, phi from +z)
+    c0, w0 = oracle.orientation_nodes(1.0, 2.0, 0.0, 76, 76)
+    assert c0.shape == (1, 3) and abs(c0[0, 2] - math.cos(1.0)) < 1e-15
+    assert abs(math.atan2(c0[0, 1], c0[0, 0]) - 2.0) < 1e-14
+
+
+def test_isotropic_orientation_weights_uniform_on_sphere():
+    c, wt = oracle.orientation_nodes(0.3, 1.1, 0.0, 40, 40, isotropic=True)
+    # second moments of a uniform unit vector: <c c^T> = I/3
+    M = (c * wt[:, None]).T @ c
+    assert np.max(np.abs(M - np.eye(3) / 3.0)) < 1e-12
+
+
+# -------------------------------------------------------------------- models
+
+def _model(**kw):
+    m = W.Model(**kw)
+    return m
+
+
+def _q_along(direction, qs):
+    d = np.asarray(direction, dtype=float)
+    d = d / np.linalg.norm(d)
+    return np.outer(qs, d)
+
+
+def test_sphere_dsigma_closed_form():
+    R, drho, phi = 50.0, 2e-6, 0.01
+    m = _model(kind=W.SPHERE, radius=R, sld=drho, volume_fraction=phi)
+    qs = np.linspace(0.0, 0.3, 301)
+    got = oracle.dsigma(m, _q_along([0.3, -0.2, 0.9], qs))
+    V = 4.0 / 3.0 * math.pi * R ** 3
+    x = qs * R
+    f = np.where(x > 0, 3 * sp.spherical_jn(1, np.maximum(x, 1e-300)) / np.maximum(x, 1e-300), 1.0)
+    ref = phi * drho ** 2 * V * f ** 2
+    assert np.max(np.abs(got - ref) / ref[0]) < 1e-12
+    assert abs(got[0] / (phi * drho ** 2 * V) - 1.0) < 1e-14   # P(0) = 1
+
+
+def test_sphere_guinier_limit():
+    """Guinier law: 1 - P = Q^2 Rg^2 / 3 + O(Q^4) with Rg^2 = 3 R^2 / 5; for a
+    sphere the next term is P - exp(-Q^2 Rg^2/3) = -(QR)^4 / 350 + O((QR)^6)."""
+    R = 50.0
+    m = _model(kind=W.SPHERE, radius=R, sld=1.0, volume_fraction=1.0)
+    Rg2 = 3.0 * R * R / 5.0
+    V = 4.0 / 3.0 * math.pi * R ** 3
+    for x in [0.02, 0.05, 0.1, 0.2]:
+        q = x / R
+        P = oracle.dsigma(m, [[0.0, 0.0, q]])[0] / V
+        assert abs((1.0 - P) / (q * q * Rg2 / 3.0) - 1.0) < 0.2 * x * x
+        d4 = (P - math.exp(-q * q * Rg2 / 3.0)) / x ** 4
+        assert abs(d4 + 1.0 / 350.0) < 2e-3 * x * x + 1e-7 / x ** 4
+
+
+def test_polydisperse_sphere_against_schulz_integral():
+    """<|F|^2> and <V> as integrals over the Schulz density (scipy gamma
+    pdf, adaptive quadrature) vs the 40-node rule."""
+    rbar, p, drho, phi = 40.0, 0.1, 1e-6, 0.05
+    m = _model(kind=W.SPHERE, radius=rbar, sld=drho, volume_fraction=phi, poly=p, n_poly=40)
+    z = 1.0 / p ** 2 - 1.0
+    import scipy.stats as st
+    pdf = st.gamma(a=z + 1.0, scale=rbar / (z + 1.0)).pdf
+    V = lambda r: 4.0 / 3.0 * math.pi * r ** 3
+    Vm = si.quad(lambda r: pdf(r) * V(r), 0, 4 * rbar, epsrel=1e-13, limit=200)[0]
+    for q in [0.0, 0.01, 0.05, 0.1, 0.2]:
+        def integrand(r):
+            x = q * r
+            f = 1.0 if x == 0 else 3 * sp.spherical_jn(1, x) / x
+            return pdf(r) * (drho * V(r) * f) ** 2
+        F2 = si.quad(integrand, 0, 4 * rbar, epsrel=1e-12, limit=400)[0]
+        ref = phi / Vm * F2
+        got = oracle.dsigma(m, [[0.0, q, 0.0]])[0]
+        assert abs(got - ref) <= 1e-7 * ref + 1e-12 * phi * drho ** 2 * Vm, (q, got, ref)
+
+
+def test_core_shell_reduces_to_sphere():
+    rc, t = 40.0, 10.0
+    qs = np.linspace(0.0, 0.25, 101)
+    Q = _q_along([1, 2, 3], qs)
+    # shell SLD = core SLD -> homogeneous sphere of the outer radius
+    cs = _model(kind=W.CORE_SHELL, radius=rc, thickness=t, sld=3e-6, sld_shell=3e-6,
+                sld_solvent=1e-6, volume_fraction=0.1)
+    sph = _model(kind=W.SPHERE, radius=rc + t, sld=2e-6, volume_fraction=0.1)
+    a, b = oracle.dsigma(cs, Q), oracle.dsigma(sph, Q)
+    assert np.max(np.abs(a - b)) < 1e-12 * b[0]
+    # shell SLD = solvent SLD -> core sphere, diluted by (core volume / outer volume)
+    cs2 = _model(kind=W.CORE_SHELL, radius=rc, thickness=t, sld=5e-6, sld_shell=1e-6,
+                 sld_solvent=1e-6, volume_fraction=0.1)
+    sph2 = _model(kind=W.SPHERE, radius=rc, sld=4e-6, volume_fraction=0.1)
+    a2, b2 = oracle.dsigma(cs2, Q), oracle.dsigma(sph2, Q)
+    ratio = rc ** 3 / (rc + t) ** 3
+    assert np.max(np.abs(a2 - ratio * b2)) < 1e-12 * b2[0]
+
+
+def test_ellipsoid_with_equal_radii_is_sphere():
+    R = 30.0
+    qs = np.linspace(0.0, 0.3, 61)
+    for th, ph, sig in [(0.3, 0.4, 0.0), (1.2, 2.0, 0.2)]:
+        e = _model(kind=W.ELLIPSOID, radius=R, radius_polar=R, sld=2e-6, volume_fraction=0.01,
+                   axis_theta=th, axis_phi=ph, sigma_orient=sig, n_gamma=12, n_psi=12)
+        s = _model(kind=W.SPHERE, radius=R, sld=2e-6, volume_fraction=0.01)
+        Q = _q_along([0.2, 0.7, -0.1], qs)
+        assert np.max(np.abs(oracle.dsigma(e, Q) - oracle.dsigma(s, Q))) < 1e-12 * 1e-4
+
+
+def test_ellipsoid_oriented_projections():
+    """Q along the axis probes the polar radius, Q normal to it the equatorial one."""
+    re, rp = 20.0, 60.0
+    e = _model(kind=W.ELLIPSOID, radius=re, radius_polar=rp, sld=1.0, volume_fraction=1.0,
+               axis_theta=0.5 * math.pi, axis_phi=0.0)
+    V = 4.0 / 3.0 * math.pi * rp * re * re
+    for q in [0.01, 0.05, 0.11]:
+        along = oracle.dsigma(e, [[q, 0, 0]])[0] / V
+        normal = oracle.dsigma(e, [[0, q, 0]])[0] / V
+        f = lambda x: 3 * sp.spherical_jn(1, x) / x
+        assert abs(along - f(q * rp) ** 2) < 1e-13
+        assert abs(normal - f(q * re) ** 2) < 1e-13
+
+
+def test_cylinder_oriented_closed_form():
+    """Eq. 8 with the sinc on the axial projection and J1 on the transverse one."""
+    R, L, drho = 20.0, 400.0, 2e-6
+    m = _model(kind=W.CYLINDER, radius=R, length=L, sld=drho, volume_fraction=0.01,
+               axis_theta=0.5 * math.pi, axis_phi=0.0)
+    V = math.pi * R * R * L
+    rng = np.random.default_rng(3)
+    Q = rng.normal(size=(200, 3)) * 0.05
+    got = oracle.dsigma(m, Q)
+    qc = Q[:, 0]
+    qab = np.hypot(Q[:, 1], Q[:, 2])
+    ref = 0.01 * drho ** 2 * V * (np.sinc(qc * L / 2 / np.pi) * 2 * sp.j1(qab * R) / (qab * R)) ** 2
+    assert np.max(np.abs(got - ref)) < 1e-12 * 0.01 * drho ** 2 * V
+
+
+def test_cylinder_isotropic_average_equals_1d_integral():
+    """The isotropic 76x76 orientation average equals the textbook 1D integral
+    over mu = cos(alpha) (adaptive quadrature with scipy's J1), and does not
+    depend on the direction of Q."""
+    R, L = 20.0, 100.0
+    m = _model(kind=W.CYLINDER, radius=R, length=L, sld=1.0, volume_fraction=1.0,
+               isotropic=1, n_gamma=76, n_psi=76, axis_theta=0.4, axis_phi=0.9)
+    V = math.pi * R * R * L
+    prep = oracle.Prepared(m)
+
+    def p1d(q):
+        def f(mu):
+            qc, qab = q * mu, q * math.sqrt(max(0.0, 1 - mu * mu))
+            a = 1.0 if qab * R < 1e-12 else 2 * sp.j1(qab * R) / (qab * R)
+            s = 1.0 if qc * L < 1e-12 else math.sin(qc * L / 2) / (qc * L / 2)
+            return (s * a) ** 2
+        return si.quad(f, 0.0, 1.0, epsabs=0, epsrel=1e-12, limit=400)[0]
+
+    for q in [0.0, 0.005, 0.02, 0.05, 0.1]:
+        ref = p1d(q)
+        for d in ([0, 0, 1], [1, 0, 0], [0.3, -0.5, 0.8]):
+            got = oracle.dsigma(prep, _q_along(d, [q]))[0] / V
+            assert abs(got - ref) < 1e-6 * max(ref, 1e-3), (q, d, got, ref)
+
+
+def test_cylinder_guinier_isotropic():
+    """Isotropic cylinder: 1 - P = Q^2 Rg^2 / 3 + O(Q^4), Rg^2 = R^2/2 + L^2/12."""
+    R, L = 20.0, 60.0
+    m = _model(kind=W.CYLINDER, radius=R, length=L, sld=1.0, volume_fraction=1.0,
+               isotropic=1, n_gamma=40, n_psi=40)
+    V = math.pi * R * R * L
+    Rg2 = R * R / 2 + L * L / 12
+    prep = oracle.Prepared(m)
+    for qrg in [0.01, 0.03, 0.1]:
+        q = qrg / math.sqrt(Rg2)
+        P = oracle.dsigma(prep, [[0, 0, q]])[0] / V
+        assert abs((1.0 - P) / (qrg * qrg / 3.0) - 1.0) < 0.5 * qrg * qrg + 1e-8 / qrg ** 2
+
+
+def test_orientation_spread_tends_to_isotropic():
+    """Sec. III.A: spreading the orientation makes the pattern isotropic."""
+    R, L = 20.0, 200.0
+    base = dict(kind=W.CYLINDER, radius=R, length=L, sld=1.0, volume_fraction=1.0,
+                axis_theta=0.5 * math.pi, axis_phi=0.0, n_gamma=60, n_psi=60)
+    q = 0.03
+    Qa, Qb = [[0, q, 0]], [[0, 0, q]]   # both normal to the beam? (y) and along (z)
+    narrow = _model(sigma_orient=math.radians(2.0), **base)
+    wide = _model(sigma_orient=math.radians(170.0), **base)
+    an = abs(oracle.dsigma(narrow, Qa)[0] / oracle.dsigma(narrow, [[q, 0, 0]])[0])
+    aw = abs(oracle.dsigma(wide, Qa)[0] / oracle.dsigma(wide, [[q, 0, 0]])[0])
+    assert an > 10.0           # strongly anisotropic
+    assert abs(aw - 1.0) < 0.05  # nearly isotropic
+
+
+# ------------------------------------------------------------- the source
+
+def test_triangular_wavelength_distribution():
+    """Inverse-CDF sampling reproduces the triangular CDF on [0.9, 1.1] l0."""
+    l0, d = 6.0, 0.1
+    us = (np.arange(20000) + 0.5) / 20000
+    lam = np.array([oracle.sample_lambda(l0, d, u) for u in us])
+    t = (lam / l0 - 1.0) / d
+    cdf = np.where(t < 0, 0.5 * (1 + t) ** 2, 1 - 0.5 * (1 - t) ** 2)
+    assert np.max(np.abs(cdf - us)) < 1e-12
+    assert lam.min() > 0.9 * l0 and lam.max() < 1.1 * l0
+
+
+# -------------------------------------------------------- the whole history
+
+def _ideal_instrument(nx=8, ny=8, pix=0.02, **kw):
+    return W.Instrument(dlambda_rel=0.0, ap1_radius=0.0, ap2_radius=0.0, nx=nx, ny=ny,
+                        pixel_x=pix, pixel_y=pix, **kw)
+
+
+def _pixel_expectation(inst, dsig_fn, ix, iy, ng=6):
+    """E[w 1{pixel}] per incident neutron for an ideal pencil beam along z:
+    the thickness-weighted integral of dSigma/dOmega over the pixel's solid
+    angle, by tensor Gauss-Legendre quadrature over depth and pixel area."""
+    xg, wg = np.polynomial.legendre.leggauss(ng)
+    t = inst.sample_thickness
+    zs = 0.5 * t * (xg + 1)
+    wz = 0.5 * t * wg
+    x0 = ix * inst.pixel_x - 0.5 * inst.nx * inst.pixel_x
+    y0 = iy * inst.pixel_y - 0.5 * inst.ny * inst.pixel_y
+    xs = x0 + 0.5 * inst.pixel_x * (xg + 1)
+    ys = y0 + 0.5 * inst.pixel_y * (xg + 1)
+    wx = 0.5 * inst.pixel_x * wg
+    wy = 0.5 * inst.pixel_y * wg
+    k = 2 * math.pi / inst.lambda0
+    Z, X, Y = np.meshgrid(zs, xs, ys, indexing="ij")
+    WT = np.einsum("i,j,k->ijk", wz, wx, wy)
+    v = np.stack([X, Y, inst.det_distance - Z], axis=-1)
+    r = np.linalg.norm(v, axis=-1)
+    kout = v / r[..., None]
+    Q = k * (kout - np.array([0, 0, 1.0]))
+    dOmega_dA = kout[..., 2] / r ** 2
+    ds = dsig_fn(Q.reshape(-1, 3)).reshape(Z.shape) * 1e10
+    return float(np.sum(WT * ds * dOmega_dA))
+
+
+def test_trace_ideal_beam_matches_pixel_integrals():
+    """Pencil beam, no wavelength spread: the per-pixel mean weight equals
+    t * integral over the pixel of dSigma/dOmega dOmega (independent FP64
+    quadrature with scipy's spherical Bessel function), within 3 sigma."""
+    inst = _ideal_instrument()
+    R, drho, phi = 50.0, 2e-6, 0.01
+    m = _model(kind=W.SPHERE, radius=R, sld=drho, volume_fraction=phi)
+    V = 4 / 3 * math.pi * R ** 3
+
+    def ds(Q):
+        q = np.linalg.norm(Q, axis=1) * R
+        f = np.where(q > 1e-8, 3 * sp.spherical_jn(1, np.maximum(q, 1e-8)) / np.maximum(q, 1e-8), 1.0)
+        return phi * drho ** 2 * V * f ** 2
+
+    N = 400000
+    res = oracle.trace(inst, m, N, seed=7)
+    chi2 = []
+    for iy in range(inst.ny):
+        for ix in range(inst.nx):
+            mean = res["sum_w"][iy, ix] / N
+            var = (res["sum_w2"][iy, ix] / N - mean ** 2) / N
+            ref = _pixel_expectation(inst, ds, ix, iy)
+            sig = math.sqrt(var)
+            assert abs(mean - ref) < 3.5 * sig + 1e-9 * ref, (ix, iy, mean, ref, sig)
+            chi2.append(((mean - ref) / sig) ** 2)
+    assert np.mean(chi2) < 1.6
+    # no miss for this geometry; every history is tallied once
+    assert int(res["count"].sum()) == N
+    assert res["trans"] == pytest.approx(N)
+
+
+def _numpy_history_mc(inst, dsig_fn, n, seed):
+    """An independent Monte Carlo of the same estimator written with numpy
+    (own random numbers): source, pinholes, slab, area-uniform detector point."""
+    rng = np.random.default_rng(seed)
+    u = rng.random(n)
+    tri = rng.triangular(-1.0, 0.0, 1.0, size=n)
+    lam = inst.lambda0 * (1 + inst.dlambda_rel * tri)
+    r1 = inst.ap1_radius * np.sqrt(rng.random(n)); f1 = 2 * np.pi * rng.random(n)
+    r2 = inst.ap2_radius * np.sqrt(rng.random(n)); f2 = 2 * np.pi * rng.random(n)
+    p1 = np.stack([r1 * np.cos(f1), r1 * np.sin(f1), np.full(n, inst.ap1_z)], 1)
+    p2 = np.stack([r2 * np.cos(f2), r2 * np.sin(f2), np.full(n, inst.ap2_z)], 1)
+    kin = p2 - p1
+    kin /= np.linalg.norm(kin, axis=1)[:, None]
+    # all rays enter the front face at z = 0 here (apertures inside the face)
+    assert np.all(np.abs(p2[:, :2]) < [inst.sample_half_x, inst.sample_half_y])
+    zin = (0.0 - p2[:, 2]) / kin[:, 2]
+    zout = (inst.sample_thickness - p2[:, 2]) / kin[:, 2]
+    l = zout - zin
+    s = l * rng.random(n)
+    ps = p2 + (zin + s)[:, None] * kin
+    W_ = inst.nx * inst.pixel_x
+    H_ = inst.ny * inst.pixel_y
+    xd = (rng.random(n) - 0.5) * W_
+    yd = (rng.random(n) - 0.5) * H_
+    v = np.stack([xd, yd, np.full(n, inst.det_distance)], 1) - ps
+    r = np.linalg.norm(v, axis=1)
+    kout = v / r[:, None]
+    k = 2 * np.pi / lam
+    Q = k[:, None] * (kout - kin)
+    w = l * dsig_fn(Q) * 1e10 * W_ * H_ * kout[:, 2] / r ** 2
+    ix = np.floor((xd + W_ / 2) / inst.pixel_x).astype(int)
+    iy = np.floor((yd + H_ / 2) / inst.pixel_y).astype(int)
+    pix = iy * inst.nx + ix
+    sw = np.bincount(pix, weights=w, minlength=inst.nx * inst.ny)
+    sw2 = np.bincount(pix, weights=w * w, minlength=inst.nx * inst.ny)
+    return sw, sw2
+
+
+def test_trace_finite_beam_matches_independent_numpy_mc():
+    """Full instrument chain (triangular wavelength spread, two pinholes,
+    finite sample depth) against an independent numpy Monte Carlo of the
+    same estimator: every pixel within 4 sigma, chi^2/dof about 1."""
+    inst = W.Instrument(nx=8, ny=8, pixel_x=0.02, pixel_y=0.02, det_distance=2.0,
+                        dlambda_rel=0.25, ap1_radius=0.01, ap2_radius=0.004)
+    R, drho, phi = 60.0, 2e-6, 0.01
+    m = _model(kind=W.SPHERE, radius=R, sld=drho, volume_fraction=phi)
+    V = 4 / 3 * math.pi * R ** 3
+
+    def ds(Q):
+        q = np.linalg.norm(Q, axis=1) * R
+        q = np.maximum(q, 1e-8)
+        return phi * drho ** 2 * V * (3 * sp.spherical_jn(1, q) / q) ** 2
+
+    N = 600000
+    res = oracle.trace(inst, m, N, seed=11)
+    sw, sw2 = _numpy_history_mc(inst, ds, N, seed=5)
+    a = res["sum_w"].reshape(-1) / N
+    va = (res["sum_w2"].reshape(-1) / N - a ** 2) / N
+    b = sw / N
+    vb = (sw2 / N - b ** 2) / N
+    z = (a - b) / np.sqrt(va + vb)
+    assert np.max(np.abs(z)) < 4.5
+    assert np.mean(z ** 2) < 1.6
