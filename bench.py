@@ -1,0 +1,322 @@
+#!/usr/bin/env python3
+"""Benchmark: neutron histories/s of the SANS Monte Carlo trace on GB300.
+
+One step = one pass of the whole hot path over one batch: zero the detector,
+trace 1e9 neutron histories of the core-shell workload (core 40 + shell 10
+angstrom, SLDs (1, 3, 6)e-6, Schulz sigma/R = 0.1 with 40 nodes,
+Percus-Yevick hard spheres phi = 0.2; 128x128 detector at 5 m; triangular
++-10 % wavelength spread around 6 angstrom; two pinholes; FP32 tracing with
+FP32 Kahan tallies and the FP64 per-bin reduction), seed 1.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank traces its own index range [rank*n, (rank+1)*n)
+(weak scaling; the counter-based RNG makes the union one set of histories;
+no collective in the data path). `--impl reference` times the FP64 CPU
+oracle on the host cores on a bounded sample of the same workload.
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import sas_workloads as W  # noqa: E402
+
+METRIC = "neutron histories/s on 1 GB300 (plain vs batched+surrogate) at stated per-bin error"
+UNIT = "neutron histories/s"
+WORKLOAD = ("core-shell sphere 40+10 A, SLD (1,3,6)e-6, Schulz 0.1 x40 nodes, Percus-Yevick "
+            "phi=0.2; 128x128 detector 5 mm pixels at 5 m; lambda 6 A +-10% triangular; "
+            "2 m pinholes 8/4 mm; 1 mm x 10x10 mm sample; 1e9 neutrons per GPU per step; "
+            "FP32 trace, FP32 Kahan tallies, FP64 per-bin reduction")
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.dev)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline(cfg, target_s=12.0, threads=0):
+    """The FP64 oracle, as it stands, on the host cores: histories/s on a
+    bounded sample of the same workload (calibrated to ~target_s seconds)."""
+    import oracle
+    oracle.build()
+    inst, model = cfg["instrument"], cfg["model"]
+    prep = oracle.Prepared(model)
+    n0 = 20000
+    t = time.perf_counter()
+    oracle.trace(inst, prep, n0, seed=cfg["seed"], threads=threads)
+    dt0 = time.perf_counter() - t
+    n = int(min(max(n0, n0 * target_s / max(dt0, 1e-6)), 5e8))
+    t = time.perf_counter()
+    oracle.trace(inst, prep, n, seed=cfg["seed"], threads=threads)
+    dt = time.perf_counter() - t
+    cores = threads if threads > 0 else oracle.num_threads()
+    return {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} histories (indices 0..{n - 1}, seed {cfg['seed']}) of the same "
+                      f"workload, FP64, OpenMP {cores} threads, {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    cfg = W.core_shell_config()
+    import oracle
+    oracle.build()
+    prep = oracle.Prepared(cfg["model"])
+    inst = cfg["instrument"]
+    # size each step to a few seconds of CPU work
+    n0 = 20000
+    t = time.perf_counter()
+    oracle.trace(inst, prep, n0, seed=1)
+    dt0 = time.perf_counter() - t
+    per_step = max(n0, int(n0 * 4.0 / max(dt0, 1e-6)))
+    for w in range(args.warmup):
+        oracle.trace(inst, prep, min(per_step, 100000), seed=1, first=w * per_step)
+    times = []
+    for k in range(args.steps):
+        t = time.perf_counter()
+        oracle.trace(inst, prep, per_step, seed=1, first=k * per_step)
+        times.append(time.perf_counter() - t)
+    tot = sum(times)
+    value = per_step * args.steps / tot
+    cores = oracle.num_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD.replace("1e9 neutrons per GPU per step",
+                                                f"{per_step} neutrons per step (bounded CPU sample)")},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{per_step} histories per step x {args.steps} steps, FP64 "
+                                   f"oracle, OpenMP {cores} threads"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--neutrons", type=float, default=None, help="histories per GPU per step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_2501_06054_gb300 as sas
+    from paper_2501_06054_gb300 import flops as F
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.Stream()
+    cfg = W.core_shell_config()
+    n = int(args.neutrons) if args.neutrons else cfg["n_neutrons"]
+    first = rank * n
+    seed = cfg["seed"]
+    info = sas.sas_device_info()
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    with torch.cuda.stream(stream):
+        e = sas.Experiment(cfg["instrument"], cfg["model"], stream=stream)
+        l2_flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+        def step():
+            sas.sas_reset_detector(e.h)
+            sas.sas_trace_range(e.h, first, n, seed)
+
+        for _ in range(args.warmup):
+            step()
+        barrier()
+        sampler = ClockSampler(dev)
+        sampler.start()
+        time.sleep(0.3)
+        barrier()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        kstarts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        for k in range(args.steps):
+            l2_flush.fill_(float(k))          # untimed: flush L2 between steps
+            starts[k].record(stream)
+            sas.sas_reset_detector(e.h)
+            kstarts[k].record(stream)
+            sas.sas_trace_range(e.h, first, n, seed)
+            ends[k].record(stream)
+        barrier()
+        clocks = sampler.stop()
+        step_ms = [s.elapsed_time(t) for s, t in zip(starts, ends)]
+        kern_ms = [s.elapsed_time(t) for s, t in zip(kstarts, ends)]
+        ms = sum(step_ms) / len(step_ms)
+        kms = sum(kern_ms) / len(kern_ms)
+        t_ms = torch.tensor([ms, kms], dtype=torch.float64, device="cuda")
+        if ws > 1:
+            dist.all_reduce(t_ms, op=dist.ReduceOp.MAX)
+        ms, kms = float(t_ms[0]), float(t_ms[1])
+        d = e.read()
+        ok_counts = int(d["count"].sum()) == n
+
+        # end to end through the public API: model upload (H2D), trace,
+        # detector read-back into host buffers (D2H), every step
+        npix = e.npix
+        hbuf = {k: np.empty(npix, dt) for k, dt in (("sum_w", np.float64), ("sum_w2", np.float64),
+                                                     ("count", np.uint64))}
+        for _ in range(2):
+            sas.sas_set_model(e.h, cfg["model"])
+            sas.sas_reset_detector(e.h)
+            sas.sas_trace_range(e.h, first, n, seed)
+            sas.sas_read_detector(e.h, npix, **hbuf)
+        barrier()
+        e2e_steps = max(3, min(args.steps, 10))
+        t0 = time.perf_counter()
+        for k in range(e2e_steps):
+            sas.sas_set_model(e.h, cfg["model"])
+            sas.sas_reset_detector(e.h)
+            sas.sas_trace_range(e.h, first, n, seed)
+            sas.sas_read_detector(e.h, npix, **hbuf)
+        barrier()
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        t_e = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        if ws > 1:
+            dist.all_reduce(t_e, op=dist.ReduceOp.MAX)
+        e2e_s = float(t_e[0])
+        e.close()
+
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return 0
+
+    m = cfg["model"]
+    fl = F.flops_per_history(m.kind, m.n_poly, 1, sq=True)
+    peak_max = F.fp32_peak_tflops(info["sm_count"], 2070.0)
+    achieved = fl * n / (kms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_max, "unit": "TFLOP/s",
+                "frac": achieved / peak_max, "traffic": None,
+                "kernel": "trace_kernel<float, CORE_SHELL, TALLY_SMEM>",
+                "flops_per_history": fl,
+                "peak_note": f"FP32 CUDA cores {info['sm_count']} SMs x 128 x 2 FLOP x 2070 MHz"}
+    if clocks:
+        roofline["frac_at_sampled_clock"] = achieved / F.fp32_peak_tflops(info["sm_count"], clocks["sm_mhz"])
+    value = n * ws / (ms * 1e-3)
+    tables_bytes = (m.n_poly * 8 + 4) * 4
+    d2h = npix * 8 * 3 + 8
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "neutrons_per_step": n * ws, "seed": seed,
+                   "l2": "flushed between timed steps (256 MiB write, untimed)",
+                   "all_histories_counted": ok_counts},
+        "roofline": roofline,
+        "e2e": {"value": n * ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": tables_bytes,
+                "d2h_bytes_per_step": d2h,
+                "note": "sas_set_model (table upload) + sas_trace + sas_read_detector into host buffers"},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cfg)
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,199 @@
+/*
+ * sas.h -- C ABI of the GB300 SANS Monte Carlo trace library (libsas.so).
+ *
+ * One neutron history (Sec. II.A, instrument chain; single scattering,
+ * Sec. I): a neutron is drawn from the source (wavelength with a triangular
+ * spread), passes two pinholes (collimation), enters the sample slab, is
+ * split into a transmitted weight and a scattered branch, gets a scattering
+ * vector Q toward an area-uniform point of the 2D position-sensitive detector
+ * and the weight  l * dSigma/dOmega(Q) * dOmega,  where
+ *
+ *   dSigma/dOmega(Q) = (phi / <V>) <|F(Q)|^2> S(Q),   F = drho V f(Q)
+ *
+ * follows Eqs. (1)-(4) (amplitude, intensity, dilute-limit intensity
+ * n drho^2 V^2 P S, model A*A/V), Eq. (7) (uniaxial particles: F depends on
+ * Q_AB and Q_C) and Eq. (8) (cylinder). <.> averages over the polydispersity
+ * distribution and, for uniaxial particles, the orientation distribution
+ * (Sec. II.B). The weight is tallied on the detector pixel.
+ *
+ * Conventions for every entry point:
+ *  - Return SAS_OK or an error code; nothing aborts or prints. The text of
+ *    the last error of the calling thread is in sas_last_error().
+ *  - Units: instrument lengths in m, wavelength and particle sizes in
+ *    angstrom, SLD in 1/angstrom^2, angles in rad, Q in 1/angstrom,
+ *    dSigma/dOmega in 1/angstrom (model evaluation) or 1/m (trace weights).
+ *    The beam runs along +z; the sample front face is the plane z = 0.
+ *  - Device memory of an experiment or a batch is owned by the library.
+ *    Host buffers passed in are owned by the caller, who states their length.
+ *  - "stream" arguments are cudaStream_t values passed as void* (NULL: the
+ *    legacy default stream). Work is enqueued asynchronously on the stream;
+ *    the sas_read_* calls synchronise it.
+ *  - Random numbers: Philox4x32-10 (Salmon et al., SC'11) with
+ *    key = (seed low 32 bits, seed high 32 bits) and counter =
+ *    (draw block, experiment id, neutron index low, neutron index high).
+ *    A neutron's history depends only on (seed, experiment id, index), so
+ *    any split of an index range into sub-ranges gives the same histories.
+ */
+#ifndef SAS_H
+#define SAS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum sas_status {
+    SAS_OK = 0,
+    SAS_ERR_ARG = 1,         /* invalid argument, size mismatch, NULL pointer */
+    SAS_ERR_CUDA = 2,        /* a CUDA runtime call failed */
+    SAS_ERR_OOM = 3,         /* device allocation failed */
+    SAS_ERR_STATE = 4,       /* call out of order (e.g. trace before set_model) */
+    SAS_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+    SAS_ERR_OUT_OF_BOX = 6,  /* surrogate input outside its training box */
+    SAS_ERR_NUMERIC = 7      /* non-finite value detected */
+} sas_status;
+
+enum { SAS_SPHERE = 0, SAS_CORE_SHELL = 1, SAS_CYLINDER = 2, SAS_ELLIPSOID = 3 };
+enum { SAS_SQ_NONE = 0, SAS_SQ_HARD_SPHERE_PY = 1 };
+enum { SAS_FP32 = 0, SAS_FP64 = 1 };
+
+/* Instrument (Sec. II.A: source, collimation, sample, 2D PSD). */
+typedef struct sas_instrument {
+    double lambda0;          /* mean wavelength, angstrom */
+    double dlambda_rel;      /* half width of the triangular spread / lambda0 */
+    double ap1_radius;       /* first pinhole radius, m */
+    double ap1_z;            /* first pinhole plane, m (< ap2_z) */
+    double ap2_radius;       /* second pinhole radius, m */
+    double ap2_z;            /* second pinhole plane, m (<= 0) */
+    double sample_half_x;    /* sample slab |x| <= half_x, m */
+    double sample_half_y;    /* sample slab |y| <= half_y, m */
+    double sample_thickness; /* slab 0 <= z <= thickness, m */
+    double mu;               /* attenuation coefficient inside the sample, 1/m */
+    double det_distance;     /* detector plane z, m */
+    double pixel_x;          /* pixel pitch in x, m */
+    double pixel_y;          /* pixel pitch in y, m */
+    int64_t nx;              /* pixels in x (1..4096) */
+    int64_t ny;              /* pixels in y (1..4096); pixel index = iy * nx + ix */
+} sas_instrument;
+
+/* Sample model (Eqs. 1-4, 7, 8; polydispersity and orientation Sec. II.B). */
+typedef struct sas_model_desc {
+    int64_t kind;            /* SAS_SPHERE, SAS_CORE_SHELL, SAS_CYLINDER, SAS_ELLIPSOID */
+    int64_t sq_kind;         /* SAS_SQ_NONE or SAS_SQ_HARD_SPHERE_PY */
+    int64_t precision;       /* SAS_FP32 (tallies FP32 Kahan + FP64 reduction) or SAS_FP64 */
+    int64_t n_poly;          /* Schulz nodes of the polydisperse radius (1..64) */
+    int64_t n_gamma;         /* orientation nodes in the polar angle about the axis (1..128) */
+    int64_t n_psi;           /* orientation nodes in the azimuth about the axis (1..128) */
+    int64_t isotropic;       /* 1: axis uniform on the sphere (uniaxial models) */
+    double radius;           /* sphere R; core radius; cylinder R; ellipsoid equatorial R */
+    double thickness;        /* core-shell shell thickness */
+    double length;           /* cylinder length L */
+    double radius_polar;     /* ellipsoid polar radius (along the axis) */
+    double sld;              /* particle (core) scattering length density */
+    double sld_shell;        /* core-shell shell SLD */
+    double sld_solvent;      /* solvent SLD */
+    double volume_fraction;  /* phi */
+    double poly;             /* Schulz sigma / mean of the polydisperse radius (0: none) */
+    double sigma_orient;     /* Gaussian width of the axis about its mean, rad */
+    double axis_theta;       /* mean axis polar angle from +z, rad */
+    double axis_phi;         /* mean axis azimuth, rad */
+    double sq_radius;        /* Percus-Yevick hard-sphere radius */
+    double sq_fraction;      /* Percus-Yevick volume fraction */
+} sas_model_desc;
+
+typedef struct sas_experiment sas_experiment;   /* opaque, library-owned */
+
+/* Create an experiment on the current CUDA device: validates the instrument
+ * and allocates its FP64 detector (sum w, sum w^2, counts) and the
+ * transmitted-weight scalar in device memory. *out is owned by the caller
+ * until sas_destroy_experiment. SAS_ERR_ARG on invalid geometry. */
+sas_status sas_create_experiment(const sas_instrument *inst, void *stream,
+                                 sas_experiment **out);
+
+/* Replace the sample model: validates it, builds the FP64 quadrature tables
+ * (Schulz generalised Gauss-Laguerre nodes, Gaussian-cap orientation nodes
+ * on a Gauss-Legendre grid in (gamma, psi)) and the Percus-Yevick series,
+ * rounds them to the trace precision and uploads them (stream-ordered). */
+sas_status sas_set_model(sas_experiment *exp, const sas_model_desc *model);
+
+/* Select the Philox experiment id (counter word 1) used by later traces
+ * (default 0). */
+sas_status sas_set_experiment_id(sas_experiment *exp, uint32_t id);
+
+/* Change the stream later calls enqueue on. */
+sas_status sas_set_stream(sas_experiment *exp, void *stream);
+
+/* Zero the detector, then trace neutrons [0, n_neutrons). Asynchronous. */
+sas_status sas_trace(sas_experiment *exp, uint64_t n_neutrons, uint64_t seed);
+
+/* Trace neutrons [first, first + n) and ADD them to the detector (resume,
+ * sharding). Asynchronous. */
+sas_status sas_trace_range(sas_experiment *exp, uint64_t first, uint64_t n, uint64_t seed);
+
+/* Zero the detector and transmitted weight. Asynchronous. */
+sas_status sas_reset_detector(sas_experiment *exp);
+
+/* Copy the detector into caller-owned HOST buffers of n_pixels entries
+ * (n_pixels must equal nx*ny; any pointer may be NULL to skip it) and the
+ * transmitted weight (may be NULL). Synchronises the stream. */
+sas_status sas_read_detector(const sas_experiment *exp, double *sum_w, double *sum_w2,
+                             uint64_t *count, size_t n_pixels, double *transmitted);
+
+/* Library-owned DEVICE pointers of the detector arrays (valid until destroy). */
+sas_status sas_detector_device(const sas_experiment *exp, const double **sum_w,
+                               const double **sum_w2, const uint64_t **count,
+                               const double **transmitted);
+
+/* Parity hook: dSigma/dOmega (1/angstrom) of the experiment's model at n
+ * scattering vectors. q_xyz: DEVICE float[n][3]; out: DEVICE float[n]
+ * (model precision FP32) -- or double pointers if the model is FP64.
+ * Asynchronous on the experiment's stream. */
+sas_status sas_eval_model(sas_experiment *exp, const void *q_xyz, size_t n, void *out);
+
+/* Parity hook: per-neutron records of neutrons [first, first+n): DEVICE
+ * int32 pixel[n] (-1: missed the sample) and DEVICE double weight[n] (1/m
+ * units of the tally). Does not touch the detector. Asynchronous. */
+sas_status sas_trace_records(sas_experiment *exp, uint64_t first, uint64_t n, uint64_t seed,
+                             int32_t *pixel, double *weight);
+
+/* Block until all work on the experiment's stream is done. */
+sas_status sas_sync(sas_experiment *exp);
+
+/* Free the experiment and its device memory (NULL is accepted). */
+sas_status sas_destroy_experiment(sas_experiment *exp);
+
+/* Thread-local text of the last error (empty string if none). */
+const char *sas_last_error(void);
+
+/* Device properties used by the launch heuristics. */
+sas_status sas_device_info(int *sm_count, int *smem_per_block_optin, int *cc_major,
+                           int *cc_minor);
+
+/* ---- host-side utilities (no GPU needed): the library's own FP64 tables.
+ * They are the quadrature rules sas_set_model builds for the trace. */
+
+/* n-point Gauss-Legendre rule on [-1, 1] (Newton on P_n), n in 1..1024. */
+sas_status sas_gauss_legendre(int n, double *x, double *w);
+
+/* Schulz distribution (mean, relative width p) as n generalised
+ * Gauss-Laguerre nodes r[n] with normalised weights w[n] (Sec. II.B reading:
+ * Schulz instead of per-event Gaussian draws). p == 0: one node at the mean. */
+sas_status sas_schulz_nodes(double mean, double p, int n, double *r, double *w);
+
+/* Orientation nodes of the axis distribution about (theta, phi): Gaussian
+ * cap of width sigma (or isotropic), n_gamma x n_psi Gauss-Legendre grid.
+ * c_xyz[3 * n_gamma * n_psi], w[n_gamma * n_psi]; *n_out = nodes written. */
+sas_status sas_orientation_nodes(double theta, double phi, double sigma, int n_gamma, int n_psi,
+                                 int isotropic, double *c_xyz, double *w, int *n_out);
+
+/* Percus-Yevick constants (alpha, beta, gamma) and the first nser
+ * coefficients of G(A)/A in powers of A^2. */
+sas_status sas_py_series(double phi, double *alpha_beta_gamma, double *series, int nser);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SAS_H */

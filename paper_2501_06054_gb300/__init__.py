@@ -1,0 +1,291 @@
+"""Python binding of libsas, the GB300 SANS Monte Carlo trace library.
+
+Argument marshalling only (ctypes): every step of the trace runs in the
+library's CUDA kernels. The functions carry the C ABI's names (include/sas.h);
+device buffers are passed as torch CUDA tensors (or raw integer addresses),
+host buffers as numpy arrays owned by the caller.
+
+If the compiled library is missing and cannot be built, importing the
+library raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+SAS_OK, SAS_ERR_ARG, SAS_ERR_CUDA, SAS_ERR_OOM, SAS_ERR_STATE = 0, 1, 2, 3, 4
+SAS_ERR_TIMEOUT, SAS_ERR_OUT_OF_BOX, SAS_ERR_NUMERIC = 5, 6, 7
+SAS_SPHERE, SAS_CORE_SHELL, SAS_CYLINDER, SAS_ELLIPSOID = 0, 1, 2, 3
+SAS_SQ_NONE, SAS_SQ_HARD_SPHERE_PY = 0, 1
+SAS_FP32, SAS_FP64 = 0, 1
+
+
+class SasError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"libsas error {status}: {msg}")
+        self.status = status
+
+
+class sas_instrument(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in (
+        "lambda0", "dlambda_rel", "ap1_radius", "ap1_z", "ap2_radius", "ap2_z",
+        "sample_half_x", "sample_half_y", "sample_thickness", "mu", "det_distance",
+        "pixel_x", "pixel_y")] + [("nx", ctypes.c_int64), ("ny", ctypes.c_int64)]
+
+
+class sas_model_desc(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in (
+        "kind", "sq_kind", "precision", "n_poly", "n_gamma", "n_psi", "isotropic")] + \
+               [(n, ctypes.c_double) for n in (
+                   "radius", "thickness", "length", "radius_polar", "sld", "sld_shell",
+                   "sld_solvent", "volume_fraction", "poly", "sigma_orient", "axis_theta",
+                   "axis_phi", "sq_radius", "sq_fraction")]
+
+
+_lib = None
+_lock = threading.Lock()
+_vp = ctypes.c_void_p
+_u64 = ctypes.c_uint64
+_dp = ctypes.POINTER(ctypes.c_double)
+
+_SIGS = {
+    "sas_create_experiment": [ctypes.POINTER(sas_instrument), _vp, ctypes.POINTER(_vp)],
+    "sas_set_model": [_vp, ctypes.POINTER(sas_model_desc)],
+    "sas_set_experiment_id": [_vp, ctypes.c_uint32],
+    "sas_set_stream": [_vp, _vp],
+    "sas_trace": [_vp, _u64, _u64],
+    "sas_trace_range": [_vp, _u64, _u64, _u64],
+    "sas_reset_detector": [_vp],
+    "sas_read_detector": [_vp, _vp, _vp, _vp, ctypes.c_size_t, _vp],
+    "sas_detector_device": [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                            ctypes.POINTER(_vp)],
+    "sas_eval_model": [_vp, _vp, ctypes.c_size_t, _vp],
+    "sas_trace_records": [_vp, _u64, _u64, _u64, _vp, _vp],
+    "sas_sync": [_vp],
+    "sas_destroy_experiment": [_vp],
+    "sas_device_info": [ctypes.POINTER(ctypes.c_int)] * 4,
+    "sas_gauss_legendre": [ctypes.c_int, _dp, _dp],
+    "sas_schulz_nodes": [ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp, _dp],
+    "sas_orientation_nodes": [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                              ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.POINTER(ctypes.c_int)],
+    "sas_py_series": [ctypes.c_double, _dp, _dp, ctypes.c_int],
+}
+
+# extra entry points added by later modules of the library register here
+EXTRA_SIGS = {}
+
+
+def library_path():
+    return _build.LIB
+
+
+def lib():
+    """Load libsas.so (building it in-tree first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = ctypes.CDLL(path, mode=ctypes.RTLD_GLOBAL)
+            for name, args in {**_SIGS, **EXTRA_SIGS}.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = ctypes.c_int
+            L.sas_last_error.restype = ctypes.c_char_p
+            L.sas_last_error.argtypes = []
+            _lib = L
+    return _lib
+
+
+def sas_last_error() -> str:
+    return lib().sas_last_error().decode()
+
+
+def _check(status):
+    if status != SAS_OK:
+        raise SasError(status, sas_last_error())
+
+
+def _ptr(x):
+    """Device (or host) address of a torch tensor, numpy array or integer."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def make_instrument(d) -> sas_instrument:
+    d = d if isinstance(d, dict) else d.as_dict()
+    return sas_instrument(**{k: (int(v) if k in ("nx", "ny") else float(v)) for k, v in d.items()})
+
+
+def make_model(d) -> sas_model_desc:
+    d = d if isinstance(d, dict) else d.as_dict()
+    ints = ("kind", "sq_kind", "precision", "n_poly", "n_gamma", "n_psi", "isotropic")
+    return sas_model_desc(**{k: (int(v) if k in ints else float(v)) for k, v in d.items()})
+
+
+# ------------------------------------------------------------ C ABI names
+
+def sas_create_experiment(instrument, stream=None):
+    inst = instrument if isinstance(instrument, sas_instrument) else make_instrument(instrument)
+    h = _vp()
+    _check(lib().sas_create_experiment(ctypes.byref(inst), _stream_handle(stream), ctypes.byref(h)))
+    return h.value
+
+
+def sas_set_model(exp, model):
+    m = model if isinstance(model, sas_model_desc) else make_model(model)
+    _check(lib().sas_set_model(exp, ctypes.byref(m)))
+
+
+def sas_set_experiment_id(exp, exp_id):
+    _check(lib().sas_set_experiment_id(exp, int(exp_id)))
+
+
+def sas_set_stream(exp, stream):
+    _check(lib().sas_set_stream(exp, _stream_handle(stream)))
+
+
+def sas_trace(exp, n_neutrons, seed):
+    _check(lib().sas_trace(exp, int(n_neutrons), int(seed)))
+
+
+def sas_trace_range(exp, first, n, seed):
+    _check(lib().sas_trace_range(exp, int(first), int(n), int(seed)))
+
+
+def sas_reset_detector(exp):
+    _check(lib().sas_reset_detector(exp))
+
+
+def sas_read_detector(exp, n_pixels, sum_w=None, sum_w2=None, count=None, transmitted=True):
+    """Copy the detector to host numpy buffers (allocated here if not given)."""
+    sum_w = np.empty(n_pixels, np.float64) if sum_w is None else sum_w
+    sum_w2 = np.empty(n_pixels, np.float64) if sum_w2 is None else sum_w2
+    count = np.empty(n_pixels, np.uint64) if count is None else count
+    tr = np.zeros(1, np.float64)
+    _check(lib().sas_read_detector(exp, _ptr(sum_w), _ptr(sum_w2), _ptr(count), int(n_pixels),
+                                   _ptr(tr) if transmitted else None))
+    return dict(sum_w=sum_w, sum_w2=sum_w2, count=count, trans=float(tr[0]))
+
+
+def sas_detector_device(exp):
+    a, b, c, d = _vp(), _vp(), _vp(), _vp()
+    _check(lib().sas_detector_device(exp, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                     ctypes.byref(d)))
+    return a.value, b.value, c.value, d.value
+
+
+def sas_eval_model(exp, q_xyz, n, out):
+    _check(lib().sas_eval_model(exp, _ptr(q_xyz), int(n), _ptr(out)))
+
+
+def sas_trace_records(exp, first, n, seed, pixel, weight):
+    _check(lib().sas_trace_records(exp, int(first), int(n), int(seed), _ptr(pixel), _ptr(weight)))
+
+
+def sas_sync(exp):
+    _check(lib().sas_sync(exp))
+
+
+def sas_destroy_experiment(exp):
+    _check(lib().sas_destroy_experiment(exp))
+
+
+def sas_device_info():
+    v = [ctypes.c_int() for _ in range(4)]
+    _check(lib().sas_device_info(*[ctypes.byref(x) for x in v]))
+    return dict(sm_count=v[0].value, smem_optin=v[1].value, cc=(v[2].value, v[3].value))
+
+
+def sas_gauss_legendre(n):
+    x, w = np.empty(n), np.empty(n)
+    _check(lib().sas_gauss_legendre(int(n), x.ctypes.data_as(_dp), w.ctypes.data_as(_dp)))
+    return x, w
+
+
+def sas_schulz_nodes(mean, p, n):
+    r, w = np.empty(n), np.empty(n)
+    _check(lib().sas_schulz_nodes(float(mean), float(p), int(n), r.ctypes.data_as(_dp),
+                                  w.ctypes.data_as(_dp)))
+    k = 1 if (p <= 0.0 or n <= 1) else n
+    return r[:k], w[:k]
+
+
+def sas_orientation_nodes(theta, phi, sigma, n_gamma, n_psi, isotropic=0):
+    c = np.empty((n_gamma * n_psi, 3))
+    w = np.empty(n_gamma * n_psi)
+    k = ctypes.c_int()
+    _check(lib().sas_orientation_nodes(float(theta), float(phi), float(sigma), int(n_gamma),
+                                       int(n_psi), int(isotropic), c.ctypes.data_as(_dp),
+                                       w.ctypes.data_as(_dp), ctypes.byref(k)))
+    return c[:k.value], w[:k.value]
+
+
+def sas_py_series(phi, nser=14):
+    abg = np.empty(3)
+    s = np.empty(nser)
+    _check(lib().sas_py_series(float(phi), abg.ctypes.data_as(_dp), s.ctypes.data_as(_dp),
+                               int(nser)))
+    return abg, s
+
+
+# ------------------------------------------------------------ convenience
+
+class Experiment:
+    """Owns one sas_experiment handle (thin wrapper over the C ABI)."""
+
+    def __init__(self, instrument, model=None, stream=None):
+        self.inst = instrument if isinstance(instrument, sas_instrument) else make_instrument(instrument)
+        self.npix = int(self.inst.nx * self.inst.ny)
+        self.h = sas_create_experiment(self.inst, stream)
+        if model is not None:
+            self.set_model(model)
+
+    def set_model(self, model):
+        sas_set_model(self.h, model)
+
+    def trace(self, n, seed):
+        sas_trace(self.h, n, seed)
+
+    def trace_range(self, first, n, seed):
+        sas_trace_range(self.h, first, n, seed)
+
+    def read(self):
+        d = sas_read_detector(self.h, self.npix)
+        shp = (int(self.inst.ny), int(self.inst.nx))
+        for k in ("sum_w", "sum_w2", "count"):
+            d[k] = d[k].reshape(shp)
+        return d
+
+    def sync(self):
+        sas_sync(self.h)
+
+    def close(self):
+        if self.h:
+            sas_destroy_experiment(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

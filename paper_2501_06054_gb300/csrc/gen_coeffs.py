@@ -1,0 +1,118 @@
+"""Generates sas_coeffs.h: FP32 coefficients of the device special functions.
+
+Run once (python gen_coeffs.py > sas_coeffs.h); the output is committed.
+
+* sin / cos on [-pi/4, pi/4]: Taylor coefficients (exact rationals).
+* pi/2 and pi/4 split into three FP32 parts for Cody-Waite argument
+  reduction (first two parts with 12 significant bits so that k * part is
+  exact for |k| < 2^12).
+* a(x) = 2 J1(x) / x for 0 <= x <= X1: a polynomial in s = (x / X1)^2, fitted here
+  by Chebyshev-node least squares refined with Lawson iterations toward the
+  minimax polynomial of the absolute error.
+* x >= X1: the modulus-phase form of J1 (J1 = M cos(theta), Y1 = M sin(theta)),
+  with m(u) = M sqrt(pi x / 2) and h(u) = x (theta - x + 3 pi / 4) fitted as
+  polynomials in u = (X1 / x)^2; M and theta are computed from scipy's J1, Y1.
+* Percus-Yevick: nothing here; its series is built per experiment on the host.
+"""
+import math
+import sys
+
+import numpy as np
+import scipy.special as sp
+
+X1 = 4.0
+
+
+def f32(v):
+    return float(np.float32(v))
+
+
+def split3(c, bits=12):
+    parts = []
+    rem = c
+    for i in range(2):
+        e = math.frexp(rem)[1]
+        scale = 2.0 ** (bits - e)
+        p = math.floor(rem * scale + 0.5) / scale
+        parts.append(p)
+        rem = rem - p
+    parts.append(f32(rem))
+    return parts
+
+
+def lawson_fit(xs, ys, basis, iters=60):
+    """Weighted least squares with Lawson's weight update (approaches minimax)."""
+    A = np.stack([b(xs) for b in basis], axis=1)
+    w = np.ones_like(xs) / len(xs)
+    best = None
+    for _ in range(iters):
+        sw = np.sqrt(w)
+        c, *_ = np.linalg.lstsq(A * sw[:, None], ys * sw, rcond=None)
+        err = np.abs(A @ c - ys)
+        if best is None or err.max() < best[1]:
+            best = (c, err.max())
+        w = w * err
+        w = w / w.sum()
+    return best
+
+
+def fit_small(deg):
+    n = 4000
+    t = 0.5 * X1 * X1 * (1 - np.cos(np.pi * (np.arange(n) + 0.5) / n))
+    x = np.sqrt(t)
+    y = np.where(x > 0, 2 * sp.j1(np.maximum(x, 1e-300)) / np.maximum(x, 1e-300), 1.0)
+    s = t / (X1 * X1)
+    basis = [lambda ss, k=k: ss ** k for k in range(deg + 1)]
+    c, e = lawson_fit(s, y, basis)
+    return c, e
+
+
+def mod_phase(x):
+    j, y = sp.j1(x), sp.y1(x)
+    M = np.hypot(j, y)
+    th = np.arctan2(y, j)
+    ref = x - 0.75 * np.pi
+    th = th + 2 * np.pi * np.round((ref - th) / (2 * np.pi))
+    return M, th
+
+
+def fit_large(deg_m, deg_h):
+    n = 4000
+    u = 0.5 * (1 - np.cos(np.pi * (np.arange(n) + 0.5) / n))
+    u = np.maximum(u, 1e-6)
+    x = X1 / np.sqrt(u)
+    M, th = mod_phase(x)
+    m = M * np.sqrt(np.pi * x / 2)
+    h = x * (th - x + 0.75 * np.pi)
+    basis_m = [lambda uu, k=k: uu ** k for k in range(deg_m + 1)]
+    basis_h = [lambda uu, k=k: uu ** k for k in range(deg_h + 1)]
+    cm, em = lawson_fit(u, m, basis_m)
+    ch, eh = lawson_fit(u, h, basis_h)
+    return cm, em, ch, eh
+
+
+def main():
+    out = sys.stdout
+    cs, es = fit_small(7)
+    cm, em, ch, eh = fit_large(5, 5)
+    p2 = split3(math.pi / 2)
+    p4 = split3(math.pi / 4)
+    w = out.write
+    w("/* Generated by gen_coeffs.py -- FP32 coefficients of the device special\n")
+    w(" * functions (own fits, see the generator's docstring). Do not edit. */\n")
+    w("#pragma once\n\n")
+    w(f"#define SAS_J1_X1 {X1!r}f\n")
+    w(f"/* fit errors (FP64): small {es:.3e}, modulus {em:.3e}, phase {eh:.3e} */\n")
+    w("static const float SAS_PIO2_1 = %.9gf, SAS_PIO2_2 = %.9gf, SAS_PIO2_3 = %.9ef;\n" % tuple(p2))
+    w("static const float SAS_PIO4_1 = %.9gf, SAS_PIO4_2 = %.9gf, SAS_PIO4_3 = %.9ef;\n" % tuple(p4))
+    w("/* sin r = r + r^3 S(r^2), cos r = 1 + r^2 C(r^2): Taylor coefficients */\n")
+    S = [-1 / 6, 1 / 120, -1 / 5040, 1 / 362880, -1 / 39916800]
+    C = [-1 / 2, 1 / 24, -1 / 720, 1 / 40320, -1 / 3628800]
+    for name, arr in (("SAS_SIN_C", S), ("SAS_COS_C", C), ("SAS_J1S_C", list(cs)),
+                      ("SAS_J1M_C", list(cm)), ("SAS_J1H_C", list(ch))):
+        w(f"#define {name}_N {len(arr)}\n")
+        w(f"#define {name} {{" + ", ".join("%.9ef" % v for v in arr) + "}\n")
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,797 @@
+// Host runtime and C ABI of libsas: experiment objects, FP64 quadrature and
+// constant tables, launch configuration, error mapping.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sas_kernels.cuh"
+#include "sas_host.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+sas_status fail(sas_status s, const std::string& msg)
+{
+    g_last_error = msg;
+    return s;
+}
+
+sas_status cuda_fail(cudaError_t e, const char* what)
+{
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    return fail(e == cudaErrorMemoryAllocation ? SAS_ERR_OOM : SAS_ERR_CUDA, m);
+}
+
+#define SAS_CUDA(call, what)                        \
+    do {                                            \
+        cudaError_t _e = (call);                    \
+        if (_e != cudaSuccess) return cuda_fail(_e, what); \
+    } while (0)
+
+bool finite_all(std::initializer_list<double> v)
+{
+    for (double x : v)
+        if (!std::isfinite(x)) return false;
+    return true;
+}
+
+}  // namespace
+
+namespace sas {
+
+// ----------------------------------------------------------- quadrature
+// Gauss-Legendre nodes by Newton's method on P_n with the three-term
+// recurrence (initial guesses cos(pi (i - 1/4) / (n + 1/2))); weights
+// 2 / ((1 - x^2) P_n'(x)^2).
+void gauss_legendre(int n, double* x, double* w)
+{
+    if (n == 1) {
+        x[0] = 0.0;
+        w[0] = 2.0;
+        return;
+    }
+    for (int i = 0; i < (n + 1) / 2; ++i) {
+        double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+        double dp = 0.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            const double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        // recompute the derivative at the converged node
+        {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+        }
+        const double wi = 2.0 / ((1.0 - z * z) * dp * dp);
+        x[i] = -z;
+        x[n - 1 - i] = z;
+        w[i] = wi;
+        w[n - 1 - i] = wi;
+    }
+}
+
+// Eigenvalues and first eigenvector components of a symmetric tridiagonal
+// matrix (diag d, off-diagonal e) by the cyclic Jacobi method.
+static void jacobi_eigen(int n, const double* d, const double* e, double* lam, double* v0)
+{
+    std::vector<double> A((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) A[(size_t)i * n + i] = d[i];
+    for (int i = 0; i + 1 < n; ++i) A[(size_t)i * n + i + 1] = A[(size_t)(i + 1) * n + i] = e[i];
+    std::vector<double> row0(n, 0.0);
+    row0[0] = 1.0;   // first row of the accumulated rotation matrix
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                const double a = A[(size_t)i * n + j] * A[(size_t)i * n + j];
+                tot += a;
+                if (i != j) off += a;
+            }
+        if (off <= 1e-32 * tot) break;
+        for (int p = 0; p < n - 1; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                const double apq = A[(size_t)p * n + q];
+                if (apq == 0.0) continue;
+                const double app = A[(size_t)p * n + p], aqq = A[(size_t)q * n + q];
+                const double theta = (aqq - app) / (2.0 * apq);
+                const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+                for (int r = 0; r < n; ++r) {   // A <- A J (columns p, q)
+                    const double arp = A[(size_t)r * n + p], arq = A[(size_t)r * n + q];
+                    A[(size_t)r * n + p] = c * arp - s * arq;
+                    A[(size_t)r * n + q] = s * arp + c * arq;
+                }
+                for (int r = 0; r < n; ++r) {   // A <- J^T A (rows p, q)
+                    const double apr = A[(size_t)p * n + r], aqr = A[(size_t)q * n + r];
+                    A[(size_t)p * n + r] = c * apr - s * aqr;
+                    A[(size_t)q * n + r] = s * apr + c * aqr;
+                }
+                const double vp = row0[p], vq = row0[q];
+                row0[p] = c * vp - s * vq;
+                row0[q] = s * vp + c * vq;
+            }
+    }
+    for (int i = 0; i < n; ++i) {
+        lam[i] = A[(size_t)i * n + i];
+        v0[i] = row0[i];
+    }
+}
+
+// Generalised Gauss-Laguerre rule for x^alpha e^-x (Golub-Welsch), weights
+// normalised to sum 1, nodes ascending.
+void gauss_laguerre_gen(int n, double alpha, double* x, double* w)
+{
+    std::vector<double> d(n), e(n > 1 ? n - 1 : 1), lam(n), v0(n);
+    for (int k = 0; k < n; ++k) d[k] = 2.0 * k + alpha + 1.0;
+    for (int k = 1; k < n; ++k) e[k - 1] = std::sqrt(k * (k + alpha));
+    jacobi_eigen(n, d.data(), e.data(), lam.data(), v0.data());
+    std::vector<int> idx(n);
+    for (int i = 0; i < n; ++i) idx[i] = i;
+    std::sort(idx.begin(), idx.end(), [&](int a, int b) { return lam[a] < lam[b]; });
+    double sw = 0.0;
+    for (int i = 0; i < n; ++i) sw += v0[i] * v0[i];
+    for (int i = 0; i < n; ++i) {
+        x[i] = lam[idx[i]];
+        w[i] = v0[idx[i]] * v0[idx[i]] / sw;
+    }
+}
+
+// Schulz distribution of mean `mean`, relative width p: r_i = mean x_i/(z+1)
+// with the generalised Gauss-Laguerre rule of alpha = z = 1/p^2 - 1.
+void schulz_nodes(double mean, double p, int n, double* r, double* w)
+{
+    if (p <= 0.0 || n <= 1) {
+        r[0] = mean;
+        w[0] = 1.0;
+        return;
+    }
+    const double z = 1.0 / (p * p) - 1.0;
+    gauss_laguerre_gen(n, z, r, w);
+    for (int i = 0; i < n; ++i) r[i] = mean * r[i] / (z + 1.0);
+}
+
+// Orientation nodes: axis = cos(g) n + sin(g) (cos(s) e_theta + sin(s) e_phi),
+// g on Gauss-Legendre nodes of [0, gmax] with weight sin(g) (times the
+// Gaussian exp(-g^2 / (2 sigma^2)) unless isotropic), s on Gauss-Legendre
+// nodes of [0, 2 pi). Returns the node count.
+int orientation_nodes(double theta, double phi, double sigma, int ng, int npsi, int isotropic,
+                      double* c, double* wout)
+{
+    const double st = std::sin(theta), ct = std::cos(theta), sp = std::sin(phi), cp = std::cos(phi);
+    const double nv[3] = {st * cp, st * sp, ct};
+    const double et[3] = {ct * cp, ct * sp, -st};
+    const double ep[3] = {-sp, cp, 0.0};
+    if (!isotropic && (sigma <= 0.0 || ng * npsi <= 1)) {
+        c[0] = nv[0];
+        c[1] = nv[1];
+        c[2] = nv[2];
+        wout[0] = 1.0;
+        return 1;
+    }
+    const double gmax = isotropic ? M_PI : std::min(3.0 * sigma, M_PI);
+    std::vector<double> xg(ng), wg(ng), xs(npsi), ws(npsi);
+    gauss_legendre(ng, xg.data(), wg.data());
+    gauss_legendre(npsi, xs.data(), ws.data());
+    double tot = 0.0;
+    int k = 0;
+    for (int i = 0; i < ng; ++i) {
+        const double g = 0.5 * gmax * (xg[i] + 1.0);
+        double wgi = 0.5 * gmax * wg[i] * std::sin(g);
+        if (!isotropic) wgi *= std::exp(-g * g / (2.0 * sigma * sigma));
+        const double sg = std::sin(g), cg = std::cos(g);
+        for (int j = 0; j < npsi; ++j) {
+            const double s = M_PI * (xs[j] + 1.0);
+            const double cs = std::cos(s), ss = std::sin(s);
+            for (int a = 0; a < 3; ++a) c[3 * k + a] = cg * nv[a] + sg * (cs * et[a] + ss * ep[a]);
+            wout[k] = wgi * M_PI * ws[j];
+            tot += wout[k];
+            ++k;
+        }
+    }
+    for (int i = 0; i < k; ++i) wout[i] /= tot;
+    return k;
+}
+
+// Percus-Yevick: coefficients of G(A)/A in powers of A^2, from the Taylor
+// coefficients of the three brackets of G (derived in closed form):
+//   b1 = sin A - A cos A                      -> A^(2m+3): (-1)^m 2(m+1)/(2m+3)!
+//   b2 = 2A sin A + (2 - A^2) cos A - 2       -> A^(2m+4): (-1)^m 2(2m+3)(m+1)/(2m+4)!
+//   b3 = -A^4 cos A + 4[(3A^2-6) cos A + (A^3-6A) sin A + 6]
+//        -> A^N, N = 2m+6: (-1)^(m+1) [-N(N-1)(N-2)(N-3) - 12N(N-1)
+//                                      + 4N(N-1)(N-2) + 24N - 24] / N!
+void py_constants(double phi, double* alpha, double* beta, double* gamma, double* series, int nser)
+{
+    const double d = std::pow(1.0 - phi, 4);
+    *alpha = (1.0 + 2.0 * phi) * (1.0 + 2.0 * phi) / d;
+    *beta = -6.0 * phi * (1.0 + 0.5 * phi) * (1.0 + 0.5 * phi) / d;
+    *gamma = 0.5 * phi * (*alpha);
+    for (int m = 0; m < nser; ++m) {
+        const double sgn = (m % 2 == 0) ? 1.0 : -1.0;
+        const double c1 = sgn * 2.0 * (m + 1) / std::tgamma(2.0 * m + 4.0);
+        const double c2 = sgn * 2.0 * (2.0 * m + 3) * (m + 1) / std::tgamma(2.0 * m + 5.0);
+        const double N = 2.0 * m + 6.0;
+        const double br = -N * (N - 1) * (N - 2) * (N - 3) - 12.0 * N * (N - 1) + 4.0 * N * (N - 1) * (N - 2)
+                          + 24.0 * N - 24.0;
+        const double c3 = -sgn * br / std::tgamma(N + 1.0);
+        series[m] = (*alpha) * c1 + (*beta) * c2 + (*gamma) * c3;
+    }
+}
+
+// Tables of one model in FP64 (see sas_types.h for the layouts).
+sas_status build_model_tables(const sas_model_desc& m, ModelTables& t)
+{
+    const int np = (int)m.n_poly;
+    std::vector<double> r(np), w(np);
+    schulz_nodes(m.radius, m.poly, np, r.data(), w.data());
+    const int npoly = (m.poly > 0.0 && np > 1) ? np : 1;
+    t.poly.assign((size_t)npoly * SAS_POLY_STRIDE, 0.0);
+    double vmean = 0.0;
+    const double pi = M_PI;
+    for (int i = 0; i < npoly; ++i) {
+        double* p = t.poly.data() + (size_t)i * SAS_POLY_STRIDE;
+        const double ri = r[i];
+        if (m.kind == SAS_SPHERE) {
+            const double V = 4.0 / 3.0 * pi * ri * ri * ri;
+            const double F0 = (m.sld - m.sld_solvent) * V;
+            p[0] = ri; p[1] = 1.0 / ri; p[2] = w[i] * F0 * F0;
+            vmean += w[i] * V;
+        } else if (m.kind == SAS_CORE_SHELL) {
+            const double ro = ri + m.thickness;
+            const double Vc = 4.0 / 3.0 * pi * ri * ri * ri, Vo = 4.0 / 3.0 * pi * ro * ro * ro;
+            const double sw = std::sqrt(w[i]);
+            p[0] = ri; p[1] = 1.0 / ri; p[2] = ro; p[3] = 1.0 / ro;
+            p[4] = sw * (m.sld - m.sld_shell) * Vc;
+            p[5] = sw * (m.sld_shell - m.sld_solvent) * Vo;
+            vmean += w[i] * Vo;
+        } else if (m.kind == SAS_CYLINDER) {
+            const double V = pi * ri * ri * m.length;
+            const double F0 = (m.sld - m.sld_solvent) * V;
+            p[0] = ri; p[1] = 1.0 / ri; p[2] = 1.0 / std::sqrt(ri); p[3] = w[i] * F0 * F0;
+            vmean += w[i] * V;
+        } else {
+            const double V = 4.0 / 3.0 * pi * m.radius_polar * ri * ri;
+            const double F0 = (m.sld - m.sld_solvent) * V;
+            p[0] = ri * ri; p[1] = w[i] * F0 * F0;
+            vmean += w[i] * V;
+        }
+    }
+    t.n_poly = npoly;
+    t.scale = m.volume_fraction / vmean;
+    t.vmean = vmean;
+    if (m.kind == SAS_CYLINDER || m.kind == SAS_ELLIPSOID) {
+        const int nmax = (int)(m.n_gamma * m.n_psi);
+        std::vector<double> c((size_t)3 * std::max(nmax, 1)), wo(std::max(nmax, 1));
+        const int no = orientation_nodes(m.axis_theta, m.axis_phi, m.sigma_orient, (int)m.n_gamma,
+                                         (int)m.n_psi, (int)m.isotropic, c.data(), wo.data());
+        t.orient.assign((size_t)no * SAS_ORIENT_STRIDE, 0.0);
+        for (int i = 0; i < no; ++i) {
+            t.orient[(size_t)i * 4 + 0] = c[3 * i];
+            t.orient[(size_t)i * 4 + 1] = c[3 * i + 1];
+            t.orient[(size_t)i * 4 + 2] = c[3 * i + 2];
+            t.orient[(size_t)i * 4 + 3] = wo[i];
+        }
+        t.n_orient = no;
+    } else {
+        t.orient.assign(SAS_ORIENT_STRIDE, 0.0);
+        t.n_orient = 0;
+    }
+    t.half_length = 0.5 * m.length;
+    t.rp2 = m.radius_polar * m.radius_polar;
+    t.sq_kind = (int)m.sq_kind;
+    t.sq_2r = 2.0 * m.sq_radius;
+    t.sq_24phi = 24.0 * m.sq_fraction;
+    t.sq_switch = 3.0;
+    t.sq_series.assign(SAS_SQ_NSER, 0.0);
+    if (m.sq_kind == SAS_SQ_HARD_SPHERE_PY)
+        py_constants(m.sq_fraction, &t.sq_alpha, &t.sq_beta, &t.sq_gamma, t.sq_series.data(), SAS_SQ_NSER);
+    else
+        t.sq_alpha = t.sq_beta = t.sq_gamma = 0.0;
+    return SAS_OK;
+}
+
+template <typename T>
+ModelConst<T> model_const(const sas_model_desc& m, const ModelTables& t)
+{
+    ModelConst<T> c;
+    std::memset(&c, 0, sizeof(c));
+    c.kind = (int)m.kind;
+    c.sq_kind = t.sq_kind;
+    c.n_poly = t.n_poly;
+    c.n_orient = t.n_orient;
+    c.scale = (T)t.scale;
+    c.half_length = (T)t.half_length;
+    c.rp2 = (T)t.rp2;
+    c.sq_2r = (T)t.sq_2r;
+    c.sq_24phi = (T)t.sq_24phi;
+    c.sq_alpha = (T)t.sq_alpha;
+    c.sq_beta = (T)t.sq_beta;
+    c.sq_gamma = (T)t.sq_gamma;
+    c.sq_switch = (T)t.sq_switch;
+    for (int k = 0; k < SAS_SQ_NSER; ++k) c.sq_series[k] = (T)t.sq_series[k];
+    return c;
+}
+
+template <typename T>
+InstConst<T> inst_const(const sas_instrument& in)
+{
+    InstConst<T> c;
+    c.lambda0 = (T)in.lambda0;
+    c.dlambda = (T)in.dlambda_rel;
+    c.ap1_r = (T)in.ap1_radius;
+    c.ap1_z = (T)in.ap1_z;
+    c.ap2_r = (T)in.ap2_radius;
+    c.ap2_z = (T)in.ap2_z;
+    c.hx = (T)in.sample_half_x;
+    c.hy = (T)in.sample_half_y;
+    c.thick = (T)in.sample_thickness;
+    c.mu = (T)in.mu;
+    c.det_z = (T)in.det_distance;
+    c.px = (T)in.pixel_x;
+    c.py = (T)in.pixel_y;
+    c.half_wx = (T)(0.5 * (double)in.nx * in.pixel_x);
+    c.half_wy = (T)(0.5 * (double)in.ny * in.pixel_y);
+    c.area = (T)((double)in.nx * in.pixel_x * (double)in.ny * in.pixel_y);
+    c.two_pi = (T)(2.0 * M_PI);
+    c.nx = (int)in.nx;
+    c.ny = (int)in.ny;
+    return c;
+}
+
+template ModelConst<float> model_const<float>(const sas_model_desc&, const ModelTables&);
+template ModelConst<double> model_const<double>(const sas_model_desc&, const ModelTables&);
+template InstConst<float> inst_const<float>(const sas_instrument&);
+template InstConst<double> inst_const<double>(const sas_instrument&);
+
+sas_status validate_instrument(const sas_instrument* in)
+{
+    if (!in) return fail(SAS_ERR_ARG, "instrument is NULL");
+    if (!finite_all({in->lambda0, in->dlambda_rel, in->ap1_radius, in->ap1_z, in->ap2_radius,
+                     in->ap2_z, in->sample_half_x, in->sample_half_y, in->sample_thickness, in->mu,
+                     in->det_distance, in->pixel_x, in->pixel_y}))
+        return fail(SAS_ERR_ARG, "instrument has a non-finite value");
+    if (in->lambda0 <= 0.0) return fail(SAS_ERR_ARG, "lambda0 must be > 0");
+    if (in->dlambda_rel < 0.0 || in->dlambda_rel >= 1.0) return fail(SAS_ERR_ARG, "dlambda_rel must be in [0, 1)");
+    if (in->ap1_radius < 0.0 || in->ap2_radius < 0.0) return fail(SAS_ERR_ARG, "aperture radii must be >= 0");
+    if (!(in->ap1_z < in->ap2_z)) return fail(SAS_ERR_ARG, "ap1_z must be upstream of ap2_z");
+    if (in->ap2_z > 0.0) return fail(SAS_ERR_ARG, "ap2_z must be <= 0 (sample front face)");
+    if (in->sample_half_x <= 0.0 || in->sample_half_y <= 0.0 || in->sample_thickness <= 0.0)
+        return fail(SAS_ERR_ARG, "sample dimensions must be > 0");
+    if (in->mu < 0.0) return fail(SAS_ERR_ARG, "mu must be >= 0");
+    if (!(in->det_distance > in->sample_thickness)) return fail(SAS_ERR_ARG, "detector must be behind the sample");
+    if (in->pixel_x <= 0.0 || in->pixel_y <= 0.0) return fail(SAS_ERR_ARG, "pixel sizes must be > 0");
+    if (in->nx < 1 || in->ny < 1 || in->nx > 4096 || in->ny > 4096)
+        return fail(SAS_ERR_ARG, "nx, ny must be in [1, 4096]");
+    return SAS_OK;
+}
+
+sas_status validate_model(const sas_model_desc* m)
+{
+    if (!m) return fail(SAS_ERR_ARG, "model is NULL");
+    if (m->kind < 0 || m->kind > 3) return fail(SAS_ERR_ARG, "unknown model kind");
+    if (m->sq_kind != SAS_SQ_NONE && m->sq_kind != SAS_SQ_HARD_SPHERE_PY) return fail(SAS_ERR_ARG, "unknown S(Q) kind");
+    if (m->precision != SAS_FP32 && m->precision != SAS_FP64) return fail(SAS_ERR_ARG, "unknown precision");
+    if (m->n_poly < 1 || m->n_poly > SAS_MAX_POLY) return fail(SAS_ERR_ARG, "n_poly must be in [1, 64]");
+    if (m->n_gamma < 1 || m->n_gamma > SAS_MAX_ORIENT_SIDE || m->n_psi < 1 || m->n_psi > SAS_MAX_ORIENT_SIDE)
+        return fail(SAS_ERR_ARG, "n_gamma, n_psi must be in [1, 128]");
+    if (!finite_all({m->radius, m->thickness, m->length, m->radius_polar, m->sld, m->sld_shell,
+                     m->sld_solvent, m->volume_fraction, m->poly, m->sigma_orient, m->axis_theta,
+                     m->axis_phi, m->sq_radius, m->sq_fraction}))
+        return fail(SAS_ERR_ARG, "model has a non-finite value");
+    if (m->radius <= 0.0) return fail(SAS_ERR_ARG, "radius must be > 0");
+    if (m->kind == SAS_CORE_SHELL && m->thickness < 0.0) return fail(SAS_ERR_ARG, "thickness must be >= 0");
+    if (m->kind == SAS_CYLINDER && m->length <= 0.0) return fail(SAS_ERR_ARG, "length must be > 0");
+    if (m->kind == SAS_ELLIPSOID && m->radius_polar <= 0.0) return fail(SAS_ERR_ARG, "radius_polar must be > 0");
+    if (m->volume_fraction < 0.0) return fail(SAS_ERR_ARG, "volume_fraction must be >= 0");
+    if (m->poly < 0.0 || m->poly >= 1.0) return fail(SAS_ERR_ARG, "poly must be in [0, 1)");
+    if (m->sigma_orient < 0.0) return fail(SAS_ERR_ARG, "sigma_orient must be >= 0");
+    if (m->sq_kind == SAS_SQ_HARD_SPHERE_PY) {
+        if (m->sq_radius <= 0.0) return fail(SAS_ERR_ARG, "sq_radius must be > 0");
+        if (m->sq_fraction < 0.0 || m->sq_fraction >= 0.74) return fail(SAS_ERR_ARG, "sq_fraction must be in [0, 0.74)");
+    }
+    return SAS_OK;
+}
+
+}  // namespace sas
+
+using namespace sas;
+
+struct sas_experiment {
+    sas_instrument inst;
+    int device = 0, sm_count = 0, smem_optin = 0;
+    cudaStream_t stream = nullptr;
+    uint32_t exp_id = 0;
+    double* d_sum_w = nullptr;
+    double* d_sum_w2 = nullptr;
+    unsigned long long* d_count = nullptr;
+    double* d_trans = nullptr;
+    bool has_model = false;
+    sas_model_desc model;
+    ModelTables tables;
+    void* d_poly = nullptr;
+    void* d_orient = nullptr;
+    ModelConst<float> mcf;
+    ModelConst<double> mcd;
+    InstConst<float> icf;
+    InstConst<double> icd;
+    LaunchCfg cfg;
+    int stage_orient = 0;
+};
+
+namespace {
+
+template <typename T>
+cudaError_t dispatch_trace(sas_experiment* e, const TraceParams<T>& P, int* grid)
+{
+    switch (e->model.kind) {
+    case SAS_SPHERE: return Launcher<T, SAS_SPHERE>::trace(P, e->cfg, e->sm_count, e->stream, grid);
+    case SAS_CORE_SHELL: return Launcher<T, SAS_CORE_SHELL>::trace(P, e->cfg, e->sm_count, e->stream, grid);
+    case SAS_CYLINDER: return Launcher<T, SAS_CYLINDER>::trace(P, e->cfg, e->sm_count, e->stream, grid);
+    default: return Launcher<T, SAS_ELLIPSOID>::trace(P, e->cfg, e->sm_count, e->stream, grid);
+    }
+}
+
+template <typename T>
+cudaError_t dispatch_records(sas_experiment* e, const TraceParams<T>& P)
+{
+    switch (e->model.kind) {
+    case SAS_SPHERE: return Launcher<T, SAS_SPHERE>::records(P, e->stream);
+    case SAS_CORE_SHELL: return Launcher<T, SAS_CORE_SHELL>::records(P, e->stream);
+    case SAS_CYLINDER: return Launcher<T, SAS_CYLINDER>::records(P, e->stream);
+    default: return Launcher<T, SAS_ELLIPSOID>::records(P, e->stream);
+    }
+}
+
+template <typename T>
+cudaError_t dispatch_eval(sas_experiment* e, const ModelConst<T>& mc, const T* q, T* out, size_t n)
+{
+    const T* poly = (const T*)e->d_poly;
+    const T* orient = (const T*)e->d_orient;
+    switch (e->model.kind) {
+    case SAS_SPHERE: return Launcher<T, SAS_SPHERE>::eval(mc, poly, orient, q, out, n, e->stream);
+    case SAS_CORE_SHELL: return Launcher<T, SAS_CORE_SHELL>::eval(mc, poly, orient, q, out, n, e->stream);
+    case SAS_CYLINDER: return Launcher<T, SAS_CYLINDER>::eval(mc, poly, orient, q, out, n, e->stream);
+    default: return Launcher<T, SAS_ELLIPSOID>::eval(mc, poly, orient, q, out, n, e->stream);
+    }
+}
+
+template <typename T>
+TraceParams<T> make_params(sas_experiment* e, uint64_t first, uint64_t n, uint64_t seed)
+{
+    TraceParams<T> P;
+    std::memset(&P, 0, sizeof(P));
+    if constexpr (sizeof(T) == sizeof(float)) {
+        P.in = e->icf;
+        P.mc = e->mcf;
+    } else {
+        P.in = e->icd;
+        P.mc = e->mcd;
+    }
+    P.poly = (const T*)e->d_poly;
+    P.orient = (const T*)e->d_orient;
+    P.seed = seed;
+    P.first = first;
+    P.n = n;
+    P.exp_id = e->exp_id;
+    P.stage_orient = e->stage_orient;
+    P.sum_w = e->d_sum_w;
+    P.sum_w2 = e->d_sum_w2;
+    P.count = e->d_count;
+    P.trans = e->d_trans;
+    return P;
+}
+
+// Default launch configuration: the shared-memory histogram when it fits
+// next to the tables and the model has no orientation average (cheap
+// histories, tally-bound); otherwise the orientation table goes to shared
+// memory and tallies use FP64 global atomics (histories cost 1e5+ FLOP).
+void choose_config(sas_experiment* e)
+{
+    const size_t optin = (size_t)e->smem_optin;
+    const int npix = (int)(e->inst.nx * e->inst.ny);
+    const bool fp32 = e->model.precision == SAS_FP32;
+    const int np = e->tables.n_poly, no = e->tables.n_orient;
+    LaunchCfg c;
+    c.block = 512;
+    c.agg = 0;
+    c.ctas_per_sm = 0;
+    c.tally = TALLY_GLOBAL;
+    e->stage_orient = 0;
+    if (fp32) {
+        if (no > 1) {
+            e->stage_orient = table_bytes<float>(np, no, 1) <= optin ? 1 : 0;
+        } else if (table_bytes<float>(np, no, 0) + hist_bytes(npix) <= optin) {
+            c.tally = TALLY_SMEM;
+            c.block = 1024;
+        }
+    } else {
+        e->stage_orient = (no > 1 && table_bytes<double>(np, no, 1) <= optin) ? 1 : 0;
+        c.block = 256;
+    }
+    e->cfg = c;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sas_last_error(void) { return g_last_error.c_str(); }
+
+sas_status sas_device_info(int* sm_count, int* smem_per_block_optin, int* cc_major, int* cc_minor)
+{
+    int dev = 0;
+    SAS_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    cudaDeviceProp p;
+    SAS_CUDA(cudaGetDeviceProperties(&p, dev), "cudaGetDeviceProperties");
+    if (sm_count) *sm_count = p.multiProcessorCount;
+    if (smem_per_block_optin) *smem_per_block_optin = (int)p.sharedMemPerBlockOptin;
+    if (cc_major) *cc_major = p.major;
+    if (cc_minor) *cc_minor = p.minor;
+    return SAS_OK;
+}
+
+sas_status sas_create_experiment(const sas_instrument* inst, void* stream, sas_experiment** out)
+{
+    if (!out) return fail(SAS_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    sas_status st = validate_instrument(inst);
+    if (st != SAS_OK) return st;
+    sas_experiment* e = new (std::nothrow) sas_experiment();
+    if (!e) return fail(SAS_ERR_OOM, "host allocation failed");
+    e->inst = *inst;
+    e->stream = (cudaStream_t)stream;
+    cudaError_t ce = cudaGetDevice(&e->device);
+    if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&e->sm_count, cudaDevAttrMultiProcessorCount, e->device);
+    if (ce == cudaSuccess)
+        ce = cudaDeviceGetAttribute(&e->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, e->device);
+    const size_t npix = (size_t)inst->nx * (size_t)inst->ny;
+    if (ce == cudaSuccess) ce = cudaMalloc(&e->d_sum_w, npix * sizeof(double));
+    if (ce == cudaSuccess) ce = cudaMalloc(&e->d_sum_w2, npix * sizeof(double));
+    if (ce == cudaSuccess) ce = cudaMalloc(&e->d_count, npix * sizeof(unsigned long long));
+    if (ce == cudaSuccess) ce = cudaMalloc(&e->d_trans, sizeof(double));
+    if (ce != cudaSuccess) {
+        sas_destroy_experiment(e);
+        return cuda_fail(ce, "sas_create_experiment");
+    }
+    e->icf = inst_const<float>(*inst);
+    e->icd = inst_const<double>(*inst);
+    st = sas_reset_detector(e);
+    if (st != SAS_OK) {
+        sas_destroy_experiment(e);
+        return st;
+    }
+    *out = e;
+    return SAS_OK;
+}
+
+sas_status sas_set_model(sas_experiment* e, const sas_model_desc* m)
+{
+    if (!e) return fail(SAS_ERR_ARG, "experiment is NULL");
+    sas_status st = validate_model(m);
+    if (st != SAS_OK) return st;
+    ModelTables t;
+    st = build_model_tables(*m, t);
+    if (st != SAS_OK) return st;
+    const bool fp32 = m->precision == SAS_FP32;
+    const size_t es = fp32 ? sizeof(float) : sizeof(double);
+    std::vector<float> pf, of;
+    const void* hp;
+    const void* ho;
+    if (fp32) {
+        pf.assign(t.poly.begin(), t.poly.end());
+        of.assign(t.orient.begin(), t.orient.end());
+        hp = pf.data();
+        ho = of.data();
+    } else {
+        hp = t.poly.data();
+        ho = t.orient.data();
+    }
+    // the previous tables may still be read by queued kernels
+    SAS_CUDA(cudaStreamSynchronize(e->stream), "cudaStreamSynchronize");
+    cudaFree(e->d_poly);
+    cudaFree(e->d_orient);
+    e->d_poly = e->d_orient = nullptr;
+    e->has_model = false;
+    SAS_CUDA(cudaMalloc(&e->d_poly, t.poly.size() * es), "cudaMalloc(poly)");
+    SAS_CUDA(cudaMalloc(&e->d_orient, t.orient.size() * es), "cudaMalloc(orient)");
+    SAS_CUDA(cudaMemcpyAsync(e->d_poly, hp, t.poly.size() * es, cudaMemcpyHostToDevice, e->stream), "upload poly");
+    SAS_CUDA(cudaMemcpyAsync(e->d_orient, ho, t.orient.size() * es, cudaMemcpyHostToDevice, e->stream), "upload orient");
+    // the host vectors go out of scope: finish the copies first
+    SAS_CUDA(cudaStreamSynchronize(e->stream), "cudaStreamSynchronize");
+    e->model = *m;
+    e->tables = std::move(t);
+    e->mcf = model_const<float>(*m, e->tables);
+    e->mcd = model_const<double>(*m, e->tables);
+    e->has_model = true;
+    choose_config(e);
+    return SAS_OK;
+}
+
+sas_status sas_set_experiment_id(sas_experiment* e, uint32_t id)
+{
+    if (!e) return fail(SAS_ERR_ARG, "experiment is NULL");
+    e->exp_id = id;
+    return SAS_OK;
+}
+
+sas_status sas_set_stream(sas_experiment* e, void* stream)
+{
+    if (!e) return fail(SAS_ERR_ARG, "experiment is NULL");
+    e->stream = (cudaStream_t)stream;
+    return SAS_OK;
+}
+
+sas_status sas_reset_detector(sas_experiment* e)
+{
+    if (!e) return fail(SAS_ERR_ARG, "experiment is NULL");
+    const size_t npix = (size_t)e->inst.nx * (size_t)e->inst.ny;
+    SAS_CUDA(cudaMemsetAsync(e->d_sum_w, 0, npix * sizeof(double), e->stream), "memset");
+    SAS_CUDA(cudaMemsetAsync(e->d_sum_w2, 0, npix * sizeof(double), e->stream), "memset");
+    SAS_CUDA(cudaMemsetAsync(e->d_count, 0, npix * sizeof(unsigned long long), e->stream), "memset");
+    SAS_CUDA(cudaMemsetAsync(e->d_trans, 0, sizeof(double), e->stream), "memset");
+    return SAS_OK;
+}
+
+sas_status sas_trace_range(sas_experiment* e, uint64_t first, uint64_t n, uint64_t seed)
+{
+    if (!e) return fail(SAS_ERR_ARG, "experiment is NULL");
+    if (!e->has_model) return fail(SAS_ERR_STATE, "sas_set_model has not been called");
+    if (first + n < first) return fail(SAS_ERR_ARG, "neutron index range overflows 64 bits");
+    if (n == 0) return SAS_OK;
+    cudaError_t ce;
+    int grid = 0;
+    if (e->model.precision == SAS_FP32)
+        ce = dispatch_trace<float>(e, make_params<float>(e, first, n, seed), &grid);
+    else
+        ce = dispatch_trace<double>(e, make_params<double>(e, first, n, seed), &grid);
+    if (ce != cudaSuccess) return cuda_fail(ce, "trace launch");
+    return SAS_OK;
+}
+
+sas_status sas_trace(sas_experiment* e, uint64_t n, uint64_t seed)
+{
+    sas_status st = sas_reset_detector(e);
+    if (st != SAS_OK) return st;
+    return sas_trace_range(e, 0, n, seed);
+}
+
+sas_status sas_read_detector(const sas_experiment* e, double* sum_w, double* sum_w2, uint64_t* count,
+                             size_t n_pixels, double* transmitted)
+{
+    if (!e) return fail(SAS_ERR_ARG, "experiment is NULL");
+    const size_t npix = (size_t)e->inst.nx * (size_t)e->inst.ny;
+    if ((sum_w || sum_w2 || count) && n_pixels != npix)
+        return fail(SAS_ERR_ARG, "n_pixels does not match nx*ny");
+    if (sum_w) SAS_CUDA(cudaMemcpyAsync(sum_w, e->d_sum_w, npix * 8, cudaMemcpyDeviceToHost, e->stream), "read sum_w");
+    if (sum_w2) SAS_CUDA(cudaMemcpyAsync(sum_w2, e->d_sum_w2, npix * 8, cudaMemcpyDeviceToHost, e->stream), "read sum_w2");
+    if (count) SAS_CUDA(cudaMemcpyAsync(count, e->d_count, npix * 8, cudaMemcpyDeviceToHost, e->stream), "read count");
+    if (transmitted) SAS_CUDA(cudaMemcpyAsync(transmitted, e->d_trans, 8, cudaMemcpyDeviceToHost, e->stream), "read trans");
+    SAS_CUDA(cudaStreamSynchronize(e->stream), "cudaStreamSynchronize");
+    return SAS_OK;
+}
+
+sas_status sas_detector_device(const sas_experiment* e, const double** sum_w, const double** sum_w2,
+                               const uint64_t** count, const double** transmitted)
+{
+    if (!e) return fail(SAS_ERR_ARG, "experiment is NULL");
+    if (sum_w) *sum_w = e->d_sum_w;
+    if (sum_w2) *sum_w2 = e->d_sum_w2;
+    if (count) *count = (const uint64_t*)e->d_count;
+    if (transmitted) *transmitted = e->d_trans;
+    return SAS_OK;
+}
+
+sas_status sas_eval_model(sas_experiment* e, const void* q_xyz, size_t n, void* out)
+{
+    if (!e) return fail(SAS_ERR_ARG, "experiment is NULL");
+    if (!e->has_model) return fail(SAS_ERR_STATE, "sas_set_model has not been called");
+    if (n == 0) return SAS_OK;
+    if (!q_xyz || !out) return fail(SAS_ERR_ARG, "NULL buffer");
+    cudaError_t ce;
+    if (e->model.precision == SAS_FP32)
+        ce = dispatch_eval<float>(e, e->mcf, (const float*)q_xyz, (float*)out, n);
+    else
+        ce = dispatch_eval<double>(e, e->mcd, (const double*)q_xyz, (double*)out, n);
+    if (ce != cudaSuccess) return cuda_fail(ce, "eval launch");
+    return SAS_OK;
+}
+
+sas_status sas_trace_records(sas_experiment* e, uint64_t first, uint64_t n, uint64_t seed,
+                             int32_t* pixel, double* weight)
+{
+    if (!e) return fail(SAS_ERR_ARG, "experiment is NULL");
+    if (!e->has_model) return fail(SAS_ERR_STATE, "sas_set_model has not been called");
+    if (n == 0) return SAS_OK;
+    if (!pixel || !weight) return fail(SAS_ERR_ARG, "NULL buffer");
+    if (first + n < first) return fail(SAS_ERR_ARG, "neutron index range overflows 64 bits");
+    cudaError_t ce;
+    if (e->model.precision == SAS_FP32) {
+        TraceParams<float> P = make_params<float>(e, first, n, seed);
+        P.pixel_out = pixel;
+        P.weight_out = weight;
+        ce = dispatch_records<float>(e, P);
+    } else {
+        TraceParams<double> P = make_params<double>(e, first, n, seed);
+        P.pixel_out = pixel;
+        P.weight_out = weight;
+        ce = dispatch_records<double>(e, P);
+    }
+    if (ce != cudaSuccess) return cuda_fail(ce, "records launch");
+    return SAS_OK;
+}
+
+sas_status sas_sync(sas_experiment* e)
+{
+    if (!e) return fail(SAS_ERR_ARG, "experiment is NULL");
+    SAS_CUDA(cudaStreamSynchronize(e->stream), "cudaStreamSynchronize");
+    return SAS_OK;
+}
+
+sas_status sas_destroy_experiment(sas_experiment* e)
+{
+    if (!e) return SAS_OK;
+    if (e->stream || true) cudaStreamSynchronize(e->stream);
+    cudaFree(e->d_sum_w);
+    cudaFree(e->d_sum_w2);
+    cudaFree(e->d_count);
+    cudaFree(e->d_trans);
+    cudaFree(e->d_poly);
+    cudaFree(e->d_orient);
+    delete e;
+    return SAS_OK;
+}
+
+// ---- host-side utilities (no GPU needed): the library's own quadrature
+
+sas_status sas_gauss_legendre(int n, double* x, double* w)
+{
+    if (n < 1 || n > 1024 || !x || !w) return fail(SAS_ERR_ARG, "bad arguments");
+    gauss_legendre(n, x, w);
+    return SAS_OK;
+}
+
+sas_status sas_schulz_nodes(double mean, double p, int n, double* r, double* w)
+{
+    if (n < 1 || n > SAS_MAX_POLY || !r || !w || !(mean > 0.0) || !(p >= 0.0 && p < 1.0))
+        return fail(SAS_ERR_ARG, "bad arguments");
+    schulz_nodes(mean, p, n, r, w);
+    return SAS_OK;
+}
+
+sas_status sas_orientation_nodes(double theta, double phi, double sigma, int n_gamma, int n_psi,
+                                 int isotropic, double* c_xyz, double* w, int* n_out)
+{
+    if (n_gamma < 1 || n_psi < 1 || n_gamma > SAS_MAX_ORIENT_SIDE || n_psi > SAS_MAX_ORIENT_SIDE ||
+        !c_xyz || !w || !n_out)
+        return fail(SAS_ERR_ARG, "bad arguments");
+    *n_out = orientation_nodes(theta, phi, sigma, n_gamma, n_psi, isotropic, c_xyz, w);
+    return SAS_OK;
+}
+
+sas_status sas_py_series(double phi, double* alpha_beta_gamma, double* series, int nser)
+{
+    if (!alpha_beta_gamma || !series || nser < 1 || nser > 64) return fail(SAS_ERR_ARG, "bad arguments");
+    py_constants(phi, alpha_beta_gamma, alpha_beta_gamma + 1, alpha_beta_gamma + 2, series, nser);
+    return SAS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,19 @@
+/* Generated by gen_coeffs.py -- FP32 coefficients of the device special
+ * functions (own fits, see the generator's docstring). Do not edit. */
+#pragma once
+
+#define SAS_J1_X1 4.0f
+/* fit errors (FP64): small 1.118e-10, modulus 3.425e-09, phase 1.404e-08 */
+static const float SAS_PIO2_1 = 1.57080078f, SAS_PIO2_2 = -4.45358455e-06f, SAS_PIO2_3 = -8.705516308e-10f;
+static const float SAS_PIO4_1 = 0.785400391f, SAS_PIO4_2 = -2.22679228e-06f, SAS_PIO4_3 = -4.352758154e-10f;
+/* sin r = r + r^3 S(r^2), cos r = 1 + r^2 C(r^2): Taylor coefficients */
+#define SAS_SIN_C_N 5
+#define SAS_SIN_C {-1.666666667e-01f, 8.333333333e-03f, -1.984126984e-04f, 2.755731922e-06f, -2.505210839e-08f}
+#define SAS_COS_C_N 5
+#define SAS_COS_C {-5.000000000e-01f, 4.166666667e-02f, -1.388888889e-03f, 2.480158730e-05f, -2.755731922e-07f}
+#define SAS_J1S_C_N 8
+#define SAS_J1S_C {9.999999999e-01f, -1.999999986e+00f, 1.333333029e+00f, -4.444419945e-01f, 8.887918082e-02f, -1.183089002e-02f, 1.103495466e-03f, -6.449931052e-05f}
+#define SAS_J1M_C_N 6
+#define SAS_J1M_C {1.000000003e+00f, 1.171846577e-02f, -7.514159251e-04f, 1.757710064e-04f, -5.899622254e-05f, 1.244681187e-05f}
+#define SAS_J1H_C_N 6
+#define SAS_J1H_C {3.749999861e-01f, -1.025273366e-02f, 1.432409031e-03f, -4.877704056e-04f, 1.948607847e-04f, -4.437957135e-05f}

@@ -1,0 +1,354 @@
+// Device building blocks of the SANS trace: Philox4x32-10, the neutron
+// history geometry, the four form-factor models with their polydispersity
+// and orientation quadratures, and the Percus-Yevick structure factor.
+// Templated on the arithmetic type: float (FP32 trace, own special
+// functions from sas_math.cuh) or double (FP64 trace, CUDA's double
+// precision math functions).
+#pragma once
+
+#include <stdint.h>
+#include <cuda_runtime.h>
+#include "sas_math.cuh"
+#include "sas_types.h"
+
+namespace sas {
+
+// ------------------------------------------------------------------ Philox
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32->64-bit multiplications with the round constants 0xD2511F53 and
+// 0xCD9E8D57, key schedule incremented by the Weyl constants 0x9E3779B9 and
+// 0xBB67AE85.
+__device__ __forceinline__ uint4 philox(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// uniform on (0,1): 23 random bits plus one half (exact in float and double)
+template <typename T>
+__device__ __forceinline__ T u01(uint32_t x)
+{
+    return (T)((x >> 9) | 0u) * (T)(1.0 / 8388608.0) + (T)(0.5 / 8388608.0);
+}
+
+// --------------------------------------------------------------- math glue
+template <typename T> struct M;
+
+template <> struct M<float> {
+    static __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+    static __device__ __forceinline__ float sqrt_(float x) { return __fsqrt_rn(x); }
+    static __device__ __forceinline__ float rsqrt(float x) { return rsqrtf(x); }
+    static __device__ __forceinline__ float exp_(float x) { return __expf(x); }
+    static __device__ __forceinline__ void sincos2pi(float u, float& s, float& c)
+    {
+        sincospif(2.0f * u, &s, &c);
+    }
+    static __device__ __forceinline__ void sincos_(float x, float& s, float& c)
+    {
+        sas_sincosf(x, s, c);
+    }
+    static __device__ __forceinline__ float sphere_f(float x, float inv)
+    {
+        return sas_sphere_f(x, inv);
+    }
+    static __device__ __forceinline__ float sinc(float y, float inv) { return sas_sinc(y, inv); }
+    static __device__ __forceinline__ float cyl_a(float x, float inv, float rsx)
+    {
+        return sas_cyl_a(x, inv, rsx);
+    }
+};
+
+template <> struct M<double> {
+    static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+    static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+    static __device__ __forceinline__ double rsqrt(double x) { return rsqrt(x); }
+    static __device__ __forceinline__ double exp_(double x) { return exp(x); }
+    static __device__ __forceinline__ void sincos2pi(double u, double& s, double& c)
+    {
+        sincospi(2.0 * u, &s, &c);
+    }
+    static __device__ __forceinline__ void sincos_(double x, double& s, double& c)
+    {
+        sincos(x, &s, &c);
+    }
+    static __device__ __forceinline__ double sphere_f(double x, double inv)
+    {
+        if (x < 0.1) {   // Taylor series of 3 j1(x)/x
+            const double t = x * x;
+            return 1.0 - t * (1.0 / 10.0) + t * t * (1.0 / 280.0) - t * t * t * (1.0 / 15120.0)
+                   + t * t * t * t * (1.0 / 1330560.0);
+        }
+        double s, c;
+        sincos(x, &s, &c);
+        return 3.0 * (s - x * c) * inv * inv * inv;
+    }
+    static __device__ __forceinline__ double sinc(double y, double inv)
+    {
+        return (y < 1e-8) ? 1.0 : sin(y) * inv;
+    }
+    static __device__ __forceinline__ double cyl_a(double x, double inv, double)
+    {
+        return (x < 1e-6) ? 1.0 - 0.125 * x * x : 2.0 * j1(x) * inv;
+    }
+};
+
+// ----------------------------------------------------------- Percus-Yevick
+// S(q) = 1 / (1 + 24 phi G(A)/A), A = 2 q R (hard-sphere closed form);
+// below A = switch the series of G(A)/A in A^2 prepared on the host.
+template <typename T>
+__device__ __forceinline__ T structure_factor(T q, const ModelConst<T>& mc)
+{
+    if (mc.sq_kind != SAS_SQ_HARD_SPHERE_PY) return (T)1;
+    const T A = q * mc.sq_2r;
+    T ga;
+    if (A < mc.sq_switch) {
+        const T a2 = A * A;
+        T r = mc.sq_series[SAS_SQ_NSER - 1];
+#pragma unroll
+        for (int k = SAS_SQ_NSER - 2; k >= 0; --k) r = fma(r, a2, mc.sq_series[k]);
+        ga = r;
+    } else {
+        T s, c;
+        M<T>::sincos_(A, s, c);
+        const T iA = M<T>::rcp(A);
+        const T A2 = A * A;
+        const T b1 = s - A * c;
+        const T b2 = (T)2 * A * s + ((T)2 - A2) * c - (T)2;
+        const T b3 = -A2 * A2 * c + (T)4 * (((T)3 * A2 - (T)6) * c + (A2 * A - (T)6 * A) * s + (T)6);
+        const T i3 = iA * iA * iA;
+        ga = i3 * (mc.sq_alpha * b1 + iA * (mc.sq_beta * b2 + iA * iA * mc.sq_gamma * b3));
+    }
+    return M<T>::rcp((T)1 + mc.sq_24phi * ga);
+}
+
+// ---------------------------------------------------------------- models
+// Quadrature tables (see sas_types.h for the per-kind layout):
+//   poly   [n_poly][8]  nodes of the polydisperse radius with folded weights
+//   orient [n_orient][4] axis unit vector and normalised weight
+// Returns <|F|^2> (without the phi/<V> factor and S(Q)).
+
+template <typename T>
+__device__ __forceinline__ T avg_sphere(T q, T iq, const T* __restrict__ poly, int np)
+{
+    T acc = 0;
+#pragma unroll 4
+    for (int i = 0; i < np; ++i) {
+        const T* p = poly + 8 * i;
+        const T f = M<T>::sphere_f(q * p[0], iq * p[1]);
+        acc = fma(p[2], f * f, acc);
+    }
+    return acc;
+}
+
+template <typename T>
+__device__ __forceinline__ T avg_core_shell(T q, T iq, const T* __restrict__ poly, int np)
+{
+    T acc = 0;
+#pragma unroll 4
+    for (int i = 0; i < np; ++i) {
+        const T* p = poly + 8 * i;
+        const T f1 = M<T>::sphere_f(q * p[0], iq * p[1]);
+        const T f2 = M<T>::sphere_f(q * p[2], iq * p[3]);
+        const T F = fma(p[4], f1, p[5] * f2);
+        acc = fma(F, F, acc);
+    }
+    return acc;
+}
+
+// Kahan-compensated accumulation of the orientation sum.
+template <typename T>
+struct Kahan {
+    T s = 0, c = 0;
+    __device__ __forceinline__ void add(T v)
+    {
+        const T y = v - c;
+        const T t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+};
+
+template <typename T>
+__device__ __forceinline__ T avg_cylinder(const T qv[3], const T* __restrict__ poly, int np,
+                                          const T* __restrict__ orient, int no, T half_len)
+{
+    Kahan<T> k;
+    for (int o = 0; o < no; ++o) {
+        const T* c = orient + 4 * o;
+        const T qc = fma(qv[0], c[0], fma(qv[1], c[1], qv[2] * c[2]));
+        const T x0 = fma(qv[1], c[2], -qv[2] * c[1]);
+        const T x1 = fma(qv[2], c[0], -qv[0] * c[2]);
+        const T x2 = fma(qv[0], c[1], -qv[1] * c[0]);
+        const T qab2 = fma(x0, x0, fma(x1, x1, x2 * x2));
+        const T y = fabs(qc) * half_len;
+        const T sn = M<T>::sinc(y, M<T>::rcp(y));
+        const T qab = M<T>::sqrt_(qab2);
+        const T iq = M<T>::rcp(qab);
+        const T rsq = M<T>::rsqrt(qab);
+        T inner = 0;
+#pragma unroll 4
+        for (int i = 0; i < np; ++i) {
+            const T* p = poly + 8 * i;
+            const T a = M<T>::cyl_a(qab * p[0], iq * p[1], rsq * p[2]);
+            inner = fma(p[3], a * a, inner);
+        }
+        k.add(c[3] * sn * sn * inner);
+    }
+    return k.s;
+}
+
+template <typename T>
+__device__ __forceinline__ T avg_ellipsoid(const T qv[3], const T* __restrict__ poly, int np,
+                                           const T* __restrict__ orient, int no, T rp2)
+{
+    Kahan<T> k;
+    for (int o = 0; o < no; ++o) {
+        const T* c = orient + 4 * o;
+        const T qc = fma(qv[0], c[0], fma(qv[1], c[1], qv[2] * c[2]));
+        const T x0 = fma(qv[1], c[2], -qv[2] * c[1]);
+        const T x1 = fma(qv[2], c[0], -qv[0] * c[2]);
+        const T x2 = fma(qv[0], c[1], -qv[1] * c[0]);
+        const T qab2 = fma(x0, x0, fma(x1, x1, x2 * x2));
+        const T pol = rp2 * qc * qc;
+        T inner = 0;
+#pragma unroll 4
+        for (int i = 0; i < np; ++i) {
+            const T* p = poly + 8 * i;
+            const T x2e = fma(p[0], qab2, pol);
+            const T inv = M<T>::rsqrt(x2e);
+            const T f = M<T>::sphere_f(x2e * inv, inv);
+            inner = fma(p[1], f * f, inner);
+        }
+        k.add(c[3] * inner);
+    }
+    return k.s;
+}
+
+// dSigma/dOmega(Q) in 1/angstrom
+template <typename T, int KIND>
+__device__ __forceinline__ T dsigma(const T qv[3], const ModelConst<T>& mc,
+                                    const T* __restrict__ poly, const T* __restrict__ orient)
+{
+    const T q2 = fma(qv[0], qv[0], fma(qv[1], qv[1], qv[2] * qv[2]));
+    const T q = M<T>::sqrt_(q2);
+    T avg;
+    if (KIND == SAS_SPHERE) {
+        avg = avg_sphere<T>(q, M<T>::rcp(q), poly, mc.n_poly);
+    } else if (KIND == SAS_CORE_SHELL) {
+        avg = avg_core_shell<T>(q, M<T>::rcp(q), poly, mc.n_poly);
+    } else if (KIND == SAS_CYLINDER) {
+        avg = avg_cylinder<T>(qv, poly, mc.n_poly, orient, mc.n_orient, mc.half_length);
+    } else {
+        avg = avg_ellipsoid<T>(qv, poly, mc.n_poly, orient, mc.n_orient, mc.rp2);
+    }
+    return mc.scale * avg * structure_factor<T>(q, mc);
+}
+
+// ------------------------------------------------------------- geometry
+template <typename T>
+struct History {
+    T q[3];      // scattering vector, 1/angstrom
+    T pref;      // l * dOmega * attenuation * 1e10 (1/angstrom -> 1/m)
+    T wt;        // transmitted (unscattered) weight
+    int pixel;   // -1: the neutron missed the sample
+};
+
+// entry/exit ray parameters of the box |x|<=hx, |y|<=hy, 0<=z<=t
+template <typename T>
+__device__ __forceinline__ bool slab(const InstConst<T>& in, const T o[3], const T d[3], T& a, T& b)
+{
+    const T lo[3] = {-in.hx, -in.hy, (T)0};
+    const T hi[3] = {in.hx, in.hy, in.thick};
+    a = (T)-1e30;
+    b = (T)1e30;
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (d[k] == (T)0) {
+            ok = ok && (o[k] >= lo[k]) && (o[k] <= hi[k]);
+        } else {
+            const T id = (T)1 / d[k];
+            T t1 = (lo[k] - o[k]) * id, t2 = (hi[k] - o[k]) * id;
+            const T mn = fmin(t1, t2), mx = fmax(t1, t2);
+            a = fmax(a, mn);
+            b = fmin(b, mx);
+        }
+    }
+    a = fmax(a, (T)0);
+    return ok && (b > a);
+}
+
+// One history up to the scattering vector and the weight prefactor.
+template <typename T>
+__device__ __forceinline__ History<T> history(const InstConst<T>& in, uint64_t seed, uint32_t exp_id,
+                                              uint64_t index)
+{
+    const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    const uint4 r0 = philox(make_uint4(0u, exp_id, (uint32_t)index, (uint32_t)(index >> 32)), key);
+    const uint4 r1 = philox(make_uint4(1u, exp_id, (uint32_t)index, (uint32_t)(index >> 32)), key);
+    History<T> h;
+    // source wavelength: triangular spread by inverse CDF
+    const T u = u01<T>(r0.x);
+    const T tri = (u < (T)0.5) ? M<T>::sqrt_((T)2 * u) - (T)1 : (T)1 - M<T>::sqrt_((T)2 * ((T)1 - u));
+    const T lambda = in.lambda0 * ((T)1 + in.dlambda * tri);
+    // pinholes: area-uniform points on both discs
+    T s1, c1, s2, c2;
+    M<T>::sincos2pi(u01<T>(r0.z), s1, c1);
+    M<T>::sincos2pi(u01<T>(r1.x), s2, c2);
+    const T rr1 = in.ap1_r * M<T>::sqrt_(u01<T>(r0.y));
+    const T rr2 = in.ap2_r * M<T>::sqrt_(u01<T>(r0.w));
+    const T p2[3] = {rr2 * c2, rr2 * s2, in.ap2_z};
+    T d[3] = {p2[0] - rr1 * c1, p2[1] - rr1 * s1, in.ap2_z - in.ap1_z};
+    const T idn = M<T>::rsqrt(fma(d[0], d[0], fma(d[1], d[1], d[2] * d[2])));
+    const T ki[3] = {d[0] * idn, d[1] * idn, d[2] * idn};
+    T t_in, t_out;
+    if (!slab<T>(in, p2, ki, t_in, t_out)) {
+        h.pixel = -1;
+        h.wt = (T)1;
+        h.pref = (T)0;
+        h.q[0] = h.q[1] = h.q[2] = (T)0;
+        return h;
+    }
+    const T l = t_out - t_in;
+    h.wt = (in.mu > (T)0) ? M<T>::exp_(-in.mu * l) : (T)1;
+    const T s = u01<T>(r1.y) * l;
+    const T ps[3] = {fma(t_in + s, ki[0], p2[0]), fma(t_in + s, ki[1], p2[1]),
+                     fma(t_in + s, ki[2], p2[2])};
+    // detector point: integer pixel choice, sub-pixel position from the remainder
+    const uint64_t mx = (uint64_t)(r1.z >> 9) * (uint64_t)in.nx;
+    const uint64_t my = (uint64_t)(r1.w >> 9) * (uint64_t)in.ny;
+    const int ix = (int)(mx >> 23), iy = (int)(my >> 23);
+    const T fx = (T)(uint32_t)(mx & 0x7FFFFFu) * (T)(1.0 / 8388608.0) + (T)(0.5 / 8388608.0);
+    const T fy = (T)(uint32_t)(my & 0x7FFFFFu) * (T)(1.0 / 8388608.0) + (T)(0.5 / 8388608.0);
+    const T pd0 = fma((T)ix + fx, in.px, -in.half_wx);
+    const T pd1 = fma((T)iy + fy, in.py, -in.half_wy);
+    const T v[3] = {pd0 - ps[0], pd1 - ps[1], in.det_z - ps[2]};
+    const T ir = M<T>::rsqrt(fma(v[0], v[0], fma(v[1], v[1], v[2] * v[2])));
+    const T ko[3] = {v[0] * ir, v[1] * ir, v[2] * ir};
+    const T domega = in.area * ko[2] * ir * ir;
+    // Q = k (k_out - k_in); the z difference without cancellation
+    const T k = in.two_pi / lambda;
+    const T tin = fma(ki[0], ki[0], ki[1] * ki[1]);
+    const T tout = fma(ko[0], ko[0], ko[1] * ko[1]);
+    h.q[0] = k * (ko[0] - ki[0]);
+    h.q[1] = k * (ko[1] - ki[1]);
+    h.q[2] = k * (tin - tout) / (ko[2] + ki[2]);
+    T att = (T)1;
+    if (in.mu > (T)0) {
+        T e_in, e_out, l_out = (T)0;
+        if (slab<T>(in, ps, ko, e_in, e_out)) l_out = e_out - e_in;
+        att = M<T>::exp_(-in.mu * (s + l_out));
+    }
+    h.pref = l * domega * att * (T)1e10;
+    h.pixel = iy * in.nx + ix;
+    return h;
+}
+
+}  // namespace sas

@@ -1,0 +1,47 @@
+// Plain-data structures passed from the host runtime to the kernels.
+#pragma once
+
+#include <stdint.h>
+#include "../../include/sas.h"
+
+#define SAS_SQ_NSER 14        // terms of the Percus-Yevick G(A)/A series in A^2
+#define SAS_MAX_POLY 64
+#define SAS_MAX_ORIENT_SIDE 128
+#define SAS_POLY_STRIDE 8     // values per polydispersity node
+#define SAS_ORIENT_STRIDE 4   // values per orientation node
+
+namespace sas {
+
+// Instrument in the trace precision (derived quantities precomputed).
+template <typename T>
+struct InstConst {
+    T lambda0, dlambda;
+    T ap1_r, ap1_z, ap2_r, ap2_z;
+    T hx, hy, thick, mu;
+    T det_z, px, py, half_wx, half_wy, area;
+    T two_pi;
+    int nx, ny;
+};
+
+// Model constants in the trace precision.
+//   poly table per node (SAS_POLY_STRIDE values):
+//     sphere     {r, 1/r, w (drho V)^2, 0...}
+//     core-shell {r_c, 1/r_c, r_o, 1/r_o, sqrt(w) (rho_c - rho_s) V_c,
+//                 sqrt(w) (rho_s - rho_solv) V_o, 0, 0}
+//     cylinder   {r, 1/r, 1/sqrt(r), w (drho V)^2, 0...}
+//     ellipsoid  {r_e^2, w (drho V)^2, 0...}
+//   orient table per node: {c_x, c_y, c_z, weight}
+template <typename T>
+struct ModelConst {
+    int kind, sq_kind, n_poly, n_orient;
+    T scale;         // phi / <V>
+    T half_length;   // cylinder L / 2
+    T rp2;           // ellipsoid polar radius squared
+    T sq_2r;         // 2 R_hs
+    T sq_24phi;      // 24 phi_hs
+    T sq_alpha, sq_beta, sq_gamma;
+    T sq_switch;     // A below which the series is used
+    T sq_series[SAS_SQ_NSER];
+};
+
+}  // namespace sas
