@@ -171,6 +171,83 @@ const char *sas_last_error(void);
 sas_status sas_device_info(int *sm_count, int *smem_per_block_optin, int *cc_major,
                            int *cc_minor);
 
+/* ---- launch configuration and autotuning (single experiment) ---------- */
+
+typedef struct sas_launch_config {
+    int32_t block;           /* threads per CTA: multiple of 32 in [32, 1024] */
+    int32_t tally;           /* 0: FP64 global atomics per history;
+                                1: per-CTA FP32 Kahan shared-memory histogram (FP32 only) */
+    int32_t agg;             /* 1: combine lanes of a warp hitting the same pixel first */
+    int32_t ctas_per_sm;     /* resident CTAs per SM of the persistent grid (0: all that fit) */
+    int32_t stage_orient;    /* 1: copy the orientation table into shared memory */
+    int32_t reserved;
+} sas_launch_config;
+
+/* Read / replace the launch configuration of the experiment's trace kernel.
+ * SAS_ERR_ARG if it does not fit (shared memory) or is malformed;
+ * SAS_ERR_STATE before sas_set_model. */
+sas_status sas_get_launch_config(const sas_experiment *exp, sas_launch_config *cfg);
+sas_status sas_set_launch_config(sas_experiment *exp, const sas_launch_config *cfg);
+
+/* Autotuner: times every valid configuration (block 256/512/1024, tally,
+ * warp aggregation, orientation staging) on n_sample histories with CUDA
+ * events, keeps the fastest and caches it per (model kind, precision, node
+ * counts, detector size, S(Q)): later sas_set_model calls with the same key
+ * start from it. Zeroes the detector. Synchronous. */
+sas_status sas_autotune(sas_experiment *exp, uint64_t n_sample, uint64_t seed,
+                        sas_launch_config *best, double *best_ms);
+
+/* ---- batched form (many experiments, one persistent graph launch) ----- */
+
+typedef struct sas_batch sas_batch;                 /* opaque, library-owned */
+
+typedef struct sas_batch_config {
+    int32_t block;             /* threads per CTA: multiple of 32 in [32, 1024] */
+    int32_t ctas_per_sm;       /* 0: as many as fit */
+    int32_t use_hist;          /* 1: models without an orientation average tally
+                                  through the shared-memory histogram */
+    int32_t reserved;
+    double target_item_flop;   /* work-item size (FLOP) the index ranges are cut to */
+} sas_batch_config;
+
+/* Create a batch of n_exp experiments sharing one instrument (Sec. II.A),
+ * each with its own model (FP32 only) and neutron count; experiment e uses
+ * Philox experiment id e and its own FP64 detector. Builds all quadrature
+ * tables, cuts the index ranges into work items ordered longest-first and
+ * allocates n_exp * nx * ny * 24 bytes of detectors. */
+sas_status sas_create_batch(const sas_instrument *inst, const sas_model_desc *models,
+                            const uint64_t *counts, size_t n_exp, void *stream, sas_batch **out);
+
+/* Zero all detectors and trace every experiment: one CUDA-graph launch
+ * (memsets + one persistent kernel pulling work items from an atomic
+ * counter). The graph is captured on first use and after config changes.
+ * Asynchronous on the batch's stream. */
+sas_status sas_trace_batch(sas_batch *batch, uint64_t seed);
+
+/* Copy experiment exp's detector into caller-owned host buffers
+ * (n_pixels = nx*ny; NULL pointers skip). Synchronises the stream. */
+sas_status sas_read_batch_detector(const sas_batch *batch, size_t exp, double *sum_w, double *sum_w2,
+                                   uint64_t *count, size_t n_pixels, double *transmitted);
+
+/* Library-owned device arrays [n_exp][nx*ny] (transmitted: [n_exp]). */
+sas_status sas_batch_detector_device(const sas_batch *batch, const double **sum_w,
+                                     const double **sum_w2, const uint64_t **count,
+                                     const double **transmitted);
+
+sas_status sas_batch_set_config(sas_batch *batch, const sas_batch_config *cfg);
+sas_status sas_batch_get_config(const sas_batch *batch, sas_batch_config *cfg);
+
+/* Work items, persistent grid size, dynamic shared memory, total histories. */
+sas_status sas_batch_info(const sas_batch *batch, uint32_t *n_items, int *grid, size_t *smem,
+                          uint64_t *total_histories);
+
+/* Autotuner of the batch: times block size x item size x histogram on/off
+ * (one traced batch each, CUDA events) and keeps the fastest. Synchronous. */
+sas_status sas_batch_autotune(sas_batch *batch, uint64_t seed, sas_batch_config *best,
+                              double *best_ms);
+
+sas_status sas_destroy_batch(sas_batch *batch);
+
 /* ---- host-side utilities (no GPU needed): the library's own FP64 tables.
  * They are the quadrature rules sas_set_model builds for the trace. */
 

@@ -2,10 +2,11 @@
 
 Run once (python gen_coeffs.py > sas_coeffs.h); the output is committed.
 
-* sin / cos on [-pi/4, pi/4]: Taylor coefficients (exact rationals).
-* pi/2 and pi/4 split into three FP32 parts for Cody-Waite argument
-  reduction (first two parts with 12 significant bits so that k * part is
-  exact for |k| < 2^12).
+* sin / cos on [-pi/4, pi/4]: S(t) = (sin r - r) / r^3 and
+  C(t) = (cos r - 1) / r^2 as polynomials in t = r^2 (3 and 4 terms), fitted
+  toward the minimax absolute error on t in [0, (1.01 pi/4)^2].
+* pi/2 and pi/4 split into two FP32 parts (fl(c), fl(c - fl(c))) for the
+  FMA form of Cody-Waite argument reduction.
 * a(x) = 2 J1(x) / x for 0 <= x <= X1: a polynomial in s = (x / X1)^2, fitted here
   by Chebyshev-node least squares refined with Lawson iterations toward the
   minimax polynomial of the absolute error.
@@ -91,24 +92,43 @@ def fit_large(deg_m, deg_h):
     return cm, em, ch, eh
 
 
+def fit_trig():
+    n = 4000
+    tmax = (1.01 * math.pi / 4) ** 2
+    t = 0.5 * tmax * (1 - np.cos(np.pi * (np.arange(n) + 0.5) / n))
+    r = np.sqrt(t)
+    S = np.where(r > 1e-4, (np.sin(r) - r) / np.maximum(r, 1e-300) ** 3, -1 / 6 + t / 120)
+    C = np.where(r > 1e-4, (np.cos(r) - 1) / np.maximum(t, 1e-300), -0.5 + t / 24)
+    bS = [lambda tt, k=k: tt ** k for k in range(3)]
+    bC = [lambda tt, k=k: tt ** k for k in range(4)]
+    cS, eS = lawson_fit(t, S, bS)
+    cC, eC = lawson_fit(t, C, bC)
+    return cS, eS, cC, eC
+
+
+def split2(c):
+    hi = f32(c)
+    return [hi, f32(c - hi)]
+
+
 def main():
     out = sys.stdout
     cs, es = fit_small(7)
     cm, em, ch, eh = fit_large(5, 5)
-    p2 = split3(math.pi / 2)
-    p4 = split3(math.pi / 4)
+    cS, eS, cC, eC = fit_trig()
+    p2 = split2(math.pi / 2)
+    p4 = split2(math.pi / 4)
     w = out.write
     w("/* Generated by gen_coeffs.py -- FP32 coefficients of the device special\n")
     w(" * functions (own fits, see the generator's docstring). Do not edit. */\n")
     w("#pragma once\n\n")
     w(f"#define SAS_J1_X1 {X1!r}f\n")
-    w(f"/* fit errors (FP64): small {es:.3e}, modulus {em:.3e}, phase {eh:.3e} */\n")
-    w("static const float SAS_PIO2_1 = %.9gf, SAS_PIO2_2 = %.9gf, SAS_PIO2_3 = %.9ef;\n" % tuple(p2))
-    w("static const float SAS_PIO4_1 = %.9gf, SAS_PIO4_2 = %.9gf, SAS_PIO4_3 = %.9ef;\n" % tuple(p4))
-    w("/* sin r = r + r^3 S(r^2), cos r = 1 + r^2 C(r^2): Taylor coefficients */\n")
-    S = [-1 / 6, 1 / 120, -1 / 5040, 1 / 362880, -1 / 39916800]
-    C = [-1 / 2, 1 / 24, -1 / 720, 1 / 40320, -1 / 3628800]
-    for name, arr in (("SAS_SIN_C", S), ("SAS_COS_C", C), ("SAS_J1S_C", list(cs)),
+    w(f"/* fit errors (FP64): small {es:.3e}, modulus {em:.3e}, phase {eh:.3e}, "
+      f"S {eS:.3e}, C {eC:.3e} */\n")
+    w("#define SAS_PIO2_1 %.9ef\n#define SAS_PIO2_2 %.9ef\n" % tuple(p2))
+    w("#define SAS_PIO4_1 %.9ef\n#define SAS_PIO4_2 %.9ef\n" % tuple(p4))
+    w("/* sin r = r + r^3 S(r^2), cos r = 1 + r^2 C(r^2) */\n")
+    for name, arr in (("SAS_SIN_C", list(cS)), ("SAS_COS_C", list(cC)), ("SAS_J1S_C", list(cs)),
                       ("SAS_J1M_C", list(cm)), ("SAS_J1H_C", list(ch))):
         w(f"#define {name}_N {len(arr)}\n")
         w(f"#define {name} {{" + ", ".join("%.9ef" % v for v in arr) + "}\n")

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -45,6 +46,22 @@ bool finite_all(std::initializer_list<double> v)
 }  // namespace
 
 namespace sas {
+
+sas_status set_error(sas_status s, const std::string& msg) { return fail(s, msg); }
+sas_status set_cuda_error(cudaError_t e, const char* what) { return cuda_fail(e, what); }
+
+// Cost model of one history in FLOP (FMA = 2): the nominal per-term counts
+// of the kernels' formulas (sphere amplitude 33, cylinder radial term 22,
+// orientation node 60, geometry 150, Percus-Yevick 40).
+double host_flops_per_history(const sas_model_desc& m, int np, int no)
+{
+    double per;
+    if (m.kind == SAS_SPHERE) per = np * 36.0;
+    else if (m.kind == SAS_CORE_SHELL) per = np * 71.0;
+    else if (m.kind == SAS_CYLINDER) per = no * (60.0 + np * 22.0);
+    else per = no * (60.0 + np * 38.0);
+    return per + 150.0 + (m.sq_kind == SAS_SQ_HARD_SPHERE_PY ? 40.0 : 0.0);
+}
 
 // ----------------------------------------------------------- quadrature
 // Gauss-Legendre nodes by Newton's method on P_n with the three-term
@@ -253,15 +270,15 @@ sas_status build_model_tables(const sas_model_desc& m, ModelTables& t)
         if (m.kind == SAS_SPHERE) {
             const double V = 4.0 / 3.0 * pi * ri * ri * ri;
             const double F0 = (m.sld - m.sld_solvent) * V;
-            p[0] = ri; p[1] = 1.0 / ri; p[2] = w[i] * F0 * F0;
+            p[0] = ri; p[1] = 1.0 / ri; p[2] = 9.0 * w[i] * F0 * F0;
             vmean += w[i] * V;
         } else if (m.kind == SAS_CORE_SHELL) {
             const double ro = ri + m.thickness;
             const double Vc = 4.0 / 3.0 * pi * ri * ri * ri, Vo = 4.0 / 3.0 * pi * ro * ro * ro;
             const double sw = std::sqrt(w[i]);
             p[0] = ri; p[1] = 1.0 / ri; p[2] = ro; p[3] = 1.0 / ro;
-            p[4] = sw * (m.sld - m.sld_shell) * Vc;
-            p[5] = sw * (m.sld_shell - m.sld_solvent) * Vo;
+            p[4] = 3.0 * sw * (m.sld - m.sld_shell) * Vc;
+            p[5] = 3.0 * sw * (m.sld_shell - m.sld_solvent) * Vo;
             vmean += w[i] * Vo;
         } else if (m.kind == SAS_CYLINDER) {
             const double V = pi * ri * ri * m.length;
@@ -271,7 +288,7 @@ sas_status build_model_tables(const sas_model_desc& m, ModelTables& t)
         } else {
             const double V = 4.0 / 3.0 * pi * m.radius_polar * ri * ri;
             const double F0 = (m.sld - m.sld_solvent) * V;
-            p[0] = ri * ri; p[1] = w[i] * F0 * F0;
+            p[0] = ri * ri; p[1] = 9.0 * w[i] * F0 * F0;
             vmean += w[i] * V;
         }
     }
@@ -530,11 +547,162 @@ void choose_config(sas_experiment* e)
     e->cfg = c;
 }
 
+// Process-wide cache of tuned launch configurations, keyed by what decides
+// the kernel's cost profile: model kind, precision, node counts, detector
+// size and structure factor.
+struct TuneKey {
+    int64_t kind, precision, sq;
+    int np, no, npix;
+    bool operator==(const TuneKey& o) const
+    {
+        return kind == o.kind && precision == o.precision && sq == o.sq && np == o.np && no == o.no &&
+               npix == o.npix;
+    }
+};
+struct TuneEntry {
+    TuneKey key;
+    LaunchCfg cfg;
+    int stage_orient;
+};
+std::vector<TuneEntry> g_tuned;
+std::mutex g_tuned_mu;
+
+TuneKey tune_key(const sas_experiment* e)
+{
+    TuneKey k;
+    k.kind = e->model.kind;
+    k.precision = e->model.precision;
+    k.sq = e->model.sq_kind;
+    k.np = e->tables.n_poly;
+    k.no = e->tables.n_orient;
+    k.npix = (int)(e->inst.nx * e->inst.ny);
+    return k;
+}
+
+bool lookup_tuned(sas_experiment* e)
+{
+    std::lock_guard<std::mutex> lk(g_tuned_mu);
+    const TuneKey k = tune_key(e);
+    for (const TuneEntry& t : g_tuned)
+        if (t.key == k) {
+            e->cfg = t.cfg;
+            e->stage_orient = t.stage_orient;
+            return true;
+        }
+    return false;
+}
+
+void store_tuned(const sas_experiment* e)
+{
+    std::lock_guard<std::mutex> lk(g_tuned_mu);
+    const TuneKey k = tune_key(e);
+    for (TuneEntry& t : g_tuned)
+        if (t.key == k) {
+            t.cfg = e->cfg;
+            t.stage_orient = e->stage_orient;
+            return;
+        }
+    g_tuned.push_back(TuneEntry{k, e->cfg, e->stage_orient});
+}
+
 }  // namespace
 
 extern "C" {
 
 const char* sas_last_error(void) { return g_last_error.c_str(); }
+
+sas_status sas_get_launch_config(const sas_experiment* e, sas_launch_config* c)
+{
+    if (!e || !c) return fail(SAS_ERR_ARG, "NULL argument");
+    c->block = e->cfg.block;
+    c->tally = e->cfg.tally;
+    c->agg = e->cfg.agg;
+    c->ctas_per_sm = e->cfg.ctas_per_sm;
+    c->stage_orient = e->stage_orient;
+    c->reserved = 0;
+    return SAS_OK;
+}
+
+sas_status sas_set_launch_config(sas_experiment* e, const sas_launch_config* c)
+{
+    if (!e || !c) return fail(SAS_ERR_ARG, "NULL argument");
+    if (!e->has_model) return fail(SAS_ERR_STATE, "sas_set_model has not been called");
+    if (c->block < 32 || c->block > 1024 || c->block % 32) return fail(SAS_ERR_ARG, "bad block size");
+    if (c->tally != TALLY_GLOBAL && c->tally != TALLY_SMEM) return fail(SAS_ERR_ARG, "bad tally mode");
+    if (c->ctas_per_sm < 0) return fail(SAS_ERR_ARG, "bad ctas_per_sm");
+    const bool fp32 = e->model.precision == SAS_FP32;
+    const int np = e->tables.n_poly, no = e->tables.n_orient;
+    const size_t optin = (size_t)e->smem_optin;
+    const int stage = (c->stage_orient && no > 1) ? 1 : 0;
+    size_t need = fp32 ? table_bytes<float>(np, no, stage) : table_bytes<double>(np, no, stage);
+    if (c->tally == TALLY_SMEM) {
+        if (!fp32) return fail(SAS_ERR_ARG, "the shared-memory histogram is FP32 only");
+        need += hist_bytes((int)(e->inst.nx * e->inst.ny));
+    }
+    if (need > optin) return fail(SAS_ERR_ARG, "configuration needs more shared memory than a CTA has");
+    e->cfg.block = c->block;
+    e->cfg.tally = c->tally;
+    e->cfg.agg = c->agg ? 1 : 0;
+    e->cfg.ctas_per_sm = c->ctas_per_sm;
+    e->stage_orient = stage;
+    return SAS_OK;
+}
+
+// Time the candidate launch configurations on n_sample histories (after one
+// warm-up each) and keep the fastest; the result is cached for every later
+// experiment with the same key.
+sas_status sas_autotune(sas_experiment* e, uint64_t n_sample, uint64_t seed, sas_launch_config* best_out,
+                        double* best_ms)
+{
+    if (!e) return fail(SAS_ERR_ARG, "experiment is NULL");
+    if (!e->has_model) return fail(SAS_ERR_STATE, "sas_set_model has not been called");
+    if (n_sample == 0) return fail(SAS_ERR_ARG, "n_sample must be > 0");
+    const int blocks[] = {256, 512, 1024};
+    cudaEvent_t e0, e1;
+    SAS_CUDA(cudaEventCreate(&e0), "event");
+    SAS_CUDA(cudaEventCreate(&e1), "event");
+    sas_launch_config best;
+    sas_get_launch_config(e, &best);
+    float best_t = 1e30f;
+    const bool aniso = e->tables.n_orient > 1;
+    for (int tally : {TALLY_SMEM, TALLY_GLOBAL})
+        for (int agg : {0, 1})
+            for (int stage : {1, 0}) {
+                if (!aniso && stage) continue;
+                for (int blk : blocks) {
+                    sas_launch_config c;
+                    c.block = blk;
+                    c.tally = tally;
+                    c.agg = agg;
+                    c.ctas_per_sm = 0;
+                    c.stage_orient = stage;
+                    c.reserved = 0;
+                    if (sas_set_launch_config(e, &c) != SAS_OK) continue;
+                    if (sas_trace_range(e, 0, n_sample, seed) != SAS_OK) continue;
+                    cudaEventRecord(e0, e->stream);
+                    sas_status st = sas_trace_range(e, 0, n_sample, seed);
+                    cudaEventRecord(e1, e->stream);
+                    if (cudaEventSynchronize(e1) != cudaSuccess || st != SAS_OK) continue;
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (ms < best_t) {
+                        best_t = ms;
+                        best = c;
+                    }
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    sas_status st = sas_reset_detector(e);
+    if (st != SAS_OK) return st;
+    if (best_t >= 1e30f) return fail(SAS_ERR_CUDA, "no launch configuration ran");
+    st = sas_set_launch_config(e, &best);
+    if (st != SAS_OK) return st;
+    store_tuned(e);
+    if (best_out) *best_out = best;
+    if (best_ms) *best_ms = best_t;
+    return SAS_OK;
+}
 
 sas_status sas_device_info(int* sm_count, int* smem_per_block_optin, int* cc_major, int* cc_minor)
 {
@@ -622,7 +790,7 @@ sas_status sas_set_model(sas_experiment* e, const sas_model_desc* m)
     e->mcf = model_const<float>(*m, e->tables);
     e->mcd = model_const<double>(*m, e->tables);
     e->has_model = true;
-    choose_config(e);
+    if (!lookup_tuned(e)) choose_config(e);
     return SAS_OK;
 }
 

@@ -3,14 +3,16 @@
 #pragma once
 
 #define SAS_J1_X1 4.0f
-/* fit errors (FP64): small 1.118e-10, modulus 3.425e-09, phase 1.404e-08 */
-static const float SAS_PIO2_1 = 1.57080078f, SAS_PIO2_2 = -4.45358455e-06f, SAS_PIO2_3 = -8.705516308e-10f;
-static const float SAS_PIO4_1 = 0.785400391f, SAS_PIO4_2 = -2.22679228e-06f, SAS_PIO4_3 = -4.352758154e-10f;
-/* sin r = r + r^3 S(r^2), cos r = 1 + r^2 C(r^2): Taylor coefficients */
-#define SAS_SIN_C_N 5
-#define SAS_SIN_C {-1.666666667e-01f, 8.333333333e-03f, -1.984126984e-04f, 2.755731922e-06f, -2.505210839e-08f}
-#define SAS_COS_C_N 5
-#define SAS_COS_C {-5.000000000e-01f, 4.166666667e-02f, -1.388888889e-03f, 2.480158730e-05f, -2.755731922e-07f}
+/* fit errors (FP64): small 1.118e-10, modulus 3.425e-09, phase 1.404e-08, S 2.137e-08, C 9.145e-10 */
+#define SAS_PIO2_1 1.570796371e+00f
+#define SAS_PIO2_2 -4.371138829e-08f
+#define SAS_PIO4_1 7.853981853e-01f
+#define SAS_PIO4_2 -2.185569414e-08f
+/* sin r = r + r^3 S(r^2), cos r = 1 + r^2 C(r^2) */
+#define SAS_SIN_C_N 3
+#define SAS_SIN_C {-1.666666455e-01f, 8.332725399e-03f, -1.958295501e-04f}
+#define SAS_COS_C_N 4
+#define SAS_COS_C {-4.999999992e-01f, 4.166663354e-02f, -1.388677625e-03f, 2.437042503e-05f}
 #define SAS_J1S_C_N 8
 #define SAS_J1S_C {9.999999999e-01f, -1.999999986e+00f, 1.333333029e+00f, -4.444419945e-01f, 8.887918082e-02f, -1.183089002e-02f, 1.103495466e-03f, -6.449931052e-05f}
 #define SAS_J1M_C_N 6

@@ -54,9 +54,10 @@ template <> struct M<float> {
     {
         sas_sincosf(x, s, c);
     }
-    static __device__ __forceinline__ float sphere_f(float x, float inv)
+    // (sin x - x cos x) / x^3 = f(x) / 3
+    static __device__ __forceinline__ float sphere_g(float x, float inv)
     {
-        return sas_sphere_f(x, inv);
+        return sas_sphere_g(x, inv);
     }
     static __device__ __forceinline__ float sinc(float y, float inv) { return sas_sinc(y, inv); }
     static __device__ __forceinline__ float cyl_a(float x, float inv, float rsx)
@@ -67,9 +68,9 @@ template <> struct M<float> {
 
 template <> struct M<double> {
     static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
-    static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
-    static __device__ __forceinline__ double rsqrt(double x) { return rsqrt(x); }
-    static __device__ __forceinline__ double exp_(double x) { return exp(x); }
+    static __device__ __forceinline__ double sqrt_(double x) { return ::sqrt(x); }
+    static __device__ __forceinline__ double rsqrt(double x) { return ::rsqrt(x); }
+    static __device__ __forceinline__ double exp_(double x) { return ::exp(x); }
     static __device__ __forceinline__ void sincos2pi(double u, double& s, double& c)
     {
         sincospi(2.0 * u, &s, &c);
@@ -78,16 +79,17 @@ template <> struct M<double> {
     {
         sincos(x, &s, &c);
     }
-    static __device__ __forceinline__ double sphere_f(double x, double inv)
+    // (sin x - x cos x) / x^3 = f(x) / 3
+    static __device__ __forceinline__ double sphere_g(double x, double inv)
     {
-        if (x < 0.1) {   // Taylor series of 3 j1(x)/x
+        if (x < 0.1) {   // Taylor series of j1(x)/x
             const double t = x * x;
-            return 1.0 - t * (1.0 / 10.0) + t * t * (1.0 / 280.0) - t * t * t * (1.0 / 15120.0)
-                   + t * t * t * t * (1.0 / 1330560.0);
+            return (1.0 - t * (1.0 / 10.0) + t * t * (1.0 / 280.0) - t * t * t * (1.0 / 15120.0)
+                    + t * t * t * t * (1.0 / 1330560.0)) * (1.0 / 3.0);
         }
         double s, c;
         sincos(x, &s, &c);
-        return 3.0 * (s - x * c) * inv * inv * inv;
+        return (s - x * c) * inv * inv * inv;
     }
     static __device__ __forceinline__ double sinc(double y, double inv)
     {
@@ -141,8 +143,8 @@ __device__ __forceinline__ T avg_sphere(T q, T iq, const T* __restrict__ poly, i
 #pragma unroll 4
     for (int i = 0; i < np; ++i) {
         const T* p = poly + 8 * i;
-        const T f = M<T>::sphere_f(q * p[0], iq * p[1]);
-        acc = fma(p[2], f * f, acc);
+        const T g = M<T>::sphere_g(q * p[0], iq * p[1]);
+        acc = fma(p[2], g * g, acc);
     }
     return acc;
 }
@@ -154,9 +156,9 @@ __device__ __forceinline__ T avg_core_shell(T q, T iq, const T* __restrict__ pol
 #pragma unroll 4
     for (int i = 0; i < np; ++i) {
         const T* p = poly + 8 * i;
-        const T f1 = M<T>::sphere_f(q * p[0], iq * p[1]);
-        const T f2 = M<T>::sphere_f(q * p[2], iq * p[3]);
-        const T F = fma(p[4], f1, p[5] * f2);
+        const T g1 = M<T>::sphere_g(q * p[0], iq * p[1]);
+        const T g2 = M<T>::sphere_g(q * p[2], iq * p[3]);
+        const T F = fma(p[4], g1, p[5] * g2);
         acc = fma(F, F, acc);
     }
     return acc;
@@ -223,8 +225,8 @@ __device__ __forceinline__ T avg_ellipsoid(const T qv[3], const T* __restrict__ 
             const T* p = poly + 8 * i;
             const T x2e = fma(p[0], qab2, pol);
             const T inv = M<T>::rsqrt(x2e);
-            const T f = M<T>::sphere_f(x2e * inv, inv);
-            inner = fma(p[1], f * f, inner);
+            const T g = M<T>::sphere_g(x2e * inv, inv);
+            inner = fma(p[1], g * g, inner);
         }
         k.add(c[3] * inner);
     }

@@ -3,19 +3,21 @@
 //
 // Written for the device; the same source compiles as plain C++ (SAS_HD
 // empty) so that its arithmetic can be checked against FP64 references on a
-// host without a GPU. Only IEEE-exact primitives are used (fmaf, rintf,
-// multiplication, addition), so host and device give identical bits.
+// host without a GPU. Only IEEE-exact primitives are used (fmaf,
+// multiplication, addition, bit moves), so host and device give identical bits.
 //
-//  * sin / cos: Cody-Waite reduction by pi/2 in three parts, Taylor
-//    polynomials on [-pi/4, pi/4] (Abramowitz and Stegun 4.3.65/4.3.66 style).
-//  * sphere amplitude f(x) = 3 (sin x - x cos x) / x^3: in the first
-//    quadrant it is evaluated as 3 (S - C) from the same polynomials, which
-//    removes the cancellation of the closed form at small x.
+//  * sin / cos: two-part FMA Cody-Waite reduction by pi/2, polynomials on
+//    [-pi/4, pi/4] fitted toward minimax (gen_coeffs.py).
+//  * sphere amplitude f(x) = 3 (sin x - x cos x) / x^3: quadrant handled by
+//    two FMAs, one select and a sign flip; in the first quadrant it is
+//    3 (S - C) from the same polynomials, free of the closed form's
+//    cancellation at small x.
 //  * cylinder radial factor a(x) = 2 J1(x) / x: a fitted polynomial in
 //    (x / X1)^2 below X1 = 4, the modulus-phase form of J1 above it.
 #pragma once
 
 #include <math.h>
+#include <string.h>
 #include "sas_coeffs.h"
 
 #if defined(__CUDACC__)
@@ -38,36 +40,60 @@ struct SasTrig {
     float t;   // r^2
     float S;   // sin r = r + r^3 S(t)
     float C;   // cos r = 1 + t C(t)
-    int q;     // quadrant k mod 4
+    int kb;    // low bits of the quadrant index k (k mod 4 = kb & 3)
 };
 
-// x = k pi/2 + r, |r| <= pi/4 (up to rounding), valid for |x| < 2^12 pi/2.
+// Round to the nearest integer with the 1.5 * 2^23 constant (valid for
+// |v| < 2^22): v + C lands on an integer grid; k = (v + C) - C and the low
+// bits of (v + C) hold k mod 2^22. Two FP32 adds, no conversion instruction.
+#define SAS_RND_C 12582912.0f
+
+SAS_HD float sas_round_magic(float v, int& kbits)
+{
+    const float t = v + SAS_RND_C;
+    float bits_src = t;
+    unsigned u;
+    memcpy(&u, &bits_src, sizeof(u));
+    kbits = (int)u;
+    return t - SAS_RND_C;
+}
+
+SAS_HD float sas_flip_sign(float v, int bit31)
+{
+    unsigned u;
+    memcpy(&u, &v, sizeof(u));
+    u ^= (unsigned)bit31 & 0x80000000u;
+    float o;
+    memcpy(&o, &u, sizeof(o));
+    return o;
+}
+
+// x = k pi/2 + r, |r| <= pi/4 (up to rounding), for |x| < 2^20. Two-part
+// Cody-Waite in FMA form: the products k * part are exact inside the FMA.
 SAS_HD SasTrig sas_reduce_pio2(float x)
 {
-    const float cs[4] = {-1.666666667e-01f, 8.333333333e-03f, -1.984126984e-04f,
-                         2.755731922e-06f};
-    const float cc[5] = SAS_COS_C;
+    const float cs[3] = SAS_SIN_C;
+    const float cc[4] = SAS_COS_C;
     SasTrig o;
-    float k = rintf(x * 0.636619772f);
+    float k = sas_round_magic(x * 0.636619772f, o.kb);
     float r = fmaf(-k, SAS_PIO2_1, x);
     r = fmaf(-k, SAS_PIO2_2, r);
-    r = fmaf(-k, SAS_PIO2_3, r);
     o.r = r;
     o.t = r * r;
     o.S = sas_horner(cs, o.t);
     o.C = sas_horner(cc, o.t);
-    o.q = ((int)k) & 3;
     return o;
 }
 
 SAS_HD void sas_trig_sincos(const SasTrig& g, float& s, float& c)
 {
-    float sr = fmaf(g.r * g.t, g.S, g.r);
-    float cr = fmaf(g.t, g.C, 1.0f);
-    float a = (g.q & 1) ? cr : sr;      // sin of the quadrant-shifted angle
-    float b = (g.q & 1) ? sr : cr;
-    s = (g.q & 2) ? -a : a;
-    c = ((g.q + 1) & 2) ? -b : b;
+    const float sr = fmaf(g.r * g.t, g.S, g.r);
+    const float cr = fmaf(g.t, g.C, 1.0f);
+    const int q = g.kb & 3;
+    const float a = (q & 1) ? cr : sr;      // sin of the quadrant-shifted angle
+    const float b = (q & 1) ? sr : cr;
+    s = (q & 2) ? -a : a;
+    c = ((q + 1) & 2) ? -b : b;
 }
 
 SAS_HD void sas_sincosf(float x, float& s, float& c)
@@ -81,23 +107,32 @@ SAS_HD float sas_sinc(float y, float inv)
     SasTrig g = sas_reduce_pio2(y);
     float s, c;
     sas_trig_sincos(g, s, c);
-    float big = s * inv;
-    float small = fmaf(g.t, g.S, 1.0f);   // k = 0: r = y exactly
-    return (g.q == 0 && fabsf(y) < 1.0f) ? small : big;
+    const float big = s * inv;
+    const float small = fmaf(g.t, g.S, 1.0f);   // k = 0: r = y exactly
+    return (y < 0.78539816f) ? small : big;
 }
 
-// f(x) = 3 (sin x - x cos x) / x^3, x >= 0; inv = 1 / x (may be inf at x = 0)
-SAS_HD float sas_sphere_f(float x, float inv)
+// g(x) = f(x) / 3 = (sin x - x cos x) / x^3 for x >= 0 (f is the sphere
+// amplitude 3 j1(x) / x); inv = 1 / x (may be inf at x = 0).
+// With x = k pi/2 + r: sin x - x cos x = +-(sin r - x cos r) for even k and
+// +-(cos r + x sin r) for odd k, the sign being (-1)^(k >> 1). In the first
+// quadrant (r = x) it is r^3 (S - C), free of cancellation.
+SAS_HD float sas_sphere_g(float x, float inv)
 {
-    SasTrig g = sas_reduce_pio2(x);
-    float s, c;
-    sas_trig_sincos(g, s, c);
-    float num = fmaf(-x, c, s);
-    float inv3 = inv * inv * inv;
-    float big = 3.0f * num * inv3;
-    float small = 3.0f * (g.S - g.C);     // first quadrant: r = x
+    const SasTrig g = sas_reduce_pio2(x);
+    const float sr = fmaf(g.r * g.t, g.S, g.r);
+    const float cr = fmaf(g.t, g.C, 1.0f);
+    const float A = fmaf(-x, cr, sr);
+    const float B = fmaf(x, sr, cr);
+    float num = (g.kb & 1) ? B : A;
+    num = sas_flip_sign(num, g.kb << 30);
+    const float big = num * inv * inv * inv;
+    const float small = g.S - g.C;
     return (x < 0.78539816f) ? small : big;
 }
+
+// f(x) = 3 (sin x - x cos x) / x^3
+SAS_HD float sas_sphere_f(float x, float inv) { return 3.0f * sas_sphere_g(x, inv); }
 
 // a(x) = 2 J1(x) / x for 0 <= x <= X1
 SAS_HD float sas_cyl_a_small(float x)
@@ -116,18 +151,17 @@ SAS_HD float sas_cyl_a_large(float x, float inv, float rsx)
     float m = sas_horner(cm, u);
     float eps = sas_horner(ch, u) * inv;
     // y' = x + eps - pi/4 = k pi/2 + r  ->  cos(theta) = sin(y')
-    float k = rintf(fmaf(x + eps, 0.636619772f, -0.5f));
-    float K = fmaf(2.0f, k, 1.0f);
+    int kb;
+    const float k = sas_round_magic(fmaf(x + eps, 0.636619772f, -0.5f), kb);
+    const float K = fmaf(2.0f, k, 1.0f);
     float r = fmaf(-K, SAS_PIO4_1, x);
     r = fmaf(-K, SAS_PIO4_2, r);
-    r = fmaf(-K, SAS_PIO4_3, r);
     r = r + eps;
-    const float cs[4] = {-1.666666667e-01f, 8.333333333e-03f, -1.984126984e-04f,
-                         2.755731922e-06f};
-    const float cc[5] = SAS_COS_C;
-    float t = r * r;
+    const float cs[3] = SAS_SIN_C;
+    const float cc[4] = SAS_COS_C;
+    const float t = r * r;
     SasTrig g;
-    g.r = r; g.t = t; g.S = sas_horner(cs, t); g.C = sas_horner(cc, t); g.q = ((int)k) & 3;
+    g.r = r; g.t = t; g.S = sas_horner(cs, t); g.C = sas_horner(cc, t); g.kb = kb;
     float s, c;
     sas_trig_sincos(g, s, c);
     // 2 sqrt(2/pi) = 1.5957691216

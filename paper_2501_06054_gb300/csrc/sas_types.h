@@ -24,12 +24,13 @@ struct InstConst {
 };
 
 // Model constants in the trace precision.
-//   poly table per node (SAS_POLY_STRIDE values):
-//     sphere     {r, 1/r, w (drho V)^2, 0...}
-//     core-shell {r_c, 1/r_c, r_o, 1/r_o, sqrt(w) (rho_c - rho_s) V_c,
-//                 sqrt(w) (rho_s - rho_solv) V_o, 0, 0}
+//   poly table per node (SAS_POLY_STRIDE values); the sphere amplitude is
+//   evaluated as g = f / 3, so its factor 3 is folded in here:
+//     sphere     {r, 1/r, 9 w (drho V)^2, 0...}
+//     core-shell {r_c, 1/r_c, r_o, 1/r_o, 3 sqrt(w) (rho_c - rho_s) V_c,
+//                 3 sqrt(w) (rho_s - rho_solv) V_o, 0, 0}
 //     cylinder   {r, 1/r, 1/sqrt(r), w (drho V)^2, 0...}
-//     ellipsoid  {r_e^2, w (drho V)^2, 0...}
+//     ellipsoid  {r_e^2, 9 w (drho V)^2, 0...}
 //   orient table per node: {c_x, c_y, c_z, weight}
 template <typename T>
 struct ModelConst {

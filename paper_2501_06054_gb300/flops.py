@@ -5,24 +5,27 @@ term in FP32, counted from the formulas the kernels evaluate (they exclude
 integer work: Philox, pixel arithmetic, selects). They convert histories/s
 into FLOP/s for the roofline against the FP32 CUDA-core peak.
 
-  sphere amplitude f(Q r) = 3 (sin x - x cos x) / x^3         38
-      x, 1/x (2 mul), quadrant (mul, rint), 3-part reduction (3 FMA),
-      r^2, sin poly (3 FMA), cos poly (4 FMA), sin r, cos r (mul + 2 FMA),
-      sin x - x cos x (FMA), 3 / x^3 (4 mul), 3 (S - C) (sub, mul)
+  sphere amplitude g(Q r) = (sin x - x cos x) / x^3           33
+      x, 1/x (2 mul), quadrant (FMA, add), 2-part reduction (2 FMA),
+      r^2, sin poly (2 FMA), cos poly (3 FMA), r^3 (mul), sin r, cos r
+      (2 FMA), the two quadrant forms (2 FMA), / x^3 (3 mul), S - C (add)
+      (the factor 3 of f = 3 g is folded into the tables)
   cylinder radial factor 2 J1(Q r)/(Q r), x <= 4 branch        22
       x, 1/x, 1/sqrt(x) (3 mul), (x/4)^2 (2 mul), polynomial (7 FMA),
       a^2 (mul), weighted sum (FMA)
   orientation node overhead (cylinder, ellipsoid)              60
       Q.c, |Q x c|^2 (11 FMA/mul), sqrt, 1/x, rsqrt (3), sinc (~26),
       weight products (3), Kahan (4)
-  ellipsoid term: |Q|_eff^2 (FMA), rsqrt, x (mul) + amplitude   41 + 3
-  core-shell node: two amplitudes + combination (FMA, FMA)       38*2 + 4 + 1
+  ellipsoid term: |Q|_eff^2 (FMA), rsqrt, x (mul), amplitude
+                  without its own x, 1/x, g^2, weighted sum        2+1+1+31+1+2 = 38
+  sphere node: amplitude, g^2, weighted sum                       33 + 3
+  core-shell node: two amplitudes + combination (mul, FMA, FMA)   2*33 + 5
   per history: geometry (wavelength, pinholes, slab, detector
                point, Q, solid angle)                           150
                Percus-Yevick S(Q)                               40
 """
 
-AMP = 38
+AMP = 33
 CYL_TERM = 22
 ORIENT_NODE = 60
 GEOMETRY = 150
@@ -31,13 +34,13 @@ PY = 40
 
 def flops_per_history(kind: int, n_poly: int, n_orient: int = 1, sq: bool = False) -> int:
     if kind == 0:        # sphere
-        per = n_poly * (AMP + 2)
+        per = n_poly * (AMP + 3)
     elif kind == 1:      # core-shell
         per = n_poly * (2 * AMP + 5)
     elif kind == 2:      # cylinder
         per = n_orient * (ORIENT_NODE + n_poly * CYL_TERM)
     else:                # ellipsoid
-        per = n_orient * (ORIENT_NODE + n_poly * (AMP + 6))
+        per = n_orient * (ORIENT_NODE + n_poly * (AMP + 5))
     return per + GEOMETRY + (PY if sq else 0)
 
 
