@@ -47,6 +47,17 @@ class sas_model_desc(ctypes.Structure):
                    "axis_phi", "sq_radius", "sq_fraction")]
 
 
+class sas_launch_config(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in (
+        "block", "tally", "agg", "ctas_per_sm", "stage_orient", "reserved")]
+
+
+class sas_batch_config(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("use_hist", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("target_item_flop", ctypes.c_double)]
+
+
 _lib = None
 _lock = threading.Lock()
 _vp = ctypes.c_void_p
@@ -74,6 +85,20 @@ _SIGS = {
     "sas_orientation_nodes": [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                               ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.POINTER(ctypes.c_int)],
     "sas_py_series": [ctypes.c_double, _dp, _dp, ctypes.c_int],
+    "sas_get_launch_config": [_vp, ctypes.POINTER(sas_launch_config)],
+    "sas_set_launch_config": [_vp, ctypes.POINTER(sas_launch_config)],
+    "sas_autotune": [_vp, _u64, _u64, ctypes.POINTER(sas_launch_config), _dp],
+    "sas_create_batch": [_vp, _vp, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(_vp)],
+    "sas_trace_batch": [_vp, _u64],
+    "sas_read_batch_detector": [_vp, ctypes.c_size_t, _vp, _vp, _vp, ctypes.c_size_t, _vp],
+    "sas_batch_detector_device": [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                  ctypes.POINTER(_vp), ctypes.POINTER(_vp)],
+    "sas_batch_set_config": [_vp, ctypes.POINTER(sas_batch_config)],
+    "sas_batch_get_config": [_vp, ctypes.POINTER(sas_batch_config)],
+    "sas_batch_info": [_vp, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_int),
+                       ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_uint64)],
+    "sas_batch_autotune": [_vp, _u64, ctypes.POINTER(sas_batch_config), _dp],
+    "sas_destroy_batch": [_vp],
 }
 
 # extra entry points added by later modules of the library register here
@@ -246,6 +271,83 @@ def sas_py_series(phi, nser=14):
     _check(lib().sas_py_series(float(phi), abg.ctypes.data_as(_dp), s.ctypes.data_as(_dp),
                                int(nser)))
     return abg, s
+
+
+def sas_get_launch_config(exp):
+    c = sas_launch_config()
+    _check(lib().sas_get_launch_config(exp, ctypes.byref(c)))
+    return c
+
+
+def sas_set_launch_config(exp, cfg):
+    _check(lib().sas_set_launch_config(exp, ctypes.byref(cfg)))
+
+
+def sas_autotune(exp, n_sample, seed):
+    c = sas_launch_config()
+    ms = ctypes.c_double()
+    _check(lib().sas_autotune(exp, int(n_sample), int(seed), ctypes.byref(c), ctypes.byref(ms)))
+    return c, ms.value
+
+
+def sas_create_batch(instrument, models, counts, stream=None):
+    inst = instrument if isinstance(instrument, sas_instrument) else make_instrument(instrument)
+    arr = (sas_model_desc * len(models))(*[m if isinstance(m, sas_model_desc) else make_model(m)
+                                           for m in models])
+    cnt = np.ascontiguousarray(np.asarray(counts, dtype=np.uint64))
+    h = _vp()
+    _check(lib().sas_create_batch(ctypes.byref(inst), ctypes.cast(arr, _vp), cnt.ctypes.data,
+                                  len(models), _stream_handle(stream), ctypes.byref(h)))
+    return h.value
+
+
+def sas_trace_batch(batch, seed):
+    _check(lib().sas_trace_batch(batch, int(seed)))
+
+
+def sas_read_batch_detector(batch, exp, n_pixels):
+    sw = np.empty(n_pixels, np.float64)
+    sw2 = np.empty(n_pixels, np.float64)
+    cnt = np.empty(n_pixels, np.uint64)
+    tr = np.zeros(1, np.float64)
+    _check(lib().sas_read_batch_detector(batch, int(exp), sw.ctypes.data, sw2.ctypes.data,
+                                         cnt.ctypes.data, int(n_pixels), tr.ctypes.data))
+    return dict(sum_w=sw, sum_w2=sw2, count=cnt, trans=float(tr[0]))
+
+
+def sas_batch_detector_device(batch):
+    a, b, c, d = _vp(), _vp(), _vp(), _vp()
+    _check(lib().sas_batch_detector_device(batch, ctypes.byref(a), ctypes.byref(b),
+                                           ctypes.byref(c), ctypes.byref(d)))
+    return a.value, b.value, c.value, d.value
+
+
+def sas_batch_set_config(batch, cfg):
+    _check(lib().sas_batch_set_config(batch, ctypes.byref(cfg)))
+
+
+def sas_batch_get_config(batch):
+    c = sas_batch_config()
+    _check(lib().sas_batch_get_config(batch, ctypes.byref(c)))
+    return c
+
+
+def sas_batch_info(batch):
+    n, g, sm, tot = ctypes.c_uint32(), ctypes.c_int(), ctypes.c_size_t(), ctypes.c_uint64()
+    _check(lib().sas_batch_info(batch, ctypes.byref(n), ctypes.byref(g), ctypes.byref(sm),
+                                ctypes.byref(tot)))
+    return dict(n_items=n.value, grid=g.value, smem=sm.value, total_histories=tot.value)
+
+
+def sas_batch_autotune(batch, seed):
+    c = sas_batch_config()
+    ms = ctypes.c_double()
+    _check(lib().sas_batch_autotune(batch, int(seed), ctypes.byref(c), ctypes.byref(ms)))
+    return c, ms.value
+
+
+def sas_destroy_batch(batch):
+    _check(lib().sas_destroy_batch(batch))
 
 
 # ------------------------------------------------------------ convenience
