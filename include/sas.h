@@ -248,6 +248,88 @@ sas_status sas_batch_autotune(sas_batch *batch, uint64_t seed, sas_batch_config 
 
 sas_status sas_destroy_batch(sas_batch *batch);
 
+/* ---- learned surrogate of the averaged cylinder form factor --------- */
+
+typedef struct sas_surrogate sas_surrogate;          /* opaque, library-owned */
+
+/* Training box. The surrogate reproduces, for oriented polydisperse
+ * cylinders inside it, the normalised averaged form factor
+ * P = <|F|^2> / (drho^2 <V^2>) that sas_set_model's quadrature gives with
+ * the same node counts (n_poly Schulz nodes; n_gamma x n_psi orientation
+ * nodes). Its inputs are the rotation-invariant features
+ * (q_par L / 2, q_perp R, L / (2R), sigma_orient, sigma_poly) plus
+ * n_fourier (sin, cos) pairs of q_par L / 8 * k, where q_par and q_perp are
+ * the components of Q along and across the mean axis; its output is log P.
+ * sigma_poly is learned on n_buckets values spread evenly over the range. */
+typedef struct sas_surrogate_box {
+    double q_max;                                 /* 1/angstrom */
+    double r_min, r_max;                          /* cylinder radius, angstrom */
+    double l_min, l_max;                          /* cylinder length, angstrom */
+    double sigma_orient_min, sigma_orient_max;    /* rad */
+    double poly_min, poly_max;                    /* Schulz relative width */
+    int32_t n_poly, n_gamma, n_psi;               /* quadrature it reproduces */
+    int32_t n_buckets;                            /* sigma_poly values in the training set */
+    int32_t n_fourier;                            /* Fourier feature pairs (0..28) */
+    int32_t reserved;
+} sas_surrogate_box;
+
+/* MLP 64 -> 256 -> 256 -> 256 -> 256 -> 1, SiLU, BF16 hidden weights (FP32
+ * master copy, biases and output layer), initialised from Philox(seed). */
+sas_status sas_create_surrogate(const sas_surrogate_box *box, uint64_t seed, void *stream,
+                                sas_surrogate **out);
+
+/* Draw n training samples uniformly in the box (Philox experiment id
+ * 0x80000001) and compute their exact targets log P on the GPU with the
+ * trace's quadrature. The data set stays in device memory. */
+sas_status sas_surrogate_generate(sas_surrogate *s, uint64_t n, uint64_t seed);
+
+/* Device pointers of the data set: raw parameters [n][8] floats
+ * (q_par, q_perp, R, L, sigma_orient, sigma_poly, bucket, 0) and log P [n]. */
+sas_status sas_surrogate_dataset(const sas_surrogate *s, const void **raw, const float **log_p,
+                                 uint64_t *n);
+
+/* Exact log P (the target quadrature) at raw parameters (DEVICE [n][8]
+ * floats, bucket index in column 6) into DEVICE log_p[n]. */
+sas_status sas_surrogate_exact(sas_surrogate *s, const void *raw, size_t n, float *log_p);
+
+/* Surrogate log P (tensor-core inference) at raw parameters (DEVICE). */
+sas_status sas_surrogate_eval(sas_surrogate *s, const void *raw, size_t n, float *log_p);
+
+/* One forward + backward pass (no update) of the mean squared error of log P
+ * over n rows (multiple of 128) of DEVICE raw / log_p; the FP32 gradient of
+ * all parameters goes to the HOST buffer grad[n_params]. */
+sas_status sas_surrogate_grad(sas_surrogate *s, const void *raw, const float *log_p, uint32_t n,
+                              float *grad, size_t n_params);
+
+/* n_steps Adam steps (CUDA-graph replay of forward, backward, weight
+ * gradients and update) over consecutive minibatches of `batch` rows
+ * (multiple of 128) of the generated data set; learning rate lr with
+ * cosine decay over total_steps. */
+sas_status sas_surrogate_train(sas_surrogate *s, uint32_t n_steps, uint32_t batch, double lr,
+                               uint32_t total_steps);
+
+/* FP32 master parameters (flat layout: W1 [256][64] (column 63 is the
+ * layer-1 bias), W2, W3, W4 [256][256] (out, in), b1 (unused, 0), b2, b3, b4,
+ * w5 [256], b5), host buffers of n_params floats. */
+sas_status sas_surrogate_get_params(const sas_surrogate *s, float *params, size_t n_params);
+sas_status sas_surrogate_set_params(sas_surrogate *s, const float *params, size_t n_params);
+sas_status sas_surrogate_info(const sas_surrogate *s, size_t *n_params, uint32_t *steps_done);
+sas_status sas_destroy_surrogate(sas_surrogate *s);
+
+/* Use the surrogate for the experiment's cylinder model when it lies in the
+ * training box (same node counts); histories whose |Q| leaves the box fall
+ * back to the exact quadrature. NULL detaches. The surrogate must outlive
+ * the attachment. */
+sas_status sas_attach_surrogate(sas_experiment *exp, const sas_surrogate *s);
+
+/* Same for every in-box cylinder experiment of a batch: they are traced by a
+ * second persistent tensor-core kernel in the batch's graph. */
+sas_status sas_batch_attach_surrogate(sas_batch *batch, const sas_surrogate *s);
+
+/* Histories evaluated by the exact fallback in the last surrogate traces. */
+sas_status sas_surrogate_fallbacks(const sas_experiment *exp, const sas_batch *batch,
+                                   uint64_t *count);
+
 /* ---- host-side utilities (no GPU needed): the library's own FP64 tables.
  * They are the quadrature rules sas_set_model builds for the trace. */
 

@@ -58,6 +58,13 @@ class sas_batch_config(ctypes.Structure):
                 ("target_item_flop", ctypes.c_double)]
 
 
+class sas_surrogate_box(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in (
+        "q_max", "r_min", "r_max", "l_min", "l_max", "sigma_orient_min", "sigma_orient_max",
+        "poly_min", "poly_max")] + [(n, ctypes.c_int32) for n in (
+            "n_poly", "n_gamma", "n_psi", "n_buckets", "n_fourier", "reserved")]
+
+
 _lib = None
 _lock = threading.Lock()
 _vp = ctypes.c_void_p
@@ -99,6 +106,20 @@ _SIGS = {
                        ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_uint64)],
     "sas_batch_autotune": [_vp, _u64, ctypes.POINTER(sas_batch_config), _dp],
     "sas_destroy_batch": [_vp],
+    "sas_create_surrogate": [ctypes.POINTER(sas_surrogate_box), _u64, _vp, ctypes.POINTER(_vp)],
+    "sas_surrogate_generate": [_vp, _u64, _u64],
+    "sas_surrogate_dataset": [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_u64)],
+    "sas_surrogate_exact": [_vp, _vp, ctypes.c_size_t, _vp],
+    "sas_surrogate_eval": [_vp, _vp, ctypes.c_size_t, _vp],
+    "sas_surrogate_grad": [_vp, _vp, _vp, ctypes.c_uint32, _vp, ctypes.c_size_t],
+    "sas_surrogate_train": [_vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_double, ctypes.c_uint32],
+    "sas_surrogate_get_params": [_vp, _vp, ctypes.c_size_t],
+    "sas_surrogate_set_params": [_vp, _vp, ctypes.c_size_t],
+    "sas_surrogate_info": [_vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_uint32)],
+    "sas_destroy_surrogate": [_vp],
+    "sas_attach_surrogate": [_vp, _vp],
+    "sas_batch_attach_surrogate": [_vp, _vp],
+    "sas_surrogate_fallbacks": [_vp, _vp, ctypes.POINTER(_u64)],
 }
 
 # extra entry points added by later modules of the library register here
@@ -348,6 +369,82 @@ def sas_batch_autotune(batch, seed):
 
 def sas_destroy_batch(batch):
     _check(lib().sas_destroy_batch(batch))
+
+
+def make_box(d) -> sas_surrogate_box:
+    ints = ("n_poly", "n_gamma", "n_psi", "n_buckets", "n_fourier", "reserved")
+    return sas_surrogate_box(**{k: (int(v) if k in ints else float(v)) for k, v in d.items()})
+
+
+def sas_create_surrogate(box, seed, stream=None):
+    b = box if isinstance(box, sas_surrogate_box) else make_box(box)
+    h = _vp()
+    _check(lib().sas_create_surrogate(ctypes.byref(b), int(seed), _stream_handle(stream),
+                                      ctypes.byref(h)))
+    return h.value
+
+
+def sas_surrogate_generate(s, n, seed):
+    _check(lib().sas_surrogate_generate(s, int(n), int(seed)))
+
+
+def sas_surrogate_dataset(s):
+    r, y, n = _vp(), _vp(), _u64()
+    _check(lib().sas_surrogate_dataset(s, ctypes.byref(r), ctypes.byref(y), ctypes.byref(n)))
+    return r.value, y.value, n.value
+
+
+def sas_surrogate_exact(s, raw, n, log_p):
+    _check(lib().sas_surrogate_exact(s, _ptr(raw), int(n), _ptr(log_p)))
+
+
+def sas_surrogate_eval(s, raw, n, log_p):
+    _check(lib().sas_surrogate_eval(s, _ptr(raw), int(n), _ptr(log_p)))
+
+
+def sas_surrogate_grad(s, raw, log_p, n, n_params):
+    g = np.empty(n_params, np.float32)
+    _check(lib().sas_surrogate_grad(s, _ptr(raw), _ptr(log_p), int(n), g.ctypes.data, n_params))
+    return g
+
+
+def sas_surrogate_train(s, n_steps, batch, lr, total_steps):
+    _check(lib().sas_surrogate_train(s, int(n_steps), int(batch), float(lr), int(total_steps)))
+
+
+def sas_surrogate_info(s):
+    n, st = ctypes.c_size_t(), ctypes.c_uint32()
+    _check(lib().sas_surrogate_info(s, ctypes.byref(n), ctypes.byref(st)))
+    return dict(n_params=n.value, steps_done=st.value)
+
+
+def sas_surrogate_get_params(s, n_params):
+    p = np.empty(n_params, np.float32)
+    _check(lib().sas_surrogate_get_params(s, p.ctypes.data, n_params))
+    return p
+
+
+def sas_surrogate_set_params(s, params):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    _check(lib().sas_surrogate_set_params(s, p.ctypes.data, p.size))
+
+
+def sas_destroy_surrogate(s):
+    _check(lib().sas_destroy_surrogate(s))
+
+
+def sas_attach_surrogate(exp, s):
+    _check(lib().sas_attach_surrogate(exp, s))
+
+
+def sas_batch_attach_surrogate(batch, s):
+    _check(lib().sas_batch_attach_surrogate(batch, s))
+
+
+def sas_surrogate_fallbacks(exp=None, batch=None):
+    c = _u64()
+    _check(lib().sas_surrogate_fallbacks(exp, batch, ctypes.byref(c)))
+    return c.value
 
 
 # ------------------------------------------------------------ convenience

@@ -13,6 +13,7 @@
 
 #include "sas_kernels.cuh"
 #include "sas_host.h"
+#include "sas_sur_host.h"
 
 namespace {
 
@@ -452,6 +453,15 @@ struct sas_experiment {
     InstConst<double> icd;
     LaunchCfg cfg;
     int stage_orient = 0;
+    // learned surrogate (cylinders in its training box)
+    const sas_surrogate* sur = nullptr;
+    WorkItem* d_items = nullptr;
+    size_t items_cap = 0;
+    unsigned int* d_queue = nullptr;
+    uint64_t* d_seed = nullptr;
+    sur::SurExp* d_sexp = nullptr;
+    BatchExp* d_bexp = nullptr;
+    unsigned long long* d_fallbacks = nullptr;
 };
 
 namespace {
@@ -605,11 +615,95 @@ void store_tuned(const sas_experiment* e)
     g_tuned.push_back(TuneEntry{k, e->cfg, e->stage_orient});
 }
 
+sas_status upload_surrogate_exp(sas_experiment* e)
+{
+    if (!e->sur || !e->has_model) return SAS_OK;
+    if (!e->d_sexp) {
+        SAS_CUDA(cudaMalloc(&e->d_sexp, sizeof(sur::SurExp)), "alloc");
+        SAS_CUDA(cudaMalloc(&e->d_bexp, sizeof(BatchExp)), "alloc");
+        SAS_CUDA(cudaMalloc(&e->d_queue, sizeof(unsigned int)), "alloc");
+        SAS_CUDA(cudaMalloc(&e->d_seed, sizeof(uint64_t)), "alloc");
+        SAS_CUDA(cudaMalloc(&e->d_fallbacks, sizeof(unsigned long long)), "alloc");
+        SAS_CUDA(cudaMemset(e->d_fallbacks, 0, sizeof(unsigned long long)), "memset");
+    }
+    const sur::SurExp se = surrogate_exp(e->model, surrogate_covers(e->sur, e->model));
+    BatchExp be;
+    std::memset(&be, 0, sizeof(be));
+    be.mc = e->mcf;
+    SAS_CUDA(cudaMemcpy(e->d_sexp, &se, sizeof(se), cudaMemcpyHostToDevice), "upload");
+    SAS_CUDA(cudaMemcpy(e->d_bexp, &be, sizeof(be), cudaMemcpyHostToDevice), "upload");
+    return SAS_OK;
+}
+
+// Cylinder trace through the tensor-core surrogate: items of 2^16
+// histories pulled by a persistent grid (one CTA per SM).
+sas_status trace_surrogate(sas_experiment* e, uint64_t first, uint64_t n, uint64_t seed)
+{
+    const uint64_t chunk = 1ull << 16;
+    std::vector<WorkItem> items;
+    for (uint64_t f = 0; f < n; f += chunk) {
+        WorkItem w;
+        w.first = first + f;
+        w.exp = 0;
+        w.n = (uint32_t)std::min<uint64_t>(chunk, n - f);
+        items.push_back(w);
+    }
+    if (items.size() > 0xFFFFFFF0ull) return fail(SAS_ERR_ARG, "too many histories for one surrogate trace");
+    if (items.size() > e->items_cap) {
+        SAS_CUDA(cudaStreamSynchronize(e->stream), "sync");
+        cudaFree(e->d_items);
+        e->d_items = nullptr;
+        SAS_CUDA(cudaMalloc(&e->d_items, items.size() * sizeof(WorkItem)), "alloc items");
+        e->items_cap = items.size();
+    }
+    SAS_CUDA(cudaMemcpyAsync(e->d_items, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice,
+                             e->stream), "upload items");
+    SAS_CUDA(cudaMemcpyAsync(e->d_seed, &seed, sizeof(seed), cudaMemcpyHostToDevice, e->stream), "upload seed");
+    SAS_CUDA(cudaMemsetAsync(e->d_queue, 0, sizeof(unsigned int), e->stream), "memset");
+    sur::STParams P;
+    std::memset(&P, 0, sizeof(P));
+    P.in = e->icf;
+    P.box = surrogate_dbox(e->sur);
+    P.params = surrogate_params(e->sur);
+    P.seed = e->d_seed;
+    P.philox_base = e->exp_id;
+    P.items = e->d_items;
+    P.n_items = (uint32_t)items.size();
+    P.queue = e->d_queue;
+    P.sexp = e->d_sexp;
+    P.bexp = e->d_bexp;
+    P.poly = (const float*)e->d_poly;
+    P.orient = (const float*)e->d_orient;
+    P.sum_w = e->d_sum_w;
+    P.sum_w2 = e->d_sum_w2;
+    P.count = e->d_count;
+    P.trans = e->d_trans;
+    P.npix = (int)(e->inst.nx * e->inst.ny);
+    P.fallbacks = e->d_fallbacks;
+    P.err = surrogate_err(e->sur);
+    const int grid = (int)std::min<uint64_t>((uint64_t)e->sm_count, items.size());
+    SAS_CUDA(launch_sur_trace(e->sur, P, grid, e->stream), "surrogate trace launch");
+    return SAS_OK;
+}
+
 }  // namespace
+
+namespace sas {
+unsigned long long* experiment_fallback_counter(const sas_experiment* e) { return e ? e->d_fallbacks : nullptr; }
+cudaStream_t experiment_stream(const sas_experiment* e) { return e->stream; }
+}  // namespace sas
 
 extern "C" {
 
 const char* sas_last_error(void) { return g_last_error.c_str(); }
+
+sas_status sas_attach_surrogate(sas_experiment* e, const sas_surrogate* s)
+{
+    if (!e) return fail(SAS_ERR_ARG, "experiment is NULL");
+    SAS_CUDA(cudaStreamSynchronize(e->stream), "sync");
+    e->sur = s;
+    return upload_surrogate_exp(e);
+}
 
 sas_status sas_get_launch_config(const sas_experiment* e, sas_launch_config* c)
 {
@@ -791,7 +885,7 @@ sas_status sas_set_model(sas_experiment* e, const sas_model_desc* m)
     e->mcd = model_const<double>(*m, e->tables);
     e->has_model = true;
     if (!lookup_tuned(e)) choose_config(e);
-    return SAS_OK;
+    return upload_surrogate_exp(e);
 }
 
 sas_status sas_set_experiment_id(sas_experiment* e, uint32_t id)
@@ -825,6 +919,8 @@ sas_status sas_trace_range(sas_experiment* e, uint64_t first, uint64_t n, uint64
     if (!e->has_model) return fail(SAS_ERR_STATE, "sas_set_model has not been called");
     if (first + n < first) return fail(SAS_ERR_ARG, "neutron index range overflows 64 bits");
     if (n == 0) return SAS_OK;
+    if (e->sur && e->model.precision == SAS_FP32 && surrogate_covers(e->sur, e->model))
+        return trace_surrogate(e, first, n, seed);
     cudaError_t ce;
     int grid = 0;
     if (e->model.precision == SAS_FP32)
@@ -924,6 +1020,12 @@ sas_status sas_destroy_experiment(sas_experiment* e)
     cudaFree(e->d_trans);
     cudaFree(e->d_poly);
     cudaFree(e->d_orient);
+    cudaFree(e->d_items);
+    cudaFree(e->d_queue);
+    cudaFree(e->d_seed);
+    cudaFree(e->d_sexp);
+    cudaFree(e->d_bexp);
+    cudaFree(e->d_fallbacks);
     delete e;
     return SAS_OK;
 }

@@ -12,11 +12,14 @@
 
 #include "sas_batch.cuh"
 #include "sas_host.h"
+#include "sas_sur_host.h"
 
 namespace sas {
 sas_status set_error(sas_status s, const std::string& msg);
 sas_status set_cuda_error(cudaError_t e, const char* what);
 double host_flops_per_history(const sas_model_desc& m, int n_poly, int n_orient);
+unsigned long long* experiment_fallback_counter(const sas_experiment* e);
+cudaStream_t experiment_stream(const sas_experiment* e);
 }  // namespace sas
 
 using namespace sas;
@@ -59,6 +62,16 @@ struct sas_batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     uint64_t total_histories = 0;
+    std::vector<sas_model_desc> models;
+    // learned surrogate for the in-box cylinder experiments
+    const sas_surrogate* sur = nullptr;
+    std::vector<int> use_sur;
+    WorkItem* d_sur_items = nullptr;
+    size_t sur_cap = 0;
+    uint32_t n_sur_items = 0;
+    unsigned int* d_sur_queue = nullptr;
+    sur::SurExp* d_sexp = nullptr;
+    unsigned long long* d_fallbacks = nullptr;
 };
 
 namespace {
@@ -77,9 +90,21 @@ sas_status build_items(sas_batch* b)
     std::vector<WorkItem> items;
     std::vector<double> icost;
     const double target = b->cfg.target_item_flop > 0 ? b->cfg.target_item_flop : 2e9;
+    std::vector<WorkItem> sitems;
     for (size_t e = 0; e < b->n_exp; ++e) {
         const uint64_t n = b->counts[e];
         if (n == 0) continue;
+        if (!b->use_sur.empty() && b->use_sur[e]) {
+            const uint64_t c = 1ull << 16;
+            for (uint64_t f = 0; f < n; f += c) {
+                WorkItem w;
+                w.first = f;
+                w.exp = (uint32_t)e;
+                w.n = (uint32_t)std::min<uint64_t>(c, n - f);
+                sitems.push_back(w);
+            }
+            continue;
+        }
         double chunk = std::floor(target / b->cost[e]);
         chunk = std::max(chunk, 1024.0);
         chunk = std::min(chunk, 1073741824.0);
@@ -108,6 +133,16 @@ sas_status build_items(sas_batch* b)
     b->n_items = (uint32_t)sorted.size();
     if (!sorted.empty())
         SAS_CUDA_B(cudaMemcpy(b->d_items, sorted.data(), sorted.size() * sizeof(WorkItem), cudaMemcpyHostToDevice),
+                   "upload items");
+    if (sitems.size() > b->sur_cap) {
+        cudaFree(b->d_sur_items);
+        b->d_sur_items = nullptr;
+        SAS_CUDA_B(cudaMalloc(&b->d_sur_items, sitems.size() * sizeof(WorkItem)), "cudaMalloc(items)");
+        b->sur_cap = sitems.size();
+    }
+    b->n_sur_items = (uint32_t)sitems.size();
+    if (!sitems.empty())
+        SAS_CUDA_B(cudaMemcpy(b->d_sur_items, sitems.data(), sitems.size() * sizeof(WorkItem), cudaMemcpyHostToDevice),
                    "upload items");
     return SAS_OK;
 }
@@ -169,6 +204,31 @@ sas_status capture(sas_batch* b)
     cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned int), b->cap);
     if (b->n_items > 0) kern<<<b->grid, b->cfg.block, b->smem, b->cap>>>(P);
     cudaError_t le = cudaGetLastError();
+    if (le == cudaSuccess && b->sur && b->n_sur_items > 0) {
+        cudaMemsetAsync(b->d_sur_queue, 0, sizeof(unsigned int), b->cap);
+        sur::STParams S;
+        std::memset(&S, 0, sizeof(S));
+        S.in = b->icf;
+        S.box = surrogate_dbox(b->sur);
+        S.params = surrogate_params(b->sur);
+        S.seed = b->d_seed;
+        S.philox_base = 0;
+        S.items = b->d_sur_items;
+        S.n_items = b->n_sur_items;
+        S.queue = b->d_sur_queue;
+        S.sexp = b->d_sexp;
+        S.bexp = b->d_exps;
+        S.poly = b->d_poly;
+        S.orient = b->d_orient;
+        S.sum_w = b->d_sum_w;
+        S.sum_w2 = b->d_sum_w2;
+        S.count = b->d_count;
+        S.trans = b->d_trans;
+        S.npix = b->npix;
+        S.fallbacks = b->d_fallbacks;
+        S.err = surrogate_err(b->sur);
+        le = launch_sur_trace(b->sur, S, (int)std::min<uint32_t>((uint32_t)b->sm_count, b->n_sur_items), b->cap);
+    }
     cudaError_t ce = cudaStreamEndCapture(b->cap, &b->graph);
     if (le != cudaSuccess) return set_cuda_error(le, "batch kernel launch (capture)");
     if (ce != cudaSuccess) return set_cuda_error(ce, "end capture");
@@ -237,6 +297,7 @@ sas_status sas_create_batch(const sas_instrument* inst, const sas_model_desc* mo
         b->orient_stageable[e] = (t.n_orient > 1) &&
                                  (table_bytes<float>(t.n_poly, t.n_orient, 1) <= (size_t)b->smem_optin);
         b->total_histories += counts[e];
+        b->models.push_back(m);
     }
     const size_t det = n_exp * (size_t)b->npix;
     ce = cudaMalloc(&b->d_exps, n_exp * sizeof(BatchExp));
@@ -382,6 +443,50 @@ sas_status sas_batch_autotune(sas_batch* b, uint64_t seed, sas_batch_config* bes
     return SAS_OK;
 }
 
+sas_status sas_batch_attach_surrogate(sas_batch* b, const sas_surrogate* s)
+{
+    if (!b) return set_error(SAS_ERR_ARG, "batch is NULL");
+    SAS_CUDA_B(cudaStreamSynchronize(b->stream), "sync");
+    drop_graph(b);
+    b->sur = s;
+    b->use_sur.assign(b->n_exp, 0);
+    if (s) {
+        std::vector<sur::SurExp> se(b->n_exp);
+        for (size_t e = 0; e < b->n_exp; ++e) {
+            b->use_sur[e] = surrogate_covers(s, b->models[e]) ? 1 : 0;
+            se[e] = surrogate_exp(b->models[e], b->use_sur[e] != 0);
+        }
+        if (!b->d_sexp) {
+            SAS_CUDA_B(cudaMalloc(&b->d_sexp, b->n_exp * sizeof(sur::SurExp)), "alloc");
+            SAS_CUDA_B(cudaMalloc(&b->d_sur_queue, sizeof(unsigned int)), "alloc");
+            SAS_CUDA_B(cudaMalloc(&b->d_fallbacks, sizeof(unsigned long long)), "alloc");
+            SAS_CUDA_B(cudaMemset(b->d_fallbacks, 0, sizeof(unsigned long long)), "memset");
+        }
+        SAS_CUDA_B(cudaMemcpy(b->d_sexp, se.data(), b->n_exp * sizeof(sur::SurExp), cudaMemcpyHostToDevice),
+                   "upload");
+    }
+    return build_items(b);
+}
+
+sas_status sas_surrogate_fallbacks(const sas_experiment* e, const sas_batch* b, uint64_t* count)
+{
+    if (!count) return set_error(SAS_ERR_ARG, "NULL argument");
+    *count = 0;
+    unsigned long long v = 0;
+    if (e && experiment_fallback_counter(e)) {
+        SAS_CUDA_B(cudaMemcpyAsync(&v, experiment_fallback_counter(e), 8, cudaMemcpyDeviceToHost,
+                                   experiment_stream(e)), "read");
+        SAS_CUDA_B(cudaStreamSynchronize(experiment_stream(e)), "sync");
+        *count += v;
+    }
+    if (b && b->d_fallbacks) {
+        SAS_CUDA_B(cudaMemcpyAsync(&v, b->d_fallbacks, 8, cudaMemcpyDeviceToHost, b->stream), "read");
+        SAS_CUDA_B(cudaStreamSynchronize(b->stream), "sync");
+        *count += v;
+    }
+    return SAS_OK;
+}
+
 sas_status sas_destroy_batch(sas_batch* b)
 {
     if (!b) return SAS_OK;
@@ -398,6 +503,10 @@ sas_status sas_destroy_batch(sas_batch* b)
     cudaFree(b->d_sum_w2);
     cudaFree(b->d_count);
     cudaFree(b->d_trans);
+    cudaFree(b->d_sur_items);
+    cudaFree(b->d_sur_queue);
+    cudaFree(b->d_sexp);
+    cudaFree(b->d_fallbacks);
     if (b->cap) cudaStreamDestroy(b->cap);
     delete b;
     return SAS_OK;

@@ -1,0 +1,152 @@
+// Surrogate box, feature map and the exact quadrature that generates the
+// training targets (device side).
+#pragma once
+
+#include "sas_batch.cuh"
+#include "sas_device.cuh"
+#include "sas_mlp.cuh"
+
+namespace sas {
+namespace sur {
+
+constexpr int MAX_BUCKETS = 64;
+constexpr int MAX_POLY = 64;
+constexpr int MAX_GL = 128;
+constexpr uint32_t DATA_EXP_ID = 0x80000001u;   // Philox experiment id of the training draws
+
+// Box and feature scaling in the trace precision (FP32).
+struct Box {
+    float q_max, r_min, r_max, l_min, l_max, so_min, so_max, sp_min, sp_max;
+    float u_max, v_max, a_min, a_max;   // feature ranges
+    float four_w;                        // angular step of the Fourier features of u
+    int n_four;                          // Fourier pairs of u
+    int n_buckets, n_poly, n_gamma, n_psi;
+};
+
+// Raw parameters of one evaluation: q_par, q_perp (1/A), R, L (A), sigma_orient
+// (rad), sigma_poly, bucket index (as float), pad.
+struct Raw {
+    float qpar, qperp, R, L, so, sp, bucket, pad;
+};
+
+// Feature vector (64 wide: [0, 5) scaled raw inputs in [-1, 1], then
+// n_four (sin, cos) pairs of k * four_w * u, column 63 = 1 (bias of layer 1)).
+__device__ __forceinline__ void features(const Box& b, float qpar, float qperp, float R, float L, float so,
+                                         float sp, float* f64)
+{
+#pragma unroll
+    for (int i = 0; i < 64; ++i) f64[i] = 0.f;
+    const float u = qpar * 0.5f * L;
+    const float v = qperp * R;
+    const float a = 0.5f * L / R;
+    f64[0] = 2.f * u / b.u_max - 1.f;
+    f64[1] = 2.f * v / b.v_max - 1.f;
+    f64[2] = 2.f * (a - b.a_min) / (b.a_max - b.a_min) - 1.f;
+    f64[3] = 2.f * (so - b.so_min) / (b.so_max - b.so_min) - 1.f;
+    f64[4] = 2.f * (sp - b.sp_min) / (b.sp_max - b.sp_min) - 1.f;
+    for (int k = 0; k < b.n_four && k < 28; ++k) {
+        float s, c;
+        sas_sincosf((float)(k + 1) * b.four_w * u, s, c);
+        f64[5 + 2 * k] = s;
+        f64[6 + 2 * k] = c;
+    }
+    f64[63] = 1.f;
+}
+
+__device__ __forceinline__ bool in_box(const Box& b, float q, float R, float L, float so, float sp)
+{
+    return q <= b.q_max && R >= b.r_min && R <= b.r_max && L >= b.l_min && L <= b.l_max && so >= b.so_min &&
+           so <= b.so_max && sp >= b.sp_min && sp <= b.sp_max;
+}
+
+// Tables for the exact quadrature of the training targets.
+struct Tables {
+    const float* gl_g;      // [n_gamma] Gauss-Legendre nodes on [-1, 1]
+    const float* glw_g;     // [n_gamma] weights
+    const float* gl_p;      // [n_psi]
+    const float* glw_p;     // [n_psi]
+    const float* bucket_sp; // [n_buckets] sigma_poly of each bucket
+    const float* poly_x;    // [n_buckets][n_poly] Schulz nodes r_i / R
+    const float* poly_w;    // [n_buckets][n_poly] w_i x_i^4 / sum(w x^4)
+};
+
+// Normalised averaged cylinder form factor P = <|F|^2> / (drho^2 <V^2>) at
+// (q_par, q_perp) about the mean axis z, by the same quadrature as the
+// trace (Gaussian cap of width so truncated at 3 so, GL in gamma and psi,
+// Schulz nodes of the bucket). Computed by one warp; every lane returns it.
+__device__ __forceinline__ double exact_pbar_warp(const Box& b, const Tables& t, const Raw& r)
+{
+    const int lane = threadIdx.x & 31;
+    const int bk = (int)r.bucket;
+    const float* px = t.poly_x + bk * b.n_poly;
+    const float* pw = t.poly_w + bk * b.n_poly;
+    const float gmax = fminf(3.0f * r.so, 3.14159265f);
+    const float inv2s2 = 0.5f / (r.so * r.so);
+    const float q2 = r.qpar * r.qpar + r.qperp * r.qperp;
+    const int no = b.n_gamma * b.n_psi;
+    Kahan<float> num, den;
+    for (int o = lane; o < no; o += 32) {
+        const int i = o / b.n_psi, k = o - i * b.n_psi;
+        const float g = 0.5f * gmax * (t.gl_g[i] + 1.0f);
+        const float psi = 3.14159265f * (t.gl_p[k] + 1.0f);
+        float sg, cg, sp, cp;
+        sas_sincosf(g, sg, cg);
+        sas_sincosf(psi, sp, cp);
+        const float wo = t.glw_g[i] * sg * __expf(-g * g * inv2s2) * t.glw_p[k];
+        const float qc = r.qperp * sg * cp + r.qpar * cg;
+        const float qab = sqrtf(fmaxf(q2 - qc * qc, 0.0f));
+        const float y = fabsf(qc) * 0.5f * r.L;
+        const float sn = sas_sinc(y, __frcp_rn(y));
+        const float qabR = qab * r.R;
+        const float iq = __frcp_rn(qabR), rsq = rsqrtf(qabR);
+        float inner = 0.f;
+        for (int j = 0; j < b.n_poly; ++j) {
+            const float x = px[j];
+            const float a = sas_cyl_a(qabR * x, iq * (1.0f / x), rsq * rsqrtf(x));
+            inner = fmaf(pw[j], a * a, inner);
+        }
+        num.add(wo * sn * sn * inner);
+        den.add(wo);
+    }
+    double n = (double)num.s - (double)num.c, d = (double)den.s - (double)den.c;
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+        n += __shfl_xor_sync(0xffffffffu, n, s);
+        d += __shfl_xor_sync(0xffffffffu, d, s);
+    }
+    return n / d;
+}
+
+struct SurExp {
+    float nx, ny, nz;      // mean axis
+    float R, L, so, sp;    // cylinder parameters
+    float scale_p;         // phi drho^2 <V^2> / <V> (1/angstrom): dSigma = scale_p P
+    int in_box;
+    int pad[3];
+};
+
+struct STParams {
+    InstConst<float> in;
+    Box box;
+    const float* params;
+    const uint64_t* seed;    // device scalar
+    uint32_t philox_base;    // Philox experiment id = philox_base + item experiment
+    // single experiment or batch items
+    const WorkItem* items;
+    uint32_t n_items;
+    unsigned int* queue;
+    const SurExp* sexp;
+    const BatchExp* bexp;    // exact fallback (model constants and table offsets)
+    const float* poly;
+    const float* orient;
+    double* sum_w;
+    double* sum_w2;
+    unsigned long long* count;
+    double* trans;
+    int npix;
+    unsigned long long* fallbacks;
+    int* err;
+};
+
+}  // namespace sur
+}  // namespace sas

@@ -177,3 +177,15 @@ def random_q(n, qmax, seed):
     v /= np.linalg.norm(v, axis=1, keepdims=True)
     r = qmax * rng.uniform(0.0, 1.0, size=n) ** (1.0 / 3.0)
     return v * r[:, None]
+
+
+def surrogate_box(n_fourier=6, n_buckets=32):
+    """Training box of the learned surrogate around the cylinder workload:
+    R in [15, 25], L in [300, 500] angstrom, sigma_orient in [10, 20] deg,
+    sigma_poly in [0.05, 0.15] (n_buckets values), |Q| <= 0.25 1/angstrom,
+    with the cylinder workload's quadrature (40 Schulz nodes, 76 x 76
+    orientation nodes)."""
+    return dict(q_max=0.25, r_min=15.0, r_max=25.0, l_min=300.0, l_max=500.0,
+                sigma_orient_min=math.radians(10.0), sigma_orient_max=math.radians(20.0),
+                poly_min=0.05, poly_max=0.15, n_poly=40, n_gamma=76, n_psi=76,
+                n_buckets=n_buckets, n_fourier=n_fourier, reserved=0)

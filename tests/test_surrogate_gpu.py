@@ -1,0 +1,211 @@
+"""Learned surrogate on the tensor cores (GPU) against the FP64 oracle.
+
+* forward (tcgen05 inference) vs the oracle network on the same weights;
+* exact training targets vs the trace oracle's quadrature;
+* gradients (tcgen05 backward + weight-gradient GEMMs + row sums) vs the
+  oracle's backpropagation on the same BF16 weights (relative 2e-2 per
+  tensor: BF16 activations and stored pre-activations);
+* training lowers the loss; the trace uses the surrogate inside its box and
+  the exact quadrature outside.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp as M
+import paper_2501_06054_gb300 as sas
+import sas_workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    yield
+
+
+def _small_box(n_fourier=4):
+    b = W.surrogate_box(n_fourier=n_fourier, n_buckets=8)
+    b.update(n_poly=12, n_gamma=16, n_psi=16)
+    return b
+
+
+def _raw(box, n, seed):
+    rng = np.random.default_rng(seed)
+    q = box["q_max"] * np.sqrt(rng.random(n))
+    ca = rng.random(n)
+    sp_b = np.array([box["poly_min"] + (box["poly_max"] - box["poly_min"]) * k / (box["n_buckets"] - 1)
+                     for k in range(box["n_buckets"])], np.float32)
+    bk = rng.integers(0, box["n_buckets"], n)
+    raw = np.zeros((n, 8), np.float32)
+    raw[:, 0] = q * ca
+    raw[:, 1] = q * np.sqrt(1 - ca ** 2)
+    raw[:, 2] = rng.uniform(box["r_min"], box["r_max"], n)
+    raw[:, 3] = rng.uniform(box["l_min"], box["l_max"], n)
+    raw[:, 4] = rng.uniform(box["sigma_orient_min"], box["sigma_orient_max"], n)
+    raw[:, 5] = sp_b[bk]
+    raw[:, 6] = bk
+    return raw
+
+
+def test_surrogate_forward_matches_oracle():
+    box = _small_box()
+    s = sas.sas_create_surrogate(box, seed=7, stream=torch.cuda.current_stream())
+    n_params = sas.sas_surrogate_info(s)["n_params"]
+    assert n_params == M.NPARAM
+    p = sas.sas_surrogate_get_params(s, n_params)
+    # give the output layer and biases some weight so the check is not trivial
+    rng = np.random.default_rng(1)
+    p[M.OFF_W5:M.OFF_B5] = rng.uniform(-1, 1, 256).astype(np.float32) * 0.3
+    p[M.OFF_B1 + 256:M.OFF_W5] = rng.normal(size=768).astype(np.float32) * 0.1
+    p[M.OFF_B5] = -1.5
+    sas.sas_surrogate_set_params(s, p)
+    n = 1000                                    # 7 full tiles and a ragged one
+    raw = _raw(box, n, 3)
+    rd = torch.tensor(raw, device="cuda")
+    out = torch.empty(n, device="cuda")
+    sas.sas_surrogate_eval(s, rd, n, out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().astype(np.float64)
+    ref = M.forward(p, M.features(box, raw.astype(np.float64)))
+    err = np.abs(got - ref)
+    assert np.median(err) < 2e-3, np.median(err)
+    assert np.all(err < 3e-2 + 1e-2 * np.abs(ref)), err.max()
+    sas.sas_destroy_surrogate(s)
+
+
+def test_exact_targets_match_oracle():
+    box = _small_box()
+    s = sas.sas_create_surrogate(box, seed=1, stream=torch.cuda.current_stream())
+    raw = _raw(box, 97, 11)
+    raw[0, :2] = 0.0                            # Q = 0
+    rd = torch.tensor(raw, device="cuda")
+    out = torch.empty(97, device="cuda")
+    sas.sas_surrogate_exact(s, rd, 97, out)
+    torch.cuda.synchronize()
+    got = np.exp(out.cpu().numpy().astype(np.float64))
+    ref = M.exact_pbar(box, raw)
+    assert abs(ref[0] - 1.0) < 1e-12
+    assert np.all(np.abs(got - ref) <= 1e-5 * ref + 1e-7), np.max(np.abs(got - ref) / ref)
+    sas.sas_destroy_surrogate(s)
+
+
+def test_exact_targets_full_grid():
+    box = W.surrogate_box()
+    s = sas.sas_create_surrogate(box, seed=1, stream=torch.cuda.current_stream())
+    raw = _raw(box, 3, 5)
+    rd = torch.tensor(raw, device="cuda")
+    out = torch.empty(3, device="cuda")
+    sas.sas_surrogate_exact(s, rd, 3, out)
+    torch.cuda.synchronize()
+    got = np.exp(out.cpu().numpy().astype(np.float64))
+    ref = M.exact_pbar(box, raw)
+    assert np.all(np.abs(got - ref) <= 1e-5 * ref + 1e-7)
+    sas.sas_destroy_surrogate(s)
+
+
+def test_generated_dataset_is_consistent():
+    box = _small_box()
+    s = sas.sas_create_surrogate(box, seed=1, stream=torch.cuda.current_stream())
+    sas.sas_surrogate_generate(s, 4096, seed=9)
+    rp, yp, n = sas.sas_surrogate_dataset(s)
+    assert n == 4096
+    torch.cuda.synchronize()
+    raw = torch.as_tensor(_Dev(rp, (n, 8), "<f4"), device="cuda").cpu().numpy()
+    y = torch.as_tensor(_Dev(yp, (n,), "<f4"), device="cuda").cpu().numpy()
+    q = np.hypot(raw[:, 0], raw[:, 1])
+    assert q.max() <= box["q_max"] * (1 + 1e-6)
+    assert raw[:, 2].min() >= box["r_min"] and raw[:, 2].max() <= box["r_max"]
+    assert np.all(np.isfinite(y)) and y.max() <= 1e-5
+    idx = np.arange(0, n, 512)
+    ref = M.exact_pbar(box, raw[idx])
+    assert np.all(np.abs(np.exp(y[idx].astype(np.float64)) - ref) <= 1e-5 * ref + 1e-7)
+    sas.sas_destroy_surrogate(s)
+
+
+class _Dev:
+    """Minimal __cuda_array_interface__ view of library-owned device memory."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = dict(shape=shape, typestr=typestr, data=(ptr, False),
+                                             version=3, strides=None)
+
+
+def test_gradients_match_oracle():
+    box = _small_box()
+    s = sas.sas_create_surrogate(box, seed=5, stream=torch.cuda.current_stream())
+    p = sas.sas_surrogate_get_params(s, M.NPARAM)
+    rng = np.random.default_rng(2)
+    p[M.OFF_W5:M.OFF_B5] = rng.uniform(-1, 1, 256).astype(np.float32) * 0.3
+    p[M.OFF_B1 + 256:M.OFF_W5] = rng.normal(size=768).astype(np.float32) * 0.05
+    sas.sas_surrogate_set_params(s, p)
+    n = 512
+    raw = _raw(box, n, 21)
+    y = (np.random.default_rng(3).normal(size=n) - 3.0).astype(np.float32)
+    rd = torch.tensor(raw, device="cuda")
+    yd = torch.tensor(y, device="cuda")
+    g = sas.sas_surrogate_grad(s, rd, yd, n, M.NPARAM).astype(np.float64)
+    loss, go = M.loss_and_grad(p, M.features(box, raw.astype(np.float64)), y.astype(np.float64))
+    go[M.OFF_B1:M.OFF_B1 + 256] = 0.0          # the layer-1 bias lives in W1[:, 63]
+    segs = dict(W1=(M.OFF_W1, M.OFF_W2), W2=(M.OFF_W2, M.OFF_W3), W3=(M.OFF_W3, M.OFF_W4),
+                W4=(M.OFF_W4, M.OFF_B1), b234=(M.OFF_B1 + 256, M.OFF_W5), w5=(M.OFF_W5, M.OFF_B5),
+                b5=(M.OFF_B5, M.OFF_B5 + 1))
+    for name, (a, b) in segs.items():
+        d = np.linalg.norm(g[a:b] - go[a:b]) / max(np.linalg.norm(go[a:b]), 1e-30)
+        assert d < 2e-2, (name, d)
+    assert np.all(g[M.OFF_B1:M.OFF_B1 + 256] == 0.0)
+    sas.sas_destroy_surrogate(s)
+
+
+def _mse(s, raw_ptr, y_ptr, n):
+    out = torch.empty(n, device="cuda")
+    sas.sas_surrogate_eval(s, raw_ptr, n, out)
+    y = torch.as_tensor(_Dev(y_ptr, (n,), "<f4"), device="cuda")
+    torch.cuda.synchronize()
+    return float(torch.mean((out - y) ** 2))
+
+
+def test_training_reduces_loss():
+    box = _small_box()
+    s = sas.sas_create_surrogate(box, seed=3, stream=torch.cuda.current_stream())
+    sas.sas_surrogate_generate(s, 1 << 17, seed=4)
+    rp, yp, n = sas.sas_surrogate_dataset(s)
+    before = _mse(s, rp, yp, n)
+    sas.sas_surrogate_train(s, 400, 4096, 2e-3, 400)
+    after = _mse(s, rp, yp, n)
+    assert sas.sas_surrogate_info(s)["steps_done"] == 400
+    assert after < 0.2 * before, (before, after)
+    sas.sas_destroy_surrogate(s)
+
+
+def test_surrogate_trace_falls_back_outside_the_box():
+    box = _small_box()
+    s = sas.sas_create_surrogate(box, seed=3, stream=torch.cuda.current_stream())
+    inst = W.instrument(nx=64, ny=64, pixel_x=0.03, pixel_y=0.03)   # corners reach |Q| = 0.3 > q_max
+    m = W.Model(kind=W.CYLINDER, radius=20.0, length=400.0, sld=2e-6, volume_fraction=0.01, poly=0.1,
+                n_poly=12, sigma_orient=math.radians(15), n_gamma=16, n_psi=16)
+    e = sas.Experiment(inst, m, stream=torch.cuda.current_stream())
+    sas.sas_attach_surrogate(e.h, s)
+    n = 20000
+    e.trace(n, seed=2)
+    d = e.read()
+    fb = sas.sas_surrogate_fallbacks(exp=e.h)
+    ref = oracle.trace(inst, m, n, seed=2)
+    assert np.array_equal(d["count"], ref["count"].astype(np.uint64))   # same histories
+    assert 0 < fb < n
+    # out-of-box model: exact path, identical to the plain trace
+    m2 = W.Model(**{**m.as_dict(), "radius": 60.0})
+    e.set_model(m2)
+    e.trace(n, seed=2)
+    d2 = e.read()
+    ref2 = oracle.trace(inst, m2, n, seed=2)
+    so = ref2["sum_w"]
+    big = so > 1e-6 * so.max()
+    assert np.all(np.abs(d2["sum_w"] - so)[big] <= 1e-4 * so[big])
+    e.close()
+    sas.sas_destroy_surrogate(s)
