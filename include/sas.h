@@ -258,8 +258,9 @@ typedef struct sas_surrogate sas_surrogate;          /* opaque, library-owned */
  * the same node counts (n_poly Schulz nodes; n_gamma x n_psi orientation
  * nodes). Its inputs are the rotation-invariant features
  * (q_par L / 2, q_perp R, L / (2R), sigma_orient, sigma_poly) plus
- * n_fourier (sin, cos) pairs of q_par L / 8 * k, where q_par and q_perp are
- * the components of Q along and across the mean axis; its output is log P.
+ * n_fourier (sin, cos) pairs of k q_par L / 4 (k = 1..n), where q_par and
+ * q_perp are the components of Q along and across the mean axis; its output
+ * is log P (trained on log max(P, 1e-6)).
  * sigma_poly is learned on n_buckets values spread evenly over the range. */
 typedef struct sas_surrogate_box {
     double q_max;                                 /* 1/angstrom */

@@ -5,7 +5,7 @@ Plain numpy definitions of what the surrogate computes:
 * the feature map of an oriented polydisperse cylinder evaluation:
   u = q_par L / 2, v = q_perp R, a = L / (2R), sigma_orient, sigma_poly,
   each scaled linearly to [-1, 1] over the training box, then n_fourier
-  (sin, cos) pairs of k u / 4 (k = 1..n), the last of 64 columns is 1 (it
+  (sin, cos) pairs of k u / 2 (k = 1..n), the last of 64 columns is 1 (it
   carries the layer-1 bias through W1[:, 63]);
 * the network log P = b5 + w5 . h4, h_l = SiLU(W_l h_{l-1} + b_l),
   SiLU(z) = z s(z), s(z) = 1/2 + tanh(z/2)/2, with BF16-rounded hidden
@@ -32,6 +32,7 @@ OFF_B1 = OFF_W4 + H * H
 OFF_W5 = OFF_B1 + 4 * H
 OFF_B5 = OFF_W5 + H
 NPARAM = OFF_B5 + 1
+TARGET_FLOOR = 1e-6
 
 
 def bf16(x):
@@ -84,8 +85,8 @@ def features(box, raw):
     F[:, 3] = 2 * (raw[:, 4] - box["sigma_orient_min"]) / (box["sigma_orient_max"] - box["sigma_orient_min"]) - 1
     F[:, 4] = 2 * (raw[:, 5] - box["poly_min"]) / (box["poly_max"] - box["poly_min"]) - 1
     for k in range(box["n_fourier"]):
-        F[:, 5 + 2 * k] = np.sin((k + 1) * 0.25 * u)
-        F[:, 6 + 2 * k] = np.cos((k + 1) * 0.25 * u)
+        F[:, 5 + 2 * k] = np.sin((k + 1) * 0.5 * u)
+        F[:, 6 + 2 * k] = np.cos((k + 1) * 0.5 * u)
     F[:, 63] = 1.0
     return F
 
@@ -139,8 +140,9 @@ def loss_and_grad(p, X, y, rnd=bf16):
 
 
 def exact_pbar(box, raw):
-    """Exact target P at raw parameters [n][8] (bucket sigma_poly in column 5)
-    with the trace oracle's quadrature about the z axis."""
+    """Exact P at raw parameters [n][8] (bucket sigma_poly in column 5)
+    with the trace oracle's quadrature about the z axis. The training
+    target is log max(P, TARGET_FLOOR)."""
     import oracle
     import sas_workloads as W
     out = np.empty(len(raw))

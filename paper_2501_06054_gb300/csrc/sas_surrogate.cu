@@ -35,6 +35,11 @@ namespace sur {
 
 // ------------------------------------------------------------- kernels
 
+// Targets are log(max(P, TARGET_FLOOR)): bins fainter than 1e-6 of P(0)
+// carry no weight in the detector comparisons, so the fit spends no
+// capacity on the depth of the minima below it.
+constexpr float TARGET_FLOOR = 1e-6f;
+
 // Training targets: per sample draw the raw parameters uniformly in the box
 // (|Q| = q_max sqrt(u): area-uniform like the detector; cos(angle to the
 // axis) uniform; sigma_poly from the bucket grid) and evaluate the exact
@@ -69,7 +74,7 @@ __global__ void data_kernel(Box b, Tables t, uint64_t seed, uint64_t first, uint
         const double p = exact_pbar_warp(b, t, r);
         if (lane == 0) {
             if (draw) raw[s] = r;
-            y[s] = (float)log(fmax(p, 1e-12));
+            y[s] = (float)log(fmax(p, (double)TARGET_FLOOR));
         }
     }
 }
@@ -755,7 +760,7 @@ sur::Box device_box(const sas_surrogate_box& b)
     d.a_min = (float)(0.5 * b.l_min / b.r_max);
     d.a_max = (float)(0.5 * b.l_max / b.r_min);
     d.n_four = b.n_fourier;
-    d.four_w = 0.25f;
+    d.four_w = 0.5f;
     d.n_buckets = b.n_buckets;
     d.n_poly = b.n_poly;
     d.n_gamma = b.n_gamma;

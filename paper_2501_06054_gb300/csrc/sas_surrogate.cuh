@@ -30,7 +30,7 @@ struct Raw {
 };
 
 // Feature vector (64 wide: [0, 5) scaled raw inputs in [-1, 1], then
-// n_four (sin, cos) pairs of k * four_w * u, column 63 = 1 (bias of layer 1)).
+// n_four (sin, cos) pairs of k * four_w * u (four_w = 1/2), column 63 = 1 (bias of layer 1)).
 __device__ __forceinline__ void features(const Box& b, float qpar, float qperp, float R, float L, float so,
                                          float sp, float* f64)
 {

@@ -114,5 +114,5 @@ def test_features_definition():
     assert abs(F[0, 1] - (2 * v / (0.25 * 25) - 1)) < 1e-15
     assert abs(F[0, 2] - (2 * (a - 6.0) / (500 / 30 - 6.0) - 1)) < 1e-12
     assert abs(F[0, 3]) < 1e-12 and abs(F[0, 4]) < 1e-12
-    assert abs(F[0, 5] - np.sin(u / 4)) < 1e-15 and abs(F[0, 8] - np.cos(u / 2)) < 1e-15
+    assert abs(F[0, 5] - np.sin(u / 2)) < 1e-15 and abs(F[0, 8] - np.cos(u)) < 1e-15
     assert F[0, 63] == 1.0 and np.all(F[0, 9:63] == 0)

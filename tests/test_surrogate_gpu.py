@@ -89,7 +89,7 @@ def test_exact_targets_match_oracle():
     sas.sas_surrogate_exact(s, rd, 97, out)
     torch.cuda.synchronize()
     got = np.exp(out.cpu().numpy().astype(np.float64))
-    ref = M.exact_pbar(box, raw)
+    ref = np.maximum(M.exact_pbar(box, raw), M.TARGET_FLOOR)
     assert abs(ref[0] - 1.0) < 1e-12
     assert np.all(np.abs(got - ref) <= 1e-5 * ref + 1e-7), np.max(np.abs(got - ref) / ref)
     sas.sas_destroy_surrogate(s)
@@ -104,7 +104,7 @@ def test_exact_targets_full_grid():
     sas.sas_surrogate_exact(s, rd, 3, out)
     torch.cuda.synchronize()
     got = np.exp(out.cpu().numpy().astype(np.float64))
-    ref = M.exact_pbar(box, raw)
+    ref = np.maximum(M.exact_pbar(box, raw), M.TARGET_FLOOR)
     assert np.all(np.abs(got - ref) <= 1e-5 * ref + 1e-7)
     sas.sas_destroy_surrogate(s)
 
@@ -123,7 +123,7 @@ def test_generated_dataset_is_consistent():
     assert raw[:, 2].min() >= box["r_min"] and raw[:, 2].max() <= box["r_max"]
     assert np.all(np.isfinite(y)) and y.max() <= 1e-5
     idx = np.arange(0, n, 512)
-    ref = M.exact_pbar(box, raw[idx])
+    ref = np.maximum(M.exact_pbar(box, raw[idx]), M.TARGET_FLOOR)
     assert np.all(np.abs(np.exp(y[idx].astype(np.float64)) - ref) <= 1e-5 * ref + 1e-7)
     sas.sas_destroy_surrogate(s)
 
