@@ -248,6 +248,32 @@ sas_status sas_batch_autotune(sas_batch *batch, uint64_t seed, sas_batch_config 
 
 sas_status sas_destroy_batch(sas_batch *batch);
 
+/* Batched trace that allocates nothing. The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc, for example
+ * code whose device memory belongs to another allocator or a fixed budget,
+ * plugins whose host application forbids device allocations, or loops that
+ * cannot accept the implicit synchronisation of an allocation.
+ *
+ * Same histories and results as sas_create_batch + sas_trace_batch with the
+ * default configuration (Philox experiment id = index e). The caller passes
+ * host inputs (instrument, n_exp models (FP32), neutron counts) and DEVICE
+ * outputs: sum_w, sum_w2, count [n_exp][nx*ny] and transmitted [n_exp]; the
+ * call zeroes them, uploads the tables and launches the batch kernel on
+ * `stream`, asynchronously.
+ * Scratch: model constants, quadrature tables, work items, the work counter
+ * and the seed go to one static device array of 8 MiB that every GPU loading
+ * the library holds until process exit. A batch whose tables and items do
+ * not fit returns SAS_ERR_ARG with the bytes it would need.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents: calls
+ * that overlap on the GPU (e.g. on two streams) race, so issue them in
+ * order on one stream or synchronise between them. */
+sas_status sas_trace_batch_static(const sas_instrument *inst, const sas_model_desc *models,
+                                  const uint64_t *counts, size_t n_exp, uint64_t seed,
+                                  double *sum_w, double *sum_w2, uint64_t *count,
+                                  double *transmitted, void *stream);
+
 /* ---- learned surrogate of the averaged cylinder form factor --------- */
 
 typedef struct sas_surrogate sas_surrogate;          /* opaque, library-owned */

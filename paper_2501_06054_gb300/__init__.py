@@ -120,6 +120,7 @@ _SIGS = {
     "sas_attach_surrogate": [_vp, _vp],
     "sas_batch_attach_surrogate": [_vp, _vp],
     "sas_surrogate_fallbacks": [_vp, _vp, ctypes.POINTER(_u64)],
+    "sas_trace_batch_static": [_vp, _vp, _vp, ctypes.c_size_t, _u64, _vp, _vp, _vp, _vp, _vp],
 }
 
 # extra entry points added by later modules of the library register here
@@ -369,6 +370,19 @@ def sas_batch_autotune(batch, seed):
 
 def sas_destroy_batch(batch):
     _check(lib().sas_destroy_batch(batch))
+
+
+def sas_trace_batch_static(instrument, models, counts, seed, sum_w, sum_w2, count, transmitted,
+                           stream=None):
+    """Batched trace without device allocation: outputs are caller-owned
+    device buffers ([n_exp][nx*ny] and [n_exp])."""
+    inst = instrument if isinstance(instrument, sas_instrument) else make_instrument(instrument)
+    arr = (sas_model_desc * len(models))(*[m if isinstance(m, sas_model_desc) else make_model(m)
+                                           for m in models])
+    cnt = np.ascontiguousarray(np.asarray(counts, dtype=np.uint64))
+    _check(lib().sas_trace_batch_static(ctypes.byref(inst), ctypes.cast(arr, _vp), cnt.ctypes.data,
+                                        len(models), int(seed), _ptr(sum_w), _ptr(sum_w2),
+                                        _ptr(count), _ptr(transmitted), _stream_handle(stream)))
 
 
 def make_box(d) -> sas_surrogate_box:
