@@ -10,6 +10,10 @@ Run once (python gen_coeffs.py > sas_coeffs.h); the output is committed.
 * a(x) = 2 J1(x) / x for 0 <= x <= X1: a polynomial in s = (x / X1)^2, fitted here
   by Chebyshev-node least squares refined with Lawson iterations toward the
   minimax polynomial of the absolute error.
+* a(x) for x <= 8 in product form (1 - x^2/j1^2)(1 - x^2/j2^2) h(x^2) with the
+  first two zeros j1, j2 of J1 (scipy) and h a degree-8 polynomial in x^2
+  fitted like the above (relative error ~1e-8); no square root, no branch
+  for the cylinder workloads' arguments, and the zeros are exact factors.
 * x >= X1: the modulus-phase form of J1 (J1 = M cos(theta), Y1 = M sin(theta)),
   with m(u) = M sqrt(pi x / 2) and h(u) = x (theta - x + 3 pi / 4) fitted as
   polynomials in u = (X1 / x)^2; M and theta are computed from scipy's J1, Y1.
@@ -106,6 +110,21 @@ def fit_trig():
     return cS, eS, cC, eC
 
 
+def fit_product(deg=8, X=8.0):
+    n = 6000
+    s = 0.5 * X * X * (1 - np.cos(np.pi * (np.arange(n) + 0.5) / n))
+    x = np.sqrt(s)
+    j = sp.jn_zeros(1, 2)
+    a = np.where(x > 0, 2 * sp.j1(np.maximum(x, 1e-300)) / np.maximum(x, 1e-300), 1.0)
+    p = (1 - s / j[0] ** 2) * (1 - s / j[1] ** 2)
+    ok = np.abs(p) > 1e-6
+    u = s / (X * X)
+    basis = [lambda uu, k=k: uu ** k for k in range(deg + 1)]
+    c, e = lawson_fit(u[ok], (a / p)[ok], basis)
+    cs = [ci / (X * X) ** k for k, ci in enumerate(c)]   # coefficients in s = x^2
+    return cs, e, 1.0 / j[0] ** 2, 1.0 / j[1] ** 2, X * X
+
+
 def split2(c):
     hi = f32(c)
     return [hi, f32(c - hi)]
@@ -116,6 +135,7 @@ def main():
     cs, es = fit_small(7)
     cm, em, ch, eh = fit_large(5, 5)
     cS, eS, cC, eC = fit_trig()
+    cP, eP, iz1, iz2, smax = fit_product()
     p2 = split2(math.pi / 2)
     p4 = split2(math.pi / 4)
     w = out.write
@@ -127,6 +147,10 @@ def main():
       f"S {eS:.3e}, C {eC:.3e} */\n")
     w("#define SAS_PIO2_1 %.9ef\n#define SAS_PIO2_2 %.9ef\n" % tuple(p2))
     w("#define SAS_PIO4_1 %.9ef\n#define SAS_PIO4_2 %.9ef\n" % tuple(p4))
+    w(f"/* 2 J1(x)/x = (1 - s z1)(1 - s z2) h(s), s = x^2 <= {smax:g}; fit error of h {eP:.3e} */\n")
+    w("#define SAS_J1P_SMAX %.9ef\n#define SAS_J1P_Z1 %.9ef\n#define SAS_J1P_Z2 %.9ef\n" % (smax, iz1, iz2))
+    w(f"#define SAS_J1P_C_N {len(cP)}\n")
+    w("#define SAS_J1P_C {" + ", ".join("%.9ef" % v for v in cP) + "}\n")
     w("/* sin r = r + r^3 S(r^2), cos r = 1 + r^2 C(r^2) */\n")
     for name, arr in (("SAS_SIN_C", list(cS)), ("SAS_COS_C", list(cC)), ("SAS_J1S_C", list(cs)),
                       ("SAS_J1M_C", list(cm)), ("SAS_J1H_C", list(ch))):

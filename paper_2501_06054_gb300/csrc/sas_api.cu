@@ -52,14 +52,15 @@ sas_status set_error(sas_status s, const std::string& msg) { return fail(s, msg)
 sas_status set_cuda_error(cudaError_t e, const char* what) { return cuda_fail(e, what); }
 
 // Cost model of one history in FLOP (FMA = 2): the nominal per-term counts
-// of the kernels' formulas (sphere amplitude 33, cylinder radial term 22,
-// orientation node 60, geometry 150, Percus-Yevick 40).
+// of the kernels' formulas (sphere amplitude 33, core-shell node 62,
+// cylinder radial term 26, orientation node 60, geometry 150,
+// Percus-Yevick 40).
 double host_flops_per_history(const sas_model_desc& m, int np, int no)
 {
     double per;
     if (m.kind == SAS_SPHERE) per = np * 36.0;
-    else if (m.kind == SAS_CORE_SHELL) per = np * 71.0;
-    else if (m.kind == SAS_CYLINDER) per = no * (60.0 + np * 22.0);
+    else if (m.kind == SAS_CORE_SHELL) per = np * 62.0 + 20.0;
+    else if (m.kind == SAS_CYLINDER) per = no * (60.0 + np * 26.0);
     else per = no * (60.0 + np * 38.0);
     return per + 150.0 + (m.sq_kind == SAS_SQ_HARD_SPHERE_PY ? 40.0 : 0.0);
 }
@@ -284,7 +285,7 @@ sas_status build_model_tables(const sas_model_desc& m, ModelTables& t)
         } else if (m.kind == SAS_CYLINDER) {
             const double V = pi * ri * ri * m.length;
             const double F0 = (m.sld - m.sld_solvent) * V;
-            p[0] = ri; p[1] = 1.0 / ri; p[2] = 1.0 / std::sqrt(ri); p[3] = w[i] * F0 * F0;
+            p[0] = ri; p[1] = 1.0 / ri; p[2] = 1.0 / std::sqrt(ri); p[3] = w[i] * F0 * F0; p[4] = ri * ri;
             vmean += w[i] * V;
         } else {
             const double V = 4.0 / 3.0 * pi * m.radius_polar * ri * ri;
@@ -338,6 +339,7 @@ ModelConst<T> model_const(const sas_model_desc& m, const ModelTables& t)
     c.n_orient = t.n_orient;
     c.scale = (T)t.scale;
     c.half_length = (T)t.half_length;
+    c.shell = (T)m.thickness;
     c.rp2 = (T)t.rp2;
     c.sq_2r = (T)t.sq_2r;
     c.sq_24phi = (T)t.sq_24phi;

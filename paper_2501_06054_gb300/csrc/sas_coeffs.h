@@ -8,6 +8,12 @@
 #define SAS_PIO2_2 -4.371138829e-08f
 #define SAS_PIO4_1 7.853981853e-01f
 #define SAS_PIO4_2 -2.185569414e-08f
+/* 2 J1(x)/x = (1 - s z1)(1 - s z2) h(s), s = x^2 <= 64; fit error of h 6.653e-10 */
+#define SAS_J1P_SMAX 6.400000000e+01f
+#define SAS_J1P_Z1 6.811074783e-02f
+#define SAS_J1P_Z2 2.031758155e-02f
+#define SAS_J1P_C_N 9
+#define SAS_J1P_C {9.999999993e-01f, -3.657166892e-02f, 5.905152050e-04f, -5.678942625e-06f, 3.695457932e-08f, -1.747459128e-10f, 6.223534431e-13f, -1.621063729e-15f, 2.424090897e-18f}
 /* sin r = r + r^3 S(r^2), cos r = 1 + r^2 C(r^2) */
 #define SAS_SIN_C_N 3
 #define SAS_SIN_C {-1.666666455e-01f, 8.332725399e-03f, -1.958295501e-04f}

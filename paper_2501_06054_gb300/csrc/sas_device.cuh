@@ -150,16 +150,29 @@ __device__ __forceinline__ T avg_sphere(T q, T iq, const T* __restrict__ poly, i
 }
 
 template <typename T>
-__device__ __forceinline__ T avg_core_shell(T q, T iq, const T* __restrict__ poly, int np)
+__device__ __forceinline__ T avg_core_shell(T q, T iq, const T* __restrict__ poly, int np, T shell)
 {
     T acc = 0;
+    if constexpr (sizeof(T) == sizeof(float)) {
+        float st, ct;
+        sas_sincosf(q * shell, st, ct);
 #pragma unroll 4
-    for (int i = 0; i < np; ++i) {
-        const T* p = poly + 8 * i;
-        const T g1 = M<T>::sphere_g(q * p[0], iq * p[1]);
-        const T g2 = M<T>::sphere_g(q * p[2], iq * p[3]);
-        const T F = fma(p[4], g1, p[5] * g2);
-        acc = fma(F, F, acc);
+        for (int i = 0; i < np; ++i) {
+            const T* p = poly + 8 * i;
+            float g1, g2;
+            sas_sphere_g2(q * p[0], iq * p[1], q * p[2], iq * p[3], st, ct, g1, g2);
+            const T F = fma(p[4], g1, p[5] * g2);
+            acc = fma(F, F, acc);
+        }
+    } else {
+#pragma unroll 4
+        for (int i = 0; i < np; ++i) {
+            const T* p = poly + 8 * i;
+            const T g1 = M<T>::sphere_g(q * p[0], iq * p[1]);
+            const T g2 = M<T>::sphere_g(q * p[2], iq * p[3]);
+            const T F = fma(p[4], g1, p[5] * g2);
+            acc = fma(F, F, acc);
+        }
     }
     return acc;
 }
@@ -177,6 +190,9 @@ struct Kahan {
     }
 };
 
+// FP32: 2 J1(x)/x from s = x^2 = |Q x c|^2 r^2 by the product form for
+// x <= 8 (no square root per term); larger x (tails of broad size
+// distributions) take the modulus-phase form. FP64: the C library's j1.
 template <typename T>
 __device__ __forceinline__ T avg_cylinder(const T qv[3], const T* __restrict__ poly, int np,
                                           const T* __restrict__ orient, int no, T half_len)
@@ -192,14 +208,29 @@ __device__ __forceinline__ T avg_cylinder(const T qv[3], const T* __restrict__ p
         const T y = fabs(qc) * half_len;
         const T sn = M<T>::sinc(y, M<T>::rcp(y));
         const T qab = M<T>::sqrt_(qab2);
-        const T iq = M<T>::rcp(qab);
-        const T rsq = M<T>::rsqrt(qab);
         T inner = 0;
+        if constexpr (sizeof(T) == sizeof(float)) {
 #pragma unroll 4
-        for (int i = 0; i < np; ++i) {
-            const T* p = poly + 8 * i;
-            const T a = M<T>::cyl_a(qab * p[0], iq * p[1], rsq * p[2]);
-            inner = fma(p[3], a * a, inner);
+            for (int i = 0; i < np; ++i) {
+                const T* p = poly + 8 * i;
+                const float sx = qab2 * p[4];
+                float a;
+                if (sx <= SAS_J1P_SMAX) {
+                    a = sas_cyl_a_s(sx);
+                } else {
+                    const float x = qab * p[0];
+                    a = sas_cyl_a_large(x, __frcp_rn(x), rsqrtf(x));
+                }
+                inner = fma(p[3], a * a, inner);
+            }
+        } else {
+            const T iq = M<T>::rcp(qab);
+#pragma unroll 4
+            for (int i = 0; i < np; ++i) {
+                const T* p = poly + 8 * i;
+                const T a = M<T>::cyl_a(qab * p[0], iq * p[1], 0);
+                inner = fma(p[3], a * a, inner);
+            }
         }
         k.add(c[3] * sn * sn * inner);
     }
@@ -244,7 +275,7 @@ __device__ __forceinline__ T dsigma(const T qv[3], const ModelConst<T>& mc,
     if (KIND == SAS_SPHERE) {
         avg = avg_sphere<T>(q, M<T>::rcp(q), poly, mc.n_poly);
     } else if (KIND == SAS_CORE_SHELL) {
-        avg = avg_core_shell<T>(q, M<T>::rcp(q), poly, mc.n_poly);
+        avg = avg_core_shell<T>(q, M<T>::rcp(q), poly, mc.n_poly, mc.shell);
     } else if (KIND == SAS_CYLINDER) {
         avg = avg_cylinder<T>(qv, poly, mc.n_poly, orient, mc.n_orient, mc.half_length);
     } else {

@@ -134,6 +134,37 @@ SAS_HD float sas_sphere_g(float x, float inv)
 // f(x) = 3 (sin x - x cos x) / x^3
 SAS_HD float sas_sphere_f(float x, float inv) { return 3.0f * sas_sphere_g(x, inv); }
 
+// g at two radii r and r + t of the same history: x1 = q r, x2 = q (r + t).
+// x2 = k pi/2 + (r1 + q t) with the quadrant of x1, so sin and cos of the
+// reduced angle of x2 follow from those of x1 by angle addition with
+// (st, ct) = (sin q t, cos q t); below pi/4 g(x2) uses its Taylor series.
+SAS_HD void sas_sphere_g2(float x1, float inv1, float x2, float inv2, float st, float ct, float& g1,
+                          float& g2)
+{
+    const SasTrig g = sas_reduce_pio2(x1);
+    const float sr = fmaf(g.r * g.t, g.S, g.r);
+    const float cr = fmaf(g.t, g.C, 1.0f);
+    const int flip = g.kb << 30;
+    // inner radius
+    const float A1 = fmaf(-x1, cr, sr);
+    const float B1 = fmaf(x1, sr, cr);
+    float num1 = (g.kb & 1) ? B1 : A1;
+    num1 = sas_flip_sign(num1, flip);
+    g1 = (x1 < 0.78539816f) ? (g.S - g.C) : num1 * inv1 * inv1 * inv1;
+    // outer radius: sin, cos of (r + q t)
+    const float sr2 = fmaf(sr, ct, cr * st);
+    const float cr2 = fmaf(cr, ct, -sr * st);
+    const float A2 = fmaf(-x2, cr2, sr2);
+    const float B2 = fmaf(x2, sr2, cr2);
+    float num2 = (g.kb & 1) ? B2 : A2;
+    num2 = sas_flip_sign(num2, flip);
+    // g(x) = 1/3 - x^2/30 + x^4/840 - x^6/45360 + x^8/3991680 - ...
+    const float c[5] = {3.333333333e-01f, -3.333333333e-02f, 1.190476190e-03f, -2.204585538e-05f,
+                        2.505210839e-07f};
+    const float small2 = sas_horner(c, x2 * x2);
+    g2 = (x2 < 0.78539816f) ? small2 : num2 * inv2 * inv2 * inv2;
+}
+
 // a(x) = 2 J1(x) / x for 0 <= x <= X1
 SAS_HD float sas_cyl_a_small(float x)
 {
@@ -166,6 +197,17 @@ SAS_HD float sas_cyl_a_large(float x, float inv, float rsx)
     sas_trig_sincos(g, s, c);
     // 2 sqrt(2/pi) = 1.5957691216
     return 1.5957691216f * m * inv * rsx * s;
+}
+
+// a(x) = 2 J1(x) / x from s = x^2 <= SAS_J1P_SMAX (x <= 8): product of the
+// first two zero factors and a fitted polynomial; no square root needed.
+SAS_HD float sas_cyl_a_s(float s)
+{
+    const float c[9] = SAS_J1P_C;
+    const float h = sas_horner(c, s);
+    const float p1 = fmaf(-s, SAS_J1P_Z1, 1.0f);
+    const float p2 = fmaf(-s, SAS_J1P_Z2, 1.0f);
+    return p1 * p2 * h;
 }
 
 SAS_HD float sas_cyl_a(float x, float inv, float rsx)

@@ -98,11 +98,18 @@ __device__ __forceinline__ double exact_pbar_warp(const Box& b, const Tables& t,
         const float y = fabsf(qc) * 0.5f * r.L;
         const float sn = sas_sinc(y, __frcp_rn(y));
         const float qabR = qab * r.R;
-        const float iq = __frcp_rn(qabR), rsq = rsqrtf(qabR);
+        const float qabR2 = qabR * qabR;
         float inner = 0.f;
         for (int j = 0; j < b.n_poly; ++j) {
             const float x = px[j];
-            const float a = sas_cyl_a(qabR * x, iq * (1.0f / x), rsq * rsqrtf(x));
+            const float sx = qabR2 * (x * x);
+            float a;
+            if (sx <= SAS_J1P_SMAX) {
+                a = sas_cyl_a_s(sx);
+            } else {
+                const float xx = qabR * x;
+                a = sas_cyl_a_large(xx, __frcp_rn(xx), rsqrtf(xx));
+            }
             inner = fmaf(pw[j], a * a, inner);
         }
         num.add(wo * sn * sn * inner);

@@ -29,7 +29,7 @@ struct InstConst {
 //     sphere     {r, 1/r, 9 w (drho V)^2, 0...}
 //     core-shell {r_c, 1/r_c, r_o, 1/r_o, 3 sqrt(w) (rho_c - rho_s) V_c,
 //                 3 sqrt(w) (rho_s - rho_solv) V_o, 0, 0}
-//     cylinder   {r, 1/r, 1/sqrt(r), w (drho V)^2, 0...}
+//     cylinder   {r, 1/r, 1/sqrt(r), w (drho V)^2, r^2, 0...}
 //     ellipsoid  {r_e^2, 9 w (drho V)^2, 0...}
 //   orient table per node: {c_x, c_y, c_z, weight}
 template <typename T>
@@ -37,6 +37,7 @@ struct ModelConst {
     int kind, sq_kind, n_poly, n_orient;
     T scale;         // phi / <V>
     T half_length;   // cylinder L / 2
+    T shell;         // core-shell shell thickness
     T rp2;           // ellipsoid polar radius squared
     T sq_2r;         // 2 R_hs
     T sq_24phi;      // 24 phi_hs

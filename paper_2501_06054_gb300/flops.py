@@ -10,23 +10,30 @@ into FLOP/s for the roofline against the FP32 CUDA-core peak.
       r^2, sin poly (2 FMA), cos poly (3 FMA), r^3 (mul), sin r, cos r
       (2 FMA), the two quadrant forms (2 FMA), / x^3 (3 mul), S - C (add)
       (the factor 3 of f = 3 g is folded into the tables)
-  cylinder radial factor 2 J1(Q r)/(Q r), x <= 4 branch        22
-      x, 1/x, 1/sqrt(x) (3 mul), (x/4)^2 (2 mul), polynomial (7 FMA),
-      a^2 (mul), weighted sum (FMA)
+  cylinder radial factor 2 J1(Q r)/(Q r), x <= 8 product form  26
+      x^2 = |Q x c|^2 r^2 (mul), zero factors (2 FMA), polynomial
+      (8 FMA), product (2 mul), a^2 (mul), weighted sum (FMA)
   orientation node overhead (cylinder, ellipsoid)              60
       Q.c, |Q x c|^2 (11 FMA/mul), sqrt, 1/x, rsqrt (3), sinc (~26),
       weight products (3), Kahan (4)
   ellipsoid term: |Q|_eff^2 (FMA), rsqrt, x (mul), amplitude
                   without its own x, 1/x, g^2, weighted sum        2+1+1+31+1+2 = 38
   sphere node: amplitude, g^2, weighted sum                       33 + 3
-  core-shell node: two amplitudes + combination (mul, FMA, FMA)   2*33 + 5
+  core-shell node: inner amplitude 33; outer amplitude by angle
+      addition from the inner reduced angle: x, 1/x (2 mul), sin and
+      cos of (r + q t) (2 mul + 2 FMA), two quadrant forms (2 FMA),
+      / x^3 (3 mul), x^2 and its Taylor form (mul + 4 FMA) = 24;
+      combination (mul, FMA, FMA) 5                                33 + 24 + 5
+      per history sin, cos of q t                                   20
   per history: geometry (wavelength, pinholes, slab, detector
                point, Q, solid angle)                           150
                Percus-Yevick S(Q)                               40
 """
 
 AMP = 33
-CYL_TERM = 22
+CYL_TERM = 26
+CS_NODE = 62
+CS_HISTORY = 20
 ORIENT_NODE = 60
 GEOMETRY = 150
 PY = 40
@@ -36,7 +43,7 @@ def flops_per_history(kind: int, n_poly: int, n_orient: int = 1, sq: bool = Fals
     if kind == 0:        # sphere
         per = n_poly * (AMP + 3)
     elif kind == 1:      # core-shell
-        per = n_poly * (2 * AMP + 5)
+        per = n_poly * CS_NODE + CS_HISTORY
     elif kind == 2:      # cylinder
         per = n_orient * (ORIENT_NODE + n_poly * CYL_TERM)
     else:                # ellipsoid
