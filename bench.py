@@ -284,6 +284,53 @@ def secondary(stream, info):
     return out
 
 
+def run_single_workload(args):
+    """Time the cylinder workload alone (exact quadrature, or the learned
+    surrogate after training it), one GPU; prints one JSON line."""
+    import torch
+    import paper_2501_06054_gb300 as sas
+    from paper_2501_06054_gb300 import flops as F
+    stream = torch.cuda.Stream()
+    info = sas.sas_device_info()
+    cfg = W.cylinder_config()
+    m = cfg["model"]
+    n = int(args.neutrons) if args.neutrons else (2_000_000 if args.workload == "cylinder" else 100_000_000)
+    with torch.cuda.stream(stream):
+        e = sas.Experiment(cfg["instrument"], m, stream=stream)
+        extra = {}
+        if args.workload == "cylinder_surrogate":
+            sur = sas.sas_create_surrogate(W.surrogate_box(n_fourier=6), seed=1, stream=stream)
+            sas.sas_surrogate_generate(sur, 10_000_000, 1)
+            sas.sas_surrogate_train(sur, args.train_steps, 32768, 1e-3, args.train_steps)
+            sas.sas_attach_surrogate(e.h, sur)
+            flop = 2.0 * (64 * 256 + 3 * 256 * 256 + 256)
+            pk = _peaks()
+            peak, unit, bound = (pk.get("bf16_tflops_sustained") or 1703.0), "TFLOP/s", "tensor"
+            kernel = "sas::sur::sur_trace_kernel"
+        else:
+            flop = F.flops_per_history(m.kind, m.n_poly, m.n_gamma * m.n_psi)
+            peak, unit, bound = F.fp32_peak_tflops(info["sm_count"], 2070.0), "TFLOP/s", "alu"
+            kernel = "trace_kernel<float, CYLINDER, TALLY_GLOBAL>"
+        for _ in range(args.warmup):
+            e.trace(n, cfg["seed"])
+        ms = []
+        for _ in range(args.steps):
+            ms.append(_events_ms(lambda: e.trace(n, cfg["seed"]), stream))
+        t = sum(ms) / len(ms)
+        e.close()
+    rate = n / (t * 1e-3)
+    line = {"metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16" if bound == "tensor" else "f32", "data": "synthetic",
+            "config": {"workload": args.workload + ": " + "cylinder R=20 L=400 A, axis N(15 deg) about x, "
+                       "Schulz 0.1 x40, 76x76 orientation nodes, 256x256 detector", "neutrons_per_step": n},
+            "roofline": {"bound": bound, "achieved": flop * rate / 1e12, "peak": peak, "unit": unit,
+                         "frac": flop * rate / 1e12 / peak, "traffic": None, "kernel": kernel,
+                         "flops_per_history": flop}, "gpu_launches": args.steps}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -334,11 +381,17 @@ def main():
     ap.add_argument("--neutrons", type=float, default=None, help="histories per GPU per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true")
+    ap.add_argument("--workload", default="core_shell",
+                    choices=["core_shell", "cylinder", "cylinder_surrogate"],
+                    help="core_shell: the headline step; the others time one workload alone")
+    ap.add_argument("--train-steps", type=int, default=12000)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "core_shell":
+        return run_single_workload(args)
 
     import torch
     import torch.distributed as dist
