@@ -285,7 +285,7 @@ sas_status build_model_tables(const sas_model_desc& m, ModelTables& t)
         } else if (m.kind == SAS_CYLINDER) {
             const double V = pi * ri * ri * m.length;
             const double F0 = (m.sld - m.sld_solvent) * V;
-            p[0] = ri; p[1] = 1.0 / ri; p[2] = 1.0 / std::sqrt(ri); p[3] = w[i] * F0 * F0; p[4] = ri * ri;
+            p[0] = ri * ri; p[1] = w[i] * F0 * F0; p[2] = ri; p[3] = 1.0 / ri; p[4] = 1.0 / std::sqrt(ri);
             vmean += w[i] * V;
         } else {
             const double V = 4.0 / 3.0 * pi * m.radius_polar * ri * ri;

@@ -210,26 +210,40 @@ __device__ __forceinline__ T avg_cylinder(const T qv[3], const T* __restrict__ p
         const T qab = M<T>::sqrt_(qab2);
         T inner = 0;
         if constexpr (sizeof(T) == sizeof(float)) {
+            // nodes are sorted by radius: find (uniformly over the active
+            // lanes) how many need no large-x branch for any lane
+            const float qm = __uint_as_float(__reduce_max_sync(__activemask(), __float_as_uint(qab2)));
+            int lo = 0, hi = np;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (poly[8 * mid] * qm <= SAS_J1P_SMAX) lo = mid + 1;
+                else hi = mid;
+            }
 #pragma unroll 4
-            for (int i = 0; i < np; ++i) {
+            for (int i = 0; i < lo; ++i) {
+                const float2 rc = *reinterpret_cast<const float2*>(poly + 8 * i);   // (r^2, c)
+                const float a = sas_cyl_a_s(qab2 * rc.x);
+                inner = fma(rc.y, a * a, inner);
+            }
+            for (int i = lo; i < np; ++i) {
                 const T* p = poly + 8 * i;
-                const float sx = qab2 * p[4];
+                const float sx = qab2 * p[0];
                 float a;
                 if (sx <= SAS_J1P_SMAX) {
                     a = sas_cyl_a_s(sx);
                 } else {
-                    const float x = qab * p[0];
+                    const float x = qab * p[2];
                     a = sas_cyl_a_large(x, __frcp_rn(x), rsqrtf(x));
                 }
-                inner = fma(p[3], a * a, inner);
+                inner = fma(p[1], a * a, inner);
             }
         } else {
             const T iq = M<T>::rcp(qab);
 #pragma unroll 4
             for (int i = 0; i < np; ++i) {
                 const T* p = poly + 8 * i;
-                const T a = M<T>::cyl_a(qab * p[0], iq * p[1], 0);
-                inner = fma(p[3], a * a, inner);
+                const T a = M<T>::cyl_a(qab * p[2], iq * p[3], 0);
+                inner = fma(p[1], a * a, inner);
             }
         }
         k.add(c[3] * sn * sn * inner);

@@ -186,12 +186,15 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_bwd_kernel(const BwdParams P, 
         for (int ch = 0; ch < 4; ++ch) {
             const int col0 = 128 * h + 32 * ch;
             float v[32];
+            // all loads of the chunk first (they may not pass the stores below)
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const int col = col0 + j;
-                const float z = valid ? __bfloat162float(P.zt[3][(size_t)col * ld + i]) : 0.f;
-                v[j] = valid ? dout * w5[col] * dsilu(z) : 0.f;
-                if (valid) P.dzt[3][(size_t)col * ld + i] = __float2bfloat16_rn(v[j]);
+            for (int j = 0; j < 32; ++j)
+                v[j] = valid ? __bfloat162float(P.zt[3][(size_t)(col0 + j) * ld + i]) : 0.f;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] = valid ? dout * w5[col0 + j] * dsilu(v[j]) : 0.f;
+            if (valid) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) P.dzt[3][(size_t)(col0 + j) * ld + i] = __float2bfloat16_rn(v[j]);
             }
 #pragma unroll
             for (int q = 0; q < 4; ++q) st_row8(c.sm + SM_A, m, col0 + 8 * q, v + 8 * q);
@@ -204,14 +207,17 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_bwd_kernel(const BwdParams P, 
             else load_weights(c, &maps.wt[2], 4);   // next tile starts again at W4^T
             for (int ch = 0; ch < 4; ++ch) {
                 const int col0 = 128 * h + 32 * ch;
-                float v[32];
+                float z[32], v[32];
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    z[j] = valid ? __bfloat162float(P.zt[l - 1][(size_t)(col0 + j) * ld + i]) : 0.f;
                 tc::tmem_ld32(tmem_addr(c, col0), v);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int col = col0 + j;
-                    const float z = valid ? __bfloat162float(P.zt[l - 1][(size_t)col * ld + i]) : 0.f;
-                    v[j] = valid ? v[j] * dsilu(z) : 0.f;
-                    if (valid) P.dzt[l - 1][(size_t)col * ld + i] = __float2bfloat16_rn(v[j]);
+                for (int j = 0; j < 32; ++j) v[j] = valid ? v[j] * dsilu(z[j]) : 0.f;
+                if (valid) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        P.dzt[l - 1][(size_t)(col0 + j) * ld + i] = __float2bfloat16_rn(v[j]);
                 }
                 if (l > 1) {
 #pragma unroll
