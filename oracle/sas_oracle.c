@@ -38,6 +38,12 @@
 
 #define PI 3.14159265358979323846
 
+/* Planted mistakes for the pin tests' mutation check (tests/test_mutations.py):
+ * the default build compiles none of them (SAS_MUT = 0). */
+#ifndef SAS_MUT
+#define SAS_MUT 0
+#endif
+
 /* ---------------------------------------------------------------- Philox */
 
 void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
@@ -46,7 +52,7 @@ void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t
     uint32_t k0 = key[0], k1 = key[1];
     for (int round = 0; round < 10; ++round) {
         uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
-        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint64_t p1 = (uint64_t)(SAS_MUT == 10 ? 0xCD9E8D55u : 0xCD9E8D57u) * (uint64_t)c2;
         uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
         uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
         uint32_t n0 = hi1 ^ c1 ^ k0;
@@ -99,6 +105,7 @@ double oracle_sphere_f(double x)
         return 1.0 - t / 10.0 * (1.0 - t / 28.0 * (1.0 - t / 54.0 * (1.0 - t / 88.0
                                                         * (1.0 - t / 130.0))));
     }
+    if (SAS_MUT == 2) return 3.0 * (sin(x) - cos(x)) / (x * x * x);
     return 3.0 * (sin(x) - x * cos(x)) / (x * x * x);
 }
 
@@ -154,7 +161,7 @@ double oracle_sq_py(double q, double radius, double phi)
     double A = 2.0 * fabs(q) * radius;
     double d = pow(1.0 - phi, 4);
     double alpha = (1.0 + 2.0 * phi) * (1.0 + 2.0 * phi) / d;
-    double beta = -6.0 * phi * (1.0 + 0.5 * phi) * (1.0 + 0.5 * phi) / d;
+    double beta = (SAS_MUT == 3 ? 6.0 : -6.0) * phi * (1.0 + 0.5 * phi) * (1.0 + 0.5 * phi) / d;
     double gamma = 0.5 * phi * alpha;
     double GA; /* G(A)/A */
     if (A < 0.5) {
@@ -200,7 +207,7 @@ double oracle_dsigma(const oracle_model *m, const double q[3])
             double rc = m->poly_r[i], ro = rc + m->thickness;
             double Vc = sphere_volume(rc), Vo = sphere_volume(ro);
             double F = (m->sld - m->sld_shell) * Vc * oracle_sphere_f(qq * rc)
-                     + (m->sld_shell - m->sld_solvent) * Vo * oracle_sphere_f(qq * ro);
+                     + (m->sld_shell - m->sld_solvent) * (SAS_MUT == 11 ? Vc : Vo) * oracle_sphere_f(qq * ro);
             sum += m->poly_w[i] * F * F;
             vmean += m->poly_w[i] * Vo;
         }
@@ -215,12 +222,12 @@ double oracle_dsigma(const oracle_model *m, const double q[3])
             double x1 = q[2] * c[0] - q[0] * c[2];
             double x2 = q[0] * c[1] - q[1] * c[0];
             double qab = sqrt(x0 * x0 + x1 * x1 + x2 * x2);
-            double s = oracle_sinc(0.5 * qc * m->length);
+            double s = oracle_sinc(0.5 * (SAS_MUT == 4 ? qab : qc) * m->length);
             double inner = 0.0;
             for (int64_t i = 0; i < np; ++i) {
                 double r = m->poly_r[i];
                 double V = PI * r * r * m->length;
-                double F = drho * V * s * oracle_cyl_a(qab * r);
+                double F = drho * V * s * oracle_cyl_a((SAS_MUT == 4 ? qc : qab) * r);
                 inner += m->poly_w[i] * F * F;
             }
             sum += m->orient_w[o] * inner;
@@ -266,6 +273,7 @@ void oracle_dsigma_many(const oracle_model *m, const double *q, int64_t n, doubl
 double oracle_sample_lambda(double lambda0, double drel, double u)
 {
     double T = (u < 0.5) ? sqrt(2.0 * u) - 1.0 : 1.0 - sqrt(2.0 * (1.0 - u));
+    if (SAS_MUT == 1) T = 2.0 * u - 1.0;
     return lambda0 * (1.0 + drel * T);
 }
 
@@ -347,8 +355,9 @@ int oracle_history(const oracle_instrument *in, const oracle_model *m, uint64_t 
     double e_in, e_out, l_out = 0.0;
     if (slab(in, ps, k_out, &e_in, &e_out)) l_out = e_out - e_in;
     double att = exp(-in->mu * (s + l_out));
+    if (SAS_MUT == 8) domega = area * k_out[2] / rr;
     *w = l * ds * domega * att;
-    *pixel = iy * in->nx + ix;
+    *pixel = iy * in->nx + ix + (SAS_MUT == 7 && ix + 1 < in->nx ? 1 : 0);
     return 1;
 }
 

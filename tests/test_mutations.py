@@ -1,0 +1,39 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each case builds a copy of the oracle with one planted mistake
+(SAS_ORACLE_MUTATION=k; the default build has none) and runs the pin tests
+in a subprocess: at least one pin must fail. The mistakes are the kinds the
+pins exist to catch: a wrong sampling law, a dropped or transposed term, a
+sign error, an index error, a wrong constant.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+MUTATIONS = {
+    1: ("uniform instead of triangular wavelength spread", "triangular or finite_beam"),
+    2: ("sphere amplitude sin x - cos x (dropped factor x)", "sphere"),
+    3: ("Percus-Yevick beta with the wrong sign", "percus"),
+    4: ("Eq. 8 as printed: sinc on Q_AB, J1 on Q_C", "cylinder"),
+    5: ("orientation weights without sin(gamma)", "orientation or isotropic"),
+    6: ("Schulz nodes scaled by z instead of z + 1", "schulz or polydisperse"),
+    7: ("detector pixel index off by one", "ideal_beam or finite_beam"),
+    8: ("solid angle with 1/r instead of 1/r^2", "ideal_beam or finite_beam"),
+    10: ("Philox multiplier typo", "philox"),
+    11: ("core-shell outer term with the core volume", "core_shell"),
+}
+
+
+@pytest.mark.parametrize("k", sorted(MUTATIONS))
+def test_pins_catch_planted_mistake(k):
+    desc, sel = MUTATIONS[k]
+    env = dict(os.environ, SAS_ORACLE_MUTATION=str(k))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py"), "-k", sel],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+    assert r.returncode == 1, f"mutation {k} ({desc}) was not caught:\n{r.stdout[-2000:]}"
+    assert "failed" in r.stdout
