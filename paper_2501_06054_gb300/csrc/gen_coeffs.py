@@ -14,6 +14,9 @@ Run once (python gen_coeffs.py > sas_coeffs.h); the output is committed.
   first two zeros j1, j2 of J1 (scipy) and h a degree-8 polynomial in x^2
   fitted like the above (relative error ~1e-8); no square root, no branch
   for the cylinder workloads' arguments, and the zeros are exact factors.
+* the same with the first three zeros for x <= 12 (degree 10 in the centred
+  variable 2 x^2/144 - 1), used for the tail nodes of broad size
+  distributions.
 * x >= X1: the modulus-phase form of J1 (J1 = M cos(theta), Y1 = M sin(theta)),
   with m(u) = M sqrt(pi x / 2) and h(u) = x (theta - x + 3 pi / 4) fitted as
   polynomials in u = (X1 / x)^2; M and theta are computed from scipy's J1, Y1.
@@ -110,19 +113,37 @@ def fit_trig():
     return cS, eS, cC, eC
 
 
-def fit_product(deg=8, X=8.0):
-    n = 6000
+def fit_product_centered(deg=10, X=12.0, nz=3):
+    """As fit_product, in the centred variable v = 2 x^2 / X^2 - 1 (smaller
+    coefficients, stable FP32 Horner evaluation)."""
+    n = 8000
     s = 0.5 * X * X * (1 - np.cos(np.pi * (np.arange(n) + 0.5) / n))
     x = np.sqrt(s)
-    j = sp.jn_zeros(1, 2)
+    j = sp.jn_zeros(1, nz)
     a = np.where(x > 0, 2 * sp.j1(np.maximum(x, 1e-300)) / np.maximum(x, 1e-300), 1.0)
-    p = (1 - s / j[0] ** 2) * (1 - s / j[1] ** 2)
+    p = np.prod([(1 - s / j[k] ** 2) for k in range(nz)], axis=0)
+    ok = np.abs(p) > 1e-6
+    v = 2 * s / (X * X) - 1
+    basis = [lambda vv, k=k: vv ** k for k in range(deg + 1)]
+    c, e = lawson_fit(v[ok], (a / p)[ok], basis)
+    return list(c), e, [1.0 / jj ** 2 for jj in j], X * X
+
+
+def fit_product(deg=8, X=8.0, nz=2):
+    n = 8000
+    s = 0.5 * X * X * (1 - np.cos(np.pi * (np.arange(n) + 0.5) / n))
+    x = np.sqrt(s)
+    j = sp.jn_zeros(1, nz)
+    a = np.where(x > 0, 2 * sp.j1(np.maximum(x, 1e-300)) / np.maximum(x, 1e-300), 1.0)
+    p = np.prod([(1 - s / j[k] ** 2) for k in range(nz)], axis=0)
     ok = np.abs(p) > 1e-6
     u = s / (X * X)
     basis = [lambda uu, k=k: uu ** k for k in range(deg + 1)]
     c, e = lawson_fit(u[ok], (a / p)[ok], basis)
     cs = [ci / (X * X) ** k for k, ci in enumerate(c)]   # coefficients in s = x^2
-    return cs, e, 1.0 / j[0] ** 2, 1.0 / j[1] ** 2, X * X
+    if nz == 2:
+        return cs, e, 1.0 / j[0] ** 2, 1.0 / j[1] ** 2, X * X
+    return cs, e, [1.0 / jj ** 2 for jj in j], X * X
 
 
 def split2(c):
@@ -136,6 +157,7 @@ def main():
     cm, em, ch, eh = fit_large(5, 5)
     cS, eS, cC, eC = fit_trig()
     cP, eP, iz1, iz2, smax = fit_product()
+    cQ, eQ, izq, smaxq = fit_product_centered(deg=10, X=12.0, nz=3)
     p2 = split2(math.pi / 2)
     p4 = split2(math.pi / 4)
     w = out.write
@@ -151,6 +173,11 @@ def main():
     w("#define SAS_J1P_SMAX %.9ef\n#define SAS_J1P_Z1 %.9ef\n#define SAS_J1P_Z2 %.9ef\n" % (smax, iz1, iz2))
     w(f"#define SAS_J1P_C_N {len(cP)}\n")
     w("#define SAS_J1P_C {" + ", ".join("%.9ef" % v for v in cP) + "}\n")
+    w(f"/* 2 J1(x)/x = (1 - s z1)(1 - s z2)(1 - s z3) g(2 s / {smaxq:g} - 1), s <= {smaxq:g}; fit error of g {eQ:.3e} */\n")
+    w("#define SAS_J1Q_SMAX %.9ef\n#define SAS_J1Q_Z1 %.9ef\n#define SAS_J1Q_Z2 %.9ef\n#define SAS_J1Q_Z3 %.9ef\n"
+      % (smaxq, izq[0], izq[1], izq[2]))
+    w(f"#define SAS_J1Q_C_N {len(cQ)}\n")
+    w("#define SAS_J1Q_C {" + ", ".join("%.9ef" % v for v in cQ) + "}\n")
     w("/* sin r = r + r^3 S(r^2), cos r = 1 + r^2 C(r^2) */\n")
     for name, arr in (("SAS_SIN_C", list(cS)), ("SAS_COS_C", list(cC)), ("SAS_J1S_C", list(cs)),
                       ("SAS_J1M_C", list(cm)), ("SAS_J1H_C", list(ch))):

@@ -13,7 +13,14 @@
 #define SAS_J1P_Z1 6.811074783e-02f
 #define SAS_J1P_Z2 2.031758155e-02f
 #define SAS_J1P_C_N 9
-#define SAS_J1P_C {9.999999993e-01f, -3.657166892e-02f, 5.905152050e-04f, -5.678942625e-06f, 3.695457932e-08f, -1.747459128e-10f, 6.223534431e-13f, -1.621063729e-15f, 2.424090897e-18f}
+#define SAS_J1P_C {9.999999993e-01f, -3.657166892e-02f, 5.905152050e-04f, -5.678942625e-06f, 3.695457932e-08f, -1.747459127e-10f, 6.223534422e-13f, -1.621063721e-15f, 2.424090863e-18f}
+/* 2 J1(x)/x = (1 - s z1)(1 - s z2)(1 - s z3) g(2 s / 144 - 1), s <= 144; fit error of g 2.165e-10 */
+#define SAS_J1Q_SMAX 1.440000000e+02f
+#define SAS_J1Q_Z1 6.811074783e-02f
+#define SAS_J1Q_Z2 2.031758155e-02f
+#define SAS_J1Q_Z3 9.661886729e-03f
+#define SAS_J1Q_C_N 11
+#define SAS_J1Q_C {1.169814826e-01f, -2.826843847e-01f, 2.994814183e-01f, -1.884617908e-01f, 8.024855756e-02f, -2.491085858e-02f, 5.920458534e-03f, -1.115097382e-03f, 1.711073644e-04f, -2.243371898e-05f, 2.410184778e-06f}
 /* sin r = r + r^3 S(r^2), cos r = 1 + r^2 C(r^2) */
 #define SAS_SIN_C_N 3
 #define SAS_SIN_C {-1.666666455e-01f, 8.332725399e-03f, -1.958295501e-04f}

@@ -213,10 +213,17 @@ __device__ __forceinline__ T avg_cylinder(const T qv[3], const T* __restrict__ p
             // nodes are sorted by radius: find (uniformly over the active
             // lanes) how many need no large-x branch for any lane
             const float qm = __uint_as_float(__reduce_max_sync(__activemask(), __float_as_uint(qab2)));
-            int lo = 0, hi = np;
+            int lo = 0, hi = np;       // nodes [0, lo): x <= 8 in every active lane
             while (lo < hi) {
                 const int mid = (lo + hi) >> 1;
                 if (poly[8 * mid] * qm <= SAS_J1P_SMAX) lo = mid + 1;
+                else hi = mid;
+            }
+            int lo2 = lo;              // nodes [lo, lo2): x <= 12
+            hi = np;
+            while (lo2 < hi) {
+                const int mid = (lo2 + hi) >> 1;
+                if (poly[8 * mid] * qm <= SAS_J1Q_SMAX) lo2 = mid + 1;
                 else hi = mid;
             }
 #pragma unroll 4
@@ -225,12 +232,18 @@ __device__ __forceinline__ T avg_cylinder(const T qv[3], const T* __restrict__ p
                 const float a = sas_cyl_a_s(qab2 * rc.x);
                 inner = fma(rc.y, a * a, inner);
             }
-            for (int i = lo; i < np; ++i) {
+#pragma unroll 2
+            for (int i = lo; i < lo2; ++i) {
+                const float2 rc = *reinterpret_cast<const float2*>(poly + 8 * i);
+                const float a = sas_cyl_a_s3(qab2 * rc.x);
+                inner = fma(rc.y, a * a, inner);
+            }
+            for (int i = lo2; i < np; ++i) {
                 const T* p = poly + 8 * i;
                 const float sx = qab2 * p[0];
                 float a;
-                if (sx <= SAS_J1P_SMAX) {
-                    a = sas_cyl_a_s(sx);
+                if (sx <= SAS_J1Q_SMAX) {
+                    a = sas_cyl_a_s3(sx);
                 } else {
                     const float x = qab * p[2];
                     a = sas_cyl_a_large(x, __frcp_rn(x), rsqrtf(x));
@@ -321,7 +334,7 @@ __device__ __forceinline__ bool slab(const InstConst<T>& in, const T o[3], const
         if (d[k] == (T)0) {
             ok = ok && (o[k] >= lo[k]) && (o[k] <= hi[k]);
         } else {
-            const T id = (T)1 / d[k];
+            const T id = M<T>::rcp(d[k]);
             T t1 = (lo[k] - o[k]) * id, t2 = (hi[k] - o[k]) * id;
             const T mn = fmin(t1, t2), mx = fmax(t1, t2);
             a = fmax(a, mn);
@@ -381,12 +394,12 @@ __device__ __forceinline__ History<T> history(const InstConst<T>& in, uint64_t s
     const T ko[3] = {v[0] * ir, v[1] * ir, v[2] * ir};
     const T domega = in.area * ko[2] * ir * ir;
     // Q = k (k_out - k_in); the z difference without cancellation
-    const T k = in.two_pi / lambda;
+    const T k = in.two_pi * M<T>::rcp(lambda);
     const T tin = fma(ki[0], ki[0], ki[1] * ki[1]);
     const T tout = fma(ko[0], ko[0], ko[1] * ko[1]);
     h.q[0] = k * (ko[0] - ki[0]);
     h.q[1] = k * (ko[1] - ki[1]);
-    h.q[2] = k * (tin - tout) / (ko[2] + ki[2]);
+    h.q[2] = k * (tin - tout) * M<T>::rcp(ko[2] + ki[2]);
     T att = (T)1;
     if (in.mu > (T)0) {
         T e_in, e_out, l_out = (T)0;

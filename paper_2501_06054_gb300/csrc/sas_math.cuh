@@ -141,23 +141,25 @@ SAS_HD float sas_sphere_f(float x, float inv) { return 3.0f * sas_sphere_g(x, in
 SAS_HD void sas_sphere_g2(float x1, float inv1, float x2, float inv2, float st, float ct, float& g1,
                           float& g2)
 {
+    // The quadrant sign (-1)^(k >> 1) is the same for both radii (x2 shares
+    // the quadrant of x1; when x1 < pi/4 it is +1), and callers square the
+    // combination a g1 + b g2, so it is left out: g1 and g2 are returned up
+    // to one common sign.
     const SasTrig g = sas_reduce_pio2(x1);
     const float sr = fmaf(g.r * g.t, g.S, g.r);
     const float cr = fmaf(g.t, g.C, 1.0f);
-    const int flip = g.kb << 30;
+    const bool odd = (g.kb & 1) != 0;
     // inner radius
     const float A1 = fmaf(-x1, cr, sr);
     const float B1 = fmaf(x1, sr, cr);
-    float num1 = (g.kb & 1) ? B1 : A1;
-    num1 = sas_flip_sign(num1, flip);
+    const float num1 = odd ? B1 : A1;
     g1 = (x1 < 0.78539816f) ? (g.S - g.C) : num1 * inv1 * inv1 * inv1;
     // outer radius: sin, cos of (r + q t)
     const float sr2 = fmaf(sr, ct, cr * st);
     const float cr2 = fmaf(cr, ct, -sr * st);
     const float A2 = fmaf(-x2, cr2, sr2);
     const float B2 = fmaf(x2, sr2, cr2);
-    float num2 = (g.kb & 1) ? B2 : A2;
-    num2 = sas_flip_sign(num2, flip);
+    const float num2 = odd ? B2 : A2;
     // g(x) = 1/3 - x^2/30 + x^4/840 - x^6/45360 + x^8/3991680 - ...
     const float c[5] = {3.333333333e-01f, -3.333333333e-02f, 1.190476190e-03f, -2.204585538e-05f,
                         2.505210839e-07f};
@@ -208,6 +210,17 @@ SAS_HD float sas_cyl_a_s(float s)
     const float p1 = fmaf(-s, SAS_J1P_Z1, 1.0f);
     const float p2 = fmaf(-s, SAS_J1P_Z2, 1.0f);
     return p1 * p2 * h;
+}
+
+// a(x) for s = x^2 <= SAS_J1Q_SMAX (x <= 12): three zero factors and a fit.
+SAS_HD float sas_cyl_a_s3(float s)
+{
+    const float c[11] = SAS_J1Q_C;
+    const float g = sas_horner(c, fmaf(s, 2.0f / SAS_J1Q_SMAX, -1.0f));
+    const float p1 = fmaf(-s, SAS_J1Q_Z1, 1.0f);
+    const float p2 = fmaf(-s, SAS_J1Q_Z2, 1.0f);
+    const float p3 = fmaf(-s, SAS_J1Q_Z3, 1.0f);
+    return (p1 * p2) * (p3 * g);
 }
 
 SAS_HD float sas_cyl_a(float x, float inv, float rsx)
