@@ -161,7 +161,7 @@ def secondary(stream, info):
     # --- cylinder workload: exact vs surrogate on the same histories
     cfg = W.cylinder_config()
     m = cfg["model"]
-    n_ex = 2_000_000
+    n_ex = 4_000_000
     e = sas.Experiment(cfg["instrument"], m, stream=stream)
     e.trace(50_000, 1)
     ms = _events_ms(lambda: e.trace(n_ex, 1), stream)
@@ -171,9 +171,9 @@ def secondary(stream, info):
     box = W.surrogate_box(n_fourier=6)
     t0 = time.perf_counter()
     sur = sas.sas_create_surrogate(box, seed=1, stream=stream)
-    n_train, steps, batch = 10_000_000, 12_000, 32768
+    n_train, steps, batch, lr = 50_000_000, 40_000, 65536, 2e-3
     gen_ms = _events_ms(lambda: sas.sas_surrogate_generate(sur, n_train, 1), stream)
-    train_ms = _events_ms(lambda: sas.sas_surrogate_train(sur, steps, batch, 1e-3, steps), stream)
+    train_ms = _events_ms(lambda: sas.sas_surrogate_train(sur, steps, batch, lr, steps), stream)
     sas.sas_attach_surrogate(e.h, sur)
     e.trace(n_ex, 1)
     d_su = e.read()
@@ -209,7 +209,7 @@ def secondary(stream, info):
                                           "total_weight": float(abs(ss.sum() / so.sum() - 1)),
                                           "compared_on": f"{n_ex} identical histories, bins >= 1e-3 max"},
                       "training": {"samples": n_train, "generate_s": gen_ms * 1e-3, "steps": steps,
-                                   "batch": batch, "train_s": train_ms * 1e-3,
+                                   "batch": batch, "lr": lr, "train_s": train_ms * 1e-3,
                                    "train_tflops_nominal": 3 * mlp_flop * steps * batch / (train_ms * 1e-3) / 1e12},
                       "fallbacks": sas.sas_surrogate_fallbacks(exp=e.h)}}
     e.close()
@@ -300,8 +300,8 @@ def run_single_workload(args):
         extra = {}
         if args.workload == "cylinder_surrogate":
             sur = sas.sas_create_surrogate(W.surrogate_box(n_fourier=6), seed=1, stream=stream)
-            sas.sas_surrogate_generate(sur, 10_000_000, 1)
-            sas.sas_surrogate_train(sur, args.train_steps, 32768, 1e-3, args.train_steps)
+            sas.sas_surrogate_generate(sur, 50_000_000, 1)
+            sas.sas_surrogate_train(sur, args.train_steps, 65536, 2e-3, args.train_steps)
             sas.sas_attach_surrogate(e.h, sur)
             flop = 2.0 * (64 * 256 + 3 * 256 * 256 + 256)
             pk = _peaks()
@@ -384,7 +384,7 @@ def main():
     ap.add_argument("--workload", default="core_shell",
                     choices=["core_shell", "cylinder", "cylinder_surrogate"],
                     help="core_shell: the headline step; the others time one workload alone")
-    ap.add_argument("--train-steps", type=int, default=12000)
+    ap.add_argument("--train-steps", type=int, default=40000)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
