@@ -106,6 +106,9 @@ def lib():
             L.oracle_records.argtypes = [ctypes.POINTER(_Instrument), ctypes.POINTER(_Model),
                                          ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64,
                                          ctypes.c_uint64, ctypes.POINTER(ctypes.c_int64), _DP]
+            L.oracle_geometry_records.argtypes = [ctypes.POINTER(_Instrument), ctypes.c_uint64,
+                                                  ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64,
+                                                  ctypes.POINTER(ctypes.c_int64), _DP, _DP, _DP]
             L.oracle_num_threads.restype = ctypes.c_int
             L.oracle_sample_lambda.argtypes = [ctypes.c_double] * 3
             L.oracle_sample_lambda.restype = ctypes.c_double
@@ -287,6 +290,21 @@ def records(instrument, model, n, seed, first=0, exp_id=0):
                          int(first), int(n), pix.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                          w.ctypes.data_as(_DP))
     return pix, w
+
+
+def geometry_records(instrument, n, seed, first=0, exp_id=0):
+    """Per-neutron geometry: pixel (-1 on a miss), Q [n][3] (1/angstrom), the
+    prefactor with weight = prefactor * dSigma/dOmega(Q) (dSigma/dOmega in
+    1/angstrom), and the transmitted weight."""
+    inst = _inst(instrument)
+    pix = np.empty(n, dtype=np.int64)
+    q = np.empty((n, 3), dtype=np.float64)
+    pref = np.empty(n, dtype=np.float64)
+    wt = np.empty(n, dtype=np.float64)
+    lib().oracle_geometry_records(ctypes.byref(inst), int(seed), int(exp_id), int(first), int(n),
+                                  pix.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                  q.ctypes.data_as(_DP), pref.ctypes.data_as(_DP), wt.ctypes.data_as(_DP))
+    return dict(pixel=pix, q=q, pref=pref, trans=wt)
 
 
 def sample_lambda(lambda0, drel, u):

@@ -301,11 +301,13 @@ static int slab(const oracle_instrument *in, const double o[3], const double d[3
     return 1;
 }
 
-/* One neutron history. Returns 1 if it scattered onto the detector, with
- * its pixel and weight; *w_trans gets the unscattered (transmitted) weight. */
-int oracle_history(const oracle_instrument *in, const oracle_model *m, uint64_t seed,
-                   uint32_t exp_id, uint64_t index, int64_t *pixel, double *w,
-                   double *w_trans)
+/* Geometry of one neutron history (everything but the cross section).
+ * Returns 1 if it scattered onto the detector, with its pixel, the path
+ * length l in the sample, the solid-angle factor, the attenuation and Q;
+ * *w_trans gets the unscattered (transmitted) weight. */
+static int history_geometry(const oracle_instrument *in, uint64_t seed, uint32_t exp_id,
+                            uint64_t index, int64_t *pixel, double *l_path, double *d_omega,
+                            double *atten, double q_out[3], double *w_trans)
 {
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
     uint32_t c0[4] = {0u, exp_id, (uint32_t)index, (uint32_t)(index >> 32)};
@@ -349,16 +351,56 @@ int oracle_history(const oracle_instrument *in, const oracle_model *m, uint64_t 
     double domega = area * k_out[2] / (rr * rr);
     /* scattering vector Q = k_f - k_i in 1/angstrom */
     double k = 2.0 * PI / lambda;
-    double q[3] = {k * (k_out[0] - k_in[0]), k * (k_out[1] - k_in[1]), k * (k_out[2] - k_in[2])};
-    double ds = oracle_dsigma(m, q) * 1e10; /* 1/angstrom -> 1/m */
+    q_out[0] = k * (k_out[0] - k_in[0]);
+    q_out[1] = k * (k_out[1] - k_in[1]);
+    q_out[2] = k * (k_out[2] - k_in[2]);
     /* path to the exit of the sample along the scattered direction */
     double e_in, e_out, l_out = 0.0;
     if (slab(in, ps, k_out, &e_in, &e_out)) l_out = e_out - e_in;
-    double att = exp(-in->mu * (s + l_out));
+    *atten = exp(-in->mu * (s + l_out));
     if (SAS_MUT == 8) domega = area * k_out[2] / rr;
-    *w = l * ds * domega * att;
+    *l_path = l;
+    *d_omega = domega;
     *pixel = iy * in->nx + ix + (SAS_MUT == 7 && ix + 1 < in->nx ? 1 : 0);
     return 1;
+}
+
+/* One neutron history. Returns 1 if it scattered onto the detector, with
+ * its pixel and weight l dSigma/dOmega(Q) dOmega att; *w_trans gets the
+ * unscattered (transmitted) weight. */
+int oracle_history(const oracle_instrument *in, const oracle_model *m, uint64_t seed,
+                   uint32_t exp_id, uint64_t index, int64_t *pixel, double *w,
+                   double *w_trans)
+{
+    double l, domega, att, q[3];
+    if (!history_geometry(in, seed, exp_id, index, pixel, &l, &domega, &att, q, w_trans)) return 0;
+    double ds = oracle_dsigma(m, q) * 1e10; /* 1/angstrom -> 1/m */
+    *w = l * ds * domega * att;
+    return 1;
+}
+
+/* Per-neutron geometry records: pixel (-1 on a miss), Q [n][3], the
+ * prefactor l dOmega att (1/m per 1/angstrom of cross section, so that the
+ * weight is prefactor * dSigma/dOmega(Q) with dSigma/dOmega in 1/angstrom)
+ * and the transmitted weight. Lets a test weight the histories with a cross
+ * section of its own. */
+void oracle_geometry_records(const oracle_instrument *in, uint64_t seed, uint32_t exp_id,
+                             uint64_t first, uint64_t n, int64_t *pixel, double *q,
+                             double *pref, double *w_trans)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t j = 0; j < (int64_t)n; ++j) {
+        int64_t pix; double l, domega, att;
+        if (history_geometry(in, seed, exp_id, first + (uint64_t)j, &pix, &l, &domega, &att,
+                             q + 3 * j, w_trans + j)) {
+            pixel[j] = pix;
+            pref[j] = l * 1e10 * domega * att;
+        } else {
+            pixel[j] = -1;
+            pref[j] = 0.0;
+            q[3 * j] = q[3 * j + 1] = q[3 * j + 2] = 0.0;
+        }
+    }
 }
 
 /* Trace neutrons [first, first+n) and accumulate the detector in place.

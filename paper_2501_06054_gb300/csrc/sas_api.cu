@@ -458,8 +458,8 @@ struct sas_experiment {
     // learned surrogate (cylinders in its training box)
     const sas_surrogate* sur = nullptr;
     WorkItem* d_items = nullptr;
+    uint32_t* d_prefix = nullptr;      // 256-history pairs before each item
     size_t items_cap = 0;
-    unsigned int* d_queue = nullptr;
     uint64_t* d_seed = nullptr;
     sur::SurExp* d_sexp = nullptr;
     BatchExp* d_bexp = nullptr;
@@ -623,7 +623,6 @@ sas_status upload_surrogate_exp(sas_experiment* e)
     if (!e->d_sexp) {
         SAS_CUDA(cudaMalloc(&e->d_sexp, sizeof(sur::SurExp)), "alloc");
         SAS_CUDA(cudaMalloc(&e->d_bexp, sizeof(BatchExp)), "alloc");
-        SAS_CUDA(cudaMalloc(&e->d_queue, sizeof(unsigned int)), "alloc");
         SAS_CUDA(cudaMalloc(&e->d_seed, sizeof(uint64_t)), "alloc");
         SAS_CUDA(cudaMalloc(&e->d_fallbacks, sizeof(unsigned long long)), "alloc");
         SAS_CUDA(cudaMemset(e->d_fallbacks, 0, sizeof(unsigned long long)), "memset");
@@ -638,7 +637,8 @@ sas_status upload_surrogate_exp(sas_experiment* e)
 }
 
 // Cylinder trace through the tensor-core surrogate: items of 2^16
-// histories pulled by a persistent grid (one CTA per SM).
+// histories, cut into 256-history pairs that a grid of one CTA per SM takes
+// round-robin.
 sas_status trace_surrogate(sas_experiment* e, uint64_t first, uint64_t n, uint64_t seed)
 {
     const uint64_t chunk = 1ull << 16;
@@ -650,18 +650,25 @@ sas_status trace_surrogate(sas_experiment* e, uint64_t first, uint64_t n, uint64
         w.n = (uint32_t)std::min<uint64_t>(chunk, n - f);
         items.push_back(w);
     }
-    if (items.size() > 0xFFFFFFF0ull) return fail(SAS_ERR_ARG, "too many histories for one surrogate trace");
+    std::vector<uint32_t> prefix;
+    const uint64_t n_pairs = surrogate_pair_prefix(items, prefix);
+    if (n_pairs > 0xFFFFFFFFull) return fail(SAS_ERR_ARG, "too many histories for one surrogate trace");
     if (items.size() > e->items_cap) {
         SAS_CUDA(cudaStreamSynchronize(e->stream), "sync");
         cudaFree(e->d_items);
+        cudaFree(e->d_prefix);
         e->d_items = nullptr;
+        e->d_prefix = nullptr;
+        e->items_cap = 0;
         SAS_CUDA(cudaMalloc(&e->d_items, items.size() * sizeof(WorkItem)), "alloc items");
+        SAS_CUDA(cudaMalloc(&e->d_prefix, items.size() * sizeof(uint32_t)), "alloc items");
         e->items_cap = items.size();
     }
     SAS_CUDA(cudaMemcpyAsync(e->d_items, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice,
                              e->stream), "upload items");
+    SAS_CUDA(cudaMemcpyAsync(e->d_prefix, prefix.data(), prefix.size() * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                             e->stream), "upload items");
     SAS_CUDA(cudaMemcpyAsync(e->d_seed, &seed, sizeof(seed), cudaMemcpyHostToDevice, e->stream), "upload seed");
-    SAS_CUDA(cudaMemsetAsync(e->d_queue, 0, sizeof(unsigned int), e->stream), "memset");
     sur::STParams P;
     std::memset(&P, 0, sizeof(P));
     P.in = e->icf;
@@ -670,8 +677,9 @@ sas_status trace_surrogate(sas_experiment* e, uint64_t first, uint64_t n, uint64
     P.seed = e->d_seed;
     P.philox_base = e->exp_id;
     P.items = e->d_items;
+    P.pair_prefix = e->d_prefix;
     P.n_items = (uint32_t)items.size();
-    P.queue = e->d_queue;
+    P.n_pairs = (uint32_t)n_pairs;
     P.sexp = e->d_sexp;
     P.bexp = e->d_bexp;
     P.poly = (const float*)e->d_poly;
@@ -683,8 +691,7 @@ sas_status trace_surrogate(sas_experiment* e, uint64_t first, uint64_t n, uint64
     P.npix = (int)(e->inst.nx * e->inst.ny);
     P.fallbacks = e->d_fallbacks;
     P.err = surrogate_err(e->sur);
-    const int grid = (int)std::min<uint64_t>((uint64_t)e->sm_count, items.size());
-    SAS_CUDA(launch_sur_trace(e->sur, P, grid, e->stream), "surrogate trace launch");
+    SAS_CUDA(launch_sur_trace(e->sur, P, e->sm_count, e->stream), "surrogate trace launch");
     return SAS_OK;
 }
 
@@ -952,6 +959,7 @@ sas_status sas_read_detector(const sas_experiment* e, double* sum_w, double* sum
     if (count) SAS_CUDA(cudaMemcpyAsync(count, e->d_count, npix * 8, cudaMemcpyDeviceToHost, e->stream), "read count");
     if (transmitted) SAS_CUDA(cudaMemcpyAsync(transmitted, e->d_trans, 8, cudaMemcpyDeviceToHost, e->stream), "read trans");
     SAS_CUDA(cudaStreamSynchronize(e->stream), "cudaStreamSynchronize");
+    if (e->sur) return surrogate_take_error(e->sur, e->stream);
     return SAS_OK;
 }
 
@@ -1023,7 +1031,7 @@ sas_status sas_destroy_experiment(sas_experiment* e)
     cudaFree(e->d_poly);
     cudaFree(e->d_orient);
     cudaFree(e->d_items);
-    cudaFree(e->d_queue);
+    cudaFree(e->d_prefix);
     cudaFree(e->d_seed);
     cudaFree(e->d_sexp);
     cudaFree(e->d_bexp);

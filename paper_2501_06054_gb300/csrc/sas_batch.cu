@@ -67,9 +67,10 @@ struct sas_batch {
     const sas_surrogate* sur = nullptr;
     std::vector<int> use_sur;
     WorkItem* d_sur_items = nullptr;
+    uint32_t* d_sur_prefix = nullptr;  // 256-history pairs before each surrogate item
     size_t sur_cap = 0;
     uint32_t n_sur_items = 0;
-    unsigned int* d_sur_queue = nullptr;
+    uint32_t n_sur_pairs = 0;
     sur::SurExp* d_sexp = nullptr;
     unsigned long long* d_fallbacks = nullptr;
 };
@@ -134,16 +135,28 @@ sas_status build_items(sas_batch* b)
     if (!sorted.empty())
         SAS_CUDA_B(cudaMemcpy(b->d_items, sorted.data(), sorted.size() * sizeof(WorkItem), cudaMemcpyHostToDevice),
                    "upload items");
+    std::vector<uint32_t> sprefix;
+    const uint64_t n_pairs = surrogate_pair_prefix(sitems, sprefix);
+    if (n_pairs > 0xFFFFFFFFull) return set_error(SAS_ERR_ARG, "too many surrogate histories");
     if (sitems.size() > b->sur_cap) {
         cudaFree(b->d_sur_items);
+        cudaFree(b->d_sur_prefix);
         b->d_sur_items = nullptr;
+        b->d_sur_prefix = nullptr;
+        b->sur_cap = 0;
         SAS_CUDA_B(cudaMalloc(&b->d_sur_items, sitems.size() * sizeof(WorkItem)), "cudaMalloc(items)");
+        SAS_CUDA_B(cudaMalloc(&b->d_sur_prefix, sitems.size() * sizeof(uint32_t)), "cudaMalloc(items)");
         b->sur_cap = sitems.size();
     }
     b->n_sur_items = (uint32_t)sitems.size();
-    if (!sitems.empty())
+    b->n_sur_pairs = (uint32_t)n_pairs;
+    if (!sitems.empty()) {
         SAS_CUDA_B(cudaMemcpy(b->d_sur_items, sitems.data(), sitems.size() * sizeof(WorkItem), cudaMemcpyHostToDevice),
                    "upload items");
+        SAS_CUDA_B(cudaMemcpy(b->d_sur_prefix, sprefix.data(), sprefix.size() * sizeof(uint32_t),
+                              cudaMemcpyHostToDevice),
+                   "upload items");
+    }
     return SAS_OK;
 }
 
@@ -205,7 +218,6 @@ sas_status capture(sas_batch* b)
     if (b->n_items > 0) kern<<<b->grid, b->cfg.block, b->smem, b->cap>>>(P);
     cudaError_t le = cudaGetLastError();
     if (le == cudaSuccess && b->sur && b->n_sur_items > 0) {
-        cudaMemsetAsync(b->d_sur_queue, 0, sizeof(unsigned int), b->cap);
         sur::STParams S;
         std::memset(&S, 0, sizeof(S));
         S.in = b->icf;
@@ -214,8 +226,9 @@ sas_status capture(sas_batch* b)
         S.seed = b->d_seed;
         S.philox_base = 0;
         S.items = b->d_sur_items;
+        S.pair_prefix = b->d_sur_prefix;
         S.n_items = b->n_sur_items;
-        S.queue = b->d_sur_queue;
+        S.n_pairs = b->n_sur_pairs;
         S.sexp = b->d_sexp;
         S.bexp = b->d_exps;
         S.poly = b->d_poly;
@@ -227,7 +240,7 @@ sas_status capture(sas_batch* b)
         S.npix = b->npix;
         S.fallbacks = b->d_fallbacks;
         S.err = surrogate_err(b->sur);
-        le = launch_sur_trace(b->sur, S, (int)std::min<uint32_t>((uint32_t)b->sm_count, b->n_sur_items), b->cap);
+        le = launch_sur_trace(b->sur, S, b->sm_count, b->cap);
     }
     cudaError_t ce = cudaStreamEndCapture(b->cap, &b->graph);
     if (le != cudaSuccess) return set_cuda_error(le, "batch kernel launch (capture)");
@@ -380,6 +393,7 @@ sas_status sas_read_batch_detector(const sas_batch* b, size_t exp, double* sum_w
     if (transmitted)
         SAS_CUDA_B(cudaMemcpyAsync(transmitted, b->d_trans + exp, 8, cudaMemcpyDeviceToHost, b->stream), "read");
     SAS_CUDA_B(cudaStreamSynchronize(b->stream), "cudaStreamSynchronize");
+    if (b->sur) return surrogate_take_error(b->sur, b->stream);
     return SAS_OK;
 }
 
@@ -458,7 +472,6 @@ sas_status sas_batch_attach_surrogate(sas_batch* b, const sas_surrogate* s)
         }
         if (!b->d_sexp) {
             SAS_CUDA_B(cudaMalloc(&b->d_sexp, b->n_exp * sizeof(sur::SurExp)), "alloc");
-            SAS_CUDA_B(cudaMalloc(&b->d_sur_queue, sizeof(unsigned int)), "alloc");
             SAS_CUDA_B(cudaMalloc(&b->d_fallbacks, sizeof(unsigned long long)), "alloc");
             SAS_CUDA_B(cudaMemset(b->d_fallbacks, 0, sizeof(unsigned long long)), "memset");
         }
@@ -504,7 +517,7 @@ sas_status sas_destroy_batch(sas_batch* b)
     cudaFree(b->d_count);
     cudaFree(b->d_trans);
     cudaFree(b->d_sur_items);
-    cudaFree(b->d_sur_queue);
+    cudaFree(b->d_sur_prefix);
     cudaFree(b->d_sexp);
     cudaFree(b->d_fallbacks);
     if (b->cap) cudaStreamDestroy(b->cap);

@@ -15,6 +15,7 @@
 #include "sas_batch.cuh"
 #include "sas_host.h"
 #include "sas_surrogate.cuh"
+#include "sas_sur_trace.cuh"
 
 namespace sas {
 sas_status set_error(sas_status s, const std::string& msg);
@@ -433,87 +434,6 @@ __global__ void init_kernel(float* p, uint64_t seed)
     }
 }
 
-// ------------------------------------------------------ surrogate trace
-
-// Persistent: CTAs take work items; each item is traced in tiles of 128
-// histories (one per row of the MLP tile). Histories outside the training
-// box are evaluated by the exact quadrature instead.
-__global__ void __launch_bounds__(THREADS, 1) sur_trace_kernel(const STParams P, const __grid_constant__ Maps maps)
-{
-    extern __shared__ unsigned char raw_sm[];
-    Ctx c;
-    ctx_init(c, raw_sm, P.err);
-    stage_params(c, P.params);
-    load_weights(c, &maps.w1, 1);
-    __shared__ unsigned int s_item;
-    const int m = row_of_thread(), h = half_of_thread();
-    float* s_row = reinterpret_cast<float*>(c.sm + SM_ROW);
-    __syncthreads();
-    for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(P.queue, 1u);
-        __syncthreads();
-        const unsigned int it = s_item;
-        if (it >= P.n_items) break;
-        const WorkItem w = P.items[it];
-        const SurExp e = P.sexp[w.exp];
-        double* sw = P.sum_w + (size_t)w.exp * P.npix;
-        double* sw2 = P.sum_w2 + (size_t)w.exp * P.npix;
-        unsigned long long* cnt = P.count + (size_t)w.exp * P.npix;
-        Kahan<float> tr;
-        for (uint32_t base = 0; base < w.n; base += TILE) {
-            const uint32_t j = base + (uint32_t)m;
-            const bool valid = j < w.n;
-            History<float> hs;
-            bool inb = false;
-            if (h == 0) {
-                float f[64];
-#pragma unroll
-                for (int k = 0; k < 64; ++k) f[k] = 0.f;
-                hs.pixel = -1;
-                if (valid) {
-                    hs = history<float>(P.in, *P.seed, P.philox_base + w.exp, w.first + j);
-                    tr.add(hs.wt);
-                    if (hs.pixel >= 0) {
-                        const float qp = hs.q[0] * e.nx + hs.q[1] * e.ny + hs.q[2] * e.nz;
-                        const float q2 = hs.q[0] * hs.q[0] + hs.q[1] * hs.q[1] + hs.q[2] * hs.q[2];
-                        const float qt = sqrtf(fmaxf(q2 - qp * qp, 0.0f));
-                        inb = e.in_box && sqrtf(q2) <= P.box.q_max;
-                        if (inb) features(P.box, fabsf(qp), qt, e.R, e.L, e.so, e.sp, f);
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < 8; ++q) st_row8(c.sm + SM_A0, m, 8 * q, f + 8 * q);
-            }
-            const float dot = forward_tile<false>(c, maps, nullptr, nullptr, 0, 0, false);
-            s_row[h * TILE + m] = dot;
-            __syncthreads();
-            if (h == 0 && valid && hs.pixel >= 0) {
-                float ds;
-                if (inb) {
-                    ds = e.scale_p * __expf(P.params[OFF_B5] + s_row[m] + s_row[TILE + m]);
-                } else {
-                    const BatchExp& be = P.bexp[w.exp];
-                    ds = dsigma<float, SAS_CYLINDER>(hs.q, be.mc, P.poly + be.poly_off, P.orient + be.orient_off);
-                    atomicAdd(P.fallbacks, 1ull);
-                }
-                const float wt = hs.pref * ds;
-                atomicAdd(sw + hs.pixel, (double)wt);
-                atomicAdd(sw2 + hs.pixel, (double)wt * (double)wt);
-                atomicAdd(cnt + hs.pixel, 1ull);
-            }
-            __syncthreads();
-        }
-        if (h == 0) {
-            double t = (double)tr.s - (double)tr.c;
-            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-            if ((threadIdx.x & 31) == 0 && t != 0.0) atomicAdd(P.trans + w.exp, t);
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0 && !tc::mbar_wait(c.bar_tma, c.ph_tma, WAIT_NS)) atomicExch(P.err, 7);
-    ctx_finish(c);
-}
-
 }  // namespace sur
 }  // namespace sas
 
@@ -816,16 +736,41 @@ sur::SurExp surrogate_exp(const sas_model_desc& m, bool in_box)
 
 cudaError_t launch_sur_trace(const sas_surrogate* s, const sur::STParams& P, int sm_count, cudaStream_t st)
 {
+    if (P.n_pairs == 0) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(sur::sur_trace_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)SMEM_BYTES);
+                                         (int)sur::S2_SMEM);
     if (e != cudaSuccess) return e;
-    sur::sur_trace_kernel<<<sm_count, THREADS, SMEM_BYTES, st>>>(P, s->maps);
+    const int grid = (int)std::min<uint32_t>((uint32_t)sm_count, P.n_pairs);
+    sur::sur_trace_kernel<<<grid, sur::ST_THREADS, sur::S2_SMEM, st>>>(P, s->maps);
     return cudaGetLastError();
+}
+
+uint64_t surrogate_pair_prefix(const std::vector<WorkItem>& items, std::vector<uint32_t>& prefix)
+{
+    prefix.resize(items.size());
+    uint64_t n = 0;
+    for (size_t i = 0; i < items.size(); ++i) {
+        prefix[i] = (uint32_t)std::min<uint64_t>(n, 0xFFFFFFFFull);
+        n += (items[i].n + 255u) / 256u;
+    }
+    return n;
 }
 
 const float* surrogate_params(const sas_surrogate* s) { return s->d_p; }
 sur::Box surrogate_dbox(const sas_surrogate* s) { return s->dbox; }
 int* surrogate_err(const sas_surrogate* s) { return s->d_err; }
+
+sas_status surrogate_take_error(const sas_surrogate* s, cudaStream_t st)
+{
+    int e = 0;
+    cudaError_t ce = cudaMemcpyAsync(&e, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess) return set_cuda_error(ce, "read surrogate error flag");
+    if (e == 0) return SAS_OK;
+    cudaMemsetAsync(s->d_err, 0, sizeof(int), st);
+    return set_error(SAS_ERR_TIMEOUT, "a bounded wait in the surrogate trace gave up (code " + std::to_string(e) +
+                                          "); the detector is incomplete");
+}
 
 }  // namespace sas
 

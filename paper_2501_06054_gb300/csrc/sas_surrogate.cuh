@@ -138,10 +138,13 @@ struct STParams {
     const float* params;
     const uint64_t* seed;    // device scalar
     uint32_t philox_base;    // Philox experiment id = philox_base + item experiment
-    // single experiment or batch items
+    // single experiment or batch items; item i holds pairs (256 histories)
+    // pair_prefix[i] .. pair_prefix[i + 1] - 1 (every item but the last of an
+    // experiment is a multiple of 256 long)
     const WorkItem* items;
+    const uint32_t* pair_prefix;   // [n_items]
     uint32_t n_items;
-    unsigned int* queue;
+    uint32_t n_pairs;
     const SurExp* sexp;
     const BatchExp* bexp;    // exact fallback (model constants and table offsets)
     const float* poly;

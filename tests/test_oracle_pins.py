@@ -518,3 +518,33 @@ def test_trace_finite_beam_matches_independent_numpy_mc():
     z = (a - b) / np.sqrt(va + vb)
     assert np.max(np.abs(z)) < 4.5
     assert np.mean(z ** 2) < 1.6
+
+
+def test_geometry_records_split_the_weight():
+    """The per-history geometry export: the same histories as the trace
+    (pixels, transmitted weight), and prefactor x dSigma/dOmega(Q) gives
+    the records' weight both for the closed-form sphere (|Q| only) and for
+    an oriented cylinder (the direction of Q about its axis)."""
+    inst = W.Instrument(nx=8, ny=8, pixel_x=0.02, pixel_y=0.02, det_distance=2.0,
+                        dlambda_rel=0.25, ap1_radius=0.01, ap2_radius=0.004)
+    R, drho, phi = 60.0, 2e-6, 0.01
+    V = 4 / 3 * math.pi * R ** 3
+    sph = _model(kind=W.SPHERE, radius=R, sld=drho, volume_fraction=phi)
+    cyl = _model(kind=W.CYLINDER, radius=20.0, length=300.0, sld=drho, volume_fraction=phi,
+                 axis_theta=math.radians(90), axis_phi=math.radians(30))
+    n = 4000
+    g = oracle.geometry_records(inst, n, seed=3, first=77)
+    sc = g["pixel"] >= 0
+    assert sc.sum() > n // 2
+    for m in (sph, cyl):
+        pix, w = oracle.records(inst, m, n, seed=3, first=77)
+        assert np.array_equal(pix, g["pixel"])
+        if m is sph:
+            x = np.linalg.norm(g["q"][sc], axis=1) * R
+            ds = phi * drho ** 2 * V * (3 * sp.spherical_jn(1, x) / x) ** 2
+        else:
+            ds = oracle.dsigma(oracle.Prepared(m), g["q"][sc])
+        assert np.allclose(g["pref"][sc] * ds, w[sc], rtol=1e-9, atol=0)
+    full = oracle.trace(inst, sph, n, seed=3, first=77)
+    assert g["trans"].sum() == pytest.approx(full["trans"], rel=1e-12)
+    assert np.all(g["pref"][~sc] == 0.0)

@@ -209,3 +209,67 @@ def test_surrogate_trace_falls_back_outside_the_box():
     assert np.all(np.abs(d2["sum_w"] - so)[big] <= 1e-4 * so[big])
     e.close()
     sas.sas_destroy_surrogate(s)
+
+
+def _network_tally(box, p, inst, m, n, seed, first=0):
+    """Expected surrogate detector from the oracle alone: oracle geometry
+    (pixel, Q, prefactor), the oracle network on the features of Q about the
+    cylinder axis, and <V^2>/<V> from the oracle's Schulz nodes."""
+    g = oracle.geometry_records(inst, n, seed, first=first)
+    sc = g["pixel"] >= 0
+    ax = np.array([math.sin(m.axis_theta) * math.cos(m.axis_phi),
+                   math.sin(m.axis_theta) * math.sin(m.axis_phi), math.cos(m.axis_theta)])
+    q = g["q"][sc]
+    qp = q @ ax
+    qt = np.sqrt(np.maximum(np.sum(q * q, axis=1) - qp * qp, 0.0))
+    assert np.sqrt(np.sum(q * q, axis=1)).max() < box["q_max"]       # every history in the box
+    raw = np.zeros((len(qp), 8))
+    raw[:, 0], raw[:, 1] = np.abs(qp), qt
+    raw[:, 2], raw[:, 3], raw[:, 4], raw[:, 5] = m.radius, m.length, m.sigma_orient, m.poly
+    out = M.forward(p, M.features(box, raw))
+    prep = oracle.Prepared(m)
+    V = math.pi * prep.poly_r ** 2 * m.length
+    scale = m.volume_fraction * (m.sld - m.sld_solvent) ** 2 * float(np.dot(prep.poly_w, V * V)) / float(
+        np.dot(prep.poly_w, V))
+    w = g["pref"][sc] * scale * np.exp(out)
+    npix = inst.nx * inst.ny
+    return dict(sum_w=np.bincount(g["pixel"][sc], weights=w, minlength=npix),
+                count=np.bincount(g["pixel"][sc], minlength=npix), trans=float(g["trans"].sum()))
+
+
+@pytest.mark.parametrize("n, first", [(116813, 0), (700, 0), (40000, 123457)])
+def test_surrogate_trace_tallies_the_network(n, first):
+    """The warp-specialised trace (two tiles in flight, static pair
+    schedule, reversed K order on the second tile) against the oracle
+    geometry weighted by the oracle network on the same BF16 weights:
+    identical histories per pixel, per-pixel sums within the BF16 operand
+    tolerance of the network test, transmitted weight to FP32 rounding."""
+    box = _small_box()
+    s = sas.sas_create_surrogate(box, seed=7, stream=torch.cuda.current_stream())
+    p = sas.sas_surrogate_get_params(s, M.NPARAM)
+    rng = np.random.default_rng(4)
+    p[M.OFF_W5:M.OFF_B5] = rng.uniform(-1, 1, 256).astype(np.float32) * 0.3
+    p[M.OFF_B1 + 256:M.OFF_W5] = rng.normal(size=768).astype(np.float32) * 0.1
+    p[M.OFF_B5] = -2.0
+    sas.sas_surrogate_set_params(s, p)
+    inst = W.instrument(nx=48, ny=40, pixel_x=0.008, pixel_y=0.008)
+    m = W.Model(kind=W.CYLINDER, radius=19.0, length=420.0, sld=2e-6, volume_fraction=0.01, poly=0.1,
+                n_poly=12, sigma_orient=math.radians(14), n_gamma=16, n_psi=16,
+                axis_theta=math.radians(70), axis_phi=math.radians(20))
+    e = sas.Experiment(inst, m, stream=torch.cuda.current_stream())
+    sas.sas_attach_surrogate(e.h, s)
+    fb0 = sas.sas_surrogate_fallbacks(exp=e.h)
+    sas.sas_reset_detector(e.h)
+    e.trace_range(first, n, seed=5)
+    d = e.read()
+    assert sas.sas_surrogate_fallbacks(exp=e.h) == fb0                 # nothing left the box
+    ref = _network_tally(box, p, inst, m, n, seed=5, first=first)
+    assert np.array_equal(d["count"].ravel(), ref["count"].astype(np.uint64))
+    got, exp_ = d["sum_w"].ravel(), ref["sum_w"]
+    assert abs(got.sum() - exp_.sum()) <= 3e-3 * exp_.sum()
+    hit = ref["count"] >= 20
+    rel = np.abs(got - exp_)[hit] / exp_[hit]
+    assert np.median(rel) < 3e-3 and rel.max() < 3e-2, (np.median(rel), rel.max())
+    assert d["trans"] == pytest.approx(ref["trans"], rel=1e-5)
+    e.close()
+    sas.sas_destroy_surrogate(s)
