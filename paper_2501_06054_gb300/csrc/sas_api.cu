@@ -673,7 +673,7 @@ sas_status trace_surrogate(sas_experiment* e, uint64_t first, uint64_t n, uint64
     std::memset(&P, 0, sizeof(P));
     P.in = e->icf;
     P.box = surrogate_dbox(e->sur);
-    P.params = surrogate_params(e->sur);
+    P.epi = surrogate_epi(e->sur);
     P.seed = e->d_seed;
     P.philox_base = e->exp_id;
     P.items = e->d_items;

@@ -222,7 +222,7 @@ sas_status capture(sas_batch* b)
         std::memset(&S, 0, sizeof(S));
         S.in = b->icf;
         S.box = surrogate_dbox(b->sur);
-        S.params = surrogate_params(b->sur);
+        S.epi = surrogate_epi(b->sur);
         S.seed = b->d_seed;
         S.philox_base = 0;
         S.items = b->d_sur_items;

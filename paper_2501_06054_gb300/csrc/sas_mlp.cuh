@@ -19,6 +19,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include "sas_tc.cuh"
 
 namespace sas {
@@ -62,11 +63,22 @@ struct Maps {
     CUtensorMap wt[3];   // W2^T..W4^T [256 in][256 out] bf16
 };
 
-__device__ __forceinline__ float sig_(float z)
+__device__ __forceinline__ float tanh_approx(float x)
 {
     float t;
-    asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(0.5f * z));
-    return fmaf(0.5f, t, 0.5f);
+    asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(x));
+    return t;
+}
+__device__ __forceinline__ float sig_(float z) { return fmaf(0.5f, tanh_approx(0.5f * z), 0.5f); }
+
+// tanh of two values through one half-precision MUFU operation (inputs
+// rounded to f16; about 2^-11 relative error, like tanh.approx.f32)
+__device__ __forceinline__ float2 tanh2_f16(float2 x)
+{
+    const __half2 h = __floats2half2_rn(x.x, x.y);
+    uint32_t r;
+    asm("tanh.approx.f16x2 %0, %1;" : "=r"(r) : "r"(*reinterpret_cast<const uint32_t*>(&h)));
+    return __half22float2(*reinterpret_cast<const __half2*>(&r));
 }
 __device__ __forceinline__ float silu(float z) { return z * sig_(z); }
 __device__ __forceinline__ float dsilu(float z)

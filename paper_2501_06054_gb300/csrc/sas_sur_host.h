@@ -13,7 +13,8 @@ sur::SurExp surrogate_exp(const sas_model_desc& m, bool in_box);
 cudaError_t launch_sur_trace(const sas_surrogate* s, const sur::STParams& P, int sm_count, cudaStream_t st);
 // prefix[i] = 256-history pairs in items [0, i); returns the total.
 uint64_t surrogate_pair_prefix(const std::vector<WorkItem>& items, std::vector<uint32_t>& prefix);
-const float* surrogate_params(const sas_surrogate* s);
+// Trace epilogue constants [1281]: b_l / 2 (4 x 256), w5, b5 (kept current by training and set_params).
+const float* surrogate_epi(const sas_surrogate* s);
 sur::Box surrogate_dbox(const sas_surrogate* s);
 int* surrogate_err(const sas_surrogate* s);
 // SAS_ERR_TIMEOUT (and clears the flag) if a surrogate kernel on stream st gave up a wait.

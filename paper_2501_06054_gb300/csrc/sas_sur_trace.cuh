@@ -1,22 +1,24 @@
 // Cylinder trace through the learned surrogate: warp-specialised, two
 // 128-history tiles ("slots") in flight per SM.
 //
-// 9 warps per CTA. Warp 8 is the producer: one lane streams the weight
+// 17 warps per CTA. Warp 16 is the producer: one lane streams the weight
 // K blocks (64 wide, 32 KB) through a 3-stage TMA ring and issues the
 // tcgen05 MMAs of slot 0 and slot 1 alternately into two TMEM accumulators
-// (columns 0..255 and 256..511). Warps 0..7 are the epilogue: warps 0..3
-// trace the histories of a slot and write its features; for every layer all
-// eight read the slot's accumulator (row m = TMEM lane m, warps 0..3 columns
-// 0..127, warps 4..7 columns 128..255), add the bias, apply SiLU and write
-// the BF16 activations back as the next layer's A operand, or, after the
-// last layer, reduce against w5, weight and tally the histories. While the
-// epilogue works on one slot the tensor cores work on the other.
+// (columns 0..255 and 256..511). Warps 0..15 are the epilogue: for every
+// layer each reads a quarter of the slot's accumulator (row m = TMEM lane m,
+// warp w: lanes 32 (w % 4).., columns 64 (w / 4)..), adds the bias, applies
+// SiLU and writes the BF16 activations back as the next layer's A operand,
+// or, after the last layer, reduces against w5. Warps 0..3 own the histories
+// of slot 0 and warps 8..11 those of slot 1: they trace them, write their
+// features and, after the last layer, weight and tally them. While the
+// epilogue works on one slot the tensor cores work on the other; sixteen
+// warps keep the MUFU (tanh) pipe, the epilogue's bound, busy.
 //
 // Synchronisation (mbarriers):
 //   full[st]   TMA of ring stage st landed                  (producer waits)
 //   empty[st]  MMAs reading stage st's block finished        (producer waits)
 //   acc[s]     the layer MMAs of slot s finished             (epilogue waits)
-//   ready[s]   slot s's A operand written, TMEM read (256)   (producer waits)
+//   ready[s]   slot s's A operand written, TMEM read (16)    (producer waits)
 //   drain      every MMA issued finished                    (producer, at exit)
 // Every wait gives up after WAIT_NS or once another thread has given up
 // (a shared abort flag); the loops keep their trip counts so that the
@@ -34,12 +36,12 @@
 namespace sas {
 namespace sur {
 
-constexpr int ST_THREADS = 288;
+constexpr int EPI_WARPS = 16;
+constexpr int ST_THREADS = 32 * EPI_WARPS + 32;
 constexpr int RING = 3;                        // weight ring stages (32 KB each)
 constexpr uint32_t S2_A = 0;                   // 2 x 64 KB activation slots (K block 0 = features)
 constexpr uint32_t S2_W = 131072;              // RING x 32 KB weight ring
-constexpr uint32_t S2_DOT = S2_W + RING * 32768u;   // [2][128] f32: second half of the output dot
-constexpr uint32_t S2_BAR = S2_DOT + 1024;     // 11 mbarriers, TMEM address, abort flag
+constexpr uint32_t S2_BAR = S2_W + RING * 32768u;   // 11 mbarriers, TMEM address, abort flag
 constexpr size_t S2_SMEM = (size_t)S2_BAR + 128 + 1024;
 constexpr int UNITS_PER_PAIR = 26;             // layer 1: 2 slots x 1 K block; layers 2..4: 2 slots x 4
 constexpr int LOADS_PER_PAIR = 16;
@@ -58,7 +60,7 @@ struct SchedUnit {
     uint8_t l, s, kb, load, flags;   // flags: first / last unit of (l, s), last use of the load
 };
 struct SchedLoad {
-    uint8_t l, kb, role;
+    uint8_t l, kb, role, ord;   // ord: loads of the same role before this one in the pair
     int8_t free_after;
 };
 static __constant__ SchedUnit kUnits[UNITS_PER_PAIR] = {
@@ -74,9 +76,9 @@ static __constant__ SchedUnit kUnits[UNITS_PER_PAIR] = {
     {3, 1, 0, 15, U_LAST | U_RELEASE},
 };
 static __constant__ SchedLoad kLoads[LOADS_PER_PAIR] = {
-    {0, 0, 0, -3}, {1, 0, 1, -2}, {1, 1, 2, -1}, {1, 2, 0, 1}, {1, 3, 1, 2}, {1, 0, 1, 6},
-    {2, 0, 0, 7}, {2, 1, 2, 8}, {2, 2, 1, 9}, {2, 3, 0, 10}, {2, 0, 0, 14},
-    {3, 0, 1, 15}, {3, 1, 2, 16}, {3, 2, 0, 17}, {3, 3, 1, 18}, {3, 0, 1, 22},
+    {0, 0, 0, 0, -3}, {1, 0, 1, 0, -2}, {1, 1, 2, 0, -1}, {1, 2, 0, 1, 1}, {1, 3, 1, 1, 2}, {1, 0, 1, 2, 6},
+    {2, 0, 0, 2, 7}, {2, 1, 2, 1, 8}, {2, 2, 1, 3, 9}, {2, 3, 0, 3, 10}, {2, 0, 0, 4, 14},
+    {3, 0, 1, 4, 15}, {3, 1, 2, 2, 16}, {3, 2, 0, 5, 17}, {3, 3, 1, 5, 18}, {3, 0, 1, 6, 22},
 };
 
 __device__ __forceinline__ uint32_t ring_stage(uint32_t pair, uint32_t role)
@@ -84,14 +86,23 @@ __device__ __forceinline__ uint32_t ring_stage(uint32_t pair, uint32_t role)
     return role == 0 ? 0u : ((pair & 1u) ? 3u - role : role);
 }
 
-// History data a row keeps in the registers of its epilogue thread
-// (warps 0..3) from the features to the tally.
+// Phase parity of a load's full barrier (and of its release on empty). Per
+// pair role X takes 6 loads (even) and stays on stage 0; roles Y and Z take
+// 7 and 3 loads and swap stages 1 and 2 every pair, so each of those stages
+// has seen an odd number of loads before every odd pair.
+__device__ __forceinline__ uint32_t ring_parity(uint32_t pair, const SchedLoad& L)
+{
+    return ((L.role == 0 ? 0u : (pair & 1u)) + L.ord) & 1u;
+}
+
+// History data a row keeps in the registers of its owning epilogue thread
+// from the features to the tally.
 struct RowRec {
     float pref, q0, q1, q2, wt;
     int pix_flags;   // (pixel + 1) << 2 | in_box << 1 | valid
 };
 
-__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(32 * EPI_WARPS) : "memory"); }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar)
 {
@@ -139,28 +150,26 @@ __device__ __forceinline__ PairInfo pair_info(const STParams& P, uint32_t p)
 }
 
 // Trace the history of row m of slot s and write its features into the
-// slot's A operand (warps 0..3).
+// slot's A operand (the owning threads of the epilogue).
 __device__ __forceinline__ RowRec slot_features(const STParams& P, unsigned char* sm, int s, int m,
                                                 const PairInfo& pi)
 {
-    float f[64];
-#pragma unroll
-    for (int k = 0; k < 64; ++k) f[k] = 0.f;
     RowRec r;
     r.pref = r.q0 = r.q1 = r.q2 = r.wt = 0.f;
     r.pix_flags = 0;
     const uint32_t j = (uint32_t)s * 128u + (uint32_t)m;
+    float qp = 0.f, qt = 0.f;
+    bool inb = false;
+    SurExp e = P.sexp[pi.exp];
     if (j < pi.n) {
         const History<float> hs = history<float>(P.in, *P.seed, P.philox_base + pi.exp, pi.first + j);
         r.wt = hs.wt;
         int flags = 1 | ((hs.pixel + 1) << 2);
         if (hs.pixel >= 0) {
-            const SurExp e = P.sexp[pi.exp];
-            const float qp = hs.q[0] * e.nx + hs.q[1] * e.ny + hs.q[2] * e.nz;
+            qp = hs.q[0] * e.nx + hs.q[1] * e.ny + hs.q[2] * e.nz;
             const float q2 = hs.q[0] * hs.q[0] + hs.q[1] * hs.q[1] + hs.q[2] * hs.q[2];
-            const float qt = sqrtf(fmaxf(q2 - qp * qp, 0.0f));
-            const bool inb = e.in_box && sqrtf(q2) <= P.box.q_max;
-            if (inb) features(P.box, fabsf(qp), qt, e.R, e.L, e.so, e.sp, f);
+            qt = sqrtf(fmaxf(q2 - qp * qp, 0.0f));
+            inb = e.in_box && sqrtf(q2) <= P.box.q_max;
             flags |= inb ? 2 : 0;
             r.pref = hs.pref;
             r.q0 = hs.q[0];
@@ -169,9 +178,7 @@ __device__ __forceinline__ RowRec slot_features(const STParams& P, unsigned char
         }
         r.pix_flags = flags;
     }
-    unsigned char* a = sm + S2_A + (uint32_t)s * 65536u;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) mlp::st_row8(a, m, 8 * q, f + 8 * q);
+    write_features(P.box, inb, fabsf(qp), qt, e.R, e.L, e.so, e.sp, sm + S2_A + (uint32_t)s * 65536u, m);
     return r;
 }
 
@@ -208,6 +215,39 @@ __device__ __forceinline__ void flush_trans(const STParams& P, double& t, uint32
     t = 0.0;
 }
 
+// Latest weight load issued into each ring stage (pair * 16 + j + 1; 0: none).
+struct RingLast {
+    uint32_t g0 = 0, g1 = 0, g2 = 0;
+};
+
+// Issue one weight load (schedule entry j of pair `pair`) into its ring stage
+// once the stage's previous block has been released.
+__device__ __forceinline__ bool sched_load(unsigned char* sm, uint64_t* full, uint64_t* empty, const mlp::Maps& maps,
+                                           uint32_t pair, int j, volatile int* abort, RingLast& last)
+{
+    const SchedLoad L = kLoads[j];
+    const uint32_t k = ring_stage(pair, L.role);
+    if (pair > 0 || L.ord > 0)
+        if (!wait_ab(empty + k, ring_parity(pair, L) ^ 1u, abort)) return false;
+    const CUtensorMap* map = L.l == 0 ? &maps.w1 : &maps.w[L.l - 1];
+    tc::mbar_arrive_expect_tx(full + k, 32768u);
+    tc::tma_load_2d(sm + S2_W + k * 32768u, map, L.kb * 64, 0, full + k);
+    const uint32_t g = pair * LOADS_PER_PAIR + (uint32_t)j + 1u;
+    if (k == 0) last.g0 = g;
+    else if (k == 1) last.g1 = g;
+    else last.g2 = g;
+    return true;
+}
+
+// Load of the current pair issued after unit u (-1: none); loads 0 and 1 of
+// the next pair follow units 24 and 25.
+__host__ __device__ constexpr int load_after_unit(int u)
+{
+    return u == 0 ? 2 : u == 2 ? 3 : u == 3 ? 4 : u == 7 ? 5 : u == 8 ? 6 : u == 9 ? 7 : u == 10 ? 8
+         : u == 11 ? 9 : u == 15 ? 10 : u == 16 ? 11 : u == 17 ? 12 : u == 18 ? 13 : u == 19 ? 14
+         : u == 23 ? 15 : -1;
+}
+
 __global__ void __launch_bounds__(ST_THREADS, 1) sur_trace_kernel(const STParams P, const __grid_constant__ mlp::Maps maps)
 {
     extern __shared__ unsigned char raw_sm[];
@@ -227,7 +267,7 @@ __global__ void __launch_bounds__(ST_THREADS, 1) sur_trace_kernel(const STParams
         }
         for (int i = 0; i < 2; ++i) {
             tc::mbar_init(acc + i, 1);
-            tc::mbar_init(ready + i, 256);
+            tc::mbar_init(ready + i, EPI_WARPS);
         }
         tc::mbar_init(drain, 1);
         *abort = 0;
@@ -240,68 +280,68 @@ __global__ void __launch_bounds__(ST_THREADS, 1) sur_trace_kernel(const STParams
     const uint32_t tmem = *taddr;
     const uint32_t my_pairs = blockIdx.x < P.n_pairs ? (P.n_pairs - 1u - blockIdx.x) / gridDim.x + 1u : 0u;
 
-    if (warp == 8) {
+    if (warp == EPI_WARPS) {
         // ---------------------------------------------------------- producer
         if (lane == 0 && my_pairs > 0) {
-            const uint32_t total = my_pairs * UNITS_PER_PAIR;
-            const uint32_t n_loads = my_pairs * LOADS_PER_PAIR;
             const uint32_t idesc = tc::idesc_bf16(mlp::TILE, mlp::H);
-            uint32_t nld[RING] = {0u, 0u, 0u};    // loads issued per stage
-            uint8_t ld_stage[32], ld_par[32];     // stage and full-barrier parity of load g (mod 32)
-            uint32_t g_next = 0;                   // next load (over all pairs of this CTA)
-            uint32_t rd_ph[2] = {0u, 0u};
-            uint32_t issued = 0;                   // units whose MMAs were issued
-            bool ok = true;
-            // issue, in order, every load whose stage was released by unit <= v_done
-            auto issue_loads = [&](int64_t v_done) {
-                while (ok && g_next < n_loads) {
-                    const uint32_t pair = g_next / LOADS_PER_PAIR;
-                    const SchedLoad L = kLoads[g_next % LOADS_PER_PAIR];
-                    if ((int64_t)pair * UNITS_PER_PAIR + L.free_after > v_done) break;
-                    const uint32_t k = ring_stage(pair, L.role);
-                    if (nld[k] > 0) {
-                        ok = wait_ab(empty + k, (nld[k] - 1u) & 1u, abort);
+            // operand descriptors, computed once: advancing K by 16 elements
+            // (32 bytes) adds 2 to the start-address field
+            const uint64_t dA = tc::desc_sw128(tc::smem_u32(sm + S2_A));
+            const uint64_t dW0 = tc::desc_sw128(tc::smem_u32(sm + S2_W));
+            const uint64_t dW1 = dW0 + (32768u >> 4), dW2 = dW0 + (65536u >> 4);
+            uint32_t rd_ph0 = 0u, rd_ph1 = 0u;
+            RingLast last;
+            bool ok = sched_load(sm, full, empty, maps, 0, 0, abort, last) &&
+                      sched_load(sm, full, empty, maps, 0, 1, abort, last);
+            bool issued = false;
+            for (uint32_t pair = 0; pair < my_pairs && ok; ++pair) {
+                const bool more = pair + 1 < my_pairs;
+                const uint32_t pb = pair & 1u;
+                // stages of roles Y and Z this pair, and their descriptors
+                const uint64_t dY = pb ? dW2 : dW1, dZ = pb ? dW1 : dW2;
+#pragma unroll
+                for (int u = 0; u < UNITS_PER_PAIR; ++u) {
+                    if (!ok) break;
+                    const SchedUnit U = kUnits[u];
+                    if (U.flags & U_FIRST) {
+                        ok = wait_ab(ready + U.s, U.s ? rd_ph1 : rd_ph0, abort);
+                        if (U.s) rd_ph1 ^= 1u;
+                        else rd_ph0 ^= 1u;
                         if (!ok) break;
                     }
-                    const CUtensorMap* map = L.l == 0 ? &maps.w1 : &maps.w[L.l - 1];
-                    tc::mbar_arrive_expect_tx(full + k, 32768u);
-                    tc::tma_load_2d(sm + S2_W + k * 32768u, map, L.kb * 64, 0, full + k);
-                    ld_stage[g_next & 31u] = (uint8_t)k;
-                    ld_par[g_next & 31u] = (uint8_t)(nld[k] & 1u);
-                    ++nld[k];
-                    ++g_next;
-                }
-            };
-            issue_loads(-1);
-            for (uint32_t v = 0; v < total && ok; ++v) {
-                const uint32_t pair = v / UNITS_PER_PAIR;
-                const SchedUnit U = kUnits[v % UNITS_PER_PAIR];
-                if (U.flags & U_FIRST) {
-                    ok = wait_ab(ready + U.s, rd_ph[U.s], abort);
-                    rd_ph[U.s] ^= 1u;
+                    const SchedLoad L = kLoads[U.load];
+                    const uint32_t k = ring_stage(pair, L.role);
+                    ok = wait_ab(full + k, ring_parity(pair, L), abort);
                     if (!ok) break;
-                }
-                const uint32_t g = pair * LOADS_PER_PAIR + U.load;   // issued: its stage was released >= 2 units ago
-                const uint32_t k = ld_stage[g & 31u];
-                ok = wait_ab(full + k, ld_par[g & 31u], abort);
-                if (!ok) break;
-                tc::fence_after_sync();
-                const uint32_t a0 = tc::smem_u32(sm + S2_A + (uint32_t)U.s * 65536u + (uint32_t)U.kb * 16384u);
-                const uint32_t b0 = tc::smem_u32(sm + S2_W + k * 32768u);
+                    tc::fence_after_sync();
+                    const uint64_t da = dA + (((uint32_t)U.s * 65536u + (uint32_t)U.kb * 16384u) >> 4);
+                    const uint64_t db = L.role == 0 ? dW0 : (L.role == 1 ? dY : dZ);
+                    const uint32_t dtm = tmem + 256u * (uint32_t)U.s;
 #pragma unroll
-                for (int kk = 0; kk < 4; ++kk)
-                    tc::mma_bf16(tmem + 256u * (uint32_t)U.s, tc::desc_sw128(a0 + kk * 32),
-                                 tc::desc_sw128(b0 + kk * 32), idesc, ((U.flags & U_FIRST) && kk == 0) ? 0u : 1u);
-                if (U.flags & U_RELEASE) tc::mma_commit(empty + k);
-                if (U.flags & U_LAST) tc::mma_commit(acc + U.s);
-                issued = v + 1;
-                issue_loads((int64_t)v - 1);
+                    for (int kk = 0; kk < 4; ++kk)
+                        tc::mma_bf16(dtm, da + 2 * kk, db + 2 * kk, idesc, ((U.flags & U_FIRST) && kk == 0) ? 0u : 1u);
+                    issued = true;
+                    if (U.flags & U_RELEASE) tc::mma_commit(empty + k);
+                    if (U.flags & U_LAST) tc::mma_commit(acc + U.s);
+                    const int jn = load_after_unit(u);
+                    if (jn >= 0) ok = sched_load(sm, full, empty, maps, pair, jn, abort, last);
+                    else if (u == 24 && more) ok = sched_load(sm, full, empty, maps, pair + 1, 0, abort, last);
+                    else if (u == 25 && more) ok = sched_load(sm, full, empty, maps, pair + 1, 1, abort, last);
+                }
             }
-            // drain: the last load of each stage, then every MMA issued
+            // drain: the latest load of each stage (a stage takes its next load
+            // only after the previous one was consumed, so only these can
+            // still be in flight), then every MMA issued
             bool drained = true;
-            for (int k = 0; k < RING; ++k)
-                if (nld[k] > 0) drained = tc::mbar_wait(full + k, (nld[k] - 1u) & 1u, mlp::WAIT_NS) && drained;
-            if (issued > 0) {
+#pragma unroll
+            for (int k = 0; k < RING; ++k) {
+                const uint32_t g = k == 0 ? last.g0 : (k == 1 ? last.g1 : last.g2);
+                if (g == 0) continue;
+                const uint32_t pr = (g - 1u) / LOADS_PER_PAIR;
+                const SchedLoad L = kLoads[(g - 1u) % LOADS_PER_PAIR];
+                drained = tc::mbar_wait(full + k, ring_parity(pr, L), mlp::WAIT_NS) && drained;
+            }
+            if (issued) {
                 tc::mma_commit(drain);
                 drained = tc::mbar_wait(drain, 0u, mlp::WAIT_NS) && drained;
             }
@@ -312,93 +352,121 @@ __global__ void __launch_bounds__(ST_THREADS, 1) sur_trace_kernel(const STParams
         }
     } else {
         // ---------------------------------------------------------- epilogue
-        const int h = warp >> 2;
+        // Warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows m) and columns
+        // 64 (w / 4) .. + 63 of every accumulator. Warps 0..3 own the
+        // histories of slot 0, warps 8..11 those of slot 1: they trace them,
+        // keep them in registers, write their features and tally them.
+        const int q = warp >> 2;
         const int m = 32 * (warp & 3) + lane;
+        const int col_q = 64 * q;
         const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
-        const float* bias = P.params + mlp::OFF_B1;
-        const float* w5 = P.params + mlp::OFF_W5;
-        float* dot1 = reinterpret_cast<float*>(sm + S2_DOT);
-        const float b5 = __ldg(P.params + mlp::OFF_B5);
-        uint32_t acc_ph[2] = {0u, 0u};
+        const int own = q == 0 ? 0 : (q == 2 ? 1 : -1);   // slot whose histories this thread owns
+        const float* hbias = P.epi;                        // b_l / 2
+        const float* w5 = P.epi + 4 * mlp::H;
+        const float b5 = __ldg(P.epi + 5 * mlp::H);
+        uint32_t acc_ph0 = 0u, acc_ph1 = 0u;
         bool ok = true;
         double t_acc = 0.0;
         uint32_t t_exp = 0xFFFFFFFFu;
-        RowRec rec[2];
+        RowRec rec;
+        rec.pix_flags = 0;
         PairInfo cur = my_pairs > 0 ? pair_info(P, blockIdx.x) : PairInfo{0, 0, 0};
         if (my_pairs > 0) {
-#pragma unroll
-            for (int s = 0; s < 2; ++s) {
-                if (h == 0) rec[s] = slot_features(P, sm, s, m, cur);
-                tc::fence_proxy_async_smem();
-                mbar_arrive(ready + s);
+            if (own >= 0) rec = slot_features(P, sm, own, m, cur);
+            tc::fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(ready + 0);
+                mbar_arrive(ready + 1);
             }
         }
+        const float2 half2 = make_float2(0.5f, 0.5f);
         for (uint32_t it = 0; it < my_pairs; ++it) {
             const bool more = it + 1 < my_pairs;
             const PairInfo nxt = more ? pair_info(P, blockIdx.x + (it + 1) * gridDim.x) : cur;
             for (int l = 0; l < 4; ++l) {
+                const float* hb = hbias + 256 * l + col_q;
 #pragma unroll
                 for (int s = 0; s < 2; ++s) {
-                    ok = wait_ab(acc + s, acc_ph[s], abort) && ok;
-                    acc_ph[s] ^= 1u;
+                    ok = wait_ab(acc + s, s ? acc_ph1 : acc_ph0, abort) && ok;
+                    if (s) acc_ph1 ^= 1u;
+                    else acc_ph0 ^= 1u;
                     tc::fence_after_sync();
-                    const uint32_t tbase = tmem + lane_base + 256u * (uint32_t)s;
                     unsigned char* a = sm + S2_A + (uint32_t)s * 65536u;
-                    float dot = 0.f;
-#pragma unroll 1
-                    for (int ch = 0; ch < 4; ++ch) {
-                        const int col0 = 128 * h + 32 * ch;
-                        float v[32];
-                        tc::tmem_ld32(tbase + col0, v);
-                        const float4* b4 = reinterpret_cast<const float4*>(bias + 256 * l + col0);
+                    uint32_t r[64];
+                    tc::tmem_ld32_nowait(tmem + lane_base + 256u * (uint32_t)s + col_q, r);
+                    tc::tmem_ld32_nowait(tmem + lane_base + 256u * (uint32_t)s + col_q + 32, r + 32);
+                    tc::tmem_wait_ld();
+                    float2 dot2 = make_float2(0.f, 0.f);
 #pragma unroll
-                        for (int q = 0; q < 8; ++q) {
-                            const float4 bb = __ldg(b4 + q);
-                            v[4 * q + 0] = mlp::silu(v[4 * q + 0] + bb.x);
-                            v[4 * q + 1] = mlp::silu(v[4 * q + 1] + bb.y);
-                            v[4 * q + 2] = mlp::silu(v[4 * q + 2] + bb.z);
-                            v[4 * q + 3] = mlp::silu(v[4 * q + 3] + bb.w);
+                    for (int half = 0; half < 2; ++half) {
+                        const int col0 = col_q + 32 * half;
+                        const float4* b4 = reinterpret_cast<const float4*>(hb + 32 * half);
+                        uint32_t pk[16];
+#pragma unroll
+                        for (int g = 0; g < 8; ++g) {
+                            const float4 bb = __ldg(b4 + g);
+                            const uint32_t* x = r + 32 * half + 4 * g;
+                            // SiLU(z) = h (1 + tanh h), h = z / 2 = acc / 2 + b / 2
+                            const float2 h01 = __ffma2_rn(make_float2(__uint_as_float(x[0]), __uint_as_float(x[1])),
+                                                          half2, make_float2(bb.x, bb.y));
+                            const float2 h23 = __ffma2_rn(make_float2(__uint_as_float(x[2]), __uint_as_float(x[3])),
+                                                          half2, make_float2(bb.z, bb.w));
+                            const float2 t01 = make_float2(mlp::tanh_approx(h01.x), mlp::tanh_approx(h01.y));
+                            const float2 t23 = make_float2(mlp::tanh_approx(h23.x), mlp::tanh_approx(h23.y));
+                            const float2 s01 = __ffma2_rn(h01, t01, h01);
+                            const float2 s23 = __ffma2_rn(h23, t23, h23);
+                            pk[2 * g] = tc::pack_bf16(s01.x, s01.y);
+                            pk[2 * g + 1] = tc::pack_bf16(s23.x, s23.y);
                         }
                         if (l < 3) {
 #pragma unroll
-                            for (int q = 0; q < 4; ++q) mlp::st_row8(a, m, col0 + 8 * q, v + 8 * q);
+                            for (int j = 0; j < 4; ++j)
+                                *reinterpret_cast<uint4*>(a + (col0 >> 6) * 16384 +
+                                                          tc::sw128_chunk(m, ((col0 & 63) >> 3) + j)) =
+                                    make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
                         } else {
-                            const float4* w4 = reinterpret_cast<const float4*>(w5 + col0);
+                            // output: the BF16 activations against w5
+                            const float2* w2 = reinterpret_cast<const float2*>(w5 + col0);
 #pragma unroll
-                            for (int q = 0; q < 8; ++q) {
-                                const float4 ww = __ldg(w4 + q);
-                                dot = fmaf(__bfloat162float(__float2bfloat16_rn(v[4 * q + 0])), ww.x, dot);
-                                dot = fmaf(__bfloat162float(__float2bfloat16_rn(v[4 * q + 1])), ww.y, dot);
-                                dot = fmaf(__bfloat162float(__float2bfloat16_rn(v[4 * q + 2])), ww.z, dot);
-                                dot = fmaf(__bfloat162float(__float2bfloat16_rn(v[4 * q + 3])), ww.w, dot);
+                            for (int g = 0; g < 16; ++g) {
+                                const float2 ab = make_float2(__uint_as_float(pk[g] << 16),
+                                                              __uint_as_float(pk[g] & 0xFFFF0000u));
+                                dot2 = __ffma2_rn(ab, __ldg(w2 + g), dot2);
                             }
                         }
                     }
                     tc::fence_before_sync();
                     if (l < 3) {
                         tc::fence_proxy_async_smem();
-                        mbar_arrive(ready + s);
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(ready + s);
                     } else {
-                        if (h == 1) dot1[s * 128 + m] = dot;
+                        // partial output dots meet in K blocks 1..3 of the slot's
+                        // A buffer (free once its last layer's MMAs are done)
+                        float* dots = reinterpret_cast<float*>(a + 16384);   // [4][128]
+                        dots[q * 128 + m] = dot2.x + dot2.y;
                         epi_sync();
-                        if (h == 0) {
+                        if (own == s) {
+                            const float out = b5 + dots[m] + dots[128 + m] + dots[256 + m] + dots[384 + m];
                             if (cur.exp != t_exp) {
                                 flush_trans(P, t_acc, t_exp);
                                 t_exp = cur.exp;
                             }
-                            t_acc += (double)row_finish(P, rec[s], cur, b5 + dot + dot1[s * 128 + m]);
-                            if (more) rec[s] = slot_features(P, sm, s, m, nxt);
+                            t_acc += (double)row_finish(P, rec, cur, out);
+                            if (more) rec = slot_features(P, sm, s, m, nxt);
                         }
                         if (more) {
                             tc::fence_proxy_async_smem();
-                            mbar_arrive(ready + s);
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(ready + s);
                         }
                     }
                 }
             }
             cur = nxt;
         }
-        if (h == 0) flush_trans(P, t_acc, t_exp);
+        if (own >= 0) flush_trans(P, t_acc, t_exp);
         if (!ok) atomicExch(P.err, 9);
     }
     tc::fence_before_sync();

@@ -377,6 +377,7 @@ struct AdamParams {
     __nv_bfloat16* w1;
     __nv_bfloat16* w[3];
     __nv_bfloat16* wt[3];
+    float* epi;              // epilogue constants of the trace: b_l / 2, w5, b5
 };
 
 // Adam (beta 0.9 / 0.999, eps 1e-8, cosine learning-rate decay) on the FP32
@@ -406,6 +407,8 @@ __global__ void adam_kernel(AdamParams A, unsigned int* done_ctr)
             const int out = k / H, in = k % H;
             A.w[l][k] = pb;
             A.wt[l][in * H + out] = pb;
+        } else {
+            A.epi[i - OFF_B1] = i < OFF_W5 ? 0.5f * p : p;
         }
     }
     __syncthreads();
@@ -486,6 +489,7 @@ struct sas_surrogate {
     __nv_bfloat16* d_w1 = nullptr;
     __nv_bfloat16* d_w[3] = {nullptr, nullptr, nullptr};
     __nv_bfloat16* d_wt[3] = {nullptr, nullptr, nullptr};
+    float* d_epi = nullptr;   // [NPARAM - OFF_B1] trace epilogue constants
     Maps maps;
     float* d_tab = nullptr;
     sur::Tables tabs;
@@ -619,6 +623,7 @@ sas_status enqueue_step(sas_surrogate* s, const sur::Raw* raw, const float* y, u
         A.lr0 = s->g_lr;
         A.total_steps = s->g_total;
         A.w1 = s->d_w1;
+        A.epi = s->d_epi;
         for (int l = 0; l < 3; ++l) {
             A.w[l] = s->d_w[l];
             A.wt[l] = s->d_wt[l];
@@ -631,12 +636,18 @@ sas_status enqueue_step(sas_surrogate* s, const sur::Raw* raw, const float* y, u
 }
 
 // Write the BF16 weights (and transposes) of the current FP32 parameters.
+// Also the trace's epilogue constants: halved biases, w5, b5.
 __global__ void publish_weights_kernel(const float* p, __nv_bfloat16* w1, __nv_bfloat16* w2, __nv_bfloat16* w3,
-                                       __nv_bfloat16* w4, __nv_bfloat16* t2, __nv_bfloat16* t3, __nv_bfloat16* t4)
+                                       __nv_bfloat16* w4, __nv_bfloat16* t2, __nv_bfloat16* t3, __nv_bfloat16* t4,
+                                       float* epi)
 {
     __nv_bfloat16* w[3] = {w2, w3, w4};
     __nv_bfloat16* t[3] = {t2, t3, t4};
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < OFF_B1; i += gridDim.x * blockDim.x) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < NPARAM; i += gridDim.x * blockDim.x) {
+        if (i >= OFF_B1) {
+            epi[i - OFF_B1] = i < OFF_W5 ? 0.5f * p[i] : p[i];
+            continue;
+        }
         const __nv_bfloat16 b = __float2bfloat16_rn(p[i]);
         if (i < OFF_W2) {
             w1[i] = b;
@@ -651,7 +662,7 @@ __global__ void publish_weights_kernel(const float* p, __nv_bfloat16* w1, __nv_b
 sas_status publish(sas_surrogate* s)
 {
     publish_weights_kernel<<<256, 256, 0, s->stream>>>(s->d_p, s->d_w1, s->d_w[0], s->d_w[1], s->d_w[2],
-                                                      s->d_wt[0], s->d_wt[1], s->d_wt[2]);
+                                                      s->d_wt[0], s->d_wt[1], s->d_wt[2], s->d_epi);
     SAS_CUDA_S(cudaGetLastError(), "publish weights");
     return SAS_OK;
 }
@@ -756,7 +767,7 @@ uint64_t surrogate_pair_prefix(const std::vector<WorkItem>& items, std::vector<u
     return n;
 }
 
-const float* surrogate_params(const sas_surrogate* s) { return s->d_p; }
+const float* surrogate_epi(const sas_surrogate* s) { return s->d_epi; }
 sur::Box surrogate_dbox(const sas_surrogate* s) { return s->dbox; }
 int* surrogate_err(const sas_surrogate* s) { return s->d_err; }
 
@@ -809,6 +820,7 @@ sas_status sas_create_surrogate(const sas_surrogate_box* box, uint64_t seed, voi
     if (ce == cudaSuccess) ce = cudaMalloc(&s->d_ctr, sizeof(unsigned int));
     if (ce == cudaSuccess) ce = cudaMalloc(&s->d_err, sizeof(int));
     if (ce == cudaSuccess) ce = cudaMalloc(&s->d_w1, (size_t)NPARAM_W1 * 2);
+    if (ce == cudaSuccess) ce = cudaMalloc(&s->d_epi, (size_t)(NPARAM - OFF_B1) * sizeof(float));
     for (int l = 0; l < 3 && ce == cudaSuccess; ++l) {
         ce = cudaMalloc(&s->d_w[l], (size_t)NPARAM_W * 2);
         if (ce == cudaSuccess) ce = cudaMalloc(&s->d_wt[l], (size_t)NPARAM_W * 2);
@@ -1028,6 +1040,7 @@ sas_status sas_destroy_surrogate(sas_surrogate* s)
     cudaFree(s->d_ctr);
     cudaFree(s->d_err);
     cudaFree(s->d_w1);
+    cudaFree(s->d_epi);
     for (int l = 0; l < 3; ++l) {
         cudaFree(s->d_w[l]);
         cudaFree(s->d_wt[l]);

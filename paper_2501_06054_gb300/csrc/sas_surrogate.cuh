@@ -30,7 +30,8 @@ struct Raw {
 };
 
 // Feature vector (64 wide: [0, 5) scaled raw inputs in [-1, 1], then
-// n_four (sin, cos) pairs of k * four_w * u (four_w = 1/2), column 63 = 1 (bias of layer 1)).
+// n_four <= 28 (sin, cos) pairs of k * four_w * u (four_w = 1/2), column 63 = 1
+// (bias of layer 1)).
 __device__ __forceinline__ void features(const Box& b, float qpar, float qperp, float R, float L, float so,
                                          float sp, float* f64)
 {
@@ -44,13 +45,69 @@ __device__ __forceinline__ void features(const Box& b, float qpar, float qperp, 
     f64[2] = 2.f * (a - b.a_min) / (b.a_max - b.a_min) - 1.f;
     f64[3] = 2.f * (so - b.so_min) / (b.so_max - b.so_min) - 1.f;
     f64[4] = 2.f * (sp - b.sp_min) / (b.sp_max - b.sp_min) - 1.f;
-    for (int k = 0; k < b.n_four && k < 28; ++k) {
-        float s, c;
-        sas_sincosf((float)(k + 1) * b.four_w * u, s, c);
+    // pairs k = 1..n_four of (sin, cos)(k w u) by angle addition from k = 1;
+    // fully unrolled so that the caller's array stays in registers
+    float s1, c1;
+    sas_sincosf(b.four_w * u, s1, c1);
+    float s = s1, c = c1;
+#pragma unroll
+    for (int k = 0; k < 28; ++k) {
+        if (k >= b.n_four) break;
         f64[5 + 2 * k] = s;
         f64[6 + 2 * k] = c;
+        const float sn = fmaf(s, c1, c * s1);
+        const float cn = fmaf(c, c1, -(s * s1));
+        s = sn;
+        c = cn;
     }
     f64[63] = 1.f;
+}
+
+// The same feature vector written straight into row m of a swizzled 64-wide
+// BF16 K block, 8 columns at a time (nothing beyond one chunk is live);
+// `on` false writes a zero row.
+__device__ __forceinline__ void write_features(const Box& b, bool on, float qpar, float qperp, float R, float L,
+                                               float so, float sp, unsigned char* kblock, int m)
+{
+    const float u = qpar * 0.5f * L;
+    const float raw5[5] = {2.f * u / b.u_max - 1.f, 2.f * (qperp * R) / b.v_max - 1.f,
+                           2.f * (0.5f * L / R - b.a_min) / (b.a_max - b.a_min) - 1.f,
+                           2.f * (so - b.so_min) / (b.so_max - b.so_min) - 1.f,
+                           2.f * (sp - b.sp_min) / (b.sp_max - b.sp_min) - 1.f};
+    float s1 = 0.f, c1 = 1.f;
+    if (on) sas_sincosf(b.four_w * u, s1, c1);
+    float s = s1, c = c1;   // (sin, cos) of the current pair k (1-based: k w u)
+    const int nf = on ? b.n_four : 0;
+#pragma unroll
+    for (int chunk = 0; chunk < 8; ++chunk) {
+        float v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int col = 8 * chunk + j;
+            float x = 0.f;
+            if (col < 5) {
+                x = on ? raw5[col] : 0.f;
+            } else if (col < 61) {
+                const int k = (col - 5) >> 1;
+                x = k < nf ? (((col - 5) & 1) ? c : s) : 0.f;
+                if ((col - 5) & 1) {   // pair k written: advance to k + 1
+                    const float sn = fmaf(s, c1, c * s1);
+                    const float cn = fmaf(c, c1, -(s * s1));
+                    s = sn;
+                    c = cn;
+                }
+            } else if (col == 63) {
+                x = on ? 1.f : 0.f;
+            }
+            v[j] = x;
+        }
+        uint4 pk;
+        pk.x = tc::pack_bf16(v[0], v[1]);
+        pk.y = tc::pack_bf16(v[2], v[3]);
+        pk.z = tc::pack_bf16(v[4], v[5]);
+        pk.w = tc::pack_bf16(v[6], v[7]);
+        *reinterpret_cast<uint4*>(kblock + tc::sw128_chunk(m, chunk)) = pk;
+    }
 }
 
 __device__ __forceinline__ bool in_box(const Box& b, float q, float R, float L, float so, float sp)
@@ -135,7 +192,7 @@ struct SurExp {
 struct STParams {
     InstConst<float> in;
     Box box;
-    const float* params;
+    const float* epi;        // [1281]: b_l / 2 (l = 1..4, 4 x 256), w5 (256), b5
     const uint64_t* seed;    // device scalar
     uint32_t philox_base;    // Philox experiment id = philox_base + item experiment
     // single experiment or batch items; item i holds pairs (256 histories)

@@ -267,9 +267,14 @@ def test_surrogate_trace_tallies_the_network(n, first):
     assert np.array_equal(d["count"].ravel(), ref["count"].astype(np.uint64))
     got, exp_ = d["sum_w"].ravel(), ref["sum_w"]
     assert abs(got.sum() - exp_.sum()) <= 3e-3 * exp_.sum()
-    hit = ref["count"] >= 20
+    # pixels with many histories average the per-history BF16 differences;
+    # a short run has single-history pixels (bound of the network test)
+    few = n < 20 * inst.nx * inst.ny
+    hit = ref["count"] >= (1 if few else 20)
+    assert hit.sum() > 100
     rel = np.abs(got - exp_)[hit] / exp_[hit]
-    assert np.median(rel) < 3e-3 and rel.max() < 3e-2, (np.median(rel), rel.max())
+    assert np.median(rel) < (5e-3 if few else 3e-3), np.median(rel)
+    assert rel.max() < (8e-2 if few else 3e-2), rel.max()
     assert d["trans"] == pytest.approx(ref["trans"], rel=1e-5)
     e.close()
     sas.sas_destroy_surrogate(s)
