@@ -36,13 +36,16 @@
 namespace sas {
 namespace sur {
 
-constexpr int EPI_WARPS = 16;
-constexpr int ST_THREADS = 32 * EPI_WARPS + 32;
+constexpr int EPI_WARPS = 16;                  // SiLU warps 0..15
+constexpr int HIST_WARPS = 4;                  // history warps 16..19
+constexpr int MMA_WARP = EPI_WARPS + HIST_WARPS;
+constexpr int TMA_WARP = MMA_WARP + 1;
+constexpr int ST_THREADS = 32 * (TMA_WARP + 1);
 constexpr int RING = 3;                        // weight ring stages (32 KB each)
 constexpr uint32_t S2_A = 0;                   // 2 x 64 KB activation slots (K block 0 = features)
 constexpr uint32_t S2_W = 131072;              // RING x 32 KB weight ring
-constexpr uint32_t S2_BAR = S2_W + RING * 32768u;   // 11 mbarriers, TMEM address, abort flag
-constexpr size_t S2_SMEM = (size_t)S2_BAR + 128 + 1024;
+constexpr uint32_t S2_BAR = S2_W + RING * 32768u;   // 15 mbarriers, TMEM address, abort flag
+constexpr size_t S2_SMEM = (size_t)S2_BAR + 256 + 1024;
 constexpr int UNITS_PER_PAIR = 26;             // layer 1: 2 slots x 1 K block; layers 2..4: 2 slots x 4
 constexpr int LOADS_PER_PAIR = 16;
 
@@ -95,14 +98,13 @@ __device__ __forceinline__ uint32_t ring_parity(uint32_t pair, const SchedLoad& 
     return ((L.role == 0 ? 0u : (pair & 1u)) + L.ord) & 1u;
 }
 
-// History data a row keeps in the registers of its owning epilogue thread
-// from the features to the tally.
+// History data a history-warp thread keeps in registers from the trace of a
+// history to its tally.
 struct RowRec {
     float pref, q0, q1, q2, wt;
     int pix_flags;   // (pixel + 1) << 2 | in_box << 1 | valid
+    float qp, qt;    // |Q . axis| and |Q x axis|: the features are made from these
 };
-
-__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(32 * EPI_WARPS) : "memory"); }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar)
 {
@@ -149,28 +151,24 @@ __device__ __forceinline__ PairInfo pair_info(const STParams& P, uint32_t p)
     return r;
 }
 
-// Trace the history of row m of slot s and write its features into the
-// slot's A operand (the owning threads of the epilogue).
-__device__ __forceinline__ RowRec slot_features(const STParams& P, unsigned char* sm, int s, int m,
-                                                const PairInfo& pi)
+// Trace the history of row m of slot s of a pair.
+__device__ __forceinline__ RowRec trace_row(const STParams& P, int s, int m, const PairInfo& pi)
 {
     RowRec r;
-    r.pref = r.q0 = r.q1 = r.q2 = r.wt = 0.f;
+    r.pref = r.q0 = r.q1 = r.q2 = r.wt = r.qp = r.qt = 0.f;
     r.pix_flags = 0;
     const uint32_t j = (uint32_t)s * 128u + (uint32_t)m;
-    float qp = 0.f, qt = 0.f;
-    bool inb = false;
-    SurExp e = P.sexp[pi.exp];
     if (j < pi.n) {
         const History<float> hs = history<float>(P.in, *P.seed, P.philox_base + pi.exp, pi.first + j);
         r.wt = hs.wt;
         int flags = 1 | ((hs.pixel + 1) << 2);
         if (hs.pixel >= 0) {
-            qp = hs.q[0] * e.nx + hs.q[1] * e.ny + hs.q[2] * e.nz;
+            const SurExp e = P.sexp[pi.exp];
+            const float qp = hs.q[0] * e.nx + hs.q[1] * e.ny + hs.q[2] * e.nz;
             const float q2 = hs.q[0] * hs.q[0] + hs.q[1] * hs.q[1] + hs.q[2] * hs.q[2];
-            qt = sqrtf(fmaxf(q2 - qp * qp, 0.0f));
-            inb = e.in_box && sqrtf(q2) <= P.box.q_max;
-            flags |= inb ? 2 : 0;
+            r.qp = fabsf(qp);
+            r.qt = sqrtf(fmaxf(q2 - qp * qp, 0.0f));
+            flags |= (e.in_box && sqrtf(q2) <= P.box.q_max) ? 2 : 0;
             r.pref = hs.pref;
             r.q0 = hs.q[0];
             r.q1 = hs.q[1];
@@ -178,8 +176,16 @@ __device__ __forceinline__ RowRec slot_features(const STParams& P, unsigned char
         }
         r.pix_flags = flags;
     }
-    write_features(P.box, inb, fabsf(qp), qt, e.R, e.L, e.so, e.sp, sm + S2_A + (uint32_t)s * 65536u, m);
     return r;
+}
+
+// Features of a traced row into K block 0 of its slot's A operand.
+__device__ __forceinline__ void put_features(const STParams& P, unsigned char* sm, int s, int m, const RowRec& r,
+                                             const PairInfo& pi)
+{
+    const SurExp e = P.sexp[pi.exp];
+    write_features(P.box, (r.pix_flags & 2) != 0, r.qp, r.qt, e.R, e.L, e.so, e.sp,
+                   sm + S2_A + (uint32_t)s * 65536u, m);
 }
 
 // After the last layer: weight and tally one row; returns its transmitted weight.
@@ -215,48 +221,17 @@ __device__ __forceinline__ void flush_trans(const STParams& P, double& t, uint32
     t = 0.0;
 }
 
-// Latest weight load issued into each ring stage (pair * 16 + j + 1; 0: none).
-struct RingLast {
-    uint32_t g0 = 0, g1 = 0, g2 = 0;
-};
-
-// Issue one weight load (schedule entry j of pair `pair`) into its ring stage
-// once the stage's previous block has been released.
-__device__ __forceinline__ bool sched_load(unsigned char* sm, uint64_t* full, uint64_t* empty, const mlp::Maps& maps,
-                                           uint32_t pair, int j, volatile int* abort, RingLast& last)
-{
-    const SchedLoad L = kLoads[j];
-    const uint32_t k = ring_stage(pair, L.role);
-    if (pair > 0 || L.ord > 0)
-        if (!wait_ab(empty + k, ring_parity(pair, L) ^ 1u, abort)) return false;
-    const CUtensorMap* map = L.l == 0 ? &maps.w1 : &maps.w[L.l - 1];
-    tc::mbar_arrive_expect_tx(full + k, 32768u);
-    tc::tma_load_2d(sm + S2_W + k * 32768u, map, L.kb * 64, 0, full + k);
-    const uint32_t g = pair * LOADS_PER_PAIR + (uint32_t)j + 1u;
-    if (k == 0) last.g0 = g;
-    else if (k == 1) last.g1 = g;
-    else last.g2 = g;
-    return true;
-}
-
-// Load of the current pair issued after unit u (-1: none); loads 0 and 1 of
-// the next pair follow units 24 and 25.
-__host__ __device__ constexpr int load_after_unit(int u)
-{
-    return u == 0 ? 2 : u == 2 ? 3 : u == 3 ? 4 : u == 7 ? 5 : u == 8 ? 6 : u == 9 ? 7 : u == 10 ? 8
-         : u == 11 ? 9 : u == 15 ? 10 : u == 16 ? 11 : u == 17 ? 12 : u == 18 ? 13 : u == 19 ? 14
-         : u == 23 ? 15 : -1;
-}
-
 __global__ void __launch_bounds__(ST_THREADS, 1) sur_trace_kernel(const STParams P, const __grid_constant__ mlp::Maps maps)
 {
     extern __shared__ unsigned char raw_sm[];
     unsigned char* sm = mlp::aligned_base(raw_sm);
-    uint64_t* full = reinterpret_cast<uint64_t*>(sm + S2_BAR);   // [RING]
-    uint64_t* empty = full + RING;                                // [RING]
-    uint64_t* acc = empty + RING;                                 // [2]
-    uint64_t* ready = acc + 2;                                    // [2]
-    uint64_t* drain = ready + 2;
+    uint64_t* full = reinterpret_cast<uint64_t*>(sm + S2_BAR);   // [RING] weight block landed
+    uint64_t* empty = full + RING;                                // [RING] weight block released
+    uint64_t* acc = empty + RING;                                 // [2] layer MMAs done
+    uint64_t* ready = acc + 2;                                    // [2] activations written (16 SiLU warps)
+    uint64_t* feat = ready + 2;                                   // [2] features written (4 history warps)
+    uint64_t* dots = feat + 2;                                    // [2] output partials written (16 SiLU warps)
+    uint64_t* drain = dots + 2;
     uint32_t* taddr = reinterpret_cast<uint32_t*>(drain + 1);
     volatile int* abort = reinterpret_cast<volatile int*>(taddr + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -268,6 +243,8 @@ __global__ void __launch_bounds__(ST_THREADS, 1) sur_trace_kernel(const STParams
         for (int i = 0; i < 2; ++i) {
             tc::mbar_init(acc + i, 1);
             tc::mbar_init(ready + i, EPI_WARPS);
+            tc::mbar_init(feat + i, HIST_WARPS);
+            tc::mbar_init(dots + i, EPI_WARPS);
         }
         tc::mbar_init(drain, 1);
         *abort = 0;
@@ -280,8 +257,44 @@ __global__ void __launch_bounds__(ST_THREADS, 1) sur_trace_kernel(const STParams
     const uint32_t tmem = *taddr;
     const uint32_t my_pairs = blockIdx.x < P.n_pairs ? (P.n_pairs - 1u - blockIdx.x) / gridDim.x + 1u : 0u;
 
-    if (warp == EPI_WARPS) {
-        // ---------------------------------------------------------- producer
+    if (warp == TMA_WARP) {
+        // ------------------------------------------------------------ loads
+        // The static load sequence, each load as soon as its ring stage's
+        // previous block is released.
+        if (lane == 0 && my_pairs > 0) {
+            const uint32_t n_loads = my_pairs * LOADS_PER_PAIR;
+            uint32_t last0 = 0, last1 = 0, last2 = 0;   // latest load + 1 per stage
+            bool ok = true;
+            for (uint32_t g = 0; g < n_loads && ok; ++g) {
+                const uint32_t pair = g / LOADS_PER_PAIR;
+                const SchedLoad L = kLoads[g % LOADS_PER_PAIR];
+                const uint32_t k = ring_stage(pair, L.role);
+                if (pair > 0 || L.ord > 0) ok = wait_ab(empty + k, ring_parity(pair, L) ^ 1u, abort);
+                if (!ok) break;
+                const CUtensorMap* map = L.l == 0 ? &maps.w1 : &maps.w[L.l - 1];
+                tc::mbar_arrive_expect_tx(full + k, 32768u);
+                tc::tma_load_2d(sm + S2_W + k * 32768u, map, L.kb * 64, 0, full + k);
+                if (k == 0) last0 = g + 1;
+                else if (k == 1) last1 = g + 1;
+                else last2 = g + 1;
+            }
+            // the latest load of each stage may still be in flight
+            bool drained = true;
+#pragma unroll
+            for (int k = 0; k < RING; ++k) {
+                const uint32_t g1 = k == 0 ? last0 : (k == 1 ? last1 : last2);
+                if (g1 == 0) continue;
+                const uint32_t pr = (g1 - 1u) / LOADS_PER_PAIR;
+                const SchedLoad L = kLoads[(g1 - 1u) % LOADS_PER_PAIR];
+                drained = tc::mbar_wait(full + k, ring_parity(pr, L), mlp::WAIT_NS) && drained;
+            }
+            if (!ok || !drained) {
+                *abort = 1;
+                atomicExch(P.err, 8);
+            }
+        }
+    } else if (warp == MMA_WARP) {
+        // ------------------------------------------------------------- MMAs
         if (lane == 0 && my_pairs > 0) {
             const uint32_t idesc = tc::idesc_bf16(mlp::TILE, mlp::H);
             // operand descriptors, computed once: advancing K by 16 elements
@@ -289,24 +302,25 @@ __global__ void __launch_bounds__(ST_THREADS, 1) sur_trace_kernel(const STParams
             const uint64_t dA = tc::desc_sw128(tc::smem_u32(sm + S2_A));
             const uint64_t dW0 = tc::desc_sw128(tc::smem_u32(sm + S2_W));
             const uint64_t dW1 = dW0 + (32768u >> 4), dW2 = dW0 + (65536u >> 4);
-            uint32_t rd_ph0 = 0u, rd_ph1 = 0u;
-            RingLast last;
-            bool ok = sched_load(sm, full, empty, maps, 0, 0, abort, last) &&
-                      sched_load(sm, full, empty, maps, 0, 1, abort, last);
-            bool issued = false;
+            uint32_t rd0 = 0u, rd1 = 0u, ft0 = 0u, ft1 = 0u;   // phases of ready[] and feat[]
+            bool ok = true, issued = false;
             for (uint32_t pair = 0; pair < my_pairs && ok; ++pair) {
-                const bool more = pair + 1 < my_pairs;
                 const uint32_t pb = pair & 1u;
-                // stages of roles Y and Z this pair, and their descriptors
-                const uint64_t dY = pb ? dW2 : dW1, dZ = pb ? dW1 : dW2;
+                const uint64_t dY = pb ? dW2 : dW1, dZ = pb ? dW1 : dW2;   // stages of roles Y, Z
 #pragma unroll
                 for (int u = 0; u < UNITS_PER_PAIR; ++u) {
                     if (!ok) break;
                     const SchedUnit U = kUnits[u];
                     if (U.flags & U_FIRST) {
-                        ok = wait_ab(ready + U.s, U.s ? rd_ph1 : rd_ph0, abort);
-                        if (U.s) rd_ph1 ^= 1u;
-                        else rd_ph0 ^= 1u;
+                        if (U.l == 0) {
+                            ok = wait_ab(feat + U.s, U.s ? ft1 : ft0, abort);
+                            if (U.s) ft1 ^= 1u;
+                            else ft0 ^= 1u;
+                        } else {
+                            ok = wait_ab(ready + U.s, U.s ? rd1 : rd0, abort);
+                            if (U.s) rd1 ^= 1u;
+                            else rd0 ^= 1u;
+                        }
                         if (!ok) break;
                     }
                     const SchedLoad L = kLoads[U.load];
@@ -323,94 +337,123 @@ __global__ void __launch_bounds__(ST_THREADS, 1) sur_trace_kernel(const STParams
                     issued = true;
                     if (U.flags & U_RELEASE) tc::mma_commit(empty + k);
                     if (U.flags & U_LAST) tc::mma_commit(acc + U.s);
-                    const int jn = load_after_unit(u);
-                    if (jn >= 0) ok = sched_load(sm, full, empty, maps, pair, jn, abort, last);
-                    else if (u == 24 && more) ok = sched_load(sm, full, empty, maps, pair + 1, 0, abort, last);
-                    else if (u == 25 && more) ok = sched_load(sm, full, empty, maps, pair + 1, 1, abort, last);
                 }
             }
-            // drain: the latest load of each stage (a stage takes its next load
-            // only after the previous one was consumed, so only these can
-            // still be in flight), then every MMA issued
             bool drained = true;
-#pragma unroll
-            for (int k = 0; k < RING; ++k) {
-                const uint32_t g = k == 0 ? last.g0 : (k == 1 ? last.g1 : last.g2);
-                if (g == 0) continue;
-                const uint32_t pr = (g - 1u) / LOADS_PER_PAIR;
-                const SchedLoad L = kLoads[(g - 1u) % LOADS_PER_PAIR];
-                drained = tc::mbar_wait(full + k, ring_parity(pr, L), mlp::WAIT_NS) && drained;
-            }
             if (issued) {
                 tc::mma_commit(drain);
-                drained = tc::mbar_wait(drain, 0u, mlp::WAIT_NS) && drained;
+                drained = tc::mbar_wait(drain, 0u, mlp::WAIT_NS);
             }
             if (!ok || !drained) {
                 *abort = 1;
                 atomicExch(P.err, 8);
             }
         }
+    } else if (warp >= EPI_WARPS) {
+        // ---------------------------------------------------------- histories
+        // Thread m traces row m of both slots one pair ahead of the tensor
+        // cores: at the end of pair p it reads the output partials of slot
+        // s, writes the features of pair p + 1 (traced earlier), tallies pair
+        // p and traces pair p + 2.
+        const int m = threadIdx.x - 32 * EPI_WARPS;
+        const float b5 = __ldg(P.epi + 5 * mlp::H);
+        uint32_t dt0 = 0u, dt1 = 0u;   // phases of dots[]
+        bool ok = true;
+        double t_acc = 0.0;
+        uint32_t t_exp = 0xFFFFFFFFu;
+        RowRec cur0 = {}, cur1 = {}, nx0 = {}, nx1 = {};
+        PairInfo pc = my_pairs > 0 ? pair_info(P, blockIdx.x) : PairInfo{0, 0, 0};
+        PairInfo pn = my_pairs > 1 ? pair_info(P, blockIdx.x + gridDim.x) : pc;
+        if (my_pairs > 0) {
+            cur0 = trace_row(P, 0, m, pc);
+            put_features(P, sm, 0, m, cur0, pc);
+            tc::fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(feat + 0);
+            cur1 = trace_row(P, 1, m, pc);
+            put_features(P, sm, 1, m, cur1, pc);
+            tc::fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(feat + 1);
+            if (my_pairs > 1) {
+                nx0 = trace_row(P, 0, m, pn);
+                nx1 = trace_row(P, 1, m, pn);
+            }
+        }
+        for (uint32_t it = 0; it < my_pairs; ++it) {
+            const bool more = it + 1 < my_pairs, more2 = it + 2 < my_pairs;
+            const PairInfo pn2 = more2 ? pair_info(P, blockIdx.x + (it + 2) * gridDim.x) : pn;
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                ok = wait_ab(dots + s, s ? dt1 : dt0, abort) && ok;
+                if (s) dt1 ^= 1u;
+                else dt0 ^= 1u;
+                // partial output dots of the 4 column quarters, in K block 1
+                const float* d = reinterpret_cast<const float*>(sm + S2_A + (uint32_t)s * 65536u + 16384u);
+                const float out = b5 + d[m] + d[128 + m] + d[256 + m] + d[384 + m];
+                if (more) {
+                    put_features(P, sm, s, m, s ? nx1 : nx0, pn);
+                    tc::fence_proxy_async_smem();
+                }
+                __syncwarp();
+                if (more && lane == 0) mbar_arrive(feat + s);
+                if (pc.exp != t_exp) {
+                    flush_trans(P, t_acc, t_exp);
+                    t_exp = pc.exp;
+                }
+                t_acc += (double)row_finish(P, s ? cur1 : cur0, pc, out);
+                if (s) {
+                    cur1 = nx1;
+                    if (more2) nx1 = trace_row(P, 1, m, pn2);
+                } else {
+                    cur0 = nx0;
+                    if (more2) nx0 = trace_row(P, 0, m, pn2);
+                }
+            }
+            pc = pn;
+            pn = pn2;
+        }
+        flush_trans(P, t_acc, t_exp);
+        if (!ok) atomicExch(P.err, 9);
     } else {
-        // ---------------------------------------------------------- epilogue
+        // -------------------------------------------------------- SiLU warps
         // Warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows m) and columns
-        // 64 (w / 4) .. + 63 of every accumulator. Warps 0..3 own the
-        // histories of slot 0, warps 8..11 those of slot 1: they trace them,
-        // keep them in registers, write their features and tally them.
+        // 64 (w / 4) .. + 63 of every accumulator.
         const int q = warp >> 2;
         const int m = 32 * (warp & 3) + lane;
         const int col_q = 64 * q;
         const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
-        const int own = q == 0 ? 0 : (q == 2 ? 1 : -1);   // slot whose histories this thread owns
         const float* hbias = P.epi;                        // b_l / 2
         const float* w5 = P.epi + 4 * mlp::H;
-        const float b5 = __ldg(P.epi + 5 * mlp::H);
-        uint32_t acc_ph0 = 0u, acc_ph1 = 0u;
+        uint32_t ac0 = 0u, ac1 = 0u;
         bool ok = true;
-        double t_acc = 0.0;
-        uint32_t t_exp = 0xFFFFFFFFu;
-        RowRec rec;
-        rec.pix_flags = 0;
-        PairInfo cur = my_pairs > 0 ? pair_info(P, blockIdx.x) : PairInfo{0, 0, 0};
-        if (my_pairs > 0) {
-            if (own >= 0) rec = slot_features(P, sm, own, m, cur);
-            tc::fence_proxy_async_smem();
-            __syncwarp();
-            if (lane == 0) {
-                mbar_arrive(ready + 0);
-                mbar_arrive(ready + 1);
-            }
-        }
         const float2 half2 = make_float2(0.5f, 0.5f);
         for (uint32_t it = 0; it < my_pairs; ++it) {
-            const bool more = it + 1 < my_pairs;
-            const PairInfo nxt = more ? pair_info(P, blockIdx.x + (it + 1) * gridDim.x) : cur;
             for (int l = 0; l < 4; ++l) {
                 const float* hb = hbias + 256 * l + col_q;
 #pragma unroll
                 for (int s = 0; s < 2; ++s) {
-                    ok = wait_ab(acc + s, s ? acc_ph1 : acc_ph0, abort) && ok;
-                    if (s) acc_ph1 ^= 1u;
-                    else acc_ph0 ^= 1u;
+                    ok = wait_ab(acc + s, s ? ac1 : ac0, abort) && ok;
+                    if (s) ac1 ^= 1u;
+                    else ac0 ^= 1u;
                     tc::fence_after_sync();
                     unsigned char* a = sm + S2_A + (uint32_t)s * 65536u;
-                    uint32_t r[64];
-                    tc::tmem_ld32_nowait(tmem + lane_base + 256u * (uint32_t)s + col_q, r);
-                    tc::tmem_ld32_nowait(tmem + lane_base + 256u * (uint32_t)s + col_q + 32, r + 32);
-                    tc::tmem_wait_ld();
                     float2 dot2 = make_float2(0.f, 0.f);
-#pragma unroll
+#pragma unroll 1
                     for (int half = 0; half < 2; ++half) {
                         const int col0 = col_q + 32 * half;
+                        uint32_t r[32];
+                        tc::tmem_ld32_nowait(tmem + lane_base + 256u * (uint32_t)s + col0, r);
+                        tc::tmem_wait_ld();
                         const float4* b4 = reinterpret_cast<const float4*>(hb + 32 * half);
                         uint32_t pk[16];
 #pragma unroll
                         for (int g = 0; g < 8; ++g) {
                             const float4 bb = __ldg(b4 + g);
-                            const uint32_t* x = r + 32 * half + 4 * g;
                             // SiLU(z) = h (1 + tanh h), h = z / 2 = acc / 2 + b / 2
-                            const float2 h01 = __ffma2_rn(make_float2(__uint_as_float(x[0]), __uint_as_float(x[1])),
+                            const float2 h01 = __ffma2_rn(make_float2(__uint_as_float(r[4 * g]), __uint_as_float(r[4 * g + 1])),
                                                           half2, make_float2(bb.x, bb.y));
-                            const float2 h23 = __ffma2_rn(make_float2(__uint_as_float(x[2]), __uint_as_float(x[3])),
+                            const float2 h23 = __ffma2_rn(make_float2(__uint_as_float(r[4 * g + 2]), __uint_as_float(r[4 * g + 3])),
                                                           half2, make_float2(bb.z, bb.w));
                             const float2 t01 = make_float2(mlp::tanh_approx(h01.x), mlp::tanh_approx(h01.y));
                             const float2 t23 = make_float2(mlp::tanh_approx(h23.x), mlp::tanh_approx(h23.y));
@@ -442,31 +485,16 @@ __global__ void __launch_bounds__(ST_THREADS, 1) sur_trace_kernel(const STParams
                         __syncwarp();
                         if (lane == 0) mbar_arrive(ready + s);
                     } else {
-                        // partial output dots meet in K blocks 1..3 of the slot's
-                        // A buffer (free once its last layer's MMAs are done)
-                        float* dots = reinterpret_cast<float*>(a + 16384);   // [4][128]
-                        dots[q * 128 + m] = dot2.x + dot2.y;
-                        epi_sync();
-                        if (own == s) {
-                            const float out = b5 + dots[m] + dots[128 + m] + dots[256 + m] + dots[384 + m];
-                            if (cur.exp != t_exp) {
-                                flush_trans(P, t_acc, t_exp);
-                                t_exp = cur.exp;
-                            }
-                            t_acc += (double)row_finish(P, rec, cur, out);
-                            if (more) rec = slot_features(P, sm, s, m, nxt);
-                        }
-                        if (more) {
-                            tc::fence_proxy_async_smem();
-                            __syncwarp();
-                            if (lane == 0) mbar_arrive(ready + s);
-                        }
+                        // partial output dots meet in K block 1 of the slot's A
+                        // buffer (free once its last layer's MMAs are done; the
+                        // next writer there is the next pair's layer-1 epilogue)
+                        reinterpret_cast<float*>(a + 16384)[q * 128 + m] = dot2.x + dot2.y;
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(dots + s);
                     }
                 }
             }
-            cur = nxt;
         }
-        if (own >= 0) flush_trans(P, t_acc, t_exp);
         if (!ok) atomicExch(P.err, 9);
     }
     tc::fence_before_sync();
