@@ -1,25 +1,28 @@
 // Cylinder trace through the learned surrogate: warp-specialised, two
 // 128-history tiles ("slots") in flight per SM.
 //
-// 17 warps per CTA. Warp 16 is the producer: one lane streams the weight
-// K blocks (64 wide, 32 KB) through a 3-stage TMA ring and issues the
-// tcgen05 MMAs of slot 0 and slot 1 alternately into two TMEM accumulators
-// (columns 0..255 and 256..511). Warps 0..15 are the epilogue: for every
-// layer each reads a quarter of the slot's accumulator (row m = TMEM lane m,
-// warp w: lanes 32 (w % 4).., columns 64 (w / 4)..), adds the bias, applies
-// SiLU and writes the BF16 activations back as the next layer's A operand,
-// or, after the last layer, reduces against w5. Warps 0..3 own the histories
-// of slot 0 and warps 8..11 those of slot 1: they trace them, write their
-// features and, after the last layer, weight and tally them. While the
-// epilogue works on one slot the tensor cores work on the other; sixteen
-// warps keep the MUFU (tanh) pipe, the epilogue's bound, busy.
+// 22 warps per CTA, in four roles:
+// - MMA warp (0): one lane issues the tcgen05 MMAs of slot 0 and slot 1
+//   alternately into two TMEM accumulators (columns 0..255, 256..511);
+// - TMA warp (1): one lane streams the weight K blocks (64 wide, 32 KB)
+//   through a 3-stage ring in a static order;
+// - SiLU warps (4..19): each reads a quarter of a slot's accumulator (row m
+//   = TMEM lane m; lanes 32 (w % 4).., columns 64 ((w - 4) / 4)..), adds the
+//   bias, applies SiLU and writes the BF16 activations back as the next
+//   layer's A operand, or after the last layer reduces against w5; sixteen
+//   warps keep the MUFU (tanh) pipe, their bound, busy;
+// - history warps (2, 3, 20, 21): thread m traces row m of both slots one
+//   pair ahead, writes the features and tallies the weighted histories.
+// While the SiLU warps work on one slot the tensor cores work on the other.
 //
 // Synchronisation (mbarriers):
-//   full[st]   TMA of ring stage st landed                  (producer waits)
-//   empty[st]  MMAs reading stage st's block finished        (producer waits)
-//   acc[s]     the layer MMAs of slot s finished             (epilogue waits)
-//   ready[s]   slot s's A operand written, TMEM read (16)    (producer waits)
-//   drain      every MMA issued finished                    (producer, at exit)
+//   full[st]   TMA of ring stage st landed                     (MMA warp waits)
+//   empty[st]  MMAs reading stage st's block finished          (TMA warp waits)
+//   acc[s]     the layer MMAs of slot s finished               (SiLU warps wait)
+//   ready[s]   activations of slot s written, TMEM read (16)   (MMA warp waits)
+//   dots[s]    output partials of slot s written, TMEM read (16) (history warps)
+//   feat[s]    features of slot s's next pair written (4)      (MMA warp waits)
+//   drain      every MMA issued finished                       (MMA warp, at exit)
 // Every wait gives up after WAIT_NS or once another thread has given up
 // (a shared abort flag); the loops keep their trip counts so that the
 // epilogue's named barrier stays matched, the producer drains its copies and
@@ -36,11 +39,20 @@
 namespace sas {
 namespace sur {
 
-constexpr int EPI_WARPS = 16;                  // SiLU warps 0..15
-constexpr int HIST_WARPS = 4;                  // history warps 16..19
-constexpr int MMA_WARP = EPI_WARPS + HIST_WARPS;
-constexpr int TMA_WARP = MMA_WARP + 1;
-constexpr int ST_THREADS = 32 * (TMA_WARP + 1);
+// Warp roles. The single-lane MMA and TMA issuers take the oldest warps 0
+// and 1 (measured faster than placing them last); the SiLU warps 4..19 keep
+// warp % 4 equal to their TMEM lane group; history warps 2, 3, 20, 21.
+constexpr int MMA_WARP = 0;
+constexpr int TMA_WARP = 1;
+constexpr int EPI_WARP0 = 4;                   // SiLU warps 4..19
+constexpr int EPI_WARPS = 16;
+constexpr int HIST_WARPS = 4;
+constexpr int ST_THREADS = 32 * 22;
+
+__device__ __forceinline__ int hist_index(int warp)   // 0..3 for history warps, else -1
+{
+    return warp == 2 ? 0 : warp == 3 ? 1 : (warp == 20 || warp == 21) ? warp - 18 : -1;
+}
 constexpr int RING = 3;                        // weight ring stages (32 KB each)
 constexpr uint32_t S2_A = 0;                   // 2 x 64 KB activation slots (K block 0 = features)
 constexpr uint32_t S2_W = 131072;              // RING x 32 KB weight ring
@@ -349,13 +361,13 @@ __global__ void __launch_bounds__(ST_THREADS, 1) sur_trace_kernel(const STParams
                 atomicExch(P.err, 8);
             }
         }
-    } else if (warp >= EPI_WARPS) {
+    } else if (hist_index(warp) >= 0) {
         // ---------------------------------------------------------- histories
         // Thread m traces row m of both slots one pair ahead of the tensor
-        // cores: at the end of pair p it reads the output partials of slot
-        // s, writes the features of pair p + 1 (traced earlier), tallies pair
-        // p and traces pair p + 2.
-        const int m = threadIdx.x - 32 * EPI_WARPS;
+        // cores: at the end of pair p it reads the output partials of each
+        // slot, writes that slot's features of pair p + 1 (traced earlier)
+        // and tallies pair p; then it traces pair p + 2.
+        const int m = 32 * hist_index(warp) + lane;
         const float b5 = __ldg(P.epi + 5 * mlp::H);
         uint32_t dt0 = 0u, dt1 = 0u;   // phases of dots[]
         bool ok = true;
@@ -402,13 +414,14 @@ __global__ void __launch_bounds__(ST_THREADS, 1) sur_trace_kernel(const STParams
                     t_exp = pc.exp;
                 }
                 t_acc += (double)row_finish(P, s ? cur1 : cur0, pc, out);
-                if (s) {
-                    cur1 = nx1;
-                    if (more2) nx1 = trace_row(P, 1, m, pn2);
-                } else {
-                    cur0 = nx0;
-                    if (more2) nx0 = trace_row(P, 0, m, pn2);
-                }
+            }
+            // both slots handed over: trace pair p + 2 while the tensor cores
+            // and SiLU warps run pair p + 1
+            cur0 = nx0;
+            cur1 = nx1;
+            if (more2) {
+                nx0 = trace_row(P, 0, m, pn2);
+                nx1 = trace_row(P, 1, m, pn2);
             }
             pc = pn;
             pn = pn2;
@@ -418,8 +431,8 @@ __global__ void __launch_bounds__(ST_THREADS, 1) sur_trace_kernel(const STParams
     } else {
         // -------------------------------------------------------- SiLU warps
         // Warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows m) and columns
-        // 64 (w / 4) .. + 63 of every accumulator.
-        const int q = warp >> 2;
+        // 64 ((w - 4) / 4) .. + 63 of every accumulator.
+        const int q = (warp - EPI_WARP0) >> 2;
         const int m = 32 * (warp & 3) + lane;
         const int col_q = 64 * q;
         const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
