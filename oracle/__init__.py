@@ -80,7 +80,9 @@ class _Model(ctypes.Structure):
                [(n, ctypes.c_double) for n in (
                    "radius", "thickness", "length", "radius_polar", "sld", "sld_shell",
                    "sld_solvent", "volume_fraction", "sq_radius", "sq_fraction")] + \
-               [("poly_r", _DP), ("poly_w", _DP), ("orient_c", _DP), ("orient_w", _DP)]
+               [("poly_r", _DP), ("poly_w", _DP), ("orient_c", _DP), ("orient_w", _DP)] + \
+               [("event", ctypes.c_int64), ("orient_mode", ctypes.c_int64), ("poly", ctypes.c_double),
+                ("axis_theta", ctypes.c_double), ("axis_phi", ctypes.c_double)]
 
 
 def lib():
@@ -109,6 +111,14 @@ def lib():
             L.oracle_geometry_records.argtypes = [ctypes.POINTER(_Instrument), ctypes.c_uint64,
                                                   ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64,
                                                   ctypes.POINTER(ctypes.c_int64), _DP, _DP, _DP]
+            L.oracle_erfcinv.argtypes = [ctypes.c_double]
+            L.oracle_erfcinv.restype = ctypes.c_double
+            L.oracle_event_radius.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_uint32]
+            L.oracle_event_radius.restype = ctypes.c_double
+            L.oracle_event_axis.argtypes = [ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_uint32,
+                                            ctypes.c_uint32, _DP]
+            L.oracle_dsigma_event_many.argtypes = [ctypes.POINTER(_Model), _DP, ctypes.c_uint64, ctypes.c_uint32,
+                                                   ctypes.c_uint64, ctypes.c_int64, _DP]
             L.oracle_num_threads.restype = ctypes.c_int
             L.oracle_sample_lambda.argtypes = [ctypes.c_double] * 3
             L.oracle_sample_lambda.restype = ctypes.c_double
@@ -155,6 +165,41 @@ def schulz_nodes(mean: float, p: float, n: int):
     return mean * x / (z + 1.0), w
 
 
+def gaussian_nodes(mean: float, p: float, n: int):
+    """Nodes and normalised weights of the Gaussian N(mean, (p mean)^2)
+    restricted to positive values (Sec. II.B): Gauss-Legendre on
+    [max(0, mean (1 - 8p)), mean (1 + 8p)] weighted by the density; the
+    mass beyond 8 sigma is below 1e-15. p == 0 or n == 1 gives the mean."""
+    if p <= 0.0 or n <= 1:
+        return np.array([float(mean)]), np.array([1.0])
+    a, b = max(0.0, mean * (1.0 - 8.0 * p)), mean * (1.0 + 8.0 * p)
+    x, w = gauss_legendre(n)
+    r = 0.5 * (b - a) * (x + 1.0) + a
+    wr = 0.5 * (b - a) * w * np.exp(-0.5 * ((r - mean) / (p * mean)) ** 2)
+    return r, wr / wr.sum()
+
+
+def radius_nodes(m):
+    """Nodes of the polydisperse radius for the model's distribution
+    (poly_dist 0: Schulz, 1: Gaussian restricted to r > 0)."""
+    if int(m.get("poly_dist", 0)) == 1:
+        return gaussian_nodes(m["radius"], m["poly"], int(m["n_poly"]))
+    return schulz_nodes(m["radius"], m["poly"], int(m["n_poly"]))
+
+
+def uniform_angle_nodes(n_theta, n_phi):
+    """Axis nodes for theta ~ U[0, pi], phi ~ U[0, 2 pi] (Sec. II.B; uniform
+    in the angles, so not uniform on the sphere): Gauss-Legendre in both."""
+    xt, wt = gauss_legendre(n_theta)
+    xp, wp = gauss_legendre(n_phi)
+    th = 0.5 * math.pi * (xt + 1.0)
+    ph = math.pi * (xp + 1.0)
+    T, P = np.meshgrid(th, ph, indexing="ij")
+    c = np.stack([np.sin(T) * np.cos(P), np.sin(T) * np.sin(P), np.cos(T)], axis=-1)
+    W = np.outer(wt, wp).reshape(-1)
+    return c.reshape(-1, 3), W / W.sum()
+
+
 def axis_from_angles(theta: float, phi: float):
     n = np.array([math.sin(theta) * math.cos(phi), math.sin(theta) * math.sin(phi),
                   math.cos(theta)])
@@ -196,11 +241,14 @@ class Prepared:
         m = model if isinstance(model, dict) else model.as_dict()
         self.m = m
         kind = int(m["kind"])
-        self.poly_r, self.poly_w = schulz_nodes(m["radius"], m["poly"], int(m["n_poly"]))
-        if kind in (2, 3):
+        self.poly_r, self.poly_w = radius_nodes(m)
+        iso = int(m["isotropic"])
+        if kind in (2, 3) and iso == 2:
+            self.orient_c, self.orient_w = uniform_angle_nodes(int(m["n_gamma"]), int(m["n_psi"]))
+        elif kind in (2, 3):
             self.orient_c, self.orient_w = orientation_nodes(
                 m["axis_theta"], m["axis_phi"], m["sigma_orient"], int(m["n_gamma"]),
-                int(m["n_psi"]), bool(m["isotropic"]))
+                int(m["n_psi"]), bool(iso))
         else:
             self.orient_c, self.orient_w = np.zeros((1, 3)), np.ones(1)
         self.poly_r = np.ascontiguousarray(self.poly_r, dtype=np.float64)
@@ -217,7 +265,9 @@ class Prepared:
                         poly_r=self.poly_r.ctypes.data_as(_DP),
                         poly_w=self.poly_w.ctypes.data_as(_DP),
                         orient_c=self.orient_c.ctypes.data_as(_DP),
-                        orient_w=self.orient_w.ctypes.data_as(_DP))
+                        orient_w=self.orient_w.ctypes.data_as(_DP),
+                        event=int(m.get("sampling", 0)), orient_mode=iso, poly=float(m["poly"]),
+                        axis_theta=float(m["axis_theta"]), axis_phi=float(m["axis_phi"]))
 
 
 def _inst(instrument):
@@ -305,6 +355,33 @@ def geometry_records(instrument, n, seed, first=0, exp_id=0):
                                   pix.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                                   q.ctypes.data_as(_DP), pref.ctypes.data_as(_DP), wt.ctypes.data_as(_DP))
     return dict(pixel=pix, q=q, pref=pref, trans=wt)
+
+
+def erfcinv(y):
+    return lib().oracle_erfcinv(float(y))
+
+
+def event_radius(mean, p, word):
+    """Radius drawn by the per-event estimator from the 32-bit Philox word."""
+    return lib().oracle_event_radius(float(mean), float(p), int(word) & 0xFFFFFFFF)
+
+
+def event_axis(mode, theta, phi, word_a, word_b):
+    c = np.empty(3)
+    lib().oracle_event_axis(int(mode), float(theta), float(phi), int(word_a) & 0xFFFFFFFF,
+                            int(word_b) & 0xFFFFFFFF, c.ctypes.data_as(_DP))
+    return c
+
+
+def dsigma_event(model, q, seed, first=0, exp_id=0):
+    """Per-event estimates of dSigma/dOmega (1/angstrom) at q [n][3]; row i
+    uses the draws of neutron index first + i."""
+    prep = model if isinstance(model, Prepared) else Prepared(model)
+    q = np.ascontiguousarray(q, dtype=np.float64).reshape(-1, 3)
+    out = np.empty(len(q))
+    lib().oracle_dsigma_event_many(ctypes.byref(prep.c), q.ctypes.data_as(_DP), int(seed), int(exp_id),
+                                   int(first), len(q), out.ctypes.data_as(_DP))
+    return out
 
 
 def sample_lambda(lambda0, drel, u):

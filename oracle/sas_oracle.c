@@ -66,6 +66,8 @@ void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t
 
 /* uniform on (0,1): 23 random bits plus one half, exact in float and double */
 static double u01(uint32_t x) { return ((double)(x >> 9) + 0.5) * (1.0 / 8388608.0); }
+/* 1 - u01(x), also exact */
+static double u01c(uint32_t x) { return ((double)(8388607u - (x >> 9)) + 0.5) * (1.0 / 8388608.0); }
 
 /* ------------------------------------------------------------ structures */
 
@@ -91,6 +93,14 @@ typedef struct {
     const double *poly_w;  /* [n_poly] normalised weights */
     const double *orient_c;/* [n_orient][3] particle axis unit vectors */
     const double *orient_w;/* [n_orient] normalised weights */
+    /* per-event sampling (Sec. II.B): each history draws one radius and one
+     * axis instead of averaging over the nodes above, which then serve only
+     * for <V> of the radius distribution */
+    int64_t event;         /* 0: quadrature average, 1: per-event draws */
+    int64_t orient_mode;   /* axis draw: 0 fixed mean axis, 1 uniform on the sphere,
+                              2 theta ~ U[0, pi], phi ~ U[0, 2 pi] */
+    double poly;           /* sigma / mean of the Gaussian radius (0: monodisperse) */
+    double axis_theta, axis_phi;   /* fixed axis (orient_mode 0) */
 } oracle_model;
 
 /* --------------------------------------------------------- model pieces */
@@ -266,6 +276,111 @@ void oracle_dsigma_many(const oracle_model *m, const double *q, int64_t n, doubl
     for (int64_t i = 0; i < n; ++i) out[i] = oracle_dsigma(m, q + 3 * i);
 }
 
+/* ------------------------------------------------- per-event sampling */
+
+/* Inverse complementary error function on (0, 2): the x with erfc(x) = y,
+ * by bisection on the monotone erfc to 1e-6 and Newton steps on
+ * erfc(x) - y (derivative -2/sqrt(pi) exp(-x^2)) to full precision. */
+double oracle_erfcinv(double y)
+{
+    if (!(y > 0.0 && y < 2.0)) return y <= 0.0 ? INFINITY : -INFINITY;
+    double lo = -27.0, hi = 27.0;           /* erfc(lo) = 2, erfc(hi) = 0 to double range */
+    while (hi - lo > 1e-6) {
+        double mid = 0.5 * (lo + hi);
+        if (erfc(mid) > y) lo = mid; else hi = mid;
+    }
+    double x = 0.5 * (lo + hi);
+    for (int it = 0; it < 8; ++it) {
+        double f = erfc(x) - y;
+        double d = -2.0 / sqrt(PI) * exp(-x * x);
+        if (d == 0.0) break;
+        double step = f / d;
+        x -= step;
+        if (fabs(step) <= 1e-16 * fabs(x)) break;
+    }
+    return x;
+}
+
+/* Polydisperse radius of one event: Gaussian N(R, (p R)^2) restricted to
+ * R > 0 (Sec. II.B: non-positive draws are redrawn). The restricted law is
+ * sampled by inversion, z = Phi^-1(lo + u (1 - lo)) with lo = Phi(-1/p) and
+ * Phi^-1(v) = -sqrt(2) erfcinv(2 v); u and 1 - u are both exact, and the
+ * upper half uses 1 - v = (1 - u)(1 - lo) so neither tail loses digits.  */
+double oracle_event_radius(double R, double p, uint32_t x)
+{
+    if (p <= 0.0) return R;
+    double lo = 0.5 * erfc(1.0 / (p * sqrt(2.0)));
+    double u = u01(x), uc = u01c(x);
+    double v = lo + u * (1.0 - lo), z;
+    if (v < 0.5) z = -sqrt(2.0) * oracle_erfcinv(2.0 * v);
+    else z = sqrt(2.0) * oracle_erfcinv(2.0 * uc * (1.0 - lo));
+    if (SAS_MUT == 12) z = -sqrt(2.0) * oracle_erfcinv(2.0 * u);   /* drops the restriction */
+    return R * (1.0 + p * z);
+}
+
+/* Particle axis of one event from two uniforms (Sec. II.B): mode 1 uniform
+ * on the sphere (cos theta = 1 - 2 u), mode 2 theta = pi u, phi = 2 pi u'. */
+void oracle_event_axis(int64_t mode, double theta0, double phi0, uint32_t xa, uint32_t xb, double c[3])
+{
+    double ct, st;
+    if (mode == 1) {
+        ct = 1.0 - 2.0 * u01(xa);
+        st = sqrt(fmax(0.0, 1.0 - ct * ct));
+    } else if (mode == 2) {
+        double th = PI * u01(xa);
+        ct = cos(th); st = sin(th);
+    } else {
+        ct = cos(theta0); st = sin(theta0);
+        c[0] = st * cos(phi0); c[1] = st * sin(phi0); c[2] = ct;
+        return;
+    }
+    double ph = 2.0 * PI * u01(xb);
+    c[0] = st * cos(ph); c[1] = st * sin(ph); c[2] = ct;
+}
+
+/* Volume of one particle of the polydisperse parameter r (the quantity the
+ * cross section is normalised by through <V>). */
+static double model_volume(const oracle_model *m, double r)
+{
+    if (m->kind == 0) return sphere_volume(r);
+    if (m->kind == 1) return sphere_volume(r + m->thickness);
+    if (m->kind == 2) return PI * r * r * m->length;
+    return 4.0 / 3.0 * PI * m->radius_polar * r * r;
+}
+
+/* Per-event estimate of dSigma/dOmega(Q): (phi / <V>) |F(Q; r, c)|^2 S(Q)
+ * for the radius r and axis c drawn from Philox block 2 of the history
+ * (words: radius, axis polar, axis azimuth, spare). <V> is the mean over
+ * the radius distribution (the model's nodes). Its expectation over the
+ * draws is the quadrature average of oracle_dsigma with matching nodes. */
+double oracle_dsigma_event(const oracle_model *m, const double q[3], uint64_t seed,
+                           uint32_t exp_id, uint64_t index)
+{
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t c2[4] = {2u, exp_id, (uint32_t)index, (uint32_t)(index >> 32)};
+    uint32_t x[4];
+    oracle_philox4x32_10(c2, key, x);
+    double r = oracle_event_radius(m->radius, m->poly, x[0]);
+    double c[3];
+    oracle_event_axis(m->kind >= 2 ? m->orient_mode : 0, m->axis_theta, m->axis_phi, x[1], x[2], c);
+    double one = 1.0;
+    oracle_model single = *m;
+    single.n_poly = 1; single.poly_r = &r; single.poly_w = &one;
+    single.n_orient = 1; single.orient_c = c; single.orient_w = &one;
+    double vmean = 0.0;
+    for (int64_t i = 0; i < m->n_poly; ++i) vmean += m->poly_w[i] * model_volume(m, m->poly_r[i]);
+    /* oracle_dsigma of the single node carries phi / V(r); rescale to phi / <V> */
+    return oracle_dsigma(&single, q) * model_volume(m, r) / vmean;
+}
+
+void oracle_dsigma_event_many(const oracle_model *m, const double *q, uint64_t seed, uint32_t exp_id,
+                              uint64_t first, int64_t n, double *out)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i)
+        out[i] = oracle_dsigma_event(m, q + 3 * i, seed, exp_id, first + (uint64_t)i);
+}
+
 /* ------------------------------------------------------------- geometry */
 
 /* source wavelength from one uniform: triangular on [l0 (1-d), l0 (1+d)],
@@ -374,7 +489,8 @@ int oracle_history(const oracle_instrument *in, const oracle_model *m, uint64_t 
 {
     double l, domega, att, q[3];
     if (!history_geometry(in, seed, exp_id, index, pixel, &l, &domega, &att, q, w_trans)) return 0;
-    double ds = oracle_dsigma(m, q) * 1e10; /* 1/angstrom -> 1/m */
+    double ds = (m->event ? oracle_dsigma_event(m, q, seed, exp_id, index) : oracle_dsigma(m, q))
+              * 1e10; /* 1/angstrom -> 1/m */
     *w = l * ds * domega * att;
     return 1;
 }

@@ -39,6 +39,9 @@ MODEL_NAMES = {SPHERE: "sphere", CORE_SHELL: "core_shell", CYLINDER: "cylinder",
                ELLIPSOID: "ellipsoid"}
 SQ_NONE, SQ_HARD_SPHERE_PY = 0, 1
 FP32, FP64 = 0, 1
+QUADRATURE, PER_EVENT = 0, 1              # sampling: averages over nodes / one draw per history
+SCHULZ, GAUSSIAN = 0, 1                   # poly_dist of the polydisperse radius
+CAP, ISOTROPIC, UNIFORM_ANGLES = 0, 1, 2  # isotropic: axis distribution of uniaxial models
 
 
 @dataclass
@@ -71,7 +74,7 @@ class Model:
     n_poly: int = 1
     n_gamma: int = 1
     n_psi: int = 1
-    isotropic: int = 0
+    isotropic: int = CAP             # CAP (Gaussian about the mean axis), ISOTROPIC, UNIFORM_ANGLES
     radius: float = 50.0            # sphere R, core radius, cylinder R, ellipsoid equatorial R
     thickness: float = 0.0          # core-shell shell thickness
     length: float = 0.0             # cylinder length
@@ -86,6 +89,8 @@ class Model:
     axis_phi: float = 0.0           # rad, azimuth of the mean axis
     sq_radius: float = 0.0
     sq_fraction: float = 0.0
+    sampling: int = QUADRATURE      # PER_EVENT: one radius and axis drawn per history (Sec. II.B)
+    poly_dist: int = SCHULZ         # GAUSSIAN: N(R, (poly R)^2) restricted to R > 0
 
     def as_dict(self):
         return asdict(self)

@@ -25,15 +25,18 @@ MUTATIONS = {
     8: ("solid angle with 1/r instead of 1/r^2", "ideal_beam or finite_beam"),
     10: ("Philox multiplier typo", "philox"),
     11: ("core-shell outer term with the core volume", "core_shell"),
+    12: ("per-event radius drawn without the positivity restriction", "restricted_gaussian",
+         "test_event_oracle.py"),
 }
 
 
 @pytest.mark.parametrize("k", sorted(MUTATIONS))
 def test_pins_catch_planted_mistake(k):
-    desc, sel = MUTATIONS[k]
+    desc, sel = MUTATIONS[k][:2]
+    pins = MUTATIONS[k][2] if len(MUTATIONS[k]) > 2 else "test_oracle_pins.py"
     env = dict(os.environ, SAS_ORACLE_MUTATION=str(k))
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py"), "-k", sel],
+                        os.path.join(ROOT, "tests", pins), "-k", sel],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
     assert r.returncode == 1, f"mutation {k} ({desc}) was not caught:\n{r.stdout[-2000:]}"
     assert "failed" in r.stdout
