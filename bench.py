@@ -281,7 +281,57 @@ def secondary(stream, info):
         "speedup_batched_vs_plain": ms_plain / ms_b, "surrogate_fallbacks": fb,
         "work_items": ib["n_items"]}
     sas.sas_destroy_surrogate(sur)
+    out["per_event"] = per_event(stream)
     return out
+
+
+def _bin_rel_err(d, n):
+    """Median relative standard error of the bins holding >= 1e-3 of the
+    largest bin: sqrt(sum w^2 - (sum w)^2 / n) / sum w."""
+    sw, sw2 = d["sum_w"].ravel(), d["sum_w2"].ravel()
+    big = sw >= 1e-3 * sw.max()
+    var = np.maximum(sw2[big] - sw[big] ** 2 / n, 0.0)
+    return float(np.median(np.sqrt(var) / sw[big]))
+
+
+def per_event(stream):
+    """The paper's per-event estimator (Sec. II.B: one Gaussian radius and
+    one axis drawn per history) against the quadrature over the same laws:
+    histories/s of each, the per-bin relative standard error of each after
+    the same number of histories, and the ratio of the figures of merit
+    1 / (err^2 t) at equal work."""
+    import paper_2501_06054_gb300 as sas
+    cs = W.core_shell_config()["model"].as_dict()
+    cy = W.cylinder_config()["model"].as_dict()
+    cases = {
+        "core_shell": (W.core_shell_config()["instrument"],
+                       dict(cs, poly_dist=W.GAUSSIAN),
+                       "core-shell 40+10 A, Gaussian 0.1 on the core radius (40 nodes for the quadrature), "
+                       "Percus-Yevick phi 0.2, 128x128", 200_000_000, 20_000_000),
+        "cylinder": (W.cylinder_config()["instrument"],
+                     dict(cy, poly_dist=W.GAUSSIAN, isotropic=W.UNIFORM_ANGLES),
+                     "cylinder R=20 L=400 A, Gaussian 0.1 on R (40 nodes), axis theta ~ U[0,pi], phi ~ U[0,2pi] "
+                     "(76x76 nodes for the quadrature), 256x256", 200_000_000, 2_000_000),
+    }
+    res = {}
+    for name, (inst, base, desc, n_ev, n_q) in cases.items():
+        row = {"workload": desc, "unit": UNIT}
+        errs = {}
+        for mode, n_time in (("per_event", n_ev), ("quadrature", n_q)):
+            m = W.Model(**dict(base, sampling=W.PER_EVENT if mode == "per_event" else W.QUADRATURE))
+            e = sas.Experiment(inst, m, stream=stream)
+            e.trace(min(n_time, 1_000_000), 1)
+            ms = _events_ms(lambda: e.trace(n_time, 1), stream)
+            e.trace(n_q, 2)   # the same histories for both estimators
+            errs[mode] = _bin_rel_err(e.read(), n_q)
+            row[mode] = {"value": n_time / (ms * 1e-3), "histories_timed": n_time,
+                         "median_bin_rel_err": errs[mode]}
+            e.close()
+        row["histories_for_error"] = n_q
+        row["fom_ratio_per_event_vs_quadrature"] = (row["per_event"]["value"] / row["quadrature"]["value"]) * \
+            (errs["quadrature"] / errs["per_event"]) ** 2
+        res[name] = row
+    return res
 
 
 def run_single_workload(args):

@@ -58,6 +58,13 @@ typedef enum sas_status {
 enum { SAS_SPHERE = 0, SAS_CORE_SHELL = 1, SAS_CYLINDER = 2, SAS_ELLIPSOID = 3 };
 enum { SAS_SQ_NONE = 0, SAS_SQ_HARD_SPHERE_PY = 1 };
 enum { SAS_FP32 = 0, SAS_FP64 = 1 };
+/* sampling: average every history over the quadrature nodes, or draw one
+ * polydisperse radius and one particle axis per history (the paper's
+ * per-event estimator, Sec. II.B) */
+enum { SAS_QUADRATURE = 0, SAS_PER_EVENT = 1 };
+/* law of the polydisperse radius: Schulz, or the Gaussian of Sec. II.B
+ * restricted to positive radii */
+enum { SAS_POLY_SCHULZ = 0, SAS_POLY_GAUSSIAN = 1 };
 
 /* Instrument (Sec. II.A: source, collimation, sample, 2D PSD). */
 typedef struct sas_instrument {
@@ -86,7 +93,9 @@ typedef struct sas_model_desc {
     int64_t n_poly;          /* Schulz nodes of the polydisperse radius (1..64) */
     int64_t n_gamma;         /* orientation nodes in the polar angle about the axis (1..128) */
     int64_t n_psi;           /* orientation nodes in the azimuth about the axis (1..128) */
-    int64_t isotropic;       /* 1: axis uniform on the sphere (uniaxial models) */
+    int64_t isotropic;       /* axis law of the uniaxial models: 0 Gaussian cap about the mean
+                                axis (width sigma_orient), 1 uniform on the sphere, 2 uniform in
+                                the angles, theta ~ U[0, pi], phi ~ U[0, 2 pi] (Sec. II.B) */
     double radius;           /* sphere R; core radius; cylinder R; ellipsoid equatorial R */
     double thickness;        /* core-shell shell thickness */
     double length;           /* cylinder length L */
@@ -95,12 +104,20 @@ typedef struct sas_model_desc {
     double sld_shell;        /* core-shell shell SLD */
     double sld_solvent;      /* solvent SLD */
     double volume_fraction;  /* phi */
-    double poly;             /* Schulz sigma / mean of the polydisperse radius (0: none) */
+    double poly;             /* sigma / mean of the polydisperse radius (0: none) */
     double sigma_orient;     /* Gaussian width of the axis about its mean, rad */
     double axis_theta;       /* mean axis polar angle from +z, rad */
     double axis_phi;         /* mean axis azimuth, rad */
     double sq_radius;        /* Percus-Yevick hard-sphere radius */
     double sq_fraction;      /* Percus-Yevick volume fraction */
+    int64_t sampling;        /* SAS_QUADRATURE or SAS_PER_EVENT. Per-event histories draw the
+                                radius from the Gaussian law (poly_dist must be SAS_POLY_GAUSSIAN
+                                unless poly = 0) by inversion of its distribution function, and
+                                the axis uniformly (isotropic 1 or 2; or fixed: sigma_orient 0),
+                                from Philox block 2 of the history; dSigma/dOmega is then
+                                (phi / <V>) |F(Q; r, axis)|^2 S(Q), whose mean over the draws is
+                                the quadrature average over the same laws. */
+    int64_t poly_dist;       /* SAS_POLY_SCHULZ or SAS_POLY_GAUSSIAN */
 } sas_model_desc;
 
 typedef struct sas_experiment sas_experiment;   /* opaque, library-owned */
@@ -149,7 +166,9 @@ sas_status sas_detector_device(const sas_experiment *exp, const double **sum_w,
 /* Parity hook: dSigma/dOmega (1/angstrom) of the experiment's model at n
  * scattering vectors. q_xyz: DEVICE float[n][3]; out: DEVICE float[n]
  * (model precision FP32) -- or double pointers if the model is FP64.
- * Asynchronous on the experiment's stream. */
+ * Asynchronous on the experiment's stream. SAS_ERR_STATE for a per-event
+ * model (its cross section is a random draw per history; the records below
+ * give its per-history values). */
 sas_status sas_eval_model(sas_experiment *exp, const void *q_xyz, size_t n, void *out);
 
 /* Parity hook: per-neutron records of neutrons [first, first+n): DEVICE

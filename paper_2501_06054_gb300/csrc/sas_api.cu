@@ -57,6 +57,7 @@ sas_status set_cuda_error(cudaError_t e, const char* what) { return cuda_fail(e,
 // Percus-Yevick 40).
 double host_flops_per_history(const sas_model_desc& m, int np, int no)
 {
+    if (m.sampling == SAS_PER_EVENT) { np = 1; no = 1; }
     double per;
     if (m.kind == SAS_SPHERE) per = np * 36.0;
     else if (m.kind == SAS_CORE_SHELL) per = np * 62.0 + 20.0;
@@ -189,6 +190,56 @@ void schulz_nodes(double mean, double p, int n, double* r, double* w)
     for (int i = 0; i < n; ++i) r[i] = mean * r[i] / (z + 1.0);
 }
 
+// Gaussian N(mean, (p mean)^2) restricted to positive values (the
+// polydispersity law of Sec. II.B): Gauss-Legendre nodes on
+// [max(0, mean (1 - 8p)), mean (1 + 8p)] weighted by the density and
+// normalised; the mass beyond 8 sigma is below 1e-15.
+void gaussian_nodes(double mean, double p, int n, double* r, double* w)
+{
+    if (p <= 0.0 || n <= 1) {
+        r[0] = mean;
+        w[0] = 1.0;
+        for (int i = 1; i < n; ++i) r[i] = mean, w[i] = 0.0;
+        return;
+    }
+    const double a = std::max(0.0, mean * (1.0 - 8.0 * p)), b = mean * (1.0 + 8.0 * p), sd = p * mean;
+    std::vector<double> x(n), wx(n);
+    gauss_legendre(n, x.data(), wx.data());
+    double tot = 0.0;
+    for (int i = 0; i < n; ++i) {
+        r[i] = 0.5 * (b - a) * (x[i] + 1.0) + a;
+        const double d = (r[i] - mean) / sd;
+        w[i] = 0.5 * (b - a) * wx[i] * std::exp(-0.5 * d * d);
+        tot += w[i];
+    }
+    for (int i = 0; i < n; ++i) w[i] /= tot;
+}
+
+// Axis nodes for theta ~ U[0, pi], phi ~ U[0, 2 pi] (Sec. II.B; uniform in
+// the angles, not on the sphere): Gauss-Legendre in both angles.
+int uniform_angle_nodes(int nt, int np, double* c, double* wout)
+{
+    std::vector<double> xt(nt), wt(nt), xp(np), wp(np);
+    gauss_legendre(nt, xt.data(), wt.data());
+    gauss_legendre(np, xp.data(), wp.data());
+    double tot = 0.0;
+    int k = 0;
+    for (int i = 0; i < nt; ++i) {
+        const double th = 0.5 * M_PI * (xt[i] + 1.0), st = std::sin(th), ct = std::cos(th);
+        for (int j = 0; j < np; ++j) {
+            const double ph = M_PI * (xp[j] + 1.0);
+            c[3 * k] = st * std::cos(ph);
+            c[3 * k + 1] = st * std::sin(ph);
+            c[3 * k + 2] = ct;
+            wout[k] = wt[i] * wp[j];
+            tot += wout[k];
+            ++k;
+        }
+    }
+    for (int i = 0; i < k; ++i) wout[i] /= tot;
+    return k;
+}
+
 // Orientation nodes: axis = cos(g) n + sin(g) (cos(s) e_theta + sin(s) e_phi),
 // g on Gauss-Legendre nodes of [0, gmax] with weight sin(g) (times the
 // Gaussian exp(-g^2 / (2 sigma^2)) unless isotropic), s on Gauss-Legendre
@@ -261,7 +312,8 @@ sas_status build_model_tables(const sas_model_desc& m, ModelTables& t)
 {
     const int np = (int)m.n_poly;
     std::vector<double> r(np), w(np);
-    schulz_nodes(m.radius, m.poly, np, r.data(), w.data());
+    if (m.poly_dist == SAS_POLY_GAUSSIAN) gaussian_nodes(m.radius, m.poly, np, r.data(), w.data());
+    else schulz_nodes(m.radius, m.poly, np, r.data(), w.data());
     const int npoly = (m.poly > 0.0 && np > 1) ? np : 1;
     t.poly.assign((size_t)npoly * SAS_POLY_STRIDE, 0.0);
     double vmean = 0.0;
@@ -300,8 +352,10 @@ sas_status build_model_tables(const sas_model_desc& m, ModelTables& t)
     if (m.kind == SAS_CYLINDER || m.kind == SAS_ELLIPSOID) {
         const int nmax = (int)(m.n_gamma * m.n_psi);
         std::vector<double> c((size_t)3 * std::max(nmax, 1)), wo(std::max(nmax, 1));
-        const int no = orientation_nodes(m.axis_theta, m.axis_phi, m.sigma_orient, (int)m.n_gamma,
-                                         (int)m.n_psi, (int)m.isotropic, c.data(), wo.data());
+        const int no = m.isotropic == 2
+                           ? uniform_angle_nodes((int)m.n_gamma, (int)m.n_psi, c.data(), wo.data())
+                           : orientation_nodes(m.axis_theta, m.axis_phi, m.sigma_orient, (int)m.n_gamma,
+                                               (int)m.n_psi, (int)m.isotropic, c.data(), wo.data());
         t.orient.assign((size_t)no * SAS_ORIENT_STRIDE, 0.0);
         for (int i = 0; i < no; ++i) {
             t.orient[(size_t)i * 4 + 0] = c[3 * i];
@@ -313,6 +367,16 @@ sas_status build_model_tables(const sas_model_desc& m, ModelTables& t)
     } else {
         t.orient.assign(SAS_ORIENT_STRIDE, 0.0);
         t.n_orient = 0;
+    }
+    if (m.sampling == SAS_PER_EVENT) {
+        // per-event histories draw their own radius and axis: the nodes only
+        // gave <V> above, and one node keeps the kernels' staging minimal
+        t.poly.resize(SAS_POLY_STRIDE);
+        t.n_poly = 1;
+        if (t.n_orient > 0) {
+            t.orient.resize(SAS_ORIENT_STRIDE);
+            t.n_orient = 1;
+        }
     }
     t.half_length = 0.5 * m.length;
     t.rp2 = m.radius_polar * m.radius_polar;
@@ -348,6 +412,20 @@ ModelConst<T> model_const(const sas_model_desc& m, const ModelTables& t)
     c.sq_gamma = (T)t.sq_gamma;
     c.sq_switch = (T)t.sq_switch;
     for (int k = 0; k < SAS_SQ_NSER; ++k) c.sq_series[k] = (T)t.sq_series[k];
+    c.event = m.sampling == SAS_PER_EVENT ? 1 : 0;
+    c.orient_mode = (m.kind == SAS_CYLINDER || m.kind == SAS_ELLIPSOID) ? (int)m.isotropic : 0;
+    c.ev_r = (T)m.radius;
+    c.ev_p = (T)(m.poly_dist == SAS_POLY_GAUSSIAN ? m.poly : 0.0);
+    const double lo = c.ev_p > (T)0 ? 0.5 * std::erfc(1.0 / (m.poly * std::sqrt(2.0))) : 0.0;
+    c.ev_lo = (T)lo;
+    c.ev_1mlo = (T)(1.0 - lo);
+    c.ev_c1 = (T)(m.kind == SAS_CORE_SHELL ? m.sld - m.sld_shell : m.sld - m.sld_solvent);
+    c.ev_c2 = (T)(m.kind == SAS_CORE_SHELL ? m.sld_shell - m.sld_solvent : 0.0);
+    c.ev_len = (T)m.length;
+    c.ev_rp = (T)m.radius_polar;
+    c.ev_axis[0] = (T)(std::sin(m.axis_theta) * std::cos(m.axis_phi));
+    c.ev_axis[1] = (T)(std::sin(m.axis_theta) * std::sin(m.axis_phi));
+    c.ev_axis[2] = (T)std::cos(m.axis_theta);
     return c;
 }
 
@@ -424,6 +502,18 @@ sas_status validate_model(const sas_model_desc* m)
     if (m->volume_fraction < 0.0) return fail(SAS_ERR_ARG, "volume_fraction must be >= 0");
     if (m->poly < 0.0 || m->poly >= 1.0) return fail(SAS_ERR_ARG, "poly must be in [0, 1)");
     if (m->sigma_orient < 0.0) return fail(SAS_ERR_ARG, "sigma_orient must be >= 0");
+    if (m->isotropic < 0 || m->isotropic > 2) return fail(SAS_ERR_ARG, "isotropic must be 0, 1 or 2");
+    if (m->sampling != SAS_QUADRATURE && m->sampling != SAS_PER_EVENT) return fail(SAS_ERR_ARG, "unknown sampling");
+    if (m->poly_dist != SAS_POLY_SCHULZ && m->poly_dist != SAS_POLY_GAUSSIAN)
+        return fail(SAS_ERR_ARG, "unknown poly_dist");
+    if (m->sampling == SAS_PER_EVENT) {
+        if (m->poly > 0.0 && m->poly_dist != SAS_POLY_GAUSSIAN)
+            return fail(SAS_ERR_ARG, "per-event sampling draws Gaussian radii (Sec. II.B): set poly_dist to "
+                                     "SAS_POLY_GAUSSIAN or poly to 0");
+        if ((m->kind == SAS_CYLINDER || m->kind == SAS_ELLIPSOID) && m->isotropic == 0 && m->sigma_orient > 0.0)
+            return fail(SAS_ERR_ARG, "per-event axes are uniform on the sphere (isotropic 1), in the angles "
+                                     "(isotropic 2) or fixed (sigma_orient 0); the Gaussian cap is a quadrature option");
+    }
     if (m->sq_kind == SAS_SQ_HARD_SPHERE_PY) {
         if (m->sq_radius <= 0.0) return fail(SAS_ERR_ARG, "sq_radius must be > 0");
         if (m->sq_fraction < 0.0 || m->sq_fraction >= 0.74) return fail(SAS_ERR_ARG, "sq_fraction must be in [0, 0.74)");
@@ -980,6 +1070,9 @@ sas_status sas_eval_model(sas_experiment* e, const void* q_xyz, size_t n, void* 
     if (!e->has_model) return fail(SAS_ERR_STATE, "sas_set_model has not been called");
     if (n == 0) return SAS_OK;
     if (!q_xyz || !out) return fail(SAS_ERR_ARG, "NULL buffer");
+    if (e->model.sampling == SAS_PER_EVENT)
+        return fail(SAS_ERR_STATE, "a per-event model has no deterministic dSigma/dOmega; evaluate the same model "
+                                   "with sampling SAS_QUADRATURE");
     cudaError_t ce;
     if (e->model.precision == SAS_FP32)
         ce = dispatch_eval<float>(e, e->mcf, (const float*)q_xyz, (float*)out, n);

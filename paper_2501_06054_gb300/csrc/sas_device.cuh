@@ -42,6 +42,8 @@ __device__ __forceinline__ T u01(uint32_t x)
 template <typename T> struct M;
 
 template <> struct M<float> {
+    static __device__ __forceinline__ float erfcinv_(float y) { return erfcinvf(y); }
+    static __device__ __forceinline__ void sincospi_(float u, float& s, float& c) { sincospif(u, &s, &c); }
     static __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
     static __device__ __forceinline__ float sqrt_(float x) { return __fsqrt_rn(x); }
     static __device__ __forceinline__ float rsqrt(float x) { return rsqrtf(x); }
@@ -67,6 +69,8 @@ template <> struct M<float> {
 };
 
 template <> struct M<double> {
+    static __device__ __forceinline__ double erfcinv_(double y) { return erfcinv(y); }
+    static __device__ __forceinline__ void sincospi_(double u, double& s, double& c) { sincospi(u, &s, &c); }
     static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
     static __device__ __forceinline__ double sqrt_(double x) { return ::sqrt(x); }
     static __device__ __forceinline__ double rsqrt(double x) { return ::rsqrt(x); }
@@ -309,6 +313,115 @@ __device__ __forceinline__ T dsigma(const T qv[3], const ModelConst<T>& mc,
         avg = avg_ellipsoid<T>(qv, poly, mc.n_poly, orient, mc.n_orient, mc.rp2);
     }
     return mc.scale * avg * structure_factor<T>(q, mc);
+}
+
+// ------------------------------------------------ per-event sampling
+// Philox block 2 of a history: radius, axis polar, axis azimuth, spare.
+__device__ __forceinline__ uint4 event_draws(uint64_t seed, uint32_t exp_id, uint64_t index)
+{
+    const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    return philox(make_uint4(2u, exp_id, (uint32_t)index, (uint32_t)(index >> 32)), key);
+}
+
+// 1 - u01(x), exact
+template <typename T>
+__device__ __forceinline__ T u01c(uint32_t x)
+{
+    return ((T)(8388607u - (x >> 9)) + (T)0.5) * (T)(1.0 / 8388608.0);
+}
+
+// One event of the model (Sec. II.B): the radius from N(R, (pR)^2)
+// restricted to R > 0, sampled by inversion z = Phi^-1(lo + u (1 - lo)),
+// Phi^-1(v) = -sqrt(2) erfcinv(2 v) (upper half through 1 - v = (1 - u)(1 - lo));
+// the axis uniform on the sphere or in the angles. Returns
+// (phi / <V>) |F(Q; r, axis)|^2 S(Q); its expectation over the draws is the
+// quadrature average over the same laws.
+template <typename T, int KIND>
+__device__ __forceinline__ T dsigma_event(const T qv[3], const ModelConst<T>& mc, uint4 rb)
+{
+    const T q2 = fma(qv[0], qv[0], fma(qv[1], qv[1], qv[2] * qv[2]));
+    const T q = M<T>::sqrt_(q2);
+    T r = mc.ev_r;
+    if (mc.ev_p > (T)0) {
+        const T u = u01<T>(rb.x);
+        const T v = fma(u, mc.ev_1mlo, mc.ev_lo);
+        const T z = (v < (T)0.5) ? -(T)1.41421356237309515 * M<T>::erfcinv_((T)2 * v)
+                                 : (T)1.41421356237309515 * M<T>::erfcinv_((T)2 * u01c<T>(rb.x) * mc.ev_1mlo);
+        r = mc.ev_r * fma(mc.ev_p, z, (T)1);
+    }
+    const T pi = (T)3.14159265358979323846;
+    T F2;
+    if (KIND == SAS_SPHERE) {
+        const T x = q * r;
+        const T g = M<T>::sphere_g(x, M<T>::rcp(x));
+        const T V = (T)(4.0 / 3.0) * pi * r * r * r;
+        const T F = (T)3 * mc.ev_c1 * V * g;
+        F2 = F * F;
+    } else if (KIND == SAS_CORE_SHELL) {
+        const T ro = r + mc.shell;
+        const T xc = q * r, xo = q * ro;
+        const T Vc = (T)(4.0 / 3.0) * pi * r * r * r, Vo = (T)(4.0 / 3.0) * pi * ro * ro * ro;
+        const T F = (T)3 * (mc.ev_c1 * Vc * M<T>::sphere_g(xc, M<T>::rcp(xc)) +
+                            mc.ev_c2 * Vo * M<T>::sphere_g(xo, M<T>::rcp(xo)));
+        F2 = F * F;
+    } else {
+        T c[3];
+        if (mc.orient_mode == 0) {
+            c[0] = mc.ev_axis[0];
+            c[1] = mc.ev_axis[1];
+            c[2] = mc.ev_axis[2];
+        } else {
+            T ct, st, sp, cp;
+            if (mc.orient_mode == 1) {
+                ct = (T)1 - (T)2 * u01<T>(rb.y);
+                st = M<T>::sqrt_(fmax((T)0, (T)1 - ct * ct));
+            } else {
+                M<T>::sincospi_(u01<T>(rb.y), st, ct);
+            }
+            M<T>::sincospi_((T)2 * u01<T>(rb.z), sp, cp);
+            c[0] = st * cp;
+            c[1] = st * sp;
+            c[2] = ct;
+        }
+        const T qc = fma(qv[0], c[0], fma(qv[1], c[1], qv[2] * c[2]));
+        const T x0 = fma(qv[1], c[2], -qv[2] * c[1]);
+        const T x1 = fma(qv[2], c[0], -qv[0] * c[2]);
+        const T x2 = fma(qv[0], c[1], -qv[1] * c[0]);
+        const T qab2 = fma(x0, x0, fma(x1, x1, x2 * x2));
+        if (KIND == SAS_CYLINDER) {
+            const T y = fabs(qc) * (T)0.5 * mc.ev_len;
+            const T sn = M<T>::sinc(y, M<T>::rcp(y));
+            const T x = M<T>::sqrt_(qab2) * r;
+            T a;
+            if constexpr (sizeof(T) == 4) {
+                const float s = x * x;
+                if (s <= SAS_J1P_SMAX) a = sas_cyl_a_s(s);
+                else if (s <= SAS_J1Q_SMAX) a = sas_cyl_a_s3(s);
+                else a = sas_cyl_a_large(x, __frcp_rn(x), rsqrtf(x));
+            } else {
+                a = M<T>::cyl_a(x, M<T>::rcp(x), (T)0);
+            }
+            const T F = mc.ev_c1 * pi * r * r * mc.ev_len * sn * a;
+            F2 = F * F;
+        } else {
+            const T x = M<T>::sqrt_(fma(r * r, qab2, mc.ev_rp * mc.ev_rp * qc * qc));
+            const T V = (T)(4.0 / 3.0) * pi * mc.ev_rp * r * r;
+            const T F = (T)3 * mc.ev_c1 * V * M<T>::sphere_g(x, M<T>::rcp(x));
+            F2 = F * F;
+        }
+    }
+    return mc.scale * F2 * structure_factor<T>(q, mc);
+}
+
+// dSigma/dOmega of history `index` of experiment `exp_id`: the quadrature
+// average, or the per-event estimate from the history's own draws.
+template <typename T, int KIND>
+__device__ __forceinline__ T dsigma_history(const T qv[3], const ModelConst<T>& mc, const T* __restrict__ poly,
+                                            const T* __restrict__ orient, uint64_t seed, uint32_t exp_id,
+                                            uint64_t index)
+{
+    if (mc.event) return dsigma_event<T, KIND>(qv, mc, event_draws(seed, exp_id, index));
+    return dsigma<T, KIND>(qv, mc, poly, orient);
 }
 
 // ------------------------------------------------------------- geometry

@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(1024) trace_kernel(const TraceParams<T> P)
             const History<T> hs = history<T>(P.in, P.seed, P.exp_id, P.first + j);
             tr.add(hs.wt);
             if (hs.pixel >= 0) {
-                w = hs.pref * dsigma<T, KIND>(hs.q, P.mc, poly, orient);
+                w = hs.pref * dsigma_history<T, KIND>(hs.q, P.mc, poly, orient, P.seed, P.exp_id, P.first + j);
                 pix = hs.pixel;
             }
         }
@@ -225,7 +225,8 @@ __global__ void records_kernel(const TraceParams<T> P)
     if (j >= P.n) return;
     const History<T> hs = history<T>(P.in, P.seed, P.exp_id, P.first + j);
     double w = 0.0;
-    if (hs.pixel >= 0) w = (double)(hs.pref * dsigma<T, KIND>(hs.q, P.mc, P.poly, P.orient));
+    if (hs.pixel >= 0)
+        w = (double)(hs.pref * dsigma_history<T, KIND>(hs.q, P.mc, P.poly, P.orient, P.seed, P.exp_id, P.first + j));
     P.pixel_out[j] = hs.pixel;
     P.weight_out[j] = w;
 }

@@ -44,6 +44,17 @@ struct ModelConst {
     T sq_alpha, sq_beta, sq_gamma;
     T sq_switch;     // A below which the series is used
     T sq_series[SAS_SQ_NSER];
+    // per-event sampling (Sec. II.B): one radius and one axis per history
+    int event;       // 0: quadrature average over the tables, 1: per-event draws
+    int orient_mode; // axis draw: 0 fixed (ev_axis), 1 uniform on the sphere, 2 uniform angles
+    T ev_r;          // mean of the polydisperse radius
+    T ev_p;          // sigma / mean of its Gaussian (0: monodisperse)
+    T ev_lo;         // Phi(-1/p): probability mass of r <= 0, removed by the restriction
+    T ev_1mlo;       // 1 - ev_lo
+    T ev_c1, ev_c2;  // contrasts: (drho, 0), core-shell (rho_core - rho_shell, rho_shell - rho_solvent)
+    T ev_len;        // cylinder L
+    T ev_rp;         // ellipsoid polar radius
+    T ev_axis[3];    // fixed axis (orient_mode 0)
 };
 
 }  // namespace sas
