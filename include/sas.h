@@ -65,6 +65,8 @@ enum { SAS_QUADRATURE = 0, SAS_PER_EVENT = 1 };
 /* law of the polydisperse radius: Schulz, or the Gaussian of Sec. II.B
  * restricted to positive radii */
 enum { SAS_POLY_SCHULZ = 0, SAS_POLY_GAUSSIAN = 1 };
+/* largest cylinder radial table (points; 64 KB of FP32 values) */
+#define SAS_MAX_RADIAL_TABLE 8192
 
 /* Instrument (Sec. II.A: source, collimation, sample, 2D PSD). */
 typedef struct sas_instrument {
@@ -118,6 +120,14 @@ typedef struct sas_model_desc {
                                 (phi / <V>) |F(Q; r, axis)|^2 S(Q), whose mean over the draws is
                                 the quadrature average over the same laws. */
     int64_t poly_dist;       /* SAS_POLY_SCHULZ or SAS_POLY_GAUSSIAN */
+    int64_t radial_table;    /* cylinder quadrature only: 1 replaces the polydisperse radial sum of
+                                every orientation node by the interpolated table
+                                G(x) = sum_i w_i t_i^4 [2 J1(x t_i)/(x t_i)]^2, x = Q_AB rbar,
+                                t_i = r_i / rbar (built in FP64 per model up to the instrument's
+                                largest |Q|, grid doubled until the cubic Hermite error is at
+                                most 1e-7 G(0), 1e-13 for FP64 models; at most
+                                SAS_MAX_RADIAL_TABLE points, else the direct sum is kept);
+                                0 sums over the radius nodes */
 } sas_model_desc;
 
 typedef struct sas_experiment sas_experiment;   /* opaque, library-owned */
@@ -386,6 +396,14 @@ sas_status sas_gauss_legendre(int n, double *x, double *w);
  * Gauss-Laguerre nodes r[n] with normalised weights w[n] (Sec. II.B reading:
  * Schulz instead of per-event Gaussian draws). p == 0: one node at the mean. */
 sas_status sas_schulz_nodes(double mean, double p, int n, double *r, double *w);
+
+/* The cylinder radial table of sas_model_desc.radial_table on HOST arrays:
+ * radius nodes r[n_nodes] with normalised weights w, mean radius rbar,
+ * points x_k = k xmax / (n_points - 1): G[k] and D[k] = h G'(x_k).
+ * *max_err: largest error of the cubic Hermite interpolant at the interval
+ * midpoints. SAS_ERR_ARG on sizes < 2 or non-positive rbar, xmax. */
+sas_status sas_cylinder_radial_table(const double *r, const double *w, int n_nodes, double rbar,
+                                     double xmax, int n_points, double *G, double *D, double *max_err);
 
 /* Orientation nodes of the axis distribution about (theta, phi): Gaussian
  * cap of width sigma (or isotropic), n_gamma x n_psi Gauss-Legendre grid.

@@ -45,7 +45,7 @@ class sas_model_desc(ctypes.Structure):
                    "radius", "thickness", "length", "radius_polar", "sld", "sld_shell",
                    "sld_solvent", "volume_fraction", "poly", "sigma_orient", "axis_theta",
                    "axis_phi", "sq_radius", "sq_fraction")] + \
-               [(n, ctypes.c_int64) for n in ("sampling", "poly_dist")]
+               [(n, ctypes.c_int64) for n in ("sampling", "poly_dist", "radial_table")]
 
 
 class sas_launch_config(ctypes.Structure):
@@ -93,6 +93,8 @@ _SIGS = {
     "sas_orientation_nodes": [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                               ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.POINTER(ctypes.c_int)],
     "sas_py_series": [ctypes.c_double, _dp, _dp, ctypes.c_int],
+    "sas_cylinder_radial_table": [_dp, _dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                  _dp, _dp, _dp],
     "sas_get_launch_config": [_vp, ctypes.POINTER(sas_launch_config)],
     "sas_set_launch_config": [_vp, ctypes.POINTER(sas_launch_config)],
     "sas_autotune": [_vp, _u64, _u64, ctypes.POINTER(sas_launch_config), _dp],
@@ -187,7 +189,7 @@ def make_instrument(d) -> sas_instrument:
 def make_model(d) -> sas_model_desc:
     d = d if isinstance(d, dict) else d.as_dict()
     ints = ("kind", "sq_kind", "precision", "n_poly", "n_gamma", "n_psi", "isotropic", "sampling",
-            "poly_dist")
+            "poly_dist", "radial_table")
     return sas_model_desc(**{k: (int(v) if k in ints else float(v)) for k, v in d.items()})
 
 
@@ -269,6 +271,17 @@ def sas_gauss_legendre(n):
     x, w = np.empty(n), np.empty(n)
     _check(lib().sas_gauss_legendre(int(n), x.ctypes.data_as(_dp), w.ctypes.data_as(_dp)))
     return x, w
+
+
+def sas_cylinder_radial_table(r, w, rbar, xmax, n_points):
+    """(G, D, max_err) of the cylinder radial table on the host."""
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    G, D, err = np.empty(n_points), np.empty(n_points), np.zeros(1)
+    _check(lib().sas_cylinder_radial_table(r.ctypes.data_as(_dp), w.ctypes.data_as(_dp), len(r), float(rbar),
+                                           float(xmax), int(n_points), G.ctypes.data_as(_dp),
+                                           D.ctypes.data_as(_dp), err.ctypes.data_as(_dp)))
+    return G, D, float(err[0])
 
 
 def sas_schulz_nodes(mean, p, n):

@@ -58,6 +58,8 @@ sas_status set_cuda_error(cudaError_t e, const char* what) { return cuda_fail(e,
 double host_flops_per_history(const sas_model_desc& m, int np, int no)
 {
     if (m.sampling == SAS_PER_EVENT) { np = 1; no = 1; }
+    if (m.kind == SAS_CYLINDER && m.radial_table && m.sampling == SAS_QUADRATURE)
+        return no * 60.0 + 150.0 + (m.sq_kind == SAS_SQ_HARD_SPHERE_PY ? 40.0 : 0.0);
     double per;
     if (m.kind == SAS_SPHERE) per = np * 36.0;
     else if (m.kind == SAS_CORE_SHELL) per = np * 62.0 + 20.0;
@@ -240,6 +242,61 @@ int uniform_angle_nodes(int nt, int np, double* c, double* wout)
     return k;
 }
 
+// Cylinder radial table (G, h G') on [0, xmax] and its midpoint error.
+double cylinder_radial_table(const double* r, const double* w, int np, double rbar, double xmax, int n,
+                             double* G, double* D)
+{
+    const double h = xmax / (double)(n - 1);
+    auto eval = [&](double x, double& g, double& dg) {
+        g = 0.0;
+        dg = 0.0;
+        for (int i = 0; i < np; ++i) {
+            const double t = r[i] / rbar, y = x * t, t4 = t * t * t * t;
+            double a, da;
+            if (y < 1e-4) {
+                a = 1.0 - y * y / 8.0;
+                da = -y / 4.0;
+            } else {
+                a = 2.0 * ::j1(y) / y;
+                da = -2.0 * ::jn(2, y) / y;   // d/dy [2 J1(y) / y]
+            }
+            g += w[i] * t4 * a * a;
+            dg += w[i] * t4 * 2.0 * a * da * t;
+        }
+    };
+    for (int k = 0; k < n; ++k) {
+        double g, dg;
+        eval(k * h, g, dg);
+        G[k] = g;
+        D[k] = h * dg;
+    }
+    double err = 0.0;
+    for (int k = 0; k + 1 < n; ++k) {
+        double g, dg;
+        eval((k + 0.5) * h, g, dg);
+        // cubic Hermite at f = 1/2: (G0 + G1)/2 + (D0 - D1)/8
+        const double hm = 0.5 * (G[k] + G[k + 1]) + 0.125 * (D[k] - D[k + 1]);
+        err = std::max(err, std::fabs(hm - g));
+    }
+    return err;
+}
+
+// Upper bound of |Q| reachable on the instrument: the largest wavelength
+// spread k, the steepest incoming ray through both pinholes and the widest
+// angle from any sample point to any detector point, with 1 % margin.
+double instrument_q_max(const sas_instrument& in)
+{
+    const double kmax = 2.0 * M_PI / (in.lambda0 * (1.0 - in.dlambda_rel));
+    const double t_in = std::atan((in.ap1_radius + in.ap2_radius) / std::fabs(in.ap2_z - in.ap1_z));
+    const double half_w = 0.5 * in.nx * in.pixel_x, half_h = 0.5 * in.ny * in.pixel_y;
+    const double lat = std::sqrt(half_w * half_w + half_h * half_h) +
+                       std::sqrt(in.sample_half_x * in.sample_half_x + in.sample_half_y * in.sample_half_y) +
+                       in.ap2_radius;
+    const double t_out = std::atan(lat / std::max(in.det_distance - in.sample_thickness, 1e-9));
+    const double th = std::min(t_in + t_out, M_PI);
+    return 1.01 * 2.0 * kmax * std::sin(0.5 * th);
+}
+
 // Orientation nodes: axis = cos(g) n + sin(g) (cos(s) e_theta + sin(s) e_phi),
 // g on Gauss-Legendre nodes of [0, gmax] with weight sin(g) (times the
 // Gaussian exp(-g^2 / (2 sigma^2)) unless isotropic), s on Gauss-Legendre
@@ -308,7 +365,7 @@ void py_constants(double phi, double* alpha, double* beta, double* gamma, double
 }
 
 // Tables of one model in FP64 (see sas_types.h for the layouts).
-sas_status build_model_tables(const sas_model_desc& m, ModelTables& t)
+sas_status build_model_tables(const sas_model_desc& m, ModelTables& t, double q_max)
 {
     const int np = (int)m.n_poly;
     std::vector<double> r(np), w(np);
@@ -368,11 +425,54 @@ sas_status build_model_tables(const sas_model_desc& m, ModelTables& t)
         t.orient.assign(SAS_ORIENT_STRIDE, 0.0);
         t.n_orient = 0;
     }
+    t.n_rad = t.n_poly;
+    t.n_tab = 0;
+    if (m.kind == SAS_CYLINDER && m.radial_table && m.sampling == SAS_QUADRATURE && q_max > 0.0) {
+        // the polydisperse radial sum depends on x = q_AB rbar alone: tabulate
+        // G(x) with h G'(x), doubling the grid until the cubic Hermite error at
+        // the midpoints is at most 1e-7 G(0) (FP64 models: 1e-13); stored
+        // behind the nodes
+        const double rbar = m.radius, xmax = q_max * rbar;
+        std::vector<double> rr(npoly), ww(npoly);
+        for (int i = 0; i < npoly; ++i) {
+            rr[i] = t.poly[(size_t)i * SAS_POLY_STRIDE + 2];   // r
+            ww[i] = npoly == 1 ? 1.0 : w[i];
+        }
+        const double F0 = (m.sld - m.sld_solvent) * pi * rbar * rbar * m.length;
+        std::vector<double> G, D;
+        double err = 0.0, g0 = 0.0;
+        const double target = m.precision == SAS_FP64 ? 1e-13 : 1e-7;   // relative to G(0)
+        int n = 1024;
+        for (; n <= SAS_MAX_RADIAL_TABLE; n *= 2) {
+            G.assign(n, 0.0);
+            D.assign(n, 0.0);
+            err = cylinder_radial_table(rr.data(), ww.data(), npoly, rbar, xmax, n, G.data(), D.data());
+            g0 = G[0];
+            if (err <= target * g0) break;
+        }
+        if (n <= SAS_MAX_RADIAL_TABLE) {
+            const int rows = (2 * n + SAS_POLY_STRIDE - 1) / SAS_POLY_STRIDE;
+            t.poly.resize((size_t)(npoly + rows) * SAS_POLY_STRIDE, 0.0);
+            double* tab = t.poly.data() + (size_t)npoly * SAS_POLY_STRIDE;
+            for (int k = 0; k < n; ++k) {
+                tab[2 * k] = G[k];
+                tab[2 * k + 1] = D[k];
+            }
+            t.n_poly = npoly + rows;
+            t.n_tab = n;
+            t.tab_inv_h = (double)(n - 1) / xmax;
+            t.tab_xmax = xmax;
+            t.tab_c0 = F0 * F0;
+            t.tab_rbar = rbar;
+            t.tab_err = err / g0;
+        }
+    }
     if (m.sampling == SAS_PER_EVENT) {
         // per-event histories draw their own radius and axis: the nodes only
         // gave <V> above, and one node keeps the kernels' staging minimal
         t.poly.resize(SAS_POLY_STRIDE);
         t.n_poly = 1;
+        t.n_rad = 1;
         if (t.n_orient > 0) {
             t.orient.resize(SAS_ORIENT_STRIDE);
             t.n_orient = 1;
@@ -426,6 +526,12 @@ ModelConst<T> model_const(const sas_model_desc& m, const ModelTables& t)
     c.ev_axis[0] = (T)(std::sin(m.axis_theta) * std::cos(m.axis_phi));
     c.ev_axis[1] = (T)(std::sin(m.axis_theta) * std::sin(m.axis_phi));
     c.ev_axis[2] = (T)std::cos(m.axis_theta);
+    c.n_rad = t.n_rad;
+    c.n_tab = t.n_tab;
+    c.tab_inv_h = (T)t.tab_inv_h;
+    c.tab_xmax = (T)t.tab_xmax;
+    c.tab_c0 = (T)t.tab_c0;
+    c.tab_rbar = (T)t.tab_rbar;
     return c;
 }
 
@@ -506,6 +612,7 @@ sas_status validate_model(const sas_model_desc* m)
     if (m->sampling != SAS_QUADRATURE && m->sampling != SAS_PER_EVENT) return fail(SAS_ERR_ARG, "unknown sampling");
     if (m->poly_dist != SAS_POLY_SCHULZ && m->poly_dist != SAS_POLY_GAUSSIAN)
         return fail(SAS_ERR_ARG, "unknown poly_dist");
+    if (m->radial_table != 0 && m->radial_table != 1) return fail(SAS_ERR_ARG, "radial_table must be 0 or 1");
     if (m->sampling == SAS_PER_EVENT) {
         if (m->poly > 0.0 && m->poly_dist != SAS_POLY_GAUSSIAN)
             return fail(SAS_ERR_ARG, "per-event sampling draws Gaussian radii (Sec. II.B): set poly_dist to "
@@ -950,7 +1057,7 @@ sas_status sas_set_model(sas_experiment* e, const sas_model_desc* m)
     sas_status st = validate_model(m);
     if (st != SAS_OK) return st;
     ModelTables t;
-    st = build_model_tables(*m, t);
+    st = build_model_tables(*m, t, instrument_q_max(e->inst));
     if (st != SAS_OK) return st;
     const bool fp32 = m->precision == SAS_FP32;
     const size_t es = fp32 ? sizeof(float) : sizeof(double);
@@ -1147,6 +1254,16 @@ sas_status sas_schulz_nodes(double mean, double p, int n, double* r, double* w)
     if (n < 1 || n > SAS_MAX_POLY || !r || !w || !(mean > 0.0) || !(p >= 0.0 && p < 1.0))
         return fail(SAS_ERR_ARG, "bad arguments");
     schulz_nodes(mean, p, n, r, w);
+    return SAS_OK;
+}
+
+sas_status sas_cylinder_radial_table(const double* r, const double* w, int n_nodes, double rbar, double xmax,
+                                     int n_points, double* G, double* D, double* max_err)
+{
+    if (!r || !w || !G || !D || n_nodes < 1 || n_points < 2 || !(rbar > 0.0) || !(xmax > 0.0))
+        return fail(SAS_ERR_ARG, "bad arguments");
+    const double e = cylinder_radial_table(r, w, n_nodes, rbar, xmax, n_points, G, D);
+    if (max_err) *max_err = e;
     return SAS_OK;
 }
 

@@ -293,7 +293,7 @@ sas_status sas_create_batch(const sas_instrument* inst, const sas_model_desc* mo
         if (st != SAS_OK) return bail(st);
         if (m.precision != SAS_FP32) return bail(set_error(SAS_ERR_ARG, "batched experiments are FP32"));
         ModelTables t;
-        st = build_model_tables(m, t);
+        st = build_model_tables(m, t, instrument_q_max(*inst));
         if (st != SAS_OK) return bail(st);
         BatchExp& x = b->h_exps[e];
         std::memset(&x, 0, sizeof(x));

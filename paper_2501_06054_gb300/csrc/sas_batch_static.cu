@@ -95,7 +95,7 @@ sas_status sas_trace_batch_static(const sas_instrument* inst, const sas_model_de
         if (st != SAS_OK) return st;
         if (m.precision != SAS_FP32) return set_error(SAS_ERR_ARG, "batched experiments are FP32");
         ModelTables t;
-        st = build_model_tables(m, t);
+        st = build_model_tables(m, t, instrument_q_max(*inst));
         if (st != SAS_OK) return st;
         BatchExp& x = exps[e];
         std::memset(&x, 0, sizeof(x));

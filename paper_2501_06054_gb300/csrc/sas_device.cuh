@@ -268,6 +268,56 @@ __device__ __forceinline__ T avg_cylinder(const T qv[3], const T* __restrict__ p
     return k.s;
 }
 
+// Cylinder with a radial table: the polydisperse radial sum of an
+// orientation node is tab_c0 G(q_AB rbar), G by cubic Hermite interpolation
+// of (G, h G') at the grid points; beyond the table, the direct sum over the
+// radius nodes.
+template <typename T>
+__device__ __forceinline__ T avg_cylinder_tab(const T qv[3], const T* __restrict__ poly, const ModelConst<T>& mc,
+                                              const T* __restrict__ orient, int no)
+{
+    const T* __restrict__ tab = poly + SAS_POLY_STRIDE * mc.n_rad;
+    Kahan<T> k;
+    for (int o = 0; o < no; ++o) {
+        const T* c = orient + 4 * o;
+        const T qc = fma(qv[0], c[0], fma(qv[1], c[1], qv[2] * c[2]));
+        const T x0 = fma(qv[1], c[2], -qv[2] * c[1]);
+        const T x1 = fma(qv[2], c[0], -qv[0] * c[2]);
+        const T x2 = fma(qv[0], c[1], -qv[1] * c[0]);
+        const T qab2 = fma(x0, x0, fma(x1, x1, x2 * x2));
+        const T y = fabs(qc) * mc.half_length;
+        const T sn = M<T>::sinc(y, M<T>::rcp(y));
+        const T qab = M<T>::sqrt_(qab2);
+        const T x = qab * mc.tab_rbar;
+        T inner = 0;
+        if (x < mc.tab_xmax) {
+            const T s = x * mc.tab_inv_h;
+            const int i = min((int)s, mc.n_tab - 2);
+            const T f = s - (T)i, f1 = (T)1 - f;
+            const T g0 = tab[2 * i], d0 = tab[2 * i + 1], g1 = tab[2 * i + 2], d1 = tab[2 * i + 3];
+            // h00 = (1 + 2f)(1 - f)^2, h10 = f (1 - f)^2, h01 = f^2 (3 - 2f), h11 = f^2 (f - 1)
+            inner = mc.tab_c0 * (f1 * f1 * fma((T)2 * f + (T)1, g0, f * d0) + f * f * fma((T)3 - (T)2 * f, g1, -f1 * d1));
+        } else {
+            for (int j = 0; j < mc.n_rad; ++j) {
+                const T* p = poly + SAS_POLY_STRIDE * j;
+                const T xr = qab * p[2];
+                T a;
+                if constexpr (sizeof(T) == 4) {
+                    const float sx = xr * xr;
+                    if (sx <= SAS_J1P_SMAX) a = sas_cyl_a_s(sx);
+                    else if (sx <= SAS_J1Q_SMAX) a = sas_cyl_a_s3(sx);
+                    else a = sas_cyl_a_large(xr, __frcp_rn(xr), rsqrtf(xr));
+                } else {
+                    a = M<T>::cyl_a(xr, M<T>::rcp(xr), (T)0);
+                }
+                inner = fma(p[1], a * a, inner);
+            }
+        }
+        k.add(c[3] * sn * sn * inner);
+    }
+    return k.s;
+}
+
 template <typename T>
 __device__ __forceinline__ T avg_ellipsoid(const T qv[3], const T* __restrict__ poly, int np,
                                            const T* __restrict__ orient, int no, T rp2)
@@ -308,7 +358,8 @@ __device__ __forceinline__ T dsigma(const T qv[3], const ModelConst<T>& mc,
     } else if (KIND == SAS_CORE_SHELL) {
         avg = avg_core_shell<T>(q, M<T>::rcp(q), poly, mc.n_poly, mc.shell);
     } else if (KIND == SAS_CYLINDER) {
-        avg = avg_cylinder<T>(qv, poly, mc.n_poly, orient, mc.n_orient, mc.half_length);
+        avg = mc.n_tab > 0 ? avg_cylinder_tab<T>(qv, poly, mc, orient, mc.n_orient)
+                           : avg_cylinder<T>(qv, poly, mc.n_rad, orient, mc.n_orient, mc.half_length);
     } else {
         avg = avg_ellipsoid<T>(qv, poly, mc.n_poly, orient, mc.n_orient, mc.rp2);
     }

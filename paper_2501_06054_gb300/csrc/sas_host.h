@@ -14,6 +14,11 @@ struct ModelTables {
     int sq_kind = 0;
     double sq_2r = 0, sq_24phi = 0, sq_alpha = 0, sq_beta = 0, sq_gamma = 0, sq_switch = 0;
     std::vector<double> sq_series;
+    // cylinder radial table (radial_table = 1): G(x) and h G'(x) on a grid,
+    // stored behind the radius nodes in `poly`
+    int n_rad = 0;                // radius nodes (n_poly counts the table rows too)
+    int n_tab = 0;                // table points (0: no table)
+    double tab_inv_h = 0, tab_xmax = 0, tab_c0 = 0, tab_rbar = 0, tab_err = 0;
 };
 
 void gauss_legendre(int n, double* x, double* w);
@@ -22,7 +27,14 @@ void schulz_nodes(double mean, double p, int n, double* r, double* w);
 int orientation_nodes(double theta, double phi, double sigma, int ng, int npsi, int isotropic,
                       double* c, double* w);
 void py_constants(double phi, double* alpha, double* beta, double* gamma, double* series, int nser);
-sas_status build_model_tables(const sas_model_desc& m, ModelTables& t);
+// q_max: upper bound of |Q| over the instrument (for the radial table; 0: none)
+sas_status build_model_tables(const sas_model_desc& m, ModelTables& t, double q_max);
+double instrument_q_max(const sas_instrument& in);
+// G(x) = sum_i w_i t_i^4 a(x t_i)^2, a(y) = 2 J1(y) / y, t_i = r_i / rbar, and
+// D = h G'(x) at x_k = k h, h = xmax / (n - 1); returns the largest error of
+// the cubic Hermite interpolant at the interval midpoints.
+double cylinder_radial_table(const double* r, const double* w, int np, double rbar, double xmax, int n,
+                             double* G, double* D);
 sas_status validate_instrument(const sas_instrument* in);
 sas_status validate_model(const sas_model_desc* m);
 template <typename T> ModelConst<T> model_const(const sas_model_desc& m, const ModelTables& t);

@@ -55,6 +55,10 @@ struct ModelConst {
     T ev_len;        // cylinder L
     T ev_rp;         // ellipsoid polar radius
     T ev_axis[3];    // fixed axis (orient_mode 0)
+    // cylinder radial table: inner(q_AB) = tab_c0 G(q_AB rbar), G interpolated
+    int n_rad;       // radius nodes (the direct sum beyond the table)
+    int n_tab;       // table points (0: direct sum)
+    T tab_inv_h, tab_xmax, tab_c0, tab_rbar;
 };
 
 }  // namespace sas

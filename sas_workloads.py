@@ -91,6 +91,7 @@ class Model:
     sq_fraction: float = 0.0
     sampling: int = QUADRATURE      # PER_EVENT: one radius and axis drawn per history (Sec. II.B)
     poly_dist: int = SCHULZ         # GAUSSIAN: N(R, (poly R)^2) restricted to R > 0
+    radial_table: int = 0           # cylinder: 1 interpolates the polydisperse radial sum from a table
 
     def as_dict(self):
         return asdict(self)
