@@ -82,7 +82,8 @@ class _Model(ctypes.Structure):
                    "sld_solvent", "volume_fraction", "sq_radius", "sq_fraction")] + \
                [("poly_r", _DP), ("poly_w", _DP), ("orient_c", _DP), ("orient_w", _DP)] + \
                [("event", ctypes.c_int64), ("orient_mode", ctypes.c_int64), ("poly", ctypes.c_double),
-                ("axis_theta", ctypes.c_double), ("axis_phi", ctypes.c_double)]
+                ("axis_theta", ctypes.c_double), ("axis_phi", ctypes.c_double),
+                ("radius_b", ctypes.c_double), ("axis_psi", ctypes.c_double)]
 
 
 def lib():
@@ -119,6 +120,9 @@ def lib():
                                             ctypes.c_uint32, _DP]
             L.oracle_dsigma_event_many.argtypes = [ctypes.POINTER(_Model), _DP, ctypes.c_uint64, ctypes.c_uint32,
                                                    ctypes.c_uint64, ctypes.c_int64, _DP]
+            L.oracle_frame.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, _DP]
+            L.oracle_event_frame.argtypes = [ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                             ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _DP]
             L.oracle_num_threads.restype = ctypes.c_int
             L.oracle_sample_lambda.argtypes = [ctypes.c_double] * 3
             L.oracle_sample_lambda.restype = ctypes.c_double
@@ -200,6 +204,62 @@ def uniform_angle_nodes(n_theta, n_phi):
     return c.reshape(-1, 3), W / W.sum()
 
 
+def frame_from_angles(theta, phi, psi):
+    """Particle frame rows (A, B, C): C along (theta, phi); A, B the unit
+    vectors e_theta, e_phi of C rotated by psi about C (Sec. II.B)."""
+    st, ct, sp, cp = math.sin(theta), math.cos(theta), math.sin(phi), math.cos(phi)
+    et = np.array([ct * cp, ct * sp, -st])
+    ep = np.array([-sp, cp, 0.0])
+    A = math.cos(psi) * et + math.sin(psi) * ep
+    B = -math.sin(psi) * et + math.cos(psi) * ep
+    C = np.array([st * cp, st * sp, ct])
+    return np.stack([A, B, C])
+
+
+def _rotation_taking(u, v):
+    """Rotation matrix of the smallest rotation taking unit u to unit v."""
+    k = np.cross(u, v)
+    s, c = np.linalg.norm(k), float(np.dot(u, v))
+    if s < 1e-15:
+        return np.eye(3)
+    k = k / s
+    K = np.array([[0, -k[2], k[1]], [k[2], 0, -k[0]], [-k[1], k[0], 0]])
+    return np.eye(3) + s * K + (1.0 - c) * (K @ K)
+
+
+def frame_nodes(m):
+    """Orientation nodes of a particle without a symmetry axis: frames
+    [n][3][3] (rows A, B, C) and normalised weights. isotropic 0: the
+    Gaussian cap of the C axis about (axis_theta, axis_phi) (as for the
+    uniaxial models), the mean frame carried along by the smallest rotation
+    taking its C to the node's; 1: uniform rotations (Gauss-Legendre in
+    cos theta, phi and psi); 2: theta, phi and psi uniform (Sec. II.B)."""
+    iso = int(m["isotropic"])
+    ng, npsi, nr = int(m["n_gamma"]), int(m["n_psi"]), int(m.get("n_rot", 1))
+    if iso == 0:
+        F0 = frame_from_angles(m["axis_theta"], m["axis_phi"], m.get("axis_psi", 0.0))
+        c, w = orientation_nodes(m["axis_theta"], m["axis_phi"], m["sigma_orient"], ng, npsi, False)
+        frames = np.stack([(_rotation_taking(F0[2], ci) @ F0.T).T for ci in c])
+        return frames, w
+    xt, wt = gauss_legendre(ng)
+    xp, wp = gauss_legendre(npsi)
+    xr, wr = gauss_legendre(nr)
+    if iso == 1:
+        th = np.arccos(np.clip(xt, -1.0, 1.0))            # cos theta uniform on [-1, 1]
+    else:
+        th = 0.5 * math.pi * (xt + 1.0)
+    ph = math.pi * (xp + 1.0)
+    ps = math.pi * (xr + 1.0)
+    frames, w = [], []
+    for i, t in enumerate(th):
+        for j, f in enumerate(ph):
+            for k, q in enumerate(ps):
+                frames.append(frame_from_angles(t, f, q))
+                w.append(wt[i] * wp[j] * wr[k])
+    w = np.array(w)
+    return np.stack(frames), w / w.sum()
+
+
 def axis_from_angles(theta: float, phi: float):
     n = np.array([math.sin(theta) * math.cos(phi), math.sin(theta) * math.sin(phi),
                   math.cos(theta)])
@@ -243,7 +303,10 @@ class Prepared:
         kind = int(m["kind"])
         self.poly_r, self.poly_w = radius_nodes(m)
         iso = int(m["isotropic"])
-        if kind in (2, 3) and iso == 2:
+        if kind in (4, 5):
+            fr, self.orient_w = frame_nodes(m)
+            self.orient_c = fr.reshape(-1, 9)
+        elif kind in (2, 3) and iso == 2:
             self.orient_c, self.orient_w = uniform_angle_nodes(int(m["n_gamma"]), int(m["n_psi"]))
         elif kind in (2, 3):
             self.orient_c, self.orient_w = orientation_nodes(
@@ -267,7 +330,8 @@ class Prepared:
                         orient_c=self.orient_c.ctypes.data_as(_DP),
                         orient_w=self.orient_w.ctypes.data_as(_DP),
                         event=int(m.get("sampling", 0)), orient_mode=iso, poly=float(m["poly"]),
-                        axis_theta=float(m["axis_theta"]), axis_phi=float(m["axis_phi"]))
+                        axis_theta=float(m["axis_theta"]), axis_phi=float(m["axis_phi"]),
+                        radius_b=float(m.get("radius_b", 0.0)), axis_psi=float(m.get("axis_psi", 0.0)))
 
 
 def _inst(instrument):
@@ -355,6 +419,19 @@ def geometry_records(instrument, n, seed, first=0, exp_id=0):
                                   pix.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                                   q.ctypes.data_as(_DP), pref.ctypes.data_as(_DP), wt.ctypes.data_as(_DP))
     return dict(pixel=pix, q=q, pref=pref, trans=wt)
+
+
+def frame(theta, phi, psi):
+    f = np.empty(9)
+    lib().oracle_frame(float(theta), float(phi), float(psi), f.ctypes.data_as(_DP))
+    return f.reshape(3, 3)
+
+
+def event_frame(mode, theta, phi, psi, wa, wb, wc):
+    f = np.empty(9)
+    lib().oracle_event_frame(int(mode), float(theta), float(phi), float(psi), int(wa) & 0xFFFFFFFF,
+                             int(wb) & 0xFFFFFFFF, int(wc) & 0xFFFFFFFF, f.ctypes.data_as(_DP))
+    return f.reshape(3, 3)
 
 
 def erfcinv(y):

@@ -101,6 +101,12 @@ typedef struct {
                               2 theta ~ U[0, pi], phi ~ U[0, 2 pi] */
     double poly;           /* sigma / mean of the Gaussian radius (0: monodisperse) */
     double axis_theta, axis_phi;   /* fixed axis (orient_mode 0) */
+    /* particles without a symmetry axis (kinds 4, 5; Sec. II.B): sizes
+     * (radius, radius_b, radius_polar) along the particle axes (A, B, C),
+     * the orientation nodes are frames (A, B, C) of 9 doubles, and the
+     * polydisperse nodes poly_r / radius scale all three sizes alike */
+    double radius_b;
+    double axis_psi;       /* rotation about C of the fixed frame (event mode 0) */
 } oracle_model;
 
 /* --------------------------------------------------------- model pieces */
@@ -242,6 +248,38 @@ double oracle_dsigma(const oracle_model *m, const double q[3])
             }
             sum += m->orient_w[o] * inner;
         }
+    } else if (m->kind == 4 || m->kind == 5) {
+        /* triaxial ellipsoid (semi-axes a, b, c): F = drho V f(x),
+         * x = |(a Q_A, b Q_B, c Q_C)|, V = 4/3 pi a b c (Eq. 1 on the affine
+         * image of a sphere); rectangular parallelepiped (half-edges a, b, c):
+         * F = drho V sinc(a Q_A) sinc(b Q_B) sinc(c Q_C), V = 8 a b c. */
+        double drho = m->sld - m->sld_solvent;
+        double a0 = m->radius, b0 = m->radius_b, c0 = m->radius_polar;
+        double v0 = (m->kind == 4 ? 4.0 / 3.0 * PI : 8.0) * a0 * b0 * c0;
+        for (int64_t i = 0; i < np; ++i) {
+            double s = m->poly_r[i] / m->radius;
+            vmean += m->poly_w[i] * v0 * s * s * s;
+        }
+        for (int64_t o = 0; o < m->n_orient; ++o) {
+            const double *f = m->orient_c + 9 * o;
+            double qa = q[0] * f[0] + q[1] * f[1] + q[2] * f[2];
+            double qb = q[0] * f[3] + q[1] * f[4] + q[2] * f[5];
+            double qc = q[0] * f[6] + q[1] * f[7] + q[2] * f[8];
+            double inner = 0.0;
+            for (int64_t i = 0; i < np; ++i) {
+                double s = m->poly_r[i] / m->radius;
+                double V = v0 * s * s * s, F;
+                if (m->kind == 4) {
+                    double xa = s * a0 * qa, xb = s * b0 * qb, xc = s * c0 * qc;
+                    F = drho * V * oracle_sphere_f(sqrt(xa * xa + xb * xb + xc * xc));
+                } else {
+                    F = drho * V * oracle_sinc(s * a0 * qa) * oracle_sinc(s * b0 * (SAS_MUT == 13 ? qc : qb))
+                      * oracle_sinc(s * c0 * (SAS_MUT == 13 ? qb : qc));
+                }
+                inner += m->poly_w[i] * F * F;
+            }
+            sum += m->orient_w[o] * inner;
+        }
     } else {                         /* ellipsoid of revolution: equatorial radius polydisperse */
         double drho = m->sld - m->sld_solvent;
         double rp = m->radius_polar;
@@ -338,6 +376,33 @@ void oracle_event_axis(int64_t mode, double theta0, double phi0, uint32_t xa, ui
     c[0] = st * cos(ph); c[1] = st * sin(ph); c[2] = ct;
 }
 
+/* Particle frame (A, B, C) from the three angles (Sec. II.B): C along
+ * (theta, phi), A and B the spherical unit vectors e_theta, e_phi of C
+ * rotated by psi about C. */
+void oracle_frame(double theta, double phi, double psi, double f[9])
+{
+    double st = sin(theta), ct = cos(theta), sp = sin(phi), cp = cos(phi);
+    double sq = sin(psi), cq = cos(psi);
+    double et[3] = {ct * cp, ct * sp, -st}, ep[3] = {-sp, cp, 0.0};
+    for (int k = 0; k < 3; ++k) {
+        f[k] = cq * et[k] + sq * ep[k];
+        f[3 + k] = -sq * et[k] + cq * ep[k];
+    }
+    f[6] = st * cp; f[7] = st * sp; f[8] = ct;
+}
+
+/* Frame of one event for the particles without a symmetry axis: mode 1 a
+ * uniform rotation (cos theta = 1 - 2u, phi, psi uniform), mode 2 the
+ * angles uniform, theta ~ U[0, pi], phi, psi ~ U[0, 2 pi]; mode 0 the
+ * fixed frame. */
+void oracle_event_frame(int64_t mode, double theta0, double phi0, double psi0, uint32_t xa, uint32_t xb,
+                        uint32_t xc, double f[9])
+{
+    if (mode == 0) { oracle_frame(theta0, phi0, psi0, f); return; }
+    double th = mode == 1 ? acos(1.0 - 2.0 * u01(xa)) : PI * u01(xa);
+    oracle_frame(th, 2.0 * PI * u01(xb), 2.0 * PI * u01(xc), f);
+}
+
 /* Volume of one particle of the polydisperse parameter r (the quantity the
  * cross section is normalised by through <V>). */
 static double model_volume(const oracle_model *m, double r)
@@ -345,12 +410,16 @@ static double model_volume(const oracle_model *m, double r)
     if (m->kind == 0) return sphere_volume(r);
     if (m->kind == 1) return sphere_volume(r + m->thickness);
     if (m->kind == 2) return PI * r * r * m->length;
+    if (m->kind == 4 || m->kind == 5) {
+        double s = r / m->radius;
+        return (m->kind == 4 ? 4.0 / 3.0 * PI : 8.0) * m->radius * m->radius_b * m->radius_polar * s * s * s;
+    }
     return 4.0 / 3.0 * PI * m->radius_polar * r * r;
 }
 
 /* Per-event estimate of dSigma/dOmega(Q): (phi / <V>) |F(Q; r, c)|^2 S(Q)
  * for the radius r and axis c drawn from Philox block 2 of the history
- * (words: radius, axis polar, axis azimuth, spare). <V> is the mean over
+ * (words: radius, axis polar, axis azimuth, rotation about the axis). <V> is the mean over
  * the radius distribution (the model's nodes). Its expectation over the
  * draws is the quadrature average of oracle_dsigma with matching nodes. */
 double oracle_dsigma_event(const oracle_model *m, const double q[3], uint64_t seed,
@@ -361,8 +430,11 @@ double oracle_dsigma_event(const oracle_model *m, const double q[3], uint64_t se
     uint32_t x[4];
     oracle_philox4x32_10(c2, key, x);
     double r = oracle_event_radius(m->radius, m->poly, x[0]);
-    double c[3];
-    oracle_event_axis(m->kind >= 2 ? m->orient_mode : 0, m->axis_theta, m->axis_phi, x[1], x[2], c);
+    double c[9];
+    if (m->kind == 4 || m->kind == 5)
+        oracle_event_frame(m->orient_mode, m->axis_theta, m->axis_phi, m->axis_psi, x[1], x[2], x[3], c);
+    else
+        oracle_event_axis(m->kind >= 2 ? m->orient_mode : 0, m->axis_theta, m->axis_phi, x[1], x[2], c);
     double one = 1.0;
     oracle_model single = *m;
     single.n_poly = 1; single.poly_r = &r; single.poly_w = &one;

@@ -35,8 +35,10 @@ from dataclasses import dataclass, field, asdict
 import numpy as np
 
 SPHERE, CORE_SHELL, CYLINDER, ELLIPSOID = 0, 1, 2, 3
+TRIAXIAL_ELLIPSOID, PARALLELEPIPED = 4, 5        # no symmetry axis: sizes along A, B, C
 MODEL_NAMES = {SPHERE: "sphere", CORE_SHELL: "core_shell", CYLINDER: "cylinder",
-               ELLIPSOID: "ellipsoid"}
+               ELLIPSOID: "ellipsoid", TRIAXIAL_ELLIPSOID: "triaxial_ellipsoid",
+               PARALLELEPIPED: "parallelepiped"}
 SQ_NONE, SQ_HARD_SPHERE_PY = 0, 1
 FP32, FP64 = 0, 1
 QUADRATURE, PER_EVENT = 0, 1              # sampling: averages over nodes / one draw per history
@@ -75,10 +77,11 @@ class Model:
     n_gamma: int = 1
     n_psi: int = 1
     isotropic: int = CAP             # CAP (Gaussian about the mean axis), ISOTROPIC, UNIFORM_ANGLES
-    radius: float = 50.0            # sphere R, core radius, cylinder R, ellipsoid equatorial R
+    radius: float = 50.0            # sphere R, core radius, cylinder R, ellipsoid equatorial R,
+                                    # 3-axis models: semi-axis / half-edge along A
     thickness: float = 0.0          # core-shell shell thickness
     length: float = 0.0             # cylinder length
-    radius_polar: float = 0.0       # ellipsoid polar radius (along the axis)
+    radius_polar: float = 0.0       # ellipsoid polar radius (along the axis); 3-axis models: along C
     sld: float = 2.0e-6             # particle (core) SLD
     sld_shell: float = 0.0
     sld_solvent: float = 0.0
@@ -92,6 +95,9 @@ class Model:
     sampling: int = QUADRATURE      # PER_EVENT: one radius and axis drawn per history (Sec. II.B)
     poly_dist: int = SCHULZ         # GAUSSIAN: N(R, (poly R)^2) restricted to R > 0
     radial_table: int = 0           # cylinder: 1 interpolates the polydisperse radial sum from a table
+    radius_b: float = 0.0           # triaxial ellipsoid semi-axis / parallelepiped half-edge along B
+    axis_psi: float = 0.0           # rad, rotation of the particle frame about its C axis
+    n_rot: int = 1                  # quadrature nodes in psi (uniform rotations / angles)
 
     def as_dict(self):
         return asdict(self)

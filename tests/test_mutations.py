@@ -27,6 +27,7 @@ MUTATIONS = {
     11: ("core-shell outer term with the core volume", "core_shell"),
     12: ("per-event radius drawn without the positivity restriction", "restricted_gaussian",
          "test_event_oracle.py"),
+    13: ("parallelepiped with Q_B and Q_C swapped", "eq1_volume", "test_triaxial_oracle.py"),
 }
 
 
