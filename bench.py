@@ -328,6 +328,12 @@ def per_event(stream):
                      dict(cy, poly_dist=W.GAUSSIAN, isotropic=W.UNIFORM_ANGLES),
                      "cylinder R=20 L=400 A, Gaussian 0.1 on R (40 nodes), axis theta ~ U[0,pi], phi ~ U[0,2pi] "
                      "(76x76 nodes for the quadrature), 256x256", 200_000_000, 2_000_000),
+        "parallelepiped": (W.instrument(),
+                           dict(kind=W.PARALLELEPIPED, radius=15.0, radius_b=25.0, radius_polar=60.0, sld=2e-6,
+                                volume_fraction=0.01, poly=0.1, poly_dist=W.GAUSSIAN, n_poly=20,
+                                isotropic=W.UNIFORM_ANGLES, n_gamma=16, n_psi=16, n_rot=16),
+                           "parallelepiped, half-edges 15 x 25 x 60 A, Gaussian 0.1 (20 nodes), theta, phi, psi "
+                           "uniform (16^3 frames for the quadrature), 128x128", 200_000_000, 2_000_000),
     }
     res = {}
     for name, (inst, base, desc, n_ev, n_q) in cases.items():

@@ -55,7 +55,9 @@ typedef enum sas_status {
     SAS_ERR_NUMERIC = 7      /* non-finite value detected */
 } sas_status;
 
-enum { SAS_SPHERE = 0, SAS_CORE_SHELL = 1, SAS_CYLINDER = 2, SAS_ELLIPSOID = 3 };
+enum { SAS_SPHERE = 0, SAS_CORE_SHELL = 1, SAS_CYLINDER = 2, SAS_ELLIPSOID = 3,
+       /* no symmetry axis (Sec. II.B): sizes along the particle axes A, B, C */
+       SAS_TRIAXIAL_ELLIPSOID = 4, SAS_PARALLELEPIPED = 5 };
 enum { SAS_SQ_NONE = 0, SAS_SQ_HARD_SPHERE_PY = 1 };
 enum { SAS_FP32 = 0, SAS_FP64 = 1 };
 /* sampling: average every history over the quadrature nodes, or draw one
@@ -89,7 +91,8 @@ typedef struct sas_instrument {
 
 /* Sample model (Eqs. 1-4, 7, 8; polydispersity and orientation Sec. II.B). */
 typedef struct sas_model_desc {
-    int64_t kind;            /* SAS_SPHERE, SAS_CORE_SHELL, SAS_CYLINDER, SAS_ELLIPSOID */
+    int64_t kind;            /* SAS_SPHERE, SAS_CORE_SHELL, SAS_CYLINDER, SAS_ELLIPSOID,
+                                SAS_TRIAXIAL_ELLIPSOID, SAS_PARALLELEPIPED */
     int64_t sq_kind;         /* SAS_SQ_NONE or SAS_SQ_HARD_SPHERE_PY */
     int64_t precision;       /* SAS_FP32 (tallies FP32 Kahan + FP64 reduction) or SAS_FP64 */
     int64_t n_poly;          /* Schulz nodes of the polydisperse radius (1..64) */
@@ -128,6 +131,19 @@ typedef struct sas_model_desc {
                                 most 1e-7 G(0), 1e-13 for FP64 models; at most
                                 SAS_MAX_RADIAL_TABLE points, else the direct sum is kept);
                                 0 sums over the radius nodes */
+    /* The 3-axis kinds: triaxial ellipsoid with semi-axes (radius, radius_b,
+     * radius_polar) along (A, B, C), F = drho V f(|(a Q_A, b Q_B, c Q_C)|),
+     * V = 4/3 pi a b c; rectangular parallelepiped with half-edges (radius,
+     * radius_b, radius_polar), F = drho V sinc(a Q_A) sinc(b Q_B) sinc(c Q_C),
+     * V = 8 a b c (Eq. 1 for both bodies). The frame: C along (axis_theta,
+     * axis_phi), A and B rotated by axis_psi about C. Orientation laws as
+     * for the uniaxial kinds (isotropic 0: the C axis in the Gaussian cap,
+     * the mean frame carried along; 1: uniform rotations; 2: theta, phi and
+     * psi uniform), with n_rot nodes in psi. The polydisperse factor
+     * radius_i / radius scales all three sizes. */
+    double radius_b;         /* 3-axis kinds: size along B */
+    double axis_psi;         /* 3-axis kinds: rotation of the frame about C, rad */
+    int64_t n_rot;           /* 3-axis kinds: quadrature nodes in psi (1..128) */
 } sas_model_desc;
 
 typedef struct sas_experiment sas_experiment;   /* opaque, library-owned */

@@ -60,6 +60,11 @@ double host_flops_per_history(const sas_model_desc& m, int np, int no)
     if (m.sampling == SAS_PER_EVENT) { np = 1; no = 1; }
     if (m.kind == SAS_CYLINDER && m.radial_table && m.sampling == SAS_QUADRATURE)
         return no * 60.0 + 150.0 + (m.sq_kind == SAS_SQ_HARD_SPHERE_PY ? 40.0 : 0.0);
+    if (m.kind == SAS_TRIAXIAL_ELLIPSOID || m.kind == SAS_PARALLELEPIPED) {
+        const int frames = m.sampling == SAS_PER_EVENT ? 1 : std::max(no / 3, 1);
+        return frames * (20.0 + np * (m.kind == SAS_TRIAXIAL_ELLIPSOID ? 36.0 : 66.0)) + 150.0 +
+               (m.sq_kind == SAS_SQ_HARD_SPHERE_PY ? 40.0 : 0.0);
+    }
     double per;
     if (m.kind == SAS_SPHERE) per = np * 36.0;
     else if (m.kind == SAS_CORE_SHELL) per = np * 62.0 + 20.0;
@@ -242,6 +247,87 @@ int uniform_angle_nodes(int nt, int np, double* c, double* wout)
     return k;
 }
 
+// Frame (rows A, B, C) of the angles: C along (theta, phi); A, B the unit
+// vectors e_theta, e_phi of C rotated by psi about C.
+void frame_of(double theta, double phi, double psi, double* f)
+{
+    const double st = std::sin(theta), ct = std::cos(theta), sp = std::sin(phi), cp = std::cos(phi);
+    const double sq = std::sin(psi), cq = std::cos(psi);
+    const double et[3] = {ct * cp, ct * sp, -st}, ep[3] = {-sp, cp, 0.0};
+    for (int k = 0; k < 3; ++k) {
+        f[k] = cq * et[k] + sq * ep[k];
+        f[3 + k] = -sq * et[k] + cq * ep[k];
+    }
+    f[6] = st * cp;
+    f[7] = st * sp;
+    f[8] = ct;
+}
+
+// Orientation nodes of a particle without a symmetry axis: frames (9 doubles
+// each) and normalised weights. isotropic 0: the C axis on the Gaussian-cap
+// nodes, the mean frame carried along by the smallest rotation taking its C
+// to the node's (Rodrigues); 1: uniform rotations, Gauss-Legendre in
+// cos theta, phi and psi; 2: theta, phi and psi uniform.
+int frame_nodes(const sas_model_desc& m, std::vector<double>& fr, std::vector<double>& w)
+{
+    fr.clear();
+    w.clear();
+    if (m.isotropic == 0) {
+        double f0[9];
+        frame_of(m.axis_theta, m.axis_phi, m.axis_psi, f0);
+        const int nmax = std::max((int)(m.n_gamma * m.n_psi), 1);
+        std::vector<double> c((size_t)3 * nmax), wc(nmax);
+        const int n = orientation_nodes(m.axis_theta, m.axis_phi, m.sigma_orient, (int)m.n_gamma, (int)m.n_psi, 0,
+                                        c.data(), wc.data());
+        for (int o = 0; o < n; ++o) {
+            const double* u = f0 + 6;    // mean C
+            const double* v = c.data() + 3 * o;
+            double k[3] = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0]};
+            const double sn = std::sqrt(k[0] * k[0] + k[1] * k[1] + k[2] * k[2]);
+            const double cs = u[0] * v[0] + u[1] * v[1] + u[2] * v[2];
+            double R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+            if (sn > 1e-15) {
+                for (double& x : k) x /= sn;
+                const double K[9] = {0, -k[2], k[1], k[2], 0, -k[0], -k[1], k[0], 0};
+                double K2[9];
+                for (int r = 0; r < 3; ++r)
+                    for (int q = 0; q < 3; ++q) {
+                        K2[3 * r + q] = 0.0;
+                        for (int t = 0; t < 3; ++t) K2[3 * r + q] += K[3 * r + t] * K[3 * t + q];
+                    }
+                for (int e = 0; e < 9; ++e) R[e] += sn * K[e] + (1.0 - cs) * K2[e];
+            }
+            for (int row = 0; row < 3; ++row)
+                for (int r = 0; r < 3; ++r) {
+                    double x = 0.0;
+                    for (int q = 0; q < 3; ++q) x += R[3 * r + q] * f0[3 * row + q];
+                    fr.push_back(x);
+                }
+            w.push_back(wc[o]);
+        }
+        return n;
+    }
+    const int nt = (int)m.n_gamma, np = (int)m.n_psi, nr = (int)m.n_rot;
+    std::vector<double> xt(nt), wt(nt), xp(np), wp(np), xr(nr), wr(nr);
+    gauss_legendre(nt, xt.data(), wt.data());
+    gauss_legendre(np, xp.data(), wp.data());
+    gauss_legendre(nr, xr.data(), wr.data());
+    double tot = 0.0;
+    for (int i = 0; i < nt; ++i) {
+        const double th = m.isotropic == 1 ? std::acos(std::max(-1.0, std::min(1.0, xt[i]))) : 0.5 * M_PI * (xt[i] + 1.0);
+        for (int j = 0; j < np; ++j)
+            for (int k = 0; k < nr; ++k) {
+                double f[9];
+                frame_of(th, M_PI * (xp[j] + 1.0), M_PI * (xr[k] + 1.0), f);
+                fr.insert(fr.end(), f, f + 9);
+                w.push_back(wt[i] * wp[j] * wr[k]);
+                tot += w.back();
+            }
+    }
+    for (double& x : w) x /= tot;
+    return (int)w.size();
+}
+
 // Cylinder radial table (G, h G') on [0, xmax] and its midpoint error.
 double cylinder_radial_table(const double* r, const double* w, int np, double rbar, double xmax, int n,
                              double* G, double* D)
@@ -396,6 +482,14 @@ sas_status build_model_tables(const sas_model_desc& m, ModelTables& t, double q_
             const double F0 = (m.sld - m.sld_solvent) * V;
             p[0] = ri * ri; p[1] = w[i] * F0 * F0; p[2] = ri; p[3] = 1.0 / ri; p[4] = 1.0 / std::sqrt(ri);
             vmean += w[i] * V;
+        } else if (m.kind == SAS_TRIAXIAL_ELLIPSOID || m.kind == SAS_PARALLELEPIPED) {
+            const double sc = ri / m.radius;   // one polydisperse factor for the three sizes
+            const double V = (m.kind == SAS_TRIAXIAL_ELLIPSOID ? 4.0 / 3.0 * pi : 8.0) * m.radius * m.radius_b *
+                             m.radius_polar * sc * sc * sc;
+            const double F0 = (m.sld - m.sld_solvent) * V;
+            p[0] = sc;
+            p[1] = (m.kind == SAS_TRIAXIAL_ELLIPSOID ? 9.0 : 1.0) * w[i] * F0 * F0;
+            vmean += w[i] * V;
         } else {
             const double V = 4.0 / 3.0 * pi * m.radius_polar * ri * ri;
             const double F0 = (m.sld - m.sld_solvent) * V;
@@ -406,7 +500,20 @@ sas_status build_model_tables(const sas_model_desc& m, ModelTables& t, double q_
     t.n_poly = npoly;
     t.scale = m.volume_fraction / vmean;
     t.vmean = vmean;
-    if (m.kind == SAS_CYLINDER || m.kind == SAS_ELLIPSOID) {
+    if (m.kind == SAS_TRIAXIAL_ELLIPSOID || m.kind == SAS_PARALLELEPIPED) {
+        std::vector<double> fr, wf;
+        const int nf = frame_nodes(m, fr, wf);
+        t.orient.assign((size_t)3 * nf * SAS_ORIENT_STRIDE, 0.0);
+        for (int o = 0; o < nf; ++o)
+            for (int row = 0; row < 3; ++row) {
+                double* d = t.orient.data() + ((size_t)3 * o + row) * SAS_ORIENT_STRIDE;
+                d[0] = fr[9 * o + 3 * row];
+                d[1] = fr[9 * o + 3 * row + 1];
+                d[2] = fr[9 * o + 3 * row + 2];
+                d[3] = row == 0 ? wf[o] : 0.0;
+            }
+        t.n_orient = 3 * nf;
+    } else if (m.kind == SAS_CYLINDER || m.kind == SAS_ELLIPSOID) {
         const int nmax = (int)(m.n_gamma * m.n_psi);
         std::vector<double> c((size_t)3 * std::max(nmax, 1)), wo(std::max(nmax, 1));
         const int no = m.isotropic == 2
@@ -474,8 +581,9 @@ sas_status build_model_tables(const sas_model_desc& m, ModelTables& t, double q_
         t.n_poly = 1;
         t.n_rad = 1;
         if (t.n_orient > 0) {
-            t.orient.resize(SAS_ORIENT_STRIDE);
-            t.n_orient = 1;
+            const int rows = (m.kind == SAS_TRIAXIAL_ELLIPSOID || m.kind == SAS_PARALLELEPIPED) ? 3 : 1;
+            t.orient.resize((size_t)rows * SAS_ORIENT_STRIDE);
+            t.n_orient = rows;
         }
     }
     t.half_length = 0.5 * m.length;
@@ -526,6 +634,16 @@ ModelConst<T> model_const(const sas_model_desc& m, const ModelTables& t)
     c.ev_axis[0] = (T)(std::sin(m.axis_theta) * std::cos(m.axis_phi));
     c.ev_axis[1] = (T)(std::sin(m.axis_theta) * std::sin(m.axis_phi));
     c.ev_axis[2] = (T)std::cos(m.axis_theta);
+    c.ax_a = (T)m.radius;
+    c.ax_b = (T)m.radius_b;
+    c.ax_c = (T)m.radius_polar;
+    {
+        double f[9];
+        frame_of(m.axis_theta, m.axis_phi, m.axis_psi, f);
+        for (int k = 0; k < 6; ++k) c.ev_frame[k] = (T)f[k];
+    }
+    if (m.kind == SAS_TRIAXIAL_ELLIPSOID || m.kind == SAS_PARALLELEPIPED)
+        c.orient_mode = (int)m.isotropic;
     c.n_rad = t.n_rad;
     c.n_tab = t.n_tab;
     c.tab_inv_h = (T)t.tab_inv_h;
@@ -591,7 +709,14 @@ sas_status validate_instrument(const sas_instrument* in)
 sas_status validate_model(const sas_model_desc* m)
 {
     if (!m) return fail(SAS_ERR_ARG, "model is NULL");
-    if (m->kind < 0 || m->kind > 3) return fail(SAS_ERR_ARG, "unknown model kind");
+    if (m->kind < 0 || m->kind > 5) return fail(SAS_ERR_ARG, "unknown model kind");
+    const bool axes3 = m->kind == SAS_TRIAXIAL_ELLIPSOID || m->kind == SAS_PARALLELEPIPED;
+    if (axes3 && (!(m->radius_b > 0.0) || !(m->radius_polar > 0.0) || !std::isfinite(m->radius_b) ||
+                  !std::isfinite(m->axis_psi)))
+        return fail(SAS_ERR_ARG, "3-axis models need radius, radius_b, radius_polar > 0 and a finite axis_psi");
+    if (axes3 && (m->n_rot < 1 || m->n_rot > SAS_MAX_ORIENT_SIDE)) return fail(SAS_ERR_ARG, "n_rot must be in [1, 128]");
+    if (axes3 && m->isotropic != 0 && m->n_gamma * m->n_psi * m->n_rot > (1 << 17))
+        return fail(SAS_ERR_ARG, "n_gamma * n_psi * n_rot must be <= 131072");
     if (m->sq_kind != SAS_SQ_NONE && m->sq_kind != SAS_SQ_HARD_SPHERE_PY) return fail(SAS_ERR_ARG, "unknown S(Q) kind");
     if (m->precision != SAS_FP32 && m->precision != SAS_FP64) return fail(SAS_ERR_ARG, "unknown precision");
     if (m->n_poly < 1 || m->n_poly > SAS_MAX_POLY) return fail(SAS_ERR_ARG, "n_poly must be in [1, 64]");
@@ -617,7 +742,7 @@ sas_status validate_model(const sas_model_desc* m)
         if (m->poly > 0.0 && m->poly_dist != SAS_POLY_GAUSSIAN)
             return fail(SAS_ERR_ARG, "per-event sampling draws Gaussian radii (Sec. II.B): set poly_dist to "
                                      "SAS_POLY_GAUSSIAN or poly to 0");
-        if ((m->kind == SAS_CYLINDER || m->kind == SAS_ELLIPSOID) && m->isotropic == 0 && m->sigma_orient > 0.0)
+        if ((m->kind >= SAS_CYLINDER) && m->isotropic == 0 && m->sigma_orient > 0.0)
             return fail(SAS_ERR_ARG, "per-event axes are uniform on the sphere (isotropic 1), in the angles "
                                      "(isotropic 2) or fixed (sigma_orient 0); the Gaussian cap is a quadrature option");
     }
@@ -672,6 +797,8 @@ cudaError_t dispatch_trace(sas_experiment* e, const TraceParams<T>& P, int* grid
     case SAS_SPHERE: return Launcher<T, SAS_SPHERE>::trace(P, e->cfg, e->sm_count, e->stream, grid);
     case SAS_CORE_SHELL: return Launcher<T, SAS_CORE_SHELL>::trace(P, e->cfg, e->sm_count, e->stream, grid);
     case SAS_CYLINDER: return Launcher<T, SAS_CYLINDER>::trace(P, e->cfg, e->sm_count, e->stream, grid);
+    case SAS_TRIAXIAL_ELLIPSOID: return Launcher<T, SAS_TRIAXIAL_ELLIPSOID>::trace(P, e->cfg, e->sm_count, e->stream, grid);
+    case SAS_PARALLELEPIPED: return Launcher<T, SAS_PARALLELEPIPED>::trace(P, e->cfg, e->sm_count, e->stream, grid);
     default: return Launcher<T, SAS_ELLIPSOID>::trace(P, e->cfg, e->sm_count, e->stream, grid);
     }
 }
@@ -683,6 +810,8 @@ cudaError_t dispatch_records(sas_experiment* e, const TraceParams<T>& P)
     case SAS_SPHERE: return Launcher<T, SAS_SPHERE>::records(P, e->stream);
     case SAS_CORE_SHELL: return Launcher<T, SAS_CORE_SHELL>::records(P, e->stream);
     case SAS_CYLINDER: return Launcher<T, SAS_CYLINDER>::records(P, e->stream);
+    case SAS_TRIAXIAL_ELLIPSOID: return Launcher<T, SAS_TRIAXIAL_ELLIPSOID>::records(P, e->stream);
+    case SAS_PARALLELEPIPED: return Launcher<T, SAS_PARALLELEPIPED>::records(P, e->stream);
     default: return Launcher<T, SAS_ELLIPSOID>::records(P, e->stream);
     }
 }
@@ -696,6 +825,8 @@ cudaError_t dispatch_eval(sas_experiment* e, const ModelConst<T>& mc, const T* q
     case SAS_SPHERE: return Launcher<T, SAS_SPHERE>::eval(mc, poly, orient, q, out, n, e->stream);
     case SAS_CORE_SHELL: return Launcher<T, SAS_CORE_SHELL>::eval(mc, poly, orient, q, out, n, e->stream);
     case SAS_CYLINDER: return Launcher<T, SAS_CYLINDER>::eval(mc, poly, orient, q, out, n, e->stream);
+    case SAS_TRIAXIAL_ELLIPSOID: return Launcher<T, SAS_TRIAXIAL_ELLIPSOID>::eval(mc, poly, orient, q, out, n, e->stream);
+    case SAS_PARALLELEPIPED: return Launcher<T, SAS_PARALLELEPIPED>::eval(mc, poly, orient, q, out, n, e->stream);
     default: return Launcher<T, SAS_ELLIPSOID>::eval(mc, poly, orient, q, out, n, e->stream);
     }
 }

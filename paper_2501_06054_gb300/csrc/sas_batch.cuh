@@ -130,6 +130,8 @@ __global__ void __launch_bounds__(1024) batch_kernel(const BatchParams P)
             case SAS_SPHERE: batch_item<SAS_SPHERE, HIST_OK>(P, mc, s_poly, orient, w, h, seed, tr); break;
             case SAS_CORE_SHELL: batch_item<SAS_CORE_SHELL, HIST_OK>(P, mc, s_poly, orient, w, h, seed, tr); break;
             case SAS_CYLINDER: batch_item<SAS_CYLINDER, HIST_OK>(P, mc, s_poly, orient, w, h, seed, tr); break;
+            case SAS_TRIAXIAL_ELLIPSOID: batch_item<SAS_TRIAXIAL_ELLIPSOID, HIST_OK>(P, mc, s_poly, orient, w, h, seed, tr); break;
+            case SAS_PARALLELEPIPED: batch_item<SAS_PARALLELEPIPED, HIST_OK>(P, mc, s_poly, orient, w, h, seed, tr); break;
             default: batch_item<SAS_ELLIPSOID, HIST_OK>(P, mc, s_poly, orient, w, h, seed, tr); break;
             }
         } else {
@@ -137,6 +139,8 @@ __global__ void __launch_bounds__(1024) batch_kernel(const BatchParams P)
             case SAS_SPHERE: batch_item<SAS_SPHERE, 0>(P, mc, s_poly, orient, w, h, seed, tr); break;
             case SAS_CORE_SHELL: batch_item<SAS_CORE_SHELL, 0>(P, mc, s_poly, orient, w, h, seed, tr); break;
             case SAS_CYLINDER: batch_item<SAS_CYLINDER, 0>(P, mc, s_poly, orient, w, h, seed, tr); break;
+            case SAS_TRIAXIAL_ELLIPSOID: batch_item<SAS_TRIAXIAL_ELLIPSOID, 0>(P, mc, s_poly, orient, w, h, seed, tr); break;
+            case SAS_PARALLELEPIPED: batch_item<SAS_PARALLELEPIPED, 0>(P, mc, s_poly, orient, w, h, seed, tr); break;
             default: batch_item<SAS_ELLIPSOID, 0>(P, mc, s_poly, orient, w, h, seed, tr); break;
             }
         }

@@ -318,6 +318,46 @@ __device__ __forceinline__ T avg_cylinder_tab(const T qv[3], const T* __restrict
     return k.s;
 }
 
+// Particles without a symmetry axis (Eq. 1 for the body): per frame
+// (rows A, B, C of the orientation table, weight in row A) and polydisperse
+// scale s_i (poly node: s_i, coefficient):
+//   triaxial ellipsoid  F = drho V(s) 3 g(s |(a Q_A, b Q_B, c Q_C)|)
+//   parallelepiped      F = drho V(s) sinc(s a Q_A) sinc(s b Q_B) sinc(s c Q_C)
+template <typename T, int KIND>
+__device__ __forceinline__ T avg_axes3(const T qv[3], const T* __restrict__ poly, int np,
+                                       const T* __restrict__ orient, int nrows, const ModelConst<T>& mc)
+{
+    Kahan<T> k;
+    for (int o = 0; o + 2 < nrows; o += 3) {
+        const T* A = orient + 4 * o;
+        const T* B = A + 4;
+        const T* C = A + 8;
+        const T qa = mc.ax_a * fma(qv[0], A[0], fma(qv[1], A[1], qv[2] * A[2]));
+        const T qb = mc.ax_b * fma(qv[0], B[0], fma(qv[1], B[1], qv[2] * B[2]));
+        const T qc = mc.ax_c * fma(qv[0], C[0], fma(qv[1], C[1], qv[2] * C[2]));
+        T inner = 0;
+        if (KIND == SAS_TRIAXIAL_ELLIPSOID) {
+            const T x0 = M<T>::sqrt_(fma(qa, qa, fma(qb, qb, qc * qc)));
+            for (int i = 0; i < np; ++i) {
+                const T x = poly[SAS_POLY_STRIDE * i] * x0;
+                const T g = M<T>::sphere_g(x, M<T>::rcp(x));
+                inner = fma(poly[SAS_POLY_STRIDE * i + 1], g * g, inner);
+            }
+        } else {
+            const T ya0 = fabs(qa), yb0 = fabs(qb), yc0 = fabs(qc);
+            for (int i = 0; i < np; ++i) {
+                const T sc = poly[SAS_POLY_STRIDE * i];
+                const T ya = sc * ya0, yb = sc * yb0, yc = sc * yc0;
+                const T amp = M<T>::sinc(ya, M<T>::rcp(ya)) * M<T>::sinc(yb, M<T>::rcp(yb)) *
+                              M<T>::sinc(yc, M<T>::rcp(yc));
+                inner = fma(poly[SAS_POLY_STRIDE * i + 1], amp * amp, inner);
+            }
+        }
+        k.add(A[3] * inner);
+    }
+    return k.s;
+}
+
 template <typename T>
 __device__ __forceinline__ T avg_ellipsoid(const T qv[3], const T* __restrict__ poly, int np,
                                            const T* __restrict__ orient, int no, T rp2)
@@ -360,8 +400,10 @@ __device__ __forceinline__ T dsigma(const T qv[3], const ModelConst<T>& mc,
     } else if (KIND == SAS_CYLINDER) {
         avg = mc.n_tab > 0 ? avg_cylinder_tab<T>(qv, poly, mc, orient, mc.n_orient)
                            : avg_cylinder<T>(qv, poly, mc.n_rad, orient, mc.n_orient, mc.half_length);
-    } else {
+    } else if (KIND == SAS_ELLIPSOID) {
         avg = avg_ellipsoid<T>(qv, poly, mc.n_poly, orient, mc.n_orient, mc.rp2);
+    } else {
+        avg = avg_axes3<T, KIND>(qv, poly, mc.n_rad, orient, mc.n_orient, mc);
     }
     return mc.scale * avg * structure_factor<T>(q, mc);
 }
@@ -402,7 +444,50 @@ __device__ __forceinline__ T dsigma_event(const T qv[3], const ModelConst<T>& mc
     }
     const T pi = (T)3.14159265358979323846;
     T F2;
-    if (KIND == SAS_SPHERE) {
+    if constexpr (KIND == SAS_TRIAXIAL_ELLIPSOID || KIND == SAS_PARALLELEPIPED) {
+        // frame of this event: C from (theta, phi), A and B rotated by psi
+        T A[3], B[3], C[3];
+        if (mc.orient_mode == 0) {
+            for (int k = 0; k < 3; ++k) {
+                A[k] = mc.ev_frame[k];
+                B[k] = mc.ev_frame[3 + k];
+                C[k] = mc.ev_axis[k];
+            }
+        } else {
+            T ct, st, sp, cp, sq, cq;
+            if (mc.orient_mode == 1) {
+                ct = (T)1 - (T)2 * u01<T>(rb.y);
+                st = M<T>::sqrt_(fmax((T)0, (T)1 - ct * ct));
+            } else {
+                M<T>::sincospi_(u01<T>(rb.y), st, ct);
+            }
+            M<T>::sincospi_((T)2 * u01<T>(rb.z), sp, cp);
+            M<T>::sincospi_((T)2 * u01<T>(rb.w), sq, cq);
+            const T et[3] = {ct * cp, ct * sp, -st}, ep[3] = {-sp, cp, (T)0};
+            for (int k = 0; k < 3; ++k) {
+                A[k] = cq * et[k] + sq * ep[k];
+                B[k] = -sq * et[k] + cq * ep[k];
+            }
+            C[0] = st * cp;
+            C[1] = st * sp;
+            C[2] = ct;
+        }
+        const T sc = r / mc.ev_r;
+        const T qa = sc * mc.ax_a * fma(qv[0], A[0], fma(qv[1], A[1], qv[2] * A[2]));
+        const T qb = sc * mc.ax_b * fma(qv[0], B[0], fma(qv[1], B[1], qv[2] * B[2]));
+        const T qc = sc * mc.ax_c * fma(qv[0], C[0], fma(qv[1], C[1], qv[2] * C[2]));
+        const T v3 = mc.ax_a * mc.ax_b * mc.ax_c * sc * sc * sc;
+        T F;
+        if (KIND == SAS_TRIAXIAL_ELLIPSOID) {
+            const T x = M<T>::sqrt_(fma(qa, qa, fma(qb, qb, qc * qc)));
+            F = (T)3 * mc.ev_c1 * (T)(4.0 / 3.0) * pi * v3 * M<T>::sphere_g(x, M<T>::rcp(x));
+        } else {
+            const T ya = fabs(qa), yb = fabs(qb), yc = fabs(qc);
+            F = mc.ev_c1 * (T)8 * v3 * M<T>::sinc(ya, M<T>::rcp(ya)) * M<T>::sinc(yb, M<T>::rcp(yb)) *
+                M<T>::sinc(yc, M<T>::rcp(yc));
+        }
+        F2 = F * F;
+    } else if (KIND == SAS_SPHERE) {
         const T x = q * r;
         const T g = M<T>::sphere_g(x, M<T>::rcp(x));
         const T V = (T)(4.0 / 3.0) * pi * r * r * r;

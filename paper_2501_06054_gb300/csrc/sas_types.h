@@ -59,6 +59,10 @@ struct ModelConst {
     int n_rad;       // radius nodes (the direct sum beyond the table)
     int n_tab;       // table points (0: direct sum)
     T tab_inv_h, tab_xmax, tab_c0, tab_rbar;
+    // 3-axis kinds: sizes along (A, B, C) (poly nodes hold scale factors);
+    // orientation rows come in threes: (A, w), (B, 0), (C, 0)
+    T ax_a, ax_b, ax_c;
+    T ev_frame[6];   // rows A and B of the fixed frame (C is ev_axis)
 };
 
 }  // namespace sas

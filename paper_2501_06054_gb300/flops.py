@@ -25,6 +25,13 @@ into FLOP/s for the roofline against the FP32 CUDA-core peak.
       / x^3 (3 mul), x^2 and its Taylor form (mul + 4 FMA) = 24;
       combination (mul, FMA, FMA) 5                                33 + 24 + 5
       per history sin, cos of q t                                   20
+  frame node overhead (3-axis models): Q.A, Q.B, Q.C times the
+      sizes (9 FMA/mul), weight and Kahan (5)                      20
+  triaxial ellipsoid term: scale (mul), amplitude 33, g^2 and the
+      weighted sum (2)                                             36
+  parallelepiped term: three scaled arguments (3 mul), three sincs
+      (3 x 20: reduction, sin polynomial, 1/y), product, square and
+      weighted sum (3)                                             66
   per history: geometry (wavelength, pinholes, slab, detector
                point, Q, solid angle)                           150
                Percus-Yevick S(Q)                               40
@@ -32,6 +39,9 @@ into FLOP/s for the roofline against the FP32 CUDA-core peak.
 
 AMP = 33
 CYL_TERM = 26
+FRAME_NODE = 20
+TRI_TERM = 36
+BOX_TERM = 66
 CS_NODE = 62
 CS_HISTORY = 20
 ORIENT_NODE = 60
@@ -46,6 +56,10 @@ def flops_per_history(kind: int, n_poly: int, n_orient: int = 1, sq: bool = Fals
         per = n_poly * CS_NODE + CS_HISTORY
     elif kind == 2:      # cylinder
         per = n_orient * (ORIENT_NODE + n_poly * CYL_TERM)
+    elif kind == 4:      # triaxial ellipsoid (n_orient = frames)
+        per = n_orient * (FRAME_NODE + n_poly * TRI_TERM)
+    elif kind == 5:      # parallelepiped
+        per = n_orient * (FRAME_NODE + n_poly * BOX_TERM)
     else:                # ellipsoid
         per = n_orient * (ORIENT_NODE + n_poly * (AMP + 5))
     return per + GEOMETRY + (PY if sq else 0)
