@@ -83,7 +83,8 @@ class _Model(ctypes.Structure):
                [("poly_r", _DP), ("poly_w", _DP), ("orient_c", _DP), ("orient_w", _DP)] + \
                [("event", ctypes.c_int64), ("orient_mode", ctypes.c_int64), ("poly", ctypes.c_double),
                 ("axis_theta", ctypes.c_double), ("axis_phi", ctypes.c_double),
-                ("radius_b", ctypes.c_double), ("axis_psi", ctypes.c_double)]
+                ("radius_b", ctypes.c_double), ("axis_psi", ctypes.c_double),
+                ("self_att", ctypes.c_int64)]
 
 
 def lib():
@@ -126,6 +127,14 @@ def lib():
             L.oracle_num_threads.restype = ctypes.c_int
             L.oracle_sample_lambda.argtypes = [ctypes.c_double] * 3
             L.oracle_sample_lambda.restype = ctypes.c_double
+            L.oracle_model_extent.argtypes = [ctypes.POINTER(_Model)]
+            L.oracle_model_extent.restype = ctypes.c_double
+            L.oracle_sigma_s.argtypes = [ctypes.POINTER(_Model), ctypes.c_double, ctypes.c_double]
+            L.oracle_sigma_s.restype = ctypes.c_double
+            L.oracle_att_table.argtypes = [ctypes.POINTER(_Instrument), ctypes.POINTER(_Model), _DP, _DP, _DP]
+            L.oracle_att_table.restype = ctypes.c_int
+            L.oracle_att_eval.argtypes = [ctypes.POINTER(_Instrument), ctypes.POINTER(_Model), _DP,
+                                          ctypes.c_int64, _DP]
             _lib = L
     return _lib
 
@@ -331,7 +340,8 @@ class Prepared:
                         orient_w=self.orient_w.ctypes.data_as(_DP),
                         event=int(m.get("sampling", 0)), orient_mode=iso, poly=float(m["poly"]),
                         axis_theta=float(m["axis_theta"]), axis_phi=float(m["axis_phi"]),
-                        radius_b=float(m.get("radius_b", 0.0)), axis_psi=float(m.get("axis_psi", 0.0)))
+                        radius_b=float(m.get("radius_b", 0.0)), axis_psi=float(m.get("axis_psi", 0.0)),
+                        self_att=int(m.get("self_attenuation", 0)))
 
 
 def _inst(instrument):
@@ -467,3 +477,40 @@ def sample_lambda(lambda0, drel, u):
 
 def num_threads():
     return lib().oracle_num_threads()
+
+
+def model_extent(model):
+    """Largest extent of the particle (angstrom) over its polydisperse nodes."""
+    prep = model if isinstance(model, Prepared) else Prepared(model)
+    return lib().oracle_model_extent(ctypes.byref(prep.c))
+
+
+def sigma_s(model, lam, lam_min=None):
+    """Total scattering cross section per unit volume Sigma_s(lambda) in
+    1/angstrom: dSigma/dOmega integrated over all directions for a neutron
+    along +z, by the rule built at lam_min (default lam)."""
+    prep = model if isinstance(model, Prepared) else Prepared(model)
+    return lib().oracle_sigma_s(ctypes.byref(prep.c), float(lam), float(lam if lam_min is None else lam_min))
+
+
+def _att_model(model):
+    m = model if isinstance(model, dict) else model.as_dict()
+    return Prepared(dict(m, self_attenuation=1))
+
+
+def att_table(instrument, model):
+    """The trace's attenuation table for the instrument's wavelength band:
+    (lambda nodes, mu_s at the nodes in 1/m, Chebyshev coefficients)."""
+    lam, mu, c = np.zeros(8), np.zeros(8), np.zeros(8)
+    n = lib().oracle_att_table(ctypes.byref(_inst(instrument)), ctypes.byref(_att_model(model).c),
+                               lam.ctypes.data_as(_DP), mu.ctypes.data_as(_DP), c.ctypes.data_as(_DP))
+    return lam[:n], mu[:n], c[:n]
+
+
+def att_eval(instrument, model, lam):
+    """mu_s(lambda) in 1/m from the trace's table at the wavelengths lam."""
+    lam = np.ascontiguousarray(np.atleast_1d(lam), dtype=np.float64)
+    out = np.empty(len(lam))
+    lib().oracle_att_eval(ctypes.byref(_inst(instrument)), ctypes.byref(_att_model(model).c),
+                          lam.ctypes.data_as(_DP), len(lam), out.ctypes.data_as(_DP))
+    return out

@@ -17,6 +17,11 @@
  *   uniaxial particles A(Q_AB, Q_C)                           (Eq. 7)
  *   cylinder amplitude, volume pi r^2 L                       (Eq. 8)
  *
+ * Optionally the beam inside the sample is also depleted by the particles'
+ * own scattering: mu(lambda) = mu + Sigma_s(lambda), Sigma_s the model's
+ * dSigma/dOmega integrated over all directions (single scattering: a
+ * neutron scattered twice is lost, not redistributed).
+ *
  * The quadrature nodes (Schulz polydispersity, orientation distribution) are
  * computed by the Python side of the oracle and passed in as arrays.
  * Special functions come from the C library (sin, cos, j1, exp, sqrt).
@@ -107,6 +112,9 @@ typedef struct {
      * polydisperse nodes poly_r / radius scale all three sizes alike */
     double radius_b;
     double axis_psi;       /* rotation about C of the fixed frame (event mode 0) */
+    /* 1: the beam inside the sample is attenuated by the particles' own
+     * scattering as well, mu(lambda) = mu + Sigma_s(lambda) */
+    int64_t self_att;
 } oracle_model;
 
 /* --------------------------------------------------------- model pieces */
@@ -453,6 +461,181 @@ void oracle_dsigma_event_many(const oracle_model *m, const double *q, uint64_t s
         out[i] = oracle_dsigma_event(m, q + 3 * i, seed, exp_id, first + (uint64_t)i);
 }
 
+/* ------------------------------------------- scattering attenuation */
+/*
+ * The particles remove neutrons from the beam at the rate of their total
+ * scattering cross section per unit volume,
+ *
+ *   Sigma_s(lambda) = integral over all directions k_f of dSigma/dOmega(Q) dOmega,
+ *   Q = k (k_f - k_i),  k = 2 pi / lambda,  k_i along the beam axis (+z).
+ *
+ * Parametrising k_f by |Q| and the azimuth phi about z:
+ *   Q = (Q s cos phi, Q s sin phi, -Q^2 / (2 k)),  s = sqrt(1 - Q^2 / (4 k^2)),
+ *   dOmega = Q dQ dphi / k^2,  0 <= Q <= 2k.
+ *
+ * The integral is taken by a fixed product rule, built once at the shortest
+ * wavelength of the source (k_max) and scaled with k, so that Sigma_s is a
+ * smooth function of lambda:
+ *   - |Q| panels [a, b] from 0 to 2 k_max with b - a = max(pi / D, a / 8),
+ *     D the largest extent of the particle over its polydisperse nodes (a
+ *     panel is at most half a period of the amplitude's oscillation near
+ *     the origin, and grows geometrically further out); the last panel ends
+ *     at 2 k_max; 8 Gauss-Legendre nodes per panel;
+ *   - phi: the midpoint rule with n_phi = 8 clamp(ceil(Q_mid D / 2), 2, 64)
+ *     points on the panel (Q_mid its midpoint at k_max); one point for the
+ *     sphere and the core-shell sphere, whose dSigma/dOmega depends on |Q|
+ *     only.
+ * In the trace, Sigma_s(lambda) over the source's wavelength band enters as
+ * its interpolant at 8 Chebyshev points (one point without a spread).
+ */
+
+/* Gauss-Legendre nodes and weights on [-1, 1] by Newton's method on P_n. */
+static void gl_nodes(int n, double *x, double *w)
+{
+    for (int i = 0; i < n; ++i) {
+        double z = cos(PI * (i + 0.75) / (n + 0.5)), dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1; p1 = p2;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            double dz = p1 / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-16) break;
+        }
+        double p0 = 1.0, p1 = z;
+        for (int k = 2; k <= n; ++k) {
+            double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+            p0 = p1; p1 = p2;
+        }
+        dp = n * (z * p1 - p0) / (z * z - 1.0);
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+/* Largest extent of the particle (angstrom) over its polydisperse nodes. */
+double oracle_model_extent(const oracle_model *m)
+{
+    double r = 0.0;
+    for (int64_t i = 0; i < m->n_poly; ++i) r = fmax(r, m->poly_r[i]);
+    switch (m->kind) {
+    case 0: return 2.0 * r;
+    case 1: return 2.0 * (r + m->thickness);
+    case 2: return sqrt(m->length * m->length + 4.0 * r * r);
+    case 3: return 2.0 * fmax(r, m->radius_polar);
+    case 4: {
+        double f = r / m->radius;
+        return 2.0 * f * fmax(m->radius, fmax(m->radius_b, m->radius_polar));
+    }
+    default: {
+        double f = r / m->radius;
+        return 2.0 * f * sqrt(m->radius * m->radius + m->radius_b * m->radius_b +
+                              m->radius_polar * m->radius_polar);
+    }
+    }
+}
+
+/* Sigma_s(lambda) in 1/angstrom by the rule above (built at lambda_min). */
+double oracle_sigma_s(const oracle_model *m, double lambda, double lambda_min)
+{
+    const double D = oracle_model_extent(m);
+    const double kmax = 2.0 * PI / lambda_min, k = 2.0 * PI / lambda, sc = k / kmax;
+    const int iso = m->kind == 0 || m->kind == 1;
+    double gx[8], gw[8];
+    gl_nodes(8, gx, gw);
+    double total = 0.0, a = 0.0;
+    while (a < 2.0 * kmax) {
+        double b = a + fmax(PI / D, a / 8.0);
+        if (b > 2.0 * kmax) b = 2.0 * kmax;
+        int nphi = 1;
+        if (!iso) {
+            double c = ceil(0.5 * (a + b) * D / 2.0);
+            nphi = 8 * (int)fmin(fmax(c, 2.0), 64.0);
+        }
+        double panel = 0.0;
+        for (int g = 0; g < 8; ++g) {
+            double Q = sc * (0.5 * (a + b) + 0.5 * (b - a) * gx[g]);
+            double wq = sc * 0.5 * (b - a) * gw[g];
+            double st = sqrt(fmax(1.0 - Q * Q / (4.0 * k * k), 0.0));
+            double qz = -Q * Q / (2.0 * k);
+            if (SAS_MUT == 14) qz = 0.0;
+            double ring = 0.0;
+            for (int j = 0; j < nphi; ++j) {
+                double ph = 2.0 * PI * (j + 0.5) / nphi;
+                double q[3] = {Q * st * cos(ph), Q * st * sin(ph), qz};
+                ring += oracle_dsigma(m, q);
+            }
+            panel += wq * (SAS_MUT == 15 ? 1.0 : Q) * ring * (2.0 * PI / nphi);
+        }
+        total += panel;
+        a = b;
+    }
+    return total / (k * k);
+}
+
+/* The trace's attenuation table: mu_s(lambda) = 1e10 Sigma_s(lambda) in 1/m
+ * at n Chebyshev points of [lmin, lmax] and the coefficients of its
+ * interpolant sum_j c_j T_j(t), t = (2 lambda - lmin - lmax) / (lmax - lmin). */
+typedef struct {
+    int n;
+    double lmin, lmax;
+    double lam[8], mu[8], c[8];
+} oracle_att;
+
+static void att_setup(const oracle_instrument *in, const oracle_model *m, oracle_att *a)
+{
+    a->n = 0;
+    if (!m || !m->self_att) return;
+    a->lmin = in->lambda0 * (1.0 - in->dlambda_rel);
+    a->lmax = in->lambda0 * (1.0 + in->dlambda_rel);
+    const int n = in->dlambda_rel > 0.0 ? 8 : 1;
+    a->n = n;
+    for (int j = 0; j < n; ++j) {
+        double t = cos(PI * (j + 0.5) / n);
+        a->lam[j] = n > 1 ? 0.5 * (a->lmin + a->lmax) + 0.5 * (a->lmax - a->lmin) * t : in->lambda0;
+        a->mu[j] = 1e10 * oracle_sigma_s(m, a->lam[j], a->lmin);
+    }
+    for (int i = 0; i < n; ++i) {
+        double c = 0.0;
+        for (int j = 0; j < n; ++j) c += a->mu[j] * cos(PI * i * (j + 0.5) / n);
+        a->c[i] = (i == 0 ? 1.0 : 2.0) * c / n;
+    }
+}
+
+/* mu_s(lambda) in 1/m from the table: T_j(t) = cos(j arccos t). */
+static double att_mu(const oracle_att *a, double lambda)
+{
+    if (!a || a->n == 0) return 0.0;
+    if (a->n == 1) return a->c[0];
+    double t = (2.0 * lambda - a->lmin - a->lmax) / (a->lmax - a->lmin);
+    t = fmin(fmax(t, -1.0), 1.0);
+    double th = acos(t), v = 0.0;
+    for (int j = 0; j < a->n; ++j) v += a->c[j] * cos(j * th);
+    return v;
+}
+
+/* Exposes the table: lam, mu (1/m) and c, each [8]; returns n (0: off). */
+int oracle_att_table(const oracle_instrument *in, const oracle_model *m, double *lam, double *mu,
+                     double *c)
+{
+    oracle_att a;
+    att_setup(in, m, &a);
+    for (int j = 0; j < a.n; ++j) { lam[j] = a.lam[j]; mu[j] = a.mu[j]; c[j] = a.c[j]; }
+    return a.n;
+}
+
+/* mu_s at the wavelengths lam[n] from the table (1/m). */
+void oracle_att_eval(const oracle_instrument *in, const oracle_model *m, const double *lam, int64_t n,
+                     double *out)
+{
+    oracle_att a;
+    att_setup(in, m, &a);
+    for (int64_t i = 0; i < n; ++i) out[i] = att_mu(&a, lam[i]);
+}
+
 /* ------------------------------------------------------------- geometry */
 
 /* source wavelength from one uniform: triangular on [l0 (1-d), l0 (1+d)],
@@ -492,9 +675,9 @@ static int slab(const oracle_instrument *in, const double o[3], const double d[3
  * Returns 1 if it scattered onto the detector, with its pixel, the path
  * length l in the sample, the solid-angle factor, the attenuation and Q;
  * *w_trans gets the unscattered (transmitted) weight. */
-static int history_geometry(const oracle_instrument *in, uint64_t seed, uint32_t exp_id,
-                            uint64_t index, int64_t *pixel, double *l_path, double *d_omega,
-                            double *atten, double q_out[3], double *w_trans)
+static int history_geometry(const oracle_instrument *in, const oracle_att *att, uint64_t seed,
+                            uint32_t exp_id, uint64_t index, int64_t *pixel, double *l_path,
+                            double *d_omega, double *atten, double q_out[3], double *w_trans)
 {
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
     uint32_t c0[4] = {0u, exp_id, (uint32_t)index, (uint32_t)(index >> 32)};
@@ -505,6 +688,8 @@ static int history_geometry(const oracle_instrument *in, uint64_t seed, uint32_t
 
     /* source: triangular wavelength spread by inverse CDF */
     double lambda = oracle_sample_lambda(in->lambda0, in->dlambda_rel, u01(x[0]));
+    /* attenuation: the instrument's mu plus, optionally, the particles' own scattering */
+    const double mu = in->mu + att_mu(att, lambda);
     /* collimation: uniform points on the two pinhole discs */
     double r1 = in->ap1_radius * sqrt(u01(x[1])), f1 = 2.0 * PI * u01(x[2]);
     double r2 = in->ap2_radius * sqrt(u01(x[3])), f2 = 2.0 * PI * u01(x[4]);
@@ -517,7 +702,7 @@ static int history_geometry(const oracle_instrument *in, uint64_t seed, uint32_t
     double t_in, t_out;
     if (!slab(in, p2, k_in, &t_in, &t_out)) { *w_trans = 1.0; return 0; }
     double l = t_out - t_in;
-    *w_trans = exp(-in->mu * l);
+    *w_trans = exp(-mu * l);
     double s = u01(x[5]) * l;
     double ps[3] = {p2[0] + (t_in + s) * k_in[0], p2[1] + (t_in + s) * k_in[1],
                     p2[2] + (t_in + s) * k_in[2]};
@@ -544,7 +729,7 @@ static int history_geometry(const oracle_instrument *in, uint64_t seed, uint32_t
     /* path to the exit of the sample along the scattered direction */
     double e_in, e_out, l_out = 0.0;
     if (slab(in, ps, k_out, &e_in, &e_out)) l_out = e_out - e_in;
-    *atten = exp(-in->mu * (s + l_out));
+    *atten = exp(-mu * (s + l_out));
     if (SAS_MUT == 8) domega = area * k_out[2] / rr;
     *l_path = l;
     *d_omega = domega;
@@ -555,16 +740,25 @@ static int history_geometry(const oracle_instrument *in, uint64_t seed, uint32_t
 /* One neutron history. Returns 1 if it scattered onto the detector, with
  * its pixel and weight l dSigma/dOmega(Q) dOmega att; *w_trans gets the
  * unscattered (transmitted) weight. */
-int oracle_history(const oracle_instrument *in, const oracle_model *m, uint64_t seed,
-                   uint32_t exp_id, uint64_t index, int64_t *pixel, double *w,
-                   double *w_trans)
+static int history_att(const oracle_instrument *in, const oracle_model *m, const oracle_att *at,
+                       uint64_t seed, uint32_t exp_id, uint64_t index, int64_t *pixel, double *w,
+                       double *w_trans)
 {
     double l, domega, att, q[3];
-    if (!history_geometry(in, seed, exp_id, index, pixel, &l, &domega, &att, q, w_trans)) return 0;
+    if (!history_geometry(in, at, seed, exp_id, index, pixel, &l, &domega, &att, q, w_trans)) return 0;
     double ds = (m->event ? oracle_dsigma_event(m, q, seed, exp_id, index) : oracle_dsigma(m, q))
               * 1e10; /* 1/angstrom -> 1/m */
     *w = l * ds * domega * att;
     return 1;
+}
+
+int oracle_history(const oracle_instrument *in, const oracle_model *m, uint64_t seed,
+                   uint32_t exp_id, uint64_t index, int64_t *pixel, double *w,
+                   double *w_trans)
+{
+    oracle_att a;
+    att_setup(in, m, &a);
+    return history_att(in, m, &a, seed, exp_id, index, pixel, w, w_trans);
 }
 
 /* Per-neutron geometry records: pixel (-1 on a miss), Q [n][3], the
@@ -579,7 +773,7 @@ void oracle_geometry_records(const oracle_instrument *in, uint64_t seed, uint32_
 #pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < (int64_t)n; ++j) {
         int64_t pix; double l, domega, att;
-        if (history_geometry(in, seed, exp_id, first + (uint64_t)j, &pix, &l, &domega, &att,
+        if (history_geometry(in, NULL, seed, exp_id, first + (uint64_t)j, &pix, &l, &domega, &att,
                              q + 3 * j, w_trans + j)) {
             pixel[j] = pix;
             pref[j] = l * 1e10 * domega * att;
@@ -606,6 +800,8 @@ void oracle_trace(const oracle_instrument *in, const oracle_model *m, uint64_t s
     double *pw2 = calloc((size_t)nt * npix, sizeof(double));
     uint64_t *pc = calloc((size_t)nt * npix, sizeof(uint64_t));
     double *pt = calloc((size_t)nt, sizeof(double));
+    oracle_att at;
+    att_setup(in, m, &at);
 #pragma omp parallel num_threads(nt)
     {
         int tid = 0;
@@ -618,7 +814,7 @@ void oracle_trace(const oracle_instrument *in, const oracle_model *m, uint64_t s
 #pragma omp for schedule(static)
         for (int64_t j = 0; j < (int64_t)n; ++j) {
             int64_t pix; double w, wt;
-            if (oracle_history(in, m, seed, exp_id, first + (uint64_t)j, &pix, &w, &wt)) {
+            if (history_att(in, m, &at, seed, exp_id, first + (uint64_t)j, &pix, &w, &wt)) {
                 w1[pix] += w; w2[pix] += w * w; c[pix] += 1;
             }
             tr += wt;
@@ -640,10 +836,12 @@ void oracle_trace(const oracle_instrument *in, const oracle_model *m, uint64_t s
 void oracle_records(const oracle_instrument *in, const oracle_model *m, uint64_t seed,
                     uint32_t exp_id, uint64_t first, uint64_t n, int64_t *pixel, double *w)
 {
+    oracle_att at;
+    att_setup(in, m, &at);
 #pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < (int64_t)n; ++j) {
         int64_t pix; double ww, wt;
-        if (oracle_history(in, m, seed, exp_id, first + (uint64_t)j, &pix, &ww, &wt)) {
+        if (history_att(in, m, &at, seed, exp_id, first + (uint64_t)j, &pix, &ww, &wt)) {
             pixel[j] = pix; w[j] = ww;
         } else {
             pixel[j] = -1; w[j] = 0.0;

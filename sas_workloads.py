@@ -98,6 +98,7 @@ class Model:
     radius_b: float = 0.0           # triaxial ellipsoid semi-axis / parallelepiped half-edge along B
     axis_psi: float = 0.0           # rad, rotation of the particle frame about its C axis
     n_rot: int = 1                  # quadrature nodes in psi (uniform rotations / angles)
+    self_attenuation: int = 0       # 1: attenuation mu + Sigma_s(lambda), the model's own total scattering
 
     def as_dict(self):
         return asdict(self)

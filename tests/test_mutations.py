@@ -28,6 +28,10 @@ MUTATIONS = {
     12: ("per-event radius drawn without the positivity restriction", "restricted_gaussian",
          "test_event_oracle.py"),
     13: ("parallelepiped with Q_B and Q_C swapped", "eq1_volume", "test_triaxial_oracle.py"),
+    14: ("total cross section over a flat Ewald sphere (Q_z dropped)", "ewald_direction",
+         "test_attenuation_oracle.py"),
+    15: ("total cross section without the |Q| of dOmega = Q dQ dphi / k^2", "sphere_large_k",
+         "test_attenuation_oracle.py"),
 }
 
 
