@@ -298,6 +298,7 @@ def secondary(stream, info):
         "work_items": ib["n_items"]}
     sas.sas_destroy_surrogate(sur)
     out["per_event"] = per_event(stream)
+    out["self_attenuation"] = self_attenuation(stream)
     return out
 
 
@@ -353,6 +354,45 @@ def per_event(stream):
         row["fom_ratio_per_event_vs_quadrature"] = (row["per_event"]["value"] / row["quadrature"]["value"]) * \
             (errs["quadrature"] / errs["per_event"]) ** 2
         res[name] = row
+    return res
+
+
+def self_attenuation(stream):
+    """Attenuation by the particles' own scattering: the cost of building the
+    mu_s(lambda) table when the model is set (GPU integral of dSigma/dOmega
+    over all directions at 8 wavelengths), the trace rate with it on and off
+    on the same histories, and what single scattering leaves out: for a slab
+    of thickness t at normal incidence with mu_s t = x, the neutrons that
+    scatter twice or more are 1 - e^-x (1 + x) of the beam, a fraction
+    1 - x e^-x / (1 - e^-x) of the scattered ones."""
+    import time
+    import paper_2501_06054_gb300 as sas
+    res = {}
+    for name, cfg, n in (("core_shell", W.core_shell_config(), 200_000_000),
+                         ("cylinder", W.cylinder_config(), 2_000_000)):
+        inst = cfg["instrument"]
+        on = W.Model(**dict(cfg["model"].as_dict(), self_attenuation=1))
+        e = sas.Experiment(inst, cfg["model"], stream=stream)
+        t0 = time.perf_counter()
+        e.set_model(on)
+        build_ms = (time.perf_counter() - t0) * 1e3
+        tab = sas.sas_attenuation_table(e.h)
+        sig, parts = sas.sas_total_cross_section(e.h, inst.lambda0)
+        rates = {}
+        for mode, model in (("on", on), ("off", cfg["model"])):
+            e.set_model(model)
+            e.trace(min(n, 1_000_000), 1)
+            ms = _events_ms(lambda: e.trace(n, 1), stream)
+            rates[mode] = n / (ms * 1e-3)
+        e.close()
+        x = 1e10 * sig * inst.sample_thickness
+        multi = 1.0 - math.exp(-x) * (1.0 + x)
+        res[name] = {"table_build_ms": build_ms, "mu_s_at_lambda0_per_m": 1e10 * sig,
+                     "mu_s_band_per_m": [float(tab["mu_s"].min()), float(tab["mu_s"].max())],
+                     "panels": len(parts), "transmission_at_lambda0": math.exp(-x),
+                     "multiple_scattering_fraction_of_beam": multi,
+                     "multiple_scattering_fraction_of_scattered": multi / (1.0 - math.exp(-x)),
+                     "rate_on": rates["on"], "rate_off": rates["off"], "unit": UNIT, "histories_timed": n}
     return res
 
 

@@ -144,6 +144,18 @@ typedef struct sas_model_desc {
     double radius_b;         /* 3-axis kinds: size along B */
     double axis_psi;         /* 3-axis kinds: rotation of the frame about C, rad */
     int64_t n_rot;           /* 3-axis kinds: quadrature nodes in psi (1..128) */
+    /* Attenuation by the particles' own scattering (single scattering: a
+     * neutron that would scatter twice is lost, not redistributed). 1: the
+     * beam inside the sample is attenuated with mu + mu_s(lambda), where
+     * mu_s = Sigma_s = the model's dSigma/dOmega integrated over all
+     * directions for a neutron along +z (in 1/m), on the way to the
+     * scattering point and out of the sample; the transmitted weight too.
+     * Sigma_s is taken on the GPU when the model is set, by a fixed
+     * (|Q|, phi) product rule (8-node Gauss-Legendre |Q| panels of width
+     * max(pi / D, Q / 8), D the particle's largest extent; midpoint rule in
+     * phi), at the 8 Chebyshev wavelengths of the source band, and
+     * interpolated per history. Quadrature sampling only; 0: off. */
+    int64_t self_attenuation;
 } sas_model_desc;
 
 typedef struct sas_experiment sas_experiment;   /* opaque, library-owned */
@@ -196,6 +208,28 @@ sas_status sas_detector_device(const sas_experiment *exp, const double **sum_w,
  * model (its cross section is a random draw per history; the records below
  * give its per-history values). */
 sas_status sas_eval_model(sas_experiment *exp, const void *q_xyz, size_t n, void *out);
+
+/* The experiment's self-attenuation table (sas_model_desc.self_attenuation):
+ * HOST arrays of SAS_ATT_MAX doubles receive the wavelengths (angstrom), the
+ * GPU-evaluated mu_s (1/m) there, and the Chebyshev coefficients c of the
+ * interpolant sum_j c_j T_j(t), t = (2 lambda - lmin - lmax) / (lmax - lmin),
+ * with lmin_lmax[2] the source band; *n = points (1 without a wavelength
+ * spread, 0 if the model has no self-attenuation). Any array may be NULL.
+ * SAS_ERR_STATE before sas_set_model. */
+#define SAS_ATT_MAX 8
+sas_status sas_attenuation_table(const sas_experiment *exp, int *n, double *lambda, double *mu_s,
+                                 double *coef, double *lmin_lmax);
+
+/* Total scattering cross section per unit volume Sigma_s(lambda) in
+ * 1/angstrom: the experiment's dSigma/dOmega integrated over all directions
+ * for a neutron along +z, by the rule of sas_model_desc.self_attenuation
+ * (built at the shortest wavelength of the instrument's band), evaluated on
+ * the GPU at any lambda > 0 whether or not the model attenuates itself.
+ * HOST outputs: *sigma; panels[min(n, max_panels)] the share of each |Q|
+ * panel (may be NULL with max_panels 0); *n_panels = n. Synchronous.
+ * SAS_ERR_STATE before sas_set_model or for a per-event model. */
+sas_status sas_total_cross_section(sas_experiment *exp, double lambda, double *sigma, double *panels,
+                                   int max_panels, int *n_panels);
 
 /* Parity hook: per-neutron records of neutrons [first, first+n): DEVICE
  * int32 pixel[n] (-1: missed the sample) and DEVICE double weight[n] (1/m

@@ -131,6 +131,11 @@ def lib():
             L.oracle_model_extent.restype = ctypes.c_double
             L.oracle_sigma_s.argtypes = [ctypes.POINTER(_Model), ctypes.c_double, ctypes.c_double]
             L.oracle_sigma_s.restype = ctypes.c_double
+            L.oracle_sigma_s_panel.argtypes = [ctypes.POINTER(_Model), ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_int]
+            L.oracle_sigma_s_panel.restype = ctypes.c_double
+            L.oracle_sigma_s_npanels.argtypes = [ctypes.POINTER(_Model), ctypes.c_double]
+            L.oracle_sigma_s_npanels.restype = ctypes.c_int
             L.oracle_att_table.argtypes = [ctypes.POINTER(_Instrument), ctypes.POINTER(_Model), _DP, _DP, _DP]
             L.oracle_att_table.restype = ctypes.c_int
             L.oracle_att_eval.argtypes = [ctypes.POINTER(_Instrument), ctypes.POINTER(_Model), _DP,
@@ -493,6 +498,17 @@ def sigma_s(model, lam, lam_min=None):
     return lib().oracle_sigma_s(ctypes.byref(prep.c), float(lam), float(lam if lam_min is None else lam_min))
 
 
+def sigma_s_panel(model, lam, lam_min, i):
+    """The share of |Q| panel i of the rule in Sigma_s(lam) (1/angstrom)."""
+    prep = model if isinstance(model, Prepared) else Prepared(model)
+    return lib().oracle_sigma_s_panel(ctypes.byref(prep.c), float(lam), float(lam_min), int(i))
+
+
+def sigma_s_npanels(model, lam_min):
+    prep = model if isinstance(model, Prepared) else Prepared(model)
+    return lib().oracle_sigma_s_npanels(ctypes.byref(prep.c), float(lam_min))
+
+
 def _att_model(model):
     m = model if isinstance(model, dict) else model.as_dict()
     return Prepared(dict(m, self_attenuation=1))
@@ -502,7 +518,8 @@ def att_table(instrument, model):
     """The trace's attenuation table for the instrument's wavelength band:
     (lambda nodes, mu_s at the nodes in 1/m, Chebyshev coefficients)."""
     lam, mu, c = np.zeros(8), np.zeros(8), np.zeros(8)
-    n = lib().oracle_att_table(ctypes.byref(_inst(instrument)), ctypes.byref(_att_model(model).c),
+    prep = _att_model(model)   # keeps the node arrays alive during the call
+    n = lib().oracle_att_table(ctypes.byref(_inst(instrument)), ctypes.byref(prep.c),
                                lam.ctypes.data_as(_DP), mu.ctypes.data_as(_DP), c.ctypes.data_as(_DP))
     return lam[:n], mu[:n], c[:n]
 
@@ -511,6 +528,7 @@ def att_eval(instrument, model, lam):
     """mu_s(lambda) in 1/m from the trace's table at the wavelengths lam."""
     lam = np.ascontiguousarray(np.atleast_1d(lam), dtype=np.float64)
     out = np.empty(len(lam))
-    lib().oracle_att_eval(ctypes.byref(_inst(instrument)), ctypes.byref(_att_model(model).c),
+    prep = _att_model(model)
+    lib().oracle_att_eval(ctypes.byref(_inst(instrument)), ctypes.byref(prep.c),
                           lam.ctypes.data_as(_DP), len(lam), out.ctypes.data_as(_DP))
     return out

@@ -538,8 +538,10 @@ double oracle_model_extent(const oracle_model *m)
     }
 }
 
-/* Sigma_s(lambda) in 1/angstrom by the rule above (built at lambda_min). */
-double oracle_sigma_s(const oracle_model *m, double lambda, double lambda_min)
+/* Sigma_s(lambda) in 1/angstrom by the rule above (built at lambda_min):
+ * the sum over the |Q| panels, or only panel `only` (>= 0); *n_pan gets the
+ * number of panels. */
+static double sigma_s_panels(const oracle_model *m, double lambda, double lambda_min, int only, int *n_pan)
 {
     const double D = oracle_model_extent(m);
     const double kmax = 2.0 * PI / lambda_min, k = 2.0 * PI / lambda, sc = k / kmax;
@@ -547,6 +549,7 @@ double oracle_sigma_s(const oracle_model *m, double lambda, double lambda_min)
     double gx[8], gw[8];
     gl_nodes(8, gx, gw);
     double total = 0.0, a = 0.0;
+    int idx = 0;
     while (a < 2.0 * kmax) {
         double b = a + fmax(PI / D, a / 8.0);
         if (b > 2.0 * kmax) b = 2.0 * kmax;
@@ -555,25 +558,52 @@ double oracle_sigma_s(const oracle_model *m, double lambda, double lambda_min)
             double c = ceil(0.5 * (a + b) * D / 2.0);
             nphi = 8 * (int)fmin(fmax(c, 2.0), 64.0);
         }
-        double panel = 0.0;
-        for (int g = 0; g < 8; ++g) {
-            double Q = sc * (0.5 * (a + b) + 0.5 * (b - a) * gx[g]);
-            double wq = sc * 0.5 * (b - a) * gw[g];
-            double st = sqrt(fmax(1.0 - Q * Q / (4.0 * k * k), 0.0));
-            double qz = -Q * Q / (2.0 * k);
-            if (SAS_MUT == 14) qz = 0.0;
-            double ring = 0.0;
-            for (int j = 0; j < nphi; ++j) {
-                double ph = 2.0 * PI * (j + 0.5) / nphi;
-                double q[3] = {Q * st * cos(ph), Q * st * sin(ph), qz};
-                ring += oracle_dsigma(m, q);
+        if (only < 0 || idx == only) {
+            double panel = 0.0;
+            for (int g = 0; g < 8; ++g) {
+                double Q = sc * (0.5 * (a + b) + 0.5 * (b - a) * gx[g]);
+                double wq = sc * 0.5 * (b - a) * gw[g];
+                double st = sqrt(fmax(1.0 - Q * Q / (4.0 * k * k), 0.0));
+                double qz = -Q * Q / (2.0 * k);
+                if (SAS_MUT == 14) qz = 0.0;
+                double ring = 0.0;
+#pragma omp parallel for reduction(+ : ring) schedule(static) if (nphi >= 64)
+                for (int j = 0; j < nphi; ++j) {
+                    double ph = 2.0 * PI * (j + 0.5) / nphi;
+                    double q[3] = {Q * st * cos(ph), Q * st * sin(ph), qz};
+                    ring += oracle_dsigma(m, q);
+                }
+                panel += wq * (SAS_MUT == 15 ? 1.0 : Q) * ring * (2.0 * PI / nphi);
             }
-            panel += wq * (SAS_MUT == 15 ? 1.0 : Q) * ring * (2.0 * PI / nphi);
+            total += panel;
         }
-        total += panel;
         a = b;
+        ++idx;
     }
+    *n_pan = idx;
     return total / (k * k);
+}
+
+double oracle_sigma_s(const oracle_model *m, double lambda, double lambda_min)
+{
+    int n;
+    return sigma_s_panels(m, lambda, lambda_min, -1, &n);
+}
+
+/* The share of panel i in Sigma_s(lambda) (NAN if there is no panel i). */
+double oracle_sigma_s_panel(const oracle_model *m, double lambda, double lambda_min, int i)
+{
+    int n;
+    double v = sigma_s_panels(m, lambda, lambda_min, i, &n);
+    return (i >= 0 && i < n) ? v : NAN;
+}
+
+/* Number of |Q| panels of the rule built at lambda_min. */
+int oracle_sigma_s_npanels(const oracle_model *m, double lambda_min)
+{
+    int n;
+    sigma_s_panels(m, lambda_min, lambda_min, 1 << 30, &n);
+    return n;
 }
 
 /* The trace's attenuation table: mu_s(lambda) = 1e10 Sigma_s(lambda) in 1/m

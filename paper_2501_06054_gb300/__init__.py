@@ -46,7 +46,8 @@ class sas_model_desc(ctypes.Structure):
                    "sld_solvent", "volume_fraction", "poly", "sigma_orient", "axis_theta",
                    "axis_phi", "sq_radius", "sq_fraction")] + \
                [(n, ctypes.c_int64) for n in ("sampling", "poly_dist", "radial_table")] + \
-               [("radius_b", ctypes.c_double), ("axis_psi", ctypes.c_double), ("n_rot", ctypes.c_int64)]
+               [("radius_b", ctypes.c_double), ("axis_psi", ctypes.c_double), ("n_rot", ctypes.c_int64),
+                ("self_attenuation", ctypes.c_int64)]
 
 
 class sas_launch_config(ctypes.Structure):
@@ -86,6 +87,8 @@ _SIGS = {
                             ctypes.POINTER(_vp)],
     "sas_eval_model": [_vp, _vp, ctypes.c_size_t, _vp],
     "sas_trace_records": [_vp, _u64, _u64, _u64, _vp, _vp],
+    "sas_attenuation_table": [_vp, ctypes.POINTER(ctypes.c_int), _dp, _dp, _dp, _dp],
+    "sas_total_cross_section": [_vp, ctypes.c_double, _dp, _dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
     "sas_sync": [_vp],
     "sas_destroy_experiment": [_vp],
     "sas_device_info": [ctypes.POINTER(ctypes.c_int)] * 4,
@@ -190,7 +193,7 @@ def make_instrument(d) -> sas_instrument:
 def make_model(d) -> sas_model_desc:
     d = d if isinstance(d, dict) else d.as_dict()
     ints = ("kind", "sq_kind", "precision", "n_poly", "n_gamma", "n_psi", "isotropic", "sampling",
-            "poly_dist", "radial_table", "n_rot")
+            "poly_dist", "radial_table", "n_rot", "self_attenuation")
     return sas_model_desc(**{k: (int(v) if k in ints else float(v)) for k, v in d.items()})
 
 
@@ -252,6 +255,27 @@ def sas_eval_model(exp, q_xyz, n, out):
 
 def sas_trace_records(exp, first, n, seed, pixel, weight):
     _check(lib().sas_trace_records(exp, int(first), int(n), int(seed), _ptr(pixel), _ptr(weight)))
+
+
+def sas_attenuation_table(exp):
+    """The experiment's self-attenuation table: dict(lam, mu_s (1/m), coef,
+    lmin, lmax) with n points (n = 0: off)."""
+    n = ctypes.c_int()
+    lam, mu, c, lr = np.zeros(8), np.zeros(8), np.zeros(8), np.zeros(2)
+    _check(lib().sas_attenuation_table(exp, ctypes.byref(n), lam.ctypes.data_as(_dp), mu.ctypes.data_as(_dp),
+                                       c.ctypes.data_as(_dp), lr.ctypes.data_as(_dp)))
+    k = n.value
+    return dict(lam=lam[:k], mu_s=mu[:k], coef=c[:k], lmin=float(lr[0]), lmax=float(lr[1]))
+
+
+def sas_total_cross_section(exp, lam, max_panels=4096):
+    """(Sigma_s(lam) in 1/angstrom, per-panel shares) of the experiment's model."""
+    sig = np.zeros(1)
+    n = ctypes.c_int()
+    part = np.zeros(max_panels)
+    _check(lib().sas_total_cross_section(exp, float(lam), sig.ctypes.data_as(_dp), part.ctypes.data_as(_dp),
+                                         int(max_panels), ctypes.byref(n)))
+    return float(sig[0]), part[:min(n.value, max_panels)]
 
 
 def sas_sync(exp):

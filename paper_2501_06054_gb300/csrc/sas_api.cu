@@ -498,6 +498,8 @@ sas_status build_model_tables(const sas_model_desc& m, ModelTables& t, double q_
         }
     }
     t.n_poly = npoly;
+    t.r_max = 0.0;
+    for (int i = 0; i < npoly; ++i) t.r_max = std::fmax(t.r_max, r[i]);
     t.scale = m.volume_fraction / vmean;
     t.vmean = vmean;
     if (m.kind == SAS_TRIAXIAL_ELLIPSOID || m.kind == SAS_PARALLELEPIPED) {
@@ -650,6 +652,12 @@ ModelConst<T> model_const(const sas_model_desc& m, const ModelTables& t)
     c.tab_xmax = (T)t.tab_xmax;
     c.tab_c0 = (T)t.tab_c0;
     c.tab_rbar = (T)t.tab_rbar;
+    c.att.n = t.att_n;
+    if (t.att_n > 1) {
+        c.att.t_mul = (T)(2.0 / (t.att_lmax - t.att_lmin));
+        c.att.t_add = (T)(-(t.att_lmin + t.att_lmax) / (t.att_lmax - t.att_lmin));
+    }
+    for (int j = 0; j < t.att_n; ++j) c.att.c[j] = (T)t.att_c[j];
     return c;
 }
 
@@ -738,6 +746,11 @@ sas_status validate_model(const sas_model_desc* m)
     if (m->poly_dist != SAS_POLY_SCHULZ && m->poly_dist != SAS_POLY_GAUSSIAN)
         return fail(SAS_ERR_ARG, "unknown poly_dist");
     if (m->radial_table != 0 && m->radial_table != 1) return fail(SAS_ERR_ARG, "radial_table must be 0 or 1");
+    if (m->self_attenuation != 0 && m->self_attenuation != 1)
+        return fail(SAS_ERR_ARG, "self_attenuation must be 0 or 1");
+    if (m->self_attenuation && m->sampling != SAS_QUADRATURE)
+        return fail(SAS_ERR_ARG, "self_attenuation needs the model's deterministic dSigma/dOmega: sampling "
+                                 "SAS_QUADRATURE");
     if (m->sampling == SAS_PER_EVENT) {
         if (m->poly > 0.0 && m->poly_dist != SAS_POLY_GAUSSIAN)
             return fail(SAS_ERR_ARG, "per-event sampling draws Gaussian radii (Sec. II.B): set poly_dist to "
@@ -1218,6 +1231,16 @@ sas_status sas_set_model(sas_experiment* e, const sas_model_desc* m)
     SAS_CUDA(cudaStreamSynchronize(e->stream), "cudaStreamSynchronize");
     e->model = *m;
     e->tables = std::move(t);
+    if (m->self_attenuation) {
+        AttRule r;
+        att_rule(e->inst, *m, e->tables, r);
+        double mu[SAS_ATT_MAX];
+        SAS_CUDA(att_nodes(*m, e->tables, e->d_poly, e->d_orient, r, e->stream, mu), "self-attenuation table");
+        for (int j = 0; j < r.n_lambda; ++j)
+            if (!std::isfinite(mu[j]) || mu[j] < 0.0)
+                return fail(SAS_ERR_NUMERIC, "self-attenuation: non-finite or negative total cross section");
+        att_fit(r, mu, e->tables);
+    }
     e->mcf = model_const<float>(*m, e->tables);
     e->mcd = model_const<double>(*m, e->tables);
     e->has_model = true;
@@ -1317,6 +1340,48 @@ sas_status sas_eval_model(sas_experiment* e, const void* q_xyz, size_t n, void* 
     else
         ce = dispatch_eval<double>(e, e->mcd, (const double*)q_xyz, (double*)out, n);
     if (ce != cudaSuccess) return cuda_fail(ce, "eval launch");
+    return SAS_OK;
+}
+
+sas_status sas_attenuation_table(const sas_experiment* e, int* n, double* lambda, double* mu_s, double* coef,
+                                 double* lmin_lmax)
+{
+    if (!e) return fail(SAS_ERR_ARG, "experiment is NULL");
+    if (!e->has_model) return fail(SAS_ERR_STATE, "sas_set_model has not been called");
+    const ModelTables& t = e->tables;
+    if (n) *n = t.att_n;
+    for (int j = 0; j < SAS_ATT_MAX; ++j) {
+        const bool on = j < t.att_n;
+        if (lambda) lambda[j] = on ? t.att_lam[j] : 0.0;
+        if (mu_s) mu_s[j] = on ? t.att_mu[j] : 0.0;
+        if (coef) coef[j] = on ? t.att_c[j] : 0.0;
+    }
+    if (lmin_lmax) {
+        lmin_lmax[0] = t.att_lmin;
+        lmin_lmax[1] = t.att_lmax;
+    }
+    return SAS_OK;
+}
+
+sas_status sas_total_cross_section(sas_experiment* e, double lambda, double* sigma, double* panels,
+                                  int max_panels, int* n_panels)
+{
+    if (!e) return fail(SAS_ERR_ARG, "experiment is NULL");
+    if (!e->has_model) return fail(SAS_ERR_STATE, "sas_set_model has not been called");
+    if (e->model.sampling != SAS_QUADRATURE)
+        return fail(SAS_ERR_STATE, "a per-event model has no deterministic dSigma/dOmega");
+    if (!(lambda > 0.0) || !std::isfinite(lambda)) return fail(SAS_ERR_ARG, "lambda must be > 0");
+    if (max_panels < 0 || (max_panels > 0 && !panels)) return fail(SAS_ERR_ARG, "bad panel buffer");
+    AttRule r;
+    att_rule(e->inst, e->model, e->tables, r);
+    const int np = (int)r.panels.size();
+    if (n_panels) *n_panels = np;
+    std::vector<double> part((size_t)np);
+    double mu = 0.0;
+    SAS_CUDA(att_run(e->model, e->tables, e->d_poly, e->d_orient, r, &lambda, 1, e->stream, &mu, part.data()),
+             "total cross section");
+    if (sigma) *sigma = mu * 1e-10;
+    for (int i = 0; i < std::min(np, max_panels); ++i) panels[i] = part[(size_t)i];
     return SAS_OK;
 }
 

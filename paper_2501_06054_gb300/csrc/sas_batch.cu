@@ -283,6 +283,7 @@ sas_status sas_create_batch(const sas_instrument* inst, const sas_model_desc* mo
     if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
     if (ce != cudaSuccess) return bail(set_cuda_error(ce, "sas_create_batch"));
     std::vector<float> poly, orient;
+    std::vector<std::pair<size_t, ModelTables>> att_exps;   // experiments with self-attenuation
     b->h_exps.resize(n_exp);
     b->cost.resize(n_exp);
     b->hist_capable.resize(n_exp);
@@ -311,6 +312,7 @@ sas_status sas_create_batch(const sas_instrument* inst, const sas_model_desc* mo
                                  (table_bytes<float>(t.n_poly, t.n_orient, 1) <= (size_t)b->smem_optin);
         b->total_histories += counts[e];
         b->models.push_back(m);
+        if (m.self_attenuation) att_exps.emplace_back(e, t);
     }
     const size_t det = n_exp * (size_t)b->npix;
     ce = cudaMalloc(&b->d_exps, n_exp * sizeof(BatchExp));
@@ -327,6 +329,22 @@ sas_status sas_create_batch(const sas_instrument* inst, const sas_model_desc* mo
     if (ce == cudaSuccess && !orient.empty())
         ce = cudaMemcpy(b->d_orient, orient.data(), orient.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (ce != cudaSuccess) return bail(set_cuda_error(ce, "sas_create_batch allocation"));
+    // self-attenuation tables, from each experiment's tables now on the device
+    for (auto& ea : att_exps) {
+        const size_t e = ea.first;
+        ModelTables& t = ea.second;
+        AttRule r;
+        att_rule(*inst, models[e], t, r);
+        double mu[SAS_ATT_MAX];
+        ce = att_nodes(models[e], t, (const float*)b->d_poly + b->h_exps[e].poly_off,
+                       (const float*)b->d_orient + b->h_exps[e].orient_off, r, b->stream, mu);
+        if (ce != cudaSuccess) return bail(set_cuda_error(ce, "self-attenuation table"));
+        for (int j = 0; j < r.n_lambda; ++j)
+            if (!std::isfinite(mu[j]) || mu[j] < 0.0)
+                return bail(set_error(SAS_ERR_NUMERIC, "self-attenuation: non-finite or negative cross section"));
+        att_fit(r, mu, t);
+        b->h_exps[e].mc.att = model_const<float>(models[e], t).att;
+    }
     st = plan(b);
     if (st == SAS_OK) st = build_items(b);
     if (st != SAS_OK) return bail(st);

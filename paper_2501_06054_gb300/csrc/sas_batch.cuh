@@ -46,7 +46,7 @@ struct BatchParams {
     int npix;
 };
 
-template <int KIND, int HIST>
+template <int KIND, int HIST, bool ATT>
 __device__ __forceinline__ void batch_item(const BatchParams& P, const ModelConst<float>& mc,
                                            const float* poly, const float* orient,
                                            const WorkItem& w, const SmemHist& h, uint64_t seed,
@@ -62,7 +62,7 @@ __device__ __forceinline__ void batch_item(const BatchParams& P, const ModelCons
         int pix = -1;
         float wt = 0.f;
         if (j < w.n) {
-            const History<float> hs = history<float>(P.in, seed, w.exp, w.first + j);
+            const History<float> hs = history<float, ATT>(P.in, mc.att, seed, w.exp, w.first + j);
             tr.add(hs.wt);
             if (hs.pixel >= 0) {
                 wt = hs.pref * dsigma_history<float, KIND>(hs.q, mc, poly, orient, seed, w.exp, w.first + j);
@@ -76,6 +76,21 @@ __device__ __forceinline__ void batch_item(const BatchParams& P, const ModelCons
             atomicAdd(sw2 + pix, (double)wt * (double)wt);
             atomicAdd(cnt + pix, 1ull);
         }
+    }
+}
+
+template <int HIST, bool ATT>
+__device__ __forceinline__ void batch_dispatch(const BatchParams& P, const ModelConst<float>& mc, const float* poly,
+                                               const float* orient, const WorkItem& w, const SmemHist& h,
+                                               uint64_t seed, Kahan<float>& tr)
+{
+    switch (mc.kind) {
+    case SAS_SPHERE: batch_item<SAS_SPHERE, HIST, ATT>(P, mc, poly, orient, w, h, seed, tr); break;
+    case SAS_CORE_SHELL: batch_item<SAS_CORE_SHELL, HIST, ATT>(P, mc, poly, orient, w, h, seed, tr); break;
+    case SAS_CYLINDER: batch_item<SAS_CYLINDER, HIST, ATT>(P, mc, poly, orient, w, h, seed, tr); break;
+    case SAS_TRIAXIAL_ELLIPSOID: batch_item<SAS_TRIAXIAL_ELLIPSOID, HIST, ATT>(P, mc, poly, orient, w, h, seed, tr); break;
+    case SAS_PARALLELEPIPED: batch_item<SAS_PARALLELEPIPED, HIST, ATT>(P, mc, poly, orient, w, h, seed, tr); break;
+    default: batch_item<SAS_ELLIPSOID, HIST, ATT>(P, mc, poly, orient, w, h, seed, tr); break;
     }
 }
 
@@ -125,24 +140,12 @@ __global__ void __launch_bounds__(1024) batch_kernel(const BatchParams P)
         }
         __syncthreads();
         Kahan<float> tr;
-        if (hist) {
-            switch (mc.kind) {
-            case SAS_SPHERE: batch_item<SAS_SPHERE, HIST_OK>(P, mc, s_poly, orient, w, h, seed, tr); break;
-            case SAS_CORE_SHELL: batch_item<SAS_CORE_SHELL, HIST_OK>(P, mc, s_poly, orient, w, h, seed, tr); break;
-            case SAS_CYLINDER: batch_item<SAS_CYLINDER, HIST_OK>(P, mc, s_poly, orient, w, h, seed, tr); break;
-            case SAS_TRIAXIAL_ELLIPSOID: batch_item<SAS_TRIAXIAL_ELLIPSOID, HIST_OK>(P, mc, s_poly, orient, w, h, seed, tr); break;
-            case SAS_PARALLELEPIPED: batch_item<SAS_PARALLELEPIPED, HIST_OK>(P, mc, s_poly, orient, w, h, seed, tr); break;
-            default: batch_item<SAS_ELLIPSOID, HIST_OK>(P, mc, s_poly, orient, w, h, seed, tr); break;
-            }
+        if (mc.att.n > 0) {
+            if (hist) batch_dispatch<HIST_OK, true>(P, mc, s_poly, orient, w, h, seed, tr);
+            else batch_dispatch<0, true>(P, mc, s_poly, orient, w, h, seed, tr);
         } else {
-            switch (mc.kind) {
-            case SAS_SPHERE: batch_item<SAS_SPHERE, 0>(P, mc, s_poly, orient, w, h, seed, tr); break;
-            case SAS_CORE_SHELL: batch_item<SAS_CORE_SHELL, 0>(P, mc, s_poly, orient, w, h, seed, tr); break;
-            case SAS_CYLINDER: batch_item<SAS_CYLINDER, 0>(P, mc, s_poly, orient, w, h, seed, tr); break;
-            case SAS_TRIAXIAL_ELLIPSOID: batch_item<SAS_TRIAXIAL_ELLIPSOID, 0>(P, mc, s_poly, orient, w, h, seed, tr); break;
-            case SAS_PARALLELEPIPED: batch_item<SAS_PARALLELEPIPED, 0>(P, mc, s_poly, orient, w, h, seed, tr); break;
-            default: batch_item<SAS_ELLIPSOID, 0>(P, mc, s_poly, orient, w, h, seed, tr); break;
-            }
+            if (hist) batch_dispatch<HIST_OK, false>(P, mc, s_poly, orient, w, h, seed, tr);
+            else batch_dispatch<0, false>(P, mc, s_poly, orient, w, h, seed, tr);
         }
         double t = (double)tr.s - (double)tr.c;
 #pragma unroll

@@ -94,6 +94,9 @@ sas_status sas_trace_batch_static(const sas_instrument* inst, const sas_model_de
         st = validate_model(&m);
         if (st != SAS_OK) return st;
         if (m.precision != SAS_FP32) return set_error(SAS_ERR_ARG, "batched experiments are FP32");
+        if (m.self_attenuation)
+            return set_error(SAS_ERR_ARG, "the allocation-free batch does not build self-attenuation tables; "
+                                          "use sas_create_batch");
         ModelTables t;
         st = build_model_tables(m, t, instrument_q_max(*inst));
         if (st != SAS_OK) return st;

@@ -594,10 +594,31 @@ __device__ __forceinline__ bool slab(const InstConst<T>& in, const T o[3], const
     return ok && (b > a);
 }
 
-// One history up to the scattering vector and the weight prefactor.
+// mu_s(lambda) in 1/m from its Chebyshev interpolant (Clenshaw's recurrence).
 template <typename T>
-__device__ __forceinline__ History<T> history(const InstConst<T>& in, uint64_t seed, uint32_t exp_id,
-                                              uint64_t index)
+__device__ __forceinline__ T att_mu(const AttTable<T>& a, T lambda)
+{
+    const T t = fma(lambda, a.t_mul, a.t_add);
+    const T t2 = t + t;
+    T b1 = (T)0, b2 = (T)0;
+#pragma unroll
+    for (int j = SAS_ATT_MAX - 1; j >= 1; --j) {
+        if (j < a.n) {
+            const T b0 = fma(t2, b1, a.c[j] - b2);
+            b2 = b1;
+            b1 = b0;
+        }
+    }
+    return fma(t, b1, a.c[0] - b2);
+}
+
+// One history up to the scattering vector and the weight prefactor. The
+// beam inside the sample is attenuated with the instrument's mu plus, when
+// ATT and att.n > 0, the particles' own total scattering mu_s(lambda)
+// (ATT = false compiles the plain path without the table).
+template <typename T, bool ATT = true>
+__device__ __forceinline__ History<T> history(const InstConst<T>& in, const AttTable<T>& att, uint64_t seed,
+                                              uint32_t exp_id, uint64_t index)
 {
     const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
     const uint4 r0 = philox(make_uint4(0u, exp_id, (uint32_t)index, (uint32_t)(index >> 32)), key);
@@ -626,7 +647,11 @@ __device__ __forceinline__ History<T> history(const InstConst<T>& in, uint64_t s
         return h;
     }
     const T l = t_out - t_in;
-    h.wt = (in.mu > (T)0) ? M<T>::exp_(-in.mu * l) : (T)1;
+    T mu = in.mu;
+    if constexpr (ATT) {
+        if (att.n > 0) mu += att_mu<T>(att, lambda);
+    }
+    h.wt = (mu > (T)0) ? M<T>::exp_(-mu * l) : (T)1;
     const T s = u01<T>(r1.y) * l;
     const T ps[3] = {fma(t_in + s, ki[0], p2[0]), fma(t_in + s, ki[1], p2[1]),
                      fma(t_in + s, ki[2], p2[2])};
@@ -649,13 +674,13 @@ __device__ __forceinline__ History<T> history(const InstConst<T>& in, uint64_t s
     h.q[0] = k * (ko[0] - ki[0]);
     h.q[1] = k * (ko[1] - ki[1]);
     h.q[2] = k * (tin - tout) * M<T>::rcp(ko[2] + ki[2]);
-    T att = (T)1;
-    if (in.mu > (T)0) {
+    T out_att = (T)1;
+    if (mu > (T)0) {
         T e_in, e_out, l_out = (T)0;
         if (slab<T>(in, ps, ko, e_in, e_out)) l_out = e_out - e_in;
-        att = M<T>::exp_(-in.mu * (s + l_out));
+        out_att = M<T>::exp_(-mu * (s + l_out));
     }
-    h.pref = l * domega * att * (T)1e10;
+    h.pref = l * domega * out_att * (T)1e10;
     h.pixel = iy * in.nx + ix;
     return h;
 }

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <vector>
+#include <cuda_runtime.h>
 #include "sas_types.h"
 
 namespace sas {
@@ -19,6 +20,20 @@ struct ModelTables {
     int n_rad = 0;                // radius nodes (n_poly counts the table rows too)
     int n_tab = 0;                // table points (0: no table)
     double tab_inv_h = 0, tab_xmax = 0, tab_c0 = 0, tab_rbar = 0, tab_err = 0;
+    double r_max = 0;             // largest polydisperse radius node
+    // self-attenuation: mu_s (1/m) at the Chebyshev wavelengths and its
+    // interpolant (att_n = 0: off)
+    int att_n = 0;
+    double att_lmin = 0, att_lmax = 0;
+    double att_lam[SAS_ATT_MAX] = {}, att_mu[SAS_ATT_MAX] = {}, att_c[SAS_ATT_MAX] = {};
+};
+
+// The total-cross-section rule of a model for an instrument's band.
+struct AttRule {
+    int n_lambda = 0;
+    double lmin = 0, lmax = 0, kmax = 0;
+    double lam[SAS_ATT_MAX] = {};
+    std::vector<AttPanel> panels;
 };
 
 void gauss_legendre(int n, double* x, double* w);
@@ -38,6 +53,18 @@ double cylinder_radial_table(const double* r, const double* w, int np, double rb
 sas_status validate_instrument(const sas_instrument* in);
 sas_status validate_model(const sas_model_desc* m);
 template <typename T> ModelConst<T> model_const(const sas_model_desc& m, const ModelTables& t);
+// extent of the particle, the rule, and the table from mu_s at the nodes
+double model_extent(const sas_model_desc& m, const ModelTables& t);
+void att_rule(const sas_instrument& in, const sas_model_desc& m, const ModelTables& t, AttRule& r);
+void att_fit(const AttRule& r, const double* mu, ModelTables& t);
+// evaluates mu_s (1/m) at the rule's wavelengths on the GPU (kernels of the
+// model's kind and precision, tables already on the device)
+cudaError_t att_nodes(const sas_model_desc& m, const ModelTables& t, const void* d_poly, const void* d_orient,
+                      const AttRule& r, cudaStream_t s, double* mu_out);
+// the same at nl wavelengths lam (<= SAS_ATT_MAX): mu_s (1/m) and, if
+// partial_out is given, each panel's share of Sigma_s (1/angstrom), [nl][panels]
+cudaError_t att_run(const sas_model_desc& m, const ModelTables& t, const void* d_poly, const void* d_orient,
+                    const AttRule& r, const double* lam, int nl, cudaStream_t s, double* mu_out, double* partial_out);
 template <typename T> InstConst<T> inst_const(const sas_instrument& in);
 
 }  // namespace sas

@@ -144,7 +144,7 @@ __device__ __forceinline__ void tally(const TraceParams<T>& P, const SmemHist& h
 
 // ------------------------------------------------------------- kernels
 
-template <typename T, int KIND, int TALLY, int AGG>
+template <typename T, int KIND, int TALLY, int AGG, bool ATT>
 __global__ void __launch_bounds__(1024) trace_kernel(const TraceParams<T> P)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(1024) trace_kernel(const TraceParams<T> P)
         int pix = -1;
         T w = 0;
         if (j < P.n) {
-            const History<T> hs = history<T>(P.in, P.seed, P.exp_id, P.first + j);
+            const History<T> hs = history<T, ATT>(P.in, P.mc.att, P.seed, P.exp_id, P.first + j);
             tr.add(hs.wt);
             if (hs.pixel >= 0) {
                 w = hs.pref * dsigma_history<T, KIND>(hs.q, P.mc, poly, orient, P.seed, P.exp_id, P.first + j);
@@ -223,7 +223,7 @@ __global__ void records_kernel(const TraceParams<T> P)
 {
     const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= P.n) return;
-    const History<T> hs = history<T>(P.in, P.seed, P.exp_id, P.first + j);
+    const History<T> hs = history<T>(P.in, P.mc.att, P.seed, P.exp_id, P.first + j);
     double w = 0.0;
     if (hs.pixel >= 0)
         w = (double)(hs.pref * dsigma_history<T, KIND>(hs.q, P.mc, P.poly, P.orient, P.seed, P.exp_id, P.first + j));
@@ -242,6 +242,49 @@ __global__ void eval_kernel(const ModelConst<T> mc, const T* __restrict__ poly,
     out[i] = dsigma<T, KIND>(qv, mc, poly, orient);
 }
 
+// Total scattering cross section (1/angstrom): one thread per evaluation of
+// the rule, flattened over (wavelength y, |Q| panel p, node g, azimuth m);
+// panel p holds evaluations [off[p], off[p + 1]) of each wavelength's E.
+// On the Ewald sphere of k = k_lambda[y], with the panel's nodes scaled by
+// k / k_max,
+//   Q = (Q s cos phi, Q s sin phi, -Q^2 / (2k)), s = sqrt(1 - Q^2 / (4 k^2)),
+//   phi = 2 pi (m + 1/2) / n_phi,  dOmega = Q dQ dphi / k^2;
+// values[i] is the evaluation's weighted share (summed per panel by the
+// caller in a fixed order).
+template <typename T, int KIND>
+__global__ void __launch_bounds__(256) att_eval_kernel(const ModelConst<T> mc, const T* __restrict__ poly,
+                                                       const T* __restrict__ orient,
+                                                       const AttPanel* __restrict__ pan,
+                                                       const int* __restrict__ off, int n_pan, int E,
+                                                       const double* __restrict__ k_lambda, int n_lambda,
+                                                       double kmax, double* __restrict__ values)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)n_lambda * (size_t)E) return;
+    const int y = (int)(i / (size_t)E);
+    const int r = (int)(i - (size_t)y * E);
+    int lo = 0, hi = n_pan;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= r) lo = mid;
+        else hi = mid;
+    }
+    const AttPanel& P = pan[lo];
+    const int nphi = P.n_phi;
+    const int rr = r - off[lo];
+    const int g = rr / nphi;
+    const int m = rr - g * nphi;
+    const double k = k_lambda[y];
+    const double sc = k / kmax;
+    const double Q = sc * P.q[g];
+    const double st = sqrt(fmax(1.0 - Q * Q / (4.0 * k * k), 0.0));
+    double sp, cp;
+    sincospi((double)(2 * m + 1) / (double)nphi, &sp, &cp);
+    const T qv[3] = {(T)(Q * st * cp), (T)(Q * st * sp), (T)(-Q * Q / (2.0 * k))};
+    const double f = (double)dsigma<T, KIND>(qv, mc, poly, orient);
+    values[i] = sc * P.w[g] * Q * f * (2.0 * 3.14159265358979323846 / nphi) / (k * k);
+}
+
 // ------------------------------------------------------------- launchers
 
 struct LaunchCfg {
@@ -258,13 +301,18 @@ struct Launcher {
     static cudaError_t records(const TraceParams<T>& P, cudaStream_t s);
     static cudaError_t eval(const ModelConst<T>& mc, const T* poly, const T* orient, const T* q,
                             T* out, size_t n, cudaStream_t s);
+    static cudaError_t att(const ModelConst<T>& mc, const T* poly, const T* orient, const AttPanel* pan,
+                           const int* off, int n_pan, int E, const double* k_lambda, int n_lambda, double kmax,
+                           double* values, cudaStream_t s);
 };
 
 template <typename T, int KIND, int TALLY, int AGG>
 static cudaError_t launch_trace_variant(const TraceParams<T>& P, const LaunchCfg& cfg,
                                         int sm_count, cudaStream_t s, int* grid_used)
 {
-    auto kern = trace_kernel<T, KIND, TALLY, AGG>;
+    // the self-attenuation table is a separate instantiation: the plain path
+    // carries none of its instructions
+    auto kern = P.mc.att.n > 0 ? trace_kernel<T, KIND, TALLY, AGG, true> : trace_kernel<T, KIND, TALLY, AGG, false>;
     size_t smem = table_bytes<T>(P.mc.n_poly, P.mc.n_orient, P.stage_orient);
     if (TALLY == TALLY_SMEM) smem += hist_bytes(P.in.nx * P.in.ny);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -323,6 +371,20 @@ cudaError_t Launcher<T, KIND>::eval(const ModelConst<T>& mc, const T* poly, cons
     const size_t grid = (n + block - 1) / block;
     if (grid > 0x7FFFFFFFull) return cudaErrorInvalidValue;
     eval_kernel<T, KIND><<<(unsigned)grid, block, 0, s>>>(mc, poly, orient, q, out, n);
+    return cudaGetLastError();
+}
+
+template <typename T, int KIND>
+cudaError_t Launcher<T, KIND>::att(const ModelConst<T>& mc, const T* poly, const T* orient, const AttPanel* pan,
+                                   const int* off, int n_pan, int E, const double* k_lambda, int n_lambda,
+                                   double kmax, double* values, cudaStream_t s)
+{
+    const size_t total = (size_t)n_lambda * (size_t)E;
+    if (n_pan <= 0 || total == 0) return cudaSuccess;
+    const size_t grid = (total + 255) / 256;
+    if (grid > 0x7FFFFFFFull) return cudaErrorInvalidValue;
+    att_eval_kernel<T, KIND><<<(unsigned)grid, 256, 0, s>>>(mc, poly, orient, pan, off, n_pan, E, k_lambda,
+                                                              n_lambda, kmax, values);
     return cudaGetLastError();
 }
 

@@ -171,7 +171,9 @@ __device__ __forceinline__ RowRec trace_row(const STParams& P, int s, int m, con
     r.pix_flags = 0;
     const uint32_t j = (uint32_t)s * 128u + (uint32_t)m;
     if (j < pi.n) {
-        const History<float> hs = history<float>(P.in, *P.seed, P.philox_base + pi.exp, pi.first + j);
+        // the surrogate covers models without self-attenuation only
+        const AttTable<float> no_att{};
+        const History<float> hs = history<float>(P.in, no_att, *P.seed, P.philox_base + pi.exp, pi.first + j);
         r.wt = hs.wt;
         int flags = 1 | ((hs.pixel + 1) << 2);
         if (hs.pixel >= 0) {

@@ -714,6 +714,7 @@ bool surrogate_covers(const sas_surrogate* s, const sas_model_desc& m)
 {
     if (!s || m.kind != SAS_CYLINDER || m.precision != SAS_FP32 || m.isotropic) return false;
     if (m.sampling != SAS_QUADRATURE || m.poly_dist != SAS_POLY_SCHULZ) return false;   // trained on Schulz averages
+    if (m.self_attenuation) return false;   // the surrogate trace attenuates with the instrument's mu only
     const sas_surrogate_box& b = s->box;
     if (m.n_poly != b.n_poly || m.n_gamma != b.n_gamma || m.n_psi != b.n_psi) return false;
     return m.radius >= b.r_min && m.radius <= b.r_max && m.length >= b.l_min && m.length <= b.l_max &&

@@ -9,6 +9,7 @@
 #define SAS_MAX_ORIENT_SIDE 128
 #define SAS_POLY_STRIDE 8     // values per polydispersity node
 #define SAS_ORIENT_STRIDE 4   // values per orientation node
+#define SAS_ATT_GL 8          // Gauss-Legendre nodes per |Q| panel of the total cross section
 
 namespace sas {
 
@@ -21,6 +22,24 @@ struct InstConst {
     T det_z, px, py, half_wx, half_wy, area;
     T two_pi;
     int nx, ny;
+};
+
+// Attenuation of the beam by the particles' own scattering, mu_s(lambda) in
+// 1/m, as sum_j c[j] T_j(t), t = lambda * t_mul + t_add (n = 0: off).
+template <typename T>
+struct AttTable {
+    int n;
+    T t_mul, t_add;
+    T c[SAS_ATT_MAX];
+};
+
+// One |Q| panel of the total-cross-section rule at k_max: Gauss-Legendre
+// nodes q and weights w (1/angstrom) and the azimuthal points on its rings.
+struct AttPanel {
+    double q[SAS_ATT_GL];
+    double w[SAS_ATT_GL];
+    int n_phi;
+    int pad;
 };
 
 // Model constants in the trace precision.
@@ -63,6 +82,7 @@ struct ModelConst {
     // orientation rows come in threes: (A, w), (B, 0), (C, 0)
     T ax_a, ax_b, ax_c;
     T ev_frame[6];   // rows A and B of the fixed frame (C is ev_axis)
+    AttTable<T> att; // self-attenuation mu_s(lambda) (n = 0: the instrument's mu only)
 };
 
 }  // namespace sas

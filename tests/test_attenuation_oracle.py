@@ -198,3 +198,13 @@ def test_trace_uses_the_attenuation():
     mu0 = oracle.att_eval(inst, m, [inst.lambda0])[0]
     assert t0 == pytest.approx(n, rel=1e-12)
     assert t1 / n == pytest.approx(math.exp(-mu0 * inst.sample_thickness), rel=2e-3)
+
+
+def test_panels_sum_to_the_total():
+    m = W.Model(kind=W.CYLINDER, radius=20.0, length=300.0, sld=2e-6, volume_fraction=0.01, poly=0.1, n_poly=4,
+                sigma_orient=0.2, n_gamma=4, n_psi=4)
+    n = oracle.sigma_s_npanels(m, 5.4)
+    parts = [oracle.sigma_s_panel(m, 6.0, 5.4, i) for i in range(n)]
+    assert math.isnan(oracle.sigma_s_panel(m, 6.0, 5.4, n))
+    assert sum(parts) == pytest.approx(oracle.sigma_s(m, 6.0, 5.4), rel=1e-13)
+    assert all(p > 0 for p in parts)
