@@ -476,6 +476,8 @@ sas_status build_model_tables(const sas_model_desc& m, ModelTables& t, double q_
             p[0] = ri; p[1] = 1.0 / ri; p[2] = ro; p[3] = 1.0 / ro;
             p[4] = 3.0 * sw * (m.sld - m.sld_shell) * Vc;
             p[5] = 3.0 * sw * (m.sld_shell - m.sld_solvent) * Vo;
+            p[6] = p[4] / (ri * ri * ri);
+            p[7] = p[5] / (ro * ro * ro);
             vmean += w[i] * Vo;
         } else if (m.kind == SAS_CYLINDER) {
             const double V = pi * ri * ri * m.length;

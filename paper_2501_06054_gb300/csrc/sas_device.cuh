@@ -158,15 +158,34 @@ __device__ __forceinline__ T avg_core_shell(T q, T iq, const T* __restrict__ pol
 {
     T acc = 0;
     if constexpr (sizeof(T) == sizeof(float)) {
+        // sin and cos of x1 = q r_c from the special-function unit (absolute
+        // error about 1e-6 over these arguments); those of x2 = q (r_c + t) by
+        // angle addition with q t. The amplitude term c g(x) is
+        // (iq^3 c / r^3) (sin x - x cos x) for x >= 1.5 and c h(x^2) below,
+        // h the series of g to x^10 (truncation 5e-9 relative at 1.5), where
+        // the closed form's cancellation would exceed 2e-6 relative.
         float st, ct;
         sas_sincosf(q * shell, st, ct);
+        const float iq3 = iq * iq * iq;
+        const float gs[6] = {3.333333333e-01f, -3.333333333e-02f, 1.190476190e-03f, -2.204585538e-05f,
+                             2.505210839e-07f, -1.927085260e-09f};
 #pragma unroll 4
         for (int i = 0; i < np; ++i) {
-            const T* p = poly + 8 * i;
-            float g1, g2;
-            sas_sphere_g2(q * p[0], iq * p[1], q * p[2], iq * p[3], st, ct, g1, g2);
-            const T F = fma(p[4], g1, p[5] * g2);
-            acc = fma(F, F, acc);
+            const float4 pa = *reinterpret_cast<const float4*>(poly + 8 * i);       // r_c, 1/r_c, r_o, 1/r_o
+            const float4 pb = *reinterpret_cast<const float4*>(poly + 8 * i + 4);   // c_1, c_2, c_1/r_c^3, c_2/r_o^3
+            const float x1 = q * pa.x, x2 = q * pa.z;
+            float s1, c1;
+            __sincosf(x1, &s1, &c1);
+            const float s2 = fmaf(s1, ct, c1 * st);
+            const float c2 = fmaf(c1, ct, -s1 * st);
+            const float A1 = fmaf(-x1, c1, s1), A2 = fmaf(-x2, c2, s2);
+            const float h1 = sas_horner(gs, x1 * x1), h2 = sas_horner(gs, x2 * x2);
+            // select (coefficient, value) pairs, then one FMA combines them
+            const bool s1b = x1 < 1.5f, s2b = x2 < 1.5f;
+            const float k1 = s1b ? pb.x : iq3 * pb.z, v1 = s1b ? h1 : A1;
+            const float k2 = s2b ? pb.y : iq3 * pb.w, v2 = s2b ? h2 : A2;
+            const float F = fmaf(k1, v1, k2 * v2);
+            acc = fmaf(F, F, acc);
         }
     } else {
 #pragma unroll 4
