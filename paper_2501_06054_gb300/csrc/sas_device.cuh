@@ -38,6 +38,20 @@ __device__ __forceinline__ T u01(uint32_t x)
     return (T)((x >> 9) | 0u) * (T)(1.0 / 8388608.0) + (T)(0.5 / 8388608.0);
 }
 
+// FP32: the same value without an integer-to-float conversion: the 23 bits
+// as the mantissa of a float in [1, 2), minus (1 - 2^-24); exact.
+template <>
+__device__ __forceinline__ float u01<float>(uint32_t x)
+{
+    return __uint_as_float((x >> 9) | 0x3F800000u) - 0.99999994f;
+}
+
+// (float)k for 0 <= k < 2^23 without a conversion instruction (exact)
+__device__ __forceinline__ float small_uint_to_float(uint32_t k)
+{
+    return __uint_as_float(k | 0x4B000000u) - 8388608.0f;
+}
+
 // --------------------------------------------------------------- math glue
 template <typename T> struct M;
 
@@ -164,26 +178,24 @@ __device__ __forceinline__ T avg_core_shell(T q, T iq, const T* __restrict__ pol
 {
     T acc = 0;
     if constexpr (sizeof(T) == sizeof(float)) {
-        // sin and cos of x1 = q r_c from the special-function unit (absolute
-        // error about 1e-6 over these arguments); those of x2 = q (r_c + t) by
-        // angle addition with q t. The amplitude term c g(x) is
-        // (iq^3 c / r^3) (sin x - x cos x) for x >= 1.5 and c h(x^2) below,
-        // h the series of g to x^10 (truncation 5e-9 relative at 1.5), where
-        // the closed form's cancellation would exceed 2e-6 relative.
-        float st, ct;
-        sas_sincosf(q * shell, st, ct);
+        // sin and cos of x1 = q r_c and x2 = q r_o from the special-function
+        // unit (absolute error about 1e-6 over these arguments). The
+        // amplitude term c g(x) is (iq^3 c / r^3) (sin x - x cos x) for
+        // x >= 1.5 and c h(x^2) below, h the series of g to x^8 (truncation
+        // 4e-7 relative at 1.5), where the closed form's cancellation would
+        // exceed 2e-6 relative.
+        (void)shell;
         const float iq3 = iq * iq * iq;
-        const float gs[6] = {3.333333333e-01f, -3.333333333e-02f, 1.190476190e-03f, -2.204585538e-05f,
-                             2.505210839e-07f, -1.927085260e-09f};
-#pragma unroll 4
+        const float gs[5] = {3.333333333e-01f, -3.333333333e-02f, 1.190476190e-03f, -2.204585538e-05f,
+                             2.505210839e-07f};
+#pragma unroll 8
         for (int i = 0; i < np; ++i) {
             const float4 pa = *reinterpret_cast<const float4*>(poly + 8 * i);       // r_c, 1/r_c, r_o, 1/r_o
             const float4 pb = *reinterpret_cast<const float4*>(poly + 8 * i + 4);   // c_1, c_2, c_1/r_c^3, c_2/r_o^3
             const float x1 = q * pa.x, x2 = q * pa.z;
-            float s1, c1;
+            float s1, c1, s2, c2;
             __sincosf(x1, &s1, &c1);
-            const float s2 = fmaf(s1, ct, c1 * st);
-            const float c2 = fmaf(c1, ct, -s1 * st);
+            __sincosf(x2, &s2, &c2);
             const float A1 = fmaf(-x1, c1, s1), A2 = fmaf(-x2, c2, s2);
             const float h1 = sas_horner(gs, x1 * x1), h2 = sas_horner(gs, x2 * x2);
             // select (coefficient, value) pairs, then one FMA combines them
@@ -686,10 +698,20 @@ __device__ __forceinline__ History<T> history(const InstConst<T>& in, const AttT
     const uint64_t mx = (uint64_t)(r1.z >> 9) * (uint64_t)in.nx;
     const uint64_t my = (uint64_t)(r1.w >> 9) * (uint64_t)in.ny;
     const int ix = (int)(mx >> 23), iy = (int)(my >> 23);
-    const T fx = (T)(uint32_t)(mx & 0x7FFFFFu) * (T)(1.0 / 8388608.0) + (T)(0.5 / 8388608.0);
-    const T fy = (T)(uint32_t)(my & 0x7FFFFFu) * (T)(1.0 / 8388608.0) + (T)(0.5 / 8388608.0);
-    const T pd0 = fma((T)ix + fx, in.px, -in.half_wx);
-    const T pd1 = fma((T)iy + fy, in.py, -in.half_wy);
+    T fx, fy, fix, fiy;
+    if constexpr (sizeof(T) == sizeof(float)) {   // the same values, no conversion instructions
+        fx = __uint_as_float((uint32_t)(mx & 0x7FFFFFu) | 0x3F800000u) - 0.99999994f;
+        fy = __uint_as_float((uint32_t)(my & 0x7FFFFFu) | 0x3F800000u) - 0.99999994f;
+        fix = small_uint_to_float((uint32_t)ix);
+        fiy = small_uint_to_float((uint32_t)iy);
+    } else {
+        fx = (T)(uint32_t)(mx & 0x7FFFFFu) * (T)(1.0 / 8388608.0) + (T)(0.5 / 8388608.0);
+        fy = (T)(uint32_t)(my & 0x7FFFFFu) * (T)(1.0 / 8388608.0) + (T)(0.5 / 8388608.0);
+        fix = (T)ix;
+        fiy = (T)iy;
+    }
+    const T pd0 = fma(fix + fx, in.px, -in.half_wx);
+    const T pd1 = fma(fiy + fy, in.py, -in.half_wy);
     const T v[3] = {pd0 - ps[0], pd1 - ps[1], in.det_z - ps[2]};
     const T ir = M<T>::rsqrt(fma(v[0], v[0], fma(v[1], v[1], v[2] * v[2])));
     const T ko[3] = {v[0] * ir, v[1] * ir, v[2] * ir};
