@@ -90,6 +90,34 @@ def test_eval_model_parity(name, precision):
     e.close()
 
 
+def test_core_shell_series_switch_and_extreme_arguments():
+    """The FP32 core-shell node loop switches from the small-x series to the
+    closed form at x = q r = 1.5 for each radius: Q on both sides of the
+    switch of every core and outer node radius, tiny Q, and Q up to 2 / A
+    (x up to about 150, far beyond the detector's range)."""
+    m = CASES["core_shell_py"]
+    prep = oracle.Prepared(m)
+    radii = np.concatenate([prep.poly_r, prep.poly_r + m.thickness])
+    qs = np.concatenate([1.5 / radii * (1 - 3e-7), 1.5 / radii * (1 + 3e-7),
+                         np.logspace(-7, -2, 40), np.linspace(0.3, 2.0, 60)])
+    rng = np.random.default_rng(3)
+    d = rng.normal(size=(len(qs), 3))
+    q = d / np.linalg.norm(d, axis=1)[:, None] * qs[:, None]
+    qd = torch.tensor(q, dtype=torch.float32, device="cuda").contiguous()
+    out = torch.empty(len(q), dtype=torch.float32, device="cuda")
+    e = _exp(W.instrument(), m)
+    sas.sas_eval_model(e.h, qd, len(q), out)
+    torch.cuda.synchronize()
+    got = out.double().cpu().numpy()
+    ref = oracle.dsigma(prep, qd.double().cpu().numpy())
+    p0 = oracle.dsigma(prep, np.zeros((1, 3)))[0]
+    bad = np.abs(got - ref) > 1e-5 * np.abs(ref) + 1e-7 * p0
+    assert not bad.any(), (int(bad.sum()), qs[bad][:3], got[bad][:3], ref[bad][:3])
+    near = np.abs(ref) > 1e-3 * p0
+    assert np.max(np.abs(got - ref)[near] / np.abs(ref)[near]) < 1e-5
+    e.close()
+
+
 # ----------------------------------------------------------- per-neutron
 
 def _records(e, first, n, seed):
