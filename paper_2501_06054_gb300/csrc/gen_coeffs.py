@@ -14,6 +14,8 @@ Run once (python gen_coeffs.py > sas_coeffs.h); the output is committed.
   first two zeros j1, j2 of J1 (scipy) and h a degree-8 polynomial in x^2
   fitted like the above (relative error ~1e-8); no square root, no branch
   for the cylinder workloads' arguments, and the zeros are exact factors.
+* a(x) for x <= 4 as a plain degree-6 polynomial in x^2 (absolute error
+  ~8e-9), the cheapest form for the small arguments of most cylinder terms.
 * the same with the first three zeros for x <= 12 (degree 10 in the centred
   variable 2 x^2/144 - 1), used for the tail nodes of broad size
   distributions.
@@ -133,9 +135,9 @@ def fit_product(deg=8, X=8.0, nz=2):
     n = 8000
     s = 0.5 * X * X * (1 - np.cos(np.pi * (np.arange(n) + 0.5) / n))
     x = np.sqrt(s)
-    j = sp.jn_zeros(1, nz)
+    j = sp.jn_zeros(1, max(nz, 1))
     a = np.where(x > 0, 2 * sp.j1(np.maximum(x, 1e-300)) / np.maximum(x, 1e-300), 1.0)
-    p = np.prod([(1 - s / j[k] ** 2) for k in range(nz)], axis=0)
+    p = np.prod([(1 - s / j[k] ** 2) for k in range(nz)], axis=0) if nz else np.ones_like(s)
     ok = np.abs(p) > 1e-6
     u = s / (X * X)
     basis = [lambda uu, k=k: uu ** k for k in range(deg + 1)]
@@ -143,6 +145,8 @@ def fit_product(deg=8, X=8.0, nz=2):
     cs = [ci / (X * X) ** k for k, ci in enumerate(c)]   # coefficients in s = x^2
     if nz == 2:
         return cs, e, 1.0 / j[0] ** 2, 1.0 / j[1] ** 2, X * X
+    if nz == 0:
+        return cs, e, X * X
     return cs, e, [1.0 / jj ** 2 for jj in j], X * X
 
 
@@ -158,6 +162,7 @@ def main():
     cS, eS, cC, eC = fit_trig()
     cP, eP, iz1, iz2, smax = fit_product()
     cQ, eQ, izq, smaxq = fit_product_centered(deg=10, X=12.0, nz=3)
+    cR, eR, smaxr = fit_product(deg=6, X=4.0, nz=0)
     p2 = split2(math.pi / 2)
     p4 = split2(math.pi / 4)
     w = out.write
@@ -178,6 +183,10 @@ def main():
       % (smaxq, izq[0], izq[1], izq[2]))
     w(f"#define SAS_J1Q_C_N {len(cQ)}\n")
     w("#define SAS_J1Q_C {" + ", ".join("%.9ef" % v for v in cQ) + "}\n")
+    w(f"/* 2 J1(x)/x = r(s), s = x^2 <= {smaxr:g}; fit error {eR:.3e} */\n")
+    w("#define SAS_J1R_SMAX %.9ef\n" % smaxr)
+    w(f"#define SAS_J1R_C_N {len(cR)}\n")
+    w("#define SAS_J1R_C {" + ", ".join("%.9ef" % v for v in cR) + "}\n")
     w("/* sin r = r + r^3 S(r^2), cos r = 1 + r^2 C(r^2) */\n")
     for name, arr in (("SAS_SIN_C", list(cS)), ("SAS_COS_C", list(cC)), ("SAS_J1S_C", list(cs)),
                       ("SAS_J1M_C", list(cm)), ("SAS_J1H_C", list(ch))):

@@ -21,6 +21,10 @@
 #define SAS_J1Q_Z3 9.661886729e-03f
 #define SAS_J1Q_C_N 11
 #define SAS_J1Q_C {1.169814826e-01f, -2.826843847e-01f, 2.994814183e-01f, -1.884617908e-01f, 8.024855756e-02f, -2.491085858e-02f, 5.920458534e-03f, -1.115097382e-03f, 1.711073644e-04f, -2.243371898e-05f, 2.410184778e-06f}
+/* 2 J1(x)/x = r(s), s = x^2 <= 16; fit error 7.874e-09 */
+#define SAS_J1R_SMAX 1.600000000e+01f
+#define SAS_J1R_C_N 7
+#define SAS_J1R_C {9.999999921e-01f, -1.249999514e-01f, 5.208284287e-03f, -1.084883597e-04f, 1.352971110e-06f, -1.098744745e-08f, 5.233149538e-11f}
 /* sin r = r + r^3 S(r^2), cos r = 1 + r^2 C(r^2) */
 #define SAS_SIN_C_N 3
 #define SAS_SIN_C {-1.666666455e-01f, 8.332725399e-03f, -1.958295501e-04f}

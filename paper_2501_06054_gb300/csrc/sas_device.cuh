@@ -264,7 +264,14 @@ __device__ __forceinline__ T avg_cylinder(const T qv[3], const T* __restrict__ p
             // nodes are sorted by radius: find (uniformly over the active
             // lanes) how many need no large-x branch for any lane
             const float qm = __uint_as_float(__reduce_max_sync(__activemask(), __float_as_uint(qab2)));
-            int lo = 0, hi = np;       // nodes [0, lo): x <= 8 in every active lane
+            int lo0 = 0, hi = np;      // nodes [0, lo0): x <= 4 in every active lane
+            while (lo0 < hi) {
+                const int mid = (lo0 + hi) >> 1;
+                if (poly[8 * mid] * qm <= SAS_J1R_SMAX) lo0 = mid + 1;
+                else hi = mid;
+            }
+            int lo = lo0;              // nodes [lo0, lo): x <= 8
+            hi = np;
             while (lo < hi) {
                 const int mid = (lo + hi) >> 1;
                 if (poly[8 * mid] * qm <= SAS_J1P_SMAX) lo = mid + 1;
@@ -278,8 +285,14 @@ __device__ __forceinline__ T avg_cylinder(const T qv[3], const T* __restrict__ p
                 else hi = mid;
             }
 #pragma unroll 4
-            for (int i = 0; i < lo; ++i) {
+            for (int i = 0; i < lo0; ++i) {
                 const float2 rc = *reinterpret_cast<const float2*>(poly + 8 * i);   // (r^2, c)
+                const float a = sas_cyl_a_r(qab2 * rc.x);
+                inner = fma(rc.y, a * a, inner);
+            }
+#pragma unroll 4
+            for (int i = lo0; i < lo; ++i) {
+                const float2 rc = *reinterpret_cast<const float2*>(poly + 8 * i);
                 const float a = sas_cyl_a_s(qab2 * rc.x);
                 inner = fma(rc.y, a * a, inner);
             }

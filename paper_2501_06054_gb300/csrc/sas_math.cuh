@@ -212,6 +212,13 @@ SAS_HD float sas_cyl_a_s(float s)
     return p1 * p2 * h;
 }
 
+// a(x) for s = x^2 <= SAS_J1R_SMAX (x <= 4): a degree-6 polynomial in s.
+SAS_HD float sas_cyl_a_r(float s)
+{
+    const float c[SAS_J1R_C_N] = SAS_J1R_C;
+    return sas_horner(c, s);
+}
+
 // a(x) for s = x^2 <= SAS_J1Q_SMAX (x <= 12): three zero factors and a fit.
 SAS_HD float sas_cyl_a_s3(float s)
 {
