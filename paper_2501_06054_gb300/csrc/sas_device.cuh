@@ -60,7 +60,13 @@ template <> struct M<float> {
     static __device__ __forceinline__ void sincospi_(float u, float& s, float& c) { sincospif(u, &s, &c); }
     // approximate reciprocal (2 ulp; the trace's tolerances are 1e-5)
     static __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
-    static __device__ __forceinline__ float sqrt_(float x) { return __fsqrt_rn(x); }
+    // approximate square root (1 ulp; 0 -> 0)
+    static __device__ __forceinline__ float sqrt_(float x)
+    {
+        float r;
+        asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+        return r;
+    }
     // x > 0 only: x / sqrt(x) by the approximate reciprocal square root
     static __device__ __forceinline__ float sqrt_pos(float x) { return x * rsqrtf(x); }
     static __device__ __forceinline__ float rsqrt(float x) { return rsqrtf(x); }
@@ -90,7 +96,17 @@ template <> struct M<float> {
         h = fmaf(h, t, 3.333333333e-01f);
         return x < 1.5f ? h : big;
     }
-    static __device__ __forceinline__ float sinc(float y, float inv) { return sas_sinc(y, inv); }
+    // sin(y) / y for y >= 0, inv = 1 / y: the SFU's sine (absolute error
+    // about 1e-6, so 1e-6 / y in the sinc) for y >= 0.5, the series to y^6
+    // below (truncation 1e-8)
+    static __device__ __forceinline__ float sinc(float y, float inv)
+    {
+        const float t = y * y;
+        float h = fmaf(-1.984126984e-04f, t, 8.333333333e-03f);
+        h = fmaf(h, t, -1.666666667e-01f);
+        h = fmaf(h, t, 1.0f);
+        return y < 0.5f ? h : __sinf(y) * inv;
+    }
     static __device__ __forceinline__ float cyl_a(float x, float inv, float rsx)
     {
         return sas_cyl_a(x, inv, rsx);
@@ -352,8 +368,17 @@ __device__ __forceinline__ T avg_cylinder_tab(const T qv[3], const T* __restrict
         T inner = 0;
         if (x < mc.tab_xmax) {
             const T s = x * mc.tab_inv_h;
-            const int i = min((int)s, mc.n_tab - 2);
-            const T f = s - (T)i, f1 = (T)1 - f;
+            int i;
+            T fi;
+            if constexpr (sizeof(T) == sizeof(float)) {   // floor without conversion instructions (s < 2^23)
+                const float tz = __fadd_rz(s, 8388608.0f);
+                i = min(__float_as_int(tz) - 0x4B000000, mc.n_tab - 2);
+                fi = small_uint_to_float((uint32_t)i);
+            } else {
+                i = min((int)s, mc.n_tab - 2);
+                fi = (T)i;
+            }
+            const T f = s - fi, f1 = (T)1 - f;
             const T g0 = tab[2 * i], d0 = tab[2 * i + 1], g1 = tab[2 * i + 2], d1 = tab[2 * i + 3];
             // h00 = (1 + 2f)(1 - f)^2, h10 = f (1 - f)^2, h01 = f^2 (3 - 2f), h11 = f^2 (f - 1)
             inner = mc.tab_c0 * (f1 * f1 * fma((T)2 * f + (T)1, g0, f * d0) + f * f * fma((T)3 - (T)2 * f, g1, -f1 * d1));
