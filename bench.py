@@ -639,6 +639,8 @@ def main():
             line["secondary"] = {"error": repr(exc)}
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg)
+        one = cpu_baseline(cfg, target_s=3.0, threads=1)
+        line["cpu_baseline"]["one_thread"] = {"value": one["value"], "sample": one["sample"]}
     print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()

@@ -117,50 +117,61 @@ void gauss_legendre(int n, double* x, double* w)
     }
 }
 
-// Eigenvalues and first eigenvector components of a symmetric tridiagonal
-// matrix (diag d, off-diagonal e) by the cyclic Jacobi method.
-static void jacobi_eigen(int n, const double* d, const double* e, double* lam, double* v0)
+// Eigenvalues of the symmetric tridiagonal matrix (diagonal d[n],
+// off-diagonal e[n-1]) and the first component of each unit eigenvector, by
+// the implicit QL iteration with Wilkinson-type shifts (Golub and Van Loan,
+// Sec. 8.3): each sweep chases a bulge with Givens rotations from the bottom
+// of the active block up to its top; only row 0 of the accumulated rotations
+// is kept. O(n^2) work.
+static void tridiag_eigen(int n, const double* d_in, const double* e_in, double* lam, double* v0)
 {
-    std::vector<double> A((size_t)n * n, 0.0);
-    for (int i = 0; i < n; ++i) A[(size_t)i * n + i] = d[i];
-    for (int i = 0; i + 1 < n; ++i) A[(size_t)i * n + i + 1] = A[(size_t)(i + 1) * n + i] = e[i];
-    std::vector<double> row0(n, 0.0);
-    row0[0] = 1.0;   // first row of the accumulated rotation matrix
-    for (int sweep = 0; sweep < 100; ++sweep) {
-        double off = 0.0, tot = 0.0;
-        for (int i = 0; i < n; ++i)
-            for (int j = 0; j < n; ++j) {
-                const double a = A[(size_t)i * n + j] * A[(size_t)i * n + j];
-                tot += a;
-                if (i != j) off += a;
+    std::vector<double> d(d_in, d_in + n), e((size_t)n, 0.0), z((size_t)n, 0.0);
+    for (int i = 0; i + 1 < n; ++i) e[i] = e_in[i];
+    z[0] = 1.0;
+    for (int l = 0; l < n; ++l) {
+        for (int iter = 0; iter < 60; ++iter) {
+            int m = l;
+            for (; m + 1 < n; ++m) {   // a negligible coupling splits the block at m
+                const double dd = std::fabs(d[m]) + std::fabs(d[m + 1]);
+                if (std::fabs(e[m]) <= 1e-17 * dd) break;
             }
-        if (off <= 1e-32 * tot) break;
-        for (int p = 0; p < n - 1; ++p)
-            for (int q = p + 1; q < n; ++q) {
-                const double apq = A[(size_t)p * n + q];
-                if (apq == 0.0) continue;
-                const double app = A[(size_t)p * n + p], aqq = A[(size_t)q * n + q];
-                const double theta = (aqq - app) / (2.0 * apq);
-                const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
-                const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
-                for (int r = 0; r < n; ++r) {   // A <- A J (columns p, q)
-                    const double arp = A[(size_t)r * n + p], arq = A[(size_t)r * n + q];
-                    A[(size_t)r * n + p] = c * arp - s * arq;
-                    A[(size_t)r * n + q] = s * arp + c * arq;
+            if (m == l) break;
+            // shift: the eigenvalue of the leading 2x2 block closer to d[l]
+            double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+            double r = std::hypot(g, 1.0);
+            g = d[m] - d[l] + e[l] / (g + (g >= 0.0 ? r : -r));
+            double sn = 1.0, cs = 1.0, p = 0.0;
+            bool deflated = false;
+            for (int i = m - 1; i >= l; --i) {
+                const double f = sn * e[i], b = cs * e[i];
+                r = std::hypot(f, g);
+                e[i + 1] = r;
+                if (r == 0.0) {        // the bulge vanished: the block splits here
+                    d[i + 1] -= p;
+                    e[m] = 0.0;
+                    deflated = true;
+                    break;
                 }
-                for (int r = 0; r < n; ++r) {   // A <- J^T A (rows p, q)
-                    const double apr = A[(size_t)p * n + r], aqr = A[(size_t)q * n + r];
-                    A[(size_t)p * n + r] = c * apr - s * aqr;
-                    A[(size_t)q * n + r] = s * apr + c * aqr;
-                }
-                const double vp = row0[p], vq = row0[q];
-                row0[p] = c * vp - s * vq;
-                row0[q] = s * vp + c * vq;
+                sn = f / r;
+                cs = g / r;
+                g = d[i + 1] - p;
+                r = (d[i] - g) * sn + 2.0 * cs * b;
+                p = sn * r;
+                d[i + 1] = g + p;
+                g = cs * r - b;
+                const double zi = z[i], zi1 = z[i + 1];   // rotate columns i, i + 1 of row 0
+                z[i + 1] = sn * zi + cs * zi1;
+                z[i] = cs * zi - sn * zi1;
             }
+            if (deflated) continue;
+            d[l] -= p;
+            e[l] = g;
+            e[m] = 0.0;
+        }
     }
     for (int i = 0; i < n; ++i) {
-        lam[i] = A[(size_t)i * n + i];
-        v0[i] = row0[i];
+        lam[i] = d[i];
+        v0[i] = z[i];
     }
 }
 
@@ -171,7 +182,7 @@ void gauss_laguerre_gen(int n, double alpha, double* x, double* w)
     std::vector<double> d(n), e(n > 1 ? n - 1 : 1), lam(n), v0(n);
     for (int k = 0; k < n; ++k) d[k] = 2.0 * k + alpha + 1.0;
     for (int k = 1; k < n; ++k) e[k - 1] = std::sqrt(k * (k + alpha));
-    jacobi_eigen(n, d.data(), e.data(), lam.data(), v0.data());
+    tridiag_eigen(n, d.data(), e.data(), lam.data(), v0.data());
     std::vector<int> idx(n);
     for (int i = 0; i < n; ++i) idx[i] = i;
     std::sort(idx.begin(), idx.end(), [&](int a, int b) { return lam[a] < lam[b]; });
