@@ -16,6 +16,8 @@ Run once (python gen_coeffs.py > sas_coeffs.h); the output is committed.
   for the cylinder workloads' arguments, and the zeros are exact factors.
 * a(x) for x <= 4 as a plain degree-6 polynomial in x^2 (absolute error
   ~8e-9), the cheapest form for the small arguments of most cylinder terms.
+* a(x) for x <= 6 as a degree-7 polynomial in the centred variable
+  2 x^2 / 36 - 1 (absolute error ~6e-8).
 * the same with the first three zeros for x <= 12 (degree 10 in the centred
   variable 2 x^2/144 - 1), used for the tail nodes of broad size
   distributions.
@@ -121,9 +123,9 @@ def fit_product_centered(deg=10, X=12.0, nz=3):
     n = 8000
     s = 0.5 * X * X * (1 - np.cos(np.pi * (np.arange(n) + 0.5) / n))
     x = np.sqrt(s)
-    j = sp.jn_zeros(1, nz)
+    j = sp.jn_zeros(1, max(nz, 1))
     a = np.where(x > 0, 2 * sp.j1(np.maximum(x, 1e-300)) / np.maximum(x, 1e-300), 1.0)
-    p = np.prod([(1 - s / j[k] ** 2) for k in range(nz)], axis=0)
+    p = np.prod([(1 - s / j[k] ** 2) for k in range(nz)], axis=0) if nz else np.ones_like(s)
     ok = np.abs(p) > 1e-6
     v = 2 * s / (X * X) - 1
     basis = [lambda vv, k=k: vv ** k for k in range(deg + 1)]
@@ -163,6 +165,7 @@ def main():
     cP, eP, iz1, iz2, smax = fit_product()
     cQ, eQ, izq, smaxq = fit_product_centered(deg=10, X=12.0, nz=3)
     cR, eR, smaxr = fit_product(deg=6, X=4.0, nz=0)
+    cV, eV, _, smaxv = fit_product_centered(deg=7, X=6.0, nz=0)
     p2 = split2(math.pi / 2)
     p4 = split2(math.pi / 4)
     w = out.write
@@ -187,6 +190,10 @@ def main():
     w("#define SAS_J1R_SMAX %.9ef\n" % smaxr)
     w(f"#define SAS_J1R_C_N {len(cR)}\n")
     w("#define SAS_J1R_C {" + ", ".join("%.9ef" % v for v in cR) + "}\n")
+    w(f"/* 2 J1(x)/x = v(2 s / {smaxv:g} - 1), s = x^2 <= {smaxv:g}; fit error {eV:.3e} */\n")
+    w("#define SAS_J1V_SMAX %.9ef\n" % smaxv)
+    w(f"#define SAS_J1V_C_N {len(cV)}\n")
+    w("#define SAS_J1V_C {" + ", ".join("%.9ef" % v for v in cV) + "}\n")
     w("/* sin r = r + r^3 S(r^2), cos r = 1 + r^2 C(r^2) */\n")
     for name, arr in (("SAS_SIN_C", list(cS)), ("SAS_COS_C", list(cC)), ("SAS_J1S_C", list(cs)),
                       ("SAS_J1M_C", list(cm)), ("SAS_J1H_C", list(ch))):

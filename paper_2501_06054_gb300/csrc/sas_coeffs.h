@@ -25,6 +25,10 @@
 #define SAS_J1R_SMAX 1.600000000e+01f
 #define SAS_J1R_C_N 7
 #define SAS_J1R_C {9.999999921e-01f, -1.249999514e-01f, 5.208284287e-03f, -1.084883597e-04f, 1.352971110e-06f, -1.098744745e-08f, 5.233149538e-11f}
+/* 2 J1(x)/x = v(2 s / 36 - 1), s = x^2 <= 36; fit error 5.705e-08 */
+#define SAS_J1V_SMAX 3.600000000e+01f
+#define SAS_J1V_C_N 8
+#define SAS_J1V_C {-7.217181136e-02f, -2.981637351e-01f, 4.605520289e-01f, -2.369276485e-01f, 6.421195081e-02f, -1.091158982e-02f, 1.293798204e-03f, -1.110028616e-04f}
 /* sin r = r + r^3 S(r^2), cos r = 1 + r^2 C(r^2) */
 #define SAS_SIN_C_N 3
 #define SAS_SIN_C {-1.666666455e-01f, 8.332725399e-03f, -1.958295501e-04f}

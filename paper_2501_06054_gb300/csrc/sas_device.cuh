@@ -260,86 +260,107 @@ struct Kahan {
 // FP32: 2 J1(x)/x from s = x^2 = |Q x c|^2 r^2 by the product form for
 // x <= 8 (no square root per term); larger x (tails of broad size
 // distributions) take the modulus-phase form. FP64: the C library's j1.
+// Number of the ascending radius nodes whose r^2 qm stays <= smax (binary
+// search on the first value of each poly row).
+__device__ __forceinline__ int cyl_tier_end(const float* __restrict__ poly, int lo, int np, float qm, float smax)
+{
+    int hi = np;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (poly[8 * mid] * qm <= smax) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
 template <typename T>
 __device__ __forceinline__ T avg_cylinder(const T qv[3], const T* __restrict__ poly, int np,
                                           const T* __restrict__ orient, int no, T half_len)
 {
     Kahan<T> k;
-    for (int o = 0; o < no; ++o) {
-        const T* c = orient + 4 * o;
-        const T qc = fma(qv[0], c[0], fma(qv[1], c[1], qv[2] * c[2]));
-        const T x0 = fma(qv[1], c[2], -qv[2] * c[1]);
-        const T x1 = fma(qv[2], c[0], -qv[0] * c[2]);
-        const T x2 = fma(qv[0], c[1], -qv[1] * c[0]);
-        const T qab2 = fma(x0, x0, fma(x1, x1, x2 * x2));
-        const T y = fabs(qc) * half_len;
-        const T sn = M<T>::sinc(y, M<T>::rcp(y));
-        const T qab = M<T>::sqrt_(qab2);
-        T inner = 0;
-        if constexpr (sizeof(T) == sizeof(float)) {
-            // nodes are sorted by radius: find (uniformly over the active
-            // lanes) how many need no large-x branch for any lane
-            const float qm = __uint_as_float(__reduce_max_sync(__activemask(), __float_as_uint(qab2)));
-            int lo0 = 0, hi = np;      // nodes [0, lo0): x <= 4 in every active lane
-            while (lo0 < hi) {
-                const int mid = (lo0 + hi) >> 1;
-                if (poly[8 * mid] * qm <= SAS_J1R_SMAX) lo0 = mid + 1;
-                else hi = mid;
-            }
-            int lo = lo0;              // nodes [lo0, lo): x <= 8
-            hi = np;
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (poly[8 * mid] * qm <= SAS_J1P_SMAX) lo = mid + 1;
-                else hi = mid;
-            }
-            int lo2 = lo;              // nodes [lo, lo2): x <= 12
-            hi = np;
-            while (lo2 < hi) {
-                const int mid = (lo2 + hi) >> 1;
-                if (poly[8 * mid] * qm <= SAS_J1Q_SMAX) lo2 = mid + 1;
-                else hi = mid;
-            }
+    if constexpr (sizeof(T) == sizeof(float)) {
+        // FP32: 2 J1(x)/x in the cheapest form valid for x = |Q x c| r. Since
+        // |Q x c|^2 <= |Q|^2 for every axis c, the nodes (sorted by radius)
+        // are split once per history, uniformly over the warp's lanes, by
+        // the largest |Q|^2 of the warp: x <= 4, 6, 8, 12 and beyond.
+        const float q2 = fma(qv[0], qv[0], fma(qv[1], qv[1], qv[2] * qv[2]));
+        const float qm = __uint_as_float(__reduce_max_sync(__activemask(), __float_as_uint(q2)));
+        const int t4 = cyl_tier_end(poly, 0, np, qm, SAS_J1R_SMAX);
+        const int t6 = cyl_tier_end(poly, t4, np, qm, SAS_J1V_SMAX);
+        const int t8 = cyl_tier_end(poly, t6, np, qm, SAS_J1P_SMAX);
+        const int t12 = cyl_tier_end(poly, t8, np, qm, SAS_J1Q_SMAX);
+        for (int o = 0; o < no; ++o) {
+            const T* c = orient + 4 * o;
+            const T qc = fma(qv[0], c[0], fma(qv[1], c[1], qv[2] * c[2]));
+            const T x0 = fma(qv[1], c[2], -qv[2] * c[1]);
+            const T x1 = fma(qv[2], c[0], -qv[0] * c[2]);
+            const T x2 = fma(qv[0], c[1], -qv[1] * c[0]);
+            const T qab2 = fma(x0, x0, fma(x1, x1, x2 * x2));
+            const T y = fabs(qc) * half_len;
+            const T sn = M<T>::sinc(y, M<T>::rcp(y));
+            float inner = 0.f;
 #pragma unroll 4
-            for (int i = 0; i < lo0; ++i) {
+            for (int i = 0; i < t4; ++i) {
                 const float2 rc = *reinterpret_cast<const float2*>(poly + 8 * i);   // (r^2, c)
                 const float a = sas_cyl_a_r(qab2 * rc.x);
                 inner = fma(rc.y, a * a, inner);
             }
 #pragma unroll 4
-            for (int i = lo0; i < lo; ++i) {
+            for (int i = t4; i < t6; ++i) {
+                const float2 rc = *reinterpret_cast<const float2*>(poly + 8 * i);
+                const float a = sas_cyl_a_v(qab2 * rc.x);
+                inner = fma(rc.y, a * a, inner);
+            }
+#pragma unroll 2
+            for (int i = t6; i < t8; ++i) {
                 const float2 rc = *reinterpret_cast<const float2*>(poly + 8 * i);
                 const float a = sas_cyl_a_s(qab2 * rc.x);
                 inner = fma(rc.y, a * a, inner);
             }
 #pragma unroll 2
-            for (int i = lo; i < lo2; ++i) {
+            for (int i = t8; i < t12; ++i) {
                 const float2 rc = *reinterpret_cast<const float2*>(poly + 8 * i);
                 const float a = sas_cyl_a_s3(qab2 * rc.x);
                 inner = fma(rc.y, a * a, inner);
             }
-            for (int i = lo2; i < np; ++i) {
-                const T* p = poly + 8 * i;
-                const float sx = qab2 * p[0];
-                float a;
-                if (sx <= SAS_J1Q_SMAX) {
-                    a = sas_cyl_a_s3(sx);
-                } else {
-                    const float x = qab * p[2];
-                    a = sas_cyl_a_large(x, __frcp_rn(x), rsqrtf(x));
+            if (t12 < np) {
+                const float qab = M<T>::sqrt_(qab2);
+                for (int i = t12; i < np; ++i) {
+                    const T* p = poly + 8 * i;
+                    const float sx = qab2 * p[0];
+                    float a;
+                    if (sx <= SAS_J1Q_SMAX) {
+                        a = sas_cyl_a_s3(sx);
+                    } else {
+                        const float x = qab * p[2];
+                        a = sas_cyl_a_large(x, __frcp_rn(x), rsqrtf(x));
+                    }
+                    inner = fma(p[1], a * a, inner);
                 }
-                inner = fma(p[1], a * a, inner);
             }
-        } else {
+            k.add(c[3] * sn * sn * inner);
+        }
+    } else {
+        for (int o = 0; o < no; ++o) {
+            const T* c = orient + 4 * o;
+            const T qc = fma(qv[0], c[0], fma(qv[1], c[1], qv[2] * c[2]));
+            const T x0 = fma(qv[1], c[2], -qv[2] * c[1]);
+            const T x1 = fma(qv[2], c[0], -qv[0] * c[2]);
+            const T x2 = fma(qv[0], c[1], -qv[1] * c[0]);
+            const T qab2 = fma(x0, x0, fma(x1, x1, x2 * x2));
+            const T y = fabs(qc) * half_len;
+            const T sn = M<T>::sinc(y, M<T>::rcp(y));
+            const T qab = M<T>::sqrt_(qab2);
             const T iq = M<T>::rcp(qab);
+            T inner = 0;
 #pragma unroll 4
             for (int i = 0; i < np; ++i) {
                 const T* p = poly + 8 * i;
                 const T a = M<T>::cyl_a(qab * p[2], iq * p[3], 0);
                 inner = fma(p[1], a * a, inner);
             }
+            k.add(c[3] * sn * sn * inner);
         }
-        k.add(c[3] * sn * sn * inner);
     }
     return k.s;
 }

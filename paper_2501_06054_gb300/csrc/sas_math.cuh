@@ -219,6 +219,14 @@ SAS_HD float sas_cyl_a_r(float s)
     return sas_horner(c, s);
 }
 
+// a(x) for s = x^2 <= SAS_J1V_SMAX (x <= 6): a degree-7 polynomial in the
+// centred variable 2 s / 36 - 1.
+SAS_HD float sas_cyl_a_v(float s)
+{
+    const float c[SAS_J1V_C_N] = SAS_J1V_C;
+    return sas_horner(c, fmaf(s, 2.0f / SAS_J1V_SMAX, -1.0f));
+}
+
 // a(x) for s = x^2 <= SAS_J1Q_SMAX (x <= 12): three zero factors and a fit.
 SAS_HD float sas_cyl_a_s3(float s)
 {

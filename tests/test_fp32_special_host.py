@@ -5,9 +5,10 @@ moves), so the same source compiled by g++ gives the device's arithmetic
 (up to the device compiler's contraction of a separate multiply and add
 into one FMA). Checked here against scipy in FP64:
 
-* 2 J1(x)/x in its three forms: the degree-6 polynomial for x <= 4, the
-  product form with two zeros for x <= 8, the three-zero form for x <= 12,
-  and the modulus-phase form beyond;
+* 2 J1(x)/x in its forms: the degree-6 polynomial for x <= 4, the centred
+  degree-7 polynomial for x <= 6, the product form with two zeros for
+  x <= 8, the three-zero form for x <= 12, and the modulus-phase form
+  beyond;
 * sin / cos after the two-part reduction;
 * the sphere amplitude g(x) = (sin x - x cos x) / x^3.
 """
@@ -28,6 +29,7 @@ SRC = r"""
 extern "C" {
 void cyl_a_r(const float* s, float* o, int n) { for (int i = 0; i < n; ++i) o[i] = sas_cyl_a_r(s[i]); }
 void cyl_a_s(const float* s, float* o, int n) { for (int i = 0; i < n; ++i) o[i] = sas_cyl_a_s(s[i]); }
+void cyl_a_v(const float* s, float* o, int n) { for (int i = 0; i < n; ++i) o[i] = sas_cyl_a_v(s[i]); }
 void cyl_a_s3(const float* s, float* o, int n) { for (int i = 0; i < n; ++i) o[i] = sas_cyl_a_s3(s[i]); }
 void cyl_a(const float* x, float* o, int n)
 {
@@ -64,8 +66,8 @@ def _a(x):
     return np.where(x > 0, 2 * sp.j1(np.maximum(x, 1e-300)) / np.maximum(x, 1e-300), 1.0)
 
 
-@pytest.mark.parametrize("name,xmax,tol", [("cyl_a_r", 4.0, 4e-7), ("cyl_a_s", 8.0, 4e-7),
-                                           ("cyl_a_s3", 12.0, 4e-7)])
+@pytest.mark.parametrize("name,xmax,tol", [("cyl_a_r", 4.0, 4e-7), ("cyl_a_v", 6.0, 4e-7),
+                                           ("cyl_a_s", 8.0, 4e-7), ("cyl_a_s3", 12.0, 4e-7)])
 def test_j1_polynomial_forms(lib, name, xmax, tol):
     x = np.linspace(0.0, xmax, 20001).astype(np.float32)
     s = (x * x).astype(np.float32)
