@@ -11,9 +11,13 @@
 //  * sphere amplitude f(x) = 3 (sin x - x cos x) / x^3: quadrant handled by
 //    two FMAs, one select and a sign flip; in the first quadrant it is
 //    3 (S - C) from the same polynomials, free of the closed form's
-//    cancellation at small x.
-//  * cylinder radial factor a(x) = 2 J1(x) / x: a fitted polynomial in
-//    (x / X1)^2 below X1 = 4, the modulus-phase form of J1 above it.
+//    cancellation at small x. (The trace kernels take sin and cos from the
+//    special-function unit instead; these forms serve the surrogate's exact
+//    targets and the host checks.)
+//  * cylinder radial factor a(x) = 2 J1(x) / x: fitted polynomials in x^2
+//    (plain to x = 4, centred to x = 6, with the first two or three zeros of
+//    J1 as exact factors to x = 8 and 12), the modulus-phase form of J1
+//    beyond.
 #pragma once
 
 #include <math.h>
@@ -133,39 +137,6 @@ SAS_HD float sas_sphere_g(float x, float inv)
 
 // f(x) = 3 (sin x - x cos x) / x^3
 SAS_HD float sas_sphere_f(float x, float inv) { return 3.0f * sas_sphere_g(x, inv); }
-
-// g at two radii r and r + t of the same history: x1 = q r, x2 = q (r + t).
-// x2 = k pi/2 + (r1 + q t) with the quadrant of x1, so sin and cos of the
-// reduced angle of x2 follow from those of x1 by angle addition with
-// (st, ct) = (sin q t, cos q t); below pi/4 g(x2) uses its Taylor series.
-SAS_HD void sas_sphere_g2(float x1, float inv1, float x2, float inv2, float st, float ct, float& g1,
-                          float& g2)
-{
-    // The quadrant sign (-1)^(k >> 1) is the same for both radii (x2 shares
-    // the quadrant of x1; when x1 < pi/4 it is +1), and callers square the
-    // combination a g1 + b g2, so it is left out: g1 and g2 are returned up
-    // to one common sign.
-    const SasTrig g = sas_reduce_pio2(x1);
-    const float sr = fmaf(g.r * g.t, g.S, g.r);
-    const float cr = fmaf(g.t, g.C, 1.0f);
-    const bool odd = (g.kb & 1) != 0;
-    // inner radius
-    const float A1 = fmaf(-x1, cr, sr);
-    const float B1 = fmaf(x1, sr, cr);
-    const float num1 = odd ? B1 : A1;
-    g1 = (x1 < 0.78539816f) ? (g.S - g.C) : num1 * inv1 * inv1 * inv1;
-    // outer radius: sin, cos of (r + q t)
-    const float sr2 = fmaf(sr, ct, cr * st);
-    const float cr2 = fmaf(cr, ct, -sr * st);
-    const float A2 = fmaf(-x2, cr2, sr2);
-    const float B2 = fmaf(x2, sr2, cr2);
-    const float num2 = odd ? B2 : A2;
-    // g(x) = 1/3 - x^2/30 + x^4/840 - x^6/45360 + x^8/3991680 - ...
-    const float c[5] = {3.333333333e-01f, -3.333333333e-02f, 1.190476190e-03f, -2.204585538e-05f,
-                        2.505210839e-07f};
-    const float small2 = sas_horner(c, x2 * x2);
-    g2 = (x2 < 0.78539816f) ? small2 : num2 * inv2 * inv2 * inv2;
-}
 
 // a(x) = 2 J1(x) / x for 0 <= x <= X1
 SAS_HD float sas_cyl_a_small(float x)
