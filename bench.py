@@ -164,7 +164,10 @@ def secondary(stream, info):
     n_ex = 4_000_000
     e = sas.Experiment(cfg["instrument"], m, stream=stream)
     e.trace(50_000, 1)
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
     ms = _events_ms(lambda: e.trace(n_ex, 1), stream)
+    clk_ex = sampler.stop()
     d_ex = e.read()
     fl = F.flops_per_history(m.kind, m.n_poly, m.n_gamma * m.n_psi)
     rate_ex = n_ex / (ms * 1e-3)
@@ -205,7 +208,10 @@ def secondary(stream, info):
         "exact": {"value": rate_ex, "unit": UNIT, "histories": n_ex,
                   "roofline": {"bound": "alu", "achieved": fl * rate_ex / 1e12, "peak": peak,
                                "unit": "TFLOP/s", "frac": fl * rate_ex / 1e12 / peak,
-                               "flops_per_history": fl}},
+                               "flops_per_history": fl, "clocks": clk_ex,
+                               "frac_at_sampled_clock": (fl * rate_ex / 1e12 /
+                                                         F.fp32_peak_tflops(info["sm_count"], clk_ex["sm_mhz"])
+                                                         if clk_ex else None)}},
         "radial_table": {"value": rate_tab, "unit": UNIT, "histories": n_tab,
                          "speedup_vs_exact": rate_tab / rate_ex,
                          "max_bin_rel_diff_vs_exact": float(rel_tab.max()),
