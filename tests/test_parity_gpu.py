@@ -118,6 +118,43 @@ def test_core_shell_series_switch_and_extreme_arguments():
     e.close()
 
 
+EXTREME = {
+    "sphere_r200": W.Model(kind=W.SPHERE, radius=200.0, sld=2e-6, volume_fraction=0.01, poly=0.1, n_poly=20),
+    "core_shell_thick": W.Model(kind=W.CORE_SHELL, radius=150.0, thickness=60.0, sld=1e-6, sld_shell=3e-6,
+                                sld_solvent=6e-6, volume_fraction=0.05, poly=0.1, n_poly=20),
+    "cylinder_long": W.Model(kind=W.CYLINDER, radius=40.0, length=2000.0, sld=1e-6, volume_fraction=0.01,
+                             poly=0.1, n_poly=12, sigma_orient=math.radians(10), axis_theta=1.0, axis_phi=0.5,
+                             n_gamma=12, n_psi=12),
+    "ellipsoid_big": W.Model(kind=W.ELLIPSOID, radius=150.0, radius_polar=300.0, sld=2e-6, volume_fraction=0.01,
+                             poly=0.1, n_poly=12, sigma_orient=0.2, n_gamma=10, n_psi=10),
+    "parallelepiped_big": W.Model(kind=W.PARALLELEPIPED, radius=60.0, radius_b=120.0, radius_polar=400.0,
+                                  sld=2e-6, volume_fraction=0.01, poly=0.1, n_poly=8, isotropic=W.UNIFORM_ANGLES,
+                                  n_gamma=6, n_psi=6, n_rot=6),
+}
+
+
+@pytest.mark.parametrize("name", list(EXTREME))
+def test_fp32_large_arguments(name):
+    """FP32 evaluations where q r reaches a few hundred (large particles,
+    |Q| up to 0.5 1/A), where the special-function unit's argument scaling
+    loses the most: same tolerance as the other evaluations."""
+    m = EXTREME[name]
+    n = 3001
+    q = W.random_q(n, 0.5, seed=29)
+    qd = torch.tensor(q, dtype=torch.float32, device="cuda").contiguous()
+    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    e = _exp(W.instrument(), m)
+    sas.sas_eval_model(e.h, qd, n, out)
+    torch.cuda.synchronize()
+    got = out.double().cpu().numpy()
+    prep = oracle.Prepared(m)
+    ref = oracle.dsigma(prep, qd.double().cpu().numpy())
+    p0 = oracle.dsigma(prep, np.zeros((1, 3)))[0]
+    bad = np.abs(got - ref) > 1e-5 * np.abs(ref) + 1e-7 * p0
+    assert not bad.any(), (name, int(bad.sum()), got[bad][:3], ref[bad][:3])
+    e.close()
+
+
 # ----------------------------------------------------------- per-neutron
 
 def _records(e, first, n, seed):
