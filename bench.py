@@ -611,7 +611,7 @@ def main():
                 "frac": achieved / peak_max,
                 # ncu capture of the same kernel (2e7 histories): DRAM read + write per
                 # launch; it does not grow with the history count (tables, flush)
-                "traffic": 428800,
+                "traffic": 424704,
                 "kernel": "trace_kernel<float, CORE_SHELL, TALLY_SMEM>",
                 "flops_per_history": fl,
                 "amplitudes_per_s": 2 * m.n_poly * n / (kms * 1e-3),
