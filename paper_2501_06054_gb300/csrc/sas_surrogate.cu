@@ -340,29 +340,67 @@ __global__ void __launch_bounds__(THREADS, 1) wgrad_kernel(const WgParams P, con
 
 // Row reductions of the backward pass: db2..db4 (row sums of dZ_2..4^T),
 // dw5 = sum_b dout_b h4_b, db5 = sum_b dout_b. One CTA per output.
-__global__ void rowsum_kernel(float* grad, const __nv_bfloat16* dz2, const __nv_bfloat16* dz3,
-                              const __nv_bfloat16* dz4, const __nv_bfloat16* ht4, const float* dout, uint32_t batch)
+__device__ __forceinline__ float bf16_lo(uint32_t u) { return __uint_as_float(u << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t u) { return __uint_as_float(u & 0xFFFF0000u); }
+
+// batch is a multiple of 128, so every row is 16-byte aligned and reads as
+// uint4 (8 BF16) / float4 vectors. FP32 sums of 8, Kahan-compensated per
+// thread, then an FP64 tree over the block (the FP64 pipe is slow on this
+// part: only the final combination uses it).
+__global__ void __launch_bounds__(256) rowsum_kernel(float* grad, const __nv_bfloat16* dz2,
+                                                     const __nv_bfloat16* dz3, const __nv_bfloat16* dz4,
+                                                     const __nv_bfloat16* ht4, const float* dout, uint32_t batch)
 {
     const int r = blockIdx.x;   // 0..767: db2..db4; 768..1023: dw5; 1024: db5
-    const __nv_bfloat16* dz = r < 256 ? dz2 : (r < 512 ? dz3 : dz4);
-    double s = 0.0;
-    for (uint32_t b = threadIdx.x; b < batch; b += blockDim.x) {
-        float v;
-        if (r < 768) v = __bfloat162float(dz[(size_t)(r % 256) * batch + b]);
-        else if (r < 1024) v = dout[b] * __bfloat162float(ht4[(size_t)(r - 768) * batch + b]);
-        else v = dout[b];
-        s += (double)v;
+    const uint32_t n8 = batch / 8;
+    float s = 0.f, comp = 0.f;
+    auto add = [&](float v) {
+        const float y = v - comp;
+        const float t = s + y;
+        comp = (t - s) - y;
+        s = t;
+    };
+    const float4* d4 = reinterpret_cast<const float4*>(dout);
+    if (r < 768) {
+        const __nv_bfloat16* dz = r < 256 ? dz2 : (r < 512 ? dz3 : dz4);
+        const uint4* row = reinterpret_cast<const uint4*>(dz + (size_t)(r % 256) * batch);
+        for (uint32_t i = threadIdx.x; i < n8; i += blockDim.x) {
+            const uint4 u = row[i];
+            add(((bf16_lo(u.x) + bf16_hi(u.x)) + (bf16_lo(u.y) + bf16_hi(u.y))) +
+                ((bf16_lo(u.z) + bf16_hi(u.z)) + (bf16_lo(u.w) + bf16_hi(u.w))));
+        }
+    } else if (r < 1024) {
+        const uint4* row = reinterpret_cast<const uint4*>(ht4 + (size_t)(r - 768) * batch);
+        for (uint32_t i = threadIdx.x; i < n8; i += blockDim.x) {
+            const uint4 u = row[i];
+            const float4 a = d4[2 * i], b = d4[2 * i + 1];
+            float p = a.x * bf16_lo(u.x);
+            p = fmaf(a.y, bf16_hi(u.x), p);
+            p = fmaf(a.z, bf16_lo(u.y), p);
+            p = fmaf(a.w, bf16_hi(u.y), p);
+            p = fmaf(b.x, bf16_lo(u.z), p);
+            p = fmaf(b.y, bf16_hi(u.z), p);
+            p = fmaf(b.z, bf16_lo(u.w), p);
+            p = fmaf(b.w, bf16_hi(u.w), p);
+            add(p);
+        }
+    } else {
+        for (uint32_t i = threadIdx.x; i < n8; i += blockDim.x) {
+            const float4 a = d4[2 * i], b = d4[2 * i + 1];
+            add(((a.x + a.y) + (a.z + a.w)) + ((b.x + b.y) + (b.z + b.w)));
+        }
     }
-    __shared__ double red[32];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    double t = (double)s - (double)comp;
+    __shared__ double red[8];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-        if (r < 768) grad[OFF_B1 + 256 + r] = (float)t;        // b2, b3, b4
-        else if (r < 1024) grad[OFF_W5 + (r - 768)] = (float)t;
-        else grad[OFF_B5] = (float)t;
+        double tot = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+        if (r < 768) grad[OFF_B1 + 256 + r] = (float)tot;        // b2, b3, b4
+        else if (r < 1024) grad[OFF_W5 + (r - 768)] = (float)tot;
+        else grad[OFF_B5] = (float)tot;
     }
 }
 
@@ -870,6 +908,13 @@ sas_status sas_create_surrogate(const sas_surrogate_box* box, uint64_t seed, voi
     for (float v : s->bucket_sp) tab.push_back(v);
     push(px);
     push(pw);
+    // (x^2, w) pairs of every bucket for one 8-byte load per radial term
+    if (tab.size() % 2) tab.push_back(0.f);
+    const size_t off_x2w = tab.size();
+    for (size_t i = 0; i < px.size(); ++i) {
+        tab.push_back((float)(px[i] * px[i]));
+        tab.push_back((float)pw[i]);
+    }
     ce = cudaMalloc(&s->d_tab, tab.size() * sizeof(float));
     if (ce == cudaSuccess) ce = cudaMemcpy(s->d_tab, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (ce != cudaSuccess) return bail(set_cuda_error(ce, "surrogate tables"));
@@ -881,6 +926,7 @@ sas_status sas_create_surrogate(const sas_surrogate_box* box, uint64_t seed, voi
     s->tabs.bucket_sp = t + 2 * b.n_gamma + 2 * b.n_psi;
     s->tabs.poly_x = s->tabs.bucket_sp + b.n_buckets;
     s->tabs.poly_w = s->tabs.poly_x + (size_t)b.n_buckets * b.n_poly;
+    s->tabs.poly_x2w = reinterpret_cast<const float2*>(t + off_x2w);
     sur::init_kernel<<<256, 256, 0, s->stream>>>(s->d_p, seed);
     sas_status st = publish(s);
     if (st != SAS_OK) return bail(st);

@@ -125,6 +125,7 @@ struct Tables {
     const float* bucket_sp; // [n_buckets] sigma_poly of each bucket
     const float* poly_x;    // [n_buckets][n_poly] Schulz nodes r_i / R
     const float* poly_w;    // [n_buckets][n_poly] w_i x_i^4 / sum(w x^4)
+    const float2* poly_x2w; // [n_buckets][n_poly] (x_i^2, w_i x_i^4 / sum(w x^4))
 };
 
 // Normalised averaged cylinder form factor P = <|F|^2> / (drho^2 <V^2>) at
@@ -140,6 +141,22 @@ __device__ __forceinline__ double exact_pbar_warp(const Box& b, const Tables& t,
     const float gmax = fminf(3.0f * r.so, 3.14159265f);
     const float inv2s2 = 0.5f / (r.so * r.so);
     const float q2 = r.qpar * r.qpar + r.qperp * r.qperp;
+    const float R2 = r.R * r.R;
+    // the warp shares the sample: |Q x c| <= |Q| bounds every argument, so
+    // the (ascending) radius nodes split once into the tiers of 2 J1(x)/x
+    const float qm = q2 * R2;
+    auto tier_end = [&](int lo, float smax) {
+        int hi = b.n_poly;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (px[mid] * px[mid] * qm <= smax) lo = mid + 1;
+            else hi = mid;
+        }
+        return lo;
+    };
+    const int t4 = tier_end(0, SAS_J1R_SMAX);
+    const int t6 = tier_end(t4, SAS_J1V_SMAX);
+    const int t8 = tier_end(t6, SAS_J1P_SMAX);
     const int no = b.n_gamma * b.n_psi;
     Kahan<float> num, den;
     for (int o = lane; o < no; o += 32) {
@@ -147,27 +164,48 @@ __device__ __forceinline__ double exact_pbar_warp(const Box& b, const Tables& t,
         const float g = 0.5f * gmax * (t.gl_g[i] + 1.0f);
         const float psi = 3.14159265f * (t.gl_p[k] + 1.0f);
         float sg, cg, sp, cp;
-        sas_sincosf(g, sg, cg);
-        sas_sincosf(psi, sp, cp);
+        __sincosf(g, &sg, &cg);
+        __sincosf(psi, &sp, &cp);
         const float wo = t.glw_g[i] * sg * __expf(-g * g * inv2s2) * t.glw_p[k];
         const float qc = r.qperp * sg * cp + r.qpar * cg;
-        const float qab = sqrtf(fmaxf(q2 - qc * qc, 0.0f));
+        const float qab2 = fmaxf(q2 - qc * qc, 0.0f);
         const float y = fabsf(qc) * 0.5f * r.L;
-        const float sn = sas_sinc(y, __frcp_rn(y));
-        const float qabR = qab * r.R;
-        const float qabR2 = qabR * qabR;
+        const float sn = M<float>::sinc(y, __fdividef(1.0f, y));
+        const float qabR2 = qab2 * R2;
+        const float2* xw = t.poly_x2w + bk * b.n_poly;
         float inner = 0.f;
-        for (int j = 0; j < b.n_poly; ++j) {
-            const float x = px[j];
-            const float sx = qabR2 * (x * x);
-            float a;
-            if (sx <= SAS_J1P_SMAX) {
-                a = sas_cyl_a_s(sx);
-            } else {
-                const float xx = qabR * x;
-                a = sas_cyl_a_large(xx, __frcp_rn(xx), rsqrtf(xx));
+#pragma unroll 4
+        for (int j = 0; j < t4; ++j) {
+            const float2 v = xw[j];
+            const float a = sas_cyl_a_r(qabR2 * v.x);
+            inner = fmaf(v.y, a * a, inner);
+        }
+#pragma unroll 4
+        for (int j = t4; j < t6; ++j) {
+            const float2 v = xw[j];
+            const float a = sas_cyl_a_v(qabR2 * v.x);
+            inner = fmaf(v.y, a * a, inner);
+        }
+#pragma unroll 2
+        for (int j = t6; j < t8; ++j) {
+            const float2 v = xw[j];
+            const float a = sas_cyl_a_s(qabR2 * v.x);
+            inner = fmaf(v.y, a * a, inner);
+        }
+        if (t8 < b.n_poly) {
+            const float qabR = M<float>::sqrt_(qabR2);
+            for (int j = t8; j < b.n_poly; ++j) {
+                const float x = px[j];
+                const float sx = qabR2 * (x * x);
+                float a;
+                if (sx <= SAS_J1P_SMAX) {
+                    a = sas_cyl_a_s(sx);
+                } else {
+                    const float xx = qabR * x;
+                    a = sas_cyl_a_large(xx, __frcp_rn(xx), rsqrtf(xx));
+                }
+                inner = fmaf(pw[j], a * a, inner);
             }
-            inner = fmaf(pw[j], a * a, inner);
         }
         num.add(wo * sn * sn * inner);
         den.add(wo);
