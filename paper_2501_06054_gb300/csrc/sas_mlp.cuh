@@ -29,7 +29,9 @@ constexpr int H = 256;          // hidden width
 constexpr int KIN = 64;         // padded input width (one 64-element K block)
 constexpr int NF = 5;           // features used
 constexpr int TILE = 128;       // rows per tile (MMA M)
-constexpr int THREADS = 256;
+constexpr int THREADS = 512;    // tile kernels: 16 warps, a quarter of the columns each
+constexpr int NGROUP = THREADS / TILE;   // column groups (warps w, w + 4, ... share TMEM lanes)
+constexpr int GCOLS = H / NGROUP;        // accumulator columns per thread
 constexpr int NPARAM_W1 = H * KIN;
 constexpr int NPARAM_W = H * H;
 // flat FP32 parameter layout: W1 [256][64] | W2 | W3 | W4 [256][256] |
@@ -50,8 +52,8 @@ constexpr uint32_t SM_A = 16384;           // 128 x 256 bf16 activations (64 KB)
 constexpr uint32_t SM_B = 81920;           // 256 x 256 bf16 weights (128 KB)
 constexpr uint32_t SM_BIAS = 212992;       // 4 x 256 f32 biases
 constexpr uint32_t SM_W5 = SM_BIAS + 4096; // 256 f32
-constexpr uint32_t SM_ROW = SM_W5 + 1024;  // 2 x 128 f32 per-row scratch
-constexpr uint32_t SM_BAR = SM_ROW + 1024; // mbarriers + TMEM address
+constexpr uint32_t SM_ROW = SM_W5 + 1024;  // NGROUP x 128 f32 per-row scratch
+constexpr uint32_t SM_BAR = SM_ROW + 4 * TILE * NGROUP; // mbarriers + TMEM address
 constexpr uint32_t SM_TOTAL = SM_BAR + 64;
 constexpr size_t SMEM_BYTES = SM_TOTAL + 1024;   // + alignment slack
 
@@ -175,7 +177,7 @@ __device__ __forceinline__ void publish_smem()
 }
 
 __device__ __forceinline__ int row_of_thread() { return 32 * ((threadIdx.x >> 5) & 3) + (threadIdx.x & 31); }
-__device__ __forceinline__ int half_of_thread() { return (threadIdx.x >> 5) >> 2; }
+__device__ __forceinline__ int group_of_thread() { return (threadIdx.x >> 5) >> 2; }
 
 __device__ __forceinline__ uint32_t tmem_addr(const Ctx& c, int col)
 {
@@ -202,10 +204,10 @@ __device__ __forceinline__ void st_row8(unsigned char* buf, int m, int col, cons
 __device__ __forceinline__ float epi_hidden(Ctx& c, const float* bias, __nv_bfloat16* zt, __nv_bfloat16* ht,
                                             size_t ld, size_t col_g, bool row_valid, const float* w5)
 {
-    const int m = row_of_thread(), h = half_of_thread();
+    const int m = row_of_thread(), h = group_of_thread();
     float dot = 0.f;
-    for (int ch = 0; ch < 4; ++ch) {
-        const int col0 = 128 * h + 32 * ch;
+    for (int ch = 0; ch < GCOLS / 32; ++ch) {
+        const int col0 = GCOLS * h + 32 * ch;
         float v[32];
         tc::tmem_ld32(tmem_addr(c, col0), v);
 #pragma unroll

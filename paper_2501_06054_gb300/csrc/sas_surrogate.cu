@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_fwd_kernel(const FwdParams P, 
     stage_params(c, P.params);
     load_weights(c, &maps.w1, 1);
     __syncthreads();
-    const int m = row_of_thread(), h = half_of_thread();
+    const int m = row_of_thread(), h = group_of_thread();
     float* s_row = reinterpret_cast<float*>(c.sm + SM_ROW);
     const uint32_t ntiles = (P.batch + TILE - 1) / TILE;
     for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -133,7 +133,12 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_fwd_kernel(const FwdParams P, 
         const float dot = forward_tile<TRAIN>(c, maps, P.zt, P.ht, P.batch, i, valid);
         s_row[h * TILE + m] = dot;
         __syncthreads();
-        if (h == 0 && valid) P.out[i] = P.params[OFF_B5] + s_row[m] + s_row[TILE + m];
+        if (h == 0 && valid) {
+            float o = P.params[OFF_B5];
+#pragma unroll
+            for (int g = 0; g < NGROUP; ++g) o += s_row[g * TILE + m];
+            P.out[i] = o;
+        }
         __syncthreads();
     }
     if (threadIdx.x == 0 && !tc::mbar_wait(c.bar_tma, c.ph_tma, WAIT_NS)) atomicExch(P.err, 3);
@@ -164,7 +169,7 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_bwd_kernel(const BwdParams P, 
     stage_params(c, P.params);
     load_weights(c, &maps.wt[2], 4);
     __syncthreads();
-    const int m = row_of_thread(), h = half_of_thread();
+    const int m = row_of_thread(), h = group_of_thread();
     float* s_row = reinterpret_cast<float*>(c.sm + SM_ROW);
     const float* w5 = reinterpret_cast<const float*>(c.sm + SM_W5);
     const size_t ld = P.batch;
@@ -184,8 +189,8 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_bwd_kernel(const BwdParams P, 
         __syncthreads();
         const float dout = s_row[m];
         // dZ4 = dout w5 SiLU'(z4)
-        for (int ch = 0; ch < 4; ++ch) {
-            const int col0 = 128 * h + 32 * ch;
+        for (int ch = 0; ch < GCOLS / 32; ++ch) {
+            const int col0 = GCOLS * h + 32 * ch;
             float v[32];
             // all loads of the chunk first (they may not pass the stores below)
 #pragma unroll
@@ -206,8 +211,8 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_bwd_kernel(const BwdParams P, 
             wait_layer(c);
             if (l > 1) load_weights(c, &maps.wt[l - 2], 4);
             else load_weights(c, &maps.wt[2], 4);   // next tile starts again at W4^T
-            for (int ch = 0; ch < 4; ++ch) {
-                const int col0 = 128 * h + 32 * ch;
+            for (int ch = 0; ch < GCOLS / 32; ++ch) {
+                const int col0 = GCOLS * h + 32 * ch;
                 float z[32], v[32];
 #pragma unroll
                 for (int j = 0; j < 32; ++j)
@@ -252,7 +257,9 @@ struct WgParams {
     int* err;
 };
 
-__global__ void __launch_bounds__(THREADS, 1) wgrad_kernel(const WgParams P, const __grid_constant__ WgMaps maps)
+constexpr int WG_THREADS = 256;
+
+__global__ void __launch_bounds__(WG_THREADS, 1) wgrad_kernel(const WgParams P, const __grid_constant__ WgMaps maps)
 {
     extern __shared__ unsigned char raw_sm[];
     unsigned char* sm = aligned_base(raw_sm);
@@ -320,7 +327,7 @@ __global__ void __launch_bounds__(THREADS, 1) wgrad_kernel(const WgParams P, con
     if (nkb > 0) {
         if (!tc::mbar_wait(done, 0, WAIT_NS)) atomicExch(P.err, 6);
         tc::fence_after_sync();
-        const int m = row_of_thread(), h = half_of_thread();
+        const int m = row_of_thread(), h = (int)(threadIdx.x >> 7);   // 256 threads: two column halves
         const int ncols = N / 2;                 // columns per thread
         const int off = layer == 0 ? OFF_W1 : (layer == 1 ? OFF_W2 : (layer == 2 ? OFF_W3 : OFF_W4));
         float* g = P.grad + off + (size_t)(mh * 128 + m) * N;
@@ -648,7 +655,7 @@ sas_status enqueue_step(sas_surrogate* s, const sur::Raw* raw, const float* y, u
     W.kb_per = (W.kb_total + splits - 1) / splits;
     splits = (W.kb_total + W.kb_per - 1) / W.kb_per;
     W.err = s->d_err;
-    sur::wgrad_kernel<<<dim3(splits, 2, 4), THREADS, sur::WG_SMEM, st>>>(W, s->wg);
+    sur::wgrad_kernel<<<dim3(splits, 2, 4), sur::WG_THREADS, sur::WG_SMEM, st>>>(W, s->wg);
     sur::rowsum_kernel<<<1025, 256, 0, st>>>(s->d_g, s->d_dzt[1], s->d_dzt[2], s->d_dzt[3], s->d_ht[3],
                                              s->d_dout, B);
     if (adam) {
