@@ -922,6 +922,13 @@ sas_status sas_create_surrogate(const sas_surrogate_box* box, uint64_t seed, voi
         tab.push_back((float)(px[i] * px[i]));
         tab.push_back((float)pw[i]);
     }
+    // (cos, sin) of the psi nodes
+    const size_t off_psi = tab.size();
+    for (int k = 0; k < b.n_psi; ++k) {
+        const double psi = M_PI * (xp[k] + 1.0);
+        tab.push_back((float)std::cos(psi));
+        tab.push_back((float)std::sin(psi));
+    }
     ce = cudaMalloc(&s->d_tab, tab.size() * sizeof(float));
     if (ce == cudaSuccess) ce = cudaMemcpy(s->d_tab, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (ce != cudaSuccess) return bail(set_cuda_error(ce, "surrogate tables"));
@@ -934,6 +941,7 @@ sas_status sas_create_surrogate(const sas_surrogate_box* box, uint64_t seed, voi
     s->tabs.poly_x = s->tabs.bucket_sp + b.n_buckets;
     s->tabs.poly_w = s->tabs.poly_x + (size_t)b.n_buckets * b.n_poly;
     s->tabs.poly_x2w = reinterpret_cast<const float2*>(t + off_x2w);
+    s->tabs.psi_cs = reinterpret_cast<const float2*>(t + off_psi);
     sur::init_kernel<<<256, 256, 0, s->stream>>>(s->d_p, seed);
     sas_status st = publish(s);
     if (st != SAS_OK) return bail(st);

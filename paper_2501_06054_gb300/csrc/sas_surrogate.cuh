@@ -126,6 +126,7 @@ struct Tables {
     const float* poly_x;    // [n_buckets][n_poly] Schulz nodes r_i / R
     const float* poly_w;    // [n_buckets][n_poly] w_i x_i^4 / sum(w x^4)
     const float2* poly_x2w; // [n_buckets][n_poly] (x_i^2, w_i x_i^4 / sum(w x^4))
+    const float2* psi_cs;   // [n_psi] (cos, sin) of the psi nodes pi (gl_p + 1)
 };
 
 // Normalised averaged cylinder form factor P = <|F|^2> / (drho^2 <V^2>) at
@@ -159,13 +160,13 @@ __device__ __forceinline__ double exact_pbar_warp(const Box& b, const Tables& t,
     const int t8 = tier_end(t6, SAS_J1P_SMAX);
     const int no = b.n_gamma * b.n_psi;
     Kahan<float> num, den;
+    int i = lane / b.n_psi, k = lane - i * b.n_psi;    // node o = i n_psi + k, stepped by 32
     for (int o = lane; o < no; o += 32) {
-        const int i = o / b.n_psi, k = o - i * b.n_psi;
         const float g = 0.5f * gmax * (t.gl_g[i] + 1.0f);
-        const float psi = 3.14159265f * (t.gl_p[k] + 1.0f);
-        float sg, cg, sp, cp;
+        float sg, cg;
         __sincosf(g, &sg, &cg);
-        __sincosf(psi, &sp, &cp);
+        const float2 pcs = t.psi_cs[k];
+        const float cp = pcs.x, sp = pcs.y;
         const float wo = t.glw_g[i] * sg * __expf(-g * g * inv2s2) * t.glw_p[k];
         const float qc = r.qperp * sg * cp + r.qpar * cg;
         const float qab2 = fmaxf(q2 - qc * qc, 0.0f);
@@ -209,6 +210,7 @@ __device__ __forceinline__ double exact_pbar_warp(const Box& b, const Tables& t,
         }
         num.add(wo * sn * sn * inner);
         den.add(wo);
+        for (k += 32; k >= b.n_psi; k -= b.n_psi) ++i;
     }
     double n = (double)num.s - (double)num.c, d = (double)den.s - (double)den.c;
 #pragma unroll
