@@ -375,6 +375,7 @@ void oracle_event_axis(int64_t mode, double theta0, double phi0, uint32_t xa, ui
     } else if (mode == 2) {
         double th = PI * u01(xa);
         ct = cos(th); st = sin(th);
+        if (SAS_MUT == 16) { ct = 1.0 - 2.0 * u01(xa); st = sqrt(fmax(0.0, 1.0 - ct * ct)); }
     } else {
         ct = cos(theta0); st = sin(theta0);
         c[0] = st * cos(phi0); c[1] = st * sin(phi0); c[2] = ct;
@@ -393,8 +394,8 @@ void oracle_frame(double theta, double phi, double psi, double f[9])
     double sq = sin(psi), cq = cos(psi);
     double et[3] = {ct * cp, ct * sp, -st}, ep[3] = {-sp, cp, 0.0};
     for (int k = 0; k < 3; ++k) {
-        f[k] = cq * et[k] + sq * ep[k];
-        f[3 + k] = -sq * et[k] + cq * ep[k];
+        f[k] = cq * et[k] + (SAS_MUT == 18 ? -sq : sq) * ep[k];
+        f[3 + k] = (SAS_MUT == 18 ? sq : -sq) * et[k] + cq * ep[k];
     }
     f[6] = st * cp; f[7] = st * sp; f[8] = ct;
 }
@@ -631,7 +632,7 @@ static void att_setup(const oracle_instrument *in, const oracle_model *m, oracle
     for (int i = 0; i < n; ++i) {
         double c = 0.0;
         for (int j = 0; j < n; ++j) c += a->mu[j] * cos(PI * i * (j + 0.5) / n);
-        a->c[i] = (i == 0 ? 1.0 : 2.0) * c / n;
+        a->c[i] = (i == 0 && SAS_MUT != 17 ? 1.0 : 2.0) * c / n;
     }
 }
 

@@ -32,6 +32,11 @@ MUTATIONS = {
          "test_attenuation_oracle.py"),
     15: ("total cross section without the |Q| of dOmega = Q dQ dphi / k^2", "sphere_large_k",
          "test_attenuation_oracle.py"),
+    16: ("per-event axis uniform on the sphere where the angles are asked for", "event_axis_definitions",
+         "test_event_oracle.py"),
+    17: ("Chebyshev interpolant with the constant term not halved", "chebyshev_table",
+         "test_attenuation_oracle.py"),
+    18: ("particle frame rotated by -psi instead of psi", "frame_definition", "test_triaxial_oracle.py"),
 }
 
 
