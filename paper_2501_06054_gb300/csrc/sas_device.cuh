@@ -299,25 +299,25 @@ __device__ __forceinline__ T avg_cylinder(const T qv[3], const T* __restrict__ p
             const T y = fabs(qc) * half_len;
             const T sn = M<T>::sinc(y, M<T>::rcp(y));
             float inner = 0.f;
-#pragma unroll 4
+#pragma unroll 8
             for (int i = 0; i < t4; ++i) {
                 const float2 rc = *reinterpret_cast<const float2*>(poly + 8 * i);   // (r^2, c)
                 const float a = sas_cyl_a_r(qab2 * rc.x);
                 inner = fma(rc.y, a * a, inner);
             }
-#pragma unroll 4
+#pragma unroll 8
             for (int i = t4; i < t6; ++i) {
                 const float2 rc = *reinterpret_cast<const float2*>(poly + 8 * i);
                 const float a = sas_cyl_a_v(qab2 * rc.x);
                 inner = fma(rc.y, a * a, inner);
             }
-#pragma unroll 2
+#pragma unroll 4
             for (int i = t6; i < t8; ++i) {
                 const float2 rc = *reinterpret_cast<const float2*>(poly + 8 * i);
                 const float a = sas_cyl_a_s(qab2 * rc.x);
                 inner = fma(rc.y, a * a, inner);
             }
-#pragma unroll 2
+#pragma unroll 4
             for (int i = t8; i < t12; ++i) {
                 const float2 rc = *reinterpret_cast<const float2*>(poly + 8 * i);
                 const float a = sas_cyl_a_s3(qab2 * rc.x);
@@ -375,6 +375,8 @@ __device__ __forceinline__ T avg_cylinder_tab(const T qv[3], const T* __restrict
 {
     const T* __restrict__ tab = poly + SAS_POLY_STRIDE * mc.n_rad;
     Kahan<T> k;
+    constexpr int kUnroll = sizeof(T) == sizeof(float) ? 4 : 1;   // FP32: four orientation nodes in flight
+#pragma unroll kUnroll
     for (int o = 0; o < no; ++o) {
         const T* c = orient + 4 * o;
         const T qc = fma(qv[0], c[0], fma(qv[1], c[1], qv[2] * c[2]));
