@@ -186,7 +186,7 @@ def secondary(stream, info):
     box = W.surrogate_box(n_fourier=6)
     t0 = time.perf_counter()
     sur = sas.sas_create_surrogate(box, seed=1, stream=stream)
-    n_train, steps, batch, lr = 50_000_000, 40_000, 65536, 2e-3
+    n_train, steps, batch, lr = 50_000_000, 60_000, 65536, 2e-3
     gen_ms = _events_ms(lambda: sas.sas_surrogate_generate(sur, n_train, 1), stream)
     train_ms = _events_ms(lambda: sas.sas_surrogate_train(sur, steps, batch, lr, steps), stream)
     sas.sas_attach_surrogate(e.h, sur)
@@ -502,7 +502,7 @@ def main():
     ap.add_argument("--workload", default="core_shell",
                     choices=["core_shell", "cylinder", "cylinder_surrogate"],
                     help="core_shell: the headline step; the others time one workload alone")
-    ap.add_argument("--train-steps", type=int, default=40000)
+    ap.add_argument("--train-steps", type=int, default=60000)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
