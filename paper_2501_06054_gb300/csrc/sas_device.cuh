@@ -1,9 +1,11 @@
 // Device building blocks of the SANS trace: Philox4x32-10, the neutron
-// history geometry, the four form-factor models with their polydispersity
-// and orientation quadratures, and the Percus-Yevick structure factor.
-// Templated on the arithmetic type: float (FP32 trace, own special
-// functions from sas_math.cuh) or double (FP64 trace, CUDA's double
-// precision math functions).
+// history geometry, the six form-factor models with their polydispersity
+// and orientation quadratures (or per-event draws), the Percus-Yevick
+// structure factor and the self-attenuation table. Templated on the
+// arithmetic type: float (FP32 trace: sin, cos and sine from the
+// special-function unit where the tolerances allow, own polynomial forms of
+// 2 J1(x)/x and of the small-argument series) or double (FP64 trace, CUDA's
+// double precision math functions).
 #pragma once
 
 #include <stdint.h>
@@ -257,9 +259,6 @@ struct Kahan {
     }
 };
 
-// FP32: 2 J1(x)/x from s = x^2 = |Q x c|^2 r^2 by the product form for
-// x <= 8 (no square root per term); larger x (tails of broad size
-// distributions) take the modulus-phase form. FP64: the C library's j1.
 // Number of the ascending radius nodes whose r^2 qm stays <= smax (binary
 // search on the first value of each poly row).
 __device__ __forceinline__ int cyl_tier_end(const float* __restrict__ poly, int lo, int np, float qm, float smax)
@@ -273,6 +272,10 @@ __device__ __forceinline__ int cyl_tier_end(const float* __restrict__ poly, int 
     return lo;
 }
 
+// Orientation and polydispersity average of the cylinder. FP32: 2 J1(x)/x
+// from s = x^2 = |Q x c|^2 r^2 without a square root per term, by the
+// cheapest polynomial form valid for the node's tier; the modulus-phase form
+// beyond x = 12 (tails of broad size distributions). FP64: CUDA's j1.
 template <typename T>
 __device__ __forceinline__ T avg_cylinder(const T qv[3], const T* __restrict__ poly, int np,
                                           const T* __restrict__ orient, int no, T half_len)
