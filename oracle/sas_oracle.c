@@ -43,6 +43,8 @@
 
 #define PI 3.14159265358979323846
 
+static void gl_nodes(int n, double *x, double *w);
+
 /* Planted mistakes for the pin tests' mutation check (tests/test_mutations.py):
  * the default build compiles none of them (SAS_MUT = 0). */
 #ifndef SAS_MUT
@@ -115,6 +117,9 @@ typedef struct {
     /* 1: the beam inside the sample is attenuated by the particles' own
      * scattering as well, mu(lambda) = mu + Sigma_s(lambda) */
     int64_t self_att;
+    /* capped cylinder and barbell (kinds 6, 7): Gauss-Legendre nodes of the
+     * integral over each spherical end cap (1 to 64) */
+    int64_t n_cap;
 } oracle_model;
 
 /* --------------------------------------------------------- model pieces */
@@ -288,6 +293,63 @@ double oracle_dsigma(const oracle_model *m, const double q[3])
             }
             sum += m->orient_w[o] * inner;
         }
+    } else if (m->kind == 6 || m->kind == 7) {
+        /* capped cylinder (6) and barbell (7): a cylinder of radius r and
+         * length L along the axis with two spherical end caps of radius R >= r.
+         * The caps are the parts of the spheres beyond the end faces z = +-L/2;
+         * the sphere centres sit at +-(L/2 -+ h), h = sqrt(R^2 - r^2), inside
+         * the cylinder for the capped cylinder and outside for the barbell,
+         * so each cap is H = R -+ h high. Eq. 1 summed over slices normal to
+         * the axis, each a disk of radius rho(z) with amplitude
+         * pi rho^2 a(Q_AB rho) e^(i Q_C z), a(x) = 2 J1(x)/x; on a cap the
+         * slice at depth R u below its tip has rho^2 = R^2 u (2 - u):
+         *   F = drho [pi r^2 L sinc(Q_C L / 2) a(Q_AB r)
+         *      + 2 pi R^3 int_0^(H/R) cos(Q_C (L/2 + H - R u)) u (2 - u) a(Q_AB R sqrt(u (2 - u))) du],
+         * the cap integral by an n_cap point Gauss-Legendre rule. (u = 1 - t
+         * with t the slice's height above the sphere centre in units of R;
+         * written in u the rule has no cancellation for R >> r.) The
+         * capped cylinder's H = R - h is formed as r^2 / (R + h). One
+         * polydisperse factor s = r_i / radius scales r, R and L alike. */
+        double drho = m->sld - m->sld_solvent;
+        double r0 = m->radius, R0 = m->radius_polar, L0 = m->length;
+        double h0 = sqrt(fmax(R0 * R0 - r0 * r0, 0.0));
+        double H0 = (m->kind == 6) != (SAS_MUT == 19) ? r0 * r0 / (R0 + h0) : R0 + h0;
+        int nc = (int)m->n_cap;
+        double gx[64], gw[64], uj[64], wj[64];
+        gl_nodes(nc, gx, gw);
+        for (int j = 0; j < nc; ++j) {
+            uj[j] = 0.5 * (H0 / R0) * (1.0 + gx[j]);
+            wj[j] = 0.5 * (H0 / R0) * gw[j];
+        }
+        /* int_0^(H/R) u (2 - u) du = (H/R)^2 (1 - H / 3R) */
+        double v0 = PI * r0 * r0 * L0 + 2.0 * PI * R0 * H0 * H0 * (1.0 - H0 / (3.0 * R0));
+        for (int64_t i = 0; i < np; ++i) {
+            double sc = m->poly_r[i] / r0;
+            vmean += m->poly_w[i] * v0 * sc * sc * sc;
+        }
+        for (int64_t o = 0; o < m->n_orient; ++o) {
+            const double *c = m->orient_c + 3 * o;
+            double qc = q[0] * c[0] + q[1] * c[1] + q[2] * c[2];
+            double x0 = q[1] * c[2] - q[2] * c[1];
+            double x1 = q[2] * c[0] - q[0] * c[2];
+            double x2 = q[0] * c[1] - q[1] * c[0];
+            double qab = sqrt(x0 * x0 + x1 * x1 + x2 * x2);
+            double inner = 0.0;
+            for (int64_t i = 0; i < np; ++i) {
+                double sc = m->poly_r[i] / r0;
+                double r = sc * r0, R = sc * R0, L = sc * L0, H = sc * H0;
+                double F = PI * r * r * L * oracle_sinc(0.5 * qc * L) * oracle_cyl_a(qab * r);
+                double cap = 0.0;
+                for (int j = 0; j < nc; ++j) {
+                    double v = uj[j] * (2.0 - uj[j]);
+                    cap += wj[j] * cos(qc * (0.5 * L + H - R * uj[j])) * (SAS_MUT == 20 ? 1.0 : v)
+                         * oracle_cyl_a(qab * (SAS_MUT == 21 ? R : R * sqrt(v)));
+                }
+                F = drho * (F + 2.0 * PI * R * R * R * cap);
+                inner += m->poly_w[i] * F * F;
+            }
+            sum += m->orient_w[o] * inner;
+        }
     } else {                         /* ellipsoid of revolution: equatorial radius polydisperse */
         double drho = m->sld - m->sld_solvent;
         double rp = m->radius_polar;
@@ -423,6 +485,12 @@ static double model_volume(const oracle_model *m, double r)
         double s = r / m->radius;
         return (m->kind == 4 ? 4.0 / 3.0 * PI : 8.0) * m->radius * m->radius_b * m->radius_polar * s * s * s;
     }
+    if (m->kind == 6 || m->kind == 7) {
+        double s = r / m->radius, R = m->radius_polar, r0 = m->radius;
+        double h = sqrt(fmax(R * R - r0 * r0, 0.0));
+        double H = m->kind == 6 ? r0 * r0 / (R + h) : R + h;
+        return (PI * r0 * r0 * m->length + 2.0 * PI * R * H * H * (1.0 - H / (3.0 * R))) * s * s * s;
+    }
     return 4.0 / 3.0 * PI * m->radius_polar * r * r;
 }
 
@@ -530,6 +598,13 @@ double oracle_model_extent(const oracle_model *m)
     case 4: {
         double f = r / m->radius;
         return 2.0 * f * fmax(m->radius, fmax(m->radius_b, m->radius_polar));
+    }
+    case 6:
+    case 7: {   /* tip to tip along the axis, L + 2H, or the caps' diameter */
+        double f = r / m->radius, R = m->radius_polar, r0 = m->radius;
+        double h = sqrt(fmax(R * R - r0 * r0, 0.0));
+        double H = m->kind == 6 ? r0 * r0 / (R + h) : R + h;
+        return f * fmax(m->length + 2.0 * H, 2.0 * R);
     }
     default: {
         double f = r / m->radius;

@@ -36,9 +36,11 @@ import numpy as np
 
 SPHERE, CORE_SHELL, CYLINDER, ELLIPSOID = 0, 1, 2, 3
 TRIAXIAL_ELLIPSOID, PARALLELEPIPED = 4, 5        # no symmetry axis: sizes along A, B, C
+CAPPED_CYLINDER, BARBELL = 6, 7                  # cylinder with spherical end caps (radius_polar)
 MODEL_NAMES = {SPHERE: "sphere", CORE_SHELL: "core_shell", CYLINDER: "cylinder",
                ELLIPSOID: "ellipsoid", TRIAXIAL_ELLIPSOID: "triaxial_ellipsoid",
-               PARALLELEPIPED: "parallelepiped"}
+               PARALLELEPIPED: "parallelepiped", CAPPED_CYLINDER: "capped_cylinder",
+               BARBELL: "barbell"}
 SQ_NONE, SQ_HARD_SPHERE_PY = 0, 1
 FP32, FP64 = 0, 1
 QUADRATURE, PER_EVENT = 0, 1              # sampling: averages over nodes / one draw per history
@@ -80,8 +82,9 @@ class Model:
     radius: float = 50.0            # sphere R, core radius, cylinder R, ellipsoid equatorial R,
                                     # 3-axis models: semi-axis / half-edge along A
     thickness: float = 0.0          # core-shell shell thickness
-    length: float = 0.0             # cylinder length
-    radius_polar: float = 0.0       # ellipsoid polar radius (along the axis); 3-axis models: along C
+    length: float = 0.0             # cylinder length (capped cylinder, barbell: between the end faces)
+    radius_polar: float = 0.0       # ellipsoid polar radius (along the axis); 3-axis models: along C;
+                                    # capped cylinder, barbell: radius of the end caps' spheres (>= radius)
     sld: float = 2.0e-6             # particle (core) SLD
     sld_shell: float = 0.0
     sld_solvent: float = 0.0
@@ -99,6 +102,7 @@ class Model:
     axis_psi: float = 0.0           # rad, rotation of the particle frame about its C axis
     n_rot: int = 1                  # quadrature nodes in psi (uniform rotations / angles)
     self_attenuation: int = 0       # 1: attenuation mu + Sigma_s(lambda), the model's own total scattering
+    n_cap: int = 16                 # capped cylinder, barbell: Gauss-Legendre nodes over each end cap
 
     def as_dict(self):
         return asdict(self)

@@ -37,6 +37,10 @@ MUTATIONS = {
     17: ("Chebyshev interpolant with the constant term not halved", "chebyshev_table",
          "test_attenuation_oracle.py"),
     18: ("particle frame rotated by -psi instead of psi", "frame_definition", "test_triaxial_oracle.py"),
+    19: ("capped cylinder with the sphere centres outside the cylinder", "forward_scattering",
+         "test_capped_oracle.py"),
+    20: ("cap slices without their area factor rho^2 / R^2", "forward_scattering", "test_capped_oracle.py"),
+    21: ("cap slices with the sphere's radius instead of the slice's", "eq1_shells", "test_capped_oracle.py"),
 }
 
 
