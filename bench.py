@@ -305,7 +305,40 @@ def secondary(stream, info):
     sas.sas_destroy_surrogate(sur)
     out["per_event"] = per_event(stream)
     out["self_attenuation"] = self_attenuation(stream)
+    out["capped"] = capped_models(stream)
     return out
+
+
+CAPPED_DESC = {"capped_cylinder": "r=20, caps R=25, L=200 A, Schulz 0.1 (10 nodes), Gaussian axis spread 15 deg "
+                                  "(16x16 nodes), 16 slices per cap, 128x128, FP32",
+               "barbell": "r=10, bells R=25, L=100 A, Schulz 0.1 (10 nodes), axis uniform on the sphere (16x16 "
+                          "nodes), 16 slices per bell, 128x128, FP32"}
+
+
+def capped_models(stream):
+    """Capped cylinder and barbell (the cylinder's amplitude plus n_cap disk
+    slices per cap, Eq. 1): histories/s and slice terms/s (orientation nodes
+    x radius nodes x (n_cap + 1) per history)."""
+    import paper_2501_06054_gb300 as sas
+    from paper_2501_06054_gb300 import flops as F
+    info = sas.sas_device_info()
+    peak = F.fp32_peak_tflops(info["sm_count"], 2070.0)
+    res = {}
+    for cfg in (W.capped_cylinder_config(), W.barbell_config()):
+        inst, m = cfg["instrument"], cfg["model"]
+        n = 20_000_000
+        e = sas.Experiment(inst, m, stream=stream)
+        e.trace(200_000, 1)
+        ms = _events_ms(lambda: e.trace(n, 1), stream)
+        e.close()
+        terms = m.n_gamma * m.n_psi * m.n_poly * (m.n_cap + 1)
+        rate = n / (ms * 1e-3)
+        fl = F.flops_per_history(m.kind, m.n_poly, m.n_gamma * m.n_psi, n_cap=m.n_cap)
+        res[cfg["name"]] = {"workload": W.MODEL_NAMES[m.kind] + " " + CAPPED_DESC[cfg["name"]], "value": rate,
+                            "unit": UNIT, "histories_timed": n, "slice_terms_per_history": terms,
+                            "slice_terms_per_s": rate * terms, "tflops_nominal": fl * rate / 1e12,
+                            "frac_fp32_nominal": fl * rate / 1e12 / peak}
+    return res
 
 
 def _bin_rel_err(d, n):
@@ -410,9 +443,12 @@ def run_single_workload(args):
     from paper_2501_06054_gb300 import flops as F
     stream = torch.cuda.Stream()
     info = sas.sas_device_info()
-    cfg = W.cylinder_config()
+    capped = args.workload in ("capped_cylinder", "barbell")
+    cfg = W.capped_cylinder_config() if args.workload == "capped_cylinder" else \
+        W.barbell_config() if args.workload == "barbell" else W.cylinder_config()
     m = cfg["model"]
-    n = int(args.neutrons) if args.neutrons else (2_000_000 if args.workload == "cylinder" else 100_000_000)
+    n = int(args.neutrons) if args.neutrons else (2_000_000 if args.workload == "cylinder" else
+                                                  20_000_000 if capped else 100_000_000)
     with torch.cuda.stream(stream):
         e = sas.Experiment(cfg["instrument"], m, stream=stream)
         extra = {}
@@ -426,9 +462,9 @@ def run_single_workload(args):
             peak, unit, bound = (pk.get("bf16_tflops_sustained") or 1703.0), "TFLOP/s", "tensor"
             kernel = "sas::sur::sur_trace_kernel"
         else:
-            flop = F.flops_per_history(m.kind, m.n_poly, m.n_gamma * m.n_psi)
+            flop = F.flops_per_history(m.kind, m.n_poly, m.n_gamma * m.n_psi, n_cap=m.n_cap)
             peak, unit, bound = F.fp32_peak_tflops(info["sm_count"], 2070.0), "TFLOP/s", "alu"
-            kernel = "trace_kernel<float, CYLINDER, TALLY_GLOBAL>"
+            kernel = "trace_kernel<float, %s>" % W.MODEL_NAMES[m.kind].upper()
         for _ in range(args.warmup):
             e.trace(n, cfg["seed"])
         ms = []
@@ -440,8 +476,10 @@ def run_single_workload(args):
     line = {"metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16" if bound == "tensor" else "f32", "data": "synthetic",
-            "config": {"workload": args.workload + ": " + "cylinder R=20 L=400 A, axis N(15 deg) about x, "
-                       "Schulz 0.1 x40, 76x76 orientation nodes, 256x256 detector", "neutrons_per_step": n},
+            "config": {"workload": args.workload + ": " + (
+                W.MODEL_NAMES[m.kind] + " " + CAPPED_DESC[args.workload]
+                if capped else "cylinder R=20 L=400 A, axis N(15 deg) about x, Schulz 0.1 x40, 76x76 "
+                               "orientation nodes, 256x256 detector"), "neutrons_per_step": n},
             "roofline": {"bound": bound, "achieved": flop * rate / 1e12, "peak": peak, "unit": unit,
                          "frac": flop * rate / 1e12 / peak, "traffic": None, "kernel": kernel,
                          "flops_per_history": flop}, "gpu_launches": args.steps}
@@ -500,7 +538,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true")
     ap.add_argument("--workload", default="core_shell",
-                    choices=["core_shell", "cylinder", "cylinder_surrogate"],
+                    choices=["core_shell", "cylinder", "cylinder_surrogate", "capped_cylinder", "barbell"],
                     help="core_shell: the headline step; the others time one workload alone")
     ap.add_argument("--train-steps", type=int, default=60000)
     args = ap.parse_args()

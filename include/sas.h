@@ -57,7 +57,11 @@ typedef enum sas_status {
 
 enum { SAS_SPHERE = 0, SAS_CORE_SHELL = 1, SAS_CYLINDER = 2, SAS_ELLIPSOID = 3,
        /* no symmetry axis (Sec. II.B): sizes along the particle axes A, B, C */
-       SAS_TRIAXIAL_ELLIPSOID = 4, SAS_PARALLELEPIPED = 5 };
+       SAS_TRIAXIAL_ELLIPSOID = 4, SAS_PARALLELEPIPED = 5,
+       /* cylinders with spherical end caps (Sec. III: the expensive models) */
+       SAS_CAPPED_CYLINDER = 6, SAS_BARBELL = 7 };
+/* largest Gauss-Legendre rule over an end cap */
+#define SAS_MAX_CAP_NODES 64
 enum { SAS_SQ_NONE = 0, SAS_SQ_HARD_SPHERE_PY = 1 };
 enum { SAS_FP32 = 0, SAS_FP64 = 1 };
 /* sampling: average every history over the quadrature nodes, or draw one
@@ -92,7 +96,8 @@ typedef struct sas_instrument {
 /* Sample model (Eqs. 1-4, 7, 8; polydispersity and orientation Sec. II.B). */
 typedef struct sas_model_desc {
     int64_t kind;            /* SAS_SPHERE, SAS_CORE_SHELL, SAS_CYLINDER, SAS_ELLIPSOID,
-                                SAS_TRIAXIAL_ELLIPSOID, SAS_PARALLELEPIPED */
+                                SAS_TRIAXIAL_ELLIPSOID, SAS_PARALLELEPIPED, SAS_CAPPED_CYLINDER,
+                                SAS_BARBELL */
     int64_t sq_kind;         /* SAS_SQ_NONE or SAS_SQ_HARD_SPHERE_PY */
     int64_t precision;       /* SAS_FP32 (tallies FP32 Kahan + FP64 reduction) or SAS_FP64 */
     int64_t n_poly;          /* Schulz nodes of the polydisperse radius (1..64) */
@@ -156,6 +161,21 @@ typedef struct sas_model_desc {
      * phi), at the 8 Chebyshev wavelengths of the source band, and
      * interpolated per history. Quadrature sampling only; 0: off. */
     int64_t self_attenuation;
+    /* Capped cylinder and barbell: a cylinder of radius `radius` and length
+     * `length` (>= 0) along the axis, closed by two spherical caps of radius
+     * R = `radius_polar` >= radius: the parts of two spheres beyond the end
+     * faces, their centres h = sqrt(R^2 - r^2) inside the cylinder (capped
+     * cylinder; caps H = R - h high) or outside it (barbell; H = R + h).
+     * Eq. 1 summed over disk slices normal to the axis:
+     *   F = drho [pi r^2 L sinc(Q_C L / 2) 2 J1(Q_AB r) / (Q_AB r)
+     *      + sum_j c_j cos(Q_C z_j) 2 J1(Q_AB rho_j) / (Q_AB rho_j)],
+     * over the n_cap Gauss-Legendre slices of a cap at depth R u_j below its
+     * tip, u_j in [0, H / R]: z_j = L / 2 + H - R u_j,
+     * rho_j^2 = R^2 u_j (2 - u_j), c_j = 2 pi R^3 w_j u_j (2 - u_j);
+     * V = pi r^2 L + 2 pi R H^2 (1 - H / 3R). The polydisperse factor
+     * radius_i / radius scales r, R and L alike. Axis laws as for the
+     * cylinder; quadrature sampling only; radial_table does not apply. */
+    int64_t n_cap;           /* slices per cap (1..SAS_MAX_CAP_NODES); other kinds ignore it */
 } sas_model_desc;
 
 typedef struct sas_experiment sas_experiment;   /* opaque, library-owned */

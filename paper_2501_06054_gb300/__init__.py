@@ -47,7 +47,7 @@ class sas_model_desc(ctypes.Structure):
                    "axis_phi", "sq_radius", "sq_fraction")] + \
                [(n, ctypes.c_int64) for n in ("sampling", "poly_dist", "radial_table")] + \
                [("radius_b", ctypes.c_double), ("axis_psi", ctypes.c_double), ("n_rot", ctypes.c_int64),
-                ("self_attenuation", ctypes.c_int64)]
+                ("self_attenuation", ctypes.c_int64), ("n_cap", ctypes.c_int64)]
 
 
 class sas_launch_config(ctypes.Structure):
@@ -193,7 +193,7 @@ def make_instrument(d) -> sas_instrument:
 def make_model(d) -> sas_model_desc:
     d = d if isinstance(d, dict) else d.as_dict()
     ints = ("kind", "sq_kind", "precision", "n_poly", "n_gamma", "n_psi", "isotropic", "sampling",
-            "poly_dist", "radial_table", "n_rot", "self_attenuation")
+            "poly_dist", "radial_table", "n_rot", "self_attenuation", "n_cap")
     return sas_model_desc(**{k: (int(v) if k in ints else float(v)) for k, v in d.items()})
 
 

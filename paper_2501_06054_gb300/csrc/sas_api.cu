@@ -65,6 +65,13 @@ double host_flops_per_history(const sas_model_desc& m, int np, int no)
         return frames * (20.0 + np * (m.kind == SAS_TRIAXIAL_ELLIPSOID ? 36.0 : 66.0)) + 150.0 +
                (m.sq_kind == SAS_SQ_HARD_SPHERE_PY ? 40.0 : 0.0);
     }
+    if (m.kind == SAS_CAPPED_CYLINDER || m.kind == SAS_BARBELL) {
+        // per radius node: the cylinder term (sinc, 2 J1(x)/x; 60) and per cap
+        // slice cos + 2 J1(x)/x (30)
+        const int nr = (m.poly > 0.0 && m.n_poly > 1) ? (int)m.n_poly : 1;
+        return no * (40.0 + nr * (60.0 + 30.0 * (double)m.n_cap)) + 150.0 +
+               (m.sq_kind == SAS_SQ_HARD_SPHERE_PY ? 40.0 : 0.0);
+    }
     double per;
     if (m.kind == SAS_SPHERE) per = np * 36.0;
     else if (m.kind == SAS_CORE_SHELL) per = np * 62.0 + 20.0;
@@ -461,6 +468,23 @@ void py_constants(double phi, double* alpha, double* beta, double* gamma, double
     }
 }
 
+// Height of a capped cylinder's or barbell's end cap beyond the end face:
+// R - h (the capped cylinder's h = sqrt(R^2 - r^2) formed as r^2 / (R + h),
+// free of cancellation for R >> r) or R + h.
+double cap_height(const sas_model_desc& m)
+{
+    const double r = m.radius, R = m.radius_polar;
+    const double h = std::sqrt(std::fmax(R * R - r * r, 0.0));
+    return m.kind == SAS_CAPPED_CYLINDER ? r * r / (R + h) : R + h;
+}
+
+// Volume at the nominal sizes: pi r^2 L + 2 pi R H^2 (1 - H / 3R).
+double capped_volume(const sas_model_desc& m)
+{
+    const double R = m.radius_polar, H = cap_height(m);
+    return M_PI * m.radius * m.radius * m.length + 2.0 * M_PI * R * H * H * (1.0 - H / (3.0 * R));
+}
+
 // Tables of one model in FP64 (see sas_types.h for the layouts).
 sas_status build_model_tables(const sas_model_desc& m, ModelTables& t, double q_max)
 {
@@ -495,6 +519,14 @@ sas_status build_model_tables(const sas_model_desc& m, ModelTables& t, double q_
             const double F0 = (m.sld - m.sld_solvent) * V;
             p[0] = ri * ri; p[1] = w[i] * F0 * F0; p[2] = ri; p[3] = 1.0 / ri; p[4] = 1.0 / std::sqrt(ri);
             vmean += w[i] * V;
+        } else if (m.kind == SAS_CAPPED_CYLINDER || m.kind == SAS_BARBELL) {
+            const double sc = ri / m.radius;   // one polydisperse factor for r, R and L
+            const double V = capped_volume(m) * sc * sc * sc;
+            const double d = (m.sld - m.sld_solvent) * sc * sc * sc;
+            p[0] = sc;
+            p[1] = w[i] * d * d;
+            p[2] = sc * sc;
+            vmean += w[i] * V;
         } else if (m.kind == SAS_TRIAXIAL_ELLIPSOID || m.kind == SAS_PARALLELEPIPED) {
             const double sc = ri / m.radius;   // one polydisperse factor for the three sizes
             const double V = (m.kind == SAS_TRIAXIAL_ELLIPSOID ? 4.0 / 3.0 * pi : 8.0) * m.radius * m.radius_b *
@@ -528,7 +560,8 @@ sas_status build_model_tables(const sas_model_desc& m, ModelTables& t, double q_
                 d[3] = row == 0 ? wf[o] : 0.0;
             }
         t.n_orient = 3 * nf;
-    } else if (m.kind == SAS_CYLINDER || m.kind == SAS_ELLIPSOID) {
+    } else if (m.kind == SAS_CYLINDER || m.kind == SAS_ELLIPSOID || m.kind == SAS_CAPPED_CYLINDER ||
+               m.kind == SAS_BARBELL) {
         const int nmax = (int)(m.n_gamma * m.n_psi);
         std::vector<double> c((size_t)3 * std::max(nmax, 1)), wo(std::max(nmax, 1));
         const int no = m.isotropic == 2
@@ -549,6 +582,33 @@ sas_status build_model_tables(const sas_model_desc& m, ModelTables& t, double q_
     }
     t.n_rad = t.n_poly;
     t.n_tab = 0;
+    t.n_cap = 0;
+    if (m.kind == SAS_CAPPED_CYLINDER || m.kind == SAS_BARBELL) {
+        // the cap slices at depth R u_j below the tip, u_j Gauss-Legendre on
+        // [0, H / R]: z_j = L/2 + H - R u_j, rho_j^2 = R^2 u_j (2 - u_j),
+        // c_j = 2 pi R^3 w_j u_j (2 - u_j); two slices per row behind the nodes
+        const int nc = (int)m.n_cap;
+        const double r0 = m.radius, R = m.radius_polar, H = cap_height(m);
+        std::vector<double> gx(nc), gw(nc);
+        gauss_legendre(nc, gx.data(), gw.data());
+        const int rows = (nc + 1) / 2;
+        t.poly.resize((size_t)(t.n_poly + rows) * SAS_POLY_STRIDE, 0.0);
+        double* cap = t.poly.data() + (size_t)t.n_poly * SAS_POLY_STRIDE;
+        double rho2max = r0 * r0;
+        for (int j = 0; j < nc; ++j) {
+            const double u = 0.5 * (H / R) * (1.0 + gx[j]), wj = 0.5 * (H / R) * gw[j];
+            const double v = u * (2.0 - u);
+            cap[4 * j] = 0.5 * m.length + H - R * u;
+            cap[4 * j + 1] = R * R * v;
+            cap[4 * j + 2] = 2.0 * pi * R * R * R * wj * v;
+            rho2max = std::fmax(rho2max, R * R * v);
+        }
+        t.n_poly += rows;
+        t.n_cap = nc;
+        t.cap_body = pi * r0 * r0 * m.length;
+        t.cap_r2 = r0 * r0;
+        t.cap_rho2max = rho2max;
+    }
     if (m.kind == SAS_CYLINDER && m.radial_table && m.sampling == SAS_QUADRATURE && q_max > 0.0) {
         // the polydisperse radial sum depends on x = q_AB rbar alone: tabulate
         // G(x) with h G'(x), doubling the grid until the cubic Hermite error at
@@ -661,6 +721,10 @@ ModelConst<T> model_const(const sas_model_desc& m, const ModelTables& t)
         c.orient_mode = (int)m.isotropic;
     c.n_rad = t.n_rad;
     c.n_tab = t.n_tab;
+    c.n_cap = t.n_cap;
+    c.cap_body = (T)t.cap_body;
+    c.cap_r2 = (T)t.cap_r2;
+    c.cap_rho2max = (T)t.cap_rho2max;
     c.tab_inv_h = (T)t.tab_inv_h;
     c.tab_xmax = (T)t.tab_xmax;
     c.tab_c0 = (T)t.tab_c0;
@@ -730,7 +794,15 @@ sas_status validate_instrument(const sas_instrument* in)
 sas_status validate_model(const sas_model_desc* m)
 {
     if (!m) return fail(SAS_ERR_ARG, "model is NULL");
-    if (m->kind < 0 || m->kind > 5) return fail(SAS_ERR_ARG, "unknown model kind");
+    if (m->kind < 0 || m->kind > 7) return fail(SAS_ERR_ARG, "unknown model kind");
+    if (m->kind == SAS_CAPPED_CYLINDER || m->kind == SAS_BARBELL) {
+        if (!std::isfinite(m->length) || !std::isfinite(m->radius_polar) || m->length < 0.0 ||
+            !(m->radius_polar >= m->radius))
+            return fail(SAS_ERR_ARG, "capped cylinder and barbell need length >= 0 and radius_polar >= radius");
+        if (m->n_cap < 1 || m->n_cap > SAS_MAX_CAP_NODES) return fail(SAS_ERR_ARG, "n_cap must be in [1, 64]");
+        if (m->sampling != SAS_QUADRATURE)
+            return fail(SAS_ERR_ARG, "capped cylinder and barbell are quadrature models (sampling SAS_QUADRATURE)");
+    }
     const bool axes3 = m->kind == SAS_TRIAXIAL_ELLIPSOID || m->kind == SAS_PARALLELEPIPED;
     if (axes3 && (!(m->radius_b > 0.0) || !(m->radius_polar > 0.0) || !std::isfinite(m->radius_b) ||
                   !std::isfinite(m->axis_psi)))
@@ -825,6 +897,8 @@ cudaError_t dispatch_trace(sas_experiment* e, const TraceParams<T>& P, int* grid
     case SAS_CYLINDER: return Launcher<T, SAS_CYLINDER>::trace(P, e->cfg, e->sm_count, e->stream, grid);
     case SAS_TRIAXIAL_ELLIPSOID: return Launcher<T, SAS_TRIAXIAL_ELLIPSOID>::trace(P, e->cfg, e->sm_count, e->stream, grid);
     case SAS_PARALLELEPIPED: return Launcher<T, SAS_PARALLELEPIPED>::trace(P, e->cfg, e->sm_count, e->stream, grid);
+    case SAS_CAPPED_CYLINDER: return Launcher<T, SAS_CAPPED_CYLINDER>::trace(P, e->cfg, e->sm_count, e->stream, grid);
+    case SAS_BARBELL: return Launcher<T, SAS_BARBELL>::trace(P, e->cfg, e->sm_count, e->stream, grid);
     default: return Launcher<T, SAS_ELLIPSOID>::trace(P, e->cfg, e->sm_count, e->stream, grid);
     }
 }
@@ -838,6 +912,8 @@ cudaError_t dispatch_records(sas_experiment* e, const TraceParams<T>& P)
     case SAS_CYLINDER: return Launcher<T, SAS_CYLINDER>::records(P, e->stream);
     case SAS_TRIAXIAL_ELLIPSOID: return Launcher<T, SAS_TRIAXIAL_ELLIPSOID>::records(P, e->stream);
     case SAS_PARALLELEPIPED: return Launcher<T, SAS_PARALLELEPIPED>::records(P, e->stream);
+    case SAS_CAPPED_CYLINDER: return Launcher<T, SAS_CAPPED_CYLINDER>::records(P, e->stream);
+    case SAS_BARBELL: return Launcher<T, SAS_BARBELL>::records(P, e->stream);
     default: return Launcher<T, SAS_ELLIPSOID>::records(P, e->stream);
     }
 }
@@ -853,6 +929,8 @@ cudaError_t dispatch_eval(sas_experiment* e, const ModelConst<T>& mc, const T* q
     case SAS_CYLINDER: return Launcher<T, SAS_CYLINDER>::eval(mc, poly, orient, q, out, n, e->stream);
     case SAS_TRIAXIAL_ELLIPSOID: return Launcher<T, SAS_TRIAXIAL_ELLIPSOID>::eval(mc, poly, orient, q, out, n, e->stream);
     case SAS_PARALLELEPIPED: return Launcher<T, SAS_PARALLELEPIPED>::eval(mc, poly, orient, q, out, n, e->stream);
+    case SAS_CAPPED_CYLINDER: return Launcher<T, SAS_CAPPED_CYLINDER>::eval(mc, poly, orient, q, out, n, e->stream);
+    case SAS_BARBELL: return Launcher<T, SAS_BARBELL>::eval(mc, poly, orient, q, out, n, e->stream);
     default: return Launcher<T, SAS_ELLIPSOID>::eval(mc, poly, orient, q, out, n, e->stream);
     }
 }

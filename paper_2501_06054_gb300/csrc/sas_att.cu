@@ -75,6 +75,9 @@ double model_extent(const sas_model_desc& m, const ModelTables& t)
     case SAS_ELLIPSOID: return 2.0 * std::fmax(r, m.radius_polar);
     case SAS_TRIAXIAL_ELLIPSOID:
         return 2.0 * (r / m.radius) * std::fmax(m.radius, std::fmax(m.radius_b, m.radius_polar));
+    case SAS_CAPPED_CYLINDER:
+    case SAS_BARBELL:   // tip to tip, L + 2H, or the caps' diameter
+        return (r / m.radius) * std::fmax(m.length + 2.0 * cap_height(m), 2.0 * m.radius_polar);
     default:
         return 2.0 * (r / m.radius) *
                std::sqrt(m.radius * m.radius + m.radius_b * m.radius_b + m.radius_polar * m.radius_polar);
@@ -147,6 +150,8 @@ cudaError_t att_launch(const sas_model_desc& m, const ModelConst<T>& mc, const T
     case SAS_CYLINDER: return SAS_ATT_CASE(SAS_CYLINDER);
     case SAS_TRIAXIAL_ELLIPSOID: return SAS_ATT_CASE(SAS_TRIAXIAL_ELLIPSOID);
     case SAS_PARALLELEPIPED: return SAS_ATT_CASE(SAS_PARALLELEPIPED);
+    case SAS_CAPPED_CYLINDER: return SAS_ATT_CASE(SAS_CAPPED_CYLINDER);
+    case SAS_BARBELL: return SAS_ATT_CASE(SAS_BARBELL);
     default: return SAS_ATT_CASE(SAS_ELLIPSOID);
     }
 #undef SAS_ATT_CASE

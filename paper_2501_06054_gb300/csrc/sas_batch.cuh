@@ -90,6 +90,8 @@ __device__ __forceinline__ void batch_dispatch(const BatchParams& P, const Model
     case SAS_CYLINDER: batch_item<SAS_CYLINDER, HIST, ATT>(P, mc, poly, orient, w, h, seed, tr); break;
     case SAS_TRIAXIAL_ELLIPSOID: batch_item<SAS_TRIAXIAL_ELLIPSOID, HIST, ATT>(P, mc, poly, orient, w, h, seed, tr); break;
     case SAS_PARALLELEPIPED: batch_item<SAS_PARALLELEPIPED, HIST, ATT>(P, mc, poly, orient, w, h, seed, tr); break;
+    case SAS_CAPPED_CYLINDER: batch_item<SAS_CAPPED_CYLINDER, HIST, ATT>(P, mc, poly, orient, w, h, seed, tr); break;
+    case SAS_BARBELL: batch_item<SAS_BARBELL, HIST, ATT>(P, mc, poly, orient, w, h, seed, tr); break;
     default: batch_item<SAS_ELLIPSOID, HIST, ATT>(P, mc, poly, orient, w, h, seed, tr); break;
     }
 }

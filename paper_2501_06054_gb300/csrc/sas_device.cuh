@@ -429,6 +429,96 @@ __device__ __forceinline__ T avg_cylinder_tab(const T qv[3], const T* __restrict
     return k.s;
 }
 
+// 2 J1(x)/x from s = x^2 in the form of tier TIER: x <= 4, 6, 8, 12, and
+// any x (the modulus-phase form beyond 12, chosen per term).
+template <int TIER>
+__device__ __forceinline__ float cyl_a_tier(float sx)
+{
+    if constexpr (TIER == 0) return sas_cyl_a_r(sx);
+    else if constexpr (TIER == 1) return sas_cyl_a_v(sx);
+    else if constexpr (TIER == 2) return sas_cyl_a_s(sx);
+    else if constexpr (TIER == 3) return sas_cyl_a_s3(sx);
+    else {
+        if (sx <= SAS_J1Q_SMAX) return sas_cyl_a_s3(sx);
+        const float x = sqrtf(sx);
+        return sas_cyl_a_large(x, __frcp_rn(x), rsqrtf(x));
+    }
+}
+
+// FP32 amplitude of one capped-cylinder or barbell node over its slices:
+//   body a(u r^2) + sum_j c_j cos(w z_j) a(u rho_j^2),
+// u = (s |Q x c|)^2, w = s Q_C; cos from the special-function unit.
+template <int TIER>
+__device__ __forceinline__ float capped_amp(float body, float u, float w, const float* __restrict__ cap, int nc,
+                                            float r2)
+{
+    float f = body * cyl_a_tier<TIER>(u * r2);
+#pragma unroll 4
+    for (int j = 0; j < nc; ++j) {
+        const float4 c = *reinterpret_cast<const float4*>(cap + 4 * j);   // z, rho^2, c, 0
+        f = fmaf(c.z * __cosf(w * c.x), cyl_a_tier<TIER>(u * c.y), f);
+    }
+    return f;
+}
+
+// Capped cylinder and barbell (Eq. 1 over disk slices normal to the axis):
+// per orientation node and polydisperse scale s (poly node {s, coefficient,
+// s^2}), F / (drho s^3) = pi r^2 L sinc(s Q_C L / 2) a(s Q_AB r)
+//   + sum_j c_j cos(s Q_C z_j) a(s Q_AB rho_j), a(x) = 2 J1(x)/x, the cap
+// slices {z_j, rho_j^2, c_j} behind the nodes. FP32: the 2 J1(x)/x form is
+// chosen per node, uniformly over the warp, from the warp's largest |Q|^2
+// times s^2 times the largest slice radius squared.
+template <typename T>
+__device__ __forceinline__ T avg_capped(const T qv[3], const T* __restrict__ poly, int np,
+                                        const T* __restrict__ orient, int no, const ModelConst<T>& mc)
+{
+    const T* __restrict__ cap = poly + SAS_POLY_STRIDE * np;
+    const int nc = mc.n_cap;
+    Kahan<T> k;
+    float qm = 0.f;
+    if constexpr (sizeof(T) == sizeof(float)) {
+        const float q2 = fma(qv[0], qv[0], fma(qv[1], qv[1], qv[2] * qv[2]));
+        qm = __uint_as_float(__reduce_max_sync(__activemask(), __float_as_uint(q2))) * mc.cap_rho2max;
+    }
+    for (int o = 0; o < no; ++o) {
+        const T* c = orient + 4 * o;
+        const T qc = fma(qv[0], c[0], fma(qv[1], c[1], qv[2] * c[2]));
+        const T x0 = fma(qv[1], c[2], -qv[2] * c[1]);
+        const T x1 = fma(qv[2], c[0], -qv[0] * c[2]);
+        const T x2 = fma(qv[0], c[1], -qv[1] * c[0]);
+        const T qab2 = fma(x0, x0, fma(x1, x1, x2 * x2));
+        T inner = 0;
+        for (int i = 0; i < np; ++i) {
+            const T* p = poly + SAS_POLY_STRIDE * i;
+            const T w = p[0] * qc;
+            const T y = fabs(w) * mc.half_length;
+            const T body = mc.cap_body * M<T>::sinc(y, M<T>::rcp(y));
+            T F;
+            if constexpr (sizeof(T) == sizeof(float)) {
+                const float u = qab2 * p[2];
+                const float bound = qm * p[2];   // warp-uniform
+                if (bound <= SAS_J1R_SMAX) F = capped_amp<0>(body, u, w, cap, nc, mc.cap_r2);
+                else if (bound <= SAS_J1V_SMAX) F = capped_amp<1>(body, u, w, cap, nc, mc.cap_r2);
+                else if (bound <= SAS_J1P_SMAX) F = capped_amp<2>(body, u, w, cap, nc, mc.cap_r2);
+                else if (bound <= SAS_J1Q_SMAX) F = capped_amp<3>(body, u, w, cap, nc, mc.cap_r2);
+                else F = capped_amp<4>(body, u, w, cap, nc, mc.cap_r2);
+            } else {
+                const T qs = M<T>::sqrt_(qab2) * p[0];
+                T x = qs * M<T>::sqrt_(mc.cap_r2);
+                F = body * M<T>::cyl_a(x, M<T>::rcp(x), (T)0);
+                for (int j = 0; j < nc; ++j) {
+                    const T* cj = cap + 4 * j;
+                    x = qs * M<T>::sqrt_(cj[1]);
+                    F = fma(cj[2] * cos(w * cj[0]), M<T>::cyl_a(x, M<T>::rcp(x), (T)0), F);
+                }
+            }
+            inner = fma(p[1], F * F, inner);
+        }
+        k.add(c[3] * inner);
+    }
+    return k.s;
+}
+
 // Particles without a symmetry axis (Eq. 1 for the body): per frame
 // (rows A, B, C of the orientation table, weight in row A) and polydisperse
 // scale s_i (poly node: s_i, coefficient):
@@ -513,6 +603,8 @@ __device__ __forceinline__ T dsigma(const T qv[3], const ModelConst<T>& mc,
                            : avg_cylinder<T>(qv, poly, mc.n_rad, orient, mc.n_orient, mc.half_length);
     } else if (KIND == SAS_ELLIPSOID) {
         avg = avg_ellipsoid<T>(qv, poly, mc.n_poly, orient, mc.n_orient, mc.rp2);
+    } else if (KIND == SAS_CAPPED_CYLINDER || KIND == SAS_BARBELL) {
+        avg = avg_capped<T>(qv, poly, mc.n_rad, orient, mc.n_orient, mc);
     } else {
         avg = avg_axes3<T, KIND>(qv, poly, mc.n_rad, orient, mc.n_orient, mc);
     }
@@ -667,7 +759,9 @@ __device__ __forceinline__ T dsigma_history(const T qv[3], const ModelConst<T>& 
                                             const T* __restrict__ orient, uint64_t seed, uint32_t exp_id,
                                             uint64_t index)
 {
-    if (mc.event) return dsigma_event<T, KIND>(qv, mc, event_draws(seed, exp_id, index));
+    if constexpr (KIND != SAS_CAPPED_CYLINDER && KIND != SAS_BARBELL) {   // quadrature-only kinds
+        if (mc.event) return dsigma_event<T, KIND>(qv, mc, event_draws(seed, exp_id, index));
+    }
     return dsigma<T, KIND>(qv, mc, poly, orient);
 }
 

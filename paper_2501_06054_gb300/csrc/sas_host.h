@@ -21,6 +21,9 @@ struct ModelTables {
     int n_tab = 0;                // table points (0: no table)
     double tab_inv_h = 0, tab_xmax = 0, tab_c0 = 0, tab_rbar = 0, tab_err = 0;
     double r_max = 0;             // largest polydisperse radius node
+    // capped cylinder and barbell: cap slices behind the radius nodes
+    int n_cap = 0;
+    double cap_body = 0, cap_r2 = 0, cap_rho2max = 0;
     // self-attenuation: mu_s (1/m) at the Chebyshev wavelengths and its
     // interpolant (att_n = 0: off)
     int att_n = 0;
@@ -55,6 +58,8 @@ sas_status validate_model(const sas_model_desc* m);
 template <typename T> ModelConst<T> model_const(const sas_model_desc& m, const ModelTables& t);
 // extent of the particle, the rule, and the table from mu_s at the nodes
 double model_extent(const sas_model_desc& m, const ModelTables& t);
+double cap_height(const sas_model_desc& m);
+double capped_volume(const sas_model_desc& m);
 void att_rule(const sas_instrument& in, const sas_model_desc& m, const ModelTables& t, AttRule& r);
 void att_fit(const AttRule& r, const double* mu, ModelTables& t);
 // evaluates mu_s (1/m) at the rule's wavelengths on the GPU (kernels of the

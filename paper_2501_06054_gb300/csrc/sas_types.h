@@ -50,6 +50,8 @@ struct AttPanel {
 //                 c_2 = 3 sqrt(w) (rho_s - rho_solv) V_o, c_1 / r_c^3, c_2 / r_o^3}
 //     cylinder   {r^2, w (drho V)^2, r, 1/r, 1/sqrt(r), 0...}  (ascending r)
 //     ellipsoid  {r_e^2, 9 w (drho V)^2, 0...}
+//     capped cylinder, barbell {s, w (drho s^3)^2, s^2, 0...} (s = r_i / r),
+//                followed by the cap slices, two per row: {z_j, rho_j^2, c_j, 0}
 //   orient table per node: {c_x, c_y, c_z, weight}
 template <typename T>
 struct ModelConst {
@@ -83,6 +85,11 @@ struct ModelConst {
     T ax_a, ax_b, ax_c;
     T ev_frame[6];   // rows A and B of the fixed frame (C is ev_axis)
     AttTable<T> att; // self-attenuation mu_s(lambda) (n = 0: the instrument's mu only)
+    // capped cylinder and barbell: the cylinder's amplitude pi r^2 L, r^2,
+    // the largest squared slice radius (cylinder or cap) and the cap slices
+    // stored behind the n_rad radius nodes
+    int n_cap;
+    T cap_body, cap_r2, cap_rho2max;
 };
 
 }  // namespace sas

@@ -36,6 +36,13 @@ operations than counted here for the same terms.
   parallelepiped term: three scaled arguments (3 mul), three sincs
       (3 x 20: reduction, sin polynomial, 1/y), product, square and
       weighted sum (3)                                             66
+  capped cylinder and barbell: per cap slice (cos from the special-
+      function unit, not counted): argument s Q_C z (mul), x^2 (mul),
+      2 J1(x)/x for x <= 4 (6 FMA), c cos (mul), weighted sum (FMA)    17
+      per radius node: s Q_C, |y| L/2 (2 mul), sinc (~20), cylinder
+      amplitude (mul), x^2 (mul), 2 J1(x)/x (6 FMA) and its product
+      (mul), F^2 and the weighted sum (3)                          40
+      per orientation node as for the cylinder                     60
   per history: geometry (wavelength, pinholes, slab, detector
                point, Q, solid angle)                           150
                Percus-Yevick S(Q)                               40
@@ -51,9 +58,11 @@ CS_HISTORY = 20
 ORIENT_NODE = 60
 GEOMETRY = 150
 PY = 40
+CAP_SLICE = 17
+CAP_NODE = 40
 
 
-def flops_per_history(kind: int, n_poly: int, n_orient: int = 1, sq: bool = False) -> int:
+def flops_per_history(kind: int, n_poly: int, n_orient: int = 1, sq: bool = False, n_cap: int = 16) -> int:
     if kind == 0:        # sphere
         per = n_poly * (AMP + 3)
     elif kind == 1:      # core-shell
@@ -64,6 +73,8 @@ def flops_per_history(kind: int, n_poly: int, n_orient: int = 1, sq: bool = Fals
         per = n_orient * (FRAME_NODE + n_poly * TRI_TERM)
     elif kind == 5:      # parallelepiped
         per = n_orient * (FRAME_NODE + n_poly * BOX_TERM)
+    elif kind in (6, 7):  # capped cylinder, barbell
+        per = n_orient * (ORIENT_NODE + n_poly * (CAP_NODE + n_cap * CAP_SLICE))
     else:                # ellipsoid
         per = n_orient * (ORIENT_NODE + n_poly * (AMP + 5))
     return per + GEOMETRY + (PY if sq else 0)

@@ -137,6 +137,27 @@ def cylinder_config():
                 n_neutrons=10**9, seed=1)
 
 
+def capped_cylinder_config():
+    """Oriented polydisperse capped cylinder: r = 20, caps R = 25, L = 200
+    angstrom, Schulz 0.1 (10 nodes), Gaussian axis spread 15 deg (16x16
+    nodes), 16 slices per cap, 128x128, FP32."""
+    m = Model(kind=CAPPED_CYLINDER, precision=FP32, radius=20.0, radius_polar=25.0, length=200.0,
+              sld=2.0e-6, sld_solvent=0.0, volume_fraction=0.01, poly=0.1, n_poly=10,
+              sigma_orient=math.radians(15.0), axis_theta=0.5 * math.pi, axis_phi=0.0,
+              n_gamma=16, n_psi=16, n_cap=16)
+    return dict(name="capped_cylinder", instrument=instrument(), model=m, n_neutrons=10**8, seed=1)
+
+
+def barbell_config():
+    """Isotropic polydisperse barbell: r = 10, bells R = 25, L = 100
+    angstrom, Schulz 0.1 (10 nodes), axis uniform on the sphere (16x16
+    nodes), 16 slices per bell, 128x128, FP32."""
+    m = Model(kind=BARBELL, precision=FP32, radius=10.0, radius_polar=25.0, length=100.0,
+              sld=2.0e-6, sld_solvent=0.0, volume_fraction=0.01, poly=0.1, n_poly=10,
+              isotropic=ISOTROPIC, n_gamma=16, n_psi=16, n_cap=16)
+    return dict(name="barbell", instrument=instrument(), model=m, n_neutrons=10**8, seed=1)
+
+
 CONFIGS = {"sphere": sphere_config, "core_shell": core_shell_config,
            "cylinder": cylinder_config}
 
