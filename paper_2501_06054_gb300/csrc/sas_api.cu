@@ -68,7 +68,7 @@ double host_flops_per_history(const sas_model_desc& m, int np, int no)
     if (m.kind == SAS_CAPPED_CYLINDER || m.kind == SAS_BARBELL) {
         // per radius node: the cylinder term (sinc, 2 J1(x)/x; 60) and per cap
         // slice cos + 2 J1(x)/x (30)
-        const int nr = (m.poly > 0.0 && m.n_poly > 1) ? (int)m.n_poly : 1;
+        const int nr = (m.poly > 0.0 && m.n_poly > 1 && m.sampling == SAS_QUADRATURE) ? (int)m.n_poly : 1;
         return no * (40.0 + nr * (60.0 + 30.0 * (double)m.n_cap)) + 150.0 +
                (m.sq_kind == SAS_SQ_HARD_SPHERE_PY ? 40.0 : 0.0);
     }
@@ -652,8 +652,13 @@ sas_status build_model_tables(const sas_model_desc& m, ModelTables& t, double q_
     if (m.sampling == SAS_PER_EVENT) {
         // per-event histories draw their own radius and axis: the nodes only
         // gave <V> above, and one node keeps the kernels' staging minimal
-        t.poly.resize(SAS_POLY_STRIDE);
-        t.n_poly = 1;
+        // (the cap slices of the capped kinds move up behind it)
+        const int cap_rows = t.n_poly - t.n_rad;
+        if (t.n_cap > 0 && t.n_rad > 1)
+            std::copy(t.poly.begin() + (size_t)t.n_rad * SAS_POLY_STRIDE, t.poly.end(),
+                      t.poly.begin() + SAS_POLY_STRIDE);
+        t.poly.resize((size_t)(1 + (t.n_cap > 0 ? cap_rows : 0)) * SAS_POLY_STRIDE);
+        t.n_poly = 1 + (t.n_cap > 0 ? cap_rows : 0);
         t.n_rad = 1;
         if (t.n_orient > 0) {
             const int rows = (m.kind == SAS_TRIAXIAL_ELLIPSOID || m.kind == SAS_PARALLELEPIPED) ? 3 : 1;
@@ -696,7 +701,8 @@ ModelConst<T> model_const(const sas_model_desc& m, const ModelTables& t)
     c.sq_switch = (T)t.sq_switch;
     for (int k = 0; k < SAS_SQ_NSER; ++k) c.sq_series[k] = (T)t.sq_series[k];
     c.event = m.sampling == SAS_PER_EVENT ? 1 : 0;
-    c.orient_mode = (m.kind == SAS_CYLINDER || m.kind == SAS_ELLIPSOID) ? (int)m.isotropic : 0;
+    c.orient_mode = (m.kind == SAS_CYLINDER || m.kind == SAS_ELLIPSOID || m.kind == SAS_CAPPED_CYLINDER ||
+                     m.kind == SAS_BARBELL) ? (int)m.isotropic : 0;
     c.ev_r = (T)m.radius;
     c.ev_p = (T)(m.poly_dist == SAS_POLY_GAUSSIAN ? m.poly : 0.0);
     const double lo = c.ev_p > (T)0 ? 0.5 * std::erfc(1.0 / (m.poly * std::sqrt(2.0))) : 0.0;
@@ -800,8 +806,6 @@ sas_status validate_model(const sas_model_desc* m)
             !(m->radius_polar >= m->radius))
             return fail(SAS_ERR_ARG, "capped cylinder and barbell need length >= 0 and radius_polar >= radius");
         if (m->n_cap < 1 || m->n_cap > SAS_MAX_CAP_NODES) return fail(SAS_ERR_ARG, "n_cap must be in [1, 64]");
-        if (m->sampling != SAS_QUADRATURE)
-            return fail(SAS_ERR_ARG, "capped cylinder and barbell are quadrature models (sampling SAS_QUADRATURE)");
     }
     const bool axes3 = m->kind == SAS_TRIAXIAL_ELLIPSOID || m->kind == SAS_PARALLELEPIPED;
     if (axes3 && (!(m->radius_b > 0.0) || !(m->radius_polar > 0.0) || !std::isfinite(m->radius_b) ||

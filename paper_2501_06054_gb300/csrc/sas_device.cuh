@@ -633,7 +633,8 @@ __device__ __forceinline__ T u01c(uint32_t x)
 // (phi / <V>) |F(Q; r, axis)|^2 S(Q); its expectation over the draws is the
 // quadrature average over the same laws.
 template <typename T, int KIND>
-__device__ __forceinline__ T dsigma_event(const T qv[3], const ModelConst<T>& mc, uint4 rb)
+__device__ __forceinline__ T dsigma_event(const T qv[3], const ModelConst<T>& mc, const T* __restrict__ poly,
+                                          uint4 rb)
 {
     const T q2 = fma(qv[0], qv[0], fma(qv[1], qv[1], qv[2] * qv[2]));
     const T q = M<T>::sqrt_(q2);
@@ -727,7 +728,38 @@ __device__ __forceinline__ T dsigma_event(const T qv[3], const ModelConst<T>& mc
         const T x1 = fma(qv[2], c[0], -qv[0] * c[2]);
         const T x2 = fma(qv[0], c[1], -qv[1] * c[0]);
         const T qab2 = fma(x0, x0, fma(x1, x1, x2 * x2));
-        if (KIND == SAS_CYLINDER) {
+        if constexpr (KIND == SAS_CAPPED_CYLINDER || KIND == SAS_BARBELL) {
+            // the drawn scale s = r / r_mean on every size; the cap slices sit
+            // behind the single node row
+            const T sc = r / mc.ev_r;
+            const T w = sc * qc;
+            const T y = fabs(w) * mc.half_length;
+            const T body = mc.cap_body * M<T>::sinc(y, M<T>::rcp(y));
+            const T* __restrict__ cap = poly + SAS_POLY_STRIDE;
+            const int nc = mc.n_cap;
+            T A;
+            if constexpr (sizeof(T) == sizeof(float)) {
+                const float s2 = sc * sc, u = qab2 * s2;
+                const float bound = __uint_as_float(__reduce_max_sync(__activemask(), __float_as_uint(q2 * s2))) *
+                                    mc.cap_rho2max;   // warp-uniform
+                if (bound <= SAS_J1R_SMAX) A = capped_amp<0>(body, u, w, cap, nc, mc.cap_r2);
+                else if (bound <= SAS_J1V_SMAX) A = capped_amp<1>(body, u, w, cap, nc, mc.cap_r2);
+                else if (bound <= SAS_J1P_SMAX) A = capped_amp<2>(body, u, w, cap, nc, mc.cap_r2);
+                else if (bound <= SAS_J1Q_SMAX) A = capped_amp<3>(body, u, w, cap, nc, mc.cap_r2);
+                else A = capped_amp<4>(body, u, w, cap, nc, mc.cap_r2);
+            } else {
+                const T qs = M<T>::sqrt_(qab2) * sc;
+                T x = qs * M<T>::sqrt_(mc.cap_r2);
+                A = body * M<T>::cyl_a(x, M<T>::rcp(x), (T)0);
+                for (int j = 0; j < nc; ++j) {
+                    const T* cj = cap + 4 * j;
+                    x = qs * M<T>::sqrt_(cj[1]);
+                    A = fma(cj[2] * cos(w * cj[0]), M<T>::cyl_a(x, M<T>::rcp(x), (T)0), A);
+                }
+            }
+            const T F = mc.ev_c1 * sc * sc * sc * A;
+            F2 = F * F;
+        } else if (KIND == SAS_CYLINDER) {
             const T y = fabs(qc) * (T)0.5 * mc.ev_len;
             const T sn = M<T>::sinc(y, M<T>::rcp(y));
             const T x = M<T>::sqrt_(qab2) * r;
@@ -759,9 +791,7 @@ __device__ __forceinline__ T dsigma_history(const T qv[3], const ModelConst<T>& 
                                             const T* __restrict__ orient, uint64_t seed, uint32_t exp_id,
                                             uint64_t index)
 {
-    if constexpr (KIND != SAS_CAPPED_CYLINDER && KIND != SAS_BARBELL) {   // quadrature-only kinds
-        if (mc.event) return dsigma_event<T, KIND>(qv, mc, event_draws(seed, exp_id, index));
-    }
+    if (mc.event) return dsigma_event<T, KIND>(qv, mc, poly, event_draws(seed, exp_id, index));
     return dsigma<T, KIND>(qv, mc, poly, orient);
 }
 

@@ -174,3 +174,20 @@ def test_polydisperse_scales_every_size():
     v2 = np.sum(prep.poly_w * (V * s ** 3) ** 2)
     v1 = np.sum(prep.poly_w * V * s ** 3)
     assert oracle.dsigma(prep, np.zeros((1, 3)))[0] == pytest.approx(v2 / v1, rel=1e-12)
+
+
+@pytest.mark.parametrize("kind,iso", [(W.CAPPED_CYLINDER, W.ISOTROPIC), (W.BARBELL, W.UNIFORM_ANGLES)])
+def test_per_event_draws_average_to_the_quadrature(kind, iso):
+    """The per-event estimator (one Gaussian radius and one axis drawn per
+    history, Sec. II.B) has the quadrature over the same laws as its mean."""
+    base = dict(kind=kind, radius=12.0, radius_polar=18.0, length=50.0, sld=2e-6, volume_fraction=0.01,
+                poly=0.15, poly_dist=W.GAUSSIAN, n_poly=32, isotropic=iso, n_gamma=32, n_psi=32, n_cap=16)
+    quad = W.Model(**base, sampling=W.QUADRATURE)
+    ev = W.Model(**base, sampling=W.PER_EVENT)
+    n = 400000   # |F|^2 of one drawn elongated body is heavy-tailed; the z test wants many draws
+    for qv in ([0.03, 0.01, 0.0], [0.0, 0.06, 0.02]):
+        q = np.tile(np.array(qv), (n, 1))
+        d = oracle.dsigma_event(ev, q, seed=5, first=17)
+        ref = oracle.dsigma(oracle.Prepared(quad), q[:1])[0]
+        z = (d.mean() - ref) / (d.std() / math.sqrt(n))
+        assert abs(z) < 4.0, (kind, iso, qv, z)
