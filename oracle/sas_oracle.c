@@ -88,7 +88,9 @@ typedef struct {
 } oracle_instrument;
 
 typedef struct {
-    int64_t kind;          /* 0 sphere, 1 core-shell, 2 cylinder, 3 ellipsoid */
+    int64_t kind;          /* 0 sphere, 1 core-shell, 2 cylinder, 3 ellipsoid, 4 triaxial
+                              ellipsoid, 5 parallelepiped, 6 capped cylinder, 7 barbell,
+                              8 core-shell cylinder, 9 hollow cylinder, 10 core-shell ellipsoid */
     int64_t sq_kind;       /* 0 none, 1 Percus-Yevick hard spheres */
     int64_t n_poly;        /* polydispersity nodes */
     int64_t n_orient;      /* orientation nodes */
@@ -120,6 +122,10 @@ typedef struct {
     /* capped cylinder and barbell (kinds 6, 7): Gauss-Legendre nodes of the
      * integral over each spherical end cap (1 to 64) */
     int64_t n_cap;
+    /* core-shell cylinder (kind 8): thickness of the shell on the end faces;
+     * core-shell ellipsoid (kind 10): thickness of the shell along the axis
+     * (`thickness` is the shell's radial / equatorial thickness) */
+    double thickness_face;
 } oracle_model;
 
 /* --------------------------------------------------------- model pieces */
@@ -350,6 +356,78 @@ double oracle_dsigma(const oracle_model *m, const double q[3])
             }
             sum += m->orient_w[o] * inner;
         }
+    } else if (m->kind == 8 || m->kind == 9) {
+        /* core-shell cylinder (8): a core cylinder (r, L, rho_core) inside a
+         * shell that adds t around it and t_f on each end face (rho_shell);
+         * by Eq. 1 each region's amplitude is the difference of two nested
+         * cylinders, so
+         *   F = (rho_c - rho_s) pi r^2 L sinc(Q_C L/2) a(Q_AB r)
+         *     + (rho_s - rho_solv) V_o sinc(Q_C (L/2 + t_f)) a(Q_AB (r + t)),
+         * V_o = pi (r + t)^2 (L + 2 t_f), normalised by <V_o>.
+         * Hollow cylinder (9): a tube of wall material (sld) between r and
+         * r + t over the length L, solvent inside:
+         *   F = (rho - rho_solv) sinc(Q_C L/2) [pi (r + t)^2 L a(Q_AB (r + t)) - pi r^2 L a(Q_AB r)],
+         * normalised by the wall volume <pi ((r + t)^2 - r^2) L>.
+         * The core (hollow) radius r is polydisperse, t, t_f and L fixed. */
+        double t = m->thickness, L = m->length;
+        double tf = m->kind == 8 ? m->thickness_face : 0.0;
+        double d1 = m->kind == 8 ? m->sld - m->sld_shell : (SAS_MUT == 23 ? 1.0 : -1.0) * (m->sld - m->sld_solvent);
+        double d2 = m->kind == 8 ? m->sld_shell - m->sld_solvent : m->sld - m->sld_solvent;
+        for (int64_t i = 0; i < np; ++i) {
+            double r = m->poly_r[i], ro = r + t;
+            vmean += m->poly_w[i] * (m->kind == 8 ? PI * ro * ro * (L + 2.0 * tf) : PI * (ro * ro - r * r) * L);
+        }
+        for (int64_t o = 0; o < m->n_orient; ++o) {
+            const double *c = m->orient_c + 3 * o;
+            double qc = q[0] * c[0] + q[1] * c[1] + q[2] * c[2];
+            double x0 = q[1] * c[2] - q[2] * c[1];
+            double x1 = q[2] * c[0] - q[0] * c[2];
+            double x2 = q[0] * c[1] - q[1] * c[0];
+            double qab = sqrt(x0 * x0 + x1 * x1 + x2 * x2);
+            double s1 = oracle_sinc(0.5 * qc * L);
+            double s2 = oracle_sinc(qc * (0.5 * L + (SAS_MUT == 22 ? 0.0 : tf)));
+            double inner = 0.0;
+            for (int64_t i = 0; i < np; ++i) {
+                double r = m->poly_r[i], ro = r + t;
+                double F = d1 * PI * r * r * L * s1 * oracle_cyl_a(qab * r)
+                         + d2 * PI * ro * ro * (L + 2.0 * tf) * s2 * oracle_cyl_a(qab * ro);
+                inner += m->poly_w[i] * F * F;
+            }
+            sum += m->orient_w[o] * inner;
+        }
+    } else if (m->kind == 10) {
+        /* core-shell ellipsoid of revolution: core radii (r, r_p), the shell
+         * adds t at the equator and t_p at the poles; by Eq. 1 with the
+         * ellipsoid's amplitude f(x) = 3 (sin x - x cos x) / x^3,
+         *   F = (rho_c - rho_s) V_c f(x_c) + (rho_s - rho_solv) V_o f(x_o),
+         * x^2 = (Q_AB r_e)^2 + (Q_C r_p)^2 for the core and the outer
+         * surface, V = 4/3 pi r_e^2 r_p; normalised by <V_o>. The core's
+         * equatorial radius is polydisperse, r_p, t and t_p fixed. */
+        double rp = m->radius_polar, t = m->thickness;
+        double rpo = rp + (SAS_MUT == 24 ? 0.0 : m->thickness_face);
+        for (int64_t i = 0; i < np; ++i) {
+            double ro = m->poly_r[i] + t;
+            vmean += m->poly_w[i] * 4.0 / 3.0 * PI * ro * ro * (rp + m->thickness_face);
+        }
+        for (int64_t o = 0; o < m->n_orient; ++o) {
+            const double *c = m->orient_c + 3 * o;
+            double qc = q[0] * c[0] + q[1] * c[1] + q[2] * c[2];
+            double x0 = q[1] * c[2] - q[2] * c[1];
+            double x1 = q[2] * c[0] - q[0] * c[2];
+            double x2 = q[0] * c[1] - q[1] * c[0];
+            double qab2 = x0 * x0 + x1 * x1 + x2 * x2;
+            double inner = 0.0;
+            for (int64_t i = 0; i < np; ++i) {
+                double re = m->poly_r[i], ro = re + t;
+                double Vc = 4.0 / 3.0 * PI * re * re * rp, Vo = 4.0 / 3.0 * PI * ro * ro * rpo;
+                double xc = sqrt(re * re * qab2 + rp * rp * qc * qc);
+                double xo = sqrt(ro * ro * qab2 + rpo * rpo * qc * qc);
+                double F = (m->sld - m->sld_shell) * Vc * oracle_sphere_f(xc)
+                         + (m->sld_shell - m->sld_solvent) * Vo * oracle_sphere_f(xo);
+                inner += m->poly_w[i] * F * F;
+            }
+            sum += m->orient_w[o] * inner;
+        }
     } else {                         /* ellipsoid of revolution: equatorial radius polydisperse */
         double drho = m->sld - m->sld_solvent;
         double rp = m->radius_polar;
@@ -485,6 +563,13 @@ static double model_volume(const oracle_model *m, double r)
         double s = r / m->radius;
         return (m->kind == 4 ? 4.0 / 3.0 * PI : 8.0) * m->radius * m->radius_b * m->radius_polar * s * s * s;
     }
+    if (m->kind == 8) {
+        double ro = r + m->thickness;
+        return PI * ro * ro * (m->length + 2.0 * m->thickness_face);
+    }
+    if (m->kind == 9) return PI * ((r + m->thickness) * (r + m->thickness) - r * r) * m->length;
+    if (m->kind == 10)
+        return 4.0 / 3.0 * PI * (r + m->thickness) * (r + m->thickness) * (m->radius_polar + m->thickness_face);
     if (m->kind == 6 || m->kind == 7) {
         double s = r / m->radius, R = m->radius_polar, r0 = m->radius;
         double h = sqrt(fmax(R * R - r0 * r0, 0.0));
@@ -606,6 +691,12 @@ double oracle_model_extent(const oracle_model *m)
         double H = m->kind == 6 ? r0 * r0 / (R + h) : R + h;
         return f * fmax(m->length + 2.0 * H, 2.0 * R);
     }
+    case 8: {
+        double lo = m->length + 2.0 * m->thickness_face, ro = r + m->thickness;
+        return sqrt(lo * lo + 4.0 * ro * ro);
+    }
+    case 9: return sqrt(m->length * m->length + 4.0 * (r + m->thickness) * (r + m->thickness));
+    case 10: return 2.0 * fmax(r + m->thickness, m->radius_polar + m->thickness_face);
     default: {
         double f = r / m->radius;
         return 2.0 * f * sqrt(m->radius * m->radius + m->radius_b * m->radius_b +

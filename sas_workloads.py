@@ -37,10 +37,12 @@ import numpy as np
 SPHERE, CORE_SHELL, CYLINDER, ELLIPSOID = 0, 1, 2, 3
 TRIAXIAL_ELLIPSOID, PARALLELEPIPED = 4, 5        # no symmetry axis: sizes along A, B, C
 CAPPED_CYLINDER, BARBELL = 6, 7                  # cylinder with spherical end caps (radius_polar)
+CORE_SHELL_CYLINDER, HOLLOW_CYLINDER, CORE_SHELL_ELLIPSOID = 8, 9, 10
 MODEL_NAMES = {SPHERE: "sphere", CORE_SHELL: "core_shell", CYLINDER: "cylinder",
                ELLIPSOID: "ellipsoid", TRIAXIAL_ELLIPSOID: "triaxial_ellipsoid",
                PARALLELEPIPED: "parallelepiped", CAPPED_CYLINDER: "capped_cylinder",
-               BARBELL: "barbell"}
+               BARBELL: "barbell", CORE_SHELL_CYLINDER: "core_shell_cylinder",
+               HOLLOW_CYLINDER: "hollow_cylinder", CORE_SHELL_ELLIPSOID: "core_shell_ellipsoid"}
 SQ_NONE, SQ_HARD_SPHERE_PY = 0, 1
 FP32, FP64 = 0, 1
 QUADRATURE, PER_EVENT = 0, 1              # sampling: averages over nodes / one draw per history
@@ -81,7 +83,7 @@ class Model:
     isotropic: int = CAP             # CAP (Gaussian about the mean axis), ISOTROPIC, UNIFORM_ANGLES
     radius: float = 50.0            # sphere R, core radius, cylinder R, ellipsoid equatorial R,
                                     # 3-axis models: semi-axis / half-edge along A
-    thickness: float = 0.0          # core-shell shell thickness
+    thickness: float = 0.0          # core-shell shell thickness; hollow cylinder wall
     length: float = 0.0             # cylinder length (capped cylinder, barbell: between the end faces)
     radius_polar: float = 0.0       # ellipsoid polar radius (along the axis); 3-axis models: along C;
                                     # capped cylinder, barbell: radius of the end caps' spheres (>= radius)
@@ -103,6 +105,8 @@ class Model:
     n_rot: int = 1                  # quadrature nodes in psi (uniform rotations / angles)
     self_attenuation: int = 0       # 1: attenuation mu + Sigma_s(lambda), the model's own total scattering
     n_cap: int = 16                 # capped cylinder, barbell: Gauss-Legendre nodes over each end cap
+    thickness_face: float = 0.0     # core-shell cylinder: shell on the end faces; core-shell ellipsoid:
+                                    # shell along the axis (thickness: radial / equatorial shell)
 
     def as_dict(self):
         return asdict(self)

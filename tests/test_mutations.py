@@ -41,6 +41,10 @@ MUTATIONS = {
          "test_capped_oracle.py"),
     20: ("cap slices without their area factor rho^2 / R^2", "forward_scattering", "test_capped_oracle.py"),
     21: ("cap slices with the sphere's radius instead of the slice's", "eq1_shells", "test_capped_oracle.py"),
+    22: ("core-shell cylinder shell term without its face thickness", "rectangles", "test_shell_models_oracle.py"),
+    23: ("hollow cylinder with the hollow core added instead of removed", "hollow or rectangles",
+         "test_shell_models_oracle.py"),
+    24: ("core-shell ellipsoid shell without its polar thickness", "ellipsoid", "test_shell_models_oracle.py"),
 }
 
 
