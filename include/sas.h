@@ -59,7 +59,9 @@ enum { SAS_SPHERE = 0, SAS_CORE_SHELL = 1, SAS_CYLINDER = 2, SAS_ELLIPSOID = 3,
        /* no symmetry axis (Sec. II.B): sizes along the particle axes A, B, C */
        SAS_TRIAXIAL_ELLIPSOID = 4, SAS_PARALLELEPIPED = 5,
        /* cylinders with spherical end caps (Sec. III: the expensive models) */
-       SAS_CAPPED_CYLINDER = 6, SAS_BARBELL = 7 };
+       SAS_CAPPED_CYLINDER = 6, SAS_BARBELL = 7,
+       /* shelled uniaxial models (the cylinder and ellipsoid groups of Sec. II.B) */
+       SAS_CORE_SHELL_CYLINDER = 8, SAS_HOLLOW_CYLINDER = 9, SAS_CORE_SHELL_ELLIPSOID = 10 };
 /* largest Gauss-Legendre rule over an end cap */
 #define SAS_MAX_CAP_NODES 64
 enum { SAS_SQ_NONE = 0, SAS_SQ_HARD_SPHERE_PY = 1 };
@@ -97,7 +99,8 @@ typedef struct sas_instrument {
 typedef struct sas_model_desc {
     int64_t kind;            /* SAS_SPHERE, SAS_CORE_SHELL, SAS_CYLINDER, SAS_ELLIPSOID,
                                 SAS_TRIAXIAL_ELLIPSOID, SAS_PARALLELEPIPED, SAS_CAPPED_CYLINDER,
-                                SAS_BARBELL */
+                                SAS_BARBELL, SAS_CORE_SHELL_CYLINDER, SAS_HOLLOW_CYLINDER,
+                                SAS_CORE_SHELL_ELLIPSOID */
     int64_t sq_kind;         /* SAS_SQ_NONE or SAS_SQ_HARD_SPHERE_PY */
     int64_t precision;       /* SAS_FP32 (tallies FP32 Kahan + FP64 reduction) or SAS_FP64 */
     int64_t n_poly;          /* Schulz nodes of the polydisperse radius (1..64) */
@@ -176,6 +179,24 @@ typedef struct sas_model_desc {
      * radius_i / radius scales r, R and L alike. Axis laws as for the
      * cylinder; quadrature sampling only; radial_table does not apply. */
     int64_t n_cap;           /* slices per cap (1..SAS_MAX_CAP_NODES); other kinds ignore it */
+    /* Shelled uniaxial kinds (Eq. 1 region by region; the core radius
+     * `radius` is polydisperse, the other sizes fixed; a(x) = 2 J1(x)/x,
+     * f(x) = 3 (sin x - x cos x) / x^3):
+     * - core-shell cylinder: core (radius r, length L, sld) in a shell
+     *   (sld_shell) `thickness` t thick around it and `thickness_face` t_f
+     *   on each end face; F = (sld - sld_shell) pi r^2 L sinc(Q_C L/2) a(Q_AB r)
+     *   + (sld_shell - sld_solvent) V_o sinc(Q_C (L/2 + t_f)) a(Q_AB (r + t)),
+     *   V_o = pi (r + t)^2 (L + 2 t_f), normalised by <V_o>;
+     * - hollow cylinder: a tube of wall material (sld) between r and r + t
+     *   over the length L with solvent inside; F = (sld - sld_solvent)
+     *   sinc(Q_C L/2) [pi (r + t)^2 L a(Q_AB (r + t)) - pi r^2 L a(Q_AB r)],
+     *   normalised by the wall volume <pi ((r + t)^2 - r^2) L>;
+     * - core-shell ellipsoid of revolution: core radii (r, radius_polar r_p),
+     *   shell t at the equator and t_f at the poles; F = (sld - sld_shell)
+     *   V_c f(x_c) + (sld_shell - sld_solvent) V_o f(x_o), x^2 = (Q_AB r_e)^2
+     *   + (Q_C r_p)^2 for the core and the outer surface, V = 4/3 pi r_e^2 r_p,
+     *   normalised by <V_o>. */
+    double thickness_face;   /* core-shell cylinder: face shell; core-shell ellipsoid: polar shell (>= 0) */
 } sas_model_desc;
 
 typedef struct sas_experiment sas_experiment;   /* opaque, library-owned */

@@ -47,7 +47,8 @@ class sas_model_desc(ctypes.Structure):
                    "axis_phi", "sq_radius", "sq_fraction")] + \
                [(n, ctypes.c_int64) for n in ("sampling", "poly_dist", "radial_table")] + \
                [("radius_b", ctypes.c_double), ("axis_psi", ctypes.c_double), ("n_rot", ctypes.c_int64),
-                ("self_attenuation", ctypes.c_int64), ("n_cap", ctypes.c_int64)]
+                ("self_attenuation", ctypes.c_int64), ("n_cap", ctypes.c_int64),
+                ("thickness_face", ctypes.c_double)]
 
 
 class sas_launch_config(ctypes.Structure):

@@ -1,0 +1,7 @@
+// Instantiates the trace, records and evaluation kernels for the core-shell ellipsoid model.
+#include "sas_kernels.cuh"
+
+namespace sas {
+template struct Launcher<float, SAS_CORE_SHELL_ELLIPSOID>;
+template struct Launcher<double, SAS_CORE_SHELL_ELLIPSOID>;
+}  // namespace sas

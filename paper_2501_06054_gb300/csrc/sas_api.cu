@@ -72,6 +72,10 @@ double host_flops_per_history(const sas_model_desc& m, int np, int no)
         return no * (40.0 + nr * (60.0 + 30.0 * (double)m.n_cap)) + 150.0 +
                (m.sq_kind == SAS_SQ_HARD_SPHERE_PY ? 40.0 : 0.0);
     }
+    if (m.kind == SAS_CORE_SHELL_CYLINDER || m.kind == SAS_HOLLOW_CYLINDER)
+        return no * (60.0 + 26.0 + np * 2.0 * 26.0) + 150.0 + (m.sq_kind == SAS_SQ_HARD_SPHERE_PY ? 40.0 : 0.0);
+    if (m.kind == SAS_CORE_SHELL_ELLIPSOID)
+        return no * (60.0 + np * 2.0 * 38.0) + 150.0 + (m.sq_kind == SAS_SQ_HARD_SPHERE_PY ? 40.0 : 0.0);
     double per;
     if (m.kind == SAS_SPHERE) per = np * 36.0;
     else if (m.kind == SAS_CORE_SHELL) per = np * 62.0 + 20.0;
@@ -527,6 +531,24 @@ sas_status build_model_tables(const sas_model_desc& m, ModelTables& t, double q_
             p[1] = w[i] * d * d;
             p[2] = sc * sc;
             vmean += w[i] * V;
+        } else if (m.kind == SAS_CORE_SHELL_CYLINDER || m.kind == SAS_HOLLOW_CYLINDER) {
+            const bool hollow = m.kind == SAS_HOLLOW_CYLINDER;
+            const double ro = ri + m.thickness, tf = hollow ? 0.0 : m.thickness_face;
+            const double V1 = pi * ri * ri * m.length, V2 = pi * ro * ro * (m.length + 2.0 * tf);
+            const double d1 = hollow ? -(m.sld - m.sld_solvent) : m.sld - m.sld_shell;
+            const double d2 = hollow ? m.sld - m.sld_solvent : m.sld_shell - m.sld_solvent;
+            const double sw = std::sqrt(w[i]);
+            p[0] = ri * ri; p[1] = ro * ro; p[2] = sw * d1 * V1; p[3] = sw * d2 * V2;
+            p[4] = ri; p[5] = 1.0 / ri; p[6] = ro; p[7] = 1.0 / ro;
+            vmean += w[i] * (hollow ? pi * (ro * ro - ri * ri) * m.length : V2);
+        } else if (m.kind == SAS_CORE_SHELL_ELLIPSOID) {
+            const double ro = ri + m.thickness, rp = m.radius_polar, rpo = rp + m.thickness_face;
+            const double Vc = 4.0 / 3.0 * pi * ri * ri * rp, Vo = 4.0 / 3.0 * pi * ro * ro * rpo;
+            const double sw = std::sqrt(w[i]);
+            p[0] = ri * ri; p[1] = ro * ro;
+            p[2] = 3.0 * sw * (m.sld - m.sld_shell) * Vc;
+            p[3] = 3.0 * sw * (m.sld_shell - m.sld_solvent) * Vo;
+            vmean += w[i] * Vo;
         } else if (m.kind == SAS_TRIAXIAL_ELLIPSOID || m.kind == SAS_PARALLELEPIPED) {
             const double sc = ri / m.radius;   // one polydisperse factor for the three sizes
             const double V = (m.kind == SAS_TRIAXIAL_ELLIPSOID ? 4.0 / 3.0 * pi : 8.0) * m.radius * m.radius_b *
@@ -561,7 +583,8 @@ sas_status build_model_tables(const sas_model_desc& m, ModelTables& t, double q_
             }
         t.n_orient = 3 * nf;
     } else if (m.kind == SAS_CYLINDER || m.kind == SAS_ELLIPSOID || m.kind == SAS_CAPPED_CYLINDER ||
-               m.kind == SAS_BARBELL) {
+               m.kind == SAS_BARBELL || m.kind == SAS_CORE_SHELL_CYLINDER || m.kind == SAS_HOLLOW_CYLINDER ||
+               m.kind == SAS_CORE_SHELL_ELLIPSOID) {
         const int nmax = (int)(m.n_gamma * m.n_psi);
         std::vector<double> c((size_t)3 * std::max(nmax, 1)), wo(std::max(nmax, 1));
         const int no = m.isotropic == 2
@@ -702,14 +725,18 @@ ModelConst<T> model_const(const sas_model_desc& m, const ModelTables& t)
     for (int k = 0; k < SAS_SQ_NSER; ++k) c.sq_series[k] = (T)t.sq_series[k];
     c.event = m.sampling == SAS_PER_EVENT ? 1 : 0;
     c.orient_mode = (m.kind == SAS_CYLINDER || m.kind == SAS_ELLIPSOID || m.kind == SAS_CAPPED_CYLINDER ||
-                     m.kind == SAS_BARBELL) ? (int)m.isotropic : 0;
+                     m.kind == SAS_BARBELL || m.kind == SAS_CORE_SHELL_CYLINDER || m.kind == SAS_HOLLOW_CYLINDER ||
+                     m.kind == SAS_CORE_SHELL_ELLIPSOID) ? (int)m.isotropic : 0;
     c.ev_r = (T)m.radius;
     c.ev_p = (T)(m.poly_dist == SAS_POLY_GAUSSIAN ? m.poly : 0.0);
     const double lo = c.ev_p > (T)0 ? 0.5 * std::erfc(1.0 / (m.poly * std::sqrt(2.0))) : 0.0;
     c.ev_lo = (T)lo;
     c.ev_1mlo = (T)(1.0 - lo);
-    c.ev_c1 = (T)(m.kind == SAS_CORE_SHELL ? m.sld - m.sld_shell : m.sld - m.sld_solvent);
-    c.ev_c2 = (T)(m.kind == SAS_CORE_SHELL ? m.sld_shell - m.sld_solvent : 0.0);
+    const bool shelled = m.kind == SAS_CORE_SHELL || m.kind == SAS_CORE_SHELL_CYLINDER ||
+                         m.kind == SAS_CORE_SHELL_ELLIPSOID;
+    c.ev_c1 = (T)(shelled ? m.sld - m.sld_shell
+                          : m.kind == SAS_HOLLOW_CYLINDER ? -(m.sld - m.sld_solvent) : m.sld - m.sld_solvent);
+    c.ev_c2 = (T)(shelled ? m.sld_shell - m.sld_solvent : m.kind == SAS_HOLLOW_CYLINDER ? m.sld - m.sld_solvent : 0.0);
     c.ev_len = (T)m.length;
     c.ev_rp = (T)m.radius_polar;
     c.ev_axis[0] = (T)(std::sin(m.axis_theta) * std::cos(m.axis_phi));
@@ -728,6 +755,9 @@ ModelConst<T> model_const(const sas_model_desc& m, const ModelTables& t)
     c.n_rad = t.n_rad;
     c.n_tab = t.n_tab;
     c.n_cap = t.n_cap;
+    c.half_length_o = (T)(0.5 * m.length + (m.kind == SAS_CORE_SHELL_CYLINDER ? m.thickness_face : 0.0));
+    c.rp_o = (T)(m.radius_polar + (m.kind == SAS_CORE_SHELL_ELLIPSOID ? m.thickness_face : 0.0));
+    c.rp2o = c.rp_o * c.rp_o;
     c.cap_body = (T)t.cap_body;
     c.cap_r2 = (T)t.cap_r2;
     c.cap_rho2max = (T)t.cap_rho2max;
@@ -800,7 +830,16 @@ sas_status validate_instrument(const sas_instrument* in)
 sas_status validate_model(const sas_model_desc* m)
 {
     if (!m) return fail(SAS_ERR_ARG, "model is NULL");
-    if (m->kind < 0 || m->kind > 7) return fail(SAS_ERR_ARG, "unknown model kind");
+    if (m->kind < 0 || m->kind > 10) return fail(SAS_ERR_ARG, "unknown model kind");
+    if (m->kind == SAS_CORE_SHELL_CYLINDER || m->kind == SAS_HOLLOW_CYLINDER || m->kind == SAS_CORE_SHELL_ELLIPSOID) {
+        if (!std::isfinite(m->thickness_face) || m->thickness < 0.0 || m->thickness_face < 0.0)
+            return fail(SAS_ERR_ARG, "shell thicknesses must be finite and >= 0");
+        if (m->kind != SAS_CORE_SHELL_ELLIPSOID && !(m->length > 0.0)) return fail(SAS_ERR_ARG, "length must be > 0");
+        if (m->kind == SAS_HOLLOW_CYLINDER && !(m->thickness > 0.0))
+            return fail(SAS_ERR_ARG, "hollow cylinder needs a wall thickness > 0");
+        if (m->kind == SAS_CORE_SHELL_ELLIPSOID && !(m->radius_polar > 0.0))
+            return fail(SAS_ERR_ARG, "radius_polar must be > 0");
+    }
     if (m->kind == SAS_CAPPED_CYLINDER || m->kind == SAS_BARBELL) {
         if (!std::isfinite(m->length) || !std::isfinite(m->radius_polar) || m->length < 0.0 ||
             !(m->radius_polar >= m->radius))
@@ -903,6 +942,9 @@ cudaError_t dispatch_trace(sas_experiment* e, const TraceParams<T>& P, int* grid
     case SAS_PARALLELEPIPED: return Launcher<T, SAS_PARALLELEPIPED>::trace(P, e->cfg, e->sm_count, e->stream, grid);
     case SAS_CAPPED_CYLINDER: return Launcher<T, SAS_CAPPED_CYLINDER>::trace(P, e->cfg, e->sm_count, e->stream, grid);
     case SAS_BARBELL: return Launcher<T, SAS_BARBELL>::trace(P, e->cfg, e->sm_count, e->stream, grid);
+    case SAS_CORE_SHELL_CYLINDER: return Launcher<T, SAS_CORE_SHELL_CYLINDER>::trace(P, e->cfg, e->sm_count, e->stream, grid);
+    case SAS_HOLLOW_CYLINDER: return Launcher<T, SAS_HOLLOW_CYLINDER>::trace(P, e->cfg, e->sm_count, e->stream, grid);
+    case SAS_CORE_SHELL_ELLIPSOID: return Launcher<T, SAS_CORE_SHELL_ELLIPSOID>::trace(P, e->cfg, e->sm_count, e->stream, grid);
     default: return Launcher<T, SAS_ELLIPSOID>::trace(P, e->cfg, e->sm_count, e->stream, grid);
     }
 }
@@ -918,6 +960,9 @@ cudaError_t dispatch_records(sas_experiment* e, const TraceParams<T>& P)
     case SAS_PARALLELEPIPED: return Launcher<T, SAS_PARALLELEPIPED>::records(P, e->stream);
     case SAS_CAPPED_CYLINDER: return Launcher<T, SAS_CAPPED_CYLINDER>::records(P, e->stream);
     case SAS_BARBELL: return Launcher<T, SAS_BARBELL>::records(P, e->stream);
+    case SAS_CORE_SHELL_CYLINDER: return Launcher<T, SAS_CORE_SHELL_CYLINDER>::records(P, e->stream);
+    case SAS_HOLLOW_CYLINDER: return Launcher<T, SAS_HOLLOW_CYLINDER>::records(P, e->stream);
+    case SAS_CORE_SHELL_ELLIPSOID: return Launcher<T, SAS_CORE_SHELL_ELLIPSOID>::records(P, e->stream);
     default: return Launcher<T, SAS_ELLIPSOID>::records(P, e->stream);
     }
 }
@@ -935,6 +980,9 @@ cudaError_t dispatch_eval(sas_experiment* e, const ModelConst<T>& mc, const T* q
     case SAS_PARALLELEPIPED: return Launcher<T, SAS_PARALLELEPIPED>::eval(mc, poly, orient, q, out, n, e->stream);
     case SAS_CAPPED_CYLINDER: return Launcher<T, SAS_CAPPED_CYLINDER>::eval(mc, poly, orient, q, out, n, e->stream);
     case SAS_BARBELL: return Launcher<T, SAS_BARBELL>::eval(mc, poly, orient, q, out, n, e->stream);
+    case SAS_CORE_SHELL_CYLINDER: return Launcher<T, SAS_CORE_SHELL_CYLINDER>::eval(mc, poly, orient, q, out, n, e->stream);
+    case SAS_HOLLOW_CYLINDER: return Launcher<T, SAS_HOLLOW_CYLINDER>::eval(mc, poly, orient, q, out, n, e->stream);
+    case SAS_CORE_SHELL_ELLIPSOID: return Launcher<T, SAS_CORE_SHELL_ELLIPSOID>::eval(mc, poly, orient, q, out, n, e->stream);
     default: return Launcher<T, SAS_ELLIPSOID>::eval(mc, poly, orient, q, out, n, e->stream);
     }
 }

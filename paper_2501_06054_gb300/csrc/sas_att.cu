@@ -75,6 +75,13 @@ double model_extent(const sas_model_desc& m, const ModelTables& t)
     case SAS_ELLIPSOID: return 2.0 * std::fmax(r, m.radius_polar);
     case SAS_TRIAXIAL_ELLIPSOID:
         return 2.0 * (r / m.radius) * std::fmax(m.radius, std::fmax(m.radius_b, m.radius_polar));
+    case SAS_CORE_SHELL_CYLINDER:
+    case SAS_HOLLOW_CYLINDER: {   // the outer cylinder's diagonal
+        const double lo = m.length + (m.kind == SAS_CORE_SHELL_CYLINDER ? 2.0 * m.thickness_face : 0.0);
+        const double ro = r + m.thickness;
+        return std::sqrt(lo * lo + 4.0 * ro * ro);
+    }
+    case SAS_CORE_SHELL_ELLIPSOID: return 2.0 * std::fmax(r + m.thickness, m.radius_polar + m.thickness_face);
     case SAS_CAPPED_CYLINDER:
     case SAS_BARBELL:   // tip to tip, L + 2H, or the caps' diameter
         return (r / m.radius) * std::fmax(m.length + 2.0 * cap_height(m), 2.0 * m.radius_polar);
@@ -152,6 +159,9 @@ cudaError_t att_launch(const sas_model_desc& m, const ModelConst<T>& mc, const T
     case SAS_PARALLELEPIPED: return SAS_ATT_CASE(SAS_PARALLELEPIPED);
     case SAS_CAPPED_CYLINDER: return SAS_ATT_CASE(SAS_CAPPED_CYLINDER);
     case SAS_BARBELL: return SAS_ATT_CASE(SAS_BARBELL);
+    case SAS_CORE_SHELL_CYLINDER: return SAS_ATT_CASE(SAS_CORE_SHELL_CYLINDER);
+    case SAS_HOLLOW_CYLINDER: return SAS_ATT_CASE(SAS_HOLLOW_CYLINDER);
+    case SAS_CORE_SHELL_ELLIPSOID: return SAS_ATT_CASE(SAS_CORE_SHELL_ELLIPSOID);
     default: return SAS_ATT_CASE(SAS_ELLIPSOID);
     }
 #undef SAS_ATT_CASE

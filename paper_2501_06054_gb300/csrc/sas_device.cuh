@@ -519,6 +519,98 @@ __device__ __forceinline__ T avg_capped(const T qv[3], const T* __restrict__ pol
     return k.s;
 }
 
+// FP32 amplitude of one node of the shelled cylinders: the two nested
+// cylinders' terms k1 a(Q_AB r) + k2 a(Q_AB r_o), 2 J1(x)/x in the form of
+// tier TIER for both.
+template <int TIER>
+__device__ __forceinline__ float cs_cyl_amp(float k1, float k2, float qab2, float r2, float ro2)
+{
+    return fmaf(k1, cyl_a_tier<TIER>(qab2 * r2), k2 * cyl_a_tier<TIER>(qab2 * ro2));
+}
+
+// Core-shell and hollow cylinders (Eq. 1 region by region): per orientation
+// node and radius node {r^2, r_o^2, c_1, c_2, r, 1/r, r_o, 1/r_o},
+//   F = c_1 sinc(Q_C L/2) a(Q_AB r) + c_2 sinc(Q_C L_o/2) a(Q_AB r_o),
+// L_o = L + 2 t_f. FP32: the 2 J1(x)/x form chosen per node, uniformly over
+// the warp, from the warp's largest |Q|^2 times r_o^2.
+template <typename T>
+__device__ __forceinline__ T avg_cs_cylinder(const T qv[3], const T* __restrict__ poly, int np,
+                                             const T* __restrict__ orient, int no, const ModelConst<T>& mc)
+{
+    Kahan<T> k;
+    float qm = 0.f;
+    if constexpr (sizeof(T) == sizeof(float)) {
+        const float q2 = fma(qv[0], qv[0], fma(qv[1], qv[1], qv[2] * qv[2]));
+        qm = __uint_as_float(__reduce_max_sync(__activemask(), __float_as_uint(q2)));
+    }
+    for (int o = 0; o < no; ++o) {
+        const T* c = orient + 4 * o;
+        const T qc = fma(qv[0], c[0], fma(qv[1], c[1], qv[2] * c[2]));
+        const T x0 = fma(qv[1], c[2], -qv[2] * c[1]);
+        const T x1 = fma(qv[2], c[0], -qv[0] * c[2]);
+        const T x2 = fma(qv[0], c[1], -qv[1] * c[0]);
+        const T qab2 = fma(x0, x0, fma(x1, x1, x2 * x2));
+        const T y1 = fabs(qc) * mc.half_length, y2 = fabs(qc) * mc.half_length_o;
+        const T s1 = M<T>::sinc(y1, M<T>::rcp(y1)), s2 = M<T>::sinc(y2, M<T>::rcp(y2));
+        T inner = 0;
+        if constexpr (sizeof(T) == sizeof(float)) {
+            for (int i = 0; i < np; ++i) {
+                const float4 p = *reinterpret_cast<const float4*>(poly + SAS_POLY_STRIDE * i);   // r^2, r_o^2, c_1, c_2
+                const float k1 = s1 * p.z, k2 = s2 * p.w;
+                const float bound = qm * p.y;   // warp-uniform
+                float F;
+                if (bound <= SAS_J1R_SMAX) F = cs_cyl_amp<0>(k1, k2, qab2, p.x, p.y);
+                else if (bound <= SAS_J1V_SMAX) F = cs_cyl_amp<1>(k1, k2, qab2, p.x, p.y);
+                else if (bound <= SAS_J1P_SMAX) F = cs_cyl_amp<2>(k1, k2, qab2, p.x, p.y);
+                else if (bound <= SAS_J1Q_SMAX) F = cs_cyl_amp<3>(k1, k2, qab2, p.x, p.y);
+                else F = cs_cyl_amp<4>(k1, k2, qab2, p.x, p.y);
+                inner = fmaf(F, F, inner);
+            }
+        } else {
+            const T qab = M<T>::sqrt_(qab2), iq = M<T>::rcp(qab);
+            for (int i = 0; i < np; ++i) {
+                const T* p = poly + SAS_POLY_STRIDE * i;
+                const T F = s1 * p[2] * M<T>::cyl_a(qab * p[4], iq * p[5], 0) +
+                            s2 * p[3] * M<T>::cyl_a(qab * p[6], iq * p[7], 0);
+                inner = fma(F, F, inner);
+            }
+        }
+        k.add(c[3] * inner);
+    }
+    return k.s;
+}
+
+// Core-shell ellipsoid of revolution: per orientation node and radius node
+// {r_e^2, r_o^2, 3 c_1, 3 c_2}, F = 3 c_1 g(x_c) + 3 c_2 g(x_o) with
+// x^2 = r^2 Q_AB^2 + r_p^2 Q_C^2 for the core and the outer surface.
+template <typename T>
+__device__ __forceinline__ T avg_cs_ellipsoid(const T qv[3], const T* __restrict__ poly, int np,
+                                              const T* __restrict__ orient, int no, const ModelConst<T>& mc)
+{
+    Kahan<T> k;
+    for (int o = 0; o < no; ++o) {
+        const T* c = orient + 4 * o;
+        const T qc = fma(qv[0], c[0], fma(qv[1], c[1], qv[2] * c[2]));
+        const T x0 = fma(qv[1], c[2], -qv[2] * c[1]);
+        const T x1 = fma(qv[2], c[0], -qv[0] * c[2]);
+        const T x2 = fma(qv[0], c[1], -qv[1] * c[0]);
+        const T qab2 = fma(x0, x0, fma(x1, x1, x2 * x2));
+        const T qc2 = qc * qc;
+        const T pc = mc.rp2 * qc2, po = mc.rp2o * qc2;
+        T inner = 0;
+        for (int i = 0; i < np; ++i) {
+            const T* p = poly + SAS_POLY_STRIDE * i;
+            // floored so that Q = 0 gives x = 0 (the series branch), not 0 * inf
+            const T xc2 = fmax(fma(p[0], qab2, pc), (T)1e-30), xo2 = fmax(fma(p[1], qab2, po), (T)1e-30);
+            const T ic = M<T>::rsqrt(xc2), io = M<T>::rsqrt(xo2);
+            const T F = p[2] * M<T>::sphere_g(xc2 * ic, ic) + p[3] * M<T>::sphere_g(xo2 * io, io);
+            inner = fma(F, F, inner);
+        }
+        k.add(c[3] * inner);
+    }
+    return k.s;
+}
+
 // Particles without a symmetry axis (Eq. 1 for the body): per frame
 // (rows A, B, C of the orientation table, weight in row A) and polydisperse
 // scale s_i (poly node: s_i, coefficient):
@@ -605,6 +697,10 @@ __device__ __forceinline__ T dsigma(const T qv[3], const ModelConst<T>& mc,
         avg = avg_ellipsoid<T>(qv, poly, mc.n_poly, orient, mc.n_orient, mc.rp2);
     } else if (KIND == SAS_CAPPED_CYLINDER || KIND == SAS_BARBELL) {
         avg = avg_capped<T>(qv, poly, mc.n_rad, orient, mc.n_orient, mc);
+    } else if (KIND == SAS_CORE_SHELL_CYLINDER || KIND == SAS_HOLLOW_CYLINDER) {
+        avg = avg_cs_cylinder<T>(qv, poly, mc.n_rad, orient, mc.n_orient, mc);
+    } else if (KIND == SAS_CORE_SHELL_ELLIPSOID) {
+        avg = avg_cs_ellipsoid<T>(qv, poly, mc.n_rad, orient, mc.n_orient, mc);
     } else {
         avg = avg_axes3<T, KIND>(qv, poly, mc.n_rad, orient, mc.n_orient, mc);
     }
@@ -758,6 +854,30 @@ __device__ __forceinline__ T dsigma_event(const T qv[3], const ModelConst<T>& mc
                 }
             }
             const T F = mc.ev_c1 * sc * sc * sc * A;
+            F2 = F * F;
+        } else if constexpr (KIND == SAS_CORE_SHELL_CYLINDER || KIND == SAS_HOLLOW_CYLINDER) {
+            // nested cylinders of the drawn core radius r and r + t
+            const T ro = r + mc.shell;
+            const T y1 = fabs(qc) * mc.half_length, y2 = fabs(qc) * mc.half_length_o;
+            const T qab = M<T>::sqrt_(qab2);
+            const T xa = qab * r, xb = qab * ro;
+            T a1, a2;
+            if constexpr (sizeof(T) == 4) {
+                a1 = cyl_a_tier<4>(xa * xa);
+                a2 = cyl_a_tier<4>(xb * xb);
+            } else {
+                a1 = M<T>::cyl_a(xa, M<T>::rcp(xa), (T)0);
+                a2 = M<T>::cyl_a(xb, M<T>::rcp(xb), (T)0);
+            }
+            const T F = mc.ev_c1 * pi * r * r * mc.ev_len * M<T>::sinc(y1, M<T>::rcp(y1)) * a1 +
+                        mc.ev_c2 * pi * ro * ro * (T)2 * mc.half_length_o * M<T>::sinc(y2, M<T>::rcp(y2)) * a2;
+            F2 = F * F;
+        } else if constexpr (KIND == SAS_CORE_SHELL_ELLIPSOID) {
+            const T ro = r + mc.shell;
+            const T xc = M<T>::sqrt_(fma(r * r, qab2, mc.ev_rp * mc.ev_rp * qc * qc));
+            const T xo = M<T>::sqrt_(fma(ro * ro, qab2, mc.rp2o * qc * qc));
+            const T F = (T)4 * pi * (mc.ev_c1 * mc.ev_rp * r * r * M<T>::sphere_g(xc, M<T>::rcp(xc)) +
+                                     mc.ev_c2 * mc.rp_o * ro * ro * M<T>::sphere_g(xo, M<T>::rcp(xo)));
             F2 = F * F;
         } else if (KIND == SAS_CYLINDER) {
             const T y = fabs(qc) * (T)0.5 * mc.ev_len;
