@@ -315,10 +315,20 @@ CAPPED_DESC = {"capped_cylinder": "r=20, caps R=25, L=200 A, Schulz 0.1 (10 node
                           "nodes), 16 slices per bell, 128x128, FP32"}
 
 
+SHELLED_DESC = {
+    "core_shell_cylinder": "core-shell cylinder r=20, shell 5, faces 5, L=200 A, SLD 1/3/6 (x1e-6), Schulz 0.1 "
+                           "(10 nodes), Gaussian axis spread 15 deg (16x16 nodes), 128x128, FP32",
+    "hollow_cylinder": "hollow cylinder r=20, wall 5, L=200 A, Schulz 0.1 (10 nodes), Gaussian axis spread 15 deg "
+                       "(16x16 nodes), 128x128, FP32",
+    "core_shell_ellipsoid": "core-shell ellipsoid r=20, r_p=60, shells 5 A, SLD 1/3/6 (x1e-6), Schulz 0.1 "
+                            "(10 nodes), axis uniform on the sphere (16x16 nodes), 128x128, FP32"}
+
+
 def capped_models(stream):
     """Capped cylinder and barbell (the cylinder's amplitude plus n_cap disk
     slices per cap, Eq. 1): histories/s and slice terms/s (orientation nodes
-    x radius nodes x (n_cap + 1) per history)."""
+    x radius nodes x (n_cap + 1) per history); the shelled uniaxial models:
+    histories/s and (orientation x radius) node terms/s."""
     import paper_2501_06054_gb300 as sas
     from paper_2501_06054_gb300 import flops as F
     info = sas.sas_device_info()
@@ -338,6 +348,17 @@ def capped_models(stream):
                             "unit": UNIT, "histories_timed": n, "slice_terms_per_history": terms,
                             "slice_terms_per_s": rate * terms, "tflops_nominal": fl * rate / 1e12,
                             "frac_fp32_nominal": fl * rate / 1e12 / peak}
+    # the shelled uniaxial models: two nested bodies per radius node
+    for cfg in W.shelled_configs():
+        inst, m = cfg["instrument"], cfg["model"]
+        n = 40_000_000
+        e = sas.Experiment(inst, m, stream=stream)
+        e.trace(200_000, 1)
+        ms = _events_ms(lambda: e.trace(n, 1), stream)
+        e.close()
+        rate = n / (ms * 1e-3)
+        res[cfg["name"]] = {"workload": SHELLED_DESC[cfg["name"]], "value": rate, "unit": UNIT,
+                            "histories_timed": n, "node_terms_per_s": rate * m.n_gamma * m.n_psi * m.n_poly}
     return res
 
 

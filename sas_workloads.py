@@ -162,6 +162,24 @@ def barbell_config():
     return dict(name="barbell", instrument=instrument(), model=m, n_neutrons=10**8, seed=1)
 
 
+def shelled_configs():
+    """The shelled uniaxial models at one size each: core-shell cylinder
+    (r = 20, shell 5, faces 5, L = 200 A), hollow cylinder (r = 20, wall 5,
+    L = 200 A), both with a Gaussian axis spread of 15 deg, and the
+    core-shell ellipsoid (r = 20, r_p = 60, shells 5 A) with the axis uniform
+    on the sphere; Schulz 0.1 (10 nodes), 16x16 orientation nodes, SLDs
+    1, 3, 6 (x1e-6) for core, shell and solvent, 128x128, FP32."""
+    common = dict(precision=FP32, radius=20.0, thickness=5.0, sld=1.0e-6, sld_shell=3.0e-6, sld_solvent=6.0e-6,
+                  volume_fraction=0.01, poly=0.1, n_poly=10, n_gamma=16, n_psi=16)
+    cyl = dict(common, length=200.0, sigma_orient=math.radians(15.0), axis_theta=0.5 * math.pi, axis_phi=0.0)
+    return [dict(name="core_shell_cylinder", instrument=instrument(),
+                 model=Model(kind=CORE_SHELL_CYLINDER, thickness_face=5.0, **cyl)),
+            dict(name="hollow_cylinder", instrument=instrument(), model=Model(kind=HOLLOW_CYLINDER, **cyl)),
+            dict(name="core_shell_ellipsoid", instrument=instrument(),
+                 model=Model(kind=CORE_SHELL_ELLIPSOID, radius_polar=60.0, thickness_face=5.0,
+                             isotropic=ISOTROPIC, **common))]
+
+
 CONFIGS = {"sphere": sphere_config, "core_shell": core_shell_config,
            "cylinder": cylinder_config}
 
