@@ -84,7 +84,8 @@ class _Model(ctypes.Structure):
                [("event", ctypes.c_int64), ("orient_mode", ctypes.c_int64), ("poly", ctypes.c_double),
                 ("axis_theta", ctypes.c_double), ("axis_phi", ctypes.c_double),
                 ("radius_b", ctypes.c_double), ("axis_psi", ctypes.c_double),
-                ("self_att", ctypes.c_int64), ("n_cap", ctypes.c_int64), ("thickness_face", ctypes.c_double)]
+                ("self_att", ctypes.c_int64), ("n_cap", ctypes.c_int64), ("thickness_face", ctypes.c_double),
+                ("sld_face", ctypes.c_double)]
 
 
 def lib():
@@ -320,9 +321,9 @@ class Prepared:
         if kind in (4, 5):
             fr, self.orient_w = frame_nodes(m)
             self.orient_c = fr.reshape(-1, 9)
-        elif kind in (2, 3, 6, 7, 8, 9, 10) and iso == 2:
+        elif kind in (2, 3, 6, 7, 8, 9, 10, 11) and iso == 2:
             self.orient_c, self.orient_w = uniform_angle_nodes(int(m["n_gamma"]), int(m["n_psi"]))
-        elif kind in (2, 3, 6, 7, 8, 9, 10):
+        elif kind in (2, 3, 6, 7, 8, 9, 10, 11):
             self.orient_c, self.orient_w = orientation_nodes(
                 m["axis_theta"], m["axis_phi"], m["sigma_orient"], int(m["n_gamma"]),
                 int(m["n_psi"]), bool(iso))
@@ -347,7 +348,8 @@ class Prepared:
                         axis_theta=float(m["axis_theta"]), axis_phi=float(m["axis_phi"]),
                         radius_b=float(m.get("radius_b", 0.0)), axis_psi=float(m.get("axis_psi", 0.0)),
                         self_att=int(m.get("self_attenuation", 0)), n_cap=int(m.get("n_cap", 16)),
-                        thickness_face=float(m.get("thickness_face", 0.0)))
+                        thickness_face=float(m.get("thickness_face", 0.0)),
+                        sld_face=float(m.get("sld_face", 0.0)))
 
 
 def _inst(instrument):

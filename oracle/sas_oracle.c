@@ -90,7 +90,8 @@ typedef struct {
 typedef struct {
     int64_t kind;          /* 0 sphere, 1 core-shell, 2 cylinder, 3 ellipsoid, 4 triaxial
                               ellipsoid, 5 parallelepiped, 6 capped cylinder, 7 barbell,
-                              8 core-shell cylinder, 9 hollow cylinder, 10 core-shell ellipsoid */
+                              8 core-shell cylinder, 9 hollow cylinder, 10 core-shell ellipsoid,
+                              11 core-shell bicelle */
     int64_t sq_kind;       /* 0 none, 1 Percus-Yevick hard spheres */
     int64_t n_poly;        /* polydispersity nodes */
     int64_t n_orient;      /* orientation nodes */
@@ -126,6 +127,8 @@ typedef struct {
      * core-shell ellipsoid (kind 10): thickness of the shell along the axis
      * (`thickness` is the shell's radial / equatorial thickness) */
     double thickness_face;
+    /* core-shell bicelle (kind 11): density of the face layers */
+    double sld_face;
 } oracle_model;
 
 /* --------------------------------------------------------- model pieces */
@@ -395,6 +398,40 @@ double oracle_dsigma(const oracle_model *m, const double q[3])
             }
             sum += m->orient_w[o] * inner;
         }
+    } else if (m->kind == 11) {
+        /* core-shell bicelle: a core cylinder (r, L, rho_core) closed on each
+         * end face by a layer t_f thick of the core's radius (rho_face), the
+         * whole wrapped in a rim t thick over the full length L + 2 t_f
+         * (rho_rim = sld_shell). Nested cylinders C1 = (r, L),
+         * C2 = (r, L + 2 t_f), C3 = (r + t, L + 2 t_f), so by Eq. 1
+         *   F = (rho_c - rho_f) C1 + (rho_f - rho_r) C2 + (rho_r - rho_solv) C3,
+         * C = pi R^2 H sinc(Q_C H/2) a(Q_AB R); normalised by <V(C3)>. The
+         * core radius is polydisperse, t, t_f and L fixed. */
+        double t = m->thickness, L = m->length, tf = m->thickness_face, Lo = L + 2.0 * tf;
+        double dc = m->sld - m->sld_face, df = m->sld_face - m->sld_shell, dr = m->sld_shell - m->sld_solvent;
+        for (int64_t i = 0; i < np; ++i) {
+            double ro = m->poly_r[i] + t;
+            vmean += m->poly_w[i] * PI * ro * ro * Lo;
+        }
+        for (int64_t o = 0; o < m->n_orient; ++o) {
+            const double *c = m->orient_c + 3 * o;
+            double qc = q[0] * c[0] + q[1] * c[1] + q[2] * c[2];
+            double x0 = q[1] * c[2] - q[2] * c[1];
+            double x1 = q[2] * c[0] - q[0] * c[2];
+            double x2 = q[0] * c[1] - q[1] * c[0];
+            double qab = sqrt(x0 * x0 + x1 * x1 + x2 * x2);
+            double s1 = oracle_sinc(0.5 * qc * L), s2 = oracle_sinc(0.5 * qc * Lo);
+            double inner = 0.0;
+            for (int64_t i = 0; i < np; ++i) {
+                double r = m->poly_r[i], ro = r + t;
+                double ar = oracle_cyl_a(qab * r), ao = oracle_cyl_a(qab * ro);
+                double F = dc * PI * r * r * L * s1 * ar
+                         + df * PI * r * r * Lo * s2 * ar
+                         + dr * PI * ro * ro * Lo * (SAS_MUT == 25 ? s1 : s2) * ao;
+                inner += m->poly_w[i] * F * F;
+            }
+            sum += m->orient_w[o] * inner;
+        }
     } else if (m->kind == 10) {
         /* core-shell ellipsoid of revolution: core radii (r, r_p), the shell
          * adds t at the equator and t_p at the poles; by Eq. 1 with the
@@ -568,6 +605,8 @@ static double model_volume(const oracle_model *m, double r)
         return PI * ro * ro * (m->length + 2.0 * m->thickness_face);
     }
     if (m->kind == 9) return PI * ((r + m->thickness) * (r + m->thickness) - r * r) * m->length;
+    if (m->kind == 11)
+        return PI * (r + m->thickness) * (r + m->thickness) * (m->length + 2.0 * m->thickness_face);
     if (m->kind == 10)
         return 4.0 / 3.0 * PI * (r + m->thickness) * (r + m->thickness) * (m->radius_polar + m->thickness_face);
     if (m->kind == 6 || m->kind == 7) {
@@ -691,7 +730,8 @@ double oracle_model_extent(const oracle_model *m)
         double H = m->kind == 6 ? r0 * r0 / (R + h) : R + h;
         return f * fmax(m->length + 2.0 * H, 2.0 * R);
     }
-    case 8: {
+    case 8:
+    case 11: {
         double lo = m->length + 2.0 * m->thickness_face, ro = r + m->thickness;
         return sqrt(lo * lo + 4.0 * ro * ro);
     }

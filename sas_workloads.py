@@ -37,12 +37,13 @@ import numpy as np
 SPHERE, CORE_SHELL, CYLINDER, ELLIPSOID = 0, 1, 2, 3
 TRIAXIAL_ELLIPSOID, PARALLELEPIPED = 4, 5        # no symmetry axis: sizes along A, B, C
 CAPPED_CYLINDER, BARBELL = 6, 7                  # cylinder with spherical end caps (radius_polar)
-CORE_SHELL_CYLINDER, HOLLOW_CYLINDER, CORE_SHELL_ELLIPSOID = 8, 9, 10
+CORE_SHELL_CYLINDER, HOLLOW_CYLINDER, CORE_SHELL_ELLIPSOID, CORE_SHELL_BICELLE = 8, 9, 10, 11
 MODEL_NAMES = {SPHERE: "sphere", CORE_SHELL: "core_shell", CYLINDER: "cylinder",
                ELLIPSOID: "ellipsoid", TRIAXIAL_ELLIPSOID: "triaxial_ellipsoid",
                PARALLELEPIPED: "parallelepiped", CAPPED_CYLINDER: "capped_cylinder",
                BARBELL: "barbell", CORE_SHELL_CYLINDER: "core_shell_cylinder",
-               HOLLOW_CYLINDER: "hollow_cylinder", CORE_SHELL_ELLIPSOID: "core_shell_ellipsoid"}
+               HOLLOW_CYLINDER: "hollow_cylinder", CORE_SHELL_ELLIPSOID: "core_shell_ellipsoid",
+               CORE_SHELL_BICELLE: "core_shell_bicelle"}
 SQ_NONE, SQ_HARD_SPHERE_PY = 0, 1
 FP32, FP64 = 0, 1
 QUADRATURE, PER_EVENT = 0, 1              # sampling: averages over nodes / one draw per history
@@ -107,6 +108,7 @@ class Model:
     n_cap: int = 16                 # capped cylinder, barbell: Gauss-Legendre nodes over each end cap
     thickness_face: float = 0.0     # core-shell cylinder: shell on the end faces; core-shell ellipsoid:
                                     # shell along the axis (thickness: radial / equatorial shell)
+    sld_face: float = 0.0           # core-shell bicelle: SLD of the face layers (sld_shell is the rim's)
 
     def as_dict(self):
         return asdict(self)

@@ -45,6 +45,7 @@ MUTATIONS = {
     23: ("hollow cylinder with the hollow core added instead of removed", "hollow or rectangles",
          "test_shell_models_oracle.py"),
     24: ("core-shell ellipsoid shell without its polar thickness", "ellipsoid", "test_shell_models_oracle.py"),
+    25: ("bicelle rim over the core's length only", "bicelle", "test_shell_models_oracle.py"),
 }
 
 

@@ -1,12 +1,14 @@
 """Pins of the oracle's shelled uniaxial models: the core-shell cylinder
 (core r x L, shell t around it and t_f on the end faces), the hollow
-cylinder (a tube of wall material between r and r + t, solvent inside) and
+cylinder (a tube of wall material between r and r + t, solvent inside),
 the core-shell ellipsoid of revolution (core radii r, r_p; shell t at the
-equator and t_p at the poles).
+equator and t_p at the poles) and the core-shell bicelle (core r x L, face
+layers t_f of the core's radius, a rim t around both over L + 2 t_f).
 
 * reductions to the plain models: no shell, a shell of the core's density,
   a hollow cylinder as a core-shell cylinder with a solvent core, the
-  core-shell ellipsoid with r_p = r, t_p = t as the core-shell sphere;
+  core-shell ellipsoid with r_p = r, t_p = t as the core-shell sphere, the
+  bicelle with faces of the rim's density as the core-shell cylinder;
 * fixed axes against Eq. 1 integrated over the body by brute force: for the
   cylinders, disjoint (rho, z) rectangles of each density with the azimuth
   in closed form (2 pi J0) and Gauss-Legendre in rho and z; for the
@@ -145,6 +147,38 @@ def test_cylinders_against_eq1_rectangles(kind):
         assert ds * V == pytest.approx(F * F, rel=1e-9, abs=1e-12 * V * V), q
 
 
+def test_bicelle_reductions():
+    q = _q(40, 6)
+    kw = dict(radius=18.0, thickness=5.0, thickness_face=7.0, length=80.0, sld_solvent=0.5, poly=0.1, n_poly=10,
+              sigma_orient=0.3, n_gamma=8, n_psi=8)
+    # faces of the rim's density: the core-shell cylinder
+    a = _m(W.CORE_SHELL_BICELLE, sld=2.0, sld_shell=3.0, sld_face=3.0, **kw)
+    b = _m(W.CORE_SHELL_CYLINDER, sld=2.0, sld_shell=3.0, **kw)
+    assert np.allclose(oracle.dsigma(oracle.Prepared(a), q), oracle.dsigma(oracle.Prepared(b), q), rtol=1e-12)
+    # one density throughout: the plain cylinder of the outer sizes (monodisperse)
+    mono = dict(kw, poly=0.0, n_poly=1)
+    a = _m(W.CORE_SHELL_BICELLE, sld=2.0, sld_shell=2.0, sld_face=2.0, **mono)
+    b = _m(W.CYLINDER, radius=23.0, length=94.0, sld=2.0, sld_solvent=0.5, sigma_orient=0.3, n_gamma=8, n_psi=8)
+    assert np.allclose(oracle.dsigma(oracle.Prepared(a), q), oracle.dsigma(oracle.Prepared(b), q), rtol=1e-12)
+
+
+def test_bicelle_against_eq1_rectangles():
+    r, t, L, tf = 18.0, 6.0, 90.0, 8.0
+    rc, rr, rf, rv = 1.5, 4.0, 2.5, 0.5
+    m = _m(W.CORE_SHELL_BICELLE, radius=r, thickness=t, length=L, thickness_face=tf, sld=rc, sld_shell=rr,
+           sld_face=rf, sld_solvent=rv)
+    V = math.pi * (r + t) ** 2 * (L + 2 * tf)
+    prep = oracle.Prepared(m)
+    h = 0.5 * L
+    for q in _q(10, 7):
+        qz, qp = _axis_parts(q, 1.1, 0.6)
+        F = (rc - rv) * _rect(qz, qp, 0.0, r, -h, h)
+        F += (rf - rv) * 2.0 * _rect(qz, qp, 0.0, r, h, h + tf)          # face layers
+        F += (rr - rv) * _rect(qz, qp, r, r + t, -h - tf, h + tf)         # rim over the full length
+        ds = oracle.dsigma(prep, q[None, :])[0]
+        assert ds * V == pytest.approx(F * F, rel=1e-9, abs=1e-12 * V * V), q
+
+
 def test_core_shell_ellipsoid_against_eq1_ball():
     r, rp, t, tp = 15.0, 40.0, 5.0, 9.0
     rc, rs, rv = 1.0, 3.5, 0.5
@@ -160,10 +194,11 @@ def test_core_shell_ellipsoid_against_eq1_ball():
         assert ds * V == pytest.approx(F * F, rel=1e-9, abs=1e-12 * V * V), q
 
 
-@pytest.mark.parametrize("kind", [W.CORE_SHELL_CYLINDER, W.HOLLOW_CYLINDER, W.CORE_SHELL_ELLIPSOID])
+@pytest.mark.parametrize("kind", [W.CORE_SHELL_CYLINDER, W.HOLLOW_CYLINDER, W.CORE_SHELL_ELLIPSOID,
+                                  W.CORE_SHELL_BICELLE])
 def test_per_event_draws_average_to_the_quadrature(kind):
     base = dict(kind=kind, radius=12.0, thickness=4.0, thickness_face=6.0, length=60.0, radius_polar=30.0,
-                sld=1e-6, sld_shell=3e-6, sld_solvent=0.0, volume_fraction=0.01, poly=0.15,
+                sld=1e-6, sld_shell=3e-6, sld_face=2e-6, sld_solvent=0.0, volume_fraction=0.01, poly=0.15,
                 poly_dist=W.GAUSSIAN, n_poly=32, isotropic=W.ISOTROPIC, n_gamma=32, n_psi=32)
     quad = W.Model(**base, sampling=W.QUADRATURE)
     ev = W.Model(**base, sampling=W.PER_EVENT)
