@@ -321,7 +321,10 @@ SHELLED_DESC = {
     "hollow_cylinder": "hollow cylinder r=20, wall 5, L=200 A, Schulz 0.1 (10 nodes), Gaussian axis spread 15 deg "
                        "(16x16 nodes), 128x128, FP32",
     "core_shell_ellipsoid": "core-shell ellipsoid r=20, r_p=60, shells 5 A, SLD 1/3/6 (x1e-6), Schulz 0.1 "
-                            "(10 nodes), axis uniform on the sphere (16x16 nodes), 128x128, FP32"}
+                            "(10 nodes), axis uniform on the sphere (16x16 nodes), 128x128, FP32",
+    "core_shell_bicelle": "core-shell bicelle r=20, rim 5, faces 5, L=200 A, SLD core/face/rim/solvent 1/2/3/6 "
+                          "(x1e-6), Schulz 0.1 (10 nodes), Gaussian axis spread 15 deg (16x16 nodes), 128x128, "
+                          "FP32"}
 
 
 def capped_models(stream):

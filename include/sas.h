@@ -61,7 +61,8 @@ enum { SAS_SPHERE = 0, SAS_CORE_SHELL = 1, SAS_CYLINDER = 2, SAS_ELLIPSOID = 3,
        /* cylinders with spherical end caps (Sec. III: the expensive models) */
        SAS_CAPPED_CYLINDER = 6, SAS_BARBELL = 7,
        /* shelled uniaxial models (the cylinder and ellipsoid groups of Sec. II.B) */
-       SAS_CORE_SHELL_CYLINDER = 8, SAS_HOLLOW_CYLINDER = 9, SAS_CORE_SHELL_ELLIPSOID = 10 };
+       SAS_CORE_SHELL_CYLINDER = 8, SAS_HOLLOW_CYLINDER = 9, SAS_CORE_SHELL_ELLIPSOID = 10,
+       SAS_CORE_SHELL_BICELLE = 11 };
 /* largest Gauss-Legendre rule over an end cap */
 #define SAS_MAX_CAP_NODES 64
 enum { SAS_SQ_NONE = 0, SAS_SQ_HARD_SPHERE_PY = 1 };
@@ -100,7 +101,7 @@ typedef struct sas_model_desc {
     int64_t kind;            /* SAS_SPHERE, SAS_CORE_SHELL, SAS_CYLINDER, SAS_ELLIPSOID,
                                 SAS_TRIAXIAL_ELLIPSOID, SAS_PARALLELEPIPED, SAS_CAPPED_CYLINDER,
                                 SAS_BARBELL, SAS_CORE_SHELL_CYLINDER, SAS_HOLLOW_CYLINDER,
-                                SAS_CORE_SHELL_ELLIPSOID */
+                                SAS_CORE_SHELL_ELLIPSOID, SAS_CORE_SHELL_BICELLE */
     int64_t sq_kind;         /* SAS_SQ_NONE or SAS_SQ_HARD_SPHERE_PY */
     int64_t precision;       /* SAS_FP32 (tallies FP32 Kahan + FP64 reduction) or SAS_FP64 */
     int64_t n_poly;          /* Schulz nodes of the polydisperse radius (1..64) */
@@ -195,8 +196,16 @@ typedef struct sas_model_desc {
      *   shell t at the equator and t_f at the poles; F = (sld - sld_shell)
      *   V_c f(x_c) + (sld_shell - sld_solvent) V_o f(x_o), x^2 = (Q_AB r_e)^2
      *   + (Q_C r_p)^2 for the core and the outer surface, V = 4/3 pi r_e^2 r_p,
-     *   normalised by <V_o>. */
-    double thickness_face;   /* core-shell cylinder: face shell; core-shell ellipsoid: polar shell (>= 0) */
+     *   normalised by <V_o>;
+     * - core-shell bicelle: core (r, L, sld) closed on each end face by a
+     *   layer `thickness_face` t_f thick of the core's radius (sld_face), the
+     *   whole wrapped in a rim `thickness` t thick over L + 2 t_f
+     *   (sld_shell); with the nested cylinders C(R, H) = pi R^2 H
+     *   sinc(Q_C H/2) a(Q_AB R): F = (sld - sld_face) C(r, L) + (sld_face -
+     *   sld_shell) C(r, L + 2 t_f) + (sld_shell - sld_solvent) C(r + t, L + 2 t_f),
+     *   normalised by <pi (r + t)^2 (L + 2 t_f)>. */
+    double thickness_face;   /* core-shell cylinder, bicelle: face layer; core-shell ellipsoid: polar shell (>= 0) */
+    double sld_face;         /* core-shell bicelle: SLD of the face layers */
 } sas_model_desc;
 
 typedef struct sas_experiment sas_experiment;   /* opaque, library-owned */

@@ -48,7 +48,7 @@ class sas_model_desc(ctypes.Structure):
                [(n, ctypes.c_int64) for n in ("sampling", "poly_dist", "radial_table")] + \
                [("radius_b", ctypes.c_double), ("axis_psi", ctypes.c_double), ("n_rot", ctypes.c_int64),
                 ("self_attenuation", ctypes.c_int64), ("n_cap", ctypes.c_int64),
-                ("thickness_face", ctypes.c_double)]
+                ("thickness_face", ctypes.c_double), ("sld_face", ctypes.c_double)]
 
 
 class sas_launch_config(ctypes.Structure):

@@ -72,7 +72,7 @@ double host_flops_per_history(const sas_model_desc& m, int np, int no)
         return no * (40.0 + nr * (60.0 + 30.0 * (double)m.n_cap)) + 150.0 +
                (m.sq_kind == SAS_SQ_HARD_SPHERE_PY ? 40.0 : 0.0);
     }
-    if (m.kind == SAS_CORE_SHELL_CYLINDER || m.kind == SAS_HOLLOW_CYLINDER)
+    if (shelled_cylinder(m.kind))
         return no * (60.0 + 26.0 + np * 2.0 * 26.0) + 150.0 + (m.sq_kind == SAS_SQ_HARD_SPHERE_PY ? 40.0 : 0.0);
     if (m.kind == SAS_CORE_SHELL_ELLIPSOID)
         return no * (60.0 + np * 2.0 * 38.0) + 150.0 + (m.sq_kind == SAS_SQ_HARD_SPHERE_PY ? 40.0 : 0.0);
@@ -489,6 +489,32 @@ double capped_volume(const sas_model_desc& m)
     return M_PI * m.radius * m.radius * m.length + 2.0 * M_PI * R * H * H * (1.0 - H / (3.0 * R));
 }
 
+// Shelled cylinders: the face layer t_f (0 for the hollow cylinder) and the
+// contrasts of the nested cylinders (r, L), (r, L + 2 t_f), (r + t, L),
+// (r + t, L + 2 t_f) in the amplitude (Eq. 1 region by region).
+bool shelled_cylinder(int64_t kind)
+{
+    return kind == SAS_CORE_SHELL_CYLINDER || kind == SAS_HOLLOW_CYLINDER || kind == SAS_CORE_SHELL_BICELLE;
+}
+
+double face_layer(const sas_model_desc& m) { return m.kind == SAS_HOLLOW_CYLINDER ? 0.0 : m.thickness_face; }
+
+void shelled_contrasts(const sas_model_desc& m, double d[4])
+{
+    d[0] = d[1] = d[2] = d[3] = 0.0;
+    if (m.kind == SAS_CORE_SHELL_CYLINDER) {        // core, then the shell around core and faces
+        d[0] = m.sld - m.sld_shell;
+        d[3] = m.sld_shell - m.sld_solvent;
+    } else if (m.kind == SAS_HOLLOW_CYLINDER) {     // the tube minus its solvent core
+        d[0] = -(m.sld - m.sld_solvent);
+        d[2] = m.sld - m.sld_solvent;
+    } else {                                        // bicelle: core, core + faces, core + faces + rim
+        d[0] = m.sld - m.sld_face;
+        d[1] = m.sld_face - m.sld_shell;
+        d[3] = m.sld_shell - m.sld_solvent;
+    }
+}
+
 // Tables of one model in FP64 (see sas_types.h for the layouts).
 sas_status build_model_tables(const sas_model_desc& m, ModelTables& t, double q_max)
 {
@@ -531,16 +557,17 @@ sas_status build_model_tables(const sas_model_desc& m, ModelTables& t, double q_
             p[1] = w[i] * d * d;
             p[2] = sc * sc;
             vmean += w[i] * V;
-        } else if (m.kind == SAS_CORE_SHELL_CYLINDER || m.kind == SAS_HOLLOW_CYLINDER) {
-            const bool hollow = m.kind == SAS_HOLLOW_CYLINDER;
-            const double ro = ri + m.thickness, tf = hollow ? 0.0 : m.thickness_face;
-            const double V1 = pi * ri * ri * m.length, V2 = pi * ro * ro * (m.length + 2.0 * tf);
-            const double d1 = hollow ? -(m.sld - m.sld_solvent) : m.sld - m.sld_shell;
-            const double d2 = hollow ? m.sld - m.sld_solvent : m.sld_shell - m.sld_solvent;
+        } else if (shelled_cylinder(m.kind)) {
+            // the nested cylinders (r, L), (r, L_o), (r_o, L), (r_o, L_o)
+            const double ro = ri + m.thickness, L = m.length, Lo = L + 2.0 * face_layer(m);
+            const double V[4] = {pi * ri * ri * L, pi * ri * ri * Lo, pi * ro * ro * L, pi * ro * ro * Lo};
+            double d[4];
+            shelled_contrasts(m, d);
             const double sw = std::sqrt(w[i]);
-            p[0] = ri * ri; p[1] = ro * ro; p[2] = sw * d1 * V1; p[3] = sw * d2 * V2;
-            p[4] = ri; p[5] = 1.0 / ri; p[6] = ro; p[7] = 1.0 / ro;
-            vmean += w[i] * (hollow ? pi * (ro * ro - ri * ri) * m.length : V2);
+            p[0] = ri * ri; p[1] = ro * ro;
+            for (int k = 0; k < 4; ++k) p[2 + k] = sw * d[k] * V[k];
+            p[6] = ri; p[7] = ro;
+            vmean += w[i] * (m.kind == SAS_HOLLOW_CYLINDER ? pi * (ro * ro - ri * ri) * L : V[3]);
         } else if (m.kind == SAS_CORE_SHELL_ELLIPSOID) {
             const double ro = ri + m.thickness, rp = m.radius_polar, rpo = rp + m.thickness_face;
             const double Vc = 4.0 / 3.0 * pi * ri * ri * rp, Vo = 4.0 / 3.0 * pi * ro * ro * rpo;
@@ -583,8 +610,7 @@ sas_status build_model_tables(const sas_model_desc& m, ModelTables& t, double q_
             }
         t.n_orient = 3 * nf;
     } else if (m.kind == SAS_CYLINDER || m.kind == SAS_ELLIPSOID || m.kind == SAS_CAPPED_CYLINDER ||
-               m.kind == SAS_BARBELL || m.kind == SAS_CORE_SHELL_CYLINDER || m.kind == SAS_HOLLOW_CYLINDER ||
-               m.kind == SAS_CORE_SHELL_ELLIPSOID) {
+               m.kind == SAS_BARBELL || shelled_cylinder(m.kind) || m.kind == SAS_CORE_SHELL_ELLIPSOID) {
         const int nmax = (int)(m.n_gamma * m.n_psi);
         std::vector<double> c((size_t)3 * std::max(nmax, 1)), wo(std::max(nmax, 1));
         const int no = m.isotropic == 2
@@ -725,18 +751,17 @@ ModelConst<T> model_const(const sas_model_desc& m, const ModelTables& t)
     for (int k = 0; k < SAS_SQ_NSER; ++k) c.sq_series[k] = (T)t.sq_series[k];
     c.event = m.sampling == SAS_PER_EVENT ? 1 : 0;
     c.orient_mode = (m.kind == SAS_CYLINDER || m.kind == SAS_ELLIPSOID || m.kind == SAS_CAPPED_CYLINDER ||
-                     m.kind == SAS_BARBELL || m.kind == SAS_CORE_SHELL_CYLINDER || m.kind == SAS_HOLLOW_CYLINDER ||
-                     m.kind == SAS_CORE_SHELL_ELLIPSOID) ? (int)m.isotropic : 0;
+                     m.kind == SAS_BARBELL || shelled_cylinder(m.kind) || m.kind == SAS_CORE_SHELL_ELLIPSOID)
+                        ? (int)m.isotropic : 0;
     c.ev_r = (T)m.radius;
     c.ev_p = (T)(m.poly_dist == SAS_POLY_GAUSSIAN ? m.poly : 0.0);
     const double lo = c.ev_p > (T)0 ? 0.5 * std::erfc(1.0 / (m.poly * std::sqrt(2.0))) : 0.0;
     c.ev_lo = (T)lo;
     c.ev_1mlo = (T)(1.0 - lo);
-    const bool shelled = m.kind == SAS_CORE_SHELL || m.kind == SAS_CORE_SHELL_CYLINDER ||
-                         m.kind == SAS_CORE_SHELL_ELLIPSOID;
-    c.ev_c1 = (T)(shelled ? m.sld - m.sld_shell
-                          : m.kind == SAS_HOLLOW_CYLINDER ? -(m.sld - m.sld_solvent) : m.sld - m.sld_solvent);
-    c.ev_c2 = (T)(shelled ? m.sld_shell - m.sld_solvent : m.kind == SAS_HOLLOW_CYLINDER ? m.sld - m.sld_solvent : 0.0);
+    // contrasts of the per-event amplitudes (the shelled cylinders use ev_k)
+    const bool shelled = m.kind == SAS_CORE_SHELL || m.kind == SAS_CORE_SHELL_ELLIPSOID;
+    c.ev_c1 = (T)(shelled ? m.sld - m.sld_shell : m.sld - m.sld_solvent);
+    c.ev_c2 = (T)(shelled ? m.sld_shell - m.sld_solvent : 0.0);
     c.ev_len = (T)m.length;
     c.ev_rp = (T)m.radius_polar;
     c.ev_axis[0] = (T)(std::sin(m.axis_theta) * std::cos(m.axis_phi));
@@ -755,7 +780,12 @@ ModelConst<T> model_const(const sas_model_desc& m, const ModelTables& t)
     c.n_rad = t.n_rad;
     c.n_tab = t.n_tab;
     c.n_cap = t.n_cap;
-    c.half_length_o = (T)(0.5 * m.length + (m.kind == SAS_CORE_SHELL_CYLINDER ? m.thickness_face : 0.0));
+    c.half_length_o = (T)(0.5 * m.length + (shelled_cylinder(m.kind) ? face_layer(m) : 0.0));
+    if (shelled_cylinder(m.kind)) {
+        double d[4];
+        shelled_contrasts(m, d);
+        for (int k = 0; k < 4; ++k) c.ev_k[k] = (T)d[k];
+    }
     c.rp_o = (T)(m.radius_polar + (m.kind == SAS_CORE_SHELL_ELLIPSOID ? m.thickness_face : 0.0));
     c.rp2o = c.rp_o * c.rp_o;
     c.cap_body = (T)t.cap_body;
@@ -830,9 +860,10 @@ sas_status validate_instrument(const sas_instrument* in)
 sas_status validate_model(const sas_model_desc* m)
 {
     if (!m) return fail(SAS_ERR_ARG, "model is NULL");
-    if (m->kind < 0 || m->kind > 10) return fail(SAS_ERR_ARG, "unknown model kind");
-    if (m->kind == SAS_CORE_SHELL_CYLINDER || m->kind == SAS_HOLLOW_CYLINDER || m->kind == SAS_CORE_SHELL_ELLIPSOID) {
-        if (!std::isfinite(m->thickness_face) || m->thickness < 0.0 || m->thickness_face < 0.0)
+    if (m->kind < 0 || m->kind > 11) return fail(SAS_ERR_ARG, "unknown model kind");
+    if (shelled_cylinder(m->kind) || m->kind == SAS_CORE_SHELL_ELLIPSOID) {
+        if (!std::isfinite(m->thickness_face) || !std::isfinite(m->sld_face) || m->thickness < 0.0 ||
+            m->thickness_face < 0.0)
             return fail(SAS_ERR_ARG, "shell thicknesses must be finite and >= 0");
         if (m->kind != SAS_CORE_SHELL_ELLIPSOID && !(m->length > 0.0)) return fail(SAS_ERR_ARG, "length must be > 0");
         if (m->kind == SAS_HOLLOW_CYLINDER && !(m->thickness > 0.0))
@@ -945,6 +976,7 @@ cudaError_t dispatch_trace(sas_experiment* e, const TraceParams<T>& P, int* grid
     case SAS_CORE_SHELL_CYLINDER: return Launcher<T, SAS_CORE_SHELL_CYLINDER>::trace(P, e->cfg, e->sm_count, e->stream, grid);
     case SAS_HOLLOW_CYLINDER: return Launcher<T, SAS_HOLLOW_CYLINDER>::trace(P, e->cfg, e->sm_count, e->stream, grid);
     case SAS_CORE_SHELL_ELLIPSOID: return Launcher<T, SAS_CORE_SHELL_ELLIPSOID>::trace(P, e->cfg, e->sm_count, e->stream, grid);
+    case SAS_CORE_SHELL_BICELLE: return Launcher<T, SAS_CORE_SHELL_BICELLE>::trace(P, e->cfg, e->sm_count, e->stream, grid);
     default: return Launcher<T, SAS_ELLIPSOID>::trace(P, e->cfg, e->sm_count, e->stream, grid);
     }
 }
@@ -963,6 +995,7 @@ cudaError_t dispatch_records(sas_experiment* e, const TraceParams<T>& P)
     case SAS_CORE_SHELL_CYLINDER: return Launcher<T, SAS_CORE_SHELL_CYLINDER>::records(P, e->stream);
     case SAS_HOLLOW_CYLINDER: return Launcher<T, SAS_HOLLOW_CYLINDER>::records(P, e->stream);
     case SAS_CORE_SHELL_ELLIPSOID: return Launcher<T, SAS_CORE_SHELL_ELLIPSOID>::records(P, e->stream);
+    case SAS_CORE_SHELL_BICELLE: return Launcher<T, SAS_CORE_SHELL_BICELLE>::records(P, e->stream);
     default: return Launcher<T, SAS_ELLIPSOID>::records(P, e->stream);
     }
 }
@@ -983,6 +1016,7 @@ cudaError_t dispatch_eval(sas_experiment* e, const ModelConst<T>& mc, const T* q
     case SAS_CORE_SHELL_CYLINDER: return Launcher<T, SAS_CORE_SHELL_CYLINDER>::eval(mc, poly, orient, q, out, n, e->stream);
     case SAS_HOLLOW_CYLINDER: return Launcher<T, SAS_HOLLOW_CYLINDER>::eval(mc, poly, orient, q, out, n, e->stream);
     case SAS_CORE_SHELL_ELLIPSOID: return Launcher<T, SAS_CORE_SHELL_ELLIPSOID>::eval(mc, poly, orient, q, out, n, e->stream);
+    case SAS_CORE_SHELL_BICELLE: return Launcher<T, SAS_CORE_SHELL_BICELLE>::eval(mc, poly, orient, q, out, n, e->stream);
     default: return Launcher<T, SAS_ELLIPSOID>::eval(mc, poly, orient, q, out, n, e->stream);
     }
 }

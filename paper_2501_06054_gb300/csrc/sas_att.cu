@@ -76,8 +76,9 @@ double model_extent(const sas_model_desc& m, const ModelTables& t)
     case SAS_TRIAXIAL_ELLIPSOID:
         return 2.0 * (r / m.radius) * std::fmax(m.radius, std::fmax(m.radius_b, m.radius_polar));
     case SAS_CORE_SHELL_CYLINDER:
+    case SAS_CORE_SHELL_BICELLE:
     case SAS_HOLLOW_CYLINDER: {   // the outer cylinder's diagonal
-        const double lo = m.length + (m.kind == SAS_CORE_SHELL_CYLINDER ? 2.0 * m.thickness_face : 0.0);
+        const double lo = m.length + 2.0 * face_layer(m);
         const double ro = r + m.thickness;
         return std::sqrt(lo * lo + 4.0 * ro * ro);
     }
@@ -162,6 +163,7 @@ cudaError_t att_launch(const sas_model_desc& m, const ModelConst<T>& mc, const T
     case SAS_CORE_SHELL_CYLINDER: return SAS_ATT_CASE(SAS_CORE_SHELL_CYLINDER);
     case SAS_HOLLOW_CYLINDER: return SAS_ATT_CASE(SAS_HOLLOW_CYLINDER);
     case SAS_CORE_SHELL_ELLIPSOID: return SAS_ATT_CASE(SAS_CORE_SHELL_ELLIPSOID);
+    case SAS_CORE_SHELL_BICELLE: return SAS_ATT_CASE(SAS_CORE_SHELL_BICELLE);
     default: return SAS_ATT_CASE(SAS_ELLIPSOID);
     }
 #undef SAS_ATT_CASE

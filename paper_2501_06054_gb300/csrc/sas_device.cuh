@@ -528,11 +528,12 @@ __device__ __forceinline__ float cs_cyl_amp(float k1, float k2, float qab2, floa
     return fmaf(k1, cyl_a_tier<TIER>(qab2 * r2), k2 * cyl_a_tier<TIER>(qab2 * ro2));
 }
 
-// Core-shell and hollow cylinders (Eq. 1 region by region): per orientation
-// node and radius node {r^2, r_o^2, c_1, c_2, r, 1/r, r_o, 1/r_o},
-//   F = c_1 sinc(Q_C L/2) a(Q_AB r) + c_2 sinc(Q_C L_o/2) a(Q_AB r_o),
-// L_o = L + 2 t_f. FP32: the 2 J1(x)/x form chosen per node, uniformly over
-// the warp, from the warp's largest |Q|^2 times r_o^2.
+// Core-shell and hollow cylinders, core-shell bicelle (Eq. 1 region by
+// region, four nested cylinders): per orientation node and radius node
+// {r^2, r_o^2, c_1, c_2, c_3, c_4, r, r_o},
+//   F = (c_1 s_L + c_2 s_Lo) a(Q_AB r) + (c_3 s_L + c_4 s_Lo) a(Q_AB r_o),
+// s_H = sinc(Q_C H/2), L_o = L + 2 t_f. FP32: the 2 J1(x)/x form chosen per
+// node, uniformly over the warp, from the warp's largest |Q|^2 times r_o^2.
 template <typename T>
 __device__ __forceinline__ T avg_cs_cylinder(const T qv[3], const T* __restrict__ poly, int np,
                                              const T* __restrict__ orient, int no, const ModelConst<T>& mc)
@@ -555,8 +556,9 @@ __device__ __forceinline__ T avg_cs_cylinder(const T qv[3], const T* __restrict_
         T inner = 0;
         if constexpr (sizeof(T) == sizeof(float)) {
             for (int i = 0; i < np; ++i) {
-                const float4 p = *reinterpret_cast<const float4*>(poly + SAS_POLY_STRIDE * i);   // r^2, r_o^2, c_1, c_2
-                const float k1 = s1 * p.z, k2 = s2 * p.w;
+                const float4 p = *reinterpret_cast<const float4*>(poly + SAS_POLY_STRIDE * i);      // r^2, r_o^2, c_1, c_2
+                const float4 pc = *reinterpret_cast<const float4*>(poly + SAS_POLY_STRIDE * i + 4); // c_3, c_4, r, r_o
+                const float k1 = fmaf(s1, p.z, s2 * p.w), k2 = fmaf(s1, pc.x, s2 * pc.y);
                 const float bound = qm * p.y;   // warp-uniform
                 float F;
                 if (bound <= SAS_J1R_SMAX) F = cs_cyl_amp<0>(k1, k2, qab2, p.x, p.y);
@@ -570,8 +572,9 @@ __device__ __forceinline__ T avg_cs_cylinder(const T qv[3], const T* __restrict_
             const T qab = M<T>::sqrt_(qab2), iq = M<T>::rcp(qab);
             for (int i = 0; i < np; ++i) {
                 const T* p = poly + SAS_POLY_STRIDE * i;
-                const T F = s1 * p[2] * M<T>::cyl_a(qab * p[4], iq * p[5], 0) +
-                            s2 * p[3] * M<T>::cyl_a(qab * p[6], iq * p[7], 0);
+                const T xa = qab * p[6], xb = qab * p[7];
+                const T F = fma(s1, p[2], s2 * p[3]) * M<T>::cyl_a(xa, iq / p[6], 0) +
+                            fma(s1, p[4], s2 * p[5]) * M<T>::cyl_a(xb, iq / p[7], 0);
                 inner = fma(F, F, inner);
             }
         }
@@ -697,7 +700,7 @@ __device__ __forceinline__ T dsigma(const T qv[3], const ModelConst<T>& mc,
         avg = avg_ellipsoid<T>(qv, poly, mc.n_poly, orient, mc.n_orient, mc.rp2);
     } else if (KIND == SAS_CAPPED_CYLINDER || KIND == SAS_BARBELL) {
         avg = avg_capped<T>(qv, poly, mc.n_rad, orient, mc.n_orient, mc);
-    } else if (KIND == SAS_CORE_SHELL_CYLINDER || KIND == SAS_HOLLOW_CYLINDER) {
+    } else if (KIND == SAS_CORE_SHELL_CYLINDER || KIND == SAS_HOLLOW_CYLINDER || KIND == SAS_CORE_SHELL_BICELLE) {
         avg = avg_cs_cylinder<T>(qv, poly, mc.n_rad, orient, mc.n_orient, mc);
     } else if (KIND == SAS_CORE_SHELL_ELLIPSOID) {
         avg = avg_cs_ellipsoid<T>(qv, poly, mc.n_rad, orient, mc.n_orient, mc);
@@ -855,8 +858,9 @@ __device__ __forceinline__ T dsigma_event(const T qv[3], const ModelConst<T>& mc
             }
             const T F = mc.ev_c1 * sc * sc * sc * A;
             F2 = F * F;
-        } else if constexpr (KIND == SAS_CORE_SHELL_CYLINDER || KIND == SAS_HOLLOW_CYLINDER) {
-            // nested cylinders of the drawn core radius r and r + t
+        } else if constexpr (KIND == SAS_CORE_SHELL_CYLINDER || KIND == SAS_HOLLOW_CYLINDER ||
+                             KIND == SAS_CORE_SHELL_BICELLE) {
+            // the four nested cylinders of the drawn core radius r and r + t
             const T ro = r + mc.shell;
             const T y1 = fabs(qc) * mc.half_length, y2 = fabs(qc) * mc.half_length_o;
             const T qab = M<T>::sqrt_(qab2);
@@ -869,8 +873,10 @@ __device__ __forceinline__ T dsigma_event(const T qv[3], const ModelConst<T>& mc
                 a1 = M<T>::cyl_a(xa, M<T>::rcp(xa), (T)0);
                 a2 = M<T>::cyl_a(xb, M<T>::rcp(xb), (T)0);
             }
-            const T F = mc.ev_c1 * pi * r * r * mc.ev_len * M<T>::sinc(y1, M<T>::rcp(y1)) * a1 +
-                        mc.ev_c2 * pi * ro * ro * (T)2 * mc.half_length_o * M<T>::sinc(y2, M<T>::rcp(y2)) * a2;
+            const T sL = (T)2 * mc.half_length * M<T>::sinc(y1, M<T>::rcp(y1));
+            const T sLo = (T)2 * mc.half_length_o * M<T>::sinc(y2, M<T>::rcp(y2));
+            const T F = pi * (r * r * fma(mc.ev_k[0], sL, mc.ev_k[1] * sLo) * a1 +
+                              ro * ro * fma(mc.ev_k[2], sL, mc.ev_k[3] * sLo) * a2);
             F2 = F * F;
         } else if constexpr (KIND == SAS_CORE_SHELL_ELLIPSOID) {
             const T ro = r + mc.shell;

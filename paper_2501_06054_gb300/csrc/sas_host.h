@@ -60,6 +60,9 @@ template <typename T> ModelConst<T> model_const(const sas_model_desc& m, const M
 double model_extent(const sas_model_desc& m, const ModelTables& t);
 double cap_height(const sas_model_desc& m);
 double capped_volume(const sas_model_desc& m);
+bool shelled_cylinder(int64_t kind);
+double face_layer(const sas_model_desc& m);
+void shelled_contrasts(const sas_model_desc& m, double d[4]);
 void att_rule(const sas_instrument& in, const sas_model_desc& m, const ModelTables& t, AttRule& r);
 void att_fit(const AttRule& r, const double* mu, ModelTables& t);
 // evaluates mu_s (1/m) at the rule's wavelengths on the GPU (kernels of the

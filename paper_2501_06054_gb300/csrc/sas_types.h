@@ -52,10 +52,10 @@ struct AttPanel {
 //     ellipsoid  {r_e^2, 9 w (drho V)^2, 0...}
 //     capped cylinder, barbell {s, w (drho s^3)^2, s^2, 0...} (s = r_i / r),
 //                followed by the cap slices, two per row: {z_j, rho_j^2, c_j, 0}
-//     core-shell / hollow cylinder {r^2, r_o^2, c_1 = sqrt(w) d_1 V_1, c_2 = sqrt(w) d_2 V_2,
-//                r, 1/r, r_o, 1/r_o} (ascending r; core-shell: d_1 = rho_c - rho_s,
-//                V_1 = pi r^2 L, d_2 = rho_s - rho_solv, V_2 = pi r_o^2 (L + 2 t_f);
-//                hollow: d_1 = -(rho - rho_solv), d_2 = rho - rho_solv, t_f = 0)
+//     core-shell / hollow cylinder, bicelle {r^2, r_o^2, c_1, c_2, c_3, c_4, r, r_o}
+//                (ascending r): F = (c_1 s_L + c_2 s_Lo) a(Q_AB r) + (c_3 s_L + c_4 s_Lo) a(Q_AB r_o),
+//                s_H = sinc(Q_C H / 2), L_o = L + 2 t_f, c_k = sqrt(w) times the contrast
+//                times the volume of its nested cylinder (ModelConst ev_k: the contrasts)
 //     core-shell ellipsoid {r_e^2, r_o^2, 3 sqrt(w) (rho_c - rho_s) V_c,
 //                3 sqrt(w) (rho_s - rho_solv) V_o, 0...}
 //   orient table per node: {c_x, c_y, c_z, weight}
@@ -99,6 +99,7 @@ struct ModelConst {
     // shelled uniaxial kinds: the shell's half length L/2 + t_f (cylinders),
     // the outer polar radius r_p + t_p and its square (ellipsoid)
     T half_length_o, rp_o, rp2o;
+    T ev_k[4];       // shelled cylinders: the contrasts of c_1..c_4 (per-event amplitudes)
 };
 
 }  // namespace sas

@@ -169,8 +169,10 @@ def shelled_configs():
     (r = 20, shell 5, faces 5, L = 200 A), hollow cylinder (r = 20, wall 5,
     L = 200 A), both with a Gaussian axis spread of 15 deg, and the
     core-shell ellipsoid (r = 20, r_p = 60, shells 5 A) with the axis uniform
-    on the sphere; Schulz 0.1 (10 nodes), 16x16 orientation nodes, SLDs
-    1, 3, 6 (x1e-6) for core, shell and solvent, 128x128, FP32."""
+    on the sphere, and the core-shell bicelle (r = 20, rim 5, faces 5,
+    L = 200 A, face SLD 2e-6) with the cylinders' axis law; Schulz 0.1 (10
+    nodes), 16x16 orientation nodes, SLDs 1, 3, 6 (x1e-6) for core, shell
+    (rim) and solvent, 128x128, FP32."""
     common = dict(precision=FP32, radius=20.0, thickness=5.0, sld=1.0e-6, sld_shell=3.0e-6, sld_solvent=6.0e-6,
                   volume_fraction=0.01, poly=0.1, n_poly=10, n_gamma=16, n_psi=16)
     cyl = dict(common, length=200.0, sigma_orient=math.radians(15.0), axis_theta=0.5 * math.pi, axis_phi=0.0)
@@ -179,7 +181,10 @@ def shelled_configs():
             dict(name="hollow_cylinder", instrument=instrument(), model=Model(kind=HOLLOW_CYLINDER, **cyl)),
             dict(name="core_shell_ellipsoid", instrument=instrument(),
                  model=Model(kind=CORE_SHELL_ELLIPSOID, radius_polar=60.0, thickness_face=5.0,
-                             isotropic=ISOTROPIC, **common))]
+                             isotropic=ISOTROPIC, **common)),
+            dict(name="core_shell_bicelle", instrument=instrument(),
+                 model=Model(kind=CORE_SHELL_BICELLE, thickness_face=5.0, **dict(cyl, sld_shell=3.0e-6),
+                             sld_face=2.0e-6))]
 
 
 CONFIGS = {"sphere": sphere_config, "core_shell": core_shell_config,

@@ -1,5 +1,5 @@
 """Shelled uniaxial models (core-shell cylinder, hollow cylinder, core-shell
-ellipsoid; Eq. 1 region by region) on the GPU against the FP64 oracle:
+ellipsoid, core-shell bicelle; Eq. 1 region by region) on the GPU against the FP64 oracle:
 model evaluations over every form of 2 J1(x)/x, records (quadrature and
 per-event draws), detectors, a batch, the self-attenuation table and the
 refusals. Pixels and counts bit-exact; weights of records and detectors at
@@ -57,6 +57,13 @@ MODELS = {
                          thickness_face=8.0, sld_shell=4.0e-6, sld_solvent=2.0e-6, poly=0.0, n_poly=1),
     "csell_opposite_fp64": _m(W.CORE_SHELL_ELLIPSOID, precision=W.FP64, sld_shell=4.0e-6, sld_solvent=2.0e-6,
                               isotropic=W.ISOTROPIC, n_gamma=8, n_psi=8),
+    "bicelle_cap": _m(W.CORE_SHELL_BICELLE, sld_face=2.0e-6, sigma_orient=0.25, n_gamma=8, n_psi=8),
+    "bicelle_opposite_fp64": _m(W.CORE_SHELL_BICELLE, precision=W.FP64, sld=4.0e-6, sld_face=1.0e-6,
+                                sld_shell=5.0e-6, sld_solvent=2.0e-6, isotropic=W.ISOTROPIC, n_gamma=8, n_psi=8),
+    "bicelle_opposite": _m(W.CORE_SHELL_BICELLE, sld=4.0e-6, sld_face=1.0e-6, sld_shell=5.0e-6,
+                           sld_solvent=2.0e-6, poly=0.0, n_poly=1),
+    "bicelle_event": _m(W.CORE_SHELL_BICELLE, sld_face=2.0e-6, poly=0.2, poly_dist=W.GAUSSIAN, n_poly=16,
+                        isotropic=W.UNIFORM_ANGLES, sampling=W.PER_EVENT),
     "cscyl_event": _m(W.CORE_SHELL_CYLINDER, poly=0.2, poly_dist=W.GAUSSIAN, n_poly=16, isotropic=W.ISOTROPIC,
                       sampling=W.PER_EVENT),
     "hollow_event_fp64": _m(W.HOLLOW_CYLINDER, precision=W.FP64, poly=0.15, poly_dist=W.GAUSSIAN, n_poly=16,
@@ -94,6 +101,10 @@ def _p_s(m):
         vo = np.sum(prep.poly_w * ro ** 2)
         vw = np.sum(prep.poly_w * (ro ** 2 - prep.poly_r ** 2))
         return oracle.dsigma(prep, np.zeros((1, 3)))[0] * vo / vw
+    if m.kind == W.CORE_SHELL_BICELLE:
+        dc, df, dr = abs(m.sld - m.sld_face), abs(m.sld_face - m.sld_shell), abs(m.sld_shell - m.sld_solvent)
+        pos = W.Model(**dict(d, sld=dc + df + dr, sld_face=df + dr, sld_shell=dr, sld_solvent=0.0))
+        return oracle.dsigma(oracle.Prepared(pos), np.zeros((1, 3)))[0]
     d1, d2 = abs(m.sld - m.sld_shell), abs(m.sld_shell - m.sld_solvent)
     pos = W.Model(**dict(d, sld=d1 + d2, sld_shell=d2, sld_solvent=0.0))
     return oracle.dsigma(oracle.Prepared(pos), np.zeros((1, 3)))[0]
@@ -132,7 +143,7 @@ def _records(e, first, n, seed):
 
 @pytest.mark.parametrize("name", ["cscyl_cap", "cscyl_iso_fp64", "hollow_fixed", "hollow_angles_fp64",
                                   "csell_cap", "csell_iso_fp64", "cscyl_event", "hollow_event_fp64",
-                                  "csell_event"])
+                                  "csell_event", "bicelle_cap", "bicelle_opposite_fp64", "bicelle_event"])
 def test_records_parity(name):
     m = MODELS[name]
     inst = W.instrument(nx=64, ny=64)
@@ -156,7 +167,7 @@ def _check_detector(d, ref):
     assert np.all(np.abs(sw - so)[big] <= 1e-4 * so[big])
 
 
-@pytest.mark.parametrize("name", ["cscyl_cap", "hollow_fixed", "csell_cap", "csell_event"])
+@pytest.mark.parametrize("name", ["cscyl_cap", "hollow_fixed", "csell_cap", "csell_event", "bicelle_cap"])
 def test_trace_and_batch(name):
     m = MODELS[name]
     inst = W.instrument(nx=48, ny=48)
@@ -194,7 +205,8 @@ def test_self_attenuation_table():
                                       (W.CORE_SHELL_CYLINDER, dict(length=0.0)),
                                       (W.HOLLOW_CYLINDER, dict(thickness=0.0)),
                                       (W.CORE_SHELL_ELLIPSOID, dict(radius_polar=0.0)),
-                                      (W.CORE_SHELL_ELLIPSOID, dict(thickness_face=float("nan")))])
+                                      (W.CORE_SHELL_ELLIPSOID, dict(thickness_face=float("nan"))),
+                                      (W.CORE_SHELL_BICELLE, dict(sld_face=float("inf")))])
 def test_refusals(kind, bad):
     m = _m(kind, **bad)
     with pytest.raises(sas.SasError):
