@@ -318,7 +318,7 @@ class Prepared:
         kind = int(m["kind"])
         self.poly_r, self.poly_w = radius_nodes(m)
         iso = int(m["isotropic"])
-        if kind in (4, 5):
+        if kind in (4, 5, 12, 13):
             fr, self.orient_w = frame_nodes(m)
             self.orient_c = fr.reshape(-1, 9)
         elif kind in (2, 3, 6, 7, 8, 9, 10, 11) and iso == 2:

@@ -91,7 +91,8 @@ typedef struct {
     int64_t kind;          /* 0 sphere, 1 core-shell, 2 cylinder, 3 ellipsoid, 4 triaxial
                               ellipsoid, 5 parallelepiped, 6 capped cylinder, 7 barbell,
                               8 core-shell cylinder, 9 hollow cylinder, 10 core-shell ellipsoid,
-                              11 core-shell bicelle */
+                              11 core-shell bicelle, 12 elliptical cylinder,
+                              13 hollow rectangular prism */
     int64_t sq_kind;       /* 0 none, 1 Percus-Yevick hard spheres */
     int64_t n_poly;        /* polydispersity nodes */
     int64_t n_orient;      /* orientation nodes */
@@ -270,14 +271,26 @@ double oracle_dsigma(const oracle_model *m, const double q[3])
             }
             sum += m->orient_w[o] * inner;
         }
-    } else if (m->kind == 4 || m->kind == 5) {
+    } else if (m->kind == 4 || m->kind == 5 || m->kind == 12 || m->kind == 13) {
         /* triaxial ellipsoid (semi-axes a, b, c): F = drho V f(x),
          * x = |(a Q_A, b Q_B, c Q_C)|, V = 4/3 pi a b c (Eq. 1 on the affine
          * image of a sphere); rectangular parallelepiped (half-edges a, b, c):
-         * F = drho V sinc(a Q_A) sinc(b Q_B) sinc(c Q_C), V = 8 a b c. */
+         * F = drho V sinc(a Q_A) sinc(b Q_B) sinc(c Q_C), V = 8 a b c.
+         * Elliptical cylinder (12): cross-section semi-axes a, b along A, B,
+         * length L along C (c = L/2): F = drho V sinc(c Q_C) a(|(a Q_A, b Q_B)|),
+         * a(x) = 2 J1(x)/x (the affine image of the circular cylinder),
+         * V = pi a b L. Hollow rectangular prism (13): the parallelepiped of
+         * half-edges (a, b, c) less the inner one (a - t, b - t, c - t), walls
+         * t thick: F = drho [V sinc sinc sinc - V_i sinc_i sinc_i sinc_i],
+         * normalised by the wall volume V - V_i. */
         double drho = m->sld - m->sld_solvent;
-        double a0 = m->radius, b0 = m->radius_b, c0 = m->radius_polar;
-        double v0 = (m->kind == 4 ? 4.0 / 3.0 * PI : 8.0) * a0 * b0 * c0;
+        double a0 = m->radius, b0 = m->radius_b, c0 = m->kind == 12 ? 0.5 * m->length : m->radius_polar;
+        double t = m->kind == 13 ? m->thickness : 0.0;
+        double ai = a0 - t, bi = b0 - t, ci = c0 - t;
+        double vo = m->kind == 4 ? 4.0 / 3.0 * PI * a0 * b0 * c0
+                  : m->kind == 12 ? PI * a0 * b0 * 2.0 * c0 : 8.0 * a0 * b0 * c0;
+        double vi = m->kind == 13 ? 8.0 * ai * bi * ci : 0.0;
+        double v0 = vo - (SAS_MUT == 27 ? 0.0 : vi);
         for (int64_t i = 0; i < np; ++i) {
             double s = m->poly_r[i] / m->radius;
             vmean += m->poly_w[i] * v0 * s * s * s;
@@ -294,6 +307,13 @@ double oracle_dsigma(const oracle_model *m, const double q[3])
                 if (m->kind == 4) {
                     double xa = s * a0 * qa, xb = s * b0 * qb, xc = s * c0 * qc;
                     F = drho * V * oracle_sphere_f(sqrt(xa * xa + xb * xb + xc * xc));
+                } else if (m->kind == 12) {
+                    double xa = s * a0 * qa, xb = s * (SAS_MUT == 26 ? a0 : b0) * qb;
+                    F = drho * V * oracle_sinc(s * c0 * qc) * oracle_cyl_a(sqrt(xa * xa + xb * xb));
+                } else if (m->kind == 13) {
+                    double s3 = s * s * s;
+                    F = drho * s3 * (vo * oracle_sinc(s * a0 * qa) * oracle_sinc(s * b0 * qb) * oracle_sinc(s * c0 * qc)
+                                     - vi * oracle_sinc(s * ai * qa) * oracle_sinc(s * bi * qb) * oracle_sinc(s * ci * qc));
                 } else {
                     F = drho * V * oracle_sinc(s * a0 * qa) * oracle_sinc(s * b0 * (SAS_MUT == 13 ? qc : qb))
                       * oracle_sinc(s * c0 * (SAS_MUT == 13 ? qb : qc));
@@ -600,6 +620,15 @@ static double model_volume(const oracle_model *m, double r)
         double s = r / m->radius;
         return (m->kind == 4 ? 4.0 / 3.0 * PI : 8.0) * m->radius * m->radius_b * m->radius_polar * s * s * s;
     }
+    if (m->kind == 12) {
+        double s = r / m->radius;
+        return PI * m->radius * m->radius_b * m->length * s * s * s;
+    }
+    if (m->kind == 13) {
+        double s = r / m->radius, t = m->thickness;
+        return 8.0 * (m->radius * m->radius_b * m->radius_polar -
+                      (m->radius - t) * (m->radius_b - t) * (m->radius_polar - t)) * s * s * s;
+    }
     if (m->kind == 8) {
         double ro = r + m->thickness;
         return PI * ro * ro * (m->length + 2.0 * m->thickness_face);
@@ -632,7 +661,7 @@ double oracle_dsigma_event(const oracle_model *m, const double q[3], uint64_t se
     oracle_philox4x32_10(c2, key, x);
     double r = oracle_event_radius(m->radius, m->poly, x[0]);
     double c[9];
-    if (m->kind == 4 || m->kind == 5)
+    if (m->kind == 4 || m->kind == 5 || m->kind == 12 || m->kind == 13)
         oracle_event_frame(m->orient_mode, m->axis_theta, m->axis_phi, m->axis_psi, x[1], x[2], x[3], c);
     else
         oracle_event_axis(m->kind >= 2 ? m->orient_mode : 0, m->axis_theta, m->axis_phi, x[1], x[2], c);
@@ -737,6 +766,10 @@ double oracle_model_extent(const oracle_model *m)
     }
     case 9: return sqrt(m->length * m->length + 4.0 * (r + m->thickness) * (r + m->thickness));
     case 10: return 2.0 * fmax(r + m->thickness, m->radius_polar + m->thickness_face);
+    case 12: {
+        double f = r / m->radius, a = fmax(m->radius, m->radius_b);
+        return 2.0 * f * sqrt(a * a + 0.25 * m->length * m->length);
+    }
     default: {
         double f = r / m->radius;
         return 2.0 * f * sqrt(m->radius * m->radius + m->radius_b * m->radius_b +

@@ -38,12 +38,14 @@ SPHERE, CORE_SHELL, CYLINDER, ELLIPSOID = 0, 1, 2, 3
 TRIAXIAL_ELLIPSOID, PARALLELEPIPED = 4, 5        # no symmetry axis: sizes along A, B, C
 CAPPED_CYLINDER, BARBELL = 6, 7                  # cylinder with spherical end caps (radius_polar)
 CORE_SHELL_CYLINDER, HOLLOW_CYLINDER, CORE_SHELL_ELLIPSOID, CORE_SHELL_BICELLE = 8, 9, 10, 11
+ELLIPTICAL_CYLINDER, HOLLOW_RECTANGULAR_PRISM = 12, 13   # no symmetry axis, like the 3-axis kinds
 MODEL_NAMES = {SPHERE: "sphere", CORE_SHELL: "core_shell", CYLINDER: "cylinder",
                ELLIPSOID: "ellipsoid", TRIAXIAL_ELLIPSOID: "triaxial_ellipsoid",
                PARALLELEPIPED: "parallelepiped", CAPPED_CYLINDER: "capped_cylinder",
                BARBELL: "barbell", CORE_SHELL_CYLINDER: "core_shell_cylinder",
                HOLLOW_CYLINDER: "hollow_cylinder", CORE_SHELL_ELLIPSOID: "core_shell_ellipsoid",
-               CORE_SHELL_BICELLE: "core_shell_bicelle"}
+               CORE_SHELL_BICELLE: "core_shell_bicelle", ELLIPTICAL_CYLINDER: "elliptical_cylinder",
+               HOLLOW_RECTANGULAR_PRISM: "hollow_rectangular_prism"}
 SQ_NONE, SQ_HARD_SPHERE_PY = 0, 1
 FP32, FP64 = 0, 1
 QUADRATURE, PER_EVENT = 0, 1              # sampling: averages over nodes / one draw per history

@@ -46,6 +46,8 @@ MUTATIONS = {
          "test_shell_models_oracle.py"),
     24: ("core-shell ellipsoid shell without its polar thickness", "ellipsoid", "test_shell_models_oracle.py"),
     25: ("bicelle rim over the core's length only", "bicelle", "test_shell_models_oracle.py"),
+    26: ("elliptical cylinder with one semi-axis for both", "new_bodies_against", "test_triaxial_oracle.py"),
+    27: ("hollow prism normalised by its outer volume", "new_bodies_against", "test_triaxial_oracle.py"),
 }
 
 

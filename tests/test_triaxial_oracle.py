@@ -12,7 +12,11 @@ psi about it).
 * the isotropic average of the parallelepiped: Guinier radius
   Rg^2 = (a^2 + b^2 + c^2)/3 and independence of the direction of Q;
 * the per-event estimator (all three angles drawn) averages to the
-  quadrature over the same laws.
+  quadrature over the same laws;
+* the elliptical cylinder (semi-axes a, b, length L along C) with a = b is
+  the cylinder; it and the hollow rectangular prism (walls t thick) against
+  brute-force volume integrals (a mapped disk times the axis; six disjoint
+  wall boxes); their per-event means equal the quadrature.
 """
 import math
 
@@ -151,3 +155,90 @@ def test_per_event_frames_average_to_the_quadrature(kind, iso):
         ref = oracle.dsigma(oracle.Prepared(quad), q[:1])[0]
         z = (d.mean() - ref) / (d.std() / math.sqrt(n))
         assert abs(z) < 4.0, (kind, iso, qv, z)
+
+
+# ------------------------------------- elliptical cylinder, hollow prism
+
+def _brute_ellcyl_F(a, b, c, frame, q, n=40):
+    """Integral of exp(-i Q.r) over the elliptical cylinder |(x/a, y/b)| <= 1,
+    |z| <= c in the particle frame: the unit disk in polar coordinates
+    mapped by (a, b), z by Gauss-Legendre."""
+    x, w = np.polynomial.legendre.leggauss(n)
+    qa, qb, qc = frame @ q
+    rr = 0.5 * (x + 1.0)
+    wr = 0.5 * w * rr
+    ph = math.pi * (x + 1.0)
+    R, PH = np.meshgrid(rr, ph, indexing="ij")
+    W2 = np.outer(wr, math.pi * w) * a * b
+    arg = qa * a * R * np.cos(PH) + qb * b * R * np.sin(PH)
+    disk = np.sum(W2 * np.cos(arg)) + 1j * np.sum(W2 * np.sin(arg))
+    z = c * x
+    axial = np.sum(c * w * np.cos(qc * z)) + 1j * np.sum(c * w * np.sin(qc * z))
+    return abs(disk * axial) ** 2
+
+
+def _box_integral(qa, qb, qc, lo, hi, n=12):
+    """Integral of exp(-i Q.r) over the box lo <= r <= hi (Gauss-Legendre)."""
+    x, w = np.polynomial.legendre.leggauss(n)
+    out = 1.0 + 0j
+    for qk, l0, l1 in zip((qa, qb, qc), lo, hi):
+        u = 0.5 * (l0 + l1) + 0.5 * (l1 - l0) * x
+        out *= np.sum(0.5 * (l1 - l0) * w * np.exp(-1j * qk * u))
+    return out
+
+
+def _brute_hollow_prism_F(a, b, c, t, frame, q):
+    """The walls as six disjoint boxes: the two C faces over the full A x B,
+    the two B faces between them, the two A faces between those."""
+    qa, qb, qc = frame @ q
+    boxes = [((-a, -b, c - t), (a, b, c)), ((-a, -b, -c), (a, b, -c + t)),
+             ((-a, b - t, -c + t), (a, b, c - t)), ((-a, -b, -c + t), (a, -b + t, c - t)),
+             ((a - t, -b + t, -c + t), (a, b - t, c - t)), ((-a, -b + t, -c + t), (-a + t, b - t, c - t))]
+    F = sum(_box_integral(qa, qb, qc, lo, hi) for lo, hi in boxes)
+    return abs(F) ** 2
+
+
+def test_elliptical_cylinder_reduces_to_the_cylinder():
+    q = _q(40, 11)
+    for psi in (0.0, 1.1):
+        ell = W.Model(kind=W.ELLIPTICAL_CYLINDER, radius=20.0, radius_b=20.0, length=150.0, sld=2e-6,
+                      volume_fraction=0.01, axis_theta=1.0, axis_phi=0.4, axis_psi=psi, sigma_orient=0.3,
+                      n_gamma=10, n_psi=10)
+        cyl = W.Model(kind=W.CYLINDER, radius=20.0, length=150.0, sld=2e-6, volume_fraction=0.01, axis_theta=1.0,
+                      axis_phi=0.4, sigma_orient=0.3, n_gamma=10, n_psi=10)
+        assert np.allclose(oracle.dsigma(oracle.Prepared(ell), q), oracle.dsigma(oracle.Prepared(cyl), q),
+                           rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("kind", [W.ELLIPTICAL_CYLINDER, W.HOLLOW_RECTANGULAR_PRISM])
+def test_new_bodies_against_eq1_volume_integral(kind):
+    a, b, c, t, L = 12.0, 25.0, 35.0, 4.0, 90.0
+    th, ph, ps = 1.1, 0.6, 0.8
+    m = W.Model(kind=kind, radius=a, radius_b=b, radius_polar=c, length=L, thickness=t, sld=1.0,
+                sld_solvent=0.0, volume_fraction=1.0, axis_theta=th, axis_phi=ph, axis_psi=ps)
+    if kind == W.ELLIPTICAL_CYLINDER:
+        V = math.pi * a * b * L
+    else:
+        V = 8.0 * (a * b * c - (a - t) * (b - t) * (c - t))
+    fr = oracle.frame(th, ph, ps)
+    for q in _q(8, 13, scale=0.06):
+        ds = oracle.dsigma(oracle.Prepared(m), q[None, :])[0]
+        ref = _brute_ellcyl_F(a, b, 0.5 * L, fr, q) if kind == W.ELLIPTICAL_CYLINDER else \
+            _brute_hollow_prism_F(a, b, c, t, fr, q)
+        assert ds * V == pytest.approx(ref, rel=1e-9, abs=1e-12 * V * V)
+
+
+@pytest.mark.parametrize("kind", [W.ELLIPTICAL_CYLINDER, W.HOLLOW_RECTANGULAR_PRISM])
+def test_new_bodies_per_event_average_to_the_quadrature(kind):
+    base = dict(kind=kind, radius=10.0, radius_b=16.0, radius_polar=28.0, length=60.0, thickness=3.0, sld=2e-6,
+                volume_fraction=0.01, poly=0.15, poly_dist=W.GAUSSIAN, n_poly=32, isotropic=W.UNIFORM_ANGLES,
+                n_gamma=24, n_psi=24, n_rot=24)
+    quad = W.Model(**base, sampling=W.QUADRATURE)
+    ev = W.Model(**base, sampling=W.PER_EVENT)
+    n = 400000
+    for qv in ([0.02, 0.01, 0.0], [0.0, 0.04, 0.02]):
+        q = np.tile(np.array(qv), (n, 1))
+        d = oracle.dsigma_event(ev, q, seed=3, first=50)
+        ref = oracle.dsigma(oracle.Prepared(quad), q[:1])[0]
+        z = (d.mean() - ref) / (d.std() / math.sqrt(n))
+        assert abs(z) < 4.0, (kind, qv, z)
