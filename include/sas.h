@@ -62,7 +62,9 @@ enum { SAS_SPHERE = 0, SAS_CORE_SHELL = 1, SAS_CYLINDER = 2, SAS_ELLIPSOID = 3,
        SAS_CAPPED_CYLINDER = 6, SAS_BARBELL = 7,
        /* shelled uniaxial models (the cylinder and ellipsoid groups of Sec. II.B) */
        SAS_CORE_SHELL_CYLINDER = 8, SAS_HOLLOW_CYLINDER = 9, SAS_CORE_SHELL_ELLIPSOID = 10,
-       SAS_CORE_SHELL_BICELLE = 11 };
+       SAS_CORE_SHELL_BICELLE = 11,
+       /* no symmetry axis (Sec. II.B, the ellipsoid and parallelepiped groups) */
+       SAS_ELLIPTICAL_CYLINDER = 12, SAS_HOLLOW_RECTANGULAR_PRISM = 13 };
 /* largest Gauss-Legendre rule over an end cap */
 #define SAS_MAX_CAP_NODES 64
 enum { SAS_SQ_NONE = 0, SAS_SQ_HARD_SPHERE_PY = 1 };
@@ -101,7 +103,8 @@ typedef struct sas_model_desc {
     int64_t kind;            /* SAS_SPHERE, SAS_CORE_SHELL, SAS_CYLINDER, SAS_ELLIPSOID,
                                 SAS_TRIAXIAL_ELLIPSOID, SAS_PARALLELEPIPED, SAS_CAPPED_CYLINDER,
                                 SAS_BARBELL, SAS_CORE_SHELL_CYLINDER, SAS_HOLLOW_CYLINDER,
-                                SAS_CORE_SHELL_ELLIPSOID, SAS_CORE_SHELL_BICELLE */
+                                SAS_CORE_SHELL_ELLIPSOID, SAS_CORE_SHELL_BICELLE,
+                                SAS_ELLIPTICAL_CYLINDER, SAS_HOLLOW_RECTANGULAR_PRISM */
     int64_t sq_kind;         /* SAS_SQ_NONE or SAS_SQ_HARD_SPHERE_PY */
     int64_t precision;       /* SAS_FP32 (tallies FP32 Kahan + FP64 reduction) or SAS_FP64 */
     int64_t n_poly;          /* Schulz nodes of the polydisperse radius (1..64) */
@@ -149,7 +152,15 @@ typedef struct sas_model_desc {
      * for the uniaxial kinds (isotropic 0: the C axis in the Gaussian cap,
      * the mean frame carried along; 1: uniform rotations; 2: theta, phi and
      * psi uniform), with n_rot nodes in psi. The polydisperse factor
-     * radius_i / radius scales all three sizes. */
+     * radius_i / radius scales all three sizes. Two more bodies use the
+     * same frames: the elliptical cylinder, cross-section semi-axes
+     * (radius, radius_b) along (A, B) and `length` L along C,
+     * F = drho V sinc(Q_C L/2) 2 J1(x)/x, x = |(a Q_A, b Q_B)|, V = pi a b L;
+     * the hollow rectangular prism, half-edges (radius, radius_b,
+     * radius_polar) with walls `thickness` t thick (0 < t < every
+     * half-edge), F = drho [8 a b c sinc(a Q_A) sinc(b Q_B) sinc(c Q_C) - the
+     * same for the inner half-edges (a - t, b - t, c - t)], normalised by
+     * the wall volume. */
     double radius_b;         /* 3-axis kinds: size along B */
     double axis_psi;         /* 3-axis kinds: rotation of the frame about C, rad */
     int64_t n_rot;           /* 3-axis kinds: quadrature nodes in psi (1..128) */

@@ -60,10 +60,11 @@ double host_flops_per_history(const sas_model_desc& m, int np, int no)
     if (m.sampling == SAS_PER_EVENT) { np = 1; no = 1; }
     if (m.kind == SAS_CYLINDER && m.radial_table && m.sampling == SAS_QUADRATURE)
         return no * 60.0 + 150.0 + (m.sq_kind == SAS_SQ_HARD_SPHERE_PY ? 40.0 : 0.0);
-    if (m.kind == SAS_TRIAXIAL_ELLIPSOID || m.kind == SAS_PARALLELEPIPED) {
+    if (axes3_kind(m.kind)) {
         const int frames = m.sampling == SAS_PER_EVENT ? 1 : std::max(no / 3, 1);
-        return frames * (20.0 + np * (m.kind == SAS_TRIAXIAL_ELLIPSOID ? 36.0 : 66.0)) + 150.0 +
-               (m.sq_kind == SAS_SQ_HARD_SPHERE_PY ? 40.0 : 0.0);
+        const double term = m.kind == SAS_TRIAXIAL_ELLIPSOID ? 36.0 : m.kind == SAS_PARALLELEPIPED ? 66.0
+                          : m.kind == SAS_ELLIPTICAL_CYLINDER ? 50.0 : 132.0;
+        return frames * (20.0 + np * term) + 150.0 + (m.sq_kind == SAS_SQ_HARD_SPHERE_PY ? 40.0 : 0.0);
     }
     if (m.kind == SAS_CAPPED_CYLINDER || m.kind == SAS_BARBELL) {
         // per radius node: the cylinder term (sinc, 2 J1(x)/x; 60) and per cap
@@ -489,6 +490,13 @@ double capped_volume(const sas_model_desc& m)
     return M_PI * m.radius * m.radius * m.length + 2.0 * M_PI * R * H * H * (1.0 - H / (3.0 * R));
 }
 
+// Kinds without a symmetry axis: orientation nodes are frames (A, B, C).
+bool axes3_kind(int64_t kind)
+{
+    return kind == SAS_TRIAXIAL_ELLIPSOID || kind == SAS_PARALLELEPIPED || kind == SAS_ELLIPTICAL_CYLINDER ||
+           kind == SAS_HOLLOW_RECTANGULAR_PRISM;
+}
+
 // Shelled cylinders: the face layer t_f (0 for the hollow cylinder) and the
 // contrasts of the nested cylinders (r, L), (r, L + 2 t_f), (r + t, L),
 // (r + t, L + 2 t_f) in the amplitude (Eq. 1 region by region).
@@ -576,6 +584,21 @@ sas_status build_model_tables(const sas_model_desc& m, ModelTables& t, double q_
             p[2] = 3.0 * sw * (m.sld - m.sld_shell) * Vc;
             p[3] = 3.0 * sw * (m.sld_shell - m.sld_solvent) * Vo;
             vmean += w[i] * Vo;
+        } else if (m.kind == SAS_ELLIPTICAL_CYLINDER) {
+            const double sc = ri / m.radius;
+            const double V = pi * m.radius * m.radius_b * m.length * sc * sc * sc;
+            const double F0 = (m.sld - m.sld_solvent) * V;
+            p[0] = sc;
+            p[1] = w[i] * F0 * F0;
+            vmean += w[i] * V;
+        } else if (m.kind == SAS_HOLLOW_RECTANGULAR_PRISM) {
+            // amplitude / (drho 8 s^3) = a b c sinc sinc sinc - a_i b_i c_i sinc_i sinc_i sinc_i
+            const double sc = ri / m.radius, s3 = sc * sc * sc, t = m.thickness;
+            const double F0 = (m.sld - m.sld_solvent) * 8.0 * s3;
+            p[0] = sc;
+            p[1] = w[i] * F0 * F0;
+            vmean += w[i] * 8.0 * s3 *
+                     (m.radius * m.radius_b * m.radius_polar - (m.radius - t) * (m.radius_b - t) * (m.radius_polar - t));
         } else if (m.kind == SAS_TRIAXIAL_ELLIPSOID || m.kind == SAS_PARALLELEPIPED) {
             const double sc = ri / m.radius;   // one polydisperse factor for the three sizes
             const double V = (m.kind == SAS_TRIAXIAL_ELLIPSOID ? 4.0 / 3.0 * pi : 8.0) * m.radius * m.radius_b *
@@ -596,7 +619,7 @@ sas_status build_model_tables(const sas_model_desc& m, ModelTables& t, double q_
     for (int i = 0; i < npoly; ++i) t.r_max = std::fmax(t.r_max, r[i]);
     t.scale = m.volume_fraction / vmean;
     t.vmean = vmean;
-    if (m.kind == SAS_TRIAXIAL_ELLIPSOID || m.kind == SAS_PARALLELEPIPED) {
+    if (axes3_kind(m.kind)) {
         std::vector<double> fr, wf;
         const int nf = frame_nodes(m, fr, wf);
         t.orient.assign((size_t)3 * nf * SAS_ORIENT_STRIDE, 0.0);
@@ -710,7 +733,7 @@ sas_status build_model_tables(const sas_model_desc& m, ModelTables& t, double q_
         t.n_poly = 1 + (t.n_cap > 0 ? cap_rows : 0);
         t.n_rad = 1;
         if (t.n_orient > 0) {
-            const int rows = (m.kind == SAS_TRIAXIAL_ELLIPSOID || m.kind == SAS_PARALLELEPIPED) ? 3 : 1;
+            const int rows = axes3_kind(m.kind) ? 3 : 1;
             t.orient.resize((size_t)rows * SAS_ORIENT_STRIDE);
             t.n_orient = rows;
         }
@@ -769,13 +792,21 @@ ModelConst<T> model_const(const sas_model_desc& m, const ModelTables& t)
     c.ev_axis[2] = (T)std::cos(m.axis_theta);
     c.ax_a = (T)m.radius;
     c.ax_b = (T)m.radius_b;
-    c.ax_c = (T)m.radius_polar;
+    c.ax_c = (T)(m.kind == SAS_ELLIPTICAL_CYLINDER ? 0.5 * m.length : m.radius_polar);
+    if (m.kind == SAS_HOLLOW_RECTANGULAR_PRISM) {
+        const double t = m.thickness;
+        c.ax_ai = (T)(m.radius - t);
+        c.ax_bi = (T)(m.radius_b - t);
+        c.ax_ci = (T)(m.radius_polar - t);
+        c.ax_v = (T)(m.radius * m.radius_b * m.radius_polar);
+        c.ax_vi = (T)((m.radius - t) * (m.radius_b - t) * (m.radius_polar - t));
+    }
     {
         double f[9];
         frame_of(m.axis_theta, m.axis_phi, m.axis_psi, f);
         for (int k = 0; k < 6; ++k) c.ev_frame[k] = (T)f[k];
     }
-    if (m.kind == SAS_TRIAXIAL_ELLIPSOID || m.kind == SAS_PARALLELEPIPED)
+    if (axes3_kind(m.kind))
         c.orient_mode = (int)m.isotropic;
     c.n_rad = t.n_rad;
     c.n_tab = t.n_tab;
@@ -860,7 +891,13 @@ sas_status validate_instrument(const sas_instrument* in)
 sas_status validate_model(const sas_model_desc* m)
 {
     if (!m) return fail(SAS_ERR_ARG, "model is NULL");
-    if (m->kind < 0 || m->kind > 11) return fail(SAS_ERR_ARG, "unknown model kind");
+    if (m->kind < 0 || m->kind > 13) return fail(SAS_ERR_ARG, "unknown model kind");
+    if (m->kind == SAS_ELLIPTICAL_CYLINDER && (!(m->radius_b > 0.0) || !(m->length > 0.0) ||
+                                               !std::isfinite(m->radius_b) || !std::isfinite(m->axis_psi)))
+        return fail(SAS_ERR_ARG, "elliptical cylinder needs radius, radius_b, length > 0 and a finite axis_psi");
+    if (m->kind == SAS_HOLLOW_RECTANGULAR_PRISM &&
+        !(m->thickness > 0.0 && m->thickness < std::fmin(m->radius, std::fmin(m->radius_b, m->radius_polar))))
+        return fail(SAS_ERR_ARG, "hollow rectangular prism needs 0 < thickness < every half-edge");
     if (shelled_cylinder(m->kind) || m->kind == SAS_CORE_SHELL_ELLIPSOID) {
         if (!std::isfinite(m->thickness_face) || !std::isfinite(m->sld_face) || m->thickness < 0.0 ||
             m->thickness_face < 0.0)
@@ -877,9 +914,10 @@ sas_status validate_model(const sas_model_desc* m)
             return fail(SAS_ERR_ARG, "capped cylinder and barbell need length >= 0 and radius_polar >= radius");
         if (m->n_cap < 1 || m->n_cap > SAS_MAX_CAP_NODES) return fail(SAS_ERR_ARG, "n_cap must be in [1, 64]");
     }
-    const bool axes3 = m->kind == SAS_TRIAXIAL_ELLIPSOID || m->kind == SAS_PARALLELEPIPED;
-    if (axes3 && (!(m->radius_b > 0.0) || !(m->radius_polar > 0.0) || !std::isfinite(m->radius_b) ||
-                  !std::isfinite(m->axis_psi)))
+    const bool axes3 = axes3_kind(m->kind);
+    const bool boxlike = axes3 && m->kind != SAS_ELLIPTICAL_CYLINDER;
+    if (boxlike && (!(m->radius_b > 0.0) || !(m->radius_polar > 0.0) || !std::isfinite(m->radius_b) ||
+                    !std::isfinite(m->axis_psi)))
         return fail(SAS_ERR_ARG, "3-axis models need radius, radius_b, radius_polar > 0 and a finite axis_psi");
     if (axes3 && (m->n_rot < 1 || m->n_rot > SAS_MAX_ORIENT_SIDE)) return fail(SAS_ERR_ARG, "n_rot must be in [1, 128]");
     if (axes3 && m->isotropic != 0 && m->n_gamma * m->n_psi * m->n_rot > (1 << 17))
@@ -977,6 +1015,8 @@ cudaError_t dispatch_trace(sas_experiment* e, const TraceParams<T>& P, int* grid
     case SAS_HOLLOW_CYLINDER: return Launcher<T, SAS_HOLLOW_CYLINDER>::trace(P, e->cfg, e->sm_count, e->stream, grid);
     case SAS_CORE_SHELL_ELLIPSOID: return Launcher<T, SAS_CORE_SHELL_ELLIPSOID>::trace(P, e->cfg, e->sm_count, e->stream, grid);
     case SAS_CORE_SHELL_BICELLE: return Launcher<T, SAS_CORE_SHELL_BICELLE>::trace(P, e->cfg, e->sm_count, e->stream, grid);
+    case SAS_ELLIPTICAL_CYLINDER: return Launcher<T, SAS_ELLIPTICAL_CYLINDER>::trace(P, e->cfg, e->sm_count, e->stream, grid);
+    case SAS_HOLLOW_RECTANGULAR_PRISM: return Launcher<T, SAS_HOLLOW_RECTANGULAR_PRISM>::trace(P, e->cfg, e->sm_count, e->stream, grid);
     default: return Launcher<T, SAS_ELLIPSOID>::trace(P, e->cfg, e->sm_count, e->stream, grid);
     }
 }
@@ -996,6 +1036,8 @@ cudaError_t dispatch_records(sas_experiment* e, const TraceParams<T>& P)
     case SAS_HOLLOW_CYLINDER: return Launcher<T, SAS_HOLLOW_CYLINDER>::records(P, e->stream);
     case SAS_CORE_SHELL_ELLIPSOID: return Launcher<T, SAS_CORE_SHELL_ELLIPSOID>::records(P, e->stream);
     case SAS_CORE_SHELL_BICELLE: return Launcher<T, SAS_CORE_SHELL_BICELLE>::records(P, e->stream);
+    case SAS_ELLIPTICAL_CYLINDER: return Launcher<T, SAS_ELLIPTICAL_CYLINDER>::records(P, e->stream);
+    case SAS_HOLLOW_RECTANGULAR_PRISM: return Launcher<T, SAS_HOLLOW_RECTANGULAR_PRISM>::records(P, e->stream);
     default: return Launcher<T, SAS_ELLIPSOID>::records(P, e->stream);
     }
 }
@@ -1017,6 +1059,8 @@ cudaError_t dispatch_eval(sas_experiment* e, const ModelConst<T>& mc, const T* q
     case SAS_HOLLOW_CYLINDER: return Launcher<T, SAS_HOLLOW_CYLINDER>::eval(mc, poly, orient, q, out, n, e->stream);
     case SAS_CORE_SHELL_ELLIPSOID: return Launcher<T, SAS_CORE_SHELL_ELLIPSOID>::eval(mc, poly, orient, q, out, n, e->stream);
     case SAS_CORE_SHELL_BICELLE: return Launcher<T, SAS_CORE_SHELL_BICELLE>::eval(mc, poly, orient, q, out, n, e->stream);
+    case SAS_ELLIPTICAL_CYLINDER: return Launcher<T, SAS_ELLIPTICAL_CYLINDER>::eval(mc, poly, orient, q, out, n, e->stream);
+    case SAS_HOLLOW_RECTANGULAR_PRISM: return Launcher<T, SAS_HOLLOW_RECTANGULAR_PRISM>::eval(mc, poly, orient, q, out, n, e->stream);
     default: return Launcher<T, SAS_ELLIPSOID>::eval(mc, poly, orient, q, out, n, e->stream);
     }
 }

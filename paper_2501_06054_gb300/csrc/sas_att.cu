@@ -83,6 +83,10 @@ double model_extent(const sas_model_desc& m, const ModelTables& t)
         return std::sqrt(lo * lo + 4.0 * ro * ro);
     }
     case SAS_CORE_SHELL_ELLIPSOID: return 2.0 * std::fmax(r + m.thickness, m.radius_polar + m.thickness_face);
+    case SAS_ELLIPTICAL_CYLINDER: {
+        const double a = std::fmax(m.radius, m.radius_b);
+        return 2.0 * (r / m.radius) * std::sqrt(a * a + 0.25 * m.length * m.length);
+    }
     case SAS_CAPPED_CYLINDER:
     case SAS_BARBELL:   // tip to tip, L + 2H, or the caps' diameter
         return (r / m.radius) * std::fmax(m.length + 2.0 * cap_height(m), 2.0 * m.radius_polar);
@@ -164,6 +168,8 @@ cudaError_t att_launch(const sas_model_desc& m, const ModelConst<T>& mc, const T
     case SAS_HOLLOW_CYLINDER: return SAS_ATT_CASE(SAS_HOLLOW_CYLINDER);
     case SAS_CORE_SHELL_ELLIPSOID: return SAS_ATT_CASE(SAS_CORE_SHELL_ELLIPSOID);
     case SAS_CORE_SHELL_BICELLE: return SAS_ATT_CASE(SAS_CORE_SHELL_BICELLE);
+    case SAS_ELLIPTICAL_CYLINDER: return SAS_ATT_CASE(SAS_ELLIPTICAL_CYLINDER);
+    case SAS_HOLLOW_RECTANGULAR_PRISM: return SAS_ATT_CASE(SAS_HOLLOW_RECTANGULAR_PRISM);
     default: return SAS_ATT_CASE(SAS_ELLIPSOID);
     }
 #undef SAS_ATT_CASE

@@ -96,6 +96,8 @@ __device__ __forceinline__ void batch_dispatch(const BatchParams& P, const Model
     case SAS_HOLLOW_CYLINDER: batch_item<SAS_HOLLOW_CYLINDER, HIST, ATT>(P, mc, poly, orient, w, h, seed, tr); break;
     case SAS_CORE_SHELL_ELLIPSOID: batch_item<SAS_CORE_SHELL_ELLIPSOID, HIST, ATT>(P, mc, poly, orient, w, h, seed, tr); break;
     case SAS_CORE_SHELL_BICELLE: batch_item<SAS_CORE_SHELL_BICELLE, HIST, ATT>(P, mc, poly, orient, w, h, seed, tr); break;
+    case SAS_ELLIPTICAL_CYLINDER: batch_item<SAS_ELLIPTICAL_CYLINDER, HIST, ATT>(P, mc, poly, orient, w, h, seed, tr); break;
+    case SAS_HOLLOW_RECTANGULAR_PRISM: batch_item<SAS_HOLLOW_RECTANGULAR_PRISM, HIST, ATT>(P, mc, poly, orient, w, h, seed, tr); break;
     default: batch_item<SAS_ELLIPSOID, HIST, ATT>(P, mc, poly, orient, w, h, seed, tr); break;
     }
 }

@@ -628,11 +628,41 @@ __device__ __forceinline__ T avg_axes3(const T qv[3], const T* __restrict__ poly
         const T* A = orient + 4 * o;
         const T* B = A + 4;
         const T* C = A + 8;
-        const T qa = mc.ax_a * fma(qv[0], A[0], fma(qv[1], A[1], qv[2] * A[2]));
-        const T qb = mc.ax_b * fma(qv[0], B[0], fma(qv[1], B[1], qv[2] * B[2]));
-        const T qc = mc.ax_c * fma(qv[0], C[0], fma(qv[1], C[1], qv[2] * C[2]));
+        const T pa = fma(qv[0], A[0], fma(qv[1], A[1], qv[2] * A[2]));
+        const T pb = fma(qv[0], B[0], fma(qv[1], B[1], qv[2] * B[2]));
+        const T pc = fma(qv[0], C[0], fma(qv[1], C[1], qv[2] * C[2]));
+        const T qa = mc.ax_a * pa, qb = mc.ax_b * pb, qc = mc.ax_c * pc;
         T inner = 0;
-        if (KIND == SAS_TRIAXIAL_ELLIPSOID) {
+        if constexpr (KIND == SAS_ELLIPTICAL_CYLINDER) {
+            const T xab2 = fma(qa, qa, qb * qb), yc0 = fabs(qc);
+            for (int i = 0; i < np; ++i) {
+                const T sc = poly[SAS_POLY_STRIDE * i];
+                const T y = sc * yc0;
+                T a;
+                if constexpr (sizeof(T) == sizeof(float)) {
+                    a = cyl_a_tier<4>(sc * sc * xab2);
+                } else {
+                    const T x = sc * M<T>::sqrt_(xab2);
+                    a = M<T>::cyl_a(x, M<T>::rcp(x), (T)0);
+                }
+                const T amp = M<T>::sinc(y, M<T>::rcp(y)) * a;
+                inner = fma(poly[SAS_POLY_STRIDE * i + 1], amp * amp, inner);
+            }
+        } else if constexpr (KIND == SAS_HOLLOW_RECTANGULAR_PRISM) {
+            const T ya0 = fabs(qa), yb0 = fabs(qb), yc0 = fabs(qc);
+            const T za0 = fabs(mc.ax_ai * pa), zb0 = fabs(mc.ax_bi * pb), zc0 = fabs(mc.ax_ci * pc);
+            for (int i = 0; i < np; ++i) {
+                const T sc = poly[SAS_POLY_STRIDE * i];
+                const T ya = sc * ya0, yb = sc * yb0, yc = sc * yc0;
+                const T za = sc * za0, zb = sc * zb0, zc = sc * zc0;
+                const T outer = M<T>::sinc(ya, M<T>::rcp(ya)) * M<T>::sinc(yb, M<T>::rcp(yb)) *
+                                M<T>::sinc(yc, M<T>::rcp(yc));
+                const T hole = M<T>::sinc(za, M<T>::rcp(za)) * M<T>::sinc(zb, M<T>::rcp(zb)) *
+                               M<T>::sinc(zc, M<T>::rcp(zc));
+                const T amp = fma(mc.ax_v, outer, -mc.ax_vi * hole);
+                inner = fma(poly[SAS_POLY_STRIDE * i + 1], amp * amp, inner);
+            }
+        } else if (KIND == SAS_TRIAXIAL_ELLIPSOID) {
             const T x0 = M<T>::sqrt_(fma(qa, qa, fma(qb, qb, qc * qc)));
             for (int i = 0; i < np; ++i) {
                 const T x = poly[SAS_POLY_STRIDE * i] * x0;
@@ -747,7 +777,8 @@ __device__ __forceinline__ T dsigma_event(const T qv[3], const ModelConst<T>& mc
     }
     const T pi = (T)3.14159265358979323846;
     T F2;
-    if constexpr (KIND == SAS_TRIAXIAL_ELLIPSOID || KIND == SAS_PARALLELEPIPED) {
+    if constexpr (KIND == SAS_TRIAXIAL_ELLIPSOID || KIND == SAS_PARALLELEPIPED || KIND == SAS_ELLIPTICAL_CYLINDER ||
+                  KIND == SAS_HOLLOW_RECTANGULAR_PRISM) {
         // frame of this event: C from (theta, phi), A and B rotated by psi
         T A[3], B[3], C[3];
         if (mc.orient_mode == 0) {
@@ -776,12 +807,28 @@ __device__ __forceinline__ T dsigma_event(const T qv[3], const ModelConst<T>& mc
             C[2] = ct;
         }
         const T sc = r / mc.ev_r;
-        const T qa = sc * mc.ax_a * fma(qv[0], A[0], fma(qv[1], A[1], qv[2] * A[2]));
-        const T qb = sc * mc.ax_b * fma(qv[0], B[0], fma(qv[1], B[1], qv[2] * B[2]));
-        const T qc = sc * mc.ax_c * fma(qv[0], C[0], fma(qv[1], C[1], qv[2] * C[2]));
+        const T pa = sc * fma(qv[0], A[0], fma(qv[1], A[1], qv[2] * A[2]));
+        const T pb = sc * fma(qv[0], B[0], fma(qv[1], B[1], qv[2] * B[2]));
+        const T pc = sc * fma(qv[0], C[0], fma(qv[1], C[1], qv[2] * C[2]));
+        const T qa = mc.ax_a * pa, qb = mc.ax_b * pb, qc = mc.ax_c * pc;
         const T v3 = mc.ax_a * mc.ax_b * mc.ax_c * sc * sc * sc;
         T F;
-        if (KIND == SAS_TRIAXIAL_ELLIPSOID) {
+        if constexpr (KIND == SAS_ELLIPTICAL_CYLINDER) {
+            // V = pi a b L = 2 pi a b c
+            const T x = M<T>::sqrt_(fma(qa, qa, qb * qb)), y = fabs(qc);
+            T a;
+            if constexpr (sizeof(T) == sizeof(float)) a = cyl_a_tier<4>(x * x);
+            else a = M<T>::cyl_a(x, M<T>::rcp(x), (T)0);
+            F = mc.ev_c1 * (T)2 * pi * v3 * M<T>::sinc(y, M<T>::rcp(y)) * a;
+        } else if constexpr (KIND == SAS_HOLLOW_RECTANGULAR_PRISM) {
+            const T ya = fabs(qa), yb = fabs(qb), yc = fabs(qc);
+            const T za = fabs(mc.ax_ai * pa), zb = fabs(mc.ax_bi * pb), zc = fabs(mc.ax_ci * pc);
+            const T outer = M<T>::sinc(ya, M<T>::rcp(ya)) * M<T>::sinc(yb, M<T>::rcp(yb)) *
+                            M<T>::sinc(yc, M<T>::rcp(yc));
+            const T hole = M<T>::sinc(za, M<T>::rcp(za)) * M<T>::sinc(zb, M<T>::rcp(zb)) *
+                           M<T>::sinc(zc, M<T>::rcp(zc));
+            F = mc.ev_c1 * (T)8 * sc * sc * sc * fma(mc.ax_v, outer, -mc.ax_vi * hole);
+        } else if (KIND == SAS_TRIAXIAL_ELLIPSOID) {
             const T x = M<T>::sqrt_(fma(qa, qa, fma(qb, qb, qc * qc)));
             F = (T)3 * mc.ev_c1 * (T)(4.0 / 3.0) * pi * v3 * M<T>::sphere_g(x, M<T>::rcp(x));
         } else {

@@ -61,6 +61,7 @@ double model_extent(const sas_model_desc& m, const ModelTables& t);
 double cap_height(const sas_model_desc& m);
 double capped_volume(const sas_model_desc& m);
 bool shelled_cylinder(int64_t kind);
+bool axes3_kind(int64_t kind);
 double face_layer(const sas_model_desc& m);
 void shelled_contrasts(const sas_model_desc& m, double d[4]);
 void att_rule(const sas_instrument& in, const sas_model_desc& m, const ModelTables& t, AttRule& r);

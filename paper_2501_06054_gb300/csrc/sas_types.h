@@ -50,6 +50,8 @@ struct AttPanel {
 //                 c_2 = 3 sqrt(w) (rho_s - rho_solv) V_o, c_1 / r_c^3, c_2 / r_o^3}
 //     cylinder   {r^2, w (drho V)^2, r, 1/r, 1/sqrt(r), 0...}  (ascending r)
 //     ellipsoid  {r_e^2, 9 w (drho V)^2, 0...}
+//     elliptical cylinder {s, w (drho V(s))^2, 0...}; hollow rectangular prism
+//                {s, w (8 drho s^3)^2, 0...} (frames as for the 3-axis kinds)
 //     capped cylinder, barbell {s, w (drho s^3)^2, s^2, 0...} (s = r_i / r),
 //                followed by the cap slices, two per row: {z_j, rho_j^2, c_j, 0}
 //     core-shell / hollow cylinder, bicelle {r^2, r_o^2, c_1, c_2, c_3, c_4, r, r_o}
@@ -100,6 +102,8 @@ struct ModelConst {
     // the outer polar radius r_p + t_p and its square (ellipsoid)
     T half_length_o, rp_o, rp2o;
     T ev_k[4];       // shelled cylinders: the contrasts of c_1..c_4 (per-event amplitudes)
+    // hollow rectangular prism: inner half-edges and the two a b c products
+    T ax_ai, ax_bi, ax_ci, ax_v, ax_vi;
 };
 
 }  // namespace sas
