@@ -165,9 +165,13 @@ sas_status plan(sas_batch* b)
 {
     size_t smem = 0;
     int any_hist = 0;
+    // the histogram kernel is built without these two kinds
+    bool full = false;
+    for (const sas_model_desc& m : b->models)
+        full |= m.kind == SAS_ELLIPTICAL_CYLINDER || m.kind == SAS_HOLLOW_RECTANGULAR_PRISM;
     for (size_t e = 0; e < b->n_exp; ++e) {
         BatchExp& x = b->h_exps[e];
-        x.use_hist = (b->cfg.use_hist && b->hist_capable[e]) ? 1 : 0;
+        x.use_hist = (b->cfg.use_hist && b->hist_capable[e] && !full) ? 1 : 0;
         x.stage_orient = (!x.use_hist && b->orient_stageable[e]) ? 1 : 0;
         size_t need = table_bytes<float>(x.mc.n_poly, x.mc.n_orient, x.stage_orient);
         if (x.use_hist) need = table_bytes<float>(x.mc.n_poly, 0, 0) + hist_bytes(b->npix);

@@ -79,11 +79,25 @@ __device__ __forceinline__ void batch_item(const BatchParams& P, const ModelCons
     }
 }
 
-template <int HIST, bool ATT>
+// FULL: every kind. The histogram kernel (batch_kernel<1>) is compiled
+// without the elliptical cylinder and the hollow prism, whose code would
+// push its register allocation into spills; the host launches batch_kernel<0>
+// for any batch that holds one of them.
+template <int HIST, bool ATT, bool FULL>
 __device__ __forceinline__ void batch_dispatch(const BatchParams& P, const ModelConst<float>& mc, const float* poly,
                                                const float* orient, const WorkItem& w, const SmemHist& h,
                                                uint64_t seed, Kahan<float>& tr)
 {
+    if constexpr (FULL) {
+        if (mc.kind == SAS_ELLIPTICAL_CYLINDER) {
+            batch_item<SAS_ELLIPTICAL_CYLINDER, HIST, ATT>(P, mc, poly, orient, w, h, seed, tr);
+            return;
+        }
+        if (mc.kind == SAS_HOLLOW_RECTANGULAR_PRISM) {
+            batch_item<SAS_HOLLOW_RECTANGULAR_PRISM, HIST, ATT>(P, mc, poly, orient, w, h, seed, tr);
+            return;
+        }
+    }
     switch (mc.kind) {
     case SAS_SPHERE: batch_item<SAS_SPHERE, HIST, ATT>(P, mc, poly, orient, w, h, seed, tr); break;
     case SAS_CORE_SHELL: batch_item<SAS_CORE_SHELL, HIST, ATT>(P, mc, poly, orient, w, h, seed, tr); break;
@@ -96,8 +110,6 @@ __device__ __forceinline__ void batch_dispatch(const BatchParams& P, const Model
     case SAS_HOLLOW_CYLINDER: batch_item<SAS_HOLLOW_CYLINDER, HIST, ATT>(P, mc, poly, orient, w, h, seed, tr); break;
     case SAS_CORE_SHELL_ELLIPSOID: batch_item<SAS_CORE_SHELL_ELLIPSOID, HIST, ATT>(P, mc, poly, orient, w, h, seed, tr); break;
     case SAS_CORE_SHELL_BICELLE: batch_item<SAS_CORE_SHELL_BICELLE, HIST, ATT>(P, mc, poly, orient, w, h, seed, tr); break;
-    case SAS_ELLIPTICAL_CYLINDER: batch_item<SAS_ELLIPTICAL_CYLINDER, HIST, ATT>(P, mc, poly, orient, w, h, seed, tr); break;
-    case SAS_HOLLOW_RECTANGULAR_PRISM: batch_item<SAS_HOLLOW_RECTANGULAR_PRISM, HIST, ATT>(P, mc, poly, orient, w, h, seed, tr); break;
     default: batch_item<SAS_ELLIPSOID, HIST, ATT>(P, mc, poly, orient, w, h, seed, tr); break;
     }
 }
@@ -149,11 +161,11 @@ __global__ void __launch_bounds__(1024) batch_kernel(const BatchParams P)
         __syncthreads();
         Kahan<float> tr;
         if (mc.att.n > 0) {
-            if (hist) batch_dispatch<HIST_OK, true>(P, mc, s_poly, orient, w, h, seed, tr);
-            else batch_dispatch<0, true>(P, mc, s_poly, orient, w, h, seed, tr);
+            if (hist) batch_dispatch<HIST_OK, true, HIST_OK == 0>(P, mc, s_poly, orient, w, h, seed, tr);
+            else batch_dispatch<0, true, HIST_OK == 0>(P, mc, s_poly, orient, w, h, seed, tr);
         } else {
-            if (hist) batch_dispatch<HIST_OK, false>(P, mc, s_poly, orient, w, h, seed, tr);
-            else batch_dispatch<0, false>(P, mc, s_poly, orient, w, h, seed, tr);
+            if (hist) batch_dispatch<HIST_OK, false, HIST_OK == 0>(P, mc, s_poly, orient, w, h, seed, tr);
+            else batch_dispatch<0, false, HIST_OK == 0>(P, mc, s_poly, orient, w, h, seed, tr);
         }
         double t = (double)tr.s - (double)tr.c;
 #pragma unroll

@@ -89,6 +89,10 @@ sas_status sas_trace_batch_static(const sas_instrument* inst, const sas_model_de
     size_t smem = 0;
     int any_hist = 0;
     const double target = 2e9;
+    // the histogram kernel is built without these two kinds
+    bool full = false;
+    for (size_t e = 0; e < n_exp; ++e)
+        full |= models[e].kind == SAS_ELLIPTICAL_CYLINDER || models[e].kind == SAS_HOLLOW_RECTANGULAR_PRISM;
     for (size_t e = 0; e < n_exp; ++e) {
         const sas_model_desc& m = models[e];
         st = validate_model(&m);
@@ -107,7 +111,7 @@ sas_status sas_trace_batch_static(const sas_instrument* inst, const sas_model_de
         x.orient_off = (uint32_t)orient.size();
         for (double v : t.poly) poly.push_back((float)v);
         for (double v : t.orient) orient.push_back((float)v);
-        const bool hist = t.n_orient <= 1 &&
+        const bool hist = !full && t.n_orient <= 1 &&
                           table_bytes<float>(t.n_poly, 0, 0) + hist_bytes(npix) <= (size_t)optin;
         x.use_hist = hist ? 1 : 0;
         x.stage_orient = (!hist && t.n_orient > 1 && table_bytes<float>(t.n_poly, t.n_orient, 1) <= (size_t)optin)
