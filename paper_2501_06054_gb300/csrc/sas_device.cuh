@@ -1,5 +1,5 @@
 // Device building blocks of the SANS trace: Philox4x32-10, the neutron
-// history geometry, the twelve form-factor models with their polydispersity
+// history geometry, the fourteen form-factor models with their polydispersity
 // and orientation quadratures (or per-event draws), the Percus-Yevick
 // structure factor and the self-attenuation table. Templated on the
 // arithmetic type: float (FP32 trace: sin, cos and sine from the
