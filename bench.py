@@ -305,7 +305,7 @@ def secondary(stream, info):
     sas.sas_destroy_surrogate(sur)
     out["per_event"] = per_event(stream)
     out["self_attenuation"] = self_attenuation(stream)
-    out["capped"] = capped_models(stream)
+    out["n4_models"] = n4_models(stream)
     return out
 
 
@@ -327,7 +327,7 @@ SHELLED_DESC = {
                           "FP32"}
 
 
-def capped_models(stream):
+def n4_models(stream):
     """Capped cylinder and barbell (the cylinder's amplitude plus n_cap disk
     slices per cap, Eq. 1): histories/s and slice terms/s (orientation nodes
     x radius nodes x (n_cap + 1) per history); the shelled uniaxial models:
