@@ -85,7 +85,8 @@ class _Model(ctypes.Structure):
                 ("axis_theta", ctypes.c_double), ("axis_phi", ctypes.c_double),
                 ("radius_b", ctypes.c_double), ("axis_psi", ctypes.c_double),
                 ("self_att", ctypes.c_int64), ("n_cap", ctypes.c_int64), ("thickness_face", ctypes.c_double),
-                ("sld_face", ctypes.c_double)]
+                ("sld_face", ctypes.c_double), ("function", ctypes.c_int64)] + \
+               [(n, ctypes.c_double) for n in ("f_scale", "f_p0", "f_p1", "f_p2")]
 
 
 def lib():
@@ -349,7 +350,9 @@ class Prepared:
                         radius_b=float(m.get("radius_b", 0.0)), axis_psi=float(m.get("axis_psi", 0.0)),
                         self_att=int(m.get("self_attenuation", 0)), n_cap=int(m.get("n_cap", 16)),
                         thickness_face=float(m.get("thickness_face", 0.0)),
-                        sld_face=float(m.get("sld_face", 0.0)))
+                        sld_face=float(m.get("sld_face", 0.0)), function=int(m.get("function", 0)),
+                        f_scale=float(m.get("f_scale", 0.0)), f_p0=float(m.get("f_p0", 0.0)),
+                        f_p1=float(m.get("f_p1", 0.0)), f_p2=float(m.get("f_p2", 0.0)))
 
 
 def _inst(instrument):

@@ -92,7 +92,7 @@ typedef struct {
                               ellipsoid, 5 parallelepiped, 6 capped cylinder, 7 barbell,
                               8 core-shell cylinder, 9 hollow cylinder, 10 core-shell ellipsoid,
                               11 core-shell bicelle, 12 elliptical cylinder,
-                              13 hollow rectangular prism */
+                              13 hollow rectangular prism, 14 shape-independent */
     int64_t sq_kind;       /* 0 none, 1 Percus-Yevick hard spheres */
     int64_t n_poly;        /* polydispersity nodes */
     int64_t n_orient;      /* orientation nodes */
@@ -130,6 +130,10 @@ typedef struct {
     double thickness_face;
     /* core-shell bicelle (kind 11): density of the face layers */
     double sld_face;
+    /* shape-independent models (kind 14): dSigma/dOmega = f_scale f(|Q|), f
+     * selected by `function` with parameters f_p0..f_p2 */
+    int64_t function;
+    double f_scale, f_p0, f_p1, f_p2;
 } oracle_model;
 
 /* --------------------------------------------------------- model pieces */
@@ -228,9 +232,42 @@ static double sphere_volume(double r) { return 4.0 / 3.0 * PI * r * r * r; }
 /* Scattering cross section per unit volume dSigma/dOmega(Q) in 1/angstrom:
  * (phi / <V>) <|F|^2> S(Q), F = drho V f, averages over the polydispersity
  * nodes (and, for the uniaxial models, over the orientation nodes).      */
+/* Shape-independent models (the isotropic group G): dSigma/dOmega as a
+ * function of |Q| alone, f_scale times
+ *   0 Guinier            exp(-Q^2 Rg^2 / 3)                    (p0 = Rg)
+ *   1 Gaussian coil      Debye's 2 (exp(-u) - 1 + u) / u^2,
+ *                        u = (Q Rg)^2                          (p0 = Rg)
+ *   2 Lorentzian         1 / (1 + (Q xi)^2)                    (p0 = xi)
+ *   3 Debye-Anderson-Brumberger 1 / (1 + (Q xi)^2)^2           (p0 = xi)
+ *   4 power law          Q^-m                                  (p0 = m)
+ *   5 Gaussian peak      exp(-(Q - Q0)^2 / (2 sigma^2))        (p0 = Q0, p1 = sigma)
+ *   6 Teubner-Strey      1 / (a2 + c1 Q^2 + c2 Q^4)            (p0 = a2, p1 = c1, p2 = c2)
+ * The coil below u = 1e-3 by its series 1 - u/3 + u^2/12 (the closed form
+ * cancels there), above it with expm1. */
+static double oracle_shape_independent(const oracle_model *m, double q)
+{
+    double q2 = q * q, f;
+    switch (m->function) {
+    case 0: f = exp(-q2 * m->f_p0 * m->f_p0 / 3.0); break;
+    case 1: {
+        double u = q2 * m->f_p0 * m->f_p0;
+        f = u < 1e-3 ? 1.0 - u / 3.0 + u * u / 12.0 : 2.0 * (expm1(-u) + u) / (u * u);
+        if (SAS_MUT == 28) f = u < 1e-3 ? 1.0 : 2.0 * (exp(-u) + u) / (u * u);
+        break;
+    }
+    case 2: f = 1.0 / (1.0 + q2 * m->f_p0 * m->f_p0); break;
+    case 3: { double d = 1.0 + q2 * m->f_p0 * m->f_p0; f = 1.0 / (d * d); break; }
+    case 4: f = pow(q, -m->f_p0); break;
+    case 5: { double d = (q - m->f_p0) / m->f_p1; f = exp(-0.5 * d * d); break; }
+    default: f = 1.0 / (m->f_p0 + q2 * (m->f_p1 + q2 * m->f_p2)); break;
+    }
+    return m->f_scale * f;
+}
+
 double oracle_dsigma(const oracle_model *m, const double q[3])
 {
     double qq = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
+    if (m->kind == 14) return oracle_shape_independent(m, qq);
     double sum = 0.0, vmean = 0.0;
     int64_t np = m->n_poly;
     if (m->kind == 0) {              /* sphere */

@@ -39,13 +39,15 @@ TRIAXIAL_ELLIPSOID, PARALLELEPIPED = 4, 5        # no symmetry axis: sizes along
 CAPPED_CYLINDER, BARBELL = 6, 7                  # cylinder with spherical end caps (radius_polar)
 CORE_SHELL_CYLINDER, HOLLOW_CYLINDER, CORE_SHELL_ELLIPSOID, CORE_SHELL_BICELLE = 8, 9, 10, 11
 ELLIPTICAL_CYLINDER, HOLLOW_RECTANGULAR_PRISM = 12, 13   # no symmetry axis, like the 3-axis kinds
+SHAPE_INDEPENDENT = 14                                    # dSigma/dOmega = f_scale f(|Q|), see `function`
+GUINIER, GAUSS_COIL, LORENTZ, DAB, POWER_LAW, GAUSS_PEAK, TEUBNER_STREY = range(7)
 MODEL_NAMES = {SPHERE: "sphere", CORE_SHELL: "core_shell", CYLINDER: "cylinder",
                ELLIPSOID: "ellipsoid", TRIAXIAL_ELLIPSOID: "triaxial_ellipsoid",
                PARALLELEPIPED: "parallelepiped", CAPPED_CYLINDER: "capped_cylinder",
                BARBELL: "barbell", CORE_SHELL_CYLINDER: "core_shell_cylinder",
                HOLLOW_CYLINDER: "hollow_cylinder", CORE_SHELL_ELLIPSOID: "core_shell_ellipsoid",
                CORE_SHELL_BICELLE: "core_shell_bicelle", ELLIPTICAL_CYLINDER: "elliptical_cylinder",
-               HOLLOW_RECTANGULAR_PRISM: "hollow_rectangular_prism"}
+               HOLLOW_RECTANGULAR_PRISM: "hollow_rectangular_prism", SHAPE_INDEPENDENT: "shape_independent"}
 SQ_NONE, SQ_HARD_SPHERE_PY = 0, 1
 FP32, FP64 = 0, 1
 QUADRATURE, PER_EVENT = 0, 1              # sampling: averages over nodes / one draw per history
@@ -111,6 +113,11 @@ class Model:
     thickness_face: float = 0.0     # core-shell cylinder: shell on the end faces; core-shell ellipsoid:
                                     # shell along the axis (thickness: radial / equatorial shell)
     sld_face: float = 0.0           # core-shell bicelle: SLD of the face layers (sld_shell is the rim's)
+    function: int = GUINIER         # shape-independent: GUINIER .. TEUBNER_STREY
+    f_scale: float = 0.0            # shape-independent: dSigma/dOmega = f_scale f(|Q|), 1/angstrom
+    f_p0: float = 0.0               # shape-independent parameters (Rg, xi, m, Q0 / sigma, a2 / c1 / c2)
+    f_p1: float = 0.0
+    f_p2: float = 0.0
 
     def as_dict(self):
         return asdict(self)

@@ -48,6 +48,7 @@ MUTATIONS = {
     25: ("bicelle rim over the core's length only", "bicelle", "test_shell_models_oracle.py"),
     26: ("elliptical cylinder with one semi-axis for both", "new_bodies_against", "test_triaxial_oracle.py"),
     27: ("hollow prism normalised by its outer volume", "new_bodies_against", "test_triaxial_oracle.py"),
+    28: ("Gaussian coil without the -1 of Debye's function", "coil", "test_shape_independent_oracle.py"),
 }
 
 
