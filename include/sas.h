@@ -64,7 +64,12 @@ enum { SAS_SPHERE = 0, SAS_CORE_SHELL = 1, SAS_CYLINDER = 2, SAS_ELLIPSOID = 3,
        SAS_CORE_SHELL_CYLINDER = 8, SAS_HOLLOW_CYLINDER = 9, SAS_CORE_SHELL_ELLIPSOID = 10,
        SAS_CORE_SHELL_BICELLE = 11,
        /* no symmetry axis (Sec. II.B, the ellipsoid and parallelepiped groups) */
-       SAS_ELLIPTICAL_CYLINDER = 12, SAS_HOLLOW_RECTANGULAR_PRISM = 13 };
+       SAS_ELLIPTICAL_CYLINDER = 12, SAS_HOLLOW_RECTANGULAR_PRISM = 13,
+       /* shape-independent laws of |Q| (the isotropic group G) */
+       SAS_SHAPE_INDEPENDENT = 14 };
+/* sas_model_desc.function of SAS_SHAPE_INDEPENDENT */
+enum { SAS_FN_GUINIER = 0, SAS_FN_GAUSS_COIL = 1, SAS_FN_LORENTZ = 2, SAS_FN_DAB = 3, SAS_FN_POWER_LAW = 4,
+       SAS_FN_GAUSS_PEAK = 5, SAS_FN_TEUBNER_STREY = 6 };
 /* largest Gauss-Legendre rule over an end cap */
 #define SAS_MAX_CAP_NODES 64
 enum { SAS_SQ_NONE = 0, SAS_SQ_HARD_SPHERE_PY = 1 };
@@ -104,7 +109,8 @@ typedef struct sas_model_desc {
                                 SAS_TRIAXIAL_ELLIPSOID, SAS_PARALLELEPIPED, SAS_CAPPED_CYLINDER,
                                 SAS_BARBELL, SAS_CORE_SHELL_CYLINDER, SAS_HOLLOW_CYLINDER,
                                 SAS_CORE_SHELL_ELLIPSOID, SAS_CORE_SHELL_BICELLE,
-                                SAS_ELLIPTICAL_CYLINDER, SAS_HOLLOW_RECTANGULAR_PRISM */
+                                SAS_ELLIPTICAL_CYLINDER, SAS_HOLLOW_RECTANGULAR_PRISM,
+                                SAS_SHAPE_INDEPENDENT */
     int64_t sq_kind;         /* SAS_SQ_NONE or SAS_SQ_HARD_SPHERE_PY */
     int64_t precision;       /* SAS_FP32 (tallies FP32 Kahan + FP64 reduction) or SAS_FP64 */
     int64_t n_poly;          /* Schulz nodes of the polydisperse radius (1..64) */
@@ -217,6 +223,20 @@ typedef struct sas_model_desc {
      *   normalised by <pi (r + t)^2 (L + 2 t_f)>. */
     double thickness_face;   /* core-shell cylinder, bicelle: face layer; core-shell ellipsoid: polar shell (>= 0) */
     double sld_face;         /* core-shell bicelle: SLD of the face layers */
+    /* Shape-independent laws: dSigma/dOmega(Q) = f_scale f(|Q|) in
+     * 1/angstrom (no particle, no S(Q), no orientation or size average;
+     * quadrature sampling, no self-attenuation), f by `function`:
+     *   SAS_FN_GUINIER        exp(-Q^2 Rg^2 / 3)                   f_p0 = Rg > 0
+     *   SAS_FN_GAUSS_COIL     2 (exp(-u) - 1 + u) / u^2, u = (Q Rg)^2  f_p0 = Rg > 0
+     *   SAS_FN_LORENTZ        1 / (1 + (Q xi)^2)                   f_p0 = xi > 0
+     *   SAS_FN_DAB            1 / (1 + (Q xi)^2)^2                 f_p0 = xi > 0
+     *   SAS_FN_POWER_LAW      Q^-m                                 f_p0 = m
+     *   SAS_FN_GAUSS_PEAK     exp(-(Q - Q0)^2 / (2 sigma^2))       f_p0 = Q0, f_p1 = sigma > 0
+     *   SAS_FN_TEUBNER_STREY  1 / (a2 + c1 Q^2 + c2 Q^4)           f_p0 = a2 > 0, f_p1 = c1,
+     *                         f_p2 = c2 >= 0, positive for every Q (c1 >= 0 or c1^2 < 4 a2 c2) */
+    int64_t function;
+    double f_scale;          /* >= 0 */
+    double f_p0, f_p1, f_p2;
 } sas_model_desc;
 
 typedef struct sas_experiment sas_experiment;   /* opaque, library-owned */
@@ -354,7 +374,8 @@ typedef struct sas_batch_config {
  * each with its own model (FP32 only) and neutron count; experiment e uses
  * Philox experiment id e and its own FP64 detector. Builds all quadrature
  * tables, cuts the index ranges into work items ordered longest-first and
- * allocates n_exp * nx * ny * 24 bytes of detectors. */
+ * allocates n_exp * nx * ny * 24 bytes of detectors. SAS_ERR_ARG for an FP64
+ * model or a shape-independent law (those trace one by one). */
 sas_status sas_create_batch(const sas_instrument *inst, const sas_model_desc *models,
                             const uint64_t *counts, size_t n_exp, void *stream, sas_batch **out);
 

@@ -48,7 +48,9 @@ class sas_model_desc(ctypes.Structure):
                [(n, ctypes.c_int64) for n in ("sampling", "poly_dist", "radial_table")] + \
                [("radius_b", ctypes.c_double), ("axis_psi", ctypes.c_double), ("n_rot", ctypes.c_int64),
                 ("self_attenuation", ctypes.c_int64), ("n_cap", ctypes.c_int64),
-                ("thickness_face", ctypes.c_double), ("sld_face", ctypes.c_double)]
+                ("thickness_face", ctypes.c_double), ("sld_face", ctypes.c_double),
+                ("function", ctypes.c_int64)] + \
+               [(n, ctypes.c_double) for n in ("f_scale", "f_p0", "f_p1", "f_p2")]
 
 
 class sas_launch_config(ctypes.Structure):
@@ -194,7 +196,7 @@ def make_instrument(d) -> sas_instrument:
 def make_model(d) -> sas_model_desc:
     d = d if isinstance(d, dict) else d.as_dict()
     ints = ("kind", "sq_kind", "precision", "n_poly", "n_gamma", "n_psi", "isotropic", "sampling",
-            "poly_dist", "radial_table", "n_rot", "self_attenuation", "n_cap")
+            "poly_dist", "radial_table", "n_rot", "self_attenuation", "n_cap", "function")
     return sas_model_desc(**{k: (int(v) if k in ints else float(v)) for k, v in d.items()})
 
 

@@ -73,6 +73,7 @@ double host_flops_per_history(const sas_model_desc& m, int np, int no)
         return no * (40.0 + nr * (60.0 + 30.0 * (double)m.n_cap)) + 150.0 +
                (m.sq_kind == SAS_SQ_HARD_SPHERE_PY ? 40.0 : 0.0);
     }
+    if (m.kind == SAS_SHAPE_INDEPENDENT) return 150.0 + 30.0;
     if (shelled_cylinder(m.kind))
         return no * (60.0 + 26.0 + np * 2.0 * 26.0) + 150.0 + (m.sq_kind == SAS_SQ_HARD_SPHERE_PY ? 40.0 : 0.0);
     if (m.kind == SAS_CORE_SHELL_ELLIPSOID)
@@ -528,9 +529,10 @@ sas_status build_model_tables(const sas_model_desc& m, ModelTables& t, double q_
 {
     const int np = (int)m.n_poly;
     std::vector<double> r(np), w(np);
-    if (m.poly_dist == SAS_POLY_GAUSSIAN) gaussian_nodes(m.radius, m.poly, np, r.data(), w.data());
-    else schulz_nodes(m.radius, m.poly, np, r.data(), w.data());
-    const int npoly = (m.poly > 0.0 && np > 1) ? np : 1;
+    const double rmean = m.kind == SAS_SHAPE_INDEPENDENT ? 1.0 : m.radius;   // no particle: one dummy node
+    if (m.poly_dist == SAS_POLY_GAUSSIAN) gaussian_nodes(rmean, m.poly, np, r.data(), w.data());
+    else schulz_nodes(rmean, m.poly, np, r.data(), w.data());
+    const int npoly = (m.kind != SAS_SHAPE_INDEPENDENT && m.poly > 0.0 && np > 1) ? np : 1;
     t.poly.assign((size_t)npoly * SAS_POLY_STRIDE, 0.0);
     double vmean = 0.0;
     const double pi = M_PI;
@@ -619,6 +621,11 @@ sas_status build_model_tables(const sas_model_desc& m, ModelTables& t, double q_
     for (int i = 0; i < npoly; ++i) t.r_max = std::fmax(t.r_max, r[i]);
     t.scale = m.volume_fraction / vmean;
     t.vmean = vmean;
+    if (m.kind == SAS_SHAPE_INDEPENDENT) {   // f_scale f(|Q|): no particle and no nodes
+        std::fill(t.poly.begin(), t.poly.end(), 0.0);
+        t.scale = m.f_scale;
+        t.vmean = 1.0;
+    }
     if (axes3_kind(m.kind)) {
         std::vector<double> fr, wf;
         const int nf = frame_nodes(m, fr, wf);
@@ -817,6 +824,19 @@ ModelConst<T> model_const(const sas_model_desc& m, const ModelTables& t)
         shelled_contrasts(m, d);
         for (int k = 0; k < 4; ++k) c.ev_k[k] = (T)d[k];
     }
+    c.function = (int)m.function;
+    if (m.kind == SAS_SHAPE_INDEPENDENT) {
+        const double p0 = m.f_p0, p1 = m.f_p1;
+        switch (m.function) {
+        case SAS_FN_GUINIER: c.f_a = (T)(p0 * p0 / 3.0); break;
+        case SAS_FN_GAUSS_COIL:
+        case SAS_FN_LORENTZ:
+        case SAS_FN_DAB: c.f_a = (T)(p0 * p0); break;
+        case SAS_FN_POWER_LAW: c.f_a = (T)p0; break;
+        case SAS_FN_GAUSS_PEAK: c.f_a = (T)p0; c.f_b = (T)(0.5 / (p1 * p1)); break;
+        default: c.f_a = (T)m.f_p0; c.f_b = (T)m.f_p1; c.f_c = (T)m.f_p2; break;
+        }
+    }
     c.rp_o = (T)(m.radius_polar + (m.kind == SAS_CORE_SHELL_ELLIPSOID ? m.thickness_face : 0.0));
     c.rp2o = c.rp_o * c.rp_o;
     c.cap_body = (T)t.cap_body;
@@ -891,7 +911,21 @@ sas_status validate_instrument(const sas_instrument* in)
 sas_status validate_model(const sas_model_desc* m)
 {
     if (!m) return fail(SAS_ERR_ARG, "model is NULL");
-    if (m->kind < 0 || m->kind > 13) return fail(SAS_ERR_ARG, "unknown model kind");
+    if (m->kind < 0 || m->kind > 14) return fail(SAS_ERR_ARG, "unknown model kind");
+    if (m->kind == SAS_SHAPE_INDEPENDENT) {
+        if (m->function < SAS_FN_GUINIER || m->function > SAS_FN_TEUBNER_STREY)
+            return fail(SAS_ERR_ARG, "unknown shape-independent function");
+        if (!finite_all({m->f_scale, m->f_p0, m->f_p1, m->f_p2}) || m->f_scale < 0.0)
+            return fail(SAS_ERR_ARG, "f_scale must be finite and >= 0, f_p0..f_p2 finite");
+        const int64_t fn = m->function;
+        if ((fn <= SAS_FN_DAB && !(m->f_p0 > 0.0)) || (fn == SAS_FN_GAUSS_PEAK && !(m->f_p1 > 0.0)))
+            return fail(SAS_ERR_ARG, "Rg, xi and sigma must be > 0");
+        if (fn == SAS_FN_TEUBNER_STREY &&
+            !(m->f_p0 > 0.0 && m->f_p2 >= 0.0 && (m->f_p1 >= 0.0 || m->f_p1 * m->f_p1 < 4.0 * m->f_p0 * m->f_p2)))
+            return fail(SAS_ERR_ARG, "Teubner-Strey needs a2 > 0, c2 >= 0 and a2 + c1 Q^2 + c2 Q^4 > 0");
+        if (m->sq_kind != SAS_SQ_NONE || m->sampling != SAS_QUADRATURE || m->self_attenuation != 0)
+            return fail(SAS_ERR_ARG, "shape-independent laws take no S(Q), per-event sampling or self-attenuation");
+    }
     if (m->kind == SAS_ELLIPTICAL_CYLINDER && (!(m->radius_b > 0.0) || !(m->length > 0.0) ||
                                                !std::isfinite(m->radius_b) || !std::isfinite(m->axis_psi)))
         return fail(SAS_ERR_ARG, "elliptical cylinder needs radius, radius_b, length > 0 and a finite axis_psi");
@@ -931,7 +965,7 @@ sas_status validate_model(const sas_model_desc* m)
                      m->sld_solvent, m->volume_fraction, m->poly, m->sigma_orient, m->axis_theta,
                      m->axis_phi, m->sq_radius, m->sq_fraction}))
         return fail(SAS_ERR_ARG, "model has a non-finite value");
-    if (m->radius <= 0.0) return fail(SAS_ERR_ARG, "radius must be > 0");
+    if (m->radius <= 0.0 && m->kind != SAS_SHAPE_INDEPENDENT) return fail(SAS_ERR_ARG, "radius must be > 0");
     if (m->kind == SAS_CORE_SHELL && m->thickness < 0.0) return fail(SAS_ERR_ARG, "thickness must be >= 0");
     if (m->kind == SAS_CYLINDER && m->length <= 0.0) return fail(SAS_ERR_ARG, "length must be > 0");
     if (m->kind == SAS_ELLIPSOID && m->radius_polar <= 0.0) return fail(SAS_ERR_ARG, "radius_polar must be > 0");
@@ -1017,6 +1051,7 @@ cudaError_t dispatch_trace(sas_experiment* e, const TraceParams<T>& P, int* grid
     case SAS_CORE_SHELL_BICELLE: return Launcher<T, SAS_CORE_SHELL_BICELLE>::trace(P, e->cfg, e->sm_count, e->stream, grid);
     case SAS_ELLIPTICAL_CYLINDER: return Launcher<T, SAS_ELLIPTICAL_CYLINDER>::trace(P, e->cfg, e->sm_count, e->stream, grid);
     case SAS_HOLLOW_RECTANGULAR_PRISM: return Launcher<T, SAS_HOLLOW_RECTANGULAR_PRISM>::trace(P, e->cfg, e->sm_count, e->stream, grid);
+    case SAS_SHAPE_INDEPENDENT: return Launcher<T, SAS_SHAPE_INDEPENDENT>::trace(P, e->cfg, e->sm_count, e->stream, grid);
     default: return Launcher<T, SAS_ELLIPSOID>::trace(P, e->cfg, e->sm_count, e->stream, grid);
     }
 }
@@ -1038,6 +1073,7 @@ cudaError_t dispatch_records(sas_experiment* e, const TraceParams<T>& P)
     case SAS_CORE_SHELL_BICELLE: return Launcher<T, SAS_CORE_SHELL_BICELLE>::records(P, e->stream);
     case SAS_ELLIPTICAL_CYLINDER: return Launcher<T, SAS_ELLIPTICAL_CYLINDER>::records(P, e->stream);
     case SAS_HOLLOW_RECTANGULAR_PRISM: return Launcher<T, SAS_HOLLOW_RECTANGULAR_PRISM>::records(P, e->stream);
+    case SAS_SHAPE_INDEPENDENT: return Launcher<T, SAS_SHAPE_INDEPENDENT>::records(P, e->stream);
     default: return Launcher<T, SAS_ELLIPSOID>::records(P, e->stream);
     }
 }
@@ -1061,6 +1097,7 @@ cudaError_t dispatch_eval(sas_experiment* e, const ModelConst<T>& mc, const T* q
     case SAS_CORE_SHELL_BICELLE: return Launcher<T, SAS_CORE_SHELL_BICELLE>::eval(mc, poly, orient, q, out, n, e->stream);
     case SAS_ELLIPTICAL_CYLINDER: return Launcher<T, SAS_ELLIPTICAL_CYLINDER>::eval(mc, poly, orient, q, out, n, e->stream);
     case SAS_HOLLOW_RECTANGULAR_PRISM: return Launcher<T, SAS_HOLLOW_RECTANGULAR_PRISM>::eval(mc, poly, orient, q, out, n, e->stream);
+    case SAS_SHAPE_INDEPENDENT: return Launcher<T, SAS_SHAPE_INDEPENDENT>::eval(mc, poly, orient, q, out, n, e->stream);
     default: return Launcher<T, SAS_ELLIPSOID>::eval(mc, poly, orient, q, out, n, e->stream);
     }
 }

@@ -170,6 +170,7 @@ cudaError_t att_launch(const sas_model_desc& m, const ModelConst<T>& mc, const T
     case SAS_CORE_SHELL_BICELLE: return SAS_ATT_CASE(SAS_CORE_SHELL_BICELLE);
     case SAS_ELLIPTICAL_CYLINDER: return SAS_ATT_CASE(SAS_ELLIPTICAL_CYLINDER);
     case SAS_HOLLOW_RECTANGULAR_PRISM: return SAS_ATT_CASE(SAS_HOLLOW_RECTANGULAR_PRISM);
+    case SAS_SHAPE_INDEPENDENT: return SAS_ATT_CASE(SAS_SHAPE_INDEPENDENT);
     default: return SAS_ATT_CASE(SAS_ELLIPSOID);
     }
 #undef SAS_ATT_CASE

@@ -79,10 +79,11 @@ __device__ __forceinline__ void batch_item(const BatchParams& P, const ModelCons
     }
 }
 
-// FULL: every kind. The histogram kernel (batch_kernel<1>) is compiled
-// without the elliptical cylinder and the hollow prism, whose code would
-// push its register allocation into spills; the host launches batch_kernel<0>
-// for any batch that holds one of them.
+// FULL: every kind a batch takes (the shape-independent laws are refused on
+// the host). The histogram kernel (batch_kernel<1>) is compiled without the
+// elliptical cylinder and the hollow prism, whose code would push its
+// register allocation into spills; the host launches batch_kernel<0> for
+// any batch that holds one of them.
 template <int HIST, bool ATT, bool FULL>
 __device__ __forceinline__ void batch_dispatch(const BatchParams& P, const ModelConst<float>& mc, const float* poly,
                                                const float* orient, const WorkItem& w, const SmemHist& h,

@@ -711,12 +711,58 @@ __device__ __forceinline__ T avg_ellipsoid(const T qv[3], const T* __restrict__ 
     return k.s;
 }
 
+// Shape-independent laws f(|Q|) (parameters prepared on the host in f_a,
+// f_b, f_c): CUDA's accurate exp, expm1 and pow, one call per history. The
+// Gaussian coil takes its series sum_k 2 (-u)^k / (k + 2)! below u = 1
+// (FP32; 0.1 in FP64), where 2 (exp(-u) - 1 + u) / u^2 cancels.
+template <typename T>
+__device__ __forceinline__ T shape_independent(T q2, T q, const ModelConst<T>& mc)
+{
+    switch (mc.function) {
+    case SAS_FN_GUINIER: return exp(-q2 * mc.f_a);
+    case SAS_FN_GAUSS_COIL: {
+        const T u = q2 * mc.f_a;
+        constexpr bool fp32 = sizeof(T) == sizeof(float);
+        if (u < (fp32 ? (T)1 : (T)0.1)) {
+            constexpr int nt = fp32 ? 10 : 12;
+            T sum = 0, c = (T)2;   // c = 2 / (k + 2)!, from k = 0
+            T term[nt];
+#pragma unroll
+            for (int k = 0; k < nt; ++k) {
+                c = k == 0 ? (T)1 : c / (T)(k + 2);
+                term[k] = c;
+            }
+#pragma unroll
+            for (int k = nt - 1; k >= 0; --k) sum = fma(sum, -u, term[k]);
+            return sum;
+        }
+        return (T)2 * (expm1(-u) + u) / (u * u);
+    }
+    case SAS_FN_LORENTZ: return (T)1 / fma(q2, mc.f_a, (T)1);
+    case SAS_FN_DAB: {
+        const T d = fma(q2, mc.f_a, (T)1);
+        return (T)1 / (d * d);
+    }
+    case SAS_FN_POWER_LAW: return pow(q, -mc.f_a);
+    case SAS_FN_GAUSS_PEAK: {
+        const T d = q - mc.f_a;
+        return exp(-d * d * mc.f_b);
+    }
+    default: return (T)1 / fma(q2, fma(q2, mc.f_c, mc.f_b), mc.f_a);
+    }
+}
+
 // dSigma/dOmega(Q) in 1/angstrom
 template <typename T, int KIND>
 __device__ __forceinline__ T dsigma(const T qv[3], const ModelConst<T>& mc,
                                     const T* __restrict__ poly, const T* __restrict__ orient)
 {
     const T q2 = fma(qv[0], qv[0], fma(qv[1], qv[1], qv[2] * qv[2]));
+    if constexpr (KIND == SAS_SHAPE_INDEPENDENT) {
+        (void)poly;
+        (void)orient;
+        return mc.scale * shape_independent<T>(q2, ::sqrt(q2), mc);
+    }
     const T q = M<T>::sqrt_(q2);
     T avg;
     if (KIND == SAS_SPHERE) {
@@ -964,7 +1010,9 @@ __device__ __forceinline__ T dsigma_history(const T qv[3], const ModelConst<T>& 
                                             const T* __restrict__ orient, uint64_t seed, uint32_t exp_id,
                                             uint64_t index)
 {
-    if (mc.event) return dsigma_event<T, KIND>(qv, mc, poly, event_draws(seed, exp_id, index));
+    if constexpr (KIND != SAS_SHAPE_INDEPENDENT) {   // no draws: a law of |Q| only
+        if (mc.event) return dsigma_event<T, KIND>(qv, mc, poly, event_draws(seed, exp_id, index));
+    }
     return dsigma<T, KIND>(qv, mc, poly, orient);
 }
 

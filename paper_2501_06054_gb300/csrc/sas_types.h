@@ -104,6 +104,10 @@ struct ModelConst {
     T ev_k[4];       // shelled cylinders: the contrasts of c_1..c_4 (per-event amplitudes)
     // hollow rectangular prism: inner half-edges and the two a b c products
     T ax_ai, ax_bi, ax_ci, ax_v, ax_vi;
+    // shape-independent laws: the function and its parameters (Rg^2 / 3,
+    // Rg^2, xi^2, m, Q0 and 1 / (2 sigma^2), or a2, c1, c2 in f_a, f_b, f_c)
+    int function;
+    T f_a, f_b, f_c;
 };
 
 }  // namespace sas
