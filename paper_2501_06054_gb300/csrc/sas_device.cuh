@@ -1,7 +1,8 @@
 // Device building blocks of the SANS trace: Philox4x32-10, the neutron
-// history geometry, the fourteen form-factor models with their polydispersity
-// and orientation quadratures (or per-event draws), the Percus-Yevick
-// structure factor and the self-attenuation table. Templated on the
+// history geometry, the fourteen form-factor models with their
+// polydispersity and orientation quadratures (or per-event draws), the
+// shape-independent laws, the Percus-Yevick structure factor and the
+// self-attenuation table. Templated on the
 // arithmetic type: float (FP32 trace: sin, cos and sine from the
 // special-function unit where the tolerances allow, own polynomial forms of
 // 2 J1(x)/x and of the small-argument series) or double (FP64 trace, CUDA's
