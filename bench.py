@@ -11,8 +11,11 @@ FP32 Kahan tallies and the FP64 per-bin reduction), seed 1.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Under torchrun each rank traces its own index range [rank*n, (rank+1)*n)
-(weak scaling; the counter-based RNG makes the union one set of histories;
-no collective in the data path). `--impl reference` times the FP64 CPU
+(weak scaling; the counter-based RNG makes the union one set of histories)
+and every step ends with the one exchange of the method: an FP64
+sum-reduce of the detectors over NCCL (the paper's scatter/gather, Sec.
+II.C), inside the timed region. Rank 0 then checks the merged detector
+against one trace of the whole range. `--impl reference` times the FP64 CPU
 oracle on the host cores on a bounded sample of the same workload.
 Prints one JSON line on rank 0.
 """
@@ -578,16 +581,17 @@ def main():
 
     import paper_2501_06054_gb300 as sas
     from paper_2501_06054_gb300 import flops as F
+    from paper_2501_06054_gb300 import shard
 
     ws, rank, local = _dist()
-    if ws > 1:
-        dist.init_process_group("nccl")
     torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.cuda.current_device()
     stream = torch.cuda.Stream()
     cfg = W.core_shell_config()
     n = int(args.neutrons) if args.neutrons else cfg["n_neutrons"]
-    first = rank * n
+    first, _ = shard.weak_range(rank, n)
     seed = cfg["seed"]
     info = sas.sas_device_info()
 
@@ -599,10 +603,17 @@ def main():
     with torch.cuda.stream(stream):
         e = sas.Experiment(cfg["instrument"], cfg["model"], stream=stream)
         l2_flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        det = shard.detector_views(e.h, e.npix) if ws > 1 else None
+
+        def merge():
+            # the gather of the scatter/gather: one FP64 sum-reduce of the detector
+            if ws > 1:
+                shard.merge_detector(det)
 
         def step():
             sas.sas_reset_detector(e.h)
             sas.sas_trace_range(e.h, first, n, seed)
+            merge()
 
         for _ in range(args.warmup):
             step()
@@ -613,6 +624,7 @@ def main():
         barrier()
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         kstarts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        kends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         for k in range(args.steps):
             l2_flush.fill_(float(k))          # untimed: flush L2 between steps
@@ -620,11 +632,14 @@ def main():
             sas.sas_reset_detector(e.h)
             kstarts[k].record(stream)
             sas.sas_trace_range(e.h, first, n, seed)
+            kends[k].record(stream)
+            merge()
             ends[k].record(stream)
         barrier()
         clocks = sampler.stop()
         step_ms = [s.elapsed_time(t) for s, t in zip(starts, ends)]
-        kern_ms = [s.elapsed_time(t) for s, t in zip(kstarts, ends)]
+        kern_ms = [s.elapsed_time(t) for s, t in zip(kstarts, kends)]
+        merge_ms = [s.elapsed_time(t) for s, t in zip(kends, ends)]
         ms = sum(step_ms) / len(step_ms)
         kms = sum(kern_ms) / len(kern_ms)
         t_ms = torch.tensor([ms, kms], dtype=torch.float64, device="cuda")
@@ -632,7 +647,22 @@ def main():
             dist.all_reduce(t_ms, op=dist.ReduceOp.MAX)
         ms, kms = float(t_ms[0]), float(t_ms[1])
         d = e.read()
-        ok_counts = int(d["count"].sum()) == n
+        ok_counts = int(d["count"].sum()) == n * ws
+        merged = None
+        if ws > 1 and rank == 0:
+            # the merged detector against one trace of the whole range [0, n ws)
+            ef = sas.Experiment(cfg["instrument"], cfg["model"], stream=stream)
+            ef.trace(n * ws, seed)
+            df = ef.read()
+            ef.close()
+            big = df["sum_w"] > 1e-6 * df["sum_w"].max()
+            rel = np.abs(d["sum_w"] - df["sum_w"])[big] / df["sum_w"][big]
+            merged = {"counts_equal": bool(np.array_equal(d["count"], df["count"])),
+                      "max_bin_rel_diff": float(rel.max()),
+                      "transmitted_rel_diff": abs(d["trans"] / df["trans"] - 1.0),
+                      "merge_ms": sum(merge_ms) / len(merge_ms),
+                      "note": "detector summed over ranks (NCCL all-reduce, FP64) vs one trace of "
+                              "the whole index range on rank 0; bins >= 1e-6 max"}
 
         # end to end through the public API: model upload (H2D), trace,
         # detector read-back into host buffers (D2H), every step
@@ -643,6 +673,7 @@ def main():
             sas.sas_set_model(e.h, cfg["model"])
             sas.sas_reset_detector(e.h)
             sas.sas_trace_range(e.h, first, n, seed)
+            merge()
             sas.sas_read_detector(e.h, npix, **hbuf)
         barrier()
         e2e_steps = max(3, min(args.steps, 10))
@@ -651,6 +682,7 @@ def main():
             sas.sas_set_model(e.h, cfg["model"])
             sas.sas_reset_detector(e.h)
             sas.sas_trace_range(e.h, first, n, seed)
+            merge()
             sas.sas_read_detector(e.h, npix, **hbuf)
         barrier()
         e2e_s = (time.perf_counter() - t0) / e2e_steps
@@ -691,7 +723,8 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "neutrons_per_step": n * ws, "seed": seed,
                    "l2": "flushed between timed steps (256 MiB write, untimed)",
-                   "all_histories_counted": ok_counts},
+                   "all_histories_counted": ok_counts,
+                   "parallelism": f"dp{ws}: index ranges per rank, FP64 detector sum-reduce per step"},
         "roofline": roofline,
         "e2e": {"value": n * ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": tables_bytes,
                 "d2h_bytes_per_step": d2h,
@@ -699,6 +732,8 @@ def main():
         "gpu_launches": args.steps,
         "clocks": clocks,
     }
+    if merged is not None:
+        line["merged_detector"] = merged
     if ws == 1 and not args.no_secondary:
         try:
             with torch.cuda.stream(stream):

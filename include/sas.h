@@ -241,17 +241,23 @@ typedef struct sas_model_desc {
 
 typedef struct sas_experiment sas_experiment;   /* opaque, library-owned */
 
-/* Create an experiment on the current CUDA device: validates the instrument
- * and allocates its FP64 detector (sum w, sum w^2, counts) and the
- * transmitted-weight scalar in device memory. *out is owned by the caller
- * until sas_destroy_experiment. SAS_ERR_ARG on invalid geometry. */
+/* Create an experiment on the current CUDA device (Sec. II.A: the virtual
+ * instrument of a test run -- source, collimation by two pinholes, sample,
+ * 2D position-sensitive detector at a set distance): validates the
+ * instrument and allocates its FP64 detector (sum w, sum w^2, counts) and
+ * the transmitted-weight scalar in device memory. *out is owned by the
+ * caller until sas_destroy_experiment. SAS_ERR_ARG on invalid geometry. */
 sas_status sas_create_experiment(const sas_instrument *inst, void *stream,
                                  sas_experiment **out);
 
-/* Replace the sample model: validates it, builds the FP64 quadrature tables
+/* Replace the sample model (Sec. II.A, Eqs. 1-4: amplitude, intensity and
+ * the dilute-limit cross section phi drho^2 V P S; Eq. 7 for uniaxial
+ * bodies; Eq. 8, the cylinder; Sec. II.B: distributions of the radii and of
+ * the particle axis): validates it, builds the FP64 quadrature tables
  * (Schulz generalised Gauss-Laguerre nodes, Gaussian-cap orientation nodes
  * on a Gauss-Legendre grid in (gamma, psi)) and the Percus-Yevick series,
- * rounds them to the trace precision and uploads them (stream-ordered). */
+ * rounds them to the trace precision and uploads them (stream-ordered).
+ * SAS_ERR_ARG on an invalid model (the message names the field). */
 sas_status sas_set_model(sas_experiment *exp, const sas_model_desc *model);
 
 /* Select the Philox experiment id (counter word 1) used by later traces
@@ -261,19 +267,29 @@ sas_status sas_set_experiment_id(sas_experiment *exp, uint32_t id);
 /* Change the stream later calls enqueue on. */
 sas_status sas_set_stream(sas_experiment *exp, void *stream);
 
-/* Zero the detector, then trace neutrons [0, n_neutrons). Asynchronous. */
+/* Zero the detector, then trace neutrons [0, n_neutrons) (Sec. I: each
+ * neutron history is independent of the others, single scattering; Sec.
+ * II.A: the instrument chain; Eqs. 1-4 weight every history by the model's
+ * cross section). Asynchronous on the experiment's stream; SAS_ERR_STATE
+ * before sas_set_model. */
 sas_status sas_trace(sas_experiment *exp, uint64_t n_neutrons, uint64_t seed);
 
-/* Trace neutrons [first, first + n) and ADD them to the detector (resume,
- * sharding). Asynchronous. */
+/* Trace neutrons [first, first + n) and ADD them to the detector: resume a
+ * run, or trace one share of a scatter/gather split of the index range
+ * across processes or GPUs (Sec. II.C; the histories of any split are the
+ * histories of the whole range). Asynchronous; SAS_ERR_STATE before
+ * sas_set_model; SAS_ERR_ARG if first + n overflows 64 bits. */
 sas_status sas_trace_range(sas_experiment *exp, uint64_t first, uint64_t n, uint64_t seed);
 
 /* Zero the detector and transmitted weight. Asynchronous. */
 sas_status sas_reset_detector(sas_experiment *exp);
 
-/* Copy the detector into caller-owned HOST buffers of n_pixels entries
- * (n_pixels must equal nx*ny; any pointer may be NULL to skip it) and the
- * transmitted weight (may be NULL). Synchronises the stream. */
+/* Copy the detector (the 2D PSD of Sec. II.A: per pixel sum of weights,
+ * sum of squared weights, histories) into caller-owned HOST buffers of
+ * n_pixels entries (n_pixels must equal nx*ny, else SAS_ERR_ARG; any
+ * pointer may be NULL to skip it) and the transmitted weight (may be NULL).
+ * Intensity per incident neutron = sum_w / histories traced. Synchronises
+ * the stream. */
 sas_status sas_read_detector(const sas_experiment *exp, double *sum_w, double *sum_w2,
                              uint64_t *count, size_t n_pixels, double *transmitted);
 
@@ -282,8 +298,8 @@ sas_status sas_detector_device(const sas_experiment *exp, const double **sum_w,
                                const double **sum_w2, const uint64_t **count,
                                const double **transmitted);
 
-/* Parity hook: dSigma/dOmega (1/angstrom) of the experiment's model at n
- * scattering vectors. q_xyz: DEVICE float[n][3]; out: DEVICE float[n]
+/* Parity hook: dSigma/dOmega (1/angstrom; Eqs. 1-4, 7, 8 averaged per
+ * Sec. II.B) of the experiment's model at n scattering vectors. q_xyz: DEVICE float[n][3]; out: DEVICE float[n]
  * (model precision FP32) -- or double pointers if the model is FP64.
  * Asynchronous on the experiment's stream. SAS_ERR_STATE for a per-event
  * model (its cross section is a random draw per history; the records below
@@ -382,11 +398,14 @@ sas_status sas_create_batch(const sas_instrument *inst, const sas_model_desc *mo
 /* Zero all detectors and trace every experiment: one CUDA-graph launch
  * (memsets + one persistent kernel pulling work items from an atomic
  * counter). The graph is captured on first use and after config changes.
- * Asynchronous on the batch's stream. */
+ * Sec. I motivates the batch: large data sets of virtual experiments over a
+ * model's parameter space; each experiment's histories are those of
+ * sas_trace with experiment id e. Asynchronous on the batch's stream. */
 sas_status sas_trace_batch(sas_batch *batch, uint64_t seed);
 
-/* Copy experiment exp's detector into caller-owned host buffers
- * (n_pixels = nx*ny; NULL pointers skip). Synchronises the stream. */
+/* Copy experiment exp's detector (as sas_read_detector) into caller-owned
+ * host buffers (n_pixels = nx*ny, else SAS_ERR_ARG; exp >= n_exp is
+ * SAS_ERR_ARG; NULL pointers skip). Synchronises the stream. */
 sas_status sas_read_batch_detector(const sas_batch *batch, size_t exp, double *sum_w, double *sum_w2,
                                    uint64_t *count, size_t n_pixels, double *transmitted);
 
@@ -425,8 +444,14 @@ sas_status sas_destroy_batch(sas_batch *batch);
  * and the seed go to one static device array of 8 MiB that every GPU loading
  * the library holds until process exit. A batch whose tables and items do
  * not fit returns SAS_ERR_ARG with the bytes it would need.
- * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.
+ * Every call looks up the array's device address in the caller's current
+ * CUDA context (cudaGetSymbolAddress, with the caller's device current):
+ * each context that loads the library, e.g. a plugin host's own driver-API
+ * context, or the primary context re-created after cudaDeviceReset, has its
+ * own copy of the array. The first call in a context also loads the
+ * library's device code there; make that first call before any stream
+ * capture. The uploads are copies from pageable host memory, so the call may
+ * block until they are staged.
  * All calls share the array and it keeps the last call's contents: calls
  * that overlap on the GPU (e.g. on two streams) race, so issue them in
  * order on one stream or synchronise between them. */
@@ -435,7 +460,11 @@ sas_status sas_trace_batch_static(const sas_instrument *inst, const sas_model_de
                                   double *sum_w, double *sum_w2, uint64_t *count,
                                   double *transmitted, void *stream);
 
-/* ---- learned surrogate of the averaged cylinder form factor --------- */
+/* ---- learned surrogate of the averaged cylinder form factor ---------
+ * The paper has no learned part. The network stands in for the cylinder's
+ * cross section of Eq. 8 averaged over the radius and axis distributions of
+ * Sec. II.B, the costly step of the anisotropic models (Sec. III.B names the
+ * cylinder family among those that gain most on a GPU). */
 
 typedef struct sas_surrogate sas_surrogate;          /* opaque, library-owned */
 

@@ -42,10 +42,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "sas_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
-# SAS_ORACLE_MUTATION=<k> builds and loads a copy with planted mistake k
-# (only tests/test_mutations.py sets it, to check that the pins catch it).
-_MUT = int(os.environ.get("SAS_ORACLE_MUTATION", "0") or 0)
-_LIB_PATH = os.path.join(_BUILD, "libsas_oracle.so" if _MUT == 0 else f"libsas_oracle_mut{_MUT}.so")
+_LIB_PATH = os.path.join(_BUILD, "libsas_oracle.so")
 _lib = None
 _lock = threading.Lock()
 
@@ -58,7 +55,7 @@ def build(force: bool = False) -> str:
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
-           "-fno-fast-math", f"-DSAS_MUT={_MUT}", _SRC, "-o", tmp, "-lm"]
+           "-fno-fast-math", _SRC, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -180,8 +177,6 @@ def schulz_nodes(mean: float, p: float, n: int):
         return np.array([float(mean)]), np.array([1.0])
     z = 1.0 / (p * p) - 1.0
     x, w = gauss_laguerre_gen(n, z)
-    if _MUT == 6:
-        return mean * x / z, w
     return mean * x / (z + 1.0), w
 
 
@@ -295,7 +290,7 @@ def orientation_nodes(theta, phi, sigma, n_gamma, n_psi, isotropic=False):
     xg, wg = gauss_legendre(n_gamma)
     xp, wp = gauss_legendre(n_psi)
     gam = 0.5 * gmax * (xg + 1.0)
-    wgam = 0.5 * gmax * wg * (1.0 if _MUT == 5 else np.sin(gam))
+    wgam = 0.5 * gmax * wg * np.sin(gam)
     if not isotropic:
         wgam = wgam * np.exp(-gam * gam / (2.0 * sigma * sigma))
     psi = math.pi * (xp + 1.0)

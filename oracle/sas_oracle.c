@@ -45,12 +45,6 @@
 
 static void gl_nodes(int n, double *x, double *w);
 
-/* Planted mistakes for the pin tests' mutation check (tests/test_mutations.py):
- * the default build compiles none of them (SAS_MUT = 0). */
-#ifndef SAS_MUT
-#define SAS_MUT 0
-#endif
-
 /* ---------------------------------------------------------------- Philox */
 
 void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
@@ -59,7 +53,7 @@ void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t
     uint32_t k0 = key[0], k1 = key[1];
     for (int round = 0; round < 10; ++round) {
         uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
-        uint64_t p1 = (uint64_t)(SAS_MUT == 10 ? 0xCD9E8D55u : 0xCD9E8D57u) * (uint64_t)c2;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
         uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
         uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
         uint32_t n0 = hi1 ^ c1 ^ k0;
@@ -148,7 +142,6 @@ double oracle_sphere_f(double x)
         return 1.0 - t / 10.0 * (1.0 - t / 28.0 * (1.0 - t / 54.0 * (1.0 - t / 88.0
                                                         * (1.0 - t / 130.0))));
     }
-    if (SAS_MUT == 2) return 3.0 * (sin(x) - cos(x)) / (x * x * x);
     return 3.0 * (sin(x) - x * cos(x)) / (x * x * x);
 }
 
@@ -204,7 +197,7 @@ double oracle_sq_py(double q, double radius, double phi)
     double A = 2.0 * fabs(q) * radius;
     double d = pow(1.0 - phi, 4);
     double alpha = (1.0 + 2.0 * phi) * (1.0 + 2.0 * phi) / d;
-    double beta = (SAS_MUT == 3 ? 6.0 : -6.0) * phi * (1.0 + 0.5 * phi) * (1.0 + 0.5 * phi) / d;
+    double beta = -6.0 * phi * (1.0 + 0.5 * phi) * (1.0 + 0.5 * phi) / d;
     double gamma = 0.5 * phi * alpha;
     double GA; /* G(A)/A */
     if (A < 0.5) {
@@ -252,7 +245,6 @@ static double oracle_shape_independent(const oracle_model *m, double q)
     case 1: {
         double u = q2 * m->f_p0 * m->f_p0;
         f = u < 1e-3 ? 1.0 - u / 3.0 + u * u / 12.0 : 2.0 * (expm1(-u) + u) / (u * u);
-        if (SAS_MUT == 28) f = u < 1e-3 ? 1.0 : 2.0 * (exp(-u) + u) / (u * u);
         break;
     }
     case 2: f = 1.0 / (1.0 + q2 * m->f_p0 * m->f_p0); break;
@@ -283,7 +275,7 @@ double oracle_dsigma(const oracle_model *m, const double q[3])
             double rc = m->poly_r[i], ro = rc + m->thickness;
             double Vc = sphere_volume(rc), Vo = sphere_volume(ro);
             double F = (m->sld - m->sld_shell) * Vc * oracle_sphere_f(qq * rc)
-                     + (m->sld_shell - m->sld_solvent) * (SAS_MUT == 11 ? Vc : Vo) * oracle_sphere_f(qq * ro);
+                     + (m->sld_shell - m->sld_solvent) * Vo * oracle_sphere_f(qq * ro);
             sum += m->poly_w[i] * F * F;
             vmean += m->poly_w[i] * Vo;
         }
@@ -298,12 +290,12 @@ double oracle_dsigma(const oracle_model *m, const double q[3])
             double x1 = q[2] * c[0] - q[0] * c[2];
             double x2 = q[0] * c[1] - q[1] * c[0];
             double qab = sqrt(x0 * x0 + x1 * x1 + x2 * x2);
-            double s = oracle_sinc(0.5 * (SAS_MUT == 4 ? qab : qc) * m->length);
+            double s = oracle_sinc(0.5 * qc * m->length);
             double inner = 0.0;
             for (int64_t i = 0; i < np; ++i) {
                 double r = m->poly_r[i];
                 double V = PI * r * r * m->length;
-                double F = drho * V * s * oracle_cyl_a((SAS_MUT == 4 ? qc : qab) * r);
+                double F = drho * V * s * oracle_cyl_a(qab * r);
                 inner += m->poly_w[i] * F * F;
             }
             sum += m->orient_w[o] * inner;
@@ -327,7 +319,7 @@ double oracle_dsigma(const oracle_model *m, const double q[3])
         double vo = m->kind == 4 ? 4.0 / 3.0 * PI * a0 * b0 * c0
                   : m->kind == 12 ? PI * a0 * b0 * 2.0 * c0 : 8.0 * a0 * b0 * c0;
         double vi = m->kind == 13 ? 8.0 * ai * bi * ci : 0.0;
-        double v0 = vo - (SAS_MUT == 27 ? 0.0 : vi);
+        double v0 = vo - vi;
         for (int64_t i = 0; i < np; ++i) {
             double s = m->poly_r[i] / m->radius;
             vmean += m->poly_w[i] * v0 * s * s * s;
@@ -345,15 +337,15 @@ double oracle_dsigma(const oracle_model *m, const double q[3])
                     double xa = s * a0 * qa, xb = s * b0 * qb, xc = s * c0 * qc;
                     F = drho * V * oracle_sphere_f(sqrt(xa * xa + xb * xb + xc * xc));
                 } else if (m->kind == 12) {
-                    double xa = s * a0 * qa, xb = s * (SAS_MUT == 26 ? a0 : b0) * qb;
+                    double xa = s * a0 * qa, xb = s * b0 * qb;
                     F = drho * V * oracle_sinc(s * c0 * qc) * oracle_cyl_a(sqrt(xa * xa + xb * xb));
                 } else if (m->kind == 13) {
                     double s3 = s * s * s;
                     F = drho * s3 * (vo * oracle_sinc(s * a0 * qa) * oracle_sinc(s * b0 * qb) * oracle_sinc(s * c0 * qc)
                                      - vi * oracle_sinc(s * ai * qa) * oracle_sinc(s * bi * qb) * oracle_sinc(s * ci * qc));
                 } else {
-                    F = drho * V * oracle_sinc(s * a0 * qa) * oracle_sinc(s * b0 * (SAS_MUT == 13 ? qc : qb))
-                      * oracle_sinc(s * c0 * (SAS_MUT == 13 ? qb : qc));
+                    F = drho * V * oracle_sinc(s * a0 * qa) * oracle_sinc(s * b0 * qb)
+                      * oracle_sinc(s * c0 * qc);
                 }
                 inner += m->poly_w[i] * F * F;
             }
@@ -379,7 +371,7 @@ double oracle_dsigma(const oracle_model *m, const double q[3])
         double drho = m->sld - m->sld_solvent;
         double r0 = m->radius, R0 = m->radius_polar, L0 = m->length;
         double h0 = sqrt(fmax(R0 * R0 - r0 * r0, 0.0));
-        double H0 = (m->kind == 6) != (SAS_MUT == 19) ? r0 * r0 / (R0 + h0) : R0 + h0;
+        double H0 = m->kind == 6 ? r0 * r0 / (R0 + h0) : R0 + h0;
         int nc = (int)m->n_cap;
         double gx[64], gw[64], uj[64], wj[64];
         gl_nodes(nc, gx, gw);
@@ -408,8 +400,8 @@ double oracle_dsigma(const oracle_model *m, const double q[3])
                 double cap = 0.0;
                 for (int j = 0; j < nc; ++j) {
                     double v = uj[j] * (2.0 - uj[j]);
-                    cap += wj[j] * cos(qc * (0.5 * L + H - R * uj[j])) * (SAS_MUT == 20 ? 1.0 : v)
-                         * oracle_cyl_a(qab * (SAS_MUT == 21 ? R : R * sqrt(v)));
+                    cap += wj[j] * cos(qc * (0.5 * L + H - R * uj[j])) * v
+                         * oracle_cyl_a(qab * R * sqrt(v));
                 }
                 F = drho * (F + 2.0 * PI * R * R * R * cap);
                 inner += m->poly_w[i] * F * F;
@@ -431,7 +423,7 @@ double oracle_dsigma(const oracle_model *m, const double q[3])
          * The core (hollow) radius r is polydisperse, t, t_f and L fixed. */
         double t = m->thickness, L = m->length;
         double tf = m->kind == 8 ? m->thickness_face : 0.0;
-        double d1 = m->kind == 8 ? m->sld - m->sld_shell : (SAS_MUT == 23 ? 1.0 : -1.0) * (m->sld - m->sld_solvent);
+        double d1 = m->kind == 8 ? m->sld - m->sld_shell : -(m->sld - m->sld_solvent);
         double d2 = m->kind == 8 ? m->sld_shell - m->sld_solvent : m->sld - m->sld_solvent;
         for (int64_t i = 0; i < np; ++i) {
             double r = m->poly_r[i], ro = r + t;
@@ -445,7 +437,7 @@ double oracle_dsigma(const oracle_model *m, const double q[3])
             double x2 = q[0] * c[1] - q[1] * c[0];
             double qab = sqrt(x0 * x0 + x1 * x1 + x2 * x2);
             double s1 = oracle_sinc(0.5 * qc * L);
-            double s2 = oracle_sinc(qc * (0.5 * L + (SAS_MUT == 22 ? 0.0 : tf)));
+            double s2 = oracle_sinc(qc * (0.5 * L + tf));
             double inner = 0.0;
             for (int64_t i = 0; i < np; ++i) {
                 double r = m->poly_r[i], ro = r + t;
@@ -484,7 +476,7 @@ double oracle_dsigma(const oracle_model *m, const double q[3])
                 double ar = oracle_cyl_a(qab * r), ao = oracle_cyl_a(qab * ro);
                 double F = dc * PI * r * r * L * s1 * ar
                          + df * PI * r * r * Lo * s2 * ar
-                         + dr * PI * ro * ro * Lo * (SAS_MUT == 25 ? s1 : s2) * ao;
+                         + dr * PI * ro * ro * Lo * s2 * ao;
                 inner += m->poly_w[i] * F * F;
             }
             sum += m->orient_w[o] * inner;
@@ -498,7 +490,7 @@ double oracle_dsigma(const oracle_model *m, const double q[3])
          * surface, V = 4/3 pi r_e^2 r_p; normalised by <V_o>. The core's
          * equatorial radius is polydisperse, r_p, t and t_p fixed. */
         double rp = m->radius_polar, t = m->thickness;
-        double rpo = rp + (SAS_MUT == 24 ? 0.0 : m->thickness_face);
+        double rpo = rp + m->thickness_face;
         for (int64_t i = 0; i < np; ++i) {
             double ro = m->poly_r[i] + t;
             vmean += m->poly_w[i] * 4.0 / 3.0 * PI * ro * ro * (rp + m->thickness_face);
@@ -594,7 +586,6 @@ double oracle_event_radius(double R, double p, uint32_t x)
     double v = lo + u * (1.0 - lo), z;
     if (v < 0.5) z = -sqrt(2.0) * oracle_erfcinv(2.0 * v);
     else z = sqrt(2.0) * oracle_erfcinv(2.0 * uc * (1.0 - lo));
-    if (SAS_MUT == 12) z = -sqrt(2.0) * oracle_erfcinv(2.0 * u);   /* drops the restriction */
     return R * (1.0 + p * z);
 }
 
@@ -609,7 +600,6 @@ void oracle_event_axis(int64_t mode, double theta0, double phi0, uint32_t xa, ui
     } else if (mode == 2) {
         double th = PI * u01(xa);
         ct = cos(th); st = sin(th);
-        if (SAS_MUT == 16) { ct = 1.0 - 2.0 * u01(xa); st = sqrt(fmax(0.0, 1.0 - ct * ct)); }
     } else {
         ct = cos(theta0); st = sin(theta0);
         c[0] = st * cos(phi0); c[1] = st * sin(phi0); c[2] = ct;
@@ -628,8 +618,8 @@ void oracle_frame(double theta, double phi, double psi, double f[9])
     double sq = sin(psi), cq = cos(psi);
     double et[3] = {ct * cp, ct * sp, -st}, ep[3] = {-sp, cp, 0.0};
     for (int k = 0; k < 3; ++k) {
-        f[k] = cq * et[k] + (SAS_MUT == 18 ? -sq : sq) * ep[k];
-        f[3 + k] = (SAS_MUT == 18 ? sq : -sq) * et[k] + cq * ep[k];
+        f[k] = cq * et[k] + sq * ep[k];
+        f[3 + k] = -sq * et[k] + cq * ep[k];
     }
     f[6] = st * cp; f[7] = st * sp; f[8] = ct;
 }
@@ -842,7 +832,6 @@ static double sigma_s_panels(const oracle_model *m, double lambda, double lambda
                 double wq = sc * 0.5 * (b - a) * gw[g];
                 double st = sqrt(fmax(1.0 - Q * Q / (4.0 * k * k), 0.0));
                 double qz = -Q * Q / (2.0 * k);
-                if (SAS_MUT == 14) qz = 0.0;
                 double ring = 0.0;
 #pragma omp parallel for reduction(+ : ring) schedule(static) if (nphi >= 64)
                 for (int j = 0; j < nphi; ++j) {
@@ -850,7 +839,7 @@ static double sigma_s_panels(const oracle_model *m, double lambda, double lambda
                     double q[3] = {Q * st * cos(ph), Q * st * sin(ph), qz};
                     ring += oracle_dsigma(m, q);
                 }
-                panel += wq * (SAS_MUT == 15 ? 1.0 : Q) * ring * (2.0 * PI / nphi);
+                panel += wq * Q * ring * (2.0 * PI / nphi);
             }
             total += panel;
         }
@@ -908,7 +897,7 @@ static void att_setup(const oracle_instrument *in, const oracle_model *m, oracle
     for (int i = 0; i < n; ++i) {
         double c = 0.0;
         for (int j = 0; j < n; ++j) c += a->mu[j] * cos(PI * i * (j + 0.5) / n);
-        a->c[i] = (i == 0 && SAS_MUT != 17 ? 1.0 : 2.0) * c / n;
+        a->c[i] = (i == 0 ? 1.0 : 2.0) * c / n;
     }
 }
 
@@ -950,7 +939,6 @@ void oracle_att_eval(const oracle_instrument *in, const oracle_model *m, const d
 double oracle_sample_lambda(double lambda0, double drel, double u)
 {
     double T = (u < 0.5) ? sqrt(2.0 * u) - 1.0 : 1.0 - sqrt(2.0 * (1.0 - u));
-    if (SAS_MUT == 1) T = 2.0 * u - 1.0;
     return lambda0 * (1.0 + drel * T);
 }
 
@@ -1037,10 +1025,9 @@ static int history_geometry(const oracle_instrument *in, const oracle_att *att, 
     double e_in, e_out, l_out = 0.0;
     if (slab(in, ps, k_out, &e_in, &e_out)) l_out = e_out - e_in;
     *atten = exp(-mu * (s + l_out));
-    if (SAS_MUT == 8) domega = area * k_out[2] / rr;
     *l_path = l;
     *d_omega = domega;
-    *pixel = iy * in->nx + ix + (SAS_MUT == 7 && ix + 1 < in->nx ? 1 : 0);
+    *pixel = iy * in->nx + ix;
     return 1;
 }
 

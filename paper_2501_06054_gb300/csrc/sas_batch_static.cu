@@ -11,7 +11,6 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
-#include <mutex>
 #include <string>
 #include <vector>
 
@@ -30,31 +29,25 @@ using namespace sas;
 
 // The scratch. Host code must not pass this name to a kernel: on the host it
 // is only a stand-in for the symbol. Its device address comes from
-// cudaGetSymbolAddress (scratch_base below).
+// cudaGetSymbolAddress in the caller's current context (scratch_base below).
 static __device__ __align__(256) unsigned char g_batch_scratch[SAS_STATIC_SCRATCH_BYTES];
 
 namespace {
 
-constexpr int MAX_DEVICES = 64;
-std::mutex g_mu;
-unsigned char* g_base[MAX_DEVICES] = {};
-
-// Device address of the scratch on the current device, looked up once per
-// device with that device current.
+// Device address of the scratch in the current CUDA context, looked up on
+// every call with the caller's device current. The address belongs to the
+// module loaded in that context, not to the device: a second context on the
+// same GPU (a plugin host's own driver-API context) or the primary context
+// re-created after cudaDeviceReset gets its own copy of the array at its
+// own address, so nothing is cached across calls. The lookup is a host-side
+// table query once the module is loaded (the first call in a context loads
+// it).
 sas_status scratch_base(unsigned char** out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return set_cuda_error(e, "cudaGetDevice");
-    if (dev < 0 || dev >= MAX_DEVICES) return set_error(SAS_ERR_ARG, "device ordinal out of range");
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_base[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_batch_scratch);
-        if (e != cudaSuccess) return set_cuda_error(e, "cudaGetSymbolAddress(static batch scratch)");
-        g_base[dev] = static_cast<unsigned char*>(p);
-    }
-    *out = g_base[dev];
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_batch_scratch);
+    if (e != cudaSuccess) return set_cuda_error(e, "cudaGetSymbolAddress(static batch scratch)");
+    *out = static_cast<unsigned char*>(p);
     return SAS_OK;
 }
 

@@ -145,3 +145,35 @@ def test_host_utilities_reject_bad_sizes():
         sas.sas_schulz_nodes(10.0, 0.1, 65)
     with pytest.raises(sas.SasError):
         sas.sas_orientation_nodes(0, 0, 0.1, 129, 2)
+
+
+@pytest.mark.parametrize("name", ["sas_instrument", "sas_model_desc", "sas_launch_config",
+                                  "sas_batch_config", "sas_surrogate_box"])
+def test_struct_layout_matches_binding(name, tmp_path):
+    """The ctypes mirror of each public struct has the C header's size and
+    field offsets: a small C program compiled against include/sas.h prints
+    sizeof and offsetof for every field the binding names (a field missing
+    from the header fails the compile)."""
+    import ctypes
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    st = getattr(sas, name)
+    fields = [f[0] for f in st._fields_]
+    src = ["#include <stddef.h>", "#include <stdio.h>", '#include "sas.h"', "int main(void) {",
+           f'  printf("%zu\\n", sizeof({name}));']
+    src += [f'  printf("%zu\\n", offsetof({name}, {f}));' for f in fields]
+    src += ["  return 0;", "}"]
+    c = tmp_path / "layout.c"
+    c.write_text("\n".join(src) + "\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True,
+                                          check=True).stdout.split()]
+    assert out[0] == ctypes.sizeof(st), (name, out[0], ctypes.sizeof(st))
+    for f, off in zip(fields, out[1:]):
+        assert off == getattr(st, f).offset, (name, f, off, getattr(st, f).offset)

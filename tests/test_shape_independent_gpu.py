@@ -1,7 +1,16 @@
 """Shape-independent laws (dSigma/dOmega = f_scale f(|Q|)) on the GPU
-against the FP64 oracle: evaluations of every law in FP32 and FP64 (T1,
-with the absolute part taken from the largest value on the grid), records,
-a traced detector, and the refusals."""
+against the FP64 oracle: evaluations of every law in FP32 and FP64, records,
+a traced detector, and the refusals.
+
+Evaluation tolerance. The laws that stay within a few decades of their
+largest value over the whole grid and have no zeros (power law, Lorentzian,
+Debye-Anderson-Brumberger, Teubner-Strey) are held to the relative part of
+T1 alone (FP32 1e-5, FP64 1e-10): an absolute floor taken from their
+largest value would exceed most of the values themselves (the power law
+spans 14 decades from |Q| = 1e-4 to 1). The laws with a finite forward
+value whose tails fall below FP32's range (Guinier, Gaussian coil) or
+vanish away from a peak (Gaussian peak) keep T1's absolute part, 1e-7 of
+their forward (peak) value, the same rule as the form factors' 1e-7 P(0)."""
 import numpy as np
 import pytest
 
@@ -19,6 +28,9 @@ def _cuda():
         pytest.skip("no CUDA device")
     yield
 
+
+# laws held to the relative tolerance alone (no zeros, no underflow on the grid)
+RELATIVE_ONLY = {"lorentz", "dab", "power_law", "teubner_strey"}
 
 LAWS = {
     "guinier": (W.GUINIER, (40.0, 0.0, 0.0)),
@@ -56,8 +68,11 @@ def test_law_parity(name, precision):
     qd = torch.tensor(q, dtype=dt).double().numpy()
     ref = oracle.dsigma(oracle.Prepared(m), qd)
     rel, ab = (1e-10, 1e-13) if precision == W.FP64 else (1e-5, 1e-7)
+    if name in RELATIVE_ONLY:
+        ab = 0.0
     err = np.abs(got - ref)
-    assert np.all(err <= rel * np.abs(ref) + ab * ref.max()), (name, np.max(err / (np.abs(ref) + ref.max())))
+    assert np.all(err <= rel * np.abs(ref) + ab * ref.max()), \
+        (name, np.max(err / (rel * np.abs(ref) + ab * ref.max())))
     e.close()
 
 

@@ -1,10 +1,12 @@
-"""Multi-rank partition of the trace (CPU, gloo, world size 2).
+"""Multi-rank partition of the trace (CPU, gloo, world sizes 2 and 3).
 
 The counter-based streams make a history depend only on (seed, experiment,
 index), so ranks that trace disjoint index ranges and sum their detectors
 with one reduction reproduce the single-process run (the paper's
 scatter/gather of ncount over ranks, Sec. II.C). The ranks here run the
-oracle; the partition and the reduction are what is tested.
+oracle; the index split and the reduction are the library's own
+(`paper_2501_06054_gb300.shard`, the code bench.py's multi-GPU path runs
+over NCCL), driven over gloo.
 """
 import os
 import socket
@@ -23,49 +25,56 @@ def _free_port():
     return p
 
 
-def _rank_range(rank, world, n):
-    """The split bench.py uses for weak scaling generalised to a fixed total:
-    contiguous, disjoint, covering [0, n)."""
-    base, extra = divmod(n, world)
-    first = rank * base + min(rank, extra)
-    return first, base + (1 if rank < extra else 0)
-
-
-def _worker(rank, world, port, n, out_path):
+def _worker(rank, world, port, n, mode, dst, out_path):
     import torch.distributed as dist
     import oracle
     import sas_workloads as W
+    from paper_2501_06054_gb300 import shard
     dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank,
                             world_size=world)
     cfg = W.core_shell_config()
-    first, cnt = _rank_range(rank, world, n)
+    first, cnt = shard.rank_range(rank, world, n) if mode == "strong" else shard.weak_range(rank, n)
     r = oracle.trace(cfg["instrument"], cfg["model"], cnt, seed=3, first=first, threads=2)
-    t = torch.tensor(np.concatenate([r["sum_w"].ravel(), r["sum_w2"].ravel(),
-                                     r["count"].ravel().astype(np.float64), [r["trans"]]]))
-    dist.all_reduce(t)
-    if rank == 0:
-        np.save(out_path, t.numpy())
+    det = {"sum_w": torch.tensor(r["sum_w"].ravel()), "sum_w2": torch.tensor(r["sum_w2"].ravel()),
+           "count": torch.tensor(r["count"].ravel().astype(np.int64)),
+           "trans": torch.tensor([float(r["trans"])], dtype=torch.float64)}
+    shard.merge_detector(det, dst=dst)
+    if dst is None or rank == dst:
+        np.savez(out_path + f".{rank}.npz", **{k: v.numpy() for k, v in det.items()})
     dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("n", [20001, 64])
-def test_two_rank_partition_reproduces_single_run(tmp_path, n):
+def test_rank_ranges_partition_the_index_range():
+    from paper_2501_06054_gb300 import shard
+    for n in (0, 1, 64, 20001):
+        for w in (1, 2, 3, 8):
+            rngs = [shard.rank_range(r, w, n) for r in range(w)]
+            assert rngs[0][0] == 0 and sum(c for _, c in rngs) == n
+            assert all(rngs[i][0] + rngs[i][1] == rngs[i + 1][0] for i in range(w - 1))
+            assert max(c for _, c in rngs) - min(c for _, c in rngs) <= 1
+    assert shard.weak_range(3, 100) == (300, 100)
+    with pytest.raises(ValueError):
+        shard.rank_range(2, 2, 10)
+
+
+@pytest.mark.parametrize("world,n,mode,dst", [(2, 20001, "strong", None), (3, 64, "strong", 0),
+                                              (2, 5003, "weak", None)])
+def test_ranks_reproduce_single_run(tmp_path, world, n, mode, dst):
     import torch.multiprocessing as mp
     import oracle
     import sas_workloads as W
     oracle.build()
-    for w in (2, 3):
-        rngs = [_rank_range(r, w, n) for r in range(w)]
-        assert rngs[0][0] == 0 and sum(c for _, c in rngs) == n
-        assert all(rngs[i][0] + rngs[i][1] == rngs[i + 1][0] for i in range(w - 1))
-    out = str(tmp_path / "red.npy")
+    out = str(tmp_path / "red")
     port = _free_port()
-    mp.start_processes(_worker, args=(2, port, n, out), nprocs=2, join=True, start_method="spawn")
-    red = np.load(out)
+    mp.start_processes(_worker, args=(world, port, n, mode, dst, out), nprocs=world, join=True,
+                       start_method="spawn")
+    total = n if mode == "strong" else n * world
     cfg = W.core_shell_config()
-    full = oracle.trace(cfg["instrument"], cfg["model"], n, seed=3, threads=2)
-    npix = full["sum_w"].size
-    assert np.array_equal(red[2 * npix:3 * npix], full["count"].ravel().astype(np.float64))
-    assert np.allclose(red[:npix], full["sum_w"].ravel(), rtol=1e-12, atol=0)
-    assert np.allclose(red[npix:2 * npix], full["sum_w2"].ravel(), rtol=1e-12, atol=0)
-    assert red[-1] == pytest.approx(full["trans"])
+    full = oracle.trace(cfg["instrument"], cfg["model"], total, seed=3, threads=2)
+    holders = range(world) if dst is None else [dst]
+    for r in holders:
+        red = np.load(out + f".{r}.npz")
+        assert np.array_equal(red["count"], full["count"].ravel().astype(np.int64))
+        assert np.allclose(red["sum_w"], full["sum_w"].ravel(), rtol=1e-12, atol=0)
+        assert np.allclose(red["sum_w2"], full["sum_w2"].ravel(), rtol=1e-12, atol=0)
+        assert red["trans"][0] == pytest.approx(full["trans"], rel=1e-12)

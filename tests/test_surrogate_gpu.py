@@ -1,10 +1,13 @@
 """Learned surrogate on the tensor cores (GPU) against the FP64 oracle.
 
-* forward (tcgen05 inference) vs the oracle network on the same weights;
+* forward (tcgen05 inference) vs the oracle network on the same weights,
+  per element within a bound derived from the arithmetic (below);
 * exact training targets vs the trace oracle's quadrature;
 * gradients (tcgen05 backward + weight-gradient GEMMs + row sums) vs the
-  oracle's backpropagation on the same BF16 weights (relative 2e-2 per
-  tensor: BF16 activations and stored pre-activations);
+  oracle's backpropagation on the same BF16 weights, element by element:
+  |g - g_oracle| <= 1e-2 |g_oracle| + 1e-3 m, m the element's L1 mass (the
+  sum of the magnitudes of the per-sample terms it adds up), so that an
+  element whose terms cancel is held to an absolute floor set by its terms;
 * training lowers the loss; the trace uses the surrogate inside its box and
   the exact quadrature outside.
 """
@@ -53,6 +56,65 @@ def _raw(box, n, seed):
     return raw
 
 
+# Forward tolerance. The kernel and the oracle multiply the same BF16
+# weights; they differ in (a) the features (FP32 vs FP64 before rounding to
+# BF16), (b) SiLU, which the kernel takes as z/2 (1 + tanh(z/2)) with the
+# special-function unit's tanh.approx.f32 (relative error below 2^-11;
+# 2^-10.5 is allowed here), (c) FP32 accumulation of the K = 256 products.
+# Each layer rounds its activations to BF16 on both sides, so a deviation
+# d << ulp of an activation either vanishes (both round alike) or becomes
+# one BF16 ulp (a rounding flip), with probability E|d| / ulp. First-order
+# propagation of these independent flips through the network (variances
+# through W o W, SiLU' on the way) gives a per-sample standard deviation
+# sigma of the output; the test requires |out - out_oracle| <= 6 sigma +
+# 2e-6 (1 + |out|) for every sample, and a median of |out - out_oracle| /
+# sigma below 1 (a numpy emulation of the kernel's roundings gives 0.4 with
+# a largest ratio of 3).
+TANH_REL = 2.0 ** -10.5
+
+
+def _bf16_ulp(h):
+    a = np.abs(h)
+    e = np.floor(np.log2(np.where(a > 0, a, 1.0)))
+    return np.where(a > 0, 2.0 ** (e - 7), 2.0 ** -133)
+
+
+def _flip_var(s, h):
+    """Variance of bf16(h + d) - bf16(h) for a deviation d of std s."""
+    u = _bf16_ulp(h)
+    return np.minimum(1.0, math.sqrt(2.0 / math.pi) * s / u) * u * u + s * s
+
+
+def _forward_sigma(box, p, raw):
+    raw = np.asarray(raw, dtype=np.float64)
+    X = M.features(box, raw)
+    W1, Ws, bs, w5, _ = M.unpack(p)
+    Wl = [M.bf16(W1)] + [M.bf16(W) for W in Ws]
+    eps = 2.0 ** -24
+    # (a) FP32 features: a few roundings of the scaled inputs; the Fourier
+    # pair k carries the FP32 phase error of k u / 2 and its recurrence
+    s0 = 4 * eps * (np.abs(X) + 1.0)
+    u = 0.5 * raw[:, 0] * raw[:, 3]
+    for k in range(box["n_fourier"]):
+        sk = (k + 1) * (0.5 * u * 4 * eps + 4 * eps)
+        s0[:, 5 + 2 * k] = sk
+        s0[:, 6 + 2 * k] = sk
+    s0[:, 63] = 0.0
+    a = M.bf16(X)
+    vD = _flip_var(s0, X)
+    for l in range(4):
+        z = a @ Wl[l].T + bs[l]
+        acc = 256 * eps * (np.abs(a) @ np.abs(Wl[l]).T)          # (c)
+        vz = vD @ (Wl[l] ** 2).T + acc * acc / 3.0
+        tau = 0.5 * np.abs(z) * TANH_REL * np.abs(np.tanh(0.5 * z))   # (b)
+        h = M.silu(z)
+        vh = M.dsilu(z) ** 2 * vz + tau * tau
+        a = M.bf16(h)
+        vD = _flip_var(np.sqrt(vh), h)
+    acc = 256 * eps * (np.abs(a) @ np.abs(w5))
+    return np.sqrt(vD @ (w5 ** 2) + acc * acc / 3.0)
+
+
 def test_surrogate_forward_matches_oracle():
     box = _small_box()
     s = sas.sas_create_surrogate(box, seed=7, stream=torch.cuda.current_stream())
@@ -74,8 +136,11 @@ def test_surrogate_forward_matches_oracle():
     got = out.cpu().numpy().astype(np.float64)
     ref = M.forward(p, M.features(box, raw.astype(np.float64)))
     err = np.abs(got - ref)
-    assert np.median(err) < 2e-3, np.median(err)
-    assert np.all(err < 3e-2 + 1e-2 * np.abs(ref)), err.max()
+    sig = _forward_sigma(box, p, raw)
+    bound = 6.0 * sig + 2e-6 * (1.0 + np.abs(ref))
+    assert np.all(err <= bound), (float(np.max(err / bound)), float(np.median(err)), float(np.median(sig)))
+    # and the deviations are of the size the flip model predicts, not larger
+    assert np.median(err / sig) < 1.0, float(np.median(err / sig))
     sas.sas_destroy_surrogate(s)
 
 
@@ -155,11 +220,34 @@ def test_gradients_match_oracle():
     segs = dict(W1=(M.OFF_W1, M.OFF_W2), W2=(M.OFF_W2, M.OFF_W3), W3=(M.OFF_W3, M.OFF_W4),
                 W4=(M.OFF_W4, M.OFF_B1), b234=(M.OFF_B1 + 256, M.OFF_W5), w5=(M.OFF_W5, M.OFF_B5),
                 b5=(M.OFF_B5, M.OFF_B5 + 1))
+    mass = _grad_mass(p, M.features(box, raw.astype(np.float64)), y.astype(np.float64))
     for name, (a, b) in segs.items():
-        d = np.linalg.norm(g[a:b] - go[a:b]) / max(np.linalg.norm(go[a:b]), 1e-30)
-        assert d < 2e-2, (name, d)
+        tol = 1e-2 * np.abs(go[a:b]) + 1e-3 * mass[a:b]
+        bad = np.abs(g[a:b] - go[a:b]) > tol
+        assert not bad.any(), (name, int(bad.sum()), float(np.max(np.abs(g[a:b] - go[a:b]) / (tol + 1e-300))))
     assert np.all(g[M.OFF_B1:M.OFF_B1 + 256] == 0.0)
     sas.sas_destroy_surrogate(s)
+
+
+def _grad_mass(p, X, y):
+    """L1 mass of every gradient element: the oracle's backpropagation with
+    every factor replaced by its magnitude (sum over samples of |term|)."""
+    out, zs, hs, Wl = M.forward(p, X, keep=True)
+    n = X.shape[0]
+    dout = np.abs(2.0 * (out - y) / n)
+    mass = np.zeros(M.NPARAM)
+    a4 = np.abs(M.bf16(hs[4]))
+    mass[M.OFF_W5:M.OFF_B5] = a4.T @ dout
+    mass[M.OFF_B5] = dout.sum()
+    dh = np.outer(dout, np.abs(M.unpack(p)[3]))
+    offs = [M.OFF_W1, M.OFF_W2, M.OFF_W3, M.OFF_W4]
+    for l in range(3, -1, -1):
+        dz = dh * np.abs(M.dsilu(zs[l]))
+        gW = dz.T @ np.abs(M.bf16(hs[l]))
+        mass[offs[l]: offs[l] + gW.size] = gW.reshape(-1)
+        mass[M.OFF_B1 + l * M.H: M.OFF_B1 + (l + 1) * M.H] = dz.sum(axis=0)
+        dh = dz @ np.abs(Wl[l])
+    return mass
 
 
 def _mse(s, raw_ptr, y_ptr, n):
