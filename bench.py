@@ -150,12 +150,158 @@ def _events_ms(fn, stream):
     return a.elapsed_time(b)
 
 
+def _train_surrogate(sas, box, stream, n_train, steps, seed=1, batch=65536, lr=2e-3):
+    """Create, generate exact targets and train one surrogate; returns it and
+    the costs (CUDA events on the stream)."""
+    sur = sas.sas_create_surrogate(box, seed=seed, stream=stream)
+    gen_ms = _events_ms(lambda: sas.sas_surrogate_generate(sur, n_train, seed), stream)
+    train_ms = _events_ms(lambda: sas.sas_surrogate_train(sur, steps, batch, lr, steps), stream)
+    mlp_flop = 2.0 * (64 * 256 + 3 * 256 * 256 + 256)
+    return sur, {"samples": n_train, "generate_s": gen_ms * 1e-3, "steps": steps, "batch": batch, "lr": lr,
+                 "train_s": train_ms * 1e-3,
+                 "train_tflops_nominal": 3 * mlp_flop * steps * batch / (train_ms * 1e-3) / 1e12}
+
+
+def _rel_stats(rel):
+    rel = np.asarray(rel, dtype=np.float64)
+    if rel.size == 0:
+        return {"bins": 0}
+    return {"bins": int(rel.size), "median": float(np.median(rel)), "p90": float(np.percentile(rel, 90)),
+            "p99": float(np.percentile(rel, 99)), "p999": float(np.percentile(rel, 99.9)),
+            "max": float(rel.max()), "frac_bins_le_1pct": float(np.mean(rel <= 0.01))}
+
+
+def _in_box(box, m):
+    """The library's coverage rule (the model lies in the training box and
+    uses its quadrature), restated for choosing the bins to compare."""
+    return (m.kind == W.CYLINDER and m.precision == W.FP32 and m.isotropic == 0 and m.sampling == W.QUADRATURE
+            and m.poly_dist == W.SCHULZ and not m.self_attenuation and m.n_poly == box["n_poly"]
+            and m.n_gamma == box["n_gamma"] and m.n_psi == box["n_psi"]
+            and box["r_min"] <= m.radius <= box["r_max"] and box["l_min"] <= m.length <= box["l_max"]
+            and box["sigma_orient_min"] <= m.sigma_orient <= box["sigma_orient_max"]
+            and box["poly_min"] <= m.poly <= box["poly_max"] and m.sld != m.sld_solvent)
+
+
+def batched_config(stream, info, scale=1000, n_train=100_000_000, steps=100_000):
+    """The whole batched workload in one graph launch: 4096 experiments (all
+    four kinds), counts of the draw / scale, per-experiment 128x128
+    detectors; a per-experiment loop of plain launches, the batched launch
+    with the exact quadrature and the batched launch with the learned
+    surrogate serving the cylinders of its box (trained here on the batched
+    box). Per-bin error of the surrogate against the exact trace on the same
+    histories, over the covered cylinders' bins >= 1e-3 of each detector's
+    largest bin; the same three rates on the cylinder experiments alone."""
+    import torch
+    import paper_2501_06054_gb300 as sas
+    from paper_2501_06054_gb300 import flops as F
+    from paper_2501_06054_gb300 import shard
+    inst = W.instrument()
+    npix = inst.nx * inst.ny
+    models, counts = W.batched_models(n_exp=4096, seed=1)
+    cnt = np.maximum(counts // scale, 1).astype(np.uint64)
+    peak = F.fp32_peak_tflops(info["sm_count"], 2070.0)
+    box = W.batched_surrogate_box()
+    sur, training = _train_surrogate(sas, box, stream, n_train, steps)
+
+    def plain_loop(sel):
+        exs = []
+        for k in sel:
+            ex = sas.Experiment(inst, models[k], stream=stream)
+            sas.sas_set_experiment_id(ex.h, int(k))
+            exs.append((k, ex))
+
+        def run():
+            for k, ex in exs:
+                sas.sas_trace(ex.h, int(cnt[k]), 1)
+        run()
+        ms = _events_ms(run, stream)
+        for _, ex in exs:
+            ex.close()
+        return ms
+
+    def batched(sel, with_sur):
+        b = sas.sas_create_batch(inst, [models[k] for k in sel], cnt[sel], stream=stream)
+        if with_sur:
+            sas.sas_batch_attach_surrogate(b, sur)
+        sas.sas_trace_batch(b, 1)
+        ms = _events_ms(lambda: sas.sas_trace_batch(b, 1), stream)
+        return b, ms
+
+    def fp_total(sel):
+        return sum(float(F.flops_per_history(models[k].kind, models[k].n_poly,
+                                             models[k].n_gamma * models[k].n_psi)) * float(cnt[k]) for k in sel)
+
+    res = {"workload": "the 4096 batched draws (numpy PCG64 seed 1): sphere, core-shell, cylinder, ellipsoid "
+                       "uniform; sizes U[10,200] A; Schulz U[0,0.3] x40; anisotropic spread U[0,30] deg about "
+                       "uniform axes on 76x76 nodes; counts of the draw (log-uniform 1e5..1e8) / %d; 128x128 "
+                       "detector per experiment; FP32" % scale,
+           "unit": UNIT, "count_scale": 1.0 / scale, "n_exp": 4096}
+    rows = {}
+    for name, sel in (("all", np.arange(4096)),
+                      ("cylinders", np.array([k for k in range(4096) if models[k].kind == W.CYLINDER]))):
+        tot = int(cnt[sel].sum())
+        ms_plain = plain_loop(sel)
+        b, ms_b = batched(sel, False)
+        dev = {k: v.clone() for k, v in _batch_views(sas, b, len(sel), npix).items()} if name == "cylinders" \
+            else None
+        sas.sas_destroy_batch(b)
+        bs, ms_bs = batched(sel, True)
+        n_e, n_h = sas.sas_batch_surrogate_share(bs)
+        fb = sas.sas_surrogate_fallbacks(batch=bs)
+        row = {"experiments": int(len(sel)), "histories": tot,
+               "plain_loop": tot / (ms_plain * 1e-3), "batched": tot / (ms_b * 1e-3),
+               "batched_surrogate": tot / (ms_bs * 1e-3),
+               "speedup_batched_vs_plain": ms_plain / ms_b,
+               "speedup_batched_surrogate_vs_plain": ms_plain / ms_bs,
+               "roofline_batched": {"bound": "alu", "achieved": fp_total(sel) / (ms_b * 1e-3) / 1e12,
+                                    "peak": peak, "unit": "TFLOP/s",
+                                    "frac": fp_total(sel) / (ms_b * 1e-3) / 1e12 / peak,
+                                    "note": "sum over work items of the nominal FLOP per history x histories, "
+                                            "over the graph launch (memsets + persistent kernel)"},
+               "surrogate_served": {"experiments": n_e, "histories_covered": n_h,
+                                    "fallback_histories": fb, "histories_served": n_h - fb,
+                                    "share_of_histories": (n_h - fb) / max(tot, 1)}}
+        if dev is not None:
+            got = _batch_views(sas, bs, len(sel), npix)
+            rels = []
+            for j, k in enumerate(sel):
+                if not _in_box(box, models[k]):
+                    continue
+                ex = dev["sum_w"][j]
+                big = ex >= 1e-3 * ex.max()
+                rels.append(((got["sum_w"][j] - ex).abs()[big] / ex[big]).cpu().numpy())
+            row["per_bin_rel_err"] = dict(_rel_stats(np.concatenate(rels) if rels else []),
+                                          experiments=len(rels),
+                                          compared_on="identical histories (same Philox streams), surrogate vs "
+                                                      "exact quadrature, bins >= 1e-3 of each detector's max")
+            del dev
+        sas.sas_destroy_batch(bs)
+        rows[name] = row
+        torch.cuda.empty_cache()
+    res.update(rows)
+    res["surrogate"] = {"box": {k: (math.degrees(v) if k.startswith("sigma_orient") else v)
+                                for k, v in box.items()}, "training": training}
+    sas.sas_destroy_surrogate(sur)
+    return res
+
+
+def _batch_views(sas, b, n_exp, npix):
+    """Zero-copy torch views [n_exp][npix] of a batch's device detectors."""
+    import torch
+    from paper_2501_06054_gb300.shard import _CudaArray
+    sw, sw2, cn, tr = sas.sas_batch_detector_device(b)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n = n_exp * npix
+    return {"sum_w": torch.as_tensor(_CudaArray(sw, n, "<f8"), device=dev).view(n_exp, npix),
+            "count": torch.as_tensor(_CudaArray(cn, n, "<i8"), device=dev).view(n_exp, npix)}
+
+
 def secondary(stream, info):
-    """Bounded secondary measurements (each on stated samples):
-    the cylinder workload with the exact quadrature and with the learned
-    surrogate (same histories, per-bin error), and batches traced by a
-    per-experiment loop of plain launches vs one persistent graph launch
-    (with and without the surrogate)."""
+    """Bounded secondary measurements (each on stated samples): the cylinder
+    workload with the exact quadrature, the radial table and the learned
+    surrogate (same histories, per-bin error); the whole batched workload
+    (plain loop vs one graph launch vs one graph launch with the surrogate);
+    the per-event estimator, self-attenuation and the further models."""
     import torch
     import paper_2501_06054_gb300 as sas
     from paper_2501_06054_gb300 import flops as F
@@ -186,12 +332,8 @@ def secondary(stream, info):
     so_ = d_ex["sum_w"]
     bt = so_ >= 1e-3 * so_.max()
     rel_tab = np.abs(d_tab["sum_w"] - so_)[bt] / so_[bt]
-    box = W.surrogate_box(n_fourier=6)
-    t0 = time.perf_counter()
-    sur = sas.sas_create_surrogate(box, seed=1, stream=stream)
-    n_train, steps, batch, lr = 50_000_000, 60_000, 65536, 2e-3
-    gen_ms = _events_ms(lambda: sas.sas_surrogate_generate(sur, n_train, 1), stream)
-    train_ms = _events_ms(lambda: sas.sas_surrogate_train(sur, steps, batch, lr, steps), stream)
+    box = W.surrogate_box()
+    sur, training = _train_surrogate(sas, box, stream, 50_000_000, 100_000)
     sas.sas_attach_surrogate(e.h, sur)
     e.trace(n_ex, 1)
     d_su = e.read()
@@ -226,86 +368,14 @@ def secondary(stream, info):
                                    "frac": mlp_flop * rate_su / 1e12 / bf16_peak,
                                    "flops_per_history": mlp_flop,
                                    "peak_note": "MEASURED_PEAKS bf16 sustained (of measured)"},
-                      "per_bin_rel_err": {"bins": int(big.sum()), "median": float(np.median(rel)),
-                                          "p90": float(np.percentile(rel, 90)),
-                                          "p99": float(np.percentile(rel, 99)),
-                                          "max": float(rel.max()),
-                                          "frac_bins_le_1pct": float(np.mean(rel <= 0.01)),
-                                          "total_weight": float(abs(ss.sum() / so.sum() - 1)),
-                                          "compared_on": f"{n_ex} identical histories, bins >= 1e-3 max"},
-                      "training": {"samples": n_train, "generate_s": gen_ms * 1e-3, "steps": steps,
-                                   "batch": batch, "lr": lr, "train_s": train_ms * 1e-3,
-                                   "train_tflops_nominal": 3 * mlp_flop * steps * batch / (train_ms * 1e-3) / 1e12},
+                      "per_bin_rel_err": dict(_rel_stats(rel),
+                                              total_weight=float(abs(ss.sum() / so.sum() - 1)),
+                                              compared_on=f"{n_ex} identical histories, bins >= 1e-3 max"),
+                      "training": training,
                       "fallbacks": sas.sas_surrogate_fallbacks(exp=e.h)}}
     e.close()
-    # --- batches: per-experiment loop vs one graph launch (+ surrogate)
-    def plain_loop(inst, models, counts):
-        exs = []
-        for k, mm in enumerate(models):
-            ex = sas.Experiment(inst, mm, stream=stream)
-            sas.sas_set_experiment_id(ex.h, k)
-            exs.append(ex)
-
-        def run():
-            for k, ex in enumerate(exs):
-                sas.sas_trace(ex.h, int(counts[k]), 1)
-        run()
-        ms = _events_ms(run, stream)
-        for ex in exs:
-            ex.close()
-        return ms
-
-    def batched(inst, models, counts, with_sur):
-        b = sas.sas_create_batch(inst, models, counts, stream=stream)
-        if with_sur:
-            sas.sas_batch_attach_surrogate(b, sur)
-        sas.sas_trace_batch(b, 1)
-        ms = _events_ms(lambda: sas.sas_trace_batch(b, 1), stream)
-        info_b = sas.sas_batch_info(b)
-        fb = sas.sas_surrogate_fallbacks(batch=b) if with_sur else 0
-        sas.sas_destroy_batch(b)
-        return ms, info_b, fb
-
-    inst = W.instrument()
-    rng = np.random.default_rng(5)
-    nb = 256
-    cyl = []
-    for k in range(nb):
-        cyl.append(W.Model(kind=W.CYLINDER, radius=float(rng.uniform(15, 25)), length=float(rng.uniform(300, 500)),
-                           sld=2e-6, volume_fraction=0.01, poly=float(rng.uniform(0.05, 0.15)), n_poly=40,
-                           sigma_orient=float(np.radians(rng.uniform(10, 20))),
-                           axis_theta=float(np.arccos(rng.uniform(-1, 1))), axis_phi=float(rng.uniform(0, 2 * np.pi)),
-                           n_gamma=76, n_psi=76))
-    cnt = np.exp(rng.uniform(np.log(1e4), np.log(1e6), nb)).astype(np.uint64)
-    tot = int(cnt.sum())
-    ms_plain = plain_loop(inst, cyl, cnt)
-    ms_b, ib, _ = batched(inst, cyl, cnt, False)
-    ms_bs, ibs, fb = batched(inst, cyl, cnt, True)
-    out["batched_cylinders_in_box"] = {
-        "workload": f"{nb} cylinders drawn in the surrogate box (R U[15,25], L U[300,500], sigma_orient "
-                    f"U[10,20] deg, Schulz U[0.05,0.15] x40, 76x76), random axes, counts log-uniform "
-                    f"[1e4,1e6] (total {tot}), 128x128 detectors",
-        "plain_loop": tot / (ms_plain * 1e-3), "batched": tot / (ms_b * 1e-3),
-        "batched_surrogate": tot / (ms_bs * 1e-3), "unit": UNIT,
-        "speedup_batched_surrogate_vs_plain": ms_plain / ms_bs, "surrogate_fallbacks": fb,
-        "work_items": ib["n_items"]}
-    models, counts = W.batched_models(n_exp=4096, seed=1)
-    sel = np.arange(0, 4096, 64)
-    ms_ = [models[i] for i in sel]
-    cn = (counts[sel] // 100).astype(np.uint64)
-    tot = int(cn.sum())
-    ms_plain = plain_loop(inst, ms_, cn)
-    ms_b, ib, _ = batched(inst, ms_, cn, False)
-    ms_bs, _, fb = batched(inst, ms_, cn, True)
-    out["batched_config_sample"] = {
-        "workload": f"every 64th of the 4096 batched draws (64 experiments, all four kinds, sizes U[10,200], "
-                    f"polydispersity U[0,0.3], anisotropic spread U[0,30] deg, 76x76), counts of the draw / 100 "
-                    f"(total {tot}), 128x128 detectors",
-        "plain_loop": tot / (ms_plain * 1e-3), "batched": tot / (ms_b * 1e-3),
-        "batched_surrogate": tot / (ms_bs * 1e-3), "unit": UNIT,
-        "speedup_batched_vs_plain": ms_plain / ms_b, "surrogate_fallbacks": fb,
-        "work_items": ib["n_items"]}
     sas.sas_destroy_surrogate(sur)
+    out["batched_config_full"] = batched_config(stream, info)
     out["per_event"] = per_event(stream)
     out["self_attenuation"] = self_attenuation(stream)
     out["n4_models"] = n4_models(stream)
@@ -480,7 +550,7 @@ def run_single_workload(args):
         e = sas.Experiment(cfg["instrument"], m, stream=stream)
         extra = {}
         if args.workload == "cylinder_surrogate":
-            sur = sas.sas_create_surrogate(W.surrogate_box(n_fourier=6), seed=1, stream=stream)
+            sur = sas.sas_create_surrogate(W.surrogate_box(), seed=1, stream=stream)
             sas.sas_surrogate_generate(sur, 50_000_000, 1)
             sas.sas_surrogate_train(sur, args.train_steps, 65536, 2e-3, args.train_steps)
             sas.sas_attach_surrogate(e.h, sur)
@@ -567,7 +637,7 @@ def main():
     ap.add_argument("--workload", default="core_shell",
                     choices=["core_shell", "cylinder", "cylinder_surrogate", "capped_cylinder", "barbell"],
                     help="core_shell: the headline step; the others time one workload alone")
-    ap.add_argument("--train-steps", type=int, default=60000)
+    ap.add_argument("--train-steps", type=int, default=100000)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -543,7 +543,14 @@ sas_status sas_attach_surrogate(sas_experiment *exp, const sas_surrogate *s);
  * second persistent tensor-core kernel in the batch's graph. */
 sas_status sas_batch_attach_surrogate(sas_batch *batch, const sas_surrogate *s);
 
-/* Histories evaluated by the exact fallback in the last surrogate traces. */
+/* Experiments of the batch that the attached surrogate covers (their model
+ * lies in its box) and their histories; the other experiments run the exact
+ * quadrature. Of the covered histories, those whose |Q| leaves the box are
+ * counted by sas_surrogate_fallbacks. NULL outputs are skipped. */
+sas_status sas_batch_surrogate_share(const sas_batch *batch, uint64_t *experiments, uint64_t *histories);
+
+/* Histories of surrogate-covered experiments that were evaluated by the
+ * exact fallback (|Q| outside the box) since the last attach. */
 sas_status sas_surrogate_fallbacks(const sas_experiment *exp, const sas_batch *batch,
                                    uint64_t *count);
 

@@ -2,11 +2,12 @@
 
 Plain numpy definitions of what the surrogate computes:
 
-* the feature map of an oriented polydisperse cylinder evaluation:
-  u = q_par L / 2, v = q_perp R, a = L / (2R), sigma_orient, sigma_poly,
-  each scaled linearly to [-1, 1] over the training box, then n_fourier
-  (sin, cos) pairs of k u / 2 (k = 1..n), the last of 64 columns is 1 (it
-  carries the layer-1 bias through W1[:, 63]);
+* the feature map of an oriented polydisperse cylinder evaluation (see
+  `features`): u = q_par L / 2, v = q_perp R, ln a with a = L / (2R),
+  sigma_orient, sigma_poly, each scaled linearly to [-1, 1] over the
+  training box, three logarithmic envelopes, n_fourier (sin, cos) pairs of
+  k u / 2 and as many of k v / 2; the last of 64 columns is 1 (it carries
+  the layer-1 bias through W1[:, 63]);
 * the network log P = b5 + w5 . h4, h_l = SiLU(W_l h_{l-1} + b_l),
   SiLU(z) = z s(z), s(z) = 1/2 + tanh(z/2)/2, with BF16-rounded hidden
   weights and BF16-rounded inputs of every hidden matrix product (the
@@ -68,25 +69,42 @@ def dsilu(z):
 
 def box_ranges(box):
     return dict(u_max=0.5 * box["q_max"] * box["l_max"], v_max=box["q_max"] * box["r_max"],
-                a_min=0.5 * box["l_min"] / box["r_max"], a_max=0.5 * box["l_max"] / box["r_min"])
+                la_min=math.log(0.5 * box["l_min"] / box["r_max"]),
+                la_max=math.log(0.5 * box["l_max"] / box["r_min"]))
+
+
+FOURIER0 = 8
 
 
 def features(box, raw):
-    """raw [n][>=6]: q_par, q_perp, R, L, sigma_orient, sigma_poly -> [n][64]."""
+    """raw [n][>=6]: q_par, q_perp, R, L, sigma_orient, sigma_poly -> [n][64].
+
+    u = q_par L / 2, v = q_perp R, a = L / (2R); columns 0..4: u, v, ln a,
+    sigma_orient, sigma_poly scaled to [-1, 1] over the box; 5..7:
+    ln(1 + u^2) / 4 - 1, ln(1 + v^2) / 4 - 1, ln(1 + (u / a)^2) / 4 - 1;
+    from 8: n_fourier (sin, cos) pairs of k u / 2, then n_fourier pairs of
+    k v / 2 (k = 1..n); 63: 1."""
     raw = np.asarray(raw, dtype=np.float64)
     rg = box_ranges(box)
     u = raw[:, 0] * 0.5 * raw[:, 3]
     v = raw[:, 1] * raw[:, 2]
     a = 0.5 * raw[:, 3] / raw[:, 2]
+    la_max = rg["la_max"] if rg["la_max"] > rg["la_min"] else rg["la_min"] + 1.0
     F = np.zeros((raw.shape[0], KIN))
     F[:, 0] = 2 * u / rg["u_max"] - 1
     F[:, 1] = 2 * v / rg["v_max"] - 1
-    F[:, 2] = 2 * (a - rg["a_min"]) / (rg["a_max"] - rg["a_min"]) - 1
+    F[:, 2] = 2 * (np.log(a) - rg["la_min"]) / (la_max - rg["la_min"]) - 1
     F[:, 3] = 2 * (raw[:, 4] - box["sigma_orient_min"]) / (box["sigma_orient_max"] - box["sigma_orient_min"]) - 1
     F[:, 4] = 2 * (raw[:, 5] - box["poly_min"]) / (box["poly_max"] - box["poly_min"]) - 1
-    for k in range(box["n_fourier"]):
-        F[:, 5 + 2 * k] = np.sin((k + 1) * 0.5 * u)
-        F[:, 6 + 2 * k] = np.cos((k + 1) * 0.5 * u)
+    F[:, 5] = np.log1p(u * u) / 4 - 1
+    F[:, 6] = np.log1p(v * v) / 4 - 1
+    F[:, 7] = np.log1p((u / a) ** 2) / 4 - 1
+    n = box["n_fourier"]
+    for t, x in enumerate((u, v)):
+        for k in range(n):
+            c = FOURIER0 + 2 * (t * n + k)
+            F[:, c] = np.sin((k + 1) * 0.5 * x)
+            F[:, c + 1] = np.cos((k + 1) * 0.5 * x)
     F[:, 63] = 1.0
     return F
 

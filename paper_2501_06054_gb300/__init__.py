@@ -130,6 +130,7 @@ _SIGS = {
     "sas_attach_surrogate": [_vp, _vp],
     "sas_batch_attach_surrogate": [_vp, _vp],
     "sas_surrogate_fallbacks": [_vp, _vp, ctypes.POINTER(_u64)],
+    "sas_batch_surrogate_share": [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64)],
     "sas_trace_batch_static": [_vp, _vp, _vp, ctypes.c_size_t, _u64, _vp, _vp, _vp, _vp, _vp],
 }
 
@@ -496,6 +497,13 @@ def sas_attach_surrogate(exp, s):
 
 def sas_batch_attach_surrogate(batch, s):
     _check(lib().sas_batch_attach_surrogate(batch, s))
+
+
+def sas_batch_surrogate_share(batch):
+    """(experiments, histories) of the batch that the attached surrogate covers."""
+    e, h = _u64(), _u64()
+    _check(lib().sas_batch_surrogate_share(batch, ctypes.byref(e), ctypes.byref(h)))
+    return int(e.value), int(h.value)
 
 
 def sas_surrogate_fallbacks(exp=None, batch=None):

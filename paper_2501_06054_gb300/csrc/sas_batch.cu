@@ -497,12 +497,26 @@ sas_status sas_batch_attach_surrogate(sas_batch* b, const sas_surrogate* s)
         if (!b->d_sexp) {
             SAS_CUDA_B(cudaMalloc(&b->d_sexp, b->n_exp * sizeof(sur::SurExp)), "alloc");
             SAS_CUDA_B(cudaMalloc(&b->d_fallbacks, sizeof(unsigned long long)), "alloc");
-            SAS_CUDA_B(cudaMemset(b->d_fallbacks, 0, sizeof(unsigned long long)), "memset");
         }
+        SAS_CUDA_B(cudaMemset(b->d_fallbacks, 0, sizeof(unsigned long long)), "memset");
         SAS_CUDA_B(cudaMemcpy(b->d_sexp, se.data(), b->n_exp * sizeof(sur::SurExp), cudaMemcpyHostToDevice),
                    "upload");
     }
     return build_items(b);
+}
+
+sas_status sas_batch_surrogate_share(const sas_batch* b, uint64_t* experiments, uint64_t* histories)
+{
+    if (!b) return set_error(SAS_ERR_ARG, "batch is NULL");
+    uint64_t ne = 0, nh = 0;
+    for (size_t e = 0; e < b->use_sur.size(); ++e)
+        if (b->use_sur[e]) {
+            ++ne;
+            nh += b->counts[e];
+        }
+    if (experiments) *experiments = ne;
+    if (histories) *histories = nh;
+    return SAS_OK;
 }
 
 sas_status sas_surrogate_fallbacks(const sas_experiment* e, const sas_batch* b, uint64_t* count)

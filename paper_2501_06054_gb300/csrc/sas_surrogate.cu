@@ -739,8 +739,9 @@ sur::Box device_box(const sas_surrogate_box& b)
     d.sp_max = (float)b.poly_max;
     d.u_max = (float)(0.5 * b.q_max * b.l_max);
     d.v_max = (float)(b.q_max * b.r_max);
-    d.a_min = (float)(0.5 * b.l_min / b.r_max);
-    d.a_max = (float)(0.5 * b.l_max / b.r_min);
+    d.la_min = (float)std::log(0.5 * b.l_min / b.r_max);
+    d.la_max = (float)std::log(0.5 * b.l_max / b.r_min);
+    if (d.la_max <= d.la_min) d.la_max = d.la_min + 1.0f;   // a single aspect ratio
     d.n_four = b.n_fourier;
     d.four_w = 0.5f;
     d.n_buckets = b.n_buckets;
@@ -845,7 +846,7 @@ sas_status sas_create_surrogate(const sas_surrogate_box* box, uint64_t seed, voi
         return set_error(SAS_ERR_ARG, "invalid surrogate box");
     if (b.n_poly < 1 || b.n_poly > sur::MAX_POLY || b.n_gamma < 1 || b.n_gamma > sur::MAX_GL || b.n_psi < 1 ||
         b.n_psi > sur::MAX_GL || b.n_buckets < 1 || b.n_buckets > sur::MAX_BUCKETS || b.n_fourier < 0 ||
-        b.n_fourier > 28)
+        b.n_fourier > 13)
         return set_error(SAS_ERR_ARG, "invalid surrogate quadrature sizes");
     if (!encode_fn()) return set_error(SAS_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
     sas_surrogate* s = new (std::nothrow) sas_surrogate();

@@ -17,9 +17,9 @@ constexpr uint32_t DATA_EXP_ID = 0x80000001u;   // Philox experiment id of the t
 // Box and feature scaling in the trace precision (FP32).
 struct Box {
     float q_max, r_min, r_max, l_min, l_max, so_min, so_max, sp_min, sp_max;
-    float u_max, v_max, a_min, a_max;   // feature ranges
-    float four_w;                        // angular step of the Fourier features of u
-    int n_four;                          // Fourier pairs of u
+    float u_max, v_max, la_min, la_max;  // feature ranges (la: ln a)
+    float four_w;                        // angular step of the Fourier features of u and v
+    int n_four;                          // Fourier pairs of u, and as many of v
     int n_buckets, n_poly, n_gamma, n_psi;
 };
 
@@ -29,37 +29,86 @@ struct Raw {
     float qpar, qperp, R, L, so, sp, bucket, pad;
 };
 
-// Feature vector (64 wide: [0, 5) scaled raw inputs in [-1, 1], then
-// n_four <= 28 (sin, cos) pairs of k * four_w * u (four_w = 1/2), column 63 = 1
-// (bias of layer 1)).
+// Feature vector (64 wide). With u = q_par L / 2, v = q_perp R, a = L / (2R):
+//   0..4   u, v, ln a, sigma_orient, sigma_poly, each scaled to [-1, 1]
+//          over the box;
+//   5..7   the envelopes ln(1 + u^2) / 4 - 1, ln(1 + v^2) / 4 - 1,
+//          ln(1 + (u / a)^2) / 4 - 1 (u / a = q_par R);
+//   8..    n_four (sin, cos) pairs of k w u, then n_four pairs of k w v
+//          (k = 1..n_four, w = four_w = 1/2);
+//   63     1 (the bias of layer 1); the columns between are 0.
+constexpr int FEAT_FOURIER0 = 8;
+
+// The eight scaled inputs and envelopes (columns 0..7).
+__device__ __forceinline__ void feature_head(const Box& b, float u, float v, float R, float L, float so, float sp,
+                                             float* h8)
+{
+    const float a = 0.5f * L / R;
+    const float ua = u / a;
+    h8[0] = 2.f * u / b.u_max - 1.f;
+    h8[1] = 2.f * v / b.v_max - 1.f;
+    h8[2] = 2.f * (__logf(a) - b.la_min) / (b.la_max - b.la_min) - 1.f;
+    h8[3] = 2.f * (so - b.so_min) / (b.so_max - b.so_min) - 1.f;
+    h8[4] = 2.f * (sp - b.sp_min) / (b.sp_max - b.sp_min) - 1.f;
+    h8[5] = 0.25f * __logf(fmaf(u, u, 1.f)) - 1.f;
+    h8[6] = 0.25f * __logf(fmaf(v, v, 1.f)) - 1.f;
+    h8[7] = 0.25f * __logf(fmaf(ua, ua, 1.f)) - 1.f;
+}
+
+// Column col (>= FEAT_FOURIER0) of the Fourier block: walks the u pairs,
+// then the v pairs, advancing the running (sin, cos) after each cosine.
+struct FourierWalk {
+    float su1, cu1, sv1, cv1, su, cu, sv, cv;
+    int end_u, end_v;
+    __device__ __forceinline__ FourierWalk(const Box& b, bool on, float u, float v)
+    {
+        su1 = 0.f, cu1 = 1.f, sv1 = 0.f, cv1 = 1.f;
+        if (on) {
+            sas_sincosf(b.four_w * u, su1, cu1);
+            sas_sincosf(b.four_w * v, sv1, cv1);
+        }
+        su = su1, cu = cu1, sv = sv1, cv = cv1;
+        const int nf = on ? b.n_four : 0;
+        end_u = FEAT_FOURIER0 + 2 * nf;
+        end_v = end_u + 2 * nf;
+    }
+    __device__ __forceinline__ float next(int col)
+    {
+        float x = 0.f;
+        if (col < end_u) {
+            const bool odd = (col - FEAT_FOURIER0) & 1;
+            x = odd ? cu : su;
+            if (odd) {
+                const float sn = fmaf(su, cu1, cu * su1);
+                const float cn = fmaf(cu, cu1, -(su * su1));
+                su = sn;
+                cu = cn;
+            }
+        } else if (col < end_v) {
+            const bool odd = (col - end_u) & 1;
+            x = odd ? cv : sv;
+            if (odd) {
+                const float sn = fmaf(sv, cv1, cv * sv1);
+                const float cn = fmaf(cv, cv1, -(sv * sv1));
+                sv = sn;
+                cv = cn;
+            }
+        }
+        return x;
+    }
+};
+
+// The feature vector in registers (the training and evaluation kernels);
+// every column index is a compile-time constant, so f64 stays in registers.
 __device__ __forceinline__ void features(const Box& b, float qpar, float qperp, float R, float L, float so,
                                          float sp, float* f64)
 {
-#pragma unroll
-    for (int i = 0; i < 64; ++i) f64[i] = 0.f;
     const float u = qpar * 0.5f * L;
     const float v = qperp * R;
-    const float a = 0.5f * L / R;
-    f64[0] = 2.f * u / b.u_max - 1.f;
-    f64[1] = 2.f * v / b.v_max - 1.f;
-    f64[2] = 2.f * (a - b.a_min) / (b.a_max - b.a_min) - 1.f;
-    f64[3] = 2.f * (so - b.so_min) / (b.so_max - b.so_min) - 1.f;
-    f64[4] = 2.f * (sp - b.sp_min) / (b.sp_max - b.sp_min) - 1.f;
-    // pairs k = 1..n_four of (sin, cos)(k w u) by angle addition from k = 1;
-    // fully unrolled so that the caller's array stays in registers
-    float s1, c1;
-    sas_sincosf(b.four_w * u, s1, c1);
-    float s = s1, c = c1;
+    feature_head(b, u, v, R, L, so, sp, f64);
+    FourierWalk fw(b, true, u, v);
 #pragma unroll
-    for (int k = 0; k < 28; ++k) {
-        if (k >= b.n_four) break;
-        f64[5 + 2 * k] = s;
-        f64[6 + 2 * k] = c;
-        const float sn = fmaf(s, c1, c * s1);
-        const float cn = fmaf(c, c1, -(s * s1));
-        s = sn;
-        c = cn;
-    }
+    for (int col = FEAT_FOURIER0; col < 63; ++col) f64[col] = fw.next(col);
     f64[63] = 1.f;
 }
 
@@ -70,42 +119,27 @@ __device__ __forceinline__ void write_features(const Box& b, bool on, float qpar
                                                float so, float sp, unsigned char* kblock, int m)
 {
     const float u = qpar * 0.5f * L;
-    const float raw5[5] = {2.f * u / b.u_max - 1.f, 2.f * (qperp * R) / b.v_max - 1.f,
-                           2.f * (0.5f * L / R - b.a_min) / (b.a_max - b.a_min) - 1.f,
-                           2.f * (so - b.so_min) / (b.so_max - b.so_min) - 1.f,
-                           2.f * (sp - b.sp_min) / (b.sp_max - b.sp_min) - 1.f};
-    float s1 = 0.f, c1 = 1.f;
-    if (on) sas_sincosf(b.four_w * u, s1, c1);
-    float s = s1, c = c1;   // (sin, cos) of the current pair k (1-based: k w u)
-    const int nf = on ? b.n_four : 0;
+    const float v = qperp * R;
+    float head[8];
+    feature_head(b, u, v, R, L, so, sp, head);
+    FourierWalk fw(b, on, u, v);
 #pragma unroll
     for (int chunk = 0; chunk < 8; ++chunk) {
-        float v[8];
+        float x8[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int col = 8 * chunk + j;
-            float x = 0.f;
-            if (col < 5) {
-                x = on ? raw5[col] : 0.f;
-            } else if (col < 61) {
-                const int k = (col - 5) >> 1;
-                x = k < nf ? (((col - 5) & 1) ? c : s) : 0.f;
-                if ((col - 5) & 1) {   // pair k written: advance to k + 1
-                    const float sn = fmaf(s, c1, c * s1);
-                    const float cn = fmaf(c, c1, -(s * s1));
-                    s = sn;
-                    c = cn;
-                }
-            } else if (col == 63) {
-                x = on ? 1.f : 0.f;
-            }
-            v[j] = x;
+            float x;
+            if (chunk == 0) x = on ? head[j] : 0.f;
+            else if (col == 63) x = on ? 1.f : 0.f;
+            else x = fw.next(col);
+            x8[j] = x;
         }
         uint4 pk;
-        pk.x = tc::pack_bf16(v[0], v[1]);
-        pk.y = tc::pack_bf16(v[2], v[3]);
-        pk.z = tc::pack_bf16(v[4], v[5]);
-        pk.w = tc::pack_bf16(v[6], v[7]);
+        pk.x = tc::pack_bf16(x8[0], x8[1]);
+        pk.y = tc::pack_bf16(x8[2], x8[3]);
+        pk.z = tc::pack_bf16(x8[4], x8[5]);
+        pk.w = tc::pack_bf16(x8[6], x8[7]);
         *reinterpret_cast<uint4*>(kblock + tc::sw128_chunk(m, chunk)) = pk;
     }
 }

@@ -255,7 +255,7 @@ def random_q(n, qmax, seed):
     return v * r[:, None]
 
 
-def surrogate_box(n_fourier=6, n_buckets=32):
+def surrogate_box(n_fourier=12, n_buckets=32):
     """Training box of the learned surrogate around the cylinder workload:
     R in [15, 25], L in [300, 500] angstrom, sigma_orient in [10, 20] deg,
     sigma_poly in [0.05, 0.15] (n_buckets values), |Q| <= 0.25 1/angstrom,
@@ -264,4 +264,20 @@ def surrogate_box(n_fourier=6, n_buckets=32):
     return dict(q_max=0.25, r_min=15.0, r_max=25.0, l_min=300.0, l_max=500.0,
                 sigma_orient_min=math.radians(10.0), sigma_orient_max=math.radians(20.0),
                 poly_min=0.05, poly_max=0.15, n_poly=40, n_gamma=76, n_psi=76,
+                n_buckets=n_buckets, n_fourier=n_fourier, reserved=0)
+
+
+def batched_surrogate_box(n_fourier=12, n_buckets=64):
+    """Training box of the learned surrogate for the cylinders of the batched
+    workload: R and L in [10, 200] angstrom, sigma_orient in [1, 30] deg,
+    sigma_poly in [0.01, 0.3] (n_buckets values), |Q| <= 0.115 1/angstrom
+    (the corner of the 128 x 128 detector seen from the edge of the sample
+    at the shortest wavelength, with the beam divergence, reaches 0.110),
+    with the batched quadrature (40 Schulz
+    nodes, 76 x 76 orientation nodes). Cylinders drawn with sigma_orient
+    below 1 deg or sigma_poly below 0.01 (about 7 % of them) run the exact
+    quadrature."""
+    return dict(q_max=0.115, r_min=10.0, r_max=200.0, l_min=10.0, l_max=200.0,
+                sigma_orient_min=math.radians(1.0), sigma_orient_max=math.radians(30.0),
+                poly_min=0.01, poly_max=0.3, n_poly=40, n_gamma=76, n_psi=76,
                 n_buckets=n_buckets, n_fourier=n_fourier, reserved=0)

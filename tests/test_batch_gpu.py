@@ -154,3 +154,44 @@ def test_launch_configs_agree(tally, agg, block):
     big = so > 1e-6 * so.max()
     assert np.all(np.abs(d["sum_w"] - so)[big] <= 1e-4 * so[big])
     ex.close()
+
+
+def test_batched_config_structure_in_one_launch():
+    """The batched workload's structure at scale: the first 1024 of the 4096
+    draws (all four kinds, sizes U[10, 200], polydispersity U[0, 0.3] with 40
+    Schulz nodes, anisotropic spreads U[0, 30] deg on the 76 x 76 grid),
+    counts of the draw / 10^4, per-experiment 128 x 128 detectors, in one
+    graph launch. Every experiment equals its own single-experiment trace
+    (Philox id e: counts bit-exact, sums to the FP32 tally precision), and
+    two experiments of each kind (those with counts nearest 1000) equal the
+    FP64 oracle."""
+    inst = W.instrument()
+    models, counts = W.batched_models(n_exp=4096, seed=1)
+    n_exp = 1024
+    models = models[:n_exp]
+    cnt = np.maximum(counts[:n_exp] // 10000, 1).astype(np.uint64)
+    st = torch.cuda.current_stream()
+    b = sas.sas_create_batch(inst, models, cnt, stream=st)
+    sas.sas_trace_batch(b, seed=3)
+    npix = inst.nx * inst.ny
+    assert sas.sas_batch_info(b)["total_histories"] == int(cnt.sum())
+    for e, m in enumerate(models):
+        d = sas.sas_read_batch_detector(b, e, npix)
+        ex = sas.Experiment(inst, m, stream=st)
+        sas.sas_set_experiment_id(ex.h, e)
+        ex.trace(int(cnt[e]), seed=3)
+        s = ex.read()
+        ex.close()
+        assert np.array_equal(d["count"], s["count"].reshape(-1)), e
+        assert np.allclose(d["sum_w"], s["sum_w"].reshape(-1), rtol=2e-5,
+                           atol=1e-7 * max(s["sum_w"].max(), 1e-300)), e
+        assert abs(d["trans"] - s["trans"]) <= 1e-9 * max(1.0, s["trans"])
+    kinds = np.array([m.kind for m in models])
+    for k in range(4):
+        idx = np.where(kinds == k)[0]
+        near = np.argsort(np.abs(cnt[idx].astype(np.int64) - 1000), kind="stable")[:2]
+        for e in idx[near]:
+            d = sas.sas_read_batch_detector(b, int(e), npix)
+            ref = oracle.trace(inst, models[e], int(cnt[e]), seed=3, exp_id=int(e))
+            _check(d, ref, int(cnt[e]))
+    sas.sas_destroy_batch(b)

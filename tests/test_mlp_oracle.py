@@ -110,9 +110,16 @@ def test_features_definition():
     raw = np.array([[0.1, 0.05, 20.0, 400.0, np.radians(15.0), 0.1]])
     F = M.features(box, raw)
     u, v, a = 0.1 * 200.0, 0.05 * 20.0, 10.0
-    assert abs(F[0, 0] - (2 * u / (0.5 * 0.25 * 500) - 1)) < 1e-15
-    assert abs(F[0, 1] - (2 * v / (0.25 * 25) - 1)) < 1e-15
-    assert abs(F[0, 2] - (2 * (a - 6.0) / (500 / 30 - 6.0) - 1)) < 1e-12
-    assert abs(F[0, 3]) < 1e-12 and abs(F[0, 4]) < 1e-12
-    assert abs(F[0, 5] - np.sin(u / 2)) < 1e-15 and abs(F[0, 8] - np.cos(u)) < 1e-15
-    assert F[0, 63] == 1.0 and np.all(F[0, 9:63] == 0)
+    a_min, a_max = 0.5 * box["l_min"] / box["r_max"], 0.5 * box["l_max"] / box["r_min"]
+    assert abs(F[0, 0] - (2 * u / (0.5 * box["q_max"] * box["l_max"]) - 1)) < 1e-15
+    assert abs(F[0, 1] - (2 * v / (box["q_max"] * box["r_max"]) - 1)) < 1e-15
+    assert abs(F[0, 2] - (2 * np.log(a / a_min) / np.log(a_max / a_min) - 1)) < 1e-12
+    assert abs(F[0, 3]) < 1e-12 and abs(F[0, 4]) < 1e-12      # the box centre
+    assert abs(F[0, 5] - (np.log(1 + u * u) / 4 - 1)) < 1e-15
+    assert abs(F[0, 6] - (np.log(1 + v * v) / 4 - 1)) < 1e-15
+    assert abs(F[0, 7] - (np.log(1 + (0.1 * 20.0) ** 2) / 4 - 1)) < 1e-15   # (u / a)^2 = (q_par R)^2
+    # u pairs k = 1, 2 at columns 8..11, v pairs at 12..15
+    assert abs(F[0, 8] - np.sin(u / 2)) < 1e-15 and abs(F[0, 9] - np.cos(u / 2)) < 1e-15
+    assert abs(F[0, 10] - np.sin(u)) < 1e-15 and abs(F[0, 11] - np.cos(u)) < 1e-15
+    assert abs(F[0, 12] - np.sin(v / 2)) < 1e-15 and abs(F[0, 15] - np.cos(v)) < 1e-15
+    assert F[0, 63] == 1.0 and np.all(F[0, 16:63] == 0)

@@ -94,11 +94,17 @@ def _forward_sigma(box, p, raw):
     # (a) FP32 features: a few roundings of the scaled inputs; the Fourier
     # pair k carries the FP32 phase error of k u / 2 and its recurrence
     s0 = 4 * eps * (np.abs(X) + 1.0)
+    s0[:, 2] = 2.0 ** -19                    # ln a by the special-function unit's log2
+    s0[:, 5:8] = 2.0 ** -20                  # the three logarithmic envelopes
     u = 0.5 * raw[:, 0] * raw[:, 3]
-    for k in range(box["n_fourier"]):
-        sk = (k + 1) * (0.5 * u * 4 * eps + 4 * eps)
-        s0[:, 5 + 2 * k] = sk
-        s0[:, 6 + 2 * k] = sk
+    v = raw[:, 1] * raw[:, 2]
+    n = box["n_fourier"]
+    for t, x in enumerate((u, v)):
+        for k in range(n):
+            sk = (k + 1) * (0.5 * x * 4 * eps + 4 * eps)
+            c = M.FOURIER0 + 2 * (t * n + k)
+            s0[:, c] = sk
+            s0[:, c + 1] = sk
     s0[:, 63] = 0.0
     a = M.bf16(X)
     vD = _flip_var(s0, X)
