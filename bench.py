@@ -138,6 +138,44 @@ def cpu_baseline(cfg, target_s=12.0, threads=0):
                       f"workload, FP64, OpenMP {cores} threads, {dt:.1f} s"}
 
 
+# Sources the core-shell trace kernel is compiled from: the counters recorded
+# under profiles/ apply only while their hash is the one recorded there.
+CORE_SHELL_SOURCES = ("sas_kernels.cuh", "sas_device.cuh", "sas_math.cuh", "sas_coeffs.h", "sas_types.h",
+                      "k_core_shell.cu")
+COUNTERS_FILE = os.path.join(ROOT, "profiles", "trace_core_shell_counters.txt")
+
+
+def kernel_source_hash(names=CORE_SHELL_SOURCES):
+    import hashlib
+    h = hashlib.sha1()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_2501_06054_gb300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_counters():
+    """The ncu counters of the core-shell trace kernel recorded in
+    profiles/ (one capture of 2e7 histories), or None once the kernel's
+    sources changed since the capture."""
+    if not os.path.exists(COUNTERS_FILE):
+        return None
+    rec = {}
+    with open(COUNTERS_FILE) as f:
+        for ln in f:
+            ln = ln.strip()
+            if not ln or ln.startswith("#") or "=" not in ln:
+                continue
+            k, v = (x.strip() for x in ln.split("=", 1))
+            rec[k] = v
+    if rec.get("source_hash") != kernel_source_hash():
+        return None
+    try:
+        return {k: (v if k in ("source_hash", "command") else float(v)) for k, v in rec.items()}
+    except ValueError:
+        return None
+
+
 def _events_ms(fn, stream):
     import torch
     a = torch.cuda.Event(enable_timing=True)
@@ -773,9 +811,10 @@ def main():
     achieved = fl * n / (kms * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_max, "unit": "TFLOP/s",
                 "frac": achieved / peak_max,
-                # ncu capture of the same kernel (2e7 histories): DRAM read + write per
-                # launch; it does not grow with the history count (tables, flush)
-                "traffic": 424704,
+                # DRAM read + write of one launch from the recorded ncu capture (2e7
+                # histories); the tables and the per-CTA flush do not grow with the
+                # history count, so a 1e9-history launch moves the same bytes
+                "traffic": None,
                 "kernel": "trace_kernel<float, CORE_SHELL, TALLY_SMEM>",
                 "flops_per_history": fl,
                 "amplitudes_per_s": 2 * m.n_poly * n / (kms * 1e-3),
@@ -784,6 +823,17 @@ def main():
                              "takes them from the SFU and is issue-bound (ncu: 88 % issue active)"}
     if clocks:
         roofline["frac_at_sampled_clock"] = achieved / F.fp32_peak_tflops(info["sm_count"], clocks["sm_mhz"])
+    rec = recorded_counters()
+    if rec is not None:
+        roofline["traffic"] = rec["dram_bytes_read"] + rec["dram_bytes_write"]
+        # FP32 operations the kernel executes (ncu SASS counts: FFMA 2, FADD 1,
+        # FMUL 1; the packed forms twice that), per history, at the bench's rate
+        ex_fl = rec["executed_fp32_flop"] / rec["histories"]
+        roofline["executed_fp32"] = {
+            "flop_per_history": ex_fl, "achieved": ex_fl * n / (kms * 1e-3) / 1e12,
+            "frac": ex_fl * n / (kms * 1e-3) / 1e12 / peak_max,
+            "thread_instructions_per_history": rec["thread_inst"] / rec["histories"],
+            "note": "ncu capture recorded in profiles/trace_core_shell_counters.txt (same kernel sources)"}
     value = n * ws / (ms * 1e-3)
     tables_bytes = (m.n_poly * 8 + 4) * 4
     d2h = npix * 8 * 3 + 8

@@ -383,7 +383,9 @@ typedef struct sas_batch_config {
     int32_t use_hist;          /* 1: models without an orientation average tally
                                   through the shared-memory histogram */
     int32_t reserved;
-    double target_item_flop;   /* work-item size (FLOP) the index ranges are cut to */
+    double target_item_flop;   /* work-item size (FLOP) the index ranges are cut to; an item
+                                  holds at least 4 x block histories, in whole multiples of
+                                  block (default block 1024, target 2e9) */
 } sas_batch_config;
 
 /* Create a batch of n_exp experiments sharing one instrument (Sec. II.A),
@@ -531,6 +533,15 @@ sas_status sas_surrogate_train(sas_surrogate *s, uint32_t n_steps, uint32_t batc
 sas_status sas_surrogate_get_params(const sas_surrogate *s, float *params, size_t n_params);
 sas_status sas_surrogate_set_params(sas_surrogate *s, const float *params, size_t n_params);
 sas_status sas_surrogate_info(const sas_surrogate *s, size_t *n_params, uint32_t *steps_done);
+
+/* Test hook of the bounded device waits (failure detection without a GPU
+ * fault): the next sas_surrogate_eval makes its first CTA wait, before any
+ * copy or tensor-core operation is issued, on a barrier that nothing
+ * completes; after wait_ns (1 .. 1e9 ns, else SAS_ERR_ARG) it gives up, every
+ * CTA frees its tensor memory and returns, and the call reports
+ * SAS_ERR_TIMEOUT with no output written. The hook then clears itself, so
+ * the following calls run normally. 0 disarms it. */
+sas_status sas_surrogate_test_stall(sas_surrogate *s, uint64_t wait_ns);
 sas_status sas_destroy_surrogate(sas_surrogate *s);
 
 /* Use the surrogate for the experiment's cylinder model when it lies in the

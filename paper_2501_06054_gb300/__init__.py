@@ -126,6 +126,7 @@ _SIGS = {
     "sas_surrogate_get_params": [_vp, _vp, ctypes.c_size_t],
     "sas_surrogate_set_params": [_vp, _vp, ctypes.c_size_t],
     "sas_surrogate_info": [_vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_uint32)],
+    "sas_surrogate_test_stall": [_vp, _u64],
     "sas_destroy_surrogate": [_vp],
     "sas_attach_surrogate": [_vp, _vp],
     "sas_batch_attach_surrogate": [_vp, _vp],
@@ -468,6 +469,10 @@ def sas_surrogate_grad(s, raw, log_p, n, n_params):
 
 def sas_surrogate_train(s, n_steps, batch, lr, total_steps):
     _check(lib().sas_surrogate_train(s, int(n_steps), int(batch), float(lr), int(total_steps)))
+
+
+def sas_surrogate_test_stall(s, wait_ns):
+    _check(lib().sas_surrogate_test_stall(s, int(wait_ns)))
 
 
 def sas_surrogate_info(s):

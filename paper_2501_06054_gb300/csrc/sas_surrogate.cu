@@ -93,6 +93,7 @@ struct FwdParams {
     __nv_bfloat16* zt[4];  // [256][batch]
     __nv_bfloat16* ht[4];
     int* err;
+    uint64_t stall_ns;     // test hook: > 0 makes CTA 0 wait that long on a barrier nothing completes
 };
 
 __device__ __forceinline__ uint64_t batch_row(const FwdParams& P, uint32_t i)
@@ -107,6 +108,16 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_fwd_kernel(const FwdParams P, 
     extern __shared__ unsigned char raw_sm[];
     Ctx c;
     ctx_init(c, raw_sm, P.err);
+    if (P.stall_ns) {
+        // Test of the bounded waits: before any copy or MMA is issued, CTA 0
+        // waits on the MMA barrier, which nothing completes, gives up after
+        // stall_ns and records the failure; every CTA then frees its tensor
+        // memory and returns without work, and the host reports
+        // SAS_ERR_TIMEOUT.
+        if (blockIdx.x == 0 && threadIdx.x == 0 && !tc::mbar_wait(c.bar_mma, 0, P.stall_ns)) atomicExch(P.err, 9);
+        ctx_finish(c);
+        return;
+    }
     stage_params(c, P.params);
     load_weights(c, &maps.w1, 1);
     __syncthreads();
@@ -239,10 +250,13 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_bwd_kernel(const BwdParams P, 
 }
 
 // Weight gradients dW_l[out][in] = sum_b dZ_l^T[out][b] H_{l-1}^T[in][b]:
-// M = 128 rows of `out` per CTA, N = 256 (64 for layer 1), K = the batch,
-// split over CTAs; 4-stage TMA pipeline; FP32 atomics into the gradient.
-constexpr int WG_STAGES = 4;
-constexpr uint32_t WG_A_BYTES = 16384, WG_B_BYTES = 32768;
+// both 128-row halves of `out` per CTA into two TMEM accumulators (columns
+// 0..255 and 256..511), so that H^T is read once per layer; N = 256 (64 for
+// layer 1), K = the batch, split over CTAs; 3-stage TMA pipeline (a stage
+// holds the two dZ^T halves and the H^T block); FP32 atomics into the
+// gradient. The kernel is bound by reading dZ^T and H^T.
+constexpr int WG_STAGES = 3;
+constexpr uint32_t WG_A_BYTES = 32768, WG_B_BYTES = 32768;   // A: two 128 x 64 halves
 constexpr size_t WG_SMEM = (size_t)WG_STAGES * (WG_A_BYTES + WG_B_BYTES) + 256 + 1024;
 
 struct WgMaps {
@@ -264,7 +278,6 @@ __global__ void __launch_bounds__(WG_THREADS, 1) wgrad_kernel(const WgParams P, 
     extern __shared__ unsigned char raw_sm[];
     unsigned char* sm = aligned_base(raw_sm);
     const int layer = blockIdx.z;          // 0..3
-    const int mh = blockIdx.y;             // row half of `out`
     const uint32_t kb0 = blockIdx.x * P.kb_per;
     const uint32_t nkb = min(P.kb_per, P.kb_total > kb0 ? P.kb_total - kb0 : 0u);
     const int N = layer == 0 ? 64 : 256;
@@ -281,30 +294,34 @@ __global__ void __launch_bounds__(WG_THREADS, 1) wgrad_kernel(const WgParams P, 
         tc::mbar_init(done, 1);
         tc::fence_mbar_init();
     }
-    if (threadIdx.x < 32) tc::tmem_alloc(taddr, 256);
+    if (threadIdx.x < 32) tc::tmem_alloc(taddr, 512);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *taddr;
     auto a_buf = [&](int s) { return sm + s * (WG_A_BYTES + WG_B_BYTES); };
     auto b_buf = [&](int s) { return sm + s * (WG_A_BYTES + WG_B_BYTES) + WG_A_BYTES; };
+    auto load = [&](int s, uint32_t kb) {
+        tc::mbar_arrive_expect_tx(full + s, WG_A_BYTES + bbytes);
+        tc::tma_load_2d(a_buf(s), &maps.dz[layer], (int)(kb * 64), 0, full + s);
+        tc::tma_load_2d(a_buf(s) + WG_A_BYTES / 2, &maps.dz[layer], (int)(kb * 64), 128, full + s);
+        tc::tma_load_2d(b_buf(s), &maps.h[layer], (int)(kb * 64), 0, full + s);
+    };
     if (threadIdx.x == 0 && nkb > 0) {
         const uint32_t idesc = tc::idesc_bf16(TILE, N);
         const int pro = (int)(nkb < (uint32_t)WG_STAGES ? nkb : (uint32_t)WG_STAGES);
-        for (int s = 0; s < pro; ++s) {
-            tc::mbar_arrive_expect_tx(full + s, WG_A_BYTES + bbytes);
-            tc::tma_load_2d(a_buf(s), &maps.dz[layer], (int)((kb0 + s) * 64), mh * 128, full + s);
-            tc::tma_load_2d(b_buf(s), &maps.h[layer], (int)((kb0 + s) * 64), 0, full + s);
-        }
+        for (int s = 0; s < pro; ++s) load(s, kb0 + s);
         bool ok = true;
         for (uint32_t it = 0; it < nkb; ++it) {
             const int s = (int)(it % WG_STAGES);
             ok = ok && tc::mbar_wait(full + s, (it / WG_STAGES) & 1u, WAIT_NS);
             tc::fence_after_sync();
             for (int k = 0; k < 4; ++k) {
-                const uint64_t ad = tc::desc_sw128(tc::smem_u32(a_buf(s)) + k * 32);
                 const uint64_t bd = tc::desc_sw128(tc::smem_u32(b_buf(s)) + k * 32);
-                tc::mma_bf16(tmem, ad, bd, idesc, (it | k) ? 1u : 0u);
+                const uint64_t a0 = tc::desc_sw128(tc::smem_u32(a_buf(s)) + k * 32);
+                const uint64_t a1 = tc::desc_sw128(tc::smem_u32(a_buf(s) + WG_A_BYTES / 2) + k * 32);
+                tc::mma_bf16(tmem, a0, bd, idesc, (it | k) ? 1u : 0u);
+                tc::mma_bf16(tmem + 256u, a1, bd, idesc, (it | k) ? 1u : 0u);
             }
             tc::mma_commit(empty + s);
             // refill the stage used one iteration ago (its MMAs are done or nearly)
@@ -314,9 +331,7 @@ __global__ void __launch_bounds__(WG_THREADS, 1) wgrad_kernel(const WgParams P, 
                 const uint32_t next = prev + WG_STAGES;
                 if (next < nkb) {
                     ok = ok && tc::mbar_wait(empty + ps, (prev / WG_STAGES) & 1u, WAIT_NS);
-                    tc::mbar_arrive_expect_tx(full + ps, WG_A_BYTES + bbytes);
-                    tc::tma_load_2d(a_buf(ps), &maps.dz[layer], (int)((kb0 + next) * 64), mh * 128, full + ps);
-                    tc::tma_load_2d(b_buf(ps), &maps.h[layer], (int)((kb0 + next) * 64), 0, full + ps);
+                    load(ps, kb0 + next);
                 }
             }
         }
@@ -330,19 +345,22 @@ __global__ void __launch_bounds__(WG_THREADS, 1) wgrad_kernel(const WgParams P, 
         const int m = row_of_thread(), h = (int)(threadIdx.x >> 7);   // 256 threads: two column halves
         const int ncols = N / 2;                 // columns per thread
         const int off = layer == 0 ? OFF_W1 : (layer == 1 ? OFF_W2 : (layer == 2 ? OFF_W3 : OFF_W4));
-        float* g = P.grad + off + (size_t)(mh * 128 + m) * N;
-        for (int ch = 0; ch < ncols / 32; ++ch) {
-            const int col0 = h * ncols + 32 * ch;
-            float v[32];
-            tc::tmem_ld32(tmem + ((uint32_t)(32 * ((threadIdx.x >> 5) & 3)) << 16) + col0, v);
+        const uint32_t lane_base = (uint32_t)(32 * ((threadIdx.x >> 5) & 3)) << 16;
+        for (int hh = 0; hh < 2; ++hh) {
+            float* g = P.grad + off + (size_t)(hh * 128 + m) * N;
+            for (int ch = 0; ch < ncols / 32; ++ch) {
+                const int col0 = h * ncols + 32 * ch;
+                float v[32];
+                tc::tmem_ld32(tmem + lane_base + (uint32_t)(hh * 256 + col0), v);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) atomicAdd(g + col0 + j, v[j]);
+                for (int j = 0; j < 32; ++j) atomicAdd(g + col0 + j, v[j]);
+            }
         }
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    if (threadIdx.x < 32) tc::tmem_dealloc(tmem, 256);
+    if (threadIdx.x < 32) tc::tmem_dealloc(tmem, 512);
 }
 
 // Row reductions of the backward pass: db2..db4 (row sums of dZ_2..4^T),
@@ -556,6 +574,7 @@ struct sas_surrogate {
     uint32_t g_total = 0;
     int* d_err = nullptr;
     cudaStream_t cap = nullptr;
+    uint64_t stall_ns = 0;   // test hook for the next sas_surrogate_eval
 };
 
 namespace {
@@ -649,13 +668,13 @@ sas_status enqueue_step(sas_surrogate* s, const sur::Raw* raw, const float* y, u
     sur::WgParams W;
     W.grad = s->d_g;
     W.kb_total = B / 64;
-    // enough K splits to cover the SMs across the 4 layers x 2 row halves
-    uint32_t splits = std::max<uint32_t>(1, (uint32_t)((s->sm_count + 7) / 8));
+    // enough K splits to cover the SMs across the 4 layers
+    uint32_t splits = std::max<uint32_t>(1, (uint32_t)((s->sm_count + 3) / 4));
     splits = std::min<uint32_t>(splits, W.kb_total);
     W.kb_per = (W.kb_total + splits - 1) / splits;
     splits = (W.kb_total + W.kb_per - 1) / W.kb_per;
     W.err = s->d_err;
-    sur::wgrad_kernel<<<dim3(splits, 2, 4), sur::WG_THREADS, sur::WG_SMEM, st>>>(W, s->wg);
+    sur::wgrad_kernel<<<dim3(splits, 1, 4), sur::WG_THREADS, sur::WG_SMEM, st>>>(W, s->wg);
     sur::rowsum_kernel<<<1025, 256, 0, st>>>(s->d_g, s->d_dzt[1], s->d_dzt[2], s->d_dzt[3], s->d_ht[3],
                                              s->d_dout, B);
     if (adam) {
@@ -1010,6 +1029,8 @@ sas_status sas_surrogate_eval(sas_surrogate* s, const void* raw, size_t n, float
     F.params = s->d_p;
     F.out = log_p;
     F.err = s->d_err;
+    F.stall_ns = s->stall_ns;
+    s->stall_ns = 0;
     const uint32_t ntiles = (uint32_t)((n + TILE - 1) / TILE);
     const int grid = (int)std::min<uint32_t>(ntiles, (uint32_t)s->sm_count);
     sur::mlp_fwd_kernel<false><<<grid, THREADS, SMEM_BYTES, s->stream>>>(F, s->maps);
@@ -1077,6 +1098,14 @@ sas_status sas_surrogate_set_params(sas_surrogate* s, const float* host, size_t 
     sas_status st = publish(s);
     if (st != SAS_OK) return st;
     SAS_CUDA_S(cudaStreamSynchronize(s->stream), "sync");
+    return SAS_OK;
+}
+
+sas_status sas_surrogate_test_stall(sas_surrogate* s, uint64_t wait_ns)
+{
+    if (!s) return set_error(SAS_ERR_ARG, "NULL argument");
+    if (wait_ns > 1000000000ull) return set_error(SAS_ERR_ARG, "wait_ns above 1 s");
+    s->stall_ns = wait_ns;
     return SAS_OK;
 }
 

@@ -114,15 +114,21 @@ __device__ __forceinline__ void features(const Box& b, float qpar, float qperp, 
 
 // The same feature vector written straight into row m of a swizzled 64-wide
 // BF16 K block, 8 columns at a time (nothing beyond one chunk is live);
-// `on` false writes a zero row.
-__device__ __forceinline__ void write_features(const Box& b, bool on, float qpar, float qperp, float R, float L,
-                                               float so, float sp, unsigned char* kblock, int m)
+// `on` false writes a zero row. NF > 0 fixes the number of Fourier pairs at
+// compile time (no per-column selects); NF = 0 reads it from the box.
+template <int NF>
+__device__ __forceinline__ void write_features_n(const Box& b, bool on, float qpar, float qperp, float R, float L,
+                                                 float so, float sp, unsigned char* kblock, int m)
 {
     const float u = qpar * 0.5f * L;
     const float v = qperp * R;
     float head[8];
     feature_head(b, u, v, R, L, so, sp, head);
     FourierWalk fw(b, on, u, v);
+    if constexpr (NF > 0) {
+        fw.end_u = FEAT_FOURIER0 + 2 * NF;
+        fw.end_v = FEAT_FOURIER0 + 4 * NF;
+    }
 #pragma unroll
     for (int chunk = 0; chunk < 8; ++chunk) {
         float x8[8];
@@ -132,7 +138,8 @@ __device__ __forceinline__ void write_features(const Box& b, bool on, float qpar
             float x;
             if (chunk == 0) x = on ? head[j] : 0.f;
             else if (col == 63) x = on ? 1.f : 0.f;
-            else x = fw.next(col);
+            else if (NF > 0 && col >= FEAT_FOURIER0 + 4 * NF) x = 0.f;
+            else x = (NF > 0 && !on) ? 0.f : fw.next(col);
             x8[j] = x;
         }
         uint4 pk;
@@ -142,6 +149,13 @@ __device__ __forceinline__ void write_features(const Box& b, bool on, float qpar
         pk.w = tc::pack_bf16(x8[6], x8[7]);
         *reinterpret_cast<uint4*>(kblock + tc::sw128_chunk(m, chunk)) = pk;
     }
+}
+
+__device__ __forceinline__ void write_features(const Box& b, bool on, float qpar, float qperp, float R, float L,
+                                               float so, float sp, unsigned char* kblock, int m)
+{
+    if (b.n_four == 12) write_features_n<12>(b, on, qpar, qperp, R, L, so, sp, kblock, m);
+    else write_features_n<0>(b, on, qpar, qperp, R, L, so, sp, kblock, m);
 }
 
 __device__ __forceinline__ bool in_box(const Box& b, float q, float R, float L, float so, float sp)

@@ -372,3 +372,31 @@ def test_surrogate_trace_tallies_the_network(n, first):
     assert d["trans"] == pytest.approx(ref["trans"], rel=1e-5)
     e.close()
     sas.sas_destroy_surrogate(s)
+
+
+def test_bounded_wait_gives_up_and_the_next_call_runs():
+    """Failure detection without a GPU fault: the test hook makes the first
+    CTA of the next evaluation wait on a barrier that nothing completes,
+    before any copy or tensor-core operation is issued. The wait gives up
+    after 20 ms, the call reports SAS_ERR_TIMEOUT, and the next evaluation
+    (which allocates the tensor memory again in every CTA) returns the same
+    values as the one before the failure."""
+    box = _small_box()
+    s = sas.sas_create_surrogate(box, seed=7, stream=torch.cuda.current_stream())
+    n = 1000
+    rd = torch.tensor(_raw(box, n, 3), device="cuda")
+    out0 = torch.empty(n, device="cuda")
+    sas.sas_surrogate_eval(s, rd, n, out0)
+    out1 = torch.full((n,), -7.0, device="cuda")
+    sas.sas_surrogate_test_stall(s, 20_000_000)
+    with pytest.raises(sas.SasError) as e:
+        sas.sas_surrogate_eval(s, rd, n, out1)
+    assert e.value.status == sas.SAS_ERR_TIMEOUT
+    assert torch.all(out1 == -7.0)                     # nothing was written
+    out2 = torch.empty(n, device="cuda")
+    sas.sas_surrogate_eval(s, rd, n, out2)             # the hook cleared itself
+    torch.cuda.synchronize()
+    assert torch.equal(out0, out2)
+    with pytest.raises(sas.SasError):
+        sas.sas_surrogate_test_stall(s, 2_000_000_000)
+    sas.sas_destroy_surrogate(s)
