@@ -1,5 +1,11 @@
 // Cylinder trace through the learned surrogate: warp-specialised, two
-// 128-history tiles ("slots") in flight per SM.
+// 128-history tiles ("slots") in flight per SM. The same pipeline runs the
+// training step's forward pass (MODE_TRAIN: rows of the data set instead of
+// traced histories; Z^T, H^T and X^T stored for the backward pass) and its
+// backward pass through the hidden layers (MODE_BWD: the first step forms
+// dZ4 from d loss / d out, a placeholder first-layer MMA keeps the static
+// schedule, then dH = dZ W^T with W4^T, W3^T, W2^T and dZ = dH SiLU'(z),
+// dZ^T stored for the weight gradients).
 //
 // 22 warps per CTA, in four roles:
 // - MMA warp (0): one lane issues the tcgen05 MMAs of slot 0 and slot 1
@@ -57,7 +63,8 @@ constexpr int RING = 3;                        // weight ring stages (32 KB each
 constexpr uint32_t S2_A = 0;                   // 2 x 64 KB activation slots (K block 0 = features)
 constexpr uint32_t S2_W = 131072;              // RING x 32 KB weight ring
 constexpr uint32_t S2_BAR = S2_W + RING * 32768u;   // 15 mbarriers, TMEM address, abort flag
-constexpr size_t S2_SMEM = (size_t)S2_BAR + 256 + 1024;
+constexpr uint32_t S2_DOUT = S2_BAR + 256;     // MODE_BWD: 2 x 128 floats of d loss / d out
+constexpr size_t S2_SMEM = (size_t)S2_DOUT + 1024 + 1024;
 constexpr int UNITS_PER_PAIR = 26;             // layer 1: 2 slots x 1 K block; layers 2..4: 2 slots x 4
 constexpr int LOADS_PER_PAIR = 16;
 
@@ -226,6 +233,60 @@ __device__ __forceinline__ float row_finish(const STParams& P, const RowRec& r, 
     return r.wt;
 }
 
+// ------------------------------------------------------ training forward
+// MODE_TRAIN: the history warps load the minibatch's data set rows instead
+// of tracing histories (R, L, sigma_orient, sigma_poly travel in the
+// record's pref, q0, q1, q2; pix_flags holds the row + 1), write their
+// features into the slot and X^T into global memory, and store the output.
+enum { MODE_TRACE = 0, MODE_TRAIN = 1, MODE_BWD = 2 };
+
+__device__ __forceinline__ RowRec train_row(const STParams& P, uint32_t pair, int s, int m)
+{
+    RowRec r;
+    const uint32_t i = pair * 256u + (uint32_t)s * 128u + (uint32_t)m;
+    const uint64_t row = ((uint64_t)(*P.step) * P.batch + i) % P.n_data;
+    const Raw x = P.raw[row];
+    r.qp = x.qpar;
+    r.qt = x.qperp;
+    r.pref = x.R;
+    r.q0 = x.L;
+    r.q1 = x.so;
+    r.q2 = x.sp;
+    r.wt = 0.f;
+    r.pix_flags = (int)(((i + 1u) << 2) | 3u);
+    return r;
+}
+
+__device__ __forceinline__ void train_features(const STParams& P, unsigned char* sm, int s, int m, const RowRec& r)
+{
+    unsigned char* kb = sm + S2_A + (uint32_t)s * 65536u;
+    write_features(P.box, true, r.qp, r.qt, r.pref, r.q0, r.q1, r.q2, kb, m);
+    // X^T for the layer-1 weight gradient: the row just written, read back
+    const size_t i = (size_t)((r.pix_flags >> 2) - 1);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const uint4 v = *reinterpret_cast<const uint4*>(kb + tc::sw128_chunk(m, c));
+        const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            P.xt[(size_t)(8 * c + 2 * j) * P.batch + i] = __ushort_as_bfloat16((unsigned short)(w4[j] & 0xFFFFu));
+            P.xt[(size_t)(8 * c + 2 * j + 1) * P.batch + i] = __ushort_as_bfloat16((unsigned short)(w4[j] >> 16));
+        }
+    }
+}
+
+// MODE_BWD: the history warps form d loss / d out = scale (pred - y) of each
+// row (kept in the record's wt) for the SiLU warps' first step.
+__device__ __forceinline__ RowRec bwd_row(const STParams& P, uint32_t pair, int s, int m)
+{
+    RowRec r = {};
+    const uint32_t i = pair * 256u + (uint32_t)s * 128u + (uint32_t)m;
+    const uint64_t row = ((uint64_t)(*P.step) * P.batch + i) % P.n_data;
+    r.wt = P.scale * (P.pred[i] - P.y[row]);
+    r.pix_flags = (int)(((i + 1u) << 2) | 3u);
+    return r;
+}
+
 // Warp-uniform flush of the transmitted weight accumulated for experiment `exp`.
 __device__ __forceinline__ void flush_trans(const STParams& P, double& t, uint32_t exp)
 {
@@ -235,6 +296,7 @@ __device__ __forceinline__ void flush_trans(const STParams& P, double& t, uint32
     t = 0.0;
 }
 
+template <int MODE>
 __global__ void __launch_bounds__(ST_THREADS, 1) sur_trace_kernel(const STParams P, const __grid_constant__ mlp::Maps maps)
 {
     extern __shared__ unsigned char raw_sm[];
@@ -285,7 +347,10 @@ __global__ void __launch_bounds__(ST_THREADS, 1) sur_trace_kernel(const STParams
                 const uint32_t k = ring_stage(pair, L.role);
                 if (pair > 0 || L.ord > 0) ok = wait_ab(empty + k, ring_parity(pair, L) ^ 1u, abort);
                 if (!ok) break;
-                const CUtensorMap* map = L.l == 0 ? &maps.w1 : &maps.w[L.l - 1];
+                // MODE_BWD walks the layers backward: W4^T, W3^T, W2^T after the
+                // placeholder first layer (its MMA result is not read)
+                const CUtensorMap* map = L.l == 0 ? &maps.w1
+                                                  : (MODE == MODE_BWD ? &maps.wt[3 - L.l] : &maps.w[L.l - 1]);
                 tc::mbar_arrive_expect_tx(full + k, 32768u);
                 tc::tma_load_2d(sm + S2_W + k * 32768u, map, L.kb * 64, 0, full + k);
                 if (k == 0) last0 = g + 1;
@@ -376,27 +441,42 @@ __global__ void __launch_bounds__(ST_THREADS, 1) sur_trace_kernel(const STParams
         double t_acc = 0.0;
         uint32_t t_exp = 0xFFFFFFFFu;
         RowRec cur0 = {}, cur1 = {}, nx0 = {}, nx1 = {};
-        PairInfo pc = my_pairs > 0 ? pair_info(P, blockIdx.x) : PairInfo{0, 0, 0};
-        PairInfo pn = my_pairs > 1 ? pair_info(P, blockIdx.x + gridDim.x) : pc;
+        const bool train = MODE != MODE_TRACE;
+        PairInfo pc = (my_pairs > 0 && !train) ? pair_info(P, blockIdx.x) : PairInfo{0, 0, 0};
+        PairInfo pn = (my_pairs > 1 && !train) ? pair_info(P, blockIdx.x + gridDim.x) : pc;
+        auto get_row = [&](int s, uint32_t k, const PairInfo& pi) {   // row of slot s of my k-th pair
+            if constexpr (MODE == MODE_BWD) return bwd_row(P, blockIdx.x + k * gridDim.x, s, m);
+            else return train ? train_row(P, blockIdx.x + k * gridDim.x, s, m) : trace_row(P, s, m, pi);
+        };
+        auto put_row = [&](int s, const RowRec& r, const PairInfo& pi) {
+            if constexpr (MODE == MODE_BWD) {
+                reinterpret_cast<float*>(sm + S2_DOUT)[s * 128 + m] = r.wt;
+                P.dout[(r.pix_flags >> 2) - 1] = r.wt;
+            } else if (train) {
+                train_features(P, sm, s, m, r);
+            } else {
+                put_features(P, sm, s, m, r, pi);
+            }
+        };
         if (my_pairs > 0) {
-            cur0 = trace_row(P, 0, m, pc);
-            put_features(P, sm, 0, m, cur0, pc);
+            cur0 = get_row(0, 0, pc);
+            put_row(0, cur0, pc);
             tc::fence_proxy_async_smem();
             __syncwarp();
             if (lane == 0) mbar_arrive(feat + 0);
-            cur1 = trace_row(P, 1, m, pc);
-            put_features(P, sm, 1, m, cur1, pc);
+            cur1 = get_row(1, 0, pc);
+            put_row(1, cur1, pc);
             tc::fence_proxy_async_smem();
             __syncwarp();
             if (lane == 0) mbar_arrive(feat + 1);
             if (my_pairs > 1) {
-                nx0 = trace_row(P, 0, m, pn);
-                nx1 = trace_row(P, 1, m, pn);
+                nx0 = get_row(0, 1, pn);
+                nx1 = get_row(1, 1, pn);
             }
         }
         for (uint32_t it = 0; it < my_pairs; ++it) {
             const bool more = it + 1 < my_pairs, more2 = it + 2 < my_pairs;
-            const PairInfo pn2 = more2 ? pair_info(P, blockIdx.x + (it + 2) * gridDim.x) : pn;
+            const PairInfo pn2 = (more2 && !train) ? pair_info(P, blockIdx.x + (it + 2) * gridDim.x) : pn;
 #pragma unroll
             for (int s = 0; s < 2; ++s) {
                 ok = wait_ab(dots + s, s ? dt1 : dt0, abort) && ok;
@@ -406,29 +486,33 @@ __global__ void __launch_bounds__(ST_THREADS, 1) sur_trace_kernel(const STParams
                 const float* d = reinterpret_cast<const float*>(sm + S2_A + (uint32_t)s * 65536u + 16384u);
                 const float out = b5 + d[m] + d[128 + m] + d[256 + m] + d[384 + m];
                 if (more) {
-                    put_features(P, sm, s, m, s ? nx1 : nx0, pn);
+                    put_row(s, s ? nx1 : nx0, pn);
                     tc::fence_proxy_async_smem();
                 }
                 __syncwarp();
                 if (more && lane == 0) mbar_arrive(feat + s);
-                if (pc.exp != t_exp) {
-                    flush_trans(P, t_acc, t_exp);
-                    t_exp = pc.exp;
+                if (MODE == MODE_TRAIN) {
+                    P.out[((s ? cur1 : cur0).pix_flags >> 2) - 1] = out;
+                } else if (MODE == MODE_TRACE) {
+                    if (pc.exp != t_exp) {
+                        flush_trans(P, t_acc, t_exp);
+                        t_exp = pc.exp;
+                    }
+                    t_acc += (double)row_finish(P, s ? cur1 : cur0, pc, out);
                 }
-                t_acc += (double)row_finish(P, s ? cur1 : cur0, pc, out);
             }
             // both slots handed over: trace pair p + 2 while the tensor cores
             // and SiLU warps run pair p + 1
             cur0 = nx0;
             cur1 = nx1;
             if (more2) {
-                nx0 = trace_row(P, 0, m, pn2);
-                nx1 = trace_row(P, 1, m, pn2);
+                nx0 = get_row(0, it + 2, pn2);
+                nx1 = get_row(1, it + 2, pn2);
             }
             pc = pn;
             pn = pn2;
         }
-        flush_trans(P, t_acc, t_exp);
+        if (!train) flush_trans(P, t_acc, t_exp);
         if (!ok) atomicExch(P.err, 9);
     } else {
         // -------------------------------------------------------- SiLU warps
@@ -441,9 +525,11 @@ __global__ void __launch_bounds__(ST_THREADS, 1) sur_trace_kernel(const STParams
         const float* hbias = P.epi;                        // b_l / 2
         const float* w5 = P.epi + 4 * mlp::H;
         uint32_t ac0 = 0u, ac1 = 0u;
+        uint32_t fe0 = 0u, fe1 = 0u;   // MODE_BWD: phases of feat[] (d loss / d out written)
         bool ok = true;
         const float2 half2 = make_float2(0.5f, 0.5f);
         for (uint32_t it = 0; it < my_pairs; ++it) {
+            const uint32_t row0 = (blockIdx.x + it * gridDim.x) * 256u + (uint32_t)m;   // MODE_TRAIN: slot 0's row
             for (int l = 0; l < 4; ++l) {
                 const float* hb = hbias + 256 * l + col_q;
 #pragma unroll
@@ -453,6 +539,71 @@ __global__ void __launch_bounds__(ST_THREADS, 1) sur_trace_kernel(const STParams
                     else ac0 ^= 1u;
                     tc::fence_after_sync();
                     unsigned char* a = sm + S2_A + (uint32_t)s * 65536u;
+                    if constexpr (MODE == MODE_BWD) {
+                        // Step l: l = 0 forms dZ4 = dout w5 SiLU'(z4) (the
+                        // placeholder MMA is not read); l = 1..3 form
+                        // dZ_{4-l} = dH SiLU'(z_{4-l}) from the accumulator of
+                        // dH = dZ_{5-l} W_{5-l}. dZ^T goes to global memory and,
+                        // but for the last step, into the slot as the next A.
+                        const int zl = 3 - l;   // stored layer of Z and dZ: 3, 2, 1, 0
+                        const size_t i = (size_t)row0 + (uint32_t)s * 128u;
+                        float dval = 0.f;
+                        if (l == 0) {
+                            ok = wait_ab(feat + s, s ? fe1 : fe0, abort) && ok;
+                            if (s) fe1 ^= 1u;
+                            else fe0 ^= 1u;
+                            dval = reinterpret_cast<const float*>(sm + S2_DOUT)[s * 128 + m];
+                        }
+#pragma unroll 1
+                        for (int half = 0; half < 2; ++half) {
+                            const int col0 = col_q + 32 * half;
+                            float v[32];
+                            if (l > 0) {
+                                uint32_t r[32];
+                                tc::tmem_ld32_nowait(tmem + lane_base + 256u * (uint32_t)s + col0, r);
+                                tc::tmem_wait_ld();
+#pragma unroll
+                                for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+                            } else {
+#pragma unroll
+                                for (int j = 0; j < 32; ++j) v[j] = dval * __ldg(w5 + col0 + j);
+                            }
+                            const __nv_bfloat16* zsrc = P.zt[zl] + (size_t)col0 * P.batch + i;
+                            __nv_bfloat16* dst = P.dzt[zl] + (size_t)col0 * P.batch + i;
+                            // every load of the chunk before any store (a store
+                            // could alias a later load, which would serialise them)
+                            __nv_bfloat16 zr[32];
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) zr[j] = zsrc[(size_t)j * P.batch];
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) {
+                                v[j] *= mlp::dsilu(__bfloat162float(zr[j]));
+                                dst[(size_t)j * P.batch] = __float2bfloat16_rn(v[j]);
+                            }
+                            if (l < 3) {
+#pragma unroll
+                                for (int j = 0; j < 4; ++j) {
+                                    uint4 pk4;
+                                    pk4.x = tc::pack_bf16(v[8 * j], v[8 * j + 1]);
+                                    pk4.y = tc::pack_bf16(v[8 * j + 2], v[8 * j + 3]);
+                                    pk4.z = tc::pack_bf16(v[8 * j + 4], v[8 * j + 5]);
+                                    pk4.w = tc::pack_bf16(v[8 * j + 6], v[8 * j + 7]);
+                                    *reinterpret_cast<uint4*>(a + (col0 >> 6) * 16384 +
+                                                              tc::sw128_chunk(m, ((col0 & 63) >> 3) + j)) = pk4;
+                                }
+                            }
+                        }
+                        tc::fence_before_sync();
+                        if (l < 3) {
+                            tc::fence_proxy_async_smem();
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(ready + s);
+                        } else {
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(dots + s);
+                        }
+                        continue;
+                    }
                     float2 dot2 = make_float2(0.f, 0.f);
 #pragma unroll 1
                     for (int half = 0; half < 2; ++half) {
@@ -476,6 +627,20 @@ __global__ void __launch_bounds__(ST_THREADS, 1) sur_trace_kernel(const STParams
                             const float2 s23 = __ffma2_rn(h23, t23, h23);
                             pk[2 * g] = tc::pack_bf16(s01.x, s01.y);
                             pk[2 * g + 1] = tc::pack_bf16(s23.x, s23.y);
+                            if constexpr (MODE == MODE_TRAIN) {
+                                // Z^T and H^T of the four columns for the backward pass
+                                const size_t base = (size_t)(col0 + 4 * g) * P.batch + row0 + (uint32_t)s * 128u;
+                                const uint32_t z01 = tc::pack_bf16(h01.x + h01.x, h01.y + h01.y);
+                                const uint32_t z23 = tc::pack_bf16(h23.x + h23.x, h23.y + h23.y);
+                                const uint32_t zz[4] = {z01 & 0xFFFFu, z01 >> 16, z23 & 0xFFFFu, z23 >> 16};
+                                const uint32_t hh[4] = {pk[2 * g] & 0xFFFFu, pk[2 * g] >> 16, pk[2 * g + 1] & 0xFFFFu,
+                                                        pk[2 * g + 1] >> 16};
+#pragma unroll
+                                for (int e = 0; e < 4; ++e) {
+                                    P.zt[l][base + (size_t)e * P.batch] = __ushort_as_bfloat16((unsigned short)zz[e]);
+                                    P.ht[l][base + (size_t)e * P.batch] = __ushort_as_bfloat16((unsigned short)hh[e]);
+                                }
+                            }
                         }
                         if (l < 3) {
 #pragma unroll

@@ -253,8 +253,8 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_bwd_kernel(const BwdParams P, 
 // both 128-row halves of `out` per CTA into two TMEM accumulators (columns
 // 0..255 and 256..511), so that H^T is read once per layer; N = 256 (64 for
 // layer 1), K = the batch, split over CTAs; 3-stage TMA pipeline (a stage
-// holds the two dZ^T halves and the H^T block); FP32 atomics into the
-// gradient. The kernel is bound by reading dZ^T and H^T.
+// holds the two dZ^T halves and the H^T block); FP32 vector atomics into the
+// gradient.
 constexpr int WG_STAGES = 3;
 constexpr uint32_t WG_A_BYTES = 32768, WG_B_BYTES = 32768;   // A: two 128 x 64 halves
 constexpr size_t WG_SMEM = (size_t)WG_STAGES * (WG_A_BYTES + WG_B_BYTES) + 256 + 1024;
@@ -352,8 +352,13 @@ __global__ void __launch_bounds__(WG_THREADS, 1) wgrad_kernel(const WgParams P, 
                 const int col0 = h * ncols + 32 * ch;
                 float v[32];
                 tc::tmem_ld32(tmem + lane_base + (uint32_t)(hh * 256 + col0), v);
+                // 16-byte vector reductions (four element-wise FP32 atomic adds
+                // each): the gradient rows and col0 are multiples of 4 floats
 #pragma unroll
-                for (int j = 0; j < 32; ++j) atomicAdd(g + col0 + j, v[j]);
+                for (int j = 0; j < 32; j += 4)
+                    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(g + col0 + j), "f"(v[j]),
+                                 "f"(v[j + 1]), "f"(v[j + 2]), "f"(v[j + 3])
+                                 : "memory");
             }
         }
     }
@@ -648,7 +653,30 @@ sas_status enqueue_step(sas_surrogate* s, const sur::Raw* raw, const float* y, u
         F.ht[l] = s->d_ht[l];
     }
     F.err = s->d_err;
-    sur::mlp_fwd_kernel<true><<<grid, THREADS, SMEM_BYTES, st>>>(F, s->maps);
+    if (B % 256u == 0u) {
+        // the warp-specialised kernel (two 128-row tiles in flight per SM,
+        // weights streamed through a ring) in its training mode
+        sur::STParams S;
+        std::memset(&S, 0, sizeof(S));
+        S.box = s->dbox;
+        S.epi = s->d_epi;
+        S.n_pairs = B / 256u;
+        S.err = s->d_err;
+        S.raw = raw;
+        S.n_data = n_data;
+        S.step = s->d_step;
+        S.batch = B;
+        S.out = s->d_pred;
+        S.xt = s->d_xt;
+        for (int l = 0; l < 4; ++l) {
+            S.zt[l] = s->d_zt[l];
+            S.ht[l] = s->d_ht[l];
+        }
+        const int g2 = (int)std::min<uint32_t>((uint32_t)s->sm_count, S.n_pairs);
+        sur::sur_trace_kernel<sur::MODE_TRAIN><<<g2, sur::ST_THREADS, sur::S2_SMEM, st>>>(S, s->maps);
+    } else {
+        sur::mlp_fwd_kernel<true><<<grid, THREADS, SMEM_BYTES, st>>>(F, s->maps);
+    }
     sur::BwdParams Bp;
     std::memset(&Bp, 0, sizeof(Bp));
     Bp.params = s->d_p;
@@ -664,7 +692,28 @@ sas_status enqueue_step(sas_surrogate* s, const sur::Raw* raw, const float* y, u
         Bp.dzt[l] = s->d_dzt[l];
     }
     Bp.err = s->d_err;
-    sur::mlp_bwd_kernel<<<grid, THREADS, SMEM_BYTES, st>>>(Bp, s->maps);
+    if (B % 256u == 0u) {
+        sur::STParams S;
+        std::memset(&S, 0, sizeof(S));
+        S.epi = s->d_epi;
+        S.n_pairs = B / 256u;
+        S.err = s->d_err;
+        S.n_data = n_data;
+        S.step = s->d_step;
+        S.batch = B;
+        S.pred = s->d_pred;
+        S.y = y;
+        S.scale = Bp.scale;
+        S.dout = s->d_dout;
+        for (int l = 0; l < 4; ++l) {
+            S.zt[l] = s->d_zt[l];
+            S.dzt[l] = s->d_dzt[l];
+        }
+        const int g2 = (int)std::min<uint32_t>((uint32_t)s->sm_count, S.n_pairs);
+        sur::sur_trace_kernel<sur::MODE_BWD><<<g2, sur::ST_THREADS, sur::S2_SMEM, st>>>(S, s->maps);
+    } else {
+        sur::mlp_bwd_kernel<<<grid, THREADS, SMEM_BYTES, st>>>(Bp, s->maps);
+    }
     sur::WgParams W;
     W.grad = s->d_g;
     W.kb_total = B / 64;
@@ -815,11 +864,11 @@ sur::SurExp surrogate_exp(const sas_model_desc& m, bool in_box)
 cudaError_t launch_sur_trace(const sas_surrogate* s, const sur::STParams& P, int sm_count, cudaStream_t st)
 {
     if (P.n_pairs == 0) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(sur::sur_trace_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(sur::sur_trace_kernel<sur::MODE_TRACE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sur::S2_SMEM);
     if (e != cudaSuccess) return e;
     const int grid = (int)std::min<uint32_t>((uint32_t)sm_count, P.n_pairs);
-    sur::sur_trace_kernel<<<grid, sur::ST_THREADS, sur::S2_SMEM, st>>>(P, s->maps);
+    sur::sur_trace_kernel<sur::MODE_TRACE><<<grid, sur::ST_THREADS, sur::S2_SMEM, st>>>(P, s->maps);
     return cudaGetLastError();
 }
 
@@ -969,6 +1018,10 @@ sas_status sas_create_surrogate(const sas_surrogate_box* box, uint64_t seed, voi
     SAS_CUDA_S(cudaFuncSetAttribute(sur::mlp_fwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES), "attr");
     SAS_CUDA_S(cudaFuncSetAttribute(sur::mlp_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES), "attr");
     SAS_CUDA_S(cudaFuncSetAttribute(sur::wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sur::WG_SMEM), "attr");
+    SAS_CUDA_S(cudaFuncSetAttribute(sur::sur_trace_kernel<sur::MODE_TRAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)sur::S2_SMEM), "attr");
+    SAS_CUDA_S(cudaFuncSetAttribute(sur::sur_trace_kernel<sur::MODE_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)sur::S2_SMEM), "attr");
     SAS_CUDA_S(cudaStreamSynchronize(s->stream), "sync");
     *out = s;
     return SAS_OK;

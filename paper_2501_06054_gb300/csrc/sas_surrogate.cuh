@@ -213,8 +213,7 @@ __device__ __forceinline__ double exact_pbar_warp(const Box& b, const Tables& t,
         const float g = 0.5f * gmax * (t.gl_g[i] + 1.0f);
         float sg, cg;
         __sincosf(g, &sg, &cg);
-        const float2 pcs = t.psi_cs[k];
-        const float cp = pcs.x, sp = pcs.y;
+        const float cp = t.psi_cs[k].x;   // Q lies in the plane of the axis and e_1: only cos(psi) enters
         const float wo = t.glw_g[i] * sg * __expf(-g * g * inv2s2) * t.glw_p[k];
         const float qc = r.qperp * sg * cp + r.qpar * cg;
         const float qab2 = fmaxf(q2 - qc * qc, 0.0f);
@@ -301,6 +300,26 @@ struct STParams {
     int npix;
     unsigned long long* fallbacks;
     int* err;
+    // training forward (MODE_TRAIN of the warp-specialised kernel): pair p
+    // holds rows [256 p, 256 p + 256) of the minibatch; row i reads data set
+    // row (step * batch + i) mod n_data and stores the BF16 features X^T
+    // [64][batch], pre-activations Z_l^T and activations H_l^T [256][batch]
+    // and the output log P [batch]
+    const Raw* raw;
+    uint64_t n_data;
+    const uint32_t* step;
+    uint32_t batch;
+    float* out;
+    __nv_bfloat16* xt;
+    __nv_bfloat16* zt[4];
+    __nv_bfloat16* ht[4];
+    // training backward (MODE_BWD): d loss / d out = scale (pred - y) into
+    // dout [batch]; dZ_l^T [256][batch] from the stored Z_l^T
+    const float* pred;
+    const float* y;
+    float scale;
+    float* dout;
+    __nv_bfloat16* dzt[4];
 };
 
 }  // namespace sur
