@@ -220,7 +220,7 @@ def _in_box(box, m):
             and box["poly_min"] <= m.poly <= box["poly_max"] and m.sld != m.sld_solvent)
 
 
-def batched_config(stream, info, scale=1000, n_train=100_000_000, steps=100_000):
+def batched_config(stream, info, scale=1000, n_train=100_000_000, steps=150_000):
     """The whole batched workload in one graph launch: 4096 experiments (all
     four kinds), counts of the draw / scale, per-experiment 128x128
     detectors; a per-experiment loop of plain launches, the batched launch
@@ -301,17 +301,26 @@ def batched_config(stream, info, scale=1000, n_train=100_000_000, steps=100_000)
                                     "share_of_histories": (n_h - fb) / max(tot, 1)}}
         if dev is not None:
             got = _batch_views(sas, bs, len(sel), npix)
-            rels = []
+            rels, keys = [], []
             for j, k in enumerate(sel):
                 if not _in_box(box, models[k]):
                     continue
                 ex = dev["sum_w"][j]
                 big = ex >= 1e-3 * ex.max()
                 rels.append(((got["sum_w"][j] - ex).abs()[big] / ex[big]).cpu().numpy())
+                keys.append((math.degrees(models[k].sigma_orient), 0.5 * models[k].length / models[k].radius))
             row["per_bin_rel_err"] = dict(_rel_stats(np.concatenate(rels) if rels else []),
                                           experiments=len(rels),
                                           compared_on="identical histories (same Philox streams), surrogate vs "
                                                       "exact quadrature, bins >= 1e-3 of each detector's max")
+            strata = {}
+            for name_, idx_, edges in (("sigma_orient_deg", 0, (1, 5, 10, 20, 30.01)),
+                                       ("aspect_L_over_2R", 1, (0, 0.3, 1, 3, 21))):
+                for lo, hi in zip(edges[:-1], edges[1:]):
+                    sel_ = [r for r, kk in zip(rels, keys) if lo <= kk[idx_] < hi]
+                    strata[f"{name_} [{lo}, {hi})"] = dict(_rel_stats(np.concatenate(sel_) if sel_ else []),
+                                                            experiments=len(sel_))
+            row["per_bin_rel_err_by_stratum"] = strata
             del dev
         sas.sas_destroy_batch(bs)
         rows[name] = row
