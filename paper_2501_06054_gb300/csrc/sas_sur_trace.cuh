@@ -275,6 +275,24 @@ __device__ __forceinline__ void train_features(const STParams& P, unsigned char*
     }
 }
 
+// Four columns c .. c + 3 of one row into a transposed BF16 array [col][ld]
+// (bf16x2 words v01 = columns c, c + 1 and v23 = c + 2, c + 3 of this row).
+// Lanes 2k and 2k + 1 hold adjacent rows: they swap half their words, so
+// that the even lane stores columns c, c + 1 and the odd lane c + 2, c + 3,
+// each as 32-bit words holding both rows (half the store instructions of
+// 2-byte stores). Called by all 32 lanes of the warp.
+__device__ __forceinline__ void store_pair_t(__nv_bfloat16* dst, uint32_t ld, int c, uint32_t row, uint32_t v01,
+                                             uint32_t v23, int lane)
+{
+    const bool odd = lane & 1;
+    const uint32_t r = __shfl_xor_sync(0xffffffffu, odd ? v01 : v23, 1);
+    const uint32_t lo = odd ? r : v01, hi = odd ? v23 : r;   // words of the even row, then the odd row
+    const uint32_t w0 = __byte_perm(lo, hi, 0x5410), w1 = __byte_perm(lo, hi, 0x7632);
+    uint32_t* p = reinterpret_cast<uint32_t*>(dst + (size_t)(c + (odd ? 2 : 0)) * ld + (row & ~1u));
+    p[0] = w0;
+    p[ld >> 1] = w1;
+}
+
 // MODE_BWD: the history warps form d loss / d out = scale (pred - y) of each
 // row (kept in the record's wt) for the SiLU warps' first step.
 __device__ __forceinline__ RowRec bwd_row(const STParams& P, uint32_t pair, int s, int m)
@@ -568,29 +586,28 @@ __global__ void __launch_bounds__(ST_THREADS, 1) sur_trace_kernel(const STParams
 #pragma unroll
                                 for (int j = 0; j < 32; ++j) v[j] = dval * __ldg(w5 + col0 + j);
                             }
+                            // every load of the chunk's Z before any store (a store
+                            // could alias a later load and serialise them)
+                            __nv_bfloat16 zpre[32];
                             const __nv_bfloat16* zsrc = P.zt[zl] + (size_t)col0 * P.batch + i;
-                            __nv_bfloat16* dst = P.dzt[zl] + (size_t)col0 * P.batch + i;
-                            // every load of the chunk before any store (a store
-                            // could alias a later load, which would serialise them)
-                            __nv_bfloat16 zr[32];
 #pragma unroll
-                            for (int j = 0; j < 32; ++j) zr[j] = zsrc[(size_t)j * P.batch];
+                            for (int j = 0; j < 32; ++j) zpre[j] = zsrc[(size_t)j * P.batch];
+                            uint32_t w[16];   // bf16x2 of columns (2t, 2t + 1) of this row
 #pragma unroll
-                            for (int j = 0; j < 32; ++j) {
-                                v[j] *= mlp::dsilu(__bfloat162float(zr[j]));
-                                dst[(size_t)j * P.batch] = __float2bfloat16_rn(v[j]);
+                            for (int t = 0; t < 16; ++t) {
+                                const float a0 = v[2 * t] * mlp::dsilu(__bfloat162float(zpre[2 * t]));
+                                const float a1 = v[2 * t + 1] * mlp::dsilu(__bfloat162float(zpre[2 * t + 1]));
+                                w[t] = tc::pack_bf16(a0, a1);
                             }
+#pragma unroll
+                            for (int g = 0; g < 8; ++g)
+                                store_pair_t(P.dzt[zl], P.batch, col0 + 4 * g, (uint32_t)i, w[2 * g], w[2 * g + 1], lane);
                             if (l < 3) {
 #pragma unroll
-                                for (int j = 0; j < 4; ++j) {
-                                    uint4 pk4;
-                                    pk4.x = tc::pack_bf16(v[8 * j], v[8 * j + 1]);
-                                    pk4.y = tc::pack_bf16(v[8 * j + 2], v[8 * j + 3]);
-                                    pk4.z = tc::pack_bf16(v[8 * j + 4], v[8 * j + 5]);
-                                    pk4.w = tc::pack_bf16(v[8 * j + 6], v[8 * j + 7]);
+                                for (int j = 0; j < 4; ++j)
                                     *reinterpret_cast<uint4*>(a + (col0 >> 6) * 16384 +
-                                                              tc::sw128_chunk(m, ((col0 & 63) >> 3) + j)) = pk4;
-                                }
+                                                              tc::sw128_chunk(m, ((col0 & 63) >> 3) + j)) =
+                                        make_uint4(w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]);
                             }
                         }
                         tc::fence_before_sync();
@@ -629,17 +646,11 @@ __global__ void __launch_bounds__(ST_THREADS, 1) sur_trace_kernel(const STParams
                             pk[2 * g + 1] = tc::pack_bf16(s23.x, s23.y);
                             if constexpr (MODE == MODE_TRAIN) {
                                 // Z^T and H^T of the four columns for the backward pass
-                                const size_t base = (size_t)(col0 + 4 * g) * P.batch + row0 + (uint32_t)s * 128u;
                                 const uint32_t z01 = tc::pack_bf16(h01.x + h01.x, h01.y + h01.y);
                                 const uint32_t z23 = tc::pack_bf16(h23.x + h23.x, h23.y + h23.y);
-                                const uint32_t zz[4] = {z01 & 0xFFFFu, z01 >> 16, z23 & 0xFFFFu, z23 >> 16};
-                                const uint32_t hh[4] = {pk[2 * g] & 0xFFFFu, pk[2 * g] >> 16, pk[2 * g + 1] & 0xFFFFu,
-                                                        pk[2 * g + 1] >> 16};
-#pragma unroll
-                                for (int e = 0; e < 4; ++e) {
-                                    P.zt[l][base + (size_t)e * P.batch] = __ushort_as_bfloat16((unsigned short)zz[e]);
-                                    P.ht[l][base + (size_t)e * P.batch] = __ushort_as_bfloat16((unsigned short)hh[e]);
-                                }
+                                store_pair_t(P.zt[l], P.batch, col0 + 4 * g, row0 + (uint32_t)s * 128u, z01, z23, lane);
+                                store_pair_t(P.ht[l], P.batch, col0 + 4 * g, row0 + (uint32_t)s * 128u, pk[2 * g],
+                                             pk[2 * g + 1], lane);
                             }
                         }
                         if (l < 3) {

@@ -400,3 +400,65 @@ def test_bounded_wait_gives_up_and_the_next_call_runs():
     with pytest.raises(sas.SasError):
         sas.sas_surrogate_test_stall(s, 2_000_000_000)
     sas.sas_destroy_surrogate(s)
+
+
+def test_batch_surrogate_share_counts_covered_experiments():
+    """sas_batch_surrogate_share reports the experiments (and their
+    histories) whose model lies in the attached surrogate's box; the others
+    run the exact quadrature and equal the oracle."""
+    box = _small_box()
+    s = sas.sas_create_surrogate(box, seed=3, stream=torch.cuda.current_stream())
+    inst = W.instrument(nx=32, ny=32)
+    cyl = dict(kind=W.CYLINDER, sld=2e-6, volume_fraction=0.01, n_poly=12, n_gamma=16, n_psi=16)
+    models = [W.Model(radius=20.0, length=400.0, poly=0.1, sigma_orient=math.radians(15), **cyl),
+              W.Model(radius=60.0, length=400.0, poly=0.1, sigma_orient=math.radians(15), **cyl),   # R out of box
+              W.Model(kind=W.SPHERE, radius=30.0, poly=0.1, n_poly=8),
+              W.Model(radius=18.0, length=320.0, poly=0.12, sigma_orient=math.radians(11), **cyl)]
+    counts = np.array([3000, 2000, 5000, 1000], np.uint64)
+    b = sas.sas_create_batch(inst, models, counts, stream=torch.cuda.current_stream())
+    assert sas.sas_batch_surrogate_share(b) == (0, 0)          # nothing attached
+    sas.sas_batch_attach_surrogate(b, s)
+    assert sas.sas_batch_surrogate_share(b) == (2, 4000)
+    sas.sas_trace_batch(b, seed=4)
+    npix = inst.nx * inst.ny
+    for e in (1, 2):                                               # exact path: the oracle's trace
+        d = sas.sas_read_batch_detector(b, e, npix)
+        ref = oracle.trace(inst, models[e], int(counts[e]), seed=4, exp_id=e)
+        assert np.array_equal(d["count"], ref["count"].reshape(-1).astype(np.uint64))
+        so = ref["sum_w"].reshape(-1)
+        big = so > 1e-6 * so.max()
+        assert np.all(np.abs(d["sum_w"] - so)[big] <= 1e-4 * so[big])
+    sas.sas_batch_attach_surrogate(b, None)
+    assert sas.sas_batch_surrogate_share(b) == (0, 0)
+    sas.sas_destroy_batch(b)
+    sas.sas_destroy_surrogate(s)
+
+
+def test_exact_targets_batched_box():
+    """The training targets over the batched box (R and L up to 200 A, |Q|
+    up to 0.115, sigma_orient down to 1 deg, sigma_poly down to 0.01), where
+    q_perp r reaches the large-argument forms of 2 J1(x)/x, against the
+    oracle's quadrature; the corners of the box included."""
+    box = W.batched_surrogate_box()
+    s = sas.sas_create_surrogate(box, seed=1, stream=torch.cuda.current_stream())
+    raw = _raw(box, 6, 13)
+    corners = np.array([[0.113, 0.02, 200.0, 200.0, box["sigma_orient_min"], box["poly_min"]],
+                        [0.02, 0.113, 200.0, 10.0, box["sigma_orient_max"], box["poly_max"]],
+                        [0.08, 0.08, 10.0, 200.0, box["sigma_orient_min"], box["poly_max"]]], np.float32)
+    nb = box["n_buckets"]
+    for c in corners:
+        bk = int(round((c[5] - box["poly_min"]) / (box["poly_max"] - box["poly_min"]) * (nb - 1)))
+        row = np.zeros(8, np.float32)
+        row[:6] = c
+        row[5] = np.float32(box["poly_min"] + (box["poly_max"] - box["poly_min"]) * bk / (nb - 1))
+        row[6] = bk
+        raw = np.vstack([raw, row])
+    n = len(raw)
+    rd = torch.tensor(raw, device="cuda")
+    out = torch.empty(n, device="cuda")
+    sas.sas_surrogate_exact(s, rd, n, out)
+    torch.cuda.synchronize()
+    got = np.exp(out.cpu().numpy().astype(np.float64))
+    ref = np.maximum(M.exact_pbar(box, raw), M.TARGET_FLOOR)
+    assert np.all(np.abs(got - ref) <= 1e-5 * ref + 1e-7), np.max(np.abs(got - ref) / ref)
+    sas.sas_destroy_surrogate(s)
