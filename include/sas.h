@@ -69,7 +69,9 @@ enum { SAS_SPHERE = 0, SAS_CORE_SHELL = 1, SAS_CYLINDER = 2, SAS_ELLIPSOID = 3,
        SAS_SHAPE_INDEPENDENT = 14 };
 /* sas_model_desc.function of SAS_SHAPE_INDEPENDENT */
 enum { SAS_FN_GUINIER = 0, SAS_FN_GAUSS_COIL = 1, SAS_FN_LORENTZ = 2, SAS_FN_DAB = 3, SAS_FN_POWER_LAW = 4,
-       SAS_FN_GAUSS_PEAK = 5, SAS_FN_TEUBNER_STREY = 6 };
+       SAS_FN_GAUSS_PEAK = 5, SAS_FN_TEUBNER_STREY = 6, SAS_FN_PEAK_LORENTZ = 7, SAS_FN_TWO_POWER_LAW = 8,
+       SAS_FN_GUINIER_POROD = 9, SAS_FN_GAUSS_LORENTZ_GEL = 10, SAS_FN_POLY_GAUSS_COIL = 11,
+       SAS_FN_STAR_POLYMER = 12 };
 /* largest Gauss-Legendre rule over an end cap */
 #define SAS_MAX_CAP_NODES 64
 enum { SAS_SQ_NONE = 0, SAS_SQ_HARD_SPHERE_PY = 1 };
@@ -233,7 +235,22 @@ typedef struct sas_model_desc {
      *   SAS_FN_POWER_LAW      Q^-m                                 f_p0 = m
      *   SAS_FN_GAUSS_PEAK     exp(-(Q - Q0)^2 / (2 sigma^2))       f_p0 = Q0, f_p1 = sigma > 0
      *   SAS_FN_TEUBNER_STREY  1 / (a2 + c1 Q^2 + c2 Q^4)           f_p0 = a2 > 0, f_p1 = c1,
-     *                         f_p2 = c2 >= 0, positive for every Q (c1 >= 0 or c1^2 < 4 a2 c2) */
+     *                         f_p2 = c2 >= 0, positive for every Q (c1 >= 0 or c1^2 < 4 a2 c2)
+     *   SAS_FN_PEAK_LORENTZ   1 / (1 + ((Q - Q0) / B)^2)           f_p0 = Q0, f_p1 = B > 0
+     *   SAS_FN_TWO_POWER_LAW  Q^-m1 for Q <= Qc, Qc^(m2 - m1) Q^-m2 above
+     *                                                              f_p0 = Qc > 0, f_p1 = m1, f_p2 = m2
+     *   SAS_FN_GUINIER_POROD  Q^-s exp(-Q^2 Rg^2 / (3 - s)) for Q <= Q1, D Q^-m above, with
+     *                         Q1 = sqrt((m - s)(3 - s) / 2) / Rg and D joining value and slope
+     *                                                              f_p0 = Rg > 0, f_p1 = s in [0, 3),
+     *                                                              f_p2 = m > s
+     *   SAS_FN_GAUSS_LORENTZ_GEL  exp(-Q^2 Xi^2 / 2) + r / (1 + (Q xi)^2)
+     *                                                              f_p0 = Xi > 0, f_p1 = xi > 0, f_p2 = r >= 0
+     *   SAS_FN_POLY_GAUSS_COIL  Schulz-Zimm polydisperse coil: 2 ((1 + U x)^(-1/U) + x - 1) /
+     *                         ((1 + U) x^2), x = (Q Rg)^2 / (1 + 2U), Rg the z-average
+     *                                                              f_p0 = Rg > 0, f_p1 = U = Mw/Mn - 1 >= 0
+     *   SAS_FN_STAR_POLYMER   star of f Gaussian arms: (D(v) + (f - 1) g(v)^2) / f, D Debye's
+     *                         function, g(v) = (1 - exp(-v)) / v, v = (Q Rg)^2 f / (3f - 2)
+     *                                                              f_p0 = Rg (of the star) > 0, f_p1 = f >= 1 */
     int64_t function;
     double f_scale;          /* >= 0 */
     double f_p0, f_p1, f_p2;

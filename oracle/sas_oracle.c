@@ -251,7 +251,49 @@ static double oracle_shape_independent(const oracle_model *m, double q)
     case 3: { double d = 1.0 + q2 * m->f_p0 * m->f_p0; f = 1.0 / (d * d); break; }
     case 4: f = pow(q, -m->f_p0); break;
     case 5: { double d = (q - m->f_p0) / m->f_p1; f = exp(-0.5 * d * d); break; }
-    default: f = 1.0 / (m->f_p0 + q2 * (m->f_p1 + q2 * m->f_p2)); break;
+    case 6: f = 1.0 / (m->f_p0 + q2 * (m->f_p1 + q2 * m->f_p2)); break;
+    case 7: { double d = (q - m->f_p0) / m->f_p1; f = 1.0 / (1.0 + d * d); break; }   /* peak Lorentz */
+    case 8:   /* two power laws meeting at q_c = f_p0: q^-m1 below, q_c^(m2 - m1) q^-m2 above */
+        f = q <= m->f_p0 ? pow(q, -m->f_p1) : pow(m->f_p0, m->f_p2 - m->f_p1) * pow(q, -m->f_p2);
+        break;
+    case 9: {   /* Guinier-Porod (Hammouda): Rg = f_p0, dimension variable s = f_p1, Porod exponent m = f_p2 */
+        double rg = m->f_p0, sd = m->f_p1, mp = m->f_p2;
+        double q1 = sqrt((mp - sd) * (3.0 - sd) / 2.0) / rg;
+        if (q <= q1) f = pow(q, -sd) * exp(-q2 * rg * rg / (3.0 - sd));
+        else f = pow(q1, mp - sd) * exp(-(mp - sd) / 2.0) * pow(q, -mp);
+        break;
+    }
+    case 10: {  /* Gauss-Lorentz gel: exp(-q^2 Xi^2 / 2) + r / (1 + q^2 xi^2) */
+        f = exp(-0.5 * q2 * m->f_p0 * m->f_p0) + m->f_p2 / (1.0 + q2 * m->f_p1 * m->f_p1);
+        break;
+    }
+    case 11: {  /* polydisperse Gaussian coil (Schulz-Zimm): Rg = f_p0, U = Mw/Mn - 1 = f_p1 */
+        double U = m->f_p1, x = q2 * m->f_p0 * m->f_p0 / (1.0 + 2.0 * U);
+        if (x < 1e-3) {
+            /* 2 / (1 + U) sum_{k>=2} (-x)^(k-2) prod_{j=1}^{k-1} (1 + jU) / k! */
+            double c = (1.0 + U) / 2.0, sum = c;
+            c *= -x * (1.0 + 2.0 * U) / 3.0; sum += c;
+            c *= -x * (1.0 + 3.0 * U) / 4.0; sum += c;
+            f = 2.0 * sum / (1.0 + U);
+        } else {
+            double t = U > 0.0 ? log1p(U * x) / U : x;
+            f = 2.0 * (exp(-t) + x - 1.0) / ((1.0 + U) * x * x);
+        }
+        break;
+    }
+    default: {  /* star polymer (Benoit): Rg = f_p0 of the star, f_p1 arms */
+        double fa = m->f_p1, v = q2 * m->f_p0 * m->f_p0 * fa / (3.0 * fa - 2.0);
+        double deb, g;
+        if (v < 1e-3) {
+            deb = 1.0 - v / 3.0 + v * v / 12.0;
+            g = 1.0 - v / 2.0 + v * v / 6.0;
+        } else {
+            deb = 2.0 * (expm1(-v) + v) / (v * v);
+            g = -expm1(-v) / v;
+        }
+        f = (deb + (fa - 1.0) * g * g) / fa;
+        break;
+    }
     }
     return m->f_scale * f;
 }

@@ -834,6 +834,30 @@ ModelConst<T> model_const(const sas_model_desc& m, const ModelTables& t)
         case SAS_FN_DAB: c.f_a = (T)(p0 * p0); break;
         case SAS_FN_POWER_LAW: c.f_a = (T)p0; break;
         case SAS_FN_GAUSS_PEAK: c.f_a = (T)p0; c.f_b = (T)(0.5 / (p1 * p1)); break;
+        case SAS_FN_PEAK_LORENTZ: c.f_a = (T)p0; c.f_b = (T)(1.0 / p1); break;
+        case SAS_FN_TWO_POWER_LAW:
+            c.f_a = (T)p0;
+            c.f_b = (T)p1;
+            c.f_c = (T)m.f_p2;
+            c.f_d = (T)std::pow(p0, m.f_p2 - p1);
+            break;
+        case SAS_FN_GUINIER_POROD: {
+            const double sd = p1, mp = m.f_p2;
+            const double q1 = std::sqrt((mp - sd) * (3.0 - sd) / 2.0) / p0;
+            c.f_a = (T)(p0 * p0 / (3.0 - sd));
+            c.f_b = (T)sd;
+            c.f_c = (T)mp;
+            c.f_d = (T)q1;
+            c.f_e = (T)(std::pow(q1, mp - sd) * std::exp(-(mp - sd) / 2.0));
+            break;
+        }
+        case SAS_FN_GAUSS_LORENTZ_GEL:
+            c.f_a = (T)(0.5 * p0 * p0);
+            c.f_b = (T)(p1 * p1);
+            c.f_c = (T)m.f_p2;
+            break;
+        case SAS_FN_POLY_GAUSS_COIL: c.f_a = (T)(p0 * p0 / (1.0 + 2.0 * p1)); c.f_b = (T)p1; break;
+        case SAS_FN_STAR_POLYMER: c.f_a = (T)(p0 * p0 * p1 / (3.0 * p1 - 2.0)); c.f_b = (T)p1; break;
         default: c.f_a = (T)m.f_p0; c.f_b = (T)m.f_p1; c.f_c = (T)m.f_p2; break;
         }
     }
@@ -913,7 +937,7 @@ sas_status validate_model(const sas_model_desc* m)
     if (!m) return fail(SAS_ERR_ARG, "model is NULL");
     if (m->kind < 0 || m->kind > 14) return fail(SAS_ERR_ARG, "unknown model kind");
     if (m->kind == SAS_SHAPE_INDEPENDENT) {
-        if (m->function < SAS_FN_GUINIER || m->function > SAS_FN_TEUBNER_STREY)
+        if (m->function < SAS_FN_GUINIER || m->function > SAS_FN_STAR_POLYMER)
             return fail(SAS_ERR_ARG, "unknown shape-independent function");
         if (!finite_all({m->f_scale, m->f_p0, m->f_p1, m->f_p2}) || m->f_scale < 0.0)
             return fail(SAS_ERR_ARG, "f_scale must be finite and >= 0, f_p0..f_p2 finite");
@@ -923,6 +947,18 @@ sas_status validate_model(const sas_model_desc* m)
         if (fn == SAS_FN_TEUBNER_STREY &&
             !(m->f_p0 > 0.0 && m->f_p2 >= 0.0 && (m->f_p1 >= 0.0 || m->f_p1 * m->f_p1 < 4.0 * m->f_p0 * m->f_p2)))
             return fail(SAS_ERR_ARG, "Teubner-Strey needs a2 > 0, c2 >= 0 and a2 + c1 Q^2 + c2 Q^4 > 0");
+        if (fn == SAS_FN_PEAK_LORENTZ && !(m->f_p1 > 0.0))
+            return fail(SAS_ERR_ARG, "peak Lorentz needs a width B > 0");
+        if (fn == SAS_FN_TWO_POWER_LAW && !(m->f_p0 > 0.0))
+            return fail(SAS_ERR_ARG, "two power laws need a crossover Qc > 0");
+        if (fn == SAS_FN_GUINIER_POROD && !(m->f_p0 > 0.0 && m->f_p1 >= 0.0 && m->f_p1 < 3.0 && m->f_p2 > m->f_p1))
+            return fail(SAS_ERR_ARG, "Guinier-Porod needs Rg > 0, 0 <= s < 3 and m > s");
+        if (fn == SAS_FN_GAUSS_LORENTZ_GEL && !(m->f_p0 > 0.0 && m->f_p1 > 0.0 && m->f_p2 >= 0.0))
+            return fail(SAS_ERR_ARG, "Gauss-Lorentz gel needs Xi > 0, xi > 0 and r >= 0");
+        if (fn == SAS_FN_POLY_GAUSS_COIL && !(m->f_p0 > 0.0 && m->f_p1 >= 0.0))
+            return fail(SAS_ERR_ARG, "polydisperse coil needs Rg > 0 and U = Mw/Mn - 1 >= 0");
+        if (fn == SAS_FN_STAR_POLYMER && !(m->f_p0 > 0.0 && m->f_p1 >= 1.0))
+            return fail(SAS_ERR_ARG, "star polymer needs Rg > 0 and at least one arm");
         if (m->sq_kind != SAS_SQ_NONE || m->sampling != SAS_QUADRATURE || m->self_attenuation != 0)
             return fail(SAS_ERR_ARG, "shape-independent laws take no S(Q), per-event sampling or self-attenuation");
     }

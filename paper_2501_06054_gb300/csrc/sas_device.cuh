@@ -716,29 +716,50 @@ __device__ __forceinline__ T avg_ellipsoid(const T qv[3], const T* __restrict__ 
 // f_b, f_c): CUDA's accurate exp, expm1 and pow, one call per history. The
 // Gaussian coil takes its series sum_k 2 (-u)^k / (k + 2)! below u = 1
 // (FP32; 0.1 in FP64), where 2 (exp(-u) - 1 + u) / u^2 cancels.
+// Debye's function of a Gaussian coil, D(u) = 2 (exp(-u) - 1 + u) / u^2:
+// its series below u = 1 (FP32; 0.1 in FP64), where the closed form cancels.
+template <typename T>
+__device__ __forceinline__ T debye_fn(T u)
+{
+    constexpr bool fp32 = sizeof(T) == sizeof(float);
+    if (u < (fp32 ? (T)1 : (T)0.1)) {
+        constexpr int nt = fp32 ? 10 : 12;
+        T sum = 0, c = (T)2;   // c = 2 / (k + 2)!, from k = 0
+        T term[nt];
+#pragma unroll
+        for (int k = 0; k < nt; ++k) {
+            c = k == 0 ? (T)1 : c / (T)(k + 2);
+            term[k] = c;
+        }
+#pragma unroll
+        for (int k = nt - 1; k >= 0; --k) sum = fma(sum, -u, term[k]);
+        return sum;
+    }
+    return (T)2 * (expm1(-u) + u) / (u * u);
+}
+
+// y - log(1 + y) for y >= 0 without cancellation: its series below 0.3
+// (FP32; 1e-3 in FP64), the direct difference above.
+template <typename T>
+__device__ __forceinline__ T y_minus_log1p(T y)
+{
+    constexpr bool fp32 = sizeof(T) == sizeof(float);
+    if (y < (fp32 ? (T)0.3 : (T)1e-3)) {
+        constexpr int nt = fp32 ? 12 : 4;   // y^2 (1/2 - y/3 + y^2/4 - ...)
+        T sum = 0;
+#pragma unroll
+        for (int k = nt - 1; k >= 0; --k) sum = fma(sum, -y, (T)1 / (T)(k + 2));
+        return y * y * sum;
+    }
+    return y - log1p(y);
+}
+
 template <typename T>
 __device__ __forceinline__ T shape_independent(T q2, T q, const ModelConst<T>& mc)
 {
     switch (mc.function) {
     case SAS_FN_GUINIER: return exp(-q2 * mc.f_a);
-    case SAS_FN_GAUSS_COIL: {
-        const T u = q2 * mc.f_a;
-        constexpr bool fp32 = sizeof(T) == sizeof(float);
-        if (u < (fp32 ? (T)1 : (T)0.1)) {
-            constexpr int nt = fp32 ? 10 : 12;
-            T sum = 0, c = (T)2;   // c = 2 / (k + 2)!, from k = 0
-            T term[nt];
-#pragma unroll
-            for (int k = 0; k < nt; ++k) {
-                c = k == 0 ? (T)1 : c / (T)(k + 2);
-                term[k] = c;
-            }
-#pragma unroll
-            for (int k = nt - 1; k >= 0; --k) sum = fma(sum, -u, term[k]);
-            return sum;
-        }
-        return (T)2 * (expm1(-u) + u) / (u * u);
-    }
+    case SAS_FN_GAUSS_COIL: return debye_fn<T>(q2 * mc.f_a);
     case SAS_FN_LORENTZ: return (T)1 / fma(q2, mc.f_a, (T)1);
     case SAS_FN_DAB: {
         const T d = fma(q2, mc.f_a, (T)1);
@@ -749,7 +770,33 @@ __device__ __forceinline__ T shape_independent(T q2, T q, const ModelConst<T>& m
         const T d = q - mc.f_a;
         return exp(-d * d * mc.f_b);
     }
-    default: return (T)1 / fma(q2, fma(q2, mc.f_c, mc.f_b), mc.f_a);
+    case SAS_FN_TEUBNER_STREY: return (T)1 / fma(q2, fma(q2, mc.f_c, mc.f_b), mc.f_a);
+    case SAS_FN_PEAK_LORENTZ: {   // f_a = Q0, f_b = 1 / B
+        const T d = (q - mc.f_a) * mc.f_b;
+        return (T)1 / fma(d, d, (T)1);
+    }
+    case SAS_FN_TWO_POWER_LAW:    // f_a = Qc, f_b = m1, f_c = m2, f_d = Qc^(m2 - m1)
+        return q <= mc.f_a ? pow(q, -mc.f_b) : mc.f_d * pow(q, -mc.f_c);
+    case SAS_FN_GUINIER_POROD:    // f_a = Rg^2 / (3 - s), f_b = s, f_c = m, f_d = Q1, f_e = D
+        return q <= mc.f_d ? pow(q, -mc.f_b) * exp(-q2 * mc.f_a) : mc.f_e * pow(q, -mc.f_c);
+    case SAS_FN_GAUSS_LORENTZ_GEL:   // f_a = Xi^2 / 2, f_b = xi^2, f_c = r
+        return exp(-q2 * mc.f_a) + mc.f_c / fma(q2, mc.f_b, (T)1);
+    case SAS_FN_POLY_GAUSS_COIL: {   // f_a = Rg^2 / (1 + 2U), f_b = U
+        // with t = log(1 + U x) / U: (1 + U x)^(-1/U) - 1 + x
+        //   = (exp(-t) - 1 + t) + (x - t) = t^2 D(t) / 2 + (U x - log(1 + U x)) / U,
+        // two non-negative terms, so the numerator does not cancel
+        const T x = q2 * mc.f_a, U = mc.f_b;
+        if (x < (T)1e-30) return (T)1;
+        const T y = U * x;
+        const T t = U > (T)0 ? log1p(y) / U : x;
+        const T h = U > (T)0 ? y_minus_log1p<T>(y) / U : (T)0;
+        return (t * t * debye_fn<T>(t) + (T)2 * h) / (((T)1 + U) * x * x);
+    }
+    default: {                    // star polymer: f_a = Rg^2 f / (3f - 2), f_b = f
+        const T v = q2 * mc.f_a;
+        const T g = v > (T)1e-30 ? -expm1(-v) / v : (T)1;
+        return (debye_fn<T>(v) + (mc.f_b - (T)1) * g * g) / mc.f_b;
+    }
     }
 }
 

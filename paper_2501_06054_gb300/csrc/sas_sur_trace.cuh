@@ -269,8 +269,10 @@ __device__ __forceinline__ void train_features(const STParams& P, unsigned char*
         const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            P.xt[(size_t)(8 * c + 2 * j) * P.batch + i] = __ushort_as_bfloat16((unsigned short)(w4[j] & 0xFFFFu));
-            P.xt[(size_t)(8 * c + 2 * j + 1) * P.batch + i] = __ushort_as_bfloat16((unsigned short)(w4[j] >> 16));
+            __stcs(reinterpret_cast<unsigned short*>(P.xt + (size_t)(8 * c + 2 * j) * P.batch + i),
+                   (unsigned short)(w4[j] & 0xFFFFu));
+            __stcs(reinterpret_cast<unsigned short*>(P.xt + (size_t)(8 * c + 2 * j + 1) * P.batch + i),
+                   (unsigned short)(w4[j] >> 16));
         }
     }
 }
@@ -289,8 +291,10 @@ __device__ __forceinline__ void store_pair_t(__nv_bfloat16* dst, uint32_t ld, in
     const uint32_t lo = odd ? r : v01, hi = odd ? v23 : r;   // words of the even row, then the odd row
     const uint32_t w0 = __byte_perm(lo, hi, 0x5410), w1 = __byte_perm(lo, hi, 0x7632);
     uint32_t* p = reinterpret_cast<uint32_t*>(dst + (size_t)(c + (odd ? 2 : 0)) * ld + (row & ~1u));
-    p[0] = w0;
-    p[ld >> 1] = w1;
+    // streaming stores (evict first): the activations pass through L2 once,
+    // and must not push the weights the TMA ring reads out of it
+    __stcs(reinterpret_cast<unsigned int*>(p), w0);
+    __stcs(reinterpret_cast<unsigned int*>(p + (ld >> 1)), w1);
 }
 
 // MODE_BWD: the history warps form d loss / d out = scale (pred - y) of each
@@ -591,7 +595,9 @@ __global__ void __launch_bounds__(ST_THREADS, 1) sur_trace_kernel(const STParams
                             __nv_bfloat16 zpre[32];
                             const __nv_bfloat16* zsrc = P.zt[zl] + (size_t)col0 * P.batch + i;
 #pragma unroll
-                            for (int j = 0; j < 32; ++j) zpre[j] = zsrc[(size_t)j * P.batch];
+                            for (int j = 0; j < 32; ++j)
+                                zpre[j] = __ushort_as_bfloat16(
+                                    __ldcs(reinterpret_cast<const unsigned short*>(zsrc + (size_t)j * P.batch)));
                             uint32_t w[16];   // bf16x2 of columns (2t, 2t + 1) of this row
 #pragma unroll
                             for (int t = 0; t < 16; ++t) {

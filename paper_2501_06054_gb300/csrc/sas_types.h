@@ -105,9 +105,10 @@ struct ModelConst {
     // hollow rectangular prism: inner half-edges and the two a b c products
     T ax_ai, ax_bi, ax_ci, ax_v, ax_vi;
     // shape-independent laws: the function and its parameters (Rg^2 / 3,
-    // Rg^2, xi^2, m, Q0 and 1 / (2 sigma^2), or a2, c1, c2 in f_a, f_b, f_c)
+    // Rg^2, xi^2, m, Q0 and 1 / (2 sigma^2), or a2, c1, c2 in f_a, f_b, f_c;
+    // the later laws as set in model_const)
     int function;
-    T f_a, f_b, f_c;
+    T f_a, f_b, f_c, f_d, f_e;
 };
 
 }  // namespace sas

@@ -93,6 +93,14 @@ MUTATIONS = {
     28: ("Gaussian coil without the -1 of Debye's function", "coil", "test_shape_independent_oracle.py", C,
          [("f = u < 1e-3 ? 1.0 - u / 3.0 + u * u / 12.0 : 2.0 * (expm1(-u) + u) / (u * u);",
            "f = u < 1e-3 ? 1.0 : 2.0 * (exp(-u) + u) / (u * u);")]),
+    29: ("star polymer with f instead of f - 1 arm pairs", "star", "test_shape_independent_oracle.py", C,
+         [("f = (deb + (fa - 1.0) * g * g) / fa;", "f = (deb + fa * g * g) / fa;")]),
+    30: ("polydisperse coil with the weight-average instead of the z-average radius", "poly_coil",
+         "test_shape_independent_oracle.py", C,
+         [("x = q2 * m->f_p0 * m->f_p0 / (1.0 + 2.0 * U);", "x = q2 * m->f_p0 * m->f_p0 / (1.0 + U);")]),
+    31: ("Guinier-Porod join without the Guinier factor", "guinier_porod", "test_shape_independent_oracle.py", C,
+         [("else f = pow(q1, mp - sd) * exp(-(mp - sd) / 2.0) * pow(q, -mp);",
+           "else f = pow(q1, mp - sd) * pow(q, -mp);")]),
 }
 
 

@@ -30,7 +30,8 @@ def _cuda():
 
 
 # laws held to the relative tolerance alone (no zeros, no underflow on the grid)
-RELATIVE_ONLY = {"lorentz", "dab", "power_law", "teubner_strey"}
+RELATIVE_ONLY = {"lorentz", "dab", "power_law", "teubner_strey", "peak_lorentz", "two_power_law",
+                 "guinier_porod", "guinier_porod_rod", "gauss_lorentz_gel", "poly_coil", "star"}
 
 LAWS = {
     "guinier": (W.GUINIER, (40.0, 0.0, 0.0)),
@@ -40,6 +41,13 @@ LAWS = {
     "power_law": (W.POWER_LAW, (3.6, 0.0, 0.0)),
     "gauss_peak": (W.GAUSS_PEAK, (0.05, 0.008, 0.0)),
     "teubner_strey": (W.TEUBNER_STREY, (1.0, -120.0, 1.0e4)),
+    "peak_lorentz": (W.PEAK_LORENTZ, (0.05, 0.01, 0.0)),
+    "two_power_law": (W.TWO_POWER_LAW, (0.03, 1.7, 3.9)),
+    "guinier_porod": (W.GUINIER_POROD, (40.0, 0.0, 4.0)),
+    "guinier_porod_rod": (W.GUINIER_POROD, (30.0, 1.0, 3.5)),
+    "gauss_lorentz_gel": (W.GAUSS_LORENTZ_GEL, (80.0, 25.0, 0.3)),
+    "poly_coil": (W.POLY_GAUSS_COIL, (50.0, 0.5, 0.0)),
+    "star": (W.STAR_POLYMER, (40.0, 6.0, 0.0)),
 }
 
 
@@ -84,7 +92,8 @@ def _records(e, first, n, seed):
     return pix.cpu().numpy().astype(np.int64), w.cpu().numpy()
 
 
-@pytest.mark.parametrize("name,precision", [("coil", W.FP32), ("dab", W.FP64), ("teubner_strey", W.FP32)])
+@pytest.mark.parametrize("name,precision", [("coil", W.FP32), ("dab", W.FP64), ("teubner_strey", W.FP32),
+                                            ("poly_coil", W.FP32), ("star", W.FP64), ("guinier_porod", W.FP32)])
 def test_records_and_trace(name, precision):
     m = _m(name, precision)
     inst = W.instrument(nx=64, ny=64)
@@ -106,7 +115,7 @@ def test_records_and_trace(name, precision):
     e.close()
 
 
-@pytest.mark.parametrize("bad", [dict(function=7), dict(f_p0=0.0), dict(f_scale=-1.0),
+@pytest.mark.parametrize("bad", [dict(function=13), dict(f_p0=0.0), dict(f_scale=-1.0),
                                  dict(sampling=W.PER_EVENT), dict(self_attenuation=1),
                                  dict(sq_kind=W.SQ_HARD_SPHERE_PY, sq_radius=10.0, sq_fraction=0.1)])
 def test_refusals(bad):

@@ -91,3 +91,113 @@ def test_isotropy(function, params):
     for q in (0.01, 0.07):
         v = oracle.dsigma(prep, q * d)
         assert np.max(np.abs(v / v[0] - 1)) < 1e-13
+
+
+# ---- the further laws of group G: peak Lorentz, two power laws, Guinier-Porod,
+# Gauss-Lorentz gel, polydisperse Gaussian coil, star polymer
+
+def test_peak_lorentz_maximum_and_half_width():
+    q0, b = 0.05, 0.01
+    m = _m(W.PEAK_LORENTZ, f_p0=q0, f_p1=b, f_scale=1.0)
+    assert _p(m, q0)[0] == pytest.approx(1.0, rel=1e-15)
+    lo, hi = _p(m, [q0 - b, q0 + b])
+    assert lo == pytest.approx(0.5, rel=1e-12) and hi == pytest.approx(0.5, rel=1e-12)
+    qs = np.linspace(0.001, 0.099, 37)
+    assert np.allclose(_p(m, qs), _p(m, 2 * q0 - qs), rtol=1e-12)    # symmetric about q0
+
+
+def _loglog_slope(m, q, h=1e-6):
+    a, b = _p(m, [q * (1 - h), q * (1 + h)])
+    return (math.log(b) - math.log(a)) / (math.log(1 + h) - math.log(1 - h))
+
+
+def test_two_power_law_continuity_and_slopes():
+    qc, m1, m2 = 0.03, 1.7, 3.9
+    m = _m(W.TWO_POWER_LAW, f_p0=qc, f_p1=m1, f_p2=m2, f_scale=1.0)
+    lo, hi = _p(m, [qc * (1 - 1e-12), qc * (1 + 1e-12)])
+    assert lo == pytest.approx(hi, rel=1e-9)
+    assert _p(m, qc)[0] == pytest.approx(qc ** -m1, rel=1e-13)
+    assert _loglog_slope(m, 0.01) == pytest.approx(-m1, rel=1e-6)
+    assert _loglog_slope(m, 0.1) == pytest.approx(-m2, rel=1e-6)
+
+
+@pytest.mark.parametrize("s", [0.0, 1.0, 2.0])
+def test_guinier_porod_is_smooth_at_its_join(s):
+    rg, mp = 40.0, 4.0
+    m = _m(W.GUINIER_POROD, f_p0=rg, f_p1=s, f_p2=mp, f_scale=1.0)
+    q1 = math.sqrt((mp - s) * (3 - s) / 2) / rg
+    lo, hi = _p(m, [q1 * (1 - 1e-12), q1 * (1 + 1e-12)])
+    assert lo == pytest.approx(hi, rel=1e-9)                     # the value joins
+    # and the slope: -s - 2 q^2 Rg^2 / (3 - s) reaches -m at q1
+    assert _loglog_slope(m, q1 * (1 - 1e-4)) == pytest.approx(-mp, rel=2e-3)
+    assert _loglog_slope(m, q1 * 1.5) == pytest.approx(-mp, rel=1e-6)
+    if s == 0.0:                                                 # Guinier at small q
+        q = 1e-3
+        assert _p(m, q)[0] == pytest.approx(math.exp(-(q * rg) ** 2 / 3), rel=1e-14)
+
+
+def test_gauss_lorentz_gel_limits():
+    xi_g, xi_l, r = 80.0, 25.0, 0.3
+    m = _m(W.GAUSS_LORENTZ_GEL, f_p0=xi_g, f_p1=xi_l, f_p2=r, f_scale=1.0)
+    assert _p(m, 0.0)[0] == pytest.approx(1.0 + r, rel=1e-15)
+    q = 0.04
+    assert _p(m, q)[0] == pytest.approx(math.exp(-0.5 * (q * xi_g) ** 2) + r / (1 + (q * xi_l) ** 2), rel=1e-14)
+    g0 = _m(W.GAUSS_LORENTZ_GEL, f_p0=xi_g, f_p1=xi_l, f_p2=0.0, f_scale=1.0)
+    lz = _m(W.LORENTZ, f_p0=xi_l, f_scale=r)
+    qs = np.array([0.01, 0.03, 0.08])
+    assert np.allclose(_p(m, qs), _p(g0, qs) + _p(lz, qs), rtol=1e-13)
+
+
+def test_poly_coil_against_a_schulz_zimm_average_of_chains():
+    """The closed form against its definition: Debye's function of chains
+    whose length N is Schulz-Zimm distributed (number density ~ N^z
+    e^-(z+1) N / N_n, Mw/Mn = 1 + U, U = 1/(z+1)), each weighted by N^2,
+    integrated numerically; Rg is the z-average radius of gyration, so the
+    number-average chain has Rg_n^2 = Rg^2 / (1 + 2U)."""
+    from scipy import integrate, special
+    rg = 50.0
+    for U in (0.1, 0.5, 1.0):
+        z = 1.0 / U - 1.0
+        m = _m(W.POLY_GAUSS_COIL, f_p0=rg, f_p1=U, f_scale=1.0)
+        rgn2 = rg * rg / (1 + 2 * U)
+        for q in (0.002, 0.01, 0.03, 0.1):
+            def debye(u):
+                return 2 * (math.expm1(-u) + u) / (u * u) if u > 1e-6 else 1 - u / 3
+
+            def w(n):   # N in units of N_n
+                return n ** (z + 2) * math.exp(-(z + 1) * n)
+            num = integrate.quad(lambda n: w(n) * debye(q * q * rgn2 * n), 0, np.inf, limit=400)[0]
+            den = math.exp(special.gammaln(z + 3) - (z + 3) * math.log(z + 1))
+            assert _p(m, q)[0] == pytest.approx(num / den, rel=1e-8), (U, q)
+    mono = _m(W.GAUSS_COIL, f_p0=rg, f_scale=1.0)
+    zero = _m(W.POLY_GAUSS_COIL, f_p0=rg, f_p1=0.0, f_scale=1.0)
+    qs = np.array([1e-4, 1e-2, 0.05, 0.2])
+    assert np.allclose(_p(zero, qs), _p(mono, qs), rtol=1e-12)
+
+
+def test_star_polymer_against_a_discrete_gaussian_star():
+    """f arms of n Gaussian segments from one centre: the mean over all pairs
+    of exp(-Q^2 b^2 d / 6), d the number of segments between them along the
+    star (|i - j| on one arm, i + j across arms), with Rg^2 of the star
+    = (3f - 2) / f x n b^2 / 6; the closed form is the continuous limit
+    (corrections of order 1/n). Two arms make one chain: the Gaussian coil."""
+    rg = 40.0
+    n = 4000
+    i = np.arange(1, n + 1, dtype=np.float64)
+    for fa in (3, 6):
+        b2 = 6.0 * rg * rg * fa / ((3 * fa - 2) * n)
+        m = _m(W.STAR_POLYMER, f_p0=rg, f_p1=float(fa), f_scale=1.0)
+        for q in (0.005, 0.02, 0.06):
+            x = math.exp(-q * q * b2 / 6.0)
+            k = np.arange(1, n, dtype=np.float64)
+            same = n + 2.0 * np.sum((n - k) * x ** k)            # pairs on one arm
+            s1 = np.sum(x ** i)
+            cross = s1 * s1                                     # pairs on two different arms
+            pair = (fa * same + fa * (fa - 1) * cross) / (fa * n) ** 2
+            assert _p(m, q)[0] == pytest.approx(pair, rel=2e-3), (fa, q)
+    two = _m(W.STAR_POLYMER, f_p0=rg, f_p1=2.0, f_scale=1.0)
+    one = _m(W.STAR_POLYMER, f_p0=rg, f_p1=1.0, f_scale=1.0)
+    coil = _m(W.GAUSS_COIL, f_p0=rg, f_scale=1.0)
+    qs = np.array([1e-3, 0.01, 0.05, 0.2])
+    assert np.allclose(_p(two, qs), _p(coil, qs), rtol=1e-12)
+    assert np.allclose(_p(one, qs), _p(coil, qs), rtol=1e-12)
