@@ -269,15 +269,20 @@ static double oracle_shape_independent(const oracle_model *m, double q)
     }
     case 11: {  /* polydisperse Gaussian coil (Schulz-Zimm): Rg = f_p0, U = Mw/Mn - 1 = f_p1 */
         double U = m->f_p1, x = q2 * m->f_p0 * m->f_p0 / (1.0 + 2.0 * U);
-        if (x < 1e-3) {
-            /* 2 / (1 + U) sum_{k>=2} (-x)^(k-2) prod_{j=1}^{k-1} (1 + jU) / k! */
+        if (x * (1.0 + U) < 1e-2) {
+            /* 2 / (1 + U) sum_{k>=2} (-x)^(k-2) prod_{j=1}^{k-1} (1 + jU) / k!, to k = 9: successive
+               terms shrink by x (1 + (k - 1) U) / k < 0.09 / k here, so the first omitted one is
+               below 1e-14 of the sum */
             double c = (1.0 + U) / 2.0, sum = c;
-            c *= -x * (1.0 + 2.0 * U) / 3.0; sum += c;
-            c *= -x * (1.0 + 3.0 * U) / 4.0; sum += c;
+            for (int k = 3; k <= 9; ++k) {
+                c *= -x * (1.0 + (k - 1) * U) / k;
+                sum += c;
+            }
             f = 2.0 * sum / (1.0 + U);
         } else {
             double t = U > 0.0 ? log1p(U * x) / U : x;
-            f = 2.0 * (exp(-t) + x - 1.0) / ((1.0 + U) * x * x);
+            /* exp(-t) + x - 1 written as expm1(-t) + x: rounding then scales as eps / x, not eps / x^2 */
+            f = 2.0 * (expm1(-t) + x) / ((1.0 + U) * x * x);
         }
         break;
     }

@@ -175,6 +175,29 @@ def test_poly_coil_against_a_schulz_zimm_average_of_chains():
     assert np.allclose(_p(zero, qs), _p(mono, qs), rtol=1e-12)
 
 
+def test_poly_coil_moment_series_at_small_q():
+    """Debye's function as its power series sum_k 2 (-u)^k / (k + 2)!,
+    averaged term by term over the same N^2-weighted Schulz-Zimm chains:
+    <N^k> / N_n^k = prod_{j<k} (1 + (2 + j) U). At u = Q^2 Rg_n^2 <= 0.03 forty
+    terms give the average to rounding, so the closed form and its series
+    branch must both agree to 1e-12 across their switch (cancellation or a
+    truncated series near it shows up here first)."""
+    rg = 50.0
+    for U in (0.1, 0.5, 1.0, 4.0):
+        m = _m(W.POLY_GAUSS_COIL, f_p0=rg, f_p1=U, f_scale=1.0)
+        rgn2 = rg * rg / (1 + 2 * U)
+        xs = np.logspace(-7, math.log10(0.03), 57)
+        qs = np.sqrt(xs / rgn2)
+        got = _p(m, qs)
+        for x, g in zip(xs, got):
+            s, mom, fact = 0.0, 1.0, 2.0
+            for k in range(40):
+                s += 2.0 * (-x) ** k * mom / fact
+                mom *= 1.0 + (2 + k) * U
+                fact *= k + 3
+            assert g == pytest.approx(s, rel=1e-12, abs=0.0), (U, x)
+
+
 def test_star_polymer_against_a_discrete_gaussian_star():
     """f arms of n Gaussian segments from one centre: the mean over all pairs
     of exp(-Q^2 b^2 d / 6), d the number of segments between them along the
