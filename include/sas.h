@@ -373,7 +373,14 @@ typedef struct sas_launch_config {
     int32_t agg;             /* 1: combine lanes of a warp hitting the same pixel first */
     int32_t ctas_per_sm;     /* resident CTAs per SM of the persistent grid (0: all that fit) */
     int32_t stage_orient;    /* 1: copy the orientation table into shared memory */
-    int32_t reserved;
+    int32_t order_q;         /* 1: each CTA orders its histories by |Q| before the model's
+                                average, so that a warp's lanes take the same branch of the
+                                sphere amplitude (series or closed form) at most radius nodes.
+                                Applies to FP32 sphere and core-shell sphere quadrature traces
+                                with >= 4 radius nodes and room for the ordering buffers
+                                (24 bytes per thread + 1032 bytes) in shared memory; ignored
+                                otherwise. The histories, their weights and tallies are the
+                                same either way. */
 } sas_launch_config;
 
 /* Read / replace the launch configuration of the experiment's trace kernel.

@@ -55,7 +55,7 @@ class sas_model_desc(ctypes.Structure):
 
 class sas_launch_config(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in (
-        "block", "tally", "agg", "ctas_per_sm", "stage_orient", "reserved")]
+        "block", "tally", "agg", "ctas_per_sm", "stage_orient", "order_q")]
 
 
 class sas_batch_config(ctypes.Structure):

@@ -542,17 +542,19 @@ sas_status build_model_tables(const sas_model_desc& m, ModelTables& t, double q_
         if (m.kind == SAS_SPHERE) {
             const double V = 4.0 / 3.0 * pi * ri * ri * ri;
             const double F0 = (m.sld - m.sld_solvent) * V;
-            p[0] = ri; p[1] = 1.0 / ri; p[2] = 9.0 * w[i] * F0 * F0;
+            p[2] = 9.0 * w[i] * F0 * F0;
+            p[0] = ri; p[1] = p[2] / (ri * ri * ri * ri * ri * ri); p[3] = ri * ri; p[4] = 1.0 / ri;
             vmean += w[i] * V;
         } else if (m.kind == SAS_CORE_SHELL) {
             const double ro = ri + m.thickness;
             const double Vc = 4.0 / 3.0 * pi * ri * ri * ri, Vo = 4.0 / 3.0 * pi * ro * ro * ro;
             const double sw = std::sqrt(w[i]);
-            p[0] = ri; p[1] = 1.0 / ri; p[2] = ro; p[3] = 1.0 / ro;
-            p[4] = 3.0 * sw * (m.sld - m.sld_shell) * Vc;
-            p[5] = 3.0 * sw * (m.sld_shell - m.sld_solvent) * Vo;
-            p[6] = p[4] / (ri * ri * ri);
-            p[7] = p[5] / (ro * ro * ro);
+            p[0] = ri * ri; p[1] = ro * ro;
+            p[2] = 3.0 * sw * (m.sld - m.sld_shell) * Vc;
+            p[3] = 3.0 * sw * (m.sld_shell - m.sld_solvent) * Vo;
+            p[4] = p[2] / (ri * ri * ri);
+            p[5] = p[3] / (ro * ro * ro);
+            p[6] = ri; p[7] = ro;
             vmean += w[i] * Vo;
         } else if (m.kind == SAS_CYLINDER) {
             const double V = pi * ri * ri * m.length;
@@ -1138,6 +1140,9 @@ cudaError_t dispatch_eval(sas_experiment* e, const ModelConst<T>& mc, const T* q
     }
 }
 
+bool can_order_q(const sas_experiment* e, const LaunchCfg& c);
+float order_q_scale(const sas_experiment* e);
+
 template <typename T>
 TraceParams<T> make_params(sas_experiment* e, uint64_t first, uint64_t n, uint64_t seed)
 {
@@ -1161,7 +1166,40 @@ TraceParams<T> make_params(sas_experiment* e, uint64_t first, uint64_t n, uint64
     P.sum_w2 = e->d_sum_w2;
     P.count = e->d_count;
     P.trans = e->d_trans;
+    P.q2_bin = (e->cfg.order_q && can_order_q(e, e->cfg)) ? order_q_scale(e) : 0.f;
     return P;
+}
+
+// The |Q|-ordered trace pass applies to the FP32 sphere and core-shell sphere
+// with quadrature averages over at least four radius nodes in ascending order
+// whose tables, histogram and ordering buffers fit in one CTA's shared memory.
+bool can_order_q(const sas_experiment* e, const LaunchCfg& c)
+{
+    const sas_model_desc& m = e->model;
+    if (m.precision != SAS_FP32 || (m.kind != SAS_SPHERE && m.kind != SAS_CORE_SHELL)) return false;
+    if (m.sampling != SAS_QUADRATURE) return false;
+    const int np = e->tables.n_poly;
+    if (np < 4) return false;
+    for (int i = 1; i < np; ++i)
+        if (e->tables.poly[(size_t)i * SAS_POLY_STRIDE] < e->tables.poly[(size_t)(i - 1) * SAS_POLY_STRIDE])
+            return false;   // column 0 is r (sphere) or r_c^2 (core-shell): ascending with the radius
+    size_t need = table_bytes<float>(np, e->tables.n_orient, 0) + sort_bytes(c.block);
+    if (c.tally == TALLY_SMEM) need += hist_bytes((int)(e->inst.nx * e->inst.ny));
+    return need <= (size_t)e->smem_optin;
+}
+
+// Bins per unit |Q|^2 of the ordering: SORT_BINS bins up to the largest |Q|
+// the geometry allows (shortest wavelength, detector corner seen from the
+// edge of the sample); larger values share the last bin.
+float order_q_scale(const sas_experiment* e)
+{
+    const sas_instrument& in = e->inst;
+    const double kmax = 2.0 * M_PI / (in.lambda0 * (1.0 - in.dlambda_rel));
+    const double hx = 0.5 * in.nx * in.pixel_x + in.sample_half_x + in.ap2_radius;
+    const double hy = 0.5 * in.ny * in.pixel_y + in.sample_half_y + in.ap2_radius;
+    const double theta = std::atan2(std::sqrt(hx * hx + hy * hy), in.det_distance);
+    const double qmax = 2.0 * kmax * std::sin(0.5 * theta);
+    return (float)(SORT_BINS / (qmax * qmax));
 }
 
 // Default launch configuration: the shared-memory histogram when it fits
@@ -1179,6 +1217,7 @@ void choose_config(sas_experiment* e)
     c.agg = 0;
     c.ctas_per_sm = 0;
     c.tally = TALLY_GLOBAL;
+    c.order_q = 0;
     e->stage_orient = 0;
     if (fp32) {
         if (no > 1) {
@@ -1191,6 +1230,7 @@ void choose_config(sas_experiment* e)
         e->stage_orient = (no > 1 && table_bytes<double>(np, no, 1) <= optin) ? 1 : 0;
         c.block = 256;
     }
+    c.order_q = can_order_q(e, c) ? 1 : 0;
     e->cfg = c;
 }
 
@@ -1357,7 +1397,7 @@ sas_status sas_get_launch_config(const sas_experiment* e, sas_launch_config* c)
     c->agg = e->cfg.agg;
     c->ctas_per_sm = e->cfg.ctas_per_sm;
     c->stage_orient = e->stage_orient;
-    c->reserved = 0;
+    c->order_q = e->cfg.order_q;
     return SAS_OK;
 }
 
@@ -1382,6 +1422,7 @@ sas_status sas_set_launch_config(sas_experiment* e, const sas_launch_config* c)
     e->cfg.tally = c->tally;
     e->cfg.agg = c->agg ? 1 : 0;
     e->cfg.ctas_per_sm = c->ctas_per_sm;
+    e->cfg.order_q = c->order_q ? 1 : 0;
     e->stage_orient = stage;
     return SAS_OK;
 }
@@ -1403,10 +1444,13 @@ sas_status sas_autotune(sas_experiment* e, uint64_t n_sample, uint64_t seed, sas
     sas_get_launch_config(e, &best);
     float best_t = 1e30f;
     const bool aniso = e->tables.n_orient > 1;
+    const bool orderable = can_order_q(e, LaunchCfg{32, TALLY_GLOBAL, 0, 0, 1});
     for (int tally : {TALLY_SMEM, TALLY_GLOBAL})
         for (int agg : {0, 1})
-            for (int stage : {1, 0}) {
+            for (int stage : {1, 0})
+                for (int oq : {1, 0}) {
                 if (!aniso && stage) continue;
+                if (!orderable && oq) continue;
                 for (int blk : blocks) {
                     sas_launch_config c;
                     c.block = blk;
@@ -1414,7 +1458,7 @@ sas_status sas_autotune(sas_experiment* e, uint64_t n_sample, uint64_t seed, sas
                     c.agg = agg;
                     c.ctas_per_sm = 0;
                     c.stage_orient = stage;
-                    c.reserved = 0;
+                    c.order_q = oq;
                     if (sas_set_launch_config(e, &c) != SAS_OK) continue;
                     if (sas_trace_range(e, 0, n_sample, seed) != SAS_OK) continue;
                     cudaEventRecord(e0, e->stream);

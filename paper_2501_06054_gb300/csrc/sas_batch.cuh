@@ -70,7 +70,7 @@ __device__ __forceinline__ void batch_item(const BatchParams& P, const ModelCons
             }
         }
         if (HIST) {
-            if (pix >= 0) hist_add(h, cnt, pix, wt, wt * wt, 1u);
+            if (pix >= 0) h.add(cnt, pix, wt, wt * wt, 1u);
         } else if (pix >= 0) {
             atomicAdd(sw + pix, (double)wt);
             atomicAdd(sw2 + pix, (double)wt * (double)wt);
@@ -146,19 +146,9 @@ __global__ void __launch_bounds__(1024) batch_kernel(const BatchParams P)
             orient = s_or;
         }
         SmemHist h;
-        h.npix = P.npix;
+        h.bind(smem + table_bytes<float>(mc.n_poly, 0, 0), P.npix);
         const bool hist = HIST_OK && s_e.use_hist;
-        if (hist) {
-            unsigned char* base = smem + table_bytes<float>(mc.n_poly, 0, 0);
-            h.kw = reinterpret_cast<float2*>(base);
-            h.w2 = reinterpret_cast<float*>(base + (size_t)h.npix * 8);
-            h.cnt = reinterpret_cast<uint32_t*>(base + (size_t)h.npix * 12);
-            for (int i = threadIdx.x; i < h.npix; i += blockDim.x) {
-                h.kw[i] = make_float2(0.f, 0.f);
-                h.w2[i] = 0.f;
-            }
-            for (int i = threadIdx.x; i < (h.npix + 1) / 2; i += blockDim.x) h.cnt[i] = 0u;
-        }
+        if (hist) h.clear();
         __syncthreads();
         Kahan<float> tr;
         if (mc.att.n > 0) {
@@ -174,19 +164,8 @@ __global__ void __launch_bounds__(1024) batch_kernel(const BatchParams P)
         if ((threadIdx.x & 31) == 0 && t != 0.0) atomicAdd(P.trans + w.exp, t);
         __syncthreads();
         if (hist) {   // FP64 per-bin reduction of this item into its detector
-            double* sw = P.sum_w + (size_t)w.exp * P.npix;
-            double* sw2 = P.sum_w2 + (size_t)w.exp * P.npix;
-            unsigned long long* cnt = P.count + (size_t)w.exp * P.npix;
-            for (int p = threadIdx.x; p < h.npix; p += blockDim.x) {
-                const float2 kw = h.kw[p];
-                const float s2 = h.w2[p];
-                const uint32_t c = (h.cnt[p >> 1] >> ((p & 1) * 16)) & 0xFFFFu;
-                if (c != 0u || kw.x != 0.f || s2 != 0.f) {
-                    atomicAdd(sw + p, (double)kw.x - (double)kw.y);
-                    atomicAdd(sw2 + p, (double)s2);
-                    if (c) atomicAdd(cnt + p, (unsigned long long)c);
-                }
-            }
+            h.flush(P.sum_w + (size_t)w.exp * P.npix, P.sum_w2 + (size_t)w.exp * P.npix,
+                    P.count + (size_t)w.exp * P.npix);
             __syncthreads();
         }
     }

@@ -196,7 +196,7 @@ __device__ __forceinline__ T avg_sphere(T q, T iq, const T* __restrict__ poly, i
 #pragma unroll 4
     for (int i = 0; i < np; ++i) {
         const T* p = poly + 8 * i;
-        const T g = M<T>::sphere_g(q * p[0], iq * p[1]);
+        const T g = M<T>::sphere_g(q * p[0], iq * p[4]);
         acc = fma(p[2], g * g, acc);
     }
     return acc;
@@ -219,9 +219,9 @@ __device__ __forceinline__ T avg_core_shell(T q, T iq, const T* __restrict__ pol
                              2.505210839e-07f};
 #pragma unroll 8
         for (int i = 0; i < np; ++i) {
-            const float4 pa = *reinterpret_cast<const float4*>(poly + 8 * i);       // r_c, 1/r_c, r_o, 1/r_o
-            const float4 pb = *reinterpret_cast<const float4*>(poly + 8 * i + 4);   // c_1, c_2, c_1/r_c^3, c_2/r_o^3
-            const float x1 = q * pa.x, x2 = q * pa.z;
+            const float4 pa = *reinterpret_cast<const float4*>(poly + 8 * i);       // r_c^2, r_o^2, c_1, c_2
+            const float4 pb = *reinterpret_cast<const float4*>(poly + 8 * i + 4);   // c_1/r_c^3, c_2/r_o^3, r_c, r_o
+            const float x1 = q * pb.z, x2 = q * pb.w;
             float s1, c1, s2, c2;
             __sincosf(x1, &s1, &c1);
             __sincosf(x2, &s2, &c2);
@@ -229,8 +229,8 @@ __device__ __forceinline__ T avg_core_shell(T q, T iq, const T* __restrict__ pol
             const float h1 = sas_horner(gs, x1 * x1), h2 = sas_horner(gs, x2 * x2);
             // select (coefficient, value) pairs, then one FMA combines them
             const bool s1b = x1 < 1.5f, s2b = x2 < 1.5f;
-            const float k1 = s1b ? pb.x : iq3 * pb.z, v1 = s1b ? h1 : A1;
-            const float k2 = s2b ? pb.y : iq3 * pb.w, v2 = s2b ? h2 : A2;
+            const float k1 = s1b ? pa.z : iq3 * pb.x, v1 = s1b ? h1 : A1;
+            const float k2 = s2b ? pa.w : iq3 * pb.y, v2 = s2b ? h2 : A2;
             const float F = fmaf(k1, v1, k2 * v2);
             acc = fmaf(F, F, acc);
         }
@@ -238,13 +238,157 @@ __device__ __forceinline__ T avg_core_shell(T q, T iq, const T* __restrict__ pol
 #pragma unroll 4
         for (int i = 0; i < np; ++i) {
             const T* p = poly + 8 * i;
-            const T g1 = M<T>::sphere_g(q * p[0], iq * p[1]);
-            const T g2 = M<T>::sphere_g(q * p[2], iq * p[3]);
-            const T F = fma(p[4], g1, p[5] * g2);
+            const T x1 = q * p[6], x2 = q * p[7];
+            const T g1 = M<T>::sphere_g(x1, M<T>::rcp(x1));
+            const T g2 = M<T>::sphere_g(x2, M<T>::rcp(x2));
+            const T F = fma(p[2], g1, p[3] * g2);
             acc = fma(F, F, acc);
         }
     }
     return acc;
+}
+
+// ---------------------------------------------- |Q|-ordered warps (FP32)
+// When the histories of a warp carry nearby |Q| (the trace kernel orders a
+// CTA's histories by |Q|^2 first), most nodes of the radius table fall on one
+// side of the series/closed-form switch x = 1.5 for every lane. With the
+// nodes in ascending radius, the warp's smallest and largest |Q| cut the
+// table into three runs:
+//   [0, iA)   series for every lane (largest Q times the outer radius < 1.5),
+//   [iA, iC)  the per-lane selection of the plain loops,
+//   [iC, np)  closed form for every lane (smallest Q times the radius >= 1.5),
+// and each run does only its own branch's work. Every lane takes the same
+// branch per node as the plain loops; only the closed-form run accumulates
+// its terms before the common factor iq^3 (resp. iq^6) is applied once,
+// which is safe there because q >= 1.5 / r_max.
+struct NodeSplit {
+    int iA, iC;
+};
+
+// qlo, qhi: the warp's extreme |Q|; radius columns ri (inner) and ro (outer)
+// of a table with SAS_POLY_STRIDE floats per node
+__device__ __forceinline__ NodeSplit node_split(const float* __restrict__ poly, int np, int ri, int ro,
+                                                float qlo, float qhi)
+{
+    const int lane = threadIdx.x & 31;
+    int nA = 0, nC = 0;
+    for (int c0 = 0; c0 < np; c0 += 32) {
+        const int i = c0 + lane;
+        bool a = false, c = false;
+        if (i < np) {
+            a = qhi * poly[SAS_POLY_STRIDE * i + ro] < 1.5f;
+            c = qlo * poly[SAS_POLY_STRIDE * i + ri] >= 1.5f;
+        }
+        nA += __popc(__ballot_sync(0xffffffffu, a));
+        nC += __popc(__ballot_sync(0xffffffffu, c));
+    }
+    return NodeSplit{nA, np - nC};
+}
+
+__device__ __forceinline__ float avg_core_shell_split(float q, float q2, float iq, const float* __restrict__ poly,
+                                                      int np, float shell, NodeSplit sp)
+{
+    const float gs[5] = {3.333333333e-01f, -3.333333333e-02f, 1.190476190e-03f, -2.204585538e-05f,
+                         2.505210839e-07f};
+    float acc = 0.f;
+#pragma unroll 4
+    for (int i = 0; i < sp.iA; ++i) {   // series for both radii, in x^2 = q^2 r^2
+        const float4 pa = *reinterpret_cast<const float4*>(poly + 8 * i);   // r_c^2, r_o^2, c_1, c_2
+        const float F = fmaf(pa.z, sas_horner(gs, q2 * pa.x), pa.w * sas_horner(gs, q2 * pa.y));
+        acc = fmaf(F, F, acc);
+    }
+    const float iq3 = iq * iq * iq;
+    for (int i = sp.iA; i < sp.iC; ++i) {   // per-lane selection
+        const float4 pa = *reinterpret_cast<const float4*>(poly + 8 * i);       // r_c^2, r_o^2, c_1, c_2
+        const float4 pb = *reinterpret_cast<const float4*>(poly + 8 * i + 4);   // c_1/r_c^3, c_2/r_o^3, r_c, r_o
+        const float x1 = q * pb.z, x2 = q * pb.w;
+        float s1, c1, s2, c2;
+        __sincosf(x1, &s1, &c1);
+        __sincosf(x2, &s2, &c2);
+        const bool s1b = x1 < 1.5f, s2b = x2 < 1.5f;
+        const float k1 = s1b ? pa.z : iq3 * pb.x, v1 = s1b ? sas_horner(gs, x1 * x1) : fmaf(-x1, c1, s1);
+        const float k2 = s2b ? pa.w : iq3 * pb.y, v2 = s2b ? sas_horner(gs, x2 * x2) : fmaf(-x2, c2, s2);
+        const float F = fmaf(k1, v1, k2 * v2);
+        acc = fmaf(F, F, acc);
+    }
+    // Closed form for both radii. The outer radius is r_c + t at every node,
+    // so sin and cos of x2 follow from those of x1 and of q t (accurate,
+    // once per call) by the angle-addition identities: two special-function
+    // operations per node instead of four and one shared load, which keeps
+    // this run below the MIO queue's limit. With S = sin qt, C = cos qt,
+    //   sin x2 - x2 cos x2 = s1 (C + x2 S) + c1 (S - x2 C),
+    // so the node's amplitude k1 (s1 - x1 c1) + k2 (sin x2 - x2 cos x2) is
+    //   s1 (k1 + k2 (C + x2 S)) + c1 (k2 (S - x2 C) - k1 x1).
+    float St, Ct;
+    sincospif(q * shell * 0.318309886f, &St, &Ct);
+    float accC = 0.f;
+#pragma unroll 4
+    for (int i = sp.iC; i < np; ++i) {
+        const float4 pb = *reinterpret_cast<const float4*>(poly + 8 * i + 4);   // k_1, k_2, r_c, r_o
+        const float x1 = q * pb.z, x2 = q * pb.w;
+        float s1, c1;
+        __sincosf(x1, &s1, &c1);
+        const float gam = fmaf(pb.y, fmaf(x2, St, Ct), pb.x);
+        const float del = fmaf(pb.y, fmaf(-x2, Ct, St), -pb.x * x1);
+        const float F = fmaf(s1, gam, c1 * del);
+        accC = fmaf(F, F, accC);
+    }
+    return sp.iC < np ? fmaf(iq3 * iq3, accC, acc) : acc;   // iq3^2 may overflow below q = 4e-7
+}
+
+__device__ __forceinline__ float avg_sphere_split(float q, float q2, float iq, const float* __restrict__ poly,
+                                                  int np, NodeSplit sp)
+{
+    const float gs[5] = {3.333333333e-01f, -3.333333333e-02f, 1.190476190e-03f, -2.204585538e-05f,
+                         2.505210839e-07f};
+    float acc = 0.f;
+#pragma unroll 4
+    for (int i = 0; i < sp.iA; ++i) {
+        const float2 p = *reinterpret_cast<const float2*>(poly + 8 * i + 2);   // c, r^2
+        const float g = sas_horner(gs, q2 * p.y);
+        acc = fmaf(p.x, g * g, acc);
+    }
+    for (int i = sp.iA; i < sp.iC; ++i) {
+        const float* p = poly + 8 * i;
+        const float g = M<float>::sphere_g(q * p[0], iq * p[4]);
+        acc = fmaf(p[2], g * g, acc);
+    }
+    float accC = 0.f;
+#pragma unroll 4
+    for (int i = sp.iC; i < np; ++i) {
+        const float2 p = *reinterpret_cast<const float2*>(poly + 8 * i);   // r, c / r^6
+        const float x = q * p.x;
+        float s, c;
+        __sincosf(x, &s, &c);
+        const float A = fmaf(-x, c, s);
+        accC = fmaf(p.y, A * A, accC);
+    }
+    const float iq3 = iq * iq * iq;
+    return sp.iC < np ? fmaf(iq3 * iq3, accC, acc) : acc;
+}
+
+// dSigma/dOmega at |Q|^2 = q2 for a lane of a |Q|-ordered warp (sphere and
+// core-shell sphere, quadrature averages); inactive lanes (q2 < 0) return 0.
+// Every lane of the warp calls it.
+template <int KIND>
+__device__ __forceinline__ float dsigma_sorted(float q2, const ModelConst<float>& mc, const float* __restrict__ poly)
+{
+    const bool on = q2 >= 0.f;
+    const float q = on ? M<float>::sqrt_(q2) : 0.f;
+    const float qlo = __uint_as_float(__reduce_min_sync(0xffffffffu, on ? __float_as_uint(q) : 0x7F800000u));
+    const float qhi = __uint_as_float(__reduce_max_sync(0xffffffffu, on ? __float_as_uint(q) : 0u));
+    if (qlo == __uint_as_float(0x7F800000u)) return 0.f;   // no live lane
+    const float qe = on ? q : qhi, qe2 = on ? q2 : qhi * qhi;
+    const float iq = M<float>::rcp(qe);
+    float avg;
+    if constexpr (KIND == SAS_CORE_SHELL) {
+        avg = avg_core_shell_split(qe, qe2, iq, poly, mc.n_poly, mc.shell,
+                                   node_split(poly, mc.n_poly, 6, 7, qlo, qhi));
+    } else {
+        avg = avg_sphere_split(qe, qe2, iq, poly, mc.n_poly, node_split(poly, mc.n_poly, 0, 0, qlo, qhi));
+    }
+    const float v = mc.scale * avg * structure_factor<float>(qe, mc);
+    return on ? v : 0.f;
 }
 
 // Kahan-compensated accumulation of the orientation sum.

@@ -13,6 +13,7 @@
 // (__match_any_sync) so one lane updates the bin.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include "sas_device.cuh"
 
@@ -35,7 +36,24 @@ struct TraceParams {
     double* trans;
     int* pixel_out;            // records mode
     double* weight_out;        // records mode
+    float q2_bin;              // > 0: order each CTA's histories by |Q|^2, SORT_BINS bins per q2_bin^-1
 };
+
+// |Q|^2 bins of the per-CTA ordering (plus one for histories that missed the
+// sample) and the shared memory it takes next to the histogram
+constexpr int SORT_BINS = 128;
+constexpr int SORT_PER = 2;   // histories per thread and pass
+
+// independent sort groups of a CTA: two where each half is whole warps
+__host__ __device__ inline int sort_groups(int block)
+{
+    return block % 64 == 0 ? 2 : 1;
+}
+
+__host__ __device__ inline size_t sort_bytes(int block)
+{
+    return (size_t)block * SORT_PER * 12 + (size_t)sort_groups(block) * 2 * (SORT_BINS + 1) * 4;
+}
 
 // bytes of shared memory: staged tables followed by the histogram
 template <typename T>
@@ -48,52 +66,85 @@ __host__ __device__ inline size_t table_bytes(int n_poly, int n_orient, int stag
 
 __host__ __device__ inline size_t hist_bytes(int npix)
 {
-    return (size_t)npix * 12 + (size_t)((npix + 1) / 2) * 4;
+    return (size_t)npix * 12;
 }
 
 // ------------------------------------------------------------- tallies
 
-__device__ __forceinline__ void kahan_add_shared(float2* cell, float v)
-{
-    unsigned long long* a = reinterpret_cast<unsigned long long*>(cell);
-    unsigned long long old = *reinterpret_cast<volatile unsigned long long*>(a);
-    // lock-free retry; bounded, falls back to a plain add of the sum
-    for (int it = 0; it < (1 << 16); ++it) {
-        const float s = __uint_as_float((uint32_t)old);
-        const float c = __uint_as_float((uint32_t)(old >> 32));
-        const float y = v - c;
-        const float t = s + y;
-        const float cn = (t - s) - y;
-        const unsigned long long nw =
-            ((unsigned long long)__float_as_uint(cn) << 32) | (unsigned long long)__float_as_uint(t);
-        const unsigned long long prev = atomicCAS(a, old, nw);
-        if (prev == old) return;
-        old = prev;
-    }
-    atomicAdd(&cell->x, v);
-}
-
+// Per-CTA FP32 histogram in shared memory. Each pixel holds one 64-bit word,
+//   bits  0..31  s   the FP32 running sum of w,
+//   bits 32..47  c   Kahan's compensation of s, rounded to bfloat16,
+//   bits 48..63  n   the count, carried to global memory every 2^15,
+// updated together by one compare-and-swap, and an FP32 sum of w^2. The
+// compensation is the rounding error of the last addition (at most half an
+// ulp of s); keeping it to 8 bits leaves at most 2^-10 ulp of s per
+// addition uncorrected, where plain FP32 summation leaves up to half an ulp.
 struct SmemHist {
-    float2* kw;      // (sum, compensation)
+    unsigned long long* kw;
     float* w2;
-    uint32_t* cnt;   // two 16-bit counts per word
     int npix;
-};
 
-__device__ __forceinline__ void hist_add(const SmemHist& h, unsigned long long* gcount, int p,
-                                         float w, float w2, uint32_t inc)
-{
-    kahan_add_shared(h.kw + p, w);
-    atomicAdd(h.w2 + p, w2);
-    const int sh = (p & 1) * 16;
-    uint32_t* cw = h.cnt + (p >> 1);
-    const uint32_t old = atomicAdd(cw, inc << sh);
-    const uint32_t half = (old >> sh) & 0xFFFFu;
-    if (half < 0x8000u && half + inc >= 0x8000u) {   // carry 2^15 to global memory
-        atomicSub(cw, 0x8000u << sh);
-        atomicAdd(gcount + p, 0x8000ull);
+    __device__ __forceinline__ void bind(unsigned char* base, int n)
+    {
+        npix = n;
+        kw = reinterpret_cast<unsigned long long*>(base);
+        w2 = reinterpret_cast<float*>(base + (size_t)n * 8);
     }
-}
+    __device__ __forceinline__ void clear() const
+    {
+        for (int i = threadIdx.x; i < npix; i += blockDim.x) {
+            kw[i] = 0ull;
+            w2[i] = 0.f;
+        }
+    }
+    // sum w, sum w^2 and count n of one group of histories landing in pixel p
+    __device__ __forceinline__ void add(unsigned long long* gcount, int p, float w, float ww, uint32_t n) const
+    {
+        unsigned long long* a = kw + p;
+        unsigned long long old = *reinterpret_cast<volatile unsigned long long*>(a);
+        bool done = false, carry = false;
+        // lock-free retry; bounded, falls back to plain adds of the sum and the count
+        for (int it = 0; it < (1 << 16) && !done; ++it) {
+            const float sum = __uint_as_float((uint32_t)old);
+            const float c = __uint_as_float((uint32_t)(old >> 16) & 0xFFFF0000u);
+            const float y = w - c;
+            const float t = sum + y;
+            const float cn = (t - sum) - y;
+            uint32_t cnt = (uint32_t)(old >> 48) + n;
+            carry = cnt >= 0x8000u;
+            if (carry) cnt -= 0x8000u;
+            const unsigned long long nw = ((unsigned long long)cnt << 48) |
+                                          ((unsigned long long)__bfloat16_as_ushort(__float2bfloat16_rn(cn)) << 32) |
+                                          (unsigned long long)__float_as_uint(t);
+            const unsigned long long prev = atomicCAS(a, old, nw);
+            done = prev == old;
+            old = prev;
+        }
+        if (!done) {
+            atomicAdd(reinterpret_cast<float*>(a), w);
+            atomicAdd(gcount + p, (unsigned long long)n);
+        } else if (carry) {
+            atomicAdd(gcount + p, 0x8000ull);
+        }
+        atomicAdd(w2 + p, ww);
+    }
+    // FP64 per-bin reduction of the CTA's histogram into a detector
+    __device__ __forceinline__ void flush(double* sw, double* sw2, unsigned long long* cnt) const
+    {
+        for (int p = threadIdx.x; p < npix; p += blockDim.x) {
+            const unsigned long long v = kw[p];
+            const float s2 = w2[p];
+            const double sum = (double)__uint_as_float((uint32_t)v) -
+                               (double)__uint_as_float((uint32_t)(v >> 16) & 0xFFFF0000u);
+            const uint32_t c = (uint32_t)(v >> 48);
+            if (c != 0u || sum != 0.0 || s2 != 0.f) {
+                atomicAdd(sw + p, sum);
+                atomicAdd(sw2 + p, (double)s2);
+                if (c) atomicAdd(cnt + p, (unsigned long long)c);
+            }
+        }
+    }
+};
 
 // Combine lanes of the warp that hit the same pixel. On return, the lane is
 // the group leader iff `leader`; w/w2/n are the group sums there.
@@ -134,7 +185,7 @@ __device__ __forceinline__ void tally(const TraceParams<T>& P, const SmemHist& h
     if (AGG) warp_aggregate<T>(pix, w, w2, n, lead);
     if (!lead) return;
     if (TALLY == TALLY_SMEM) {
-        hist_add(h, P.count, pix, (float)w, (float)w2, n);
+        h.add(P.count, pix, (float)w, (float)w2, n);
     } else {
         atomicAdd(P.sum_w + pix, (double)w);
         atomicAdd(P.sum_w2 + pix, (double)w2);
@@ -144,7 +195,93 @@ __device__ __forceinline__ void tally(const TraceParams<T>& P, const SmemHist& h
 
 // ------------------------------------------------------------- kernels
 
-template <typename T, int KIND, int TALLY, int AGG, bool ATT>
+// barrier of `count` threads (a multiple of 32) under the named barrier `id`
+__device__ __forceinline__ void group_sync(int id, int count)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// One pass of a |Q|-ordered trace (SORT) by a group of nb threads (tid its
+// thread, bar its named barrier) over SORT_PER x nb consecutive histories.
+// Each thread traces SORT_PER of them and counts each
+// into its |Q|^2 bin (the shared-memory atomic returns its rank in the bin);
+// after an exclusive prefix sum over the bins every history's (|Q|^2, pixel,
+// prefactor) goes to its place in bin order, and each warp then evaluates
+// and tallies 32 consecutive places, i.e. histories of nearby |Q|. Thread t
+// takes places t and SORT_PER * nb - 1 - t, pairing low and high |Q|
+// so that warps get similar work. The set of histories, their values and
+// their tallies are those of the plain loop; only which lane evaluates which
+// history changes. The bin counters alternate between two arrays: the ones
+// of this pass are cleared after the last read of them and next counted into
+// two passes later, behind this pass's and the next pass's barriers.
+template <int KIND, int TALLY, int AGG, bool ATT>
+__device__ __forceinline__ void trace_sorted_pass(const TraceParams<float>& P, const SmemHist& h, const float* poly,
+                                                  float* s_q2, int* s_pix, float* s_pref, int* s_bin,
+                                                  uint64_t base, Kahan<float>& tr, int tid, int nb, int bar)
+{
+    int key[SORT_PER], rank[SORT_PER], pix[SORT_PER];
+    float q2[SORT_PER], pref[SORT_PER];
+#pragma unroll
+    for (int k = 0; k < SORT_PER; ++k) {
+        const uint64_t j = base + (uint64_t)k * nb + tid;
+        pix[k] = -1;
+        pref[k] = 0.f;
+        q2[k] = -1.f;
+        if (j < P.n) {
+            const History<float> hs = history<float, ATT>(P.in, P.mc.att, P.seed, P.exp_id, P.first + j);
+            tr.add(hs.wt);
+            if (hs.pixel >= 0) {
+                pix[k] = hs.pixel;
+                pref[k] = hs.pref;
+                q2[k] = fmaf(hs.q[0], hs.q[0], fmaf(hs.q[1], hs.q[1], hs.q[2] * hs.q[2]));
+            }
+        }
+        key[k] = pix[k] >= 0 ? min((int)(q2[k] * P.q2_bin), SORT_BINS - 1) : SORT_BINS;
+        rank[k] = atomicAdd(s_bin + key[k], 1);
+    }
+    group_sync(bar, nb);
+    if (tid < 32) {   // exclusive prefix sum of the bin counts, in place
+        constexpr int per = (SORT_BINS + 1 + 31) / 32;
+        const int b0 = tid * per;
+        int loc[per], sum = 0;
+#pragma unroll
+        for (int k = 0; k < per; ++k) {
+            loc[k] = (b0 + k <= SORT_BINS) ? s_bin[b0 + k] : 0;
+            sum += loc[k];
+        }
+        int inc = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, inc, o);
+            if (tid >= o) inc += v;
+        }
+        int run = inc - sum;
+#pragma unroll
+        for (int k = 0; k < per; ++k) {
+            if (b0 + k <= SORT_BINS) s_bin[b0 + k] = run;
+            run += loc[k];
+        }
+    }
+    group_sync(bar, nb);
+#pragma unroll
+    for (int k = 0; k < SORT_PER; ++k) {
+        const int pos = s_bin[key[k]] + rank[k];
+        s_q2[pos] = q2[k];
+        s_pix[pos] = pix[k];
+        s_pref[pos] = pref[k];
+    }
+    group_sync(bar, nb);
+    for (int i = tid; i <= SORT_BINS; i += nb) s_bin[i] = 0;
+#pragma unroll
+    for (int k = 0; k < SORT_PER; ++k) {
+        const int slot = (k & 1) ? SORT_PER * nb - 1 - (k >> 1) * nb - tid
+                                 : (k >> 1) * nb + tid;
+        const float v = dsigma_sorted<KIND>(s_q2[slot], P.mc, poly);
+        tally<float, TALLY, AGG>(P, h, s_pix[slot], s_pref[slot] * v);
+    }
+}
+
+template <typename T, int KIND, int TALLY, int AGG, bool ATT, bool SORT = false>
 __global__ void __launch_bounds__(1024) trace_kernel(const TraceParams<T> P)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -163,17 +300,29 @@ __global__ void __launch_bounds__(1024) trace_kernel(const TraceParams<T> P)
         }
     }
     SmemHist h;
-    h.npix = P.in.nx * P.in.ny;
-    if (TALLY == TALLY_SMEM) {
-        unsigned char* base = smem + table_bytes<T>(P.mc.n_poly, P.mc.n_orient, P.stage_orient);
-        h.kw = reinterpret_cast<float2*>(base);
-        h.w2 = reinterpret_cast<float*>(base + (size_t)h.npix * 8);
-        h.cnt = reinterpret_cast<uint32_t*>(base + (size_t)h.npix * 12);
-        for (int i = threadIdx.x; i < h.npix; i += blockDim.x) {
-            h.kw[i] = make_float2(0.f, 0.f);
-            h.w2[i] = 0.f;
-        }
-        for (int i = threadIdx.x; i < (h.npix + 1) / 2; i += blockDim.x) h.cnt[i] = 0u;
+    unsigned char* hbase = smem + table_bytes<T>(P.mc.n_poly, P.mc.n_orient, P.stage_orient);
+    h.bind(hbase, P.in.nx * P.in.ny);
+    if (TALLY == TALLY_SMEM) h.clear();
+    // |Q|-ordered passes: the CTA's warps form sort_groups() independent
+    // groups (named barriers 1, 2), each with its own buffers, so that one
+    // group's barrier and prefix-sum phases overlap the other's work.
+    float* s_q2 = nullptr;
+    float* s_pref = nullptr;
+    int* s_pix = nullptr;
+    int* s_bin = nullptr;
+    int grp = 0, gsize = 0, gtid = 0;
+    if constexpr (SORT) {
+        gsize = (int)blockDim.x / sort_groups((int)blockDim.x);
+        grp = (int)threadIdx.x / gsize;
+        gtid = (int)threadIdx.x - grp * gsize;
+        const int places = SORT_PER * gsize;
+        unsigned char* gbase = hbase + (TALLY == TALLY_SMEM ? hist_bytes(h.npix) : 0) +
+                               (size_t)grp * ((size_t)places * 12 + (size_t)2 * (SORT_BINS + 1) * 4);
+        s_q2 = reinterpret_cast<float*>(gbase);
+        s_pref = s_q2 + places;
+        s_pix = reinterpret_cast<int*>(s_pref + places);
+        s_bin = s_pix + places;
+        for (int i = gtid; i < 2 * (SORT_BINS + 1); i += gsize) s_bin[i] = 0;
     }
     __syncthreads();
 
@@ -181,6 +330,17 @@ __global__ void __launch_bounds__(1024) trace_kernel(const TraceParams<T> P)
     const int wpb = blockDim.x >> 5;
     const uint64_t stride = (uint64_t)gridDim.x * wpb * 32;
     Kahan<T> tr;
+    if constexpr (SORT) {
+        static_assert(sizeof(T) == sizeof(float), "the |Q|-ordered pass is FP32");
+        const uint64_t places = (uint64_t)SORT_PER * gsize;
+        const uint64_t ngroups = (uint64_t)gridDim.x * (blockDim.x / gsize);
+        int parity = 0;
+        for (uint64_t base = ((uint64_t)blockIdx.x * (blockDim.x / gsize) + grp) * places; base < P.n;
+             base += ngroups * places, parity ^= 1)
+            trace_sorted_pass<KIND, TALLY, AGG, ATT>(P, h, poly, s_q2, s_pix, s_pref,
+                                                     s_bin + parity * (SORT_BINS + 1), base, tr, gtid, gsize,
+                                                     1 + grp);
+    } else
     for (uint64_t base = ((uint64_t)blockIdx.x * wpb + (threadIdx.x >> 5)) * 32; base < P.n;
          base += stride) {
         const uint64_t j = base + lane;
@@ -204,16 +364,7 @@ __global__ void __launch_bounds__(1024) trace_kernel(const TraceParams<T> P)
 
     if (TALLY == TALLY_SMEM) {   // FP64 per-bin reduction of the CTA's histogram
         __syncthreads();
-        for (int p = threadIdx.x; p < h.npix; p += blockDim.x) {
-            const float2 kw = h.kw[p];
-            const float s2 = h.w2[p];
-            const uint32_t c = (h.cnt[p >> 1] >> ((p & 1) * 16)) & 0xFFFFu;
-            if (c != 0u || kw.x != 0.f || s2 != 0.f) {
-                atomicAdd(P.sum_w + p, (double)kw.x - (double)kw.y);
-                atomicAdd(P.sum_w2 + p, (double)s2);
-                if (c) atomicAdd(P.count + p, (unsigned long long)c);
-            }
-        }
+        h.flush(P.sum_w, P.sum_w2, P.count);
     }
 }
 
@@ -292,6 +443,7 @@ struct LaunchCfg {
     int tally;        // TALLY_GLOBAL / TALLY_SMEM
     int agg;          // warp aggregation
     int ctas_per_sm;  // 0: as many as fit
+    int order_q;      // order each CTA's histories by |Q| (sphere, core-shell; FP32)
 };
 
 template <typename T, int KIND>
@@ -315,6 +467,13 @@ static cudaError_t launch_trace_variant(const TraceParams<T>& P, const LaunchCfg
     auto kern = P.mc.att.n > 0 ? trace_kernel<T, KIND, TALLY, AGG, true> : trace_kernel<T, KIND, TALLY, AGG, false>;
     size_t smem = table_bytes<T>(P.mc.n_poly, P.mc.n_orient, P.stage_orient);
     if (TALLY == TALLY_SMEM) smem += hist_bytes(P.in.nx * P.in.ny);
+    if constexpr (sizeof(T) == sizeof(float) && (KIND == SAS_SPHERE || KIND == SAS_CORE_SHELL)) {
+        if (P.q2_bin > 0.f) {
+            kern = P.mc.att.n > 0 ? trace_kernel<T, KIND, TALLY, AGG, true, true>
+                                  : trace_kernel<T, KIND, TALLY, AGG, false, true>;
+            smem += sort_bytes(cfg.block);
+        }
+    }
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;

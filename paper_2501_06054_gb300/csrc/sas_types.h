@@ -45,9 +45,10 @@ struct AttPanel {
 // Model constants in the trace precision.
 //   poly table per node (SAS_POLY_STRIDE values); the sphere amplitude is
 //   evaluated as g = f / 3, so its factor 3 is folded in here:
-//     sphere     {r, 1/r, 9 w (drho V)^2, 0...}
-//     core-shell {r_c, 1/r_c, r_o, 1/r_o, c_1 = 3 sqrt(w) (rho_c - rho_s) V_c,
-//                 c_2 = 3 sqrt(w) (rho_s - rho_solv) V_o, c_1 / r_c^3, c_2 / r_o^3}
+//     sphere     {r, c / r^6, c = 9 w (drho V)^2, r^2, 1/r, 0...}  (ascending r)
+//     core-shell {r_c^2, r_o^2, c_1 = 3 sqrt(w) (rho_c - rho_s) V_c,
+//                 c_2 = 3 sqrt(w) (rho_s - rho_solv) V_o, c_1 / r_c^3, c_2 / r_o^3, r_c, r_o}
+//                (ascending r_c)
 //     cylinder   {r^2, w (drho V)^2, r, 1/r, 1/sqrt(r), 0...}  (ascending r)
 //     ellipsoid  {r_e^2, 9 w (drho V)^2, 0...}
 //     elliptical cylinder {s, w (drho V(s))^2, 0...}; hollow rectangular prism

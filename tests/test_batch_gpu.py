@@ -140,11 +140,12 @@ def test_single_experiment_autotune_and_cache():
     ex2.close()
 
 
-@pytest.mark.parametrize("tally,agg,block", [(0, 0, 256), (0, 1, 1024), (1, 1, 512), (1, 0, 256)])
-def test_launch_configs_agree(tally, agg, block):
+@pytest.mark.parametrize("tally,agg,block,order_q", [(0, 0, 256, 0), (0, 1, 1024, 0), (1, 1, 512, 0), (1, 0, 256, 0),
+                                                     (1, 0, 1024, 1), (1, 1, 512, 1), (0, 0, 256, 1)])
+def test_launch_configs_agree(tally, agg, block, order_q):
     cfg = W.core_shell_config()
     ex = sas.Experiment(cfg["instrument"], cfg["model"], stream=torch.cuda.current_stream())
-    c = sas.sas_launch_config(block=block, tally=tally, agg=agg, ctas_per_sm=0, stage_orient=0)
+    c = sas.sas_launch_config(block=block, tally=tally, agg=agg, ctas_per_sm=0, stage_orient=0, order_q=order_q)
     sas.sas_set_launch_config(ex.h, c)
     ex.trace(300007, seed=8)
     d = ex.read()
