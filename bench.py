@@ -719,6 +719,7 @@ def main():
 
     with torch.cuda.stream(stream):
         e = sas.Experiment(cfg["instrument"], cfg["model"], stream=stream)
+        lc = sas.sas_get_launch_config(e.h)
         l2_flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
         det = shard.detector_views(e.h, e.npix) if ws > 1 else None
 
@@ -824,12 +825,14 @@ def main():
                 # histories); the tables and the per-CTA flush do not grow with the
                 # history count, so a 1e9-history launch moves the same bytes
                 "traffic": None,
-                "kernel": "trace_kernel<float, CORE_SHELL, TALLY_SMEM>",
+                "kernel": "trace_kernel<float, CORE_SHELL, TALLY_SMEM%s>" % (", |Q|-ordered" if lc.order_q else ""),
+                "launch": {"block": lc.block, "tally": lc.tally, "agg": lc.agg, "order_q": lc.order_q},
                 "flops_per_history": fl,
                 "amplitudes_per_s": 2 * m.n_poly * n / (kms * 1e-3),
                 "peak_note": f"FP32 CUDA cores {info['sm_count']} SMs x 128 x 2 FLOP x 2070 MHz",
-                "flop_note": "fixed nominal table (sin and cos counted as their polynomial FLOPs); the kernel "
-                             "takes them from the SFU and is issue-bound (ncu: 88 % issue active)"}
+                "flop_note": "fixed nominal table (sin and cos counted as their polynomial FLOPs, every "
+                             "node in both branches' cost); the kernel takes sin and cos from the SFU and "
+                             "evaluates one branch per node, so this is an equivalent-work rate"}
     if clocks:
         roofline["frac_at_sampled_clock"] = achieved / F.fp32_peak_tflops(info["sm_count"], clocks["sm_mhz"])
     rec = recorded_counters()
@@ -842,6 +845,7 @@ def main():
             "flop_per_history": ex_fl, "achieved": ex_fl * n / (kms * 1e-3) / 1e12,
             "frac": ex_fl * n / (kms * 1e-3) / 1e12 / peak_max,
             "thread_instructions_per_history": rec["thread_inst"] / rec["histories"],
+            "issue_active_pct": rec.get("issue_active_pct"),
             "note": "ncu capture recorded in profiles/trace_core_shell_counters.txt (same kernel sources)"}
     value = n * ws / (ms * 1e-3)
     tables_bytes = (m.n_poly * 8 + 4) * 4
