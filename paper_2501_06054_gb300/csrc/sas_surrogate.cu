@@ -579,6 +579,8 @@ struct sas_surrogate {
     uint32_t g_total = 0;
     int* d_err = nullptr;
     cudaStream_t cap = nullptr;
+    cudaStream_t side = nullptr;        // the row sums, beside the weight gradients
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     uint64_t stall_ns = 0;   // test hook for the next sas_surrogate_eval
 };
 
@@ -723,9 +725,20 @@ sas_status enqueue_step(sas_surrogate* s, const sur::Raw* raw, const float* y, u
     W.kb_per = (W.kb_total + splits - 1) / splits;
     splits = (W.kb_total + W.kb_per - 1) / W.kb_per;
     W.err = s->d_err;
+    // The row sums (b2..b4, w5, b5) and the weight gradients (W1..W4) read
+    // the backward's outputs and write disjoint parts of the gradient: the
+    // row sums run on a side stream (a parallel branch of the captured
+    // graph), so their HBM reads overlap the weight-gradient GEMMs.
+    cudaError_t fe = cudaEventRecord(s->ev_fork, st);
+    if (fe == cudaSuccess) fe = cudaStreamWaitEvent(s->side, s->ev_fork, 0);
+    if (fe != cudaSuccess) return set_cuda_error(fe, "fork");
+    sur::rowsum_kernel<<<1025, 256, 0, s->side>>>(s->d_g, s->d_dzt[1], s->d_dzt[2], s->d_dzt[3], s->d_ht[3],
+                                                  s->d_dout, B);
+    fe = cudaEventRecord(s->ev_join, s->side);
+    if (fe != cudaSuccess) return set_cuda_error(fe, "join");
     sur::wgrad_kernel<<<dim3(splits, 1, 4), sur::WG_THREADS, sur::WG_SMEM, st>>>(W, s->wg);
-    sur::rowsum_kernel<<<1025, 256, 0, st>>>(s->d_g, s->d_dzt[1], s->d_dzt[2], s->d_dzt[3], s->d_ht[3],
-                                             s->d_dout, B);
+    fe = cudaStreamWaitEvent(st, s->ev_join, 0);
+    if (fe != cudaSuccess) return set_cuda_error(fe, "join");
     if (adam) {
         sur::AdamParams A;
         A.p = s->d_p;
@@ -927,6 +940,9 @@ sas_status sas_create_surrogate(const sas_surrogate_box* box, uint64_t seed, voi
     cudaError_t ce = cudaGetDevice(&dev);
     if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, dev);
     if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking);
+    if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming);
     const size_t pb = (size_t)NPARAM * sizeof(float);
     if (ce == cudaSuccess) ce = cudaMalloc(&s->d_p, pb);
     if (ce == cudaSuccess) ce = cudaMalloc(&s->d_g, pb);
@@ -1195,6 +1211,9 @@ sas_status sas_destroy_surrogate(sas_surrogate* s)
     cudaFree(s->d_raw);
     cudaFree(s->d_y);
     if (s->cap) cudaStreamDestroy(s->cap);
+    if (s->side) cudaStreamDestroy(s->side);
+    if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+    if (s->ev_join) cudaEventDestroy(s->ev_join);
     delete s;
     return SAS_OK;
 }
