@@ -74,7 +74,7 @@ enum { SAS_FN_GUINIER = 0, SAS_FN_GAUSS_COIL = 1, SAS_FN_LORENTZ = 2, SAS_FN_DAB
        SAS_FN_STAR_POLYMER = 12 };
 /* largest Gauss-Legendre rule over an end cap */
 #define SAS_MAX_CAP_NODES 64
-enum { SAS_SQ_NONE = 0, SAS_SQ_HARD_SPHERE_PY = 1 };
+enum { SAS_SQ_NONE = 0, SAS_SQ_HARD_SPHERE_PY = 1, SAS_SQ_HAYTER_MSA = 2 };
 enum { SAS_FP32 = 0, SAS_FP64 = 1 };
 /* sampling: average every history over the quadrature nodes, or draw one
  * polydisperse radius and one particle axis per history (the paper's
@@ -113,7 +113,7 @@ typedef struct sas_model_desc {
                                 SAS_CORE_SHELL_ELLIPSOID, SAS_CORE_SHELL_BICELLE,
                                 SAS_ELLIPTICAL_CYLINDER, SAS_HOLLOW_RECTANGULAR_PRISM,
                                 SAS_SHAPE_INDEPENDENT */
-    int64_t sq_kind;         /* SAS_SQ_NONE or SAS_SQ_HARD_SPHERE_PY */
+    int64_t sq_kind;         /* SAS_SQ_NONE, SAS_SQ_HARD_SPHERE_PY or SAS_SQ_HAYTER_MSA */
     int64_t precision;       /* SAS_FP32 (tallies FP32 Kahan + FP64 reduction) or SAS_FP64 */
     int64_t n_poly;          /* Schulz nodes of the polydisperse radius (1..64) */
     int64_t n_gamma;         /* orientation nodes in the polar angle about the axis (1..128) */
@@ -133,8 +133,8 @@ typedef struct sas_model_desc {
     double sigma_orient;     /* Gaussian width of the axis about its mean, rad */
     double axis_theta;       /* mean axis polar angle from +z, rad */
     double axis_phi;         /* mean axis azimuth, rad */
-    double sq_radius;        /* Percus-Yevick hard-sphere radius */
-    double sq_fraction;      /* Percus-Yevick volume fraction */
+    double sq_radius;        /* hard-sphere (effective) radius of S(Q), angstrom */
+    double sq_fraction;      /* volume fraction of S(Q) */
     int64_t sampling;        /* SAS_QUADRATURE or SAS_PER_EVENT. Per-event histories draw the
                                 radius from the Gaussian law (poly_dist must be SAS_POLY_GAUSSIAN
                                 unless poly = 0) by inversion of its distribution function, and
@@ -254,6 +254,32 @@ typedef struct sas_model_desc {
     int64_t function;
     double f_scale;          /* >= 0 */
     double f_p0, f_p1, f_p2;
+    /* Hayter-Penfold S(Q) of charged spheres (Table II, "Hayter MSA";
+     * sq_kind SAS_SQ_HAYTER_MSA): hard spheres of diameter sigma =
+     * 2 sq_radius at volume fraction eta = sq_fraction (0 < eta < 0.45),
+     * carrying sq_charge elementary charges, in a 1:1 electrolyte of
+     * sq_salt mol/L at sq_temperature K with relative permittivity
+     * sq_dielectric. Pair potential outside the core (screened Coulomb):
+     *   beta u(r) = gamma_c sigma exp(-kappa (r - sigma)) / r,
+     *   gamma_c = Z^2 l_B / ((1 + kappa sigma / 2)^2 sigma),
+     *   l_B = e^2 / (4 pi eps0 eps_r k_B T),
+     *   kappa^2 = 4 pi l_B (2 n_salt + |Z| n_particles)   (counter-ions monovalent).
+     * The mean spherical approximation closes the Ornstein-Zernike equation
+     * (g = 0 in the core, c = -beta u outside); where it gives g(sigma+) < 0
+     * the core is widened to s sigma (volume fraction eta s^3, same
+     * potential) until g(s sigma+) = 0 (Hansen-Hayter rescaling).
+     * sas_set_model solves this on the host (Newton's method on a grid,
+     * Richardson-extrapolated over two grid spacings, about 1e-8 from the
+     * continuum) and tabulates S and dS/dQ from Q = 0 past the instrument's
+     * largest |Q| and 1/angstrom; the trace interpolates (cubic Hermite,
+     * about 1e-7). Beyond the table S - 1 decays as Q^-2 from its last
+     * value. SAS_ERR_ARG for parameters out of range, a screening length
+     * beyond 500 sigma, or no convergence. Single experiments only (a
+     * batch refuses it). */
+    double sq_charge;        /* Z >= 0, elementary charges per particle */
+    double sq_temperature;   /* K > 0 */
+    double sq_salt;          /* mol/L >= 0 */
+    double sq_dielectric;    /* relative permittivity of the solvent > 0 */
 } sas_model_desc;
 
 typedef struct sas_experiment sas_experiment;   /* opaque, library-owned */
@@ -613,6 +639,22 @@ sas_status sas_cylinder_radial_table(const double *r, const double *w, int n_nod
  * c_xyz[3 * n_gamma * n_psi], w[n_gamma * n_psi]; *n_out = nodes written. */
 sas_status sas_orientation_nodes(double theta, double phi, double sigma, int n_gamma, int n_psi,
                                  int isotropic, double *c_xyz, double *w, int *n_out);
+
+/* The Hayter-Penfold S(Q) that sas_set_model tabulates (sq_kind
+ * SAS_SQ_HAYTER_MSA; parameters as in sas_model_desc), on HOST arrays:
+ * S(Q_j) and dS/dQ(Q_j) interleaved in s_dsdq[2 j], s_dsdq[2 j + 1] at
+ * Q_j = j * (*dq) (1/angstrom), j < *n_out, from 0 past q_max; *s_rescale
+ * the Hansen-Hayter factor (1 when the plain MSA has g(sigma+) >= 0),
+ * *contact the extrapolated g at the (rescaled) contact, *gamma_c the
+ * contact potential beta u(sigma+) and *kappa (1/angstrom) the inverse
+ * screening length of the unrescaled system. Any output may be NULL except
+ * s_dsdq when n_max > 0. SAS_ERR_ARG on parameters out of range or a solve
+ * that does not converge; SAS_ERR_ARG when the table needs more than n_max
+ * points (*n_out then holds the number needed). */
+sas_status sas_hayter_msa_table(double radius_eff, double fraction, double charge, double temperature,
+                                double salt, double dielectric, double q_max, int n_max, double *dq,
+                                double *s_dsdq, int *n_out, double *s_rescale, double *contact,
+                                double *gamma_c, double *kappa);
 
 /* Percus-Yevick constants (alpha, beta, gamma) and the first nser
  * coefficients of G(A)/A in powers of A^2. */

@@ -83,7 +83,8 @@ class _Model(ctypes.Structure):
                 ("radius_b", ctypes.c_double), ("axis_psi", ctypes.c_double),
                 ("self_att", ctypes.c_int64), ("n_cap", ctypes.c_int64), ("thickness_face", ctypes.c_double),
                 ("sld_face", ctypes.c_double), ("function", ctypes.c_int64)] + \
-               [(n, ctypes.c_double) for n in ("f_scale", "f_p0", "f_p1", "f_p2")]
+               [(n, ctypes.c_double) for n in ("f_scale", "f_p0", "f_p1", "f_p2")] + \
+               [("sq_tab", _DP), ("sq_n", ctypes.c_int64), ("sq_dq", ctypes.c_double)]
 
 
 def lib():
@@ -329,6 +330,19 @@ class Prepared:
         self.poly_w = np.ascontiguousarray(self.poly_w, dtype=np.float64)
         self.orient_c = np.ascontiguousarray(self.orient_c, dtype=np.float64)
         self.orient_w = np.ascontiguousarray(self.orient_w, dtype=np.float64)
+        # Hayter-Penfold S(Q): solved here (oracle/msa.py), tabulated at
+        # Q sigma' steps of 0.02 to 1 / angstrom for the C side
+        self.sq_tab = np.zeros(2)
+        sq_n, sq_dq = 0, 0.0
+        if int(m["sq_kind"]) == 2:
+            from . import msa
+            self.msa = msa.Solution(m["sq_radius"], m["sq_fraction"], m.get("sq_charge", 0.0),
+                                    m.get("sq_temperature", 298.15), m.get("sq_salt", 0.0),
+                                    m.get("sq_dielectric", 78.4))
+            sig = self.msa.sigma * self.msa.s
+            sq_n = int(math.ceil(1.0 * sig / 0.02)) + 3
+            sq_dq, S, D = self.msa.table(0.02 / sig * (sq_n - 1), sq_n)
+            self.sq_tab = np.ascontiguousarray(np.stack([S, D], axis=1).reshape(-1))
         self.c = _Model(kind=kind, sq_kind=int(m["sq_kind"]), n_poly=len(self.poly_r),
                         n_orient=len(self.orient_w), radius=m["radius"],
                         thickness=m["thickness"], length=m["length"],
@@ -347,7 +361,8 @@ class Prepared:
                         thickness_face=float(m.get("thickness_face", 0.0)),
                         sld_face=float(m.get("sld_face", 0.0)), function=int(m.get("function", 0)),
                         f_scale=float(m.get("f_scale", 0.0)), f_p0=float(m.get("f_p0", 0.0)),
-                        f_p1=float(m.get("f_p1", 0.0)), f_p2=float(m.get("f_p2", 0.0)))
+                        f_p1=float(m.get("f_p1", 0.0)), f_p2=float(m.get("f_p2", 0.0)),
+                        sq_tab=self.sq_tab.ctypes.data_as(_DP), sq_n=sq_n, sq_dq=sq_dq)
 
 
 def _inst(instrument):

@@ -87,7 +87,7 @@ typedef struct {
                               8 core-shell cylinder, 9 hollow cylinder, 10 core-shell ellipsoid,
                               11 core-shell bicelle, 12 elliptical cylinder,
                               13 hollow rectangular prism, 14 shape-independent */
-    int64_t sq_kind;       /* 0 none, 1 Percus-Yevick hard spheres */
+    int64_t sq_kind;       /* 0 none, 1 Percus-Yevick hard spheres, 2 Hayter-Penfold (table) */
     int64_t n_poly;        /* polydispersity nodes */
     int64_t n_orient;      /* orientation nodes */
     double radius, thickness, length, radius_polar;
@@ -128,6 +128,11 @@ typedef struct {
      * selected by `function` with parameters f_p0..f_p2 */
     int64_t function;
     double f_scale, f_p0, f_p1, f_p2;
+    /* Hayter-Penfold S(Q) (sq_kind 2), solved in oracle/msa.py: S_j and
+     * dS/dQ_j interleaved at Q_j = j sq_dq, j < sq_n */
+    const double *sq_tab;
+    int64_t sq_n;
+    double sq_dq;
 } oracle_model;
 
 /* --------------------------------------------------------- model pieces */
@@ -192,6 +197,27 @@ static double b3_c(int k)
  * G(A) = alpha b1/A^2 + beta b2/A^3 + gamma b3/A^5,
  * alpha = (1+2phi)^2/(1-phi)^4, beta = -6 phi (1+phi/2)^2/(1-phi)^4,
  * gamma = phi alpha / 2.                                                    */
+double oracle_sq_py(double q, double radius, double phi);
+
+/* S(Q) from the table of a solved Hayter-Penfold model: cubic Hermite
+ * interpolation of S and dS/dQ; beyond the table S - 1 decays as Q^-2. */
+static double oracle_sq_table(const oracle_model *m, double q)
+{
+    double s = q / m->sq_dq;
+    int64_t last = m->sq_n - 1;
+    if (s >= (double)last) {
+        double r = (double)last / s;
+        return 1.0 + (m->sq_tab[2 * last] - 1.0) * r * r;
+    }
+    int64_t i = (int64_t)s;
+    double f = s - (double)i, h = m->sq_dq;
+    double s0 = m->sq_tab[2 * i], d0 = m->sq_tab[2 * i + 1] * h;
+    double s1 = m->sq_tab[2 * i + 2], d1 = m->sq_tab[2 * i + 3] * h;
+    double h00 = (1.0 + 2.0 * f) * (1.0 - f) * (1.0 - f), h10 = f * (1.0 - f) * (1.0 - f);
+    double h01 = f * f * (3.0 - 2.0 * f), h11 = f * f * (f - 1.0);
+    return h00 * s0 + h10 * d0 + h01 * s1 + h11 * d1;
+}
+
 double oracle_sq_py(double q, double radius, double phi)
 {
     double A = 2.0 * fabs(q) * radius;
@@ -586,6 +612,7 @@ double oracle_dsigma(const oracle_model *m, const double q[3])
     }
     double S = 1.0;
     if (m->sq_kind == 1) S = oracle_sq_py(qq, m->sq_radius, m->sq_fraction);
+    else if (m->sq_kind == 2) S = oracle_sq_table(m, qq);
     return m->volume_fraction / vmean * sum * S;
 }
 

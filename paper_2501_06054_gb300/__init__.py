@@ -50,7 +50,8 @@ class sas_model_desc(ctypes.Structure):
                 ("self_attenuation", ctypes.c_int64), ("n_cap", ctypes.c_int64),
                 ("thickness_face", ctypes.c_double), ("sld_face", ctypes.c_double),
                 ("function", ctypes.c_int64)] + \
-               [(n, ctypes.c_double) for n in ("f_scale", "f_p0", "f_p1", "f_p2")]
+               [(n, ctypes.c_double) for n in ("f_scale", "f_p0", "f_p1", "f_p2", "sq_charge",
+                                               "sq_temperature", "sq_salt", "sq_dielectric")]
 
 
 class sas_launch_config(ctypes.Structure):
@@ -102,6 +103,8 @@ _SIGS = {
     "sas_py_series": [ctypes.c_double, _dp, _dp, ctypes.c_int],
     "sas_cylinder_radial_table": [_dp, _dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                   _dp, _dp, _dp],
+    "sas_hayter_msa_table": [ctypes.c_double] * 7 + [ctypes.c_int, _dp, _dp, ctypes.POINTER(ctypes.c_int),
+                                                      _dp, _dp, _dp, _dp],
     "sas_get_launch_config": [_vp, ctypes.POINTER(sas_launch_config)],
     "sas_set_launch_config": [_vp, ctypes.POINTER(sas_launch_config)],
     "sas_autotune": [_vp, _u64, _u64, ctypes.POINTER(sas_launch_config), _dp],
@@ -312,6 +315,22 @@ def sas_cylinder_radial_table(r, w, rbar, xmax, n_points):
                                            float(xmax), int(n_points), G.ctypes.data_as(_dp),
                                            D.ctypes.data_as(_dp), err.ctypes.data_as(_dp)))
     return G, D, float(err[0])
+
+
+def sas_hayter_msa_table(radius_eff, fraction, charge, temperature, salt, dielectric, q_max, n_max=65536):
+    """The library's Hayter-Penfold S(Q) table on the host: dict with dq,
+    S, dS_dQ (arrays), s_rescale, contact, gamma_c, kappa."""
+    sd = np.empty(2 * n_max)
+    dq, sr, ct, gc, ka = (np.zeros(1) for _ in range(5))
+    n = ctypes.c_int(0)
+    _check(lib().sas_hayter_msa_table(float(radius_eff), float(fraction), float(charge), float(temperature),
+                                      float(salt), float(dielectric), float(q_max), int(n_max),
+                                      dq.ctypes.data_as(_dp), sd.ctypes.data_as(_dp), ctypes.byref(n),
+                                      sr.ctypes.data_as(_dp), ct.ctypes.data_as(_dp), gc.ctypes.data_as(_dp),
+                                      ka.ctypes.data_as(_dp)))
+    k = n.value
+    return dict(dq=float(dq[0]), S=sd[0:2 * k:2].copy(), dS_dQ=sd[1:2 * k:2].copy(), s_rescale=float(sr[0]),
+                contact=float(ct[0]), gamma_c=float(gc[0]), kappa=float(ka[0]))
 
 
 def sas_schulz_nodes(mean, p, n):

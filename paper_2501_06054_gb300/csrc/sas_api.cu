@@ -13,6 +13,7 @@
 
 #include "sas_kernels.cuh"
 #include "sas_host.h"
+#include "sas_msa.h"
 #include "sas_sur_host.h"
 
 namespace {
@@ -758,6 +759,21 @@ sas_status build_model_tables(const sas_model_desc& m, ModelTables& t, double q_
         py_constants(m.sq_fraction, &t.sq_alpha, &t.sq_beta, &t.sq_gamma, t.sq_series.data(), SAS_SQ_NSER);
     else
         t.sq_alpha = t.sq_beta = t.sq_gamma = 0.0;
+    if (m.sq_kind == SAS_SQ_HAYTER_MSA) {
+        const msa::Reduced r = msa::reduce(m.sq_radius, m.sq_fraction, m.sq_charge, m.sq_temperature, m.sq_salt,
+                                           m.sq_dielectric);
+        msa::Table tab;
+        std::string err;
+        // past 1/angstrom where the grid allows, else past the instrument's largest |Q|
+        if (!msa::build_table(r, std::max(1.0, 1.05 * q_max), tab, err) &&
+            !msa::build_table(r, 1.05 * q_max, tab, err))
+            return fail(SAS_ERR_ARG, err.c_str());
+        t.sq_dq = tab.dq;
+        t.sq_rescale = tab.s_rescale;
+        t.sq_contact = tab.contact;
+        t.sq_tab = tab.sd;
+        for (size_t j = 1; j < t.sq_tab.size(); j += 2) t.sq_tab[j] *= tab.dq;   // h dS/dQ
+    }
     return SAS_OK;
 }
 
@@ -781,6 +797,9 @@ ModelConst<T> model_const(const sas_model_desc& m, const ModelTables& t)
     c.sq_gamma = (T)t.sq_gamma;
     c.sq_switch = (T)t.sq_switch;
     for (int k = 0; k < SAS_SQ_NSER; ++k) c.sq_series[k] = (T)t.sq_series[k];
+    c.sq_tab = nullptr;   // set once the table is on the device
+    c.sq_n = (int)(t.sq_tab.size() / 2);
+    c.sq_inv_dq = (T)(t.sq_dq > 0.0 ? 1.0 / t.sq_dq : 0.0);
     c.event = m.sampling == SAS_PER_EVENT ? 1 : 0;
     c.orient_mode = (m.kind == SAS_CYLINDER || m.kind == SAS_ELLIPSOID || m.kind == SAS_CAPPED_CYLINDER ||
                      m.kind == SAS_BARBELL || shelled_cylinder(m.kind) || m.kind == SAS_CORE_SHELL_ELLIPSOID)
@@ -994,7 +1013,15 @@ sas_status validate_model(const sas_model_desc* m)
     if (axes3 && (m->n_rot < 1 || m->n_rot > SAS_MAX_ORIENT_SIDE)) return fail(SAS_ERR_ARG, "n_rot must be in [1, 128]");
     if (axes3 && m->isotropic != 0 && m->n_gamma * m->n_psi * m->n_rot > (1 << 17))
         return fail(SAS_ERR_ARG, "n_gamma * n_psi * n_rot must be <= 131072");
-    if (m->sq_kind != SAS_SQ_NONE && m->sq_kind != SAS_SQ_HARD_SPHERE_PY) return fail(SAS_ERR_ARG, "unknown S(Q) kind");
+    if (m->sq_kind != SAS_SQ_NONE && m->sq_kind != SAS_SQ_HARD_SPHERE_PY && m->sq_kind != SAS_SQ_HAYTER_MSA)
+        return fail(SAS_ERR_ARG, "unknown S(Q) kind");
+    if (m->sq_kind == SAS_SQ_HAYTER_MSA &&
+        (!(m->sq_radius > 0.0) || !(m->sq_fraction > 0.0 && m->sq_fraction < 0.45) || !(m->sq_charge >= 0.0) ||
+         !(m->sq_temperature > 0.0) || !(m->sq_salt >= 0.0) || !(m->sq_dielectric > 0.0) ||
+         !std::isfinite(m->sq_charge) || !std::isfinite(m->sq_salt) || !std::isfinite(m->sq_temperature) ||
+         !std::isfinite(m->sq_dielectric)))
+        return fail(SAS_ERR_ARG, "Hayter MSA needs sq_radius > 0, 0 < sq_fraction < 0.45, sq_charge >= 0, "
+                                 "sq_temperature > 0, sq_salt >= 0 and sq_dielectric > 0");
     if (m->precision != SAS_FP32 && m->precision != SAS_FP64) return fail(SAS_ERR_ARG, "unknown precision");
     if (m->n_poly < 1 || m->n_poly > SAS_MAX_POLY) return fail(SAS_ERR_ARG, "n_poly must be in [1, 64]");
     if (m->n_gamma < 1 || m->n_gamma > SAS_MAX_ORIENT_SIDE || m->n_psi < 1 || m->n_psi > SAS_MAX_ORIENT_SIDE)
@@ -1053,6 +1080,7 @@ struct sas_experiment {
     ModelTables tables;
     void* d_poly = nullptr;
     void* d_orient = nullptr;
+    void* d_sqtab = nullptr;   // Hayter-Penfold S(Q) table (model precision)
     ModelConst<float> mcf;
     ModelConst<double> mcd;
     InstConst<float> icf;
@@ -1559,8 +1587,15 @@ sas_status sas_set_model(sas_experiment* e, const sas_model_desc* m)
     SAS_CUDA(cudaStreamSynchronize(e->stream), "cudaStreamSynchronize");
     cudaFree(e->d_poly);
     cudaFree(e->d_orient);
-    e->d_poly = e->d_orient = nullptr;
+    cudaFree(e->d_sqtab);
+    e->d_poly = e->d_orient = e->d_sqtab = nullptr;
     e->has_model = false;
+    std::vector<float> sqf(t.sq_tab.begin(), t.sq_tab.end());
+    if (!t.sq_tab.empty()) {
+        SAS_CUDA(cudaMalloc(&e->d_sqtab, t.sq_tab.size() * es), "cudaMalloc(S table)");
+        SAS_CUDA(cudaMemcpyAsync(e->d_sqtab, fp32 ? (const void*)sqf.data() : (const void*)t.sq_tab.data(),
+                                 t.sq_tab.size() * es, cudaMemcpyHostToDevice, e->stream), "upload S table");
+    }
     SAS_CUDA(cudaMalloc(&e->d_poly, t.poly.size() * es), "cudaMalloc(poly)");
     SAS_CUDA(cudaMalloc(&e->d_orient, t.orient.size() * es), "cudaMalloc(orient)");
     SAS_CUDA(cudaMemcpyAsync(e->d_poly, hp, t.poly.size() * es, cudaMemcpyHostToDevice, e->stream), "upload poly");
@@ -1581,9 +1616,34 @@ sas_status sas_set_model(sas_experiment* e, const sas_model_desc* m)
     }
     e->mcf = model_const<float>(*m, e->tables);
     e->mcd = model_const<double>(*m, e->tables);
+    e->mcf.sq_tab = fp32 ? (const float*)e->d_sqtab : nullptr;
+    e->mcd.sq_tab = fp32 ? nullptr : (const double*)e->d_sqtab;
     e->has_model = true;
     if (!lookup_tuned(e)) choose_config(e);
     return upload_surrogate_exp(e);
+}
+
+sas_status sas_hayter_msa_table(double radius_eff, double fraction, double charge, double temperature, double salt,
+                                double dielectric, double q_max, int n_max, double* dq, double* s_dsdq, int* n_out,
+                                double* s_rescale, double* contact, double* gamma_c, double* kappa)
+{
+    if (!(radius_eff > 0.0) || !(fraction > 0.0 && fraction < 0.45) || !(charge >= 0.0) || !(temperature > 0.0) ||
+        !(salt >= 0.0) || !(dielectric > 0.0) || !(q_max > 0.0) || n_max < 0 || (n_max > 0 && !s_dsdq))
+        return fail(SAS_ERR_ARG, "Hayter MSA table: parameters out of range");
+    const msa::Reduced r = msa::reduce(radius_eff, fraction, charge, temperature, salt, dielectric);
+    if (gamma_c) *gamma_c = r.gamma_c;
+    if (kappa) *kappa = r.kappa;
+    msa::Table tab;
+    std::string err;
+    if (!msa::build_table(r, q_max, tab, err)) return fail(SAS_ERR_ARG, err);
+    const int n = (int)(tab.sd.size() / 2);
+    if (n_out) *n_out = n;
+    if (dq) *dq = tab.dq;
+    if (s_rescale) *s_rescale = tab.s_rescale;
+    if (contact) *contact = tab.contact;
+    if (n > n_max) return fail(SAS_ERR_ARG, "Hayter MSA table: n_max too small");
+    std::copy(tab.sd.begin(), tab.sd.end(), s_dsdq);
+    return SAS_OK;
 }
 
 sas_status sas_set_experiment_id(sas_experiment* e, uint32_t id)
@@ -1764,6 +1824,7 @@ sas_status sas_destroy_experiment(sas_experiment* e)
     cudaFree(e->d_trans);
     cudaFree(e->d_poly);
     cudaFree(e->d_orient);
+    cudaFree(e->d_sqtab);
     cudaFree(e->d_items);
     cudaFree(e->d_prefix);
     cudaFree(e->d_seed);

@@ -305,6 +305,8 @@ sas_status sas_create_batch(const sas_instrument* inst, const sas_model_desc* mo
         if (m.precision != SAS_FP32) return bail(set_error(SAS_ERR_ARG, "batched experiments are FP32"));
         if (m.kind == SAS_SHAPE_INDEPENDENT)
             return bail(set_error(SAS_ERR_ARG, "shape-independent laws are traced one by one (sas_trace), not batched"));
+        if (m.sq_kind == SAS_SQ_HAYTER_MSA)
+            return bail(set_error(SAS_ERR_ARG, "the Hayter MSA S(Q) is traced one by one (sas_trace), not batched"));
         ModelTables t;
         st = build_model_tables(m, t, instrument_q_max(*inst));
         if (st != SAS_OK) return bail(st);

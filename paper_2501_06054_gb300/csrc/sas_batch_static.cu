@@ -93,6 +93,8 @@ sas_status sas_trace_batch_static(const sas_instrument* inst, const sas_model_de
         if (m.precision != SAS_FP32) return set_error(SAS_ERR_ARG, "batched experiments are FP32");
         if (m.kind == SAS_SHAPE_INDEPENDENT)
             return set_error(SAS_ERR_ARG, "shape-independent laws are traced one by one (sas_trace), not batched");
+        if (m.sq_kind == SAS_SQ_HAYTER_MSA)
+            return set_error(SAS_ERR_ARG, "the Hayter MSA S(Q) is traced one by one (sas_trace), not batched");
         if (m.self_attenuation)
             return set_error(SAS_ERR_ARG, "the allocation-free batch does not build self-attenuation tables; "
                                           "use sas_create_batch");

@@ -160,6 +160,20 @@ template <> struct M<double> {
 template <typename T>
 __device__ __forceinline__ T structure_factor(T q, const ModelConst<T>& mc)
 {
+    if (mc.sq_kind == SAS_SQ_HAYTER_MSA) {
+        // cubic Hermite on the host-solved table; beyond it S - 1 decays as Q^-2
+        const T s = q * mc.sq_inv_dq;
+        const int last = mc.sq_n - 1;
+        if (!(s < (T)last)) {
+            const T r = (T)last / s;
+            return (T)1 + (mc.sq_tab[2 * last] - (T)1) * r * r;
+        }
+        const int i = (int)s;
+        const T f = s - (T)i, f1 = (T)1 - f;
+        const T* p = mc.sq_tab + 2 * i;
+        // h00 = (1 + 2f)(1 - f)^2, h10 = f (1 - f)^2, h01 = f^2 (3 - 2f), h11 = f^2 (f - 1)
+        return f1 * f1 * fma((T)2 * f + (T)1, p[0], f * p[1]) + f * f * fma((T)3 - (T)2 * f, p[2], -f1 * p[3]);
+    }
     if (mc.sq_kind != SAS_SQ_HARD_SPHERE_PY) return (T)1;
     const T A = q * mc.sq_2r;
     T ga;

@@ -15,6 +15,9 @@ struct ModelTables {
     int sq_kind = 0;
     double sq_2r = 0, sq_24phi = 0, sq_alpha = 0, sq_beta = 0, sq_gamma = 0, sq_switch = 0;
     std::vector<double> sq_series;
+    // Hayter-Penfold S(Q): {S_j, dq dS/dQ_j} at Q_j = j sq_dq
+    std::vector<double> sq_tab;
+    double sq_dq = 0, sq_rescale = 1, sq_contact = 0;
     // cylinder radial table (radial_table = 1): G(x) and h G'(x) on a grid,
     // stored behind the radius nodes in `poly`
     int n_rad = 0;                // radius nodes (n_poly counts the table rows too)

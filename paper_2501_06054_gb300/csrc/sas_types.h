@@ -74,6 +74,9 @@ struct ModelConst {
     T sq_alpha, sq_beta, sq_gamma;
     T sq_switch;     // A below which the series is used
     T sq_series[SAS_SQ_NSER];
+    const T* sq_tab;  // Hayter-Penfold S(Q): {S_j, dq dS/dQ_j} at Q_j = j dq (device, global memory)
+    int sq_n;
+    T sq_inv_dq;
     // per-event sampling (Sec. II.B): one radius and one axis per history
     int event;       // 0: quadrature average over the tables, 1: per-event draws
     int orient_mode; // axis draw: 0 fixed (ev_axis), 1 uniform on the sphere, 2 uniform angles

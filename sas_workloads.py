@@ -49,7 +49,7 @@ MODEL_NAMES = {SPHERE: "sphere", CORE_SHELL: "core_shell", CYLINDER: "cylinder",
                HOLLOW_CYLINDER: "hollow_cylinder", CORE_SHELL_ELLIPSOID: "core_shell_ellipsoid",
                CORE_SHELL_BICELLE: "core_shell_bicelle", ELLIPTICAL_CYLINDER: "elliptical_cylinder",
                HOLLOW_RECTANGULAR_PRISM: "hollow_rectangular_prism", SHAPE_INDEPENDENT: "shape_independent"}
-SQ_NONE, SQ_HARD_SPHERE_PY = 0, 1
+SQ_NONE, SQ_HARD_SPHERE_PY, SQ_HAYTER_MSA = 0, 1, 2
 FP32, FP64 = 0, 1
 QUADRATURE, PER_EVENT = 0, 1              # sampling: averages over nodes / one draw per history
 SCHULZ, GAUSSIAN = 0, 1                   # poly_dist of the polydisperse radius
@@ -119,6 +119,10 @@ class Model:
     f_p0: float = 0.0               # shape-independent parameters (Rg, xi, m, Q0 / sigma, a2 / c1 / c2)
     f_p1: float = 0.0
     f_p2: float = 0.0
+    sq_charge: float = 0.0          # Hayter-Penfold S(Q): particle charge Z (elementary charges)
+    sq_temperature: float = 298.15  # K
+    sq_salt: float = 0.0            # mol/L of 1:1 salt
+    sq_dielectric: float = 78.4     # relative permittivity of the solvent
 
     def as_dict(self):
         return asdict(self)

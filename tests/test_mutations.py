@@ -17,6 +17,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 C = "oracle/sas_oracle.c"
 PY = "oracle/__init__.py"
+MSA = "oracle/msa.py"
 
 # k: (mistake, -k selector, pin file, patched file, [(clean text, mistaken text), ...])
 MUTATIONS = {
@@ -101,6 +102,13 @@ MUTATIONS = {
     31: ("Guinier-Porod join without the Guinier factor", "guinier_porod", "test_shape_independent_oracle.py", C,
          [("else f = pow(q1, mp - sd) * exp(-(mp - sd) / 2.0) * pow(q, -mp);",
            "else f = pow(q1, mp - sd) * pow(q, -mp);")]),
+    32: ("screened Coulomb potential with the wrong sign", "low_density", "test_msa_oracle.py", MSA,
+         [("tail[1:] = -gamma_c * np.exp(-k * (x[1:] - 1.0)) / x[1:]",
+           "tail[1:] = gamma_c * np.exp(-k * (x[1:] - 1.0)) / x[1:]")]),
+    33: ("Bjerrum length without the relative permittivity", "textbook", "test_msa_oracle.py", MSA,
+         [("/ (4.0 * math.pi * EPS0 * dielectric * K_B * temperature)", "/ (4.0 * math.pi * EPS0 * K_B * temperature)")]),
+    34: ("MSA closure with h = 0 in the core instead of -1", "percus", "test_msa_oracle.py", MSA,
+         [("    inner = -1.0\n", "    inner = 0.0\n")]),
 }
 
 
