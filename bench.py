@@ -426,7 +426,38 @@ def secondary(stream, info):
     out["per_event"] = per_event(stream)
     out["self_attenuation"] = self_attenuation(stream)
     out["n4_models"] = n4_models(stream)
+    out["hayter_msa"] = hayter_msa(stream)
     return out
+
+
+def hayter_msa(stream):
+    """The core-shell workload with the Hayter-Penfold S(Q) of charged
+    spheres in place of the hard-sphere one: the host solve inside
+    sas_set_model (wall clock) and the trace rate (CUDA events)."""
+    import time
+    import torch
+    import paper_2501_06054_gb300 as sas
+    cfg = W.core_shell_config()
+    res = {}
+    for name, extra in (("plain_msa", dict(sq_charge=15.0, sq_salt=0.05)),
+                        ("rescaled", dict(sq_charge=40.0, sq_salt=0.002, sq_fraction=0.05))):
+        m = W.Model(**dict(cfg["model"].as_dict(), sq_kind=W.SQ_HAYTER_MSA, **extra))
+        t0 = time.perf_counter()
+        e = sas.Experiment(cfg["instrument"], m, stream=stream)
+        set_s = time.perf_counter() - t0
+        n = 200_000_000
+        e.trace(n, 1)
+        ms = _events_ms(lambda: e.trace(n, 1), stream)
+        info = sas.sas_hayter_msa_table(m.sq_radius, m.sq_fraction, m.sq_charge, m.sq_temperature, m.sq_salt,
+                                        m.sq_dielectric, 0.2)
+        res[name] = {"workload": "core-shell workload, S(Q) Hayter-Penfold: Z=%g, %g M salt, eta=%g, sigma=%g A"
+                                 % (m.sq_charge, m.sq_salt, m.sq_fraction, 2 * m.sq_radius),
+                     "set_model_s": set_s, "value": n / (ms * 1e-3), "unit": UNIT, "histories_timed": n,
+                     "s_rescale": info["s_rescale"], "gamma_c": info["gamma_c"],
+                     "kappa_sigma": info["kappa"] * 2 * m.sq_radius, "S_min": float(info["S"].min()),
+                     "S_max": float(info["S"].max())}
+        e.close()
+    return res
 
 
 CAPPED_DESC = {"capped_cylinder": "r=20, caps R=25, L=200 A, Schulz 0.1 (10 nodes), Gaussian axis spread 15 deg "
