@@ -299,110 +299,164 @@ __device__ __forceinline__ NodeSplit node_split(const float* __restrict__ poly, 
     return NodeSplit{nA, np - nC};
 }
 
-__device__ __forceinline__ float avg_core_shell_split(float q, float q2, float iq, const float* __restrict__ poly,
-                                                      int np, float shell, NodeSplit sp)
+// The runs for NV histories per lane at once (NV independent chains per
+// node, one shared-memory load of the node for all of them); q, q2 = q^2,
+// iq = 1/q per history, out[v] = <|F|^2> of history v.
+template <int NV>
+__device__ __forceinline__ void avg_core_shell_split(const float (&q)[NV], const float (&q2)[NV], const float (&iq)[NV],
+                                                     const float* __restrict__ poly, int np, float shell, NodeSplit sp,
+                                                     float (&out)[NV])
 {
     const float gs[5] = {3.333333333e-01f, -3.333333333e-02f, 1.190476190e-03f, -2.204585538e-05f,
                          2.505210839e-07f};
-    float acc = 0.f;
-#pragma unroll 4
+    float acc[NV], accC[NV], iq3[NV], St[NV], Ct[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        acc[v] = 0.f;
+        accC[v] = 0.f;
+        iq3[v] = iq[v] * iq[v] * iq[v];
+    }
+#pragma unroll 2
     for (int i = 0; i < sp.iA; ++i) {   // series for both radii, in x^2 = q^2 r^2
         const float4 pa = *reinterpret_cast<const float4*>(poly + 8 * i);   // r_c^2, r_o^2, c_1, c_2
-        const float F = fmaf(pa.z, sas_horner(gs, q2 * pa.x), pa.w * sas_horner(gs, q2 * pa.y));
-        acc = fmaf(F, F, acc);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const float F = fmaf(pa.z, sas_horner(gs, q2[v] * pa.x), pa.w * sas_horner(gs, q2[v] * pa.y));
+            acc[v] = fmaf(F, F, acc[v]);
+        }
     }
-    const float iq3 = iq * iq * iq;
     for (int i = sp.iA; i < sp.iC; ++i) {   // per-lane selection
         const float4 pa = *reinterpret_cast<const float4*>(poly + 8 * i);       // r_c^2, r_o^2, c_1, c_2
         const float4 pb = *reinterpret_cast<const float4*>(poly + 8 * i + 4);   // c_1/r_c^3, c_2/r_o^3, r_c, r_o
-        const float x1 = q * pb.z, x2 = q * pb.w;
-        float s1, c1, s2, c2;
-        __sincosf(x1, &s1, &c1);
-        __sincosf(x2, &s2, &c2);
-        const bool s1b = x1 < 1.5f, s2b = x2 < 1.5f;
-        const float k1 = s1b ? pa.z : iq3 * pb.x, v1 = s1b ? sas_horner(gs, x1 * x1) : fmaf(-x1, c1, s1);
-        const float k2 = s2b ? pa.w : iq3 * pb.y, v2 = s2b ? sas_horner(gs, x2 * x2) : fmaf(-x2, c2, s2);
-        const float F = fmaf(k1, v1, k2 * v2);
-        acc = fmaf(F, F, acc);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const float x1 = q[v] * pb.z, x2 = q[v] * pb.w;
+            float s1, c1, s2, c2;
+            __sincosf(x1, &s1, &c1);
+            __sincosf(x2, &s2, &c2);
+            const bool s1b = x1 < 1.5f, s2b = x2 < 1.5f;
+            const float k1 = s1b ? pa.z : iq3[v] * pb.x, v1 = s1b ? sas_horner(gs, x1 * x1) : fmaf(-x1, c1, s1);
+            const float k2 = s2b ? pa.w : iq3[v] * pb.y, v2 = s2b ? sas_horner(gs, x2 * x2) : fmaf(-x2, c2, s2);
+            const float F = fmaf(k1, v1, k2 * v2);
+            acc[v] = fmaf(F, F, acc[v]);
+        }
     }
     // Closed form for both radii. The outer radius is r_c + t at every node,
     // so sin and cos of x2 follow from those of x1 and of q t (accurate,
-    // once per call) by the angle-addition identities: two special-function
+    // once per history) by the angle-addition identities: two special-function
     // operations per node instead of four and one shared load, which keeps
     // this run below the MIO queue's limit. With S = sin qt, C = cos qt,
     //   sin x2 - x2 cos x2 = s1 (C + x2 S) + c1 (S - x2 C),
     // so the node's amplitude k1 (s1 - x1 c1) + k2 (sin x2 - x2 cos x2) is
     //   s1 (k1 + k2 (C + x2 S)) + c1 (k2 (S - x2 C) - k1 x1).
-    float St, Ct;
-    sincospif(q * shell * 0.318309886f, &St, &Ct);
-    float accC = 0.f;
-#pragma unroll 4
+#pragma unroll
+    for (int v = 0; v < NV; ++v) sincospif(q[v] * shell * 0.318309886f, &St[v], &Ct[v]);
+#pragma unroll 2
     for (int i = sp.iC; i < np; ++i) {
         const float4 pb = *reinterpret_cast<const float4*>(poly + 8 * i + 4);   // k_1, k_2, r_c, r_o
-        const float x1 = q * pb.z, x2 = q * pb.w;
-        float s1, c1;
-        __sincosf(x1, &s1, &c1);
-        const float gam = fmaf(pb.y, fmaf(x2, St, Ct), pb.x);
-        const float del = fmaf(pb.y, fmaf(-x2, Ct, St), -pb.x * x1);
-        const float F = fmaf(s1, gam, c1 * del);
-        accC = fmaf(F, F, accC);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const float x1 = q[v] * pb.z, x2 = q[v] * pb.w;
+            float s1, c1;
+            __sincosf(x1, &s1, &c1);
+            const float gam = fmaf(pb.y, fmaf(x2, St[v], Ct[v]), pb.x);
+            const float del = fmaf(pb.y, fmaf(-x2, Ct[v], St[v]), -pb.x * x1);
+            const float F = fmaf(s1, gam, c1 * del);
+            accC[v] = fmaf(F, F, accC[v]);
+        }
     }
-    return sp.iC < np ? fmaf(iq3 * iq3, accC, acc) : acc;   // iq3^2 may overflow below q = 4e-7
+#pragma unroll
+    for (int v = 0; v < NV; ++v)   // iq3^2 may overflow below q = 4e-7: only with a closed-form run
+        out[v] = sp.iC < np ? fmaf(iq3[v] * iq3[v], accC[v], acc[v]) : acc[v];
 }
 
-__device__ __forceinline__ float avg_sphere_split(float q, float q2, float iq, const float* __restrict__ poly,
-                                                  int np, NodeSplit sp)
+template <int NV>
+__device__ __forceinline__ void avg_sphere_split(const float (&q)[NV], const float (&q2)[NV], const float (&iq)[NV],
+                                                 const float* __restrict__ poly, int np, NodeSplit sp,
+                                                 float (&out)[NV])
 {
     const float gs[5] = {3.333333333e-01f, -3.333333333e-02f, 1.190476190e-03f, -2.204585538e-05f,
                          2.505210839e-07f};
-    float acc = 0.f;
-#pragma unroll 4
+    float acc[NV], accC[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] = accC[v] = 0.f;
+#pragma unroll 2
     for (int i = 0; i < sp.iA; ++i) {
         const float2 p = *reinterpret_cast<const float2*>(poly + 8 * i + 2);   // c, r^2
-        const float g = sas_horner(gs, q2 * p.y);
-        acc = fmaf(p.x, g * g, acc);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const float g = sas_horner(gs, q2[v] * p.y);
+            acc[v] = fmaf(p.x, g * g, acc[v]);
+        }
     }
     for (int i = sp.iA; i < sp.iC; ++i) {
         const float* p = poly + 8 * i;
-        const float g = M<float>::sphere_g(q * p[0], iq * p[4]);
-        acc = fmaf(p[2], g * g, acc);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const float g = M<float>::sphere_g(q[v] * p[0], iq[v] * p[4]);
+            acc[v] = fmaf(p[2], g * g, acc[v]);
+        }
     }
-    float accC = 0.f;
-#pragma unroll 4
+#pragma unroll 2
     for (int i = sp.iC; i < np; ++i) {
         const float2 p = *reinterpret_cast<const float2*>(poly + 8 * i);   // r, c / r^6
-        const float x = q * p.x;
-        float s, c;
-        __sincosf(x, &s, &c);
-        const float A = fmaf(-x, c, s);
-        accC = fmaf(p.y, A * A, accC);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const float x = q[v] * p.x;
+            float s, c;
+            __sincosf(x, &s, &c);
+            const float A = fmaf(-x, c, s);
+            accC[v] = fmaf(p.y, A * A, accC[v]);
+        }
     }
-    const float iq3 = iq * iq * iq;
-    return sp.iC < np ? fmaf(iq3 * iq3, accC, acc) : acc;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        const float iq3 = iq[v] * iq[v] * iq[v];
+        out[v] = sp.iC < np ? fmaf(iq3 * iq3, accC[v], acc[v]) : acc[v];
+    }
 }
 
-// dSigma/dOmega at |Q|^2 = q2 for a lane of a |Q|-ordered warp (sphere and
-// core-shell sphere, quadrature averages); inactive lanes (q2 < 0) return 0.
-// Every lane of the warp calls it.
-template <int KIND>
-__device__ __forceinline__ float dsigma_sorted(float q2, const ModelConst<float>& mc, const float* __restrict__ poly)
+// dSigma/dOmega at |Q|^2 = q2[v] for the NV histories of a lane of a
+// |Q|-ordered warp (sphere and core-shell sphere, quadrature averages);
+// inactive histories (q2 < 0) give 0. Every lane of the warp calls it.
+template <int KIND, int NV>
+__device__ __forceinline__ void dsigma_sorted(const float (&q2)[NV], const ModelConst<float>& mc,
+                                              const float* __restrict__ poly, float (&out)[NV])
 {
-    const bool on = q2 >= 0.f;
-    const float q = on ? M<float>::sqrt_(q2) : 0.f;
-    const float qlo = __uint_as_float(__reduce_min_sync(0xffffffffu, on ? __float_as_uint(q) : 0x7F800000u));
-    const float qhi = __uint_as_float(__reduce_max_sync(0xffffffffu, on ? __float_as_uint(q) : 0u));
-    if (qlo == __uint_as_float(0x7F800000u)) return 0.f;   // no live lane
-    const float qe = on ? q : qhi, qe2 = on ? q2 : qhi * qhi;
-    const float iq = M<float>::rcp(qe);
-    float avg;
-    if constexpr (KIND == SAS_CORE_SHELL) {
-        avg = avg_core_shell_split(qe, qe2, iq, poly, mc.n_poly, mc.shell,
-                                   node_split(poly, mc.n_poly, 6, 7, qlo, qhi));
-    } else {
-        avg = avg_sphere_split(qe, qe2, iq, poly, mc.n_poly, node_split(poly, mc.n_poly, 0, 0, qlo, qhi));
+    unsigned lo = 0x7F800000u, hi = 0u;
+    float q[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        q[v] = q2[v] >= 0.f ? M<float>::sqrt_(q2[v]) : 0.f;
+        if (q2[v] >= 0.f) {
+            lo = min(lo, __float_as_uint(q[v]));
+            hi = max(hi, __float_as_uint(q[v]));
+        }
     }
-    const float v = mc.scale * avg * structure_factor<float>(qe, mc);
-    return on ? v : 0.f;
+    const float qlo = __uint_as_float(__reduce_min_sync(0xffffffffu, lo));
+    const float qhi = __uint_as_float(__reduce_max_sync(0xffffffffu, hi));
+    if (qlo == __uint_as_float(0x7F800000u)) {   // no live history in the warp
+#pragma unroll
+        for (int v = 0; v < NV; ++v) out[v] = 0.f;
+        return;
+    }
+    float qe[NV], qe2[NV], iq[NV], avg[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        const bool on = q2[v] >= 0.f;
+        qe[v] = on ? q[v] : qhi;
+        qe2[v] = on ? q2[v] : qhi * qhi;
+        iq[v] = M<float>::rcp(qe[v]);
+    }
+    if constexpr (KIND == SAS_CORE_SHELL) {
+        avg_core_shell_split<NV>(qe, qe2, iq, poly, mc.n_poly, mc.shell, node_split(poly, mc.n_poly, 6, 7, qlo, qhi),
+                                 avg);
+    } else {
+        avg_sphere_split<NV>(qe, qe2, iq, poly, mc.n_poly, node_split(poly, mc.n_poly, 0, 0, qlo, qhi), avg);
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+        out[v] = q2[v] >= 0.f ? mc.scale * avg[v] * structure_factor<float>(qe[v], mc) : 0.f;
 }
 
 // Kahan-compensated accumulation of the orientation sum.

@@ -207,9 +207,10 @@ __device__ __forceinline__ void group_sync(int id, int count)
 // into its |Q|^2 bin (the shared-memory atomic returns its rank in the bin);
 // after an exclusive prefix sum over the bins every history's (|Q|^2, pixel,
 // prefactor) goes to its place in bin order, and each warp then evaluates
-// and tallies 32 consecutive places, i.e. histories of nearby |Q|. Thread t
-// takes places t and SORT_PER * nb - 1 - t, pairing low and high |Q|
-// so that warps get similar work. The set of histories, their values and
+// and tallies 32 x SORT_PER consecutive places, i.e. histories of nearby
+// |Q|, SORT_PER neighbouring places per lane in the same node loops (more
+// independent work per warp, one node-table load for all of them). The
+// set of histories, their values and
 // their tallies are those of the plain loop; only which lane evaluates which
 // history changes. The bin counters alternate between two arrays: the ones
 // of this pass are cleared after the last read of them and next counted into
@@ -272,13 +273,15 @@ __device__ __forceinline__ void trace_sorted_pass(const TraceParams<float>& P, c
     }
     group_sync(bar, nb);
     for (int i = tid; i <= SORT_BINS; i += nb) s_bin[i] = 0;
+    // a warp evaluates 32 x SORT_PER consecutive places, SORT_PER neighbours per lane
+    const int base_place = (tid >> 5) * 32 * SORT_PER + (tid & 31) * SORT_PER;
+    float q2v[SORT_PER], val[SORT_PER];
 #pragma unroll
-    for (int k = 0; k < SORT_PER; ++k) {
-        const int slot = (k & 1) ? SORT_PER * nb - 1 - (k >> 1) * nb - tid
-                                 : (k >> 1) * nb + tid;
-        const float v = dsigma_sorted<KIND>(s_q2[slot], P.mc, poly);
-        tally<float, TALLY, AGG>(P, h, s_pix[slot], s_pref[slot] * v);
-    }
+    for (int k = 0; k < SORT_PER; ++k) q2v[k] = s_q2[base_place + k];
+    dsigma_sorted<KIND, SORT_PER>(q2v, P.mc, poly, val);
+#pragma unroll
+    for (int k = 0; k < SORT_PER; ++k)
+        tally<float, TALLY, AGG>(P, h, s_pix[base_place + k], s_pref[base_place + k] * val[k]);
 }
 
 template <typename T, int KIND, int TALLY, int AGG, bool ATT, bool SORT = false>
