@@ -511,8 +511,10 @@ def n4_models(stream):
         ms = _events_ms(lambda: e.trace(n, 1), stream)
         e.close()
         rate = n / (ms * 1e-3)
+        fl = F.flops_per_history(m.kind, m.n_poly, m.n_gamma * m.n_psi)
         res[cfg["name"]] = {"workload": SHELLED_DESC[cfg["name"]], "value": rate, "unit": UNIT,
-                            "histories_timed": n, "node_terms_per_s": rate * m.n_gamma * m.n_psi * m.n_poly}
+                            "histories_timed": n, "node_terms_per_s": rate * m.n_gamma * m.n_psi * m.n_poly,
+                            "tflops_nominal": fl * rate / 1e12, "frac_fp32_nominal": fl * rate / 1e12 / peak}
     return res
 
 
@@ -619,11 +621,16 @@ def run_single_workload(args):
     stream = torch.cuda.Stream()
     info = sas.sas_device_info()
     capped = args.workload in ("capped_cylinder", "barbell")
+    shelled = args.workload in SHELLED_DESC
     cfg = W.capped_cylinder_config() if args.workload == "capped_cylinder" else \
-        W.barbell_config() if args.workload == "barbell" else W.cylinder_config()
+        W.barbell_config() if args.workload == "barbell" else \
+        {c["name"]: c for c in W.shelled_configs()}[args.workload] if shelled else W.cylinder_config()
     m = cfg["model"]
+    if shelled:
+        cfg = dict(cfg, seed=1)
     n = int(args.neutrons) if args.neutrons else (2_000_000 if args.workload == "cylinder" else
-                                                  20_000_000 if capped else 100_000_000)
+                                                  20_000_000 if capped else
+                                                  40_000_000 if shelled else 100_000_000)
     with torch.cuda.stream(stream):
         e = sas.Experiment(cfg["instrument"], m, stream=stream)
         extra = {}
@@ -653,7 +660,7 @@ def run_single_workload(args):
             "vs_baseline": None, "dtype": "bf16" if bound == "tensor" else "f32", "data": "synthetic",
             "config": {"workload": args.workload + ": " + (
                 W.MODEL_NAMES[m.kind] + " " + CAPPED_DESC[args.workload]
-                if capped else "cylinder R=20 L=400 A, axis N(15 deg) about x, Schulz 0.1 x40, 76x76 "
+                if capped else SHELLED_DESC[args.workload] if shelled else "cylinder R=20 L=400 A, axis N(15 deg) about x, Schulz 0.1 x40, 76x76 "
                                "orientation nodes, 256x256 detector"), "neutrons_per_step": n},
             "roofline": {"bound": bound, "achieved": flop * rate / 1e12, "peak": peak, "unit": unit,
                          "frac": flop * rate / 1e12 / peak, "traffic": None, "kernel": kernel,
@@ -713,7 +720,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true")
     ap.add_argument("--workload", default="core_shell",
-                    choices=["core_shell", "cylinder", "cylinder_surrogate", "capped_cylinder", "barbell"],
+                    choices=["core_shell", "cylinder", "cylinder_surrogate", "capped_cylinder", "barbell"]
+                    + list(SHELLED_DESC),
                     help="core_shell: the headline step; the others time one workload alone")
     ap.add_argument("--train-steps", type=int, default=100000)
     args = ap.parse_args()

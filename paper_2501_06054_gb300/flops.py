@@ -43,6 +43,15 @@ operations than counted here for the same terms.
       amplitude (mul), x^2 (mul), 2 J1(x)/x (6 FMA) and its product
       (mul), F^2 and the weighted sum (3)                          40
       per orientation node as for the cylinder                     60
+  shelled cylinders (core-shell, hollow, bicelle): per radius node
+      two radial factors 2 J1(x)/x without their square and sum
+      (2 x 23), the two sinc combinations (2 x (mul, FMA)), the
+      amplitude (FMA), F^2 and the sum (FMA)                       56
+      per orientation node: the cylinder's plus a second sinc      86
+  core-shell ellipsoid: per radius node two ellipsoid terms without
+      their square and sum (2 x 35), combination (mul, FMA), F^2
+      and the sum (FMA)                                            75
+      per orientation node as for the ellipsoid                    60
   per history: geometry (wavelength, pinholes, slab, detector
                point, Q, solid angle)                           150
                Percus-Yevick S(Q)                               40
@@ -60,6 +69,9 @@ GEOMETRY = 150
 PY = 40
 CAP_SLICE = 17
 CAP_NODE = 40
+CS_CYL_TERM = 56
+CS_CYL_ORIENT = 86
+CS_ELL_TERM = 75
 
 
 def flops_per_history(kind: int, n_poly: int, n_orient: int = 1, sq: bool = False, n_cap: int = 16) -> int:
@@ -75,6 +87,10 @@ def flops_per_history(kind: int, n_poly: int, n_orient: int = 1, sq: bool = Fals
         per = n_orient * (FRAME_NODE + n_poly * BOX_TERM)
     elif kind in (6, 7):  # capped cylinder, barbell
         per = n_orient * (ORIENT_NODE + n_poly * (CAP_NODE + n_cap * CAP_SLICE))
+    elif kind in (8, 9, 11):  # core-shell cylinder, hollow cylinder, core-shell bicelle
+        per = n_orient * (CS_CYL_ORIENT + n_poly * CS_CYL_TERM)
+    elif kind == 10:     # core-shell ellipsoid
+        per = n_orient * (ORIENT_NODE + n_poly * CS_ELL_TERM)
     else:                # ellipsoid
         per = n_orient * (ORIENT_NODE + n_poly * (AMP + 5))
     return per + GEOMETRY + (PY if sq else 0)
