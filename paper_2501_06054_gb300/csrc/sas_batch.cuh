@@ -65,7 +65,7 @@ __device__ __forceinline__ void batch_item(const BatchParams& P, const ModelCons
             const History<float> hs = history<float, ATT>(P.in, mc.att, seed, w.exp, w.first + j);
             tr.add(hs.wt);
             if (hs.pixel >= 0) {
-                wt = hs.pref * dsigma_history<float, KIND>(hs.q, mc, poly, orient, seed, w.exp, w.first + j);
+                wt = hs.pref * dsigma_history<float, KIND, true>(hs.q, mc, poly, orient, seed, w.exp, w.first + j);
                 pix = hs.pixel;
             }
         }

@@ -473,13 +473,14 @@ struct Kahan {
 };
 
 // Number of the ascending radius nodes whose r^2 qm stays <= smax (binary
-// search on the first value of each poly row).
-__device__ __forceinline__ int cyl_tier_end(const float* __restrict__ poly, int lo, int np, float qm, float smax)
+// search on value `col` of each poly row, the first by default).
+__device__ __forceinline__ int cyl_tier_end(const float* __restrict__ poly, int lo, int np, float qm, float smax,
+                                            int col = 0)
 {
     int hi = np;
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (poly[8 * mid] * qm <= smax) lo = mid + 1;
+        if (poly[8 * mid + col] * qm <= smax) lo = mid + 1;
         else hi = mid;
     }
     return lo;
@@ -741,21 +742,102 @@ __device__ __forceinline__ float cs_cyl_amp(float k1, float k2, float qab2, floa
     return fmaf(k1, cyl_a_tier<TIER>(qab2 * r2), k2 * cyl_a_tier<TIER>(qab2 * ro2));
 }
 
+// F of one shelled-cylinder radius node {r^2, r_o^2, c_1, c_2 | c_3, c_4, r, r_o}
+// in the 2 J1(x)/x form of tier TIER, s1 and s2 the node's two sincs.
+template <int TIER>
+__device__ __forceinline__ float cs_cyl_node(const float* __restrict__ poly, int i, float s1, float s2, float qab2)
+{
+    const float4 p = *reinterpret_cast<const float4*>(poly + SAS_POLY_STRIDE * i);      // r^2, r_o^2, c_1, c_2
+    const float2 pc = *reinterpret_cast<const float2*>(poly + SAS_POLY_STRIDE * i + 4); // c_3, c_4
+    const float k1 = fmaf(s1, p.z, s2 * p.w), k2 = fmaf(s1, pc.x, s2 * pc.y);
+    return cs_cyl_amp<TIER>(k1, k2, qab2, p.x, p.y);
+}
+
 // Core-shell and hollow cylinders, core-shell bicelle (Eq. 1 region by
 // region, four nested cylinders): per orientation node and radius node
 // {r^2, r_o^2, c_1, c_2, c_3, c_4, r, r_o},
 //   F = (c_1 s_L + c_2 s_Lo) a(Q_AB r) + (c_3 s_L + c_4 s_Lo) a(Q_AB r_o),
-// s_H = sinc(Q_C H/2), L_o = L + 2 t_f. FP32: the 2 J1(x)/x form chosen per
-// node, uniformly over the warp, from the warp's largest |Q|^2 times r_o^2.
-template <typename T>
+// s_H = sinc(Q_C H/2), L_o = L + 2 t_f. FP32: the 2 J1(x)/x form of a node
+// is chosen uniformly over the warp from the warp's largest |Q|^2 times
+// r_o^2. RUNS: the radius nodes ascend, so the forms split them into
+// consecutive runs found once per history, each run a loop of its own form;
+// otherwise (the batch kernel, whose registers are shared by every kind)
+// the form is chosen node by node.
+template <typename T, bool RUNS = true>
 __device__ __forceinline__ T avg_cs_cylinder(const T qv[3], const T* __restrict__ poly, int np,
                                              const T* __restrict__ orient, int no, const ModelConst<T>& mc)
 {
     Kahan<T> k;
-    float qm = 0.f;
-    if constexpr (sizeof(T) == sizeof(float)) {
+    if constexpr (sizeof(T) == sizeof(float) && !RUNS) {
         const float q2 = fma(qv[0], qv[0], fma(qv[1], qv[1], qv[2] * qv[2]));
-        qm = __uint_as_float(__reduce_max_sync(__activemask(), __float_as_uint(q2)));
+        const float qm = __uint_as_float(__reduce_max_sync(__activemask(), __float_as_uint(q2)));
+        for (int o = 0; o < no; ++o) {
+            const T* c = orient + 4 * o;
+            const T qc = fma(qv[0], c[0], fma(qv[1], c[1], qv[2] * c[2]));
+            const T x0 = fma(qv[1], c[2], -qv[2] * c[1]);
+            const T x1 = fma(qv[2], c[0], -qv[0] * c[2]);
+            const T x2 = fma(qv[0], c[1], -qv[1] * c[0]);
+            const T qab2 = fma(x0, x0, fma(x1, x1, x2 * x2));
+            const T y1 = fabs(qc) * mc.half_length, y2 = fabs(qc) * mc.half_length_o;
+            const T s1 = M<T>::sinc(y1, M<T>::rcp(y1)), s2 = M<T>::sinc(y2, M<T>::rcp(y2));
+            float inner = 0.f;
+            for (int i = 0; i < np; ++i) {
+                const float bound = qm * poly[SAS_POLY_STRIDE * i + 1];   // warp-uniform
+                float F;
+                if (bound <= SAS_J1R_SMAX) F = cs_cyl_node<0>(poly, i, s1, s2, qab2);
+                else if (bound <= SAS_J1V_SMAX) F = cs_cyl_node<1>(poly, i, s1, s2, qab2);
+                else if (bound <= SAS_J1P_SMAX) F = cs_cyl_node<2>(poly, i, s1, s2, qab2);
+                else if (bound <= SAS_J1Q_SMAX) F = cs_cyl_node<3>(poly, i, s1, s2, qab2);
+                else F = cs_cyl_node<4>(poly, i, s1, s2, qab2);
+                inner = fmaf(F, F, inner);
+            }
+            k.add(c[3] * inner);
+        }
+        return k.s;
+    } else if constexpr (sizeof(T) == sizeof(float)) {
+        const float q2 = fma(qv[0], qv[0], fma(qv[1], qv[1], qv[2] * qv[2]));
+        const float qm = __uint_as_float(__reduce_max_sync(__activemask(), __float_as_uint(q2)));
+        const int t4 = cyl_tier_end(poly, 0, np, qm, SAS_J1R_SMAX, 1);
+        const int t6 = cyl_tier_end(poly, t4, np, qm, SAS_J1V_SMAX, 1);
+        const int t8 = cyl_tier_end(poly, t6, np, qm, SAS_J1P_SMAX, 1);
+        const int t12 = cyl_tier_end(poly, t8, np, qm, SAS_J1Q_SMAX, 1);
+        for (int o = 0; o < no; ++o) {
+            const T* c = orient + 4 * o;
+            const T qc = fma(qv[0], c[0], fma(qv[1], c[1], qv[2] * c[2]));
+            const T x0 = fma(qv[1], c[2], -qv[2] * c[1]);
+            const T x1 = fma(qv[2], c[0], -qv[0] * c[2]);
+            const T x2 = fma(qv[0], c[1], -qv[1] * c[0]);
+            const T qab2 = fma(x0, x0, fma(x1, x1, x2 * x2));
+            const T y1 = fabs(qc) * mc.half_length, y2 = fabs(qc) * mc.half_length_o;
+            const T s1 = M<T>::sinc(y1, M<T>::rcp(y1)), s2 = M<T>::sinc(y2, M<T>::rcp(y2));
+            float inner = 0.f;
+#pragma unroll 4
+            for (int i = 0; i < t4; ++i) {
+                const float F = cs_cyl_node<0>(poly, i, s1, s2, qab2);
+                inner = fmaf(F, F, inner);
+            }
+#pragma unroll 4
+            for (int i = t4; i < t6; ++i) {
+                const float F = cs_cyl_node<1>(poly, i, s1, s2, qab2);
+                inner = fmaf(F, F, inner);
+            }
+#pragma unroll 2
+            for (int i = t6; i < t8; ++i) {
+                const float F = cs_cyl_node<2>(poly, i, s1, s2, qab2);
+                inner = fmaf(F, F, inner);
+            }
+#pragma unroll 2
+            for (int i = t8; i < t12; ++i) {
+                const float F = cs_cyl_node<3>(poly, i, s1, s2, qab2);
+                inner = fmaf(F, F, inner);
+            }
+            for (int i = t12; i < np; ++i) {
+                const float F = cs_cyl_node<4>(poly, i, s1, s2, qab2);
+                inner = fmaf(F, F, inner);
+            }
+            k.add(c[3] * inner);
+        }
+        return k.s;
     }
     for (int o = 0; o < no; ++o) {
         const T* c = orient + 4 * o;
@@ -767,29 +849,13 @@ __device__ __forceinline__ T avg_cs_cylinder(const T qv[3], const T* __restrict_
         const T y1 = fabs(qc) * mc.half_length, y2 = fabs(qc) * mc.half_length_o;
         const T s1 = M<T>::sinc(y1, M<T>::rcp(y1)), s2 = M<T>::sinc(y2, M<T>::rcp(y2));
         T inner = 0;
-        if constexpr (sizeof(T) == sizeof(float)) {
-            for (int i = 0; i < np; ++i) {
-                const float4 p = *reinterpret_cast<const float4*>(poly + SAS_POLY_STRIDE * i);      // r^2, r_o^2, c_1, c_2
-                const float4 pc = *reinterpret_cast<const float4*>(poly + SAS_POLY_STRIDE * i + 4); // c_3, c_4, r, r_o
-                const float k1 = fmaf(s1, p.z, s2 * p.w), k2 = fmaf(s1, pc.x, s2 * pc.y);
-                const float bound = qm * p.y;   // warp-uniform
-                float F;
-                if (bound <= SAS_J1R_SMAX) F = cs_cyl_amp<0>(k1, k2, qab2, p.x, p.y);
-                else if (bound <= SAS_J1V_SMAX) F = cs_cyl_amp<1>(k1, k2, qab2, p.x, p.y);
-                else if (bound <= SAS_J1P_SMAX) F = cs_cyl_amp<2>(k1, k2, qab2, p.x, p.y);
-                else if (bound <= SAS_J1Q_SMAX) F = cs_cyl_amp<3>(k1, k2, qab2, p.x, p.y);
-                else F = cs_cyl_amp<4>(k1, k2, qab2, p.x, p.y);
-                inner = fmaf(F, F, inner);
-            }
-        } else {
-            const T qab = M<T>::sqrt_(qab2), iq = M<T>::rcp(qab);
-            for (int i = 0; i < np; ++i) {
-                const T* p = poly + SAS_POLY_STRIDE * i;
-                const T xa = qab * p[6], xb = qab * p[7];
-                const T F = fma(s1, p[2], s2 * p[3]) * M<T>::cyl_a(xa, iq / p[6], 0) +
-                            fma(s1, p[4], s2 * p[5]) * M<T>::cyl_a(xb, iq / p[7], 0);
-                inner = fma(F, F, inner);
-            }
+        const T qab = M<T>::sqrt_(qab2), iq = M<T>::rcp(qab);
+        for (int i = 0; i < np; ++i) {
+            const T* p = poly + SAS_POLY_STRIDE * i;
+            const T xa = qab * p[6], xb = qab * p[7];
+            const T F = fma(s1, p[2], s2 * p[3]) * M<T>::cyl_a(xa, iq / p[6], 0) +
+                        fma(s1, p[4], s2 * p[5]) * M<T>::cyl_a(xb, iq / p[7], 0);
+            inner = fma(F, F, inner);
         }
         k.add(c[3] * inner);
     }
@@ -1012,8 +1078,9 @@ __device__ __forceinline__ T shape_independent(T q2, T q, const ModelConst<T>& m
     }
 }
 
-// dSigma/dOmega(Q) in 1/angstrom
-template <typename T, int KIND>
+// dSigma/dOmega(Q) in 1/angstrom. LEAN: the forms that need fewer
+// registers, for the batch kernel (same values).
+template <typename T, int KIND, bool LEAN = false>
 __device__ __forceinline__ T dsigma(const T qv[3], const ModelConst<T>& mc,
                                     const T* __restrict__ poly, const T* __restrict__ orient)
 {
@@ -1037,7 +1104,7 @@ __device__ __forceinline__ T dsigma(const T qv[3], const ModelConst<T>& mc,
     } else if (KIND == SAS_CAPPED_CYLINDER || KIND == SAS_BARBELL) {
         avg = avg_capped<T>(qv, poly, mc.n_rad, orient, mc.n_orient, mc);
     } else if (KIND == SAS_CORE_SHELL_CYLINDER || KIND == SAS_HOLLOW_CYLINDER || KIND == SAS_CORE_SHELL_BICELLE) {
-        avg = avg_cs_cylinder<T>(qv, poly, mc.n_rad, orient, mc.n_orient, mc);
+        avg = avg_cs_cylinder<T, !LEAN>(qv, poly, mc.n_rad, orient, mc.n_orient, mc);
     } else if (KIND == SAS_CORE_SHELL_ELLIPSOID) {
         avg = avg_cs_ellipsoid<T>(qv, poly, mc.n_rad, orient, mc.n_orient, mc);
     } else {
@@ -1265,7 +1332,7 @@ __device__ __forceinline__ T dsigma_event(const T qv[3], const ModelConst<T>& mc
 
 // dSigma/dOmega of history `index` of experiment `exp_id`: the quadrature
 // average, or the per-event estimate from the history's own draws.
-template <typename T, int KIND>
+template <typename T, int KIND, bool LEAN = false>
 __device__ __forceinline__ T dsigma_history(const T qv[3], const ModelConst<T>& mc, const T* __restrict__ poly,
                                             const T* __restrict__ orient, uint64_t seed, uint32_t exp_id,
                                             uint64_t index)
@@ -1273,7 +1340,7 @@ __device__ __forceinline__ T dsigma_history(const T qv[3], const ModelConst<T>& 
     if constexpr (KIND != SAS_SHAPE_INDEPENDENT) {   // no draws: a law of |Q| only
         if (mc.event) return dsigma_event<T, KIND>(qv, mc, poly, event_draws(seed, exp_id, index));
     }
-    return dsigma<T, KIND>(qv, mc, poly, orient);
+    return dsigma<T, KIND, LEAN>(qv, mc, poly, orient);
 }
 
 // ------------------------------------------------------------- geometry
