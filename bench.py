@@ -209,13 +209,20 @@ def _rel_stats(rel):
             "max": float(rel.max()), "frac_bins_le_1pct": float(np.mean(rel <= 0.01))}
 
 
+def _axial_length(m):
+    """A uniaxial body's length along its axis (the surrogate's L)."""
+    return 2.0 * m.radius_polar if m.kind == W.ELLIPSOID else m.length
+
+
 def _in_box(box, m):
-    """The library's coverage rule (the model lies in the training box and
-    uses its quadrature), restated for choosing the bins to compare."""
-    return (m.kind == W.CYLINDER and m.precision == W.FP32 and m.isotropic == 0 and m.sampling == W.QUADRATURE
+    """The library's coverage rule (the model is of the box's kind, lies in
+    the training box and uses its quadrature), restated for choosing the
+    bins to compare."""
+    return (m.kind == box.get("model", W.CYLINDER) and m.precision == W.FP32 and m.isotropic == 0
+            and m.sampling == W.QUADRATURE
             and m.poly_dist == W.SCHULZ and not m.self_attenuation and m.n_poly == box["n_poly"]
             and m.n_gamma == box["n_gamma"] and m.n_psi == box["n_psi"]
-            and box["r_min"] <= m.radius <= box["r_max"] and box["l_min"] <= m.length <= box["l_max"]
+            and box["r_min"] <= m.radius <= box["r_max"] and box["l_min"] <= _axial_length(m) <= box["l_max"]
             and box["sigma_orient_min"] <= m.sigma_orient <= box["sigma_orient_max"]
             and box["poly_min"] <= m.poly <= box["poly_max"] and m.sld != m.sld_solvent)
 
@@ -225,10 +232,11 @@ def batched_config(stream, info, scale=1000, n_train=100_000_000, steps=150_000)
     four kinds), counts of the draw / scale, per-experiment 128x128
     detectors; a per-experiment loop of plain launches, the batched launch
     with the exact quadrature and the batched launch with the learned
-    surrogate serving the cylinders of its box (trained here on the batched
-    box). Per-bin error of the surrogate against the exact trace on the same
-    histories, over the covered cylinders' bins >= 1e-3 of each detector's
-    largest bin; the same three rates on the cylinder experiments alone."""
+    surrogates serving the cylinders and the ellipsoids of their boxes (one
+    network per body, trained here on the batched boxes). Per-bin error of
+    the surrogates against the exact trace on the same histories, over the
+    covered experiments' bins >= 1e-3 of each detector's largest bin, per
+    body; the same three rates on the cylinder experiments alone."""
     import torch
     import paper_2501_06054_gb300 as sas
     from paper_2501_06054_gb300 import flops as F
@@ -239,7 +247,9 @@ def batched_config(stream, info, scale=1000, n_train=100_000_000, steps=150_000)
     cnt = np.maximum(counts // scale, 1).astype(np.uint64)
     peak = F.fp32_peak_tflops(info["sm_count"], 2070.0)
     box = W.batched_surrogate_box()
+    ebox = W.batched_ellipsoid_surrogate_box()
     sur, training = _train_surrogate(sas, box, stream, n_train, steps)
+    esur, etraining = _train_surrogate(sas, ebox, stream, n_train, steps)
 
     def plain_loop(sel):
         exs = []
@@ -261,6 +271,7 @@ def batched_config(stream, info, scale=1000, n_train=100_000_000, steps=150_000)
         b = sas.sas_create_batch(inst, [models[k] for k in sel], cnt[sel], stream=stream)
         if with_sur:
             sas.sas_batch_attach_surrogate(b, sur)
+            sas.sas_batch_attach_surrogate(b, esur)
         sas.sas_trace_batch(b, 1)
         ms = _events_ms(lambda: sas.sas_trace_batch(b, 1), stream)
         return b, ms
@@ -280,7 +291,7 @@ def batched_config(stream, info, scale=1000, n_train=100_000_000, steps=150_000)
         tot = int(cnt[sel].sum())
         ms_plain = plain_loop(sel)
         b, ms_b = batched(sel, False)
-        dev = {k: v.clone() for k, v in _batch_views(sas, b, len(sel), npix).items()} if name == "cylinders" \
+        dev = {k: v.clone() for k, v in _batch_views(sas, b, len(sel), npix).items()} if name == "all" \
             else None
         sas.sas_destroy_batch(b)
         bs, ms_bs = batched(sel, True)
@@ -301,26 +312,29 @@ def batched_config(stream, info, scale=1000, n_train=100_000_000, steps=150_000)
                                     "share_of_histories": (n_h - fb) / max(tot, 1)}}
         if dev is not None:
             got = _batch_views(sas, bs, len(sel), npix)
-            rels, keys = [], []
-            for j, k in enumerate(sel):
-                if not _in_box(box, models[k]):
-                    continue
-                ex = dev["sum_w"][j]
-                big = ex >= 1e-3 * ex.max()
-                rels.append(((got["sum_w"][j] - ex).abs()[big] / ex[big]).cpu().numpy())
-                keys.append((math.degrees(models[k].sigma_orient), 0.5 * models[k].length / models[k].radius))
-            row["per_bin_rel_err"] = dict(_rel_stats(np.concatenate(rels) if rels else []),
-                                          experiments=len(rels),
-                                          compared_on="identical histories (same Philox streams), surrogate vs "
-                                                      "exact quadrature, bins >= 1e-3 of each detector's max")
-            strata = {}
-            for name_, idx_, edges in (("sigma_orient_deg", 0, (1, 5, 10, 20, 30.01)),
-                                       ("aspect_L_over_2R", 1, (0, 0.3, 1, 3, 21))):
-                for lo, hi in zip(edges[:-1], edges[1:]):
-                    sel_ = [r for r, kk in zip(rels, keys) if lo <= kk[idx_] < hi]
-                    strata[f"{name_} [{lo}, {hi})"] = dict(_rel_stats(np.concatenate(sel_) if sel_ else []),
-                                                            experiments=len(sel_))
-            row["per_bin_rel_err_by_stratum"] = strata
+            row["per_bin_rel_err"], row["per_bin_rel_err_by_stratum"] = {}, {}
+            for body, bx in (("cylinders", box), ("ellipsoids", ebox)):
+                rels, keys = [], []
+                for j, k in enumerate(sel):
+                    if not _in_box(bx, models[k]):
+                        continue
+                    ex = dev["sum_w"][j]
+                    big = ex >= 1e-3 * ex.max()
+                    rels.append(((got["sum_w"][j] - ex).abs()[big] / ex[big]).cpu().numpy())
+                    keys.append((math.degrees(models[k].sigma_orient), 0.5 * _axial_length(models[k]) /
+                                 models[k].radius))
+                row["per_bin_rel_err"][body] = dict(
+                    _rel_stats(np.concatenate(rels) if rels else []), experiments=len(rels),
+                    compared_on="identical histories (same Philox streams), surrogate vs exact quadrature, "
+                                "bins >= 1e-3 of each detector's max")
+                strata = {}
+                for name_, idx_, edges in (("sigma_orient_deg", 0, (1, 5, 10, 20, 30.01)),
+                                           ("aspect_L_over_2R", 1, (0, 0.3, 1, 3, 21))):
+                    for lo, hi in zip(edges[:-1], edges[1:]):
+                        sel_ = [r for r, kk in zip(rels, keys) if lo <= kk[idx_] < hi]
+                        strata[f"{name_} [{lo}, {hi})"] = dict(_rel_stats(np.concatenate(sel_) if sel_ else []),
+                                                                experiments=len(sel_))
+                row["per_bin_rel_err_by_stratum"][body] = strata
             del dev
         sas.sas_destroy_batch(bs)
         rows[name] = row
@@ -328,7 +342,10 @@ def batched_config(stream, info, scale=1000, n_train=100_000_000, steps=150_000)
     res.update(rows)
     res["surrogate"] = {"box": {k: (math.degrees(v) if k.startswith("sigma_orient") else v)
                                 for k, v in box.items()}, "training": training}
+    res["surrogate_ellipsoid"] = {"box": {k: (math.degrees(v) if k.startswith("sigma_orient") else v)
+                                          for k, v in ebox.items()}, "training": etraining}
     sas.sas_destroy_surrogate(sur)
+    sas.sas_destroy_surrogate(esur)
     return res
 
 

@@ -512,19 +512,22 @@ sas_status sas_trace_batch_static(const sas_instrument *inst, const sas_model_de
                                   double *sum_w, double *sum_w2, uint64_t *count,
                                   double *transmitted, void *stream);
 
-/* ---- learned surrogate of the averaged cylinder form factor ---------
- * The paper has no learned part. The network stands in for the cylinder's
- * cross section of Eq. 8 averaged over the radius and axis distributions of
- * Sec. II.B, the costly step of the anisotropic models (Sec. III.B names the
- * cylinder family among those that gain most on a GPU). */
+/* ---- learned surrogate of the averaged form factor of uniaxial bodies --
+ * The paper has no learned part. The network stands in for the cross
+ * section of Eq. 8 of a cylinder or an ellipsoid of revolution averaged over
+ * the radius and axis distributions of Sec. II.B, the costly step of the
+ * anisotropic models (Sec. III.B names the cylinder family among those that
+ * gain most on a GPU). One surrogate serves one body. */
 
 typedef struct sas_surrogate sas_surrogate;          /* opaque, library-owned */
 
-/* Training box. The surrogate reproduces, for oriented polydisperse
- * cylinders inside it, the normalised averaged form factor
+/* Training box. The surrogate reproduces, for oriented polydisperse bodies
+ * of its kind inside it, the normalised averaged form factor
  * P = <|F|^2> / (drho^2 <V^2>) that sas_set_model's quadrature gives with
- * the same node counts (n_poly Schulz nodes; n_gamma x n_psi orientation
- * nodes). Its inputs are the rotation-invariant features
+ * the same node counts (n_poly Schulz nodes on the radius; n_gamma x n_psi
+ * orientation nodes). L is the body's length along its axis: the cylinder's
+ * length, or twice the polar semi-axis R_p of the ellipsoid (whose
+ * equatorial semi-axis is R). Its inputs are the rotation-invariant features
  * (q_par L / 2, q_perp R, L / (2R), sigma_orient, sigma_poly) plus
  * n_fourier (sin, cos) pairs of k q_par L / 4 (k = 1..n), where q_par and
  * q_perp are the components of Q along and across the mean axis; its output
@@ -532,14 +535,14 @@ typedef struct sas_surrogate sas_surrogate;          /* opaque, library-owned */
  * sigma_poly is learned on n_buckets values spread evenly over the range. */
 typedef struct sas_surrogate_box {
     double q_max;                                 /* 1/angstrom */
-    double r_min, r_max;                          /* cylinder radius, angstrom */
-    double l_min, l_max;                          /* cylinder length, angstrom */
+    double r_min, r_max;                          /* radius R, angstrom */
+    double l_min, l_max;                          /* length L along the axis, angstrom */
     double sigma_orient_min, sigma_orient_max;    /* rad */
     double poly_min, poly_max;                    /* Schulz relative width */
     int32_t n_poly, n_gamma, n_psi;               /* quadrature it reproduces */
     int32_t n_buckets;                            /* sigma_poly values in the training set */
-    int32_t n_fourier;                            /* Fourier feature pairs (0..28) */
-    int32_t reserved;
+    int32_t n_fourier;                            /* Fourier feature pairs (0..13) */
+    int32_t model;                                /* SAS_CYLINDER (0 reads as it) or SAS_ELLIPSOID */
 } sas_surrogate_box;
 
 /* MLP 64 -> 256 -> 256 -> 256 -> 256 -> 1, SiLU, BF16 hidden weights (FP32
@@ -594,18 +597,20 @@ sas_status sas_surrogate_info(const sas_surrogate *s, size_t *n_params, uint32_t
 sas_status sas_surrogate_test_stall(sas_surrogate *s, uint64_t wait_ns);
 sas_status sas_destroy_surrogate(sas_surrogate *s);
 
-/* Use the surrogate for the experiment's cylinder model when it lies in the
- * training box (same node counts); histories whose |Q| leaves the box fall
- * back to the exact quadrature. NULL detaches. The surrogate must outlive
- * the attachment. */
+/* Use the surrogate for the experiment's model when it is of the
+ * surrogate's kind and lies in the training box (same node counts);
+ * histories whose |Q| leaves the box fall back to the exact quadrature.
+ * NULL detaches. The surrogate must outlive the attachment. */
 sas_status sas_attach_surrogate(sas_experiment *exp, const sas_surrogate *s);
 
-/* Same for every in-box cylinder experiment of a batch: they are traced by a
- * second persistent tensor-core kernel in the batch's graph. */
+/* Same for every in-box experiment of the surrogate's kind in a batch: they
+ * are traced by a persistent tensor-core kernel in the batch's graph. A
+ * batch holds one surrogate per kind (a cylinder and an ellipsoid one);
+ * attaching replaces the one of the same kind, NULL detaches both. */
 sas_status sas_batch_attach_surrogate(sas_batch *batch, const sas_surrogate *s);
 
-/* Experiments of the batch that the attached surrogate covers (their model
- * lies in its box) and their histories; the other experiments run the exact
+/* Experiments of the batch that the attached surrogates cover (their model
+ * lies in a box) and their histories; the other experiments run the exact
  * quadrature. Of the covered histories, those whose |Q| leaves the box are
  * counted by sas_surrogate_fallbacks. NULL outputs are skipped. */
 sas_status sas_batch_surrogate_share(const sas_batch *batch, uint64_t *experiments, uint64_t *histories);

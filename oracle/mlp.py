@@ -13,7 +13,9 @@ Plain numpy definitions of what the surrogate computes:
   weights and BF16-rounded inputs of every hidden matrix product (the
   tensor-core operands), FP64 arithmetic otherwise;
 * the mean squared error of log P and its exact gradient (backpropagation);
-* the exact target P = <|F|^2> / (drho^2 <V^2>) from the trace oracle.
+* the exact target P = <|F|^2> / (drho^2 <V^2>) from the trace oracle, of
+  a cylinder of length L or of an ellipsoid of revolution of polar
+  semi-axis L / 2 (the same features serve both bodies).
 
 Flat parameter layout (float32 master copy): W1 [256][64] | W2 | W3 | W4
 [256][256] (out, in) | b1 (unused) | b2 | b3 | b4 | w5 [256] | b5.
@@ -159,18 +161,22 @@ def loss_and_grad(p, X, y, rnd=bf16):
 
 def exact_pbar(box, raw):
     """Exact P at raw parameters [n][8] (bucket sigma_poly in column 5)
-    with the trace oracle's quadrature about the z axis. The training
-    target is log max(P, TARGET_FLOOR)."""
+    with the trace oracle's quadrature about the z axis, for the box's body:
+    the cylinder of length L, or (box model ELLIPSOID) the ellipsoid of
+    revolution with polar semi-axis L / 2 and polydisperse equatorial
+    semi-axis R. The training target is log max(P, TARGET_FLOOR)."""
     import oracle
     import sas_workloads as W
+    ell = box.get("model", W.CYLINDER) == W.ELLIPSOID
     out = np.empty(len(raw))
     for i, r in enumerate(np.asarray(raw, dtype=np.float64)):
         qpar, qperp, R, L, so, sp = r[:6]
-        m = W.Model(kind=W.CYLINDER, radius=R, length=L, sld=1.0, volume_fraction=1.0, poly=sp,
+        shape = dict(kind=W.ELLIPSOID, radius_polar=0.5 * L) if ell else dict(kind=W.CYLINDER, length=L)
+        m = W.Model(radius=R, sld=1.0, volume_fraction=1.0, poly=sp,
                     n_poly=box["n_poly"], sigma_orient=so, axis_theta=0.0, axis_phi=0.0,
-                    n_gamma=box["n_gamma"], n_psi=box["n_psi"])
+                    n_gamma=box["n_gamma"], n_psi=box["n_psi"], **shape)
         prep = oracle.Prepared(m)
-        V = math.pi * prep.poly_r ** 2 * L
+        V = (4.0 / 3.0 * math.pi * prep.poly_r ** 2 * 0.5 * L) if ell else math.pi * prep.poly_r ** 2 * L
         vm = float(np.dot(prep.poly_w, V))
         v2 = float(np.dot(prep.poly_w, V * V))
         ds = oracle.dsigma(prep, np.array([[qperp, 0.0, qpar]]))[0]

@@ -69,7 +69,7 @@ class sas_surrogate_box(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in (
         "q_max", "r_min", "r_max", "l_min", "l_max", "sigma_orient_min", "sigma_orient_max",
         "poly_min", "poly_max")] + [(n, ctypes.c_int32) for n in (
-            "n_poly", "n_gamma", "n_psi", "n_buckets", "n_fourier", "reserved")]
+            "n_poly", "n_gamma", "n_psi", "n_buckets", "n_fourier", "model")]
 
 
 _lib = None
@@ -450,7 +450,7 @@ def sas_trace_batch_static(instrument, models, counts, seed, sum_w, sum_w2, coun
 
 
 def make_box(d) -> sas_surrogate_box:
-    ints = ("n_poly", "n_gamma", "n_psi", "n_buckets", "n_fourier", "reserved")
+    ints = ("n_poly", "n_gamma", "n_psi", "n_buckets", "n_fourier", "model")
     return sas_surrogate_box(**{k: (int(v) if k in ints else float(v)) for k, v in d.items()})
 
 

@@ -1087,7 +1087,7 @@ struct sas_experiment {
     InstConst<double> icd;
     LaunchCfg cfg;
     int stage_orient = 0;
-    // learned surrogate (cylinders in its training box)
+    // learned surrogate (models of its kind in its training box)
     const sas_surrogate* sur = nullptr;
     WorkItem* d_items = nullptr;
     uint32_t* d_prefix = nullptr;      // 256-history pairs before each item
@@ -1339,7 +1339,7 @@ sas_status upload_surrogate_exp(sas_experiment* e)
     return SAS_OK;
 }
 
-// Cylinder trace through the tensor-core surrogate: items of 2^16
+// Trace through the tensor-core surrogate: items of 2^16
 // histories, cut into 256-history pairs that a grid of one CTA per SM takes
 // round-robin.
 sas_status trace_surrogate(sas_experiment* e, uint64_t first, uint64_t n, uint64_t seed)

@@ -63,14 +63,15 @@ struct sas_batch {
     cudaGraphExec_t exec = nullptr;
     uint64_t total_histories = 0;
     std::vector<sas_model_desc> models;
-    // learned surrogate for the in-box cylinder experiments
-    const sas_surrogate* sur = nullptr;
+    // learned surrogates for the in-box experiments: slot 0 cylinders,
+    // slot 1 ellipsoids; use_sur[e] = serving slot + 1, or 0 (exact)
+    const sas_surrogate* sur[2] = {nullptr, nullptr};
     std::vector<int> use_sur;
-    WorkItem* d_sur_items = nullptr;
-    uint32_t* d_sur_prefix = nullptr;  // 256-history pairs before each surrogate item
-    size_t sur_cap = 0;
-    uint32_t n_sur_items = 0;
-    uint32_t n_sur_pairs = 0;
+    WorkItem* d_sur_items[2] = {nullptr, nullptr};
+    uint32_t* d_sur_prefix[2] = {nullptr, nullptr};  // 256-history pairs before each surrogate item
+    size_t sur_cap[2] = {0, 0};
+    uint32_t n_sur_items[2] = {0, 0};
+    uint32_t n_sur_pairs[2] = {0, 0};
     sur::SurExp* d_sexp = nullptr;
     unsigned long long* d_fallbacks = nullptr;
 };
@@ -91,7 +92,7 @@ sas_status build_items(sas_batch* b)
     std::vector<WorkItem> items;
     std::vector<double> icost;
     const double target = b->cfg.target_item_flop > 0 ? b->cfg.target_item_flop : 2e9;
-    std::vector<WorkItem> sitems;
+    std::vector<WorkItem> sitems[2];
     for (size_t e = 0; e < b->n_exp; ++e) {
         const uint64_t n = b->counts[e];
         if (n == 0) continue;
@@ -102,7 +103,7 @@ sas_status build_items(sas_batch* b)
                 w.first = f;
                 w.exp = (uint32_t)e;
                 w.n = (uint32_t)std::min<uint64_t>(c, n - f);
-                sitems.push_back(w);
+                sitems[b->use_sur[e] - 1].push_back(w);
             }
             continue;
         }
@@ -141,27 +142,30 @@ sas_status build_items(sas_batch* b)
     if (!sorted.empty())
         SAS_CUDA_B(cudaMemcpy(b->d_items, sorted.data(), sorted.size() * sizeof(WorkItem), cudaMemcpyHostToDevice),
                    "upload items");
-    std::vector<uint32_t> sprefix;
-    const uint64_t n_pairs = surrogate_pair_prefix(sitems, sprefix);
-    if (n_pairs > 0xFFFFFFFFull) return set_error(SAS_ERR_ARG, "too many surrogate histories");
-    if (sitems.size() > b->sur_cap) {
-        cudaFree(b->d_sur_items);
-        cudaFree(b->d_sur_prefix);
-        b->d_sur_items = nullptr;
-        b->d_sur_prefix = nullptr;
-        b->sur_cap = 0;
-        SAS_CUDA_B(cudaMalloc(&b->d_sur_items, sitems.size() * sizeof(WorkItem)), "cudaMalloc(items)");
-        SAS_CUDA_B(cudaMalloc(&b->d_sur_prefix, sitems.size() * sizeof(uint32_t)), "cudaMalloc(items)");
-        b->sur_cap = sitems.size();
-    }
-    b->n_sur_items = (uint32_t)sitems.size();
-    b->n_sur_pairs = (uint32_t)n_pairs;
-    if (!sitems.empty()) {
-        SAS_CUDA_B(cudaMemcpy(b->d_sur_items, sitems.data(), sitems.size() * sizeof(WorkItem), cudaMemcpyHostToDevice),
-                   "upload items");
-        SAS_CUDA_B(cudaMemcpy(b->d_sur_prefix, sprefix.data(), sprefix.size() * sizeof(uint32_t),
-                              cudaMemcpyHostToDevice),
-                   "upload items");
+    for (int k = 0; k < 2; ++k) {
+        const std::vector<WorkItem>& si = sitems[k];
+        std::vector<uint32_t> sprefix;
+        const uint64_t n_pairs = surrogate_pair_prefix(si, sprefix);
+        if (n_pairs > 0xFFFFFFFFull) return set_error(SAS_ERR_ARG, "too many surrogate histories");
+        if (si.size() > b->sur_cap[k]) {
+            cudaFree(b->d_sur_items[k]);
+            cudaFree(b->d_sur_prefix[k]);
+            b->d_sur_items[k] = nullptr;
+            b->d_sur_prefix[k] = nullptr;
+            b->sur_cap[k] = 0;
+            SAS_CUDA_B(cudaMalloc(&b->d_sur_items[k], si.size() * sizeof(WorkItem)), "cudaMalloc(items)");
+            SAS_CUDA_B(cudaMalloc(&b->d_sur_prefix[k], si.size() * sizeof(uint32_t)), "cudaMalloc(items)");
+            b->sur_cap[k] = si.size();
+        }
+        b->n_sur_items[k] = (uint32_t)si.size();
+        b->n_sur_pairs[k] = (uint32_t)n_pairs;
+        if (!si.empty()) {
+            SAS_CUDA_B(cudaMemcpy(b->d_sur_items[k], si.data(), si.size() * sizeof(WorkItem), cudaMemcpyHostToDevice),
+                       "upload items");
+            SAS_CUDA_B(cudaMemcpy(b->d_sur_prefix[k], sprefix.data(), sprefix.size() * sizeof(uint32_t),
+                                  cudaMemcpyHostToDevice),
+                       "upload items");
+        }
     }
     return SAS_OK;
 }
@@ -227,18 +231,19 @@ sas_status capture(sas_batch* b)
     cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned int), b->cap);
     if (b->n_items > 0) kern<<<b->grid, b->cfg.block, b->smem, b->cap>>>(P);
     cudaError_t le = cudaGetLastError();
-    if (le == cudaSuccess && b->sur && b->n_sur_items > 0) {
+    for (int k = 0; k < 2; ++k) {
+        if (le != cudaSuccess || !b->sur[k] || b->n_sur_items[k] == 0) continue;
         sur::STParams S;
         std::memset(&S, 0, sizeof(S));
         S.in = b->icf;
-        S.box = surrogate_dbox(b->sur);
-        S.epi = surrogate_epi(b->sur);
+        S.box = surrogate_dbox(b->sur[k]);
+        S.epi = surrogate_epi(b->sur[k]);
         S.seed = b->d_seed;
         S.philox_base = 0;
-        S.items = b->d_sur_items;
-        S.pair_prefix = b->d_sur_prefix;
-        S.n_items = b->n_sur_items;
-        S.n_pairs = b->n_sur_pairs;
+        S.items = b->d_sur_items[k];
+        S.pair_prefix = b->d_sur_prefix[k];
+        S.n_items = b->n_sur_items[k];
+        S.n_pairs = b->n_sur_pairs[k];
         S.sexp = b->d_sexp;
         S.bexp = b->d_exps;
         S.poly = b->d_poly;
@@ -249,8 +254,8 @@ sas_status capture(sas_batch* b)
         S.trans = b->d_trans;
         S.npix = b->npix;
         S.fallbacks = b->d_fallbacks;
-        S.err = surrogate_err(b->sur);
-        le = launch_sur_trace(b->sur, S, b->sm_count, b->cap);
+        S.err = surrogate_err(b->sur[k]);
+        le = launch_sur_trace(b->sur[k], S, b->sm_count, b->cap);
     }
     cudaError_t ce = cudaStreamEndCapture(b->cap, &b->graph);
     if (le != cudaSuccess) return set_cuda_error(le, "batch kernel launch (capture)");
@@ -425,7 +430,11 @@ sas_status sas_read_batch_detector(const sas_batch* b, size_t exp, double* sum_w
     if (transmitted)
         SAS_CUDA_B(cudaMemcpyAsync(transmitted, b->d_trans + exp, 8, cudaMemcpyDeviceToHost, b->stream), "read");
     SAS_CUDA_B(cudaStreamSynchronize(b->stream), "cudaStreamSynchronize");
-    if (b->sur) return surrogate_take_error(b->sur, b->stream);
+    for (int k = 0; k < 2; ++k)
+        if (b->sur[k]) {
+            const sas_status st = surrogate_take_error(b->sur[k], b->stream);
+            if (st != SAS_OK) return st;
+        }
     return SAS_OK;
 }
 
@@ -494,12 +503,14 @@ sas_status sas_batch_attach_surrogate(sas_batch* b, const sas_surrogate* s)
     if (!b) return set_error(SAS_ERR_ARG, "batch is NULL");
     SAS_CUDA_B(cudaStreamSynchronize(b->stream), "sync");
     drop_graph(b);
-    b->sur = s;
+    if (s) b->sur[surrogate_kind(s) == SAS_ELLIPSOID ? 1 : 0] = s;
+    else b->sur[0] = b->sur[1] = nullptr;
     b->use_sur.assign(b->n_exp, 0);
-    if (s) {
+    if (b->sur[0] || b->sur[1]) {
         std::vector<sur::SurExp> se(b->n_exp);
         for (size_t e = 0; e < b->n_exp; ++e) {
-            b->use_sur[e] = surrogate_covers(s, b->models[e]) ? 1 : 0;
+            for (int k = 0; k < 2 && !b->use_sur[e]; ++k)
+                if (surrogate_covers(b->sur[k], b->models[e])) b->use_sur[e] = k + 1;
             se[e] = surrogate_exp(b->models[e], b->use_sur[e] != 0);
         }
         if (!b->d_sexp) {
@@ -562,8 +573,10 @@ sas_status sas_destroy_batch(sas_batch* b)
     cudaFree(b->d_sum_w2);
     cudaFree(b->d_count);
     cudaFree(b->d_trans);
-    cudaFree(b->d_sur_items);
-    cudaFree(b->d_sur_prefix);
+    for (int k = 0; k < 2; ++k) {
+        cudaFree(b->d_sur_items[k]);
+        cudaFree(b->d_sur_prefix[k]);
+    }
     cudaFree(b->d_sexp);
     cudaFree(b->d_fallbacks);
     if (b->cap) cudaStreamDestroy(b->cap);

@@ -8,6 +8,7 @@
 
 namespace sas {
 bool surrogate_covers(const sas_surrogate* s, const sas_model_desc& m);
+int surrogate_kind(const sas_surrogate* s);   // SAS_CYLINDER or SAS_ELLIPSOID
 sur::SurExp surrogate_exp(const sas_model_desc& m, bool in_box);
 // Launches min(sm_count, P.n_pairs) CTAs (one per SM); nothing when there are no pairs.
 cudaError_t launch_sur_trace(const sas_surrogate* s, const sur::STParams& P, int sm_count, cudaStream_t st);

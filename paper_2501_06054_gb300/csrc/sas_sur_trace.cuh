@@ -221,7 +221,9 @@ __device__ __forceinline__ float row_finish(const STParams& P, const RowRec& r, 
         } else {
             const BatchExp& be = P.bexp[pi.exp];
             const float q[3] = {r.q0, r.q1, r.q2};
-            ds = dsigma<float, SAS_CYLINDER>(q, be.mc, P.poly + be.poly_off, P.orient + be.orient_off);
+            ds = P.box.kind == SAS_ELLIPSOID
+                     ? dsigma<float, SAS_ELLIPSOID>(q, be.mc, P.poly + be.poly_off, P.orient + be.orient_off)
+                     : dsigma<float, SAS_CYLINDER>(q, be.mc, P.poly + be.poly_off, P.orient + be.orient_off);
             atomicAdd(P.fallbacks, 1ull);
         }
         const float w = r.pref * ds;

@@ -829,6 +829,7 @@ sur::Box device_box(const sas_surrogate_box& b)
     d.n_poly = b.n_poly;
     d.n_gamma = b.n_gamma;
     d.n_psi = b.n_psi;
+    d.kind = b.model == SAS_ELLIPSOID ? SAS_ELLIPSOID : SAS_CYLINDER;
     return d;
 }
 
@@ -837,14 +838,23 @@ sur::Box device_box(const sas_surrogate_box& b)
 // exposed to sas_api.cu / sas_batch.cu
 namespace sas {
 
+int surrogate_kind(const sas_surrogate* s) { return s->dbox.kind; }
+
+// The body's length along its axis: the cylinder's L, the ellipsoid's 2 R_p.
+static double axial_length(const sas_model_desc& m)
+{
+    return m.kind == SAS_ELLIPSOID ? 2.0 * m.radius_polar : m.length;
+}
+
 bool surrogate_covers(const sas_surrogate* s, const sas_model_desc& m)
 {
-    if (!s || m.kind != SAS_CYLINDER || m.precision != SAS_FP32 || m.isotropic) return false;
+    if (!s || m.kind != s->dbox.kind || m.precision != SAS_FP32 || m.isotropic) return false;
     if (m.sampling != SAS_QUADRATURE || m.poly_dist != SAS_POLY_SCHULZ) return false;   // trained on Schulz averages
     if (m.self_attenuation) return false;   // the surrogate trace attenuates with the instrument's mu only
     const sas_surrogate_box& b = s->box;
     if (m.n_poly != b.n_poly || m.n_gamma != b.n_gamma || m.n_psi != b.n_psi) return false;
-    return m.radius >= b.r_min && m.radius <= b.r_max && m.length >= b.l_min && m.length <= b.l_max &&
+    const double L = axial_length(m);
+    return m.radius >= b.r_min && m.radius <= b.r_max && L >= b.l_min && L <= b.l_max &&
            m.sigma_orient >= b.sigma_orient_min && m.sigma_orient <= b.sigma_orient_max && m.poly >= b.poly_min &&
            m.poly <= b.poly_max && m.sld != m.sld_solvent;
 }
@@ -857,11 +867,12 @@ sur::SurExp surrogate_exp(const sas_model_desc& m, bool in_box)
     e.ny = (float)(std::sin(m.axis_theta) * std::sin(m.axis_phi));
     e.nz = (float)std::cos(m.axis_theta);
     e.R = (float)m.radius;
-    e.L = (float)m.length;
+    e.L = (float)axial_length(m);
     e.so = (float)m.sigma_orient;
     e.sp = (float)m.poly;
-    // <V^2> / <V> of the Schulz distribution: pi L <r^4> / <r^2>,
-    // <r^k> = R^k prod_{j=1..k} (z + j) / (z + 1)^k with z = 1/p^2 - 1
+    // <V^2> / <V> of the Schulz distribution of the radius r: c <r^4> / <r^2>
+    // with V = c r^2 (c = pi L for the cylinder, 4 pi R_p / 3 for the
+    // ellipsoid), <r^k> = R^k prod_{j=1..k} (z + j) / (z + 1)^k, z = 1/p^2 - 1
     double r2 = m.radius * m.radius, r4 = r2 * r2;
     if (m.poly > 0.0) {
         const double z = 1.0 / (m.poly * m.poly) - 1.0;
@@ -869,7 +880,8 @@ sur::SurExp surrogate_exp(const sas_model_desc& m, bool in_box)
         r4 *= (z + 2.0) * (z + 3.0) * (z + 4.0) / ((z + 1.0) * (z + 1.0) * (z + 1.0));
     }
     const double drho = m.sld - m.sld_solvent;
-    e.scale_p = (float)(m.volume_fraction * drho * drho * M_PI * m.length * r4 / r2);
+    const double c = m.kind == SAS_ELLIPSOID ? 4.0 * M_PI * m.radius_polar / 3.0 : M_PI * m.length;
+    e.scale_p = (float)(m.volume_fraction * drho * drho * c * r4 / r2);
     e.in_box = in_box ? 1 : 0;
     return e;
 }
@@ -925,6 +937,8 @@ sas_status sas_create_surrogate(const sas_surrogate_box* box, uint64_t seed, voi
           b.sigma_orient_min > 0 && b.sigma_orient_max >= b.sigma_orient_min && b.poly_min > 0 &&
           b.poly_max >= b.poly_min && b.poly_max < 1.0))
         return set_error(SAS_ERR_ARG, "invalid surrogate box");
+    if (b.model != 0 && b.model != SAS_CYLINDER && b.model != SAS_ELLIPSOID)
+        return set_error(SAS_ERR_ARG, "surrogate model must be SAS_CYLINDER or SAS_ELLIPSOID");
     if (b.n_poly < 1 || b.n_poly > sur::MAX_POLY || b.n_gamma < 1 || b.n_gamma > sur::MAX_GL || b.n_psi < 1 ||
         b.n_psi > sur::MAX_GL || b.n_buckets < 1 || b.n_buckets > sur::MAX_BUCKETS || b.n_fourier < 0 ||
         b.n_fourier > 13)

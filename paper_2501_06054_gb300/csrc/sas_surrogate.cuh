@@ -21,6 +21,7 @@ struct Box {
     float four_w;                        // angular step of the Fourier features of u and v
     int n_four;                          // Fourier pairs of u, and as many of v
     int n_buckets, n_poly, n_gamma, n_psi;
+    int kind;                            // SAS_CYLINDER or SAS_ELLIPSOID (L = 2 R_p)
 };
 
 // Raw parameters of one evaluation: q_par, q_perp (1/A), R, L (A), sigma_orient
@@ -177,10 +178,13 @@ struct Tables {
     const float2* psi_cs;   // [n_psi] (cos, sin) of the psi nodes pi (gl_p + 1)
 };
 
-// Normalised averaged cylinder form factor P = <|F|^2> / (drho^2 <V^2>) at
-// (q_par, q_perp) about the mean axis z, by the same quadrature as the
-// trace (Gaussian cap of width so truncated at 3 so, GL in gamma and psi,
-// Schulz nodes of the bucket). Computed by one warp; every lane returns it.
+// Normalised averaged form factor P = <|F|^2> / (drho^2 <V^2>) of the
+// box's body at (q_par, q_perp) about the mean axis z, by the same
+// quadrature as the trace (Gaussian cap of width so truncated at 3 so, GL
+// in gamma and psi, Schulz nodes of the bucket on the radius). Cylinder:
+// sinc(Q_C L / 2)^2 a(Q_AB r)^2; ellipsoid of revolution (R_p = L / 2 fixed,
+// r polydisperse, V^2 ~ r^4 as for the cylinder): (3 g(x))^2 with
+// x^2 = r^2 Q_AB^2 + R_p^2 Q_C^2. Computed by one warp; every lane returns it.
 __device__ __forceinline__ double exact_pbar_warp(const Box& b, const Tables& t, const Raw& r)
 {
     const int lane = threadIdx.x & 31;
@@ -217,6 +221,25 @@ __device__ __forceinline__ double exact_pbar_warp(const Box& b, const Tables& t,
         const float wo = t.glw_g[i] * sg * __expf(-g * g * inv2s2) * t.glw_p[k];
         const float qc = r.qperp * sg * cp + r.qpar * cg;
         const float qab2 = fmaxf(q2 - qc * qc, 0.0f);
+        if (b.kind == SAS_ELLIPSOID) {
+            const float pol = 0.25f * r.L * r.L * (qc * qc);
+            const float qabR2 = qab2 * R2;
+            const float2* xw = t.poly_x2w + bk * b.n_poly;
+            float inner = 0.f;
+#pragma unroll 4
+            for (int j = 0; j < b.n_poly; ++j) {
+                const float2 v = xw[j];
+                // floored so that Q = 0 takes the series branch
+                const float x2 = fmaxf(fmaf(qabR2, v.x, pol), 1e-30f);
+                const float inv = rsqrtf(x2);
+                const float g = 3.0f * M<float>::sphere_g(x2 * inv, inv);
+                inner = fmaf(v.y, g * g, inner);
+            }
+            num.add(wo * inner);
+            den.add(wo);
+            for (k += 32; k >= b.n_psi; k -= b.n_psi) ++i;
+            continue;
+        }
         const float y = fabsf(qc) * 0.5f * r.L;
         const float sn = M<float>::sinc(y, __fdividef(1.0f, y));
         const float qabR2 = qab2 * R2;

@@ -269,7 +269,7 @@ def surrogate_box(n_fourier=12, n_buckets=32):
     return dict(q_max=0.25, r_min=15.0, r_max=25.0, l_min=300.0, l_max=500.0,
                 sigma_orient_min=math.radians(10.0), sigma_orient_max=math.radians(20.0),
                 poly_min=0.05, poly_max=0.15, n_poly=40, n_gamma=76, n_psi=76,
-                n_buckets=n_buckets, n_fourier=n_fourier, reserved=0)
+                n_buckets=n_buckets, n_fourier=n_fourier, model=CYLINDER)
 
 
 def batched_surrogate_box(n_fourier=12, n_buckets=64):
@@ -285,4 +285,12 @@ def batched_surrogate_box(n_fourier=12, n_buckets=64):
     return dict(q_max=0.115, r_min=10.0, r_max=200.0, l_min=10.0, l_max=200.0,
                 sigma_orient_min=math.radians(1.0), sigma_orient_max=math.radians(30.0),
                 poly_min=0.01, poly_max=0.3, n_poly=40, n_gamma=76, n_psi=76,
-                n_buckets=n_buckets, n_fourier=n_fourier, reserved=0)
+                n_buckets=n_buckets, n_fourier=n_fourier, model=CYLINDER)
+
+
+def batched_ellipsoid_surrogate_box(n_fourier=12, n_buckets=64):
+    """Training box of the learned surrogate for the ellipsoids of the
+    batched workload: equatorial semi-axis R and polar semi-axis R_p in
+    [10, 200] angstrom (the box's length L = 2 R_p in [20, 400]), the other
+    ranges and the quadrature as for the batched cylinders."""
+    return dict(batched_surrogate_box(n_fourier, n_buckets), l_min=20.0, l_max=400.0, model=ELLIPSOID)

@@ -1,9 +1,13 @@
 """Pins of the FP64 surrogate oracle (CPU): forward and gradient against
 torch (float64 autograd, a library routine), the gradient against central
-finite differences of the oracle's own forward, and the bf16 rounding."""
+finite differences of the oracle's own forward, the bf16 rounding, and the
+exact target P against the closed forms it reduces to."""
+import math
+
 import numpy as np
 import pytest
 
+import oracle
 from oracle import mlp as M
 import sas_workloads as W
 
@@ -123,3 +127,32 @@ def test_features_definition():
     assert abs(F[0, 10] - np.sin(u)) < 1e-15 and abs(F[0, 11] - np.cos(u)) < 1e-15
     assert abs(F[0, 12] - np.sin(v / 2)) < 1e-15 and abs(F[0, 15] - np.cos(v)) < 1e-15
     assert F[0, 63] == 1.0 and np.all(F[0, 16:63] == 0)
+
+
+def test_exact_pbar_closed_forms():
+    """The surrogate's target P reduces to closed forms: 1 at Q = 0 for both
+    bodies; for a monodisperse ellipsoid with R_p = R (L = 2R), the sphere's
+    (3 (sin x - x cos x) / x^3)^2 at x = |Q| R whatever the axis spread; for
+    a monodisperse cylinder with an axis spread of 1e-5 rad, the aligned
+    cylinder's (2 J1(q_perp R) / (q_perp R))^2 sinc(q_par L / 2)^2."""
+    from scipy.special import j1
+    oracle.build()
+    R, L = 37.0, 150.0
+    ebox = W.batched_ellipsoid_surrogate_box(n_fourier=4, n_buckets=8)
+    ebox.update(n_poly=12, n_gamma=16, n_psi=16)
+    raw = np.array([[0.0, 0.0, R, 2 * R, math.radians(10), 0.0, 0, 0],
+                    [0.05, 0.03, R, 2 * R, math.radians(10), 0.0, 0, 0],
+                    [0.01, 0.09, R, 2 * R, math.radians(25), 0.0, 0, 0]])
+    x = np.hypot(raw[:, 0], raw[:, 1]) * R
+    with np.errstate(all="ignore"):
+        ref = np.where(x > 0, (3 * (np.sin(x) - x * np.cos(x)) / x ** 3) ** 2, 1.0)
+    assert np.allclose(M.exact_pbar(ebox, raw), ref, rtol=1e-12, atol=0)
+    cbox = W.batched_surrogate_box(n_fourier=4, n_buckets=8)
+    cbox.update(n_poly=12, n_gamma=16, n_psi=16)
+    raw = np.array([[0.0, 0.0, R, L, 1e-5, 0.0, 0, 0],
+                    [0.0, 0.06, R, L, 1e-5, 0.0, 0, 0],
+                    [0.02, 0.05, R, L, 1e-5, 0.0, 0, 0]])
+    x, y = raw[:, 1] * R, raw[:, 0] * L / 2
+    with np.errstate(all="ignore"):
+        ref = (np.where(x > 0, 2 * j1(x) / x, 1.0) * np.where(y > 0, np.sin(y) / y, 1.0)) ** 2
+    assert np.allclose(M.exact_pbar(cbox, raw), ref, rtol=1e-8, atol=0)

@@ -305,11 +305,17 @@ def test_surrogate_trace_falls_back_outside_the_box():
     sas.sas_destroy_surrogate(s)
 
 
-def _network_tally(box, p, inst, m, n, seed, first=0):
+def _axial_length(m):
+    """The body's length along its axis, the surrogate's L: the cylinder's
+    length, twice the ellipsoid's polar semi-axis."""
+    return 2.0 * m.radius_polar if m.kind == W.ELLIPSOID else m.length
+
+
+def _network_tally(box, p, inst, m, n, seed, first=0, exp_id=0):
     """Expected surrogate detector from the oracle alone: oracle geometry
     (pixel, Q, prefactor), the oracle network on the features of Q about the
-    cylinder axis, and <V^2>/<V> from the oracle's Schulz nodes."""
-    g = oracle.geometry_records(inst, n, seed, first=first)
+    body's axis, and <V^2>/<V> from the oracle's Schulz nodes."""
+    g = oracle.geometry_records(inst, n, seed, first=first, exp_id=exp_id)
     sc = g["pixel"] >= 0
     ax = np.array([math.sin(m.axis_theta) * math.cos(m.axis_phi),
                    math.sin(m.axis_theta) * math.sin(m.axis_phi), math.cos(m.axis_theta)])
@@ -319,10 +325,11 @@ def _network_tally(box, p, inst, m, n, seed, first=0):
     assert np.sqrt(np.sum(q * q, axis=1)).max() < box["q_max"]       # every history in the box
     raw = np.zeros((len(qp), 8))
     raw[:, 0], raw[:, 1] = np.abs(qp), qt
-    raw[:, 2], raw[:, 3], raw[:, 4], raw[:, 5] = m.radius, m.length, m.sigma_orient, m.poly
+    raw[:, 2], raw[:, 3], raw[:, 4], raw[:, 5] = m.radius, _axial_length(m), m.sigma_orient, m.poly
     out = M.forward(p, M.features(box, raw))
     prep = oracle.Prepared(m)
-    V = math.pi * prep.poly_r ** 2 * m.length
+    V = (4.0 / 3.0 * math.pi * prep.poly_r ** 2 * m.radius_polar if m.kind == W.ELLIPSOID
+         else math.pi * prep.poly_r ** 2 * m.length)
     scale = m.volume_fraction * (m.sld - m.sld_solvent) ** 2 * float(np.dot(prep.poly_w, V * V)) / float(
         np.dot(prep.poly_w, V))
     w = g["pref"][sc] * scale * np.exp(out)
@@ -462,3 +469,172 @@ def test_exact_targets_batched_box():
     ref = np.maximum(M.exact_pbar(box, raw), M.TARGET_FLOOR)
     assert np.all(np.abs(got - ref) <= 1e-5 * ref + 1e-7), np.max(np.abs(got - ref) / ref)
     sas.sas_destroy_surrogate(s)
+
+
+# ---- the ellipsoid of revolution (same network, L = 2 R_p) --------------
+
+def _small_ell_box(n_fourier=4):
+    b = W.batched_ellipsoid_surrogate_box(n_fourier=n_fourier, n_buckets=8)
+    b.update(n_poly=12, n_gamma=16, n_psi=16)
+    return b
+
+
+def _set_test_params(s, seed):
+    """Random but well-scaled output layer and biases, so that the network
+    output spreads over a few units of log P."""
+    p = sas.sas_surrogate_get_params(s, M.NPARAM)
+    rng = np.random.default_rng(seed)
+    p[M.OFF_W5:M.OFF_B5] = rng.uniform(-1, 1, 256).astype(np.float32) * 0.3
+    p[M.OFF_B1 + 256:M.OFF_W5] = rng.normal(size=768).astype(np.float32) * 0.1
+    p[M.OFF_B5] = -2.0
+    sas.sas_surrogate_set_params(s, p)
+    return p
+
+
+def test_exact_targets_ellipsoid_match_oracle():
+    """Training targets of the ellipsoid surrogate (polar semi-axis L / 2,
+    Schulz-distributed equatorial semi-axis) against the oracle's
+    quadrature: random rows of a small box, Q = 0, and the corners of the
+    batched ellipsoid box (R and R_p up to 200 A at |Q| up to 0.115)."""
+    for box, seed in ((_small_ell_box(), 21), (W.batched_ellipsoid_surrogate_box(), 22)):
+        s = sas.sas_create_surrogate(box, seed=1, stream=torch.cuda.current_stream())
+        raw = _raw(box, 24, seed)
+        raw[0, :2] = 0.0
+        nb = box["n_buckets"]
+        corners = np.array([[0.113, 0.02, 200.0, 400.0, box["sigma_orient_min"], box["poly_min"]],
+                            [0.02, 0.113, 200.0, 20.0, box["sigma_orient_max"], box["poly_max"]],
+                            [0.08, 0.08, 10.0, 400.0, box["sigma_orient_min"], box["poly_max"]]], np.float32)
+        for c in corners:
+            bk = int(round((c[5] - box["poly_min"]) / (box["poly_max"] - box["poly_min"]) * (nb - 1)))
+            row = np.zeros(8, np.float32)
+            row[:6] = c
+            row[5] = np.float32(box["poly_min"] + (box["poly_max"] - box["poly_min"]) * bk / (nb - 1))
+            row[6] = bk
+            raw = np.vstack([raw, row])
+        n = len(raw)
+        rd = torch.tensor(raw, device="cuda")
+        out = torch.empty(n, device="cuda")
+        sas.sas_surrogate_exact(s, rd, n, out)
+        torch.cuda.synchronize()
+        got = np.exp(out.cpu().numpy().astype(np.float64))
+        ref = np.maximum(M.exact_pbar(box, raw), M.TARGET_FLOOR)
+        assert abs(ref[0] - 1.0) < 1e-12
+        assert np.all(np.abs(got - ref) <= 1e-5 * ref + 1e-7), np.max(np.abs(got - ref) / ref)
+        sas.sas_destroy_surrogate(s)
+
+
+def test_ellipsoid_surrogate_trace_tallies_the_network():
+    """The surrogate trace of an ellipsoid of revolution against the oracle
+    geometry weighted by the oracle network (features with L = 2 R_p,
+    <V^2>/<V> of the ellipsoid), as for the cylinder."""
+    box = _small_ell_box()
+    s = sas.sas_create_surrogate(box, seed=7, stream=torch.cuda.current_stream())
+    p = _set_test_params(s, 5)
+    inst = W.instrument(nx=48, ny=40, pixel_x=0.008, pixel_y=0.008)
+    m = W.Model(kind=W.ELLIPSOID, radius=60.0, radius_polar=150.0, sld=2e-6, volume_fraction=0.01, poly=0.1,
+                n_poly=12, sigma_orient=math.radians(14), n_gamma=16, n_psi=16,
+                axis_theta=math.radians(70), axis_phi=math.radians(20))
+    e = sas.Experiment(inst, m, stream=torch.cuda.current_stream())
+    sas.sas_attach_surrogate(e.h, s)
+    fb0 = sas.sas_surrogate_fallbacks(exp=e.h)
+    sas.sas_reset_detector(e.h)
+    n, first = 60000, 123457
+    e.trace_range(first, n, seed=5)
+    d = e.read()
+    assert sas.sas_surrogate_fallbacks(exp=e.h) == fb0
+    ref = _network_tally(box, p, inst, m, n, seed=5, first=first)
+    assert np.array_equal(d["count"].ravel(), ref["count"].astype(np.uint64))
+    got, exp_ = d["sum_w"].ravel(), ref["sum_w"]
+    assert abs(got.sum() - exp_.sum()) <= 3e-3 * exp_.sum()
+    hit = ref["count"] >= 20
+    assert hit.sum() > 100
+    rel = np.abs(got - exp_)[hit] / exp_[hit]
+    assert np.median(rel) < 3e-3, np.median(rel)
+    assert rel.max() < 3e-2, rel.max()
+    assert d["trans"] == pytest.approx(ref["trans"], rel=1e-5)
+    e.close()
+    sas.sas_destroy_surrogate(s)
+
+
+def test_ellipsoid_surrogate_falls_back_outside_the_box():
+    """Histories of an ellipsoid whose |Q| leaves the box take the exact
+    ellipsoid quadrature: the same histories as the oracle's trace, some of
+    them counted as fallbacks, and those pixels' sums equal the oracle's."""
+    box = _small_ell_box()
+    s = sas.sas_create_surrogate(box, seed=3, stream=torch.cuda.current_stream())
+    inst = W.instrument(nx=64, ny=64, pixel_x=0.03, pixel_y=0.03)   # corners reach |Q| = 0.3 > q_max
+    m = W.Model(kind=W.ELLIPSOID, radius=40.0, radius_polar=90.0, sld=2e-6, volume_fraction=0.01, poly=0.1,
+                n_poly=12, sigma_orient=math.radians(15), n_gamma=16, n_psi=16, axis_theta=math.radians(50))
+    e = sas.Experiment(inst, m, stream=torch.cuda.current_stream())
+    sas.sas_attach_surrogate(e.h, s)
+    n = 20000
+    e.trace(n, seed=2)
+    d = e.read()
+    fb = sas.sas_surrogate_fallbacks(exp=e.h)
+    ref = oracle.trace(inst, m, n, seed=2)
+    assert np.array_equal(d["count"], ref["count"].astype(np.uint64))
+    assert 0 < fb < n
+    g = oracle.geometry_records(inst, n, 2)
+    sc = g["pixel"] >= 0
+    qn = np.sqrt(np.sum(g["q"][sc] ** 2, axis=1))
+    npix = inst.nx * inst.ny
+    # histories within rounding of the box edge count as inside (FP32 decides there)
+    inside = np.bincount(g["pixel"][sc], weights=(qn <= box["q_max"] * (1 + 1e-5)).astype(float), minlength=npix)
+    out_only = (inside == 0) & (ref["count"].reshape(-1) > 0)     # pixels reached by fallbacks alone
+    assert out_only.sum() > 50
+    so, got = ref["sum_w"].reshape(-1)[out_only], d["sum_w"].reshape(-1)[out_only]
+    assert np.all(np.abs(got - so) <= 1e-4 * so + 1e-12 * so.max())
+    e.close()
+    sas.sas_destroy_surrogate(s)
+
+
+def test_batch_holds_a_surrogate_per_kind():
+    """A batch holds one cylinder and one ellipsoid surrogate: each serves
+    the in-box experiments of its kind (their tallies are the oracle
+    network's), the rest run the exact quadrature and equal the oracle;
+    attaching a second surrogate of the same kind replaces the first, and
+    NULL detaches both."""
+    cbox, ebox = _small_box(), _small_ell_box()
+    st = torch.cuda.current_stream()
+    sc, se = sas.sas_create_surrogate(cbox, seed=3, stream=st), sas.sas_create_surrogate(ebox, seed=4, stream=st)
+    pc, pe = _set_test_params(sc, 8), _set_test_params(se, 9)
+    inst = W.instrument(nx=32, ny=32, pixel_x=0.008, pixel_y=0.008)
+    com = dict(sld=2e-6, volume_fraction=0.01, n_poly=12, n_gamma=16, n_psi=16, poly=0.1,
+               sigma_orient=math.radians(15), axis_theta=math.radians(60), axis_phi=math.radians(30))
+    models = [W.Model(kind=W.CYLINDER, radius=20.0, length=400.0, **com),          # cylinder surrogate
+              W.Model(kind=W.ELLIPSOID, radius=50.0, radius_polar=120.0, **com),   # ellipsoid surrogate
+              W.Model(kind=W.ELLIPSOID, radius=50.0, radius_polar=250.0, **com),   # 2 R_p out of box
+              W.Model(kind=W.SPHERE, radius=30.0, poly=0.1, n_poly=8)]
+    counts = np.array([30000, 30000, 3000, 5000], np.uint64)
+    b = sas.sas_create_batch(inst, models, counts, stream=st)
+    sas.sas_batch_attach_surrogate(b, sc)
+    assert sas.sas_batch_surrogate_share(b) == (1, 30000)
+    sas.sas_batch_attach_surrogate(b, se)
+    assert sas.sas_batch_surrogate_share(b) == (2, 60000)
+    sas.sas_trace_batch(b, seed=4)
+    npix = inst.nx * inst.ny
+    for e_, box, p in ((0, cbox, pc), (1, ebox, pe)):
+        d = sas.sas_read_batch_detector(b, e_, npix)
+        ref = _network_tally(box, p, inst, models[e_], int(counts[e_]), seed=4, exp_id=e_)
+        assert np.array_equal(d["count"], ref["count"].astype(np.uint64))
+        got, exp_ = d["sum_w"], ref["sum_w"]
+        assert abs(got.sum() - exp_.sum()) <= 3e-3 * exp_.sum()
+        hit = ref["count"] >= 20
+        rel = np.abs(got - exp_)[hit] / exp_[hit]
+        assert hit.sum() > 100 and np.median(rel) < 3e-3 and rel.max() < 3e-2, (e_, np.median(rel), rel.max())
+    for e_ in (2, 3):
+        d = sas.sas_read_batch_detector(b, e_, npix)
+        ref = oracle.trace(inst, models[e_], int(counts[e_]), seed=4, exp_id=e_)
+        assert np.array_equal(d["count"], ref["count"].reshape(-1).astype(np.uint64))
+        so = ref["sum_w"].reshape(-1)
+        big = so > 1e-6 * so.max()
+        assert np.all(np.abs(d["sum_w"] - so)[big] <= 1e-4 * so[big])
+    sc2 = sas.sas_create_surrogate(cbox, seed=5, stream=st)
+    _set_test_params(sc2, 10)
+    sas.sas_batch_attach_surrogate(b, sc2)                          # replaces sc, keeps se
+    assert sas.sas_batch_surrogate_share(b) == (2, 60000)
+    sas.sas_batch_attach_surrogate(b, None)
+    assert sas.sas_batch_surrogate_share(b) == (0, 0)
+    sas.sas_destroy_batch(b)
+    for s in (sc, se, sc2):
+        sas.sas_destroy_surrogate(s)
