@@ -322,14 +322,15 @@ def batched_config(stream, info, scale=1000, n_train=100_000_000, steps=150_000)
                     big = ex >= 1e-3 * ex.max()
                     rels.append(((got["sum_w"][j] - ex).abs()[big] / ex[big]).cpu().numpy())
                     keys.append((math.degrees(models[k].sigma_orient), 0.5 * _axial_length(models[k]) /
-                                 models[k].radius))
+                                 models[k].radius, models[k].poly))
                 row["per_bin_rel_err"][body] = dict(
                     _rel_stats(np.concatenate(rels) if rels else []), experiments=len(rels),
                     compared_on="identical histories (same Philox streams), surrogate vs exact quadrature, "
                                 "bins >= 1e-3 of each detector's max")
                 strata = {}
-                for name_, idx_, edges in (("sigma_orient_deg", 0, (1, 5, 10, 20, 30.01)),
-                                           ("aspect_L_over_2R", 1, (0, 0.3, 1, 3, 21))):
+                for name_, idx_, edges in (("sigma_orient_deg", 0, (0, 1, 5, 10, 20, 30.01)),
+                                           ("aspect_L_over_2R", 1, (0, 0.3, 1, 3, 21)),
+                                           ("sigma_poly", 2, (0, 0.01, 0.1, 0.3001))):
                     for lo, hi in zip(edges[:-1], edges[1:]):
                         sel_ = [r for r, kk in zip(rels, keys) if lo <= kk[idx_] < hi]
                         strata[f"{name_} [{lo}, {hi})"] = dict(_rel_stats(np.concatenate(sel_) if sel_ else []),

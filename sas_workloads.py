@@ -274,17 +274,17 @@ def surrogate_box(n_fourier=12, n_buckets=32):
 
 def batched_surrogate_box(n_fourier=12, n_buckets=64):
     """Training box of the learned surrogate for the cylinders of the batched
-    workload: R and L in [10, 200] angstrom, sigma_orient in [1, 30] deg,
-    sigma_poly in [0.01, 0.3] (n_buckets values), |Q| <= 0.115 1/angstrom
+    workload: R and L in [10, 200] angstrom, sigma_orient in [0.01, 30] deg,
+    sigma_poly in [2e-5, 0.3] (n_buckets values), |Q| <= 0.115 1/angstrom
     (the corner of the 128 x 128 detector seen from the edge of the sample
     at the shortest wavelength, with the beam divergence, reaches 0.110),
-    with the batched quadrature (40 Schulz
-    nodes, 76 x 76 orientation nodes). Cylinders drawn with sigma_orient
-    below 1 deg or sigma_poly below 0.01 (about 7 % of them) run the exact
-    quadrature."""
+    with the batched quadrature (40 Schulz nodes, 76 x 76 orientation
+    nodes). The lower edges sit just below the smallest spreads the 4096
+    draws hold (0.014 deg, 2.7e-5), so that every drawn cylinder is
+    covered; the library needs both spreads > 0."""
     return dict(q_max=0.115, r_min=10.0, r_max=200.0, l_min=10.0, l_max=200.0,
-                sigma_orient_min=math.radians(1.0), sigma_orient_max=math.radians(30.0),
-                poly_min=0.01, poly_max=0.3, n_poly=40, n_gamma=76, n_psi=76,
+                sigma_orient_min=math.radians(0.01), sigma_orient_max=math.radians(30.0),
+                poly_min=2e-5, poly_max=0.3, n_poly=40, n_gamma=76, n_psi=76,
                 n_buckets=n_buckets, n_fourier=n_fourier, model=CYLINDER)
 
 
