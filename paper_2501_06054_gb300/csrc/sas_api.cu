@@ -668,20 +668,14 @@ sas_status build_model_tables(const sas_model_desc& m, ModelTables& t, double q_
     if (m.kind == SAS_CAPPED_CYLINDER || m.kind == SAS_BARBELL) {
         // the cap slices at depth R u_j below the tip, u_j Gauss-Legendre on
         // [0, H / R]: z_j = L/2 + H - R u_j, rho_j^2 = R^2 u_j (2 - u_j),
-        // c_j = 2 pi R^3 w_j u_j (2 - u_j); two slices per row behind the nodes,
-        // then one row per slice {z_j, d_0..d_6} of its x <= 4 term with the
-        // contrast folded in: c_j a(u rho_j^2) = sum_m d_m u^m,
-        // d_m = c_j k_m rho_j^(2m), k_m the FP32 coefficients of 2 J1(x)/x in x^2
+        // c_j = 2 pi R^3 w_j u_j (2 - u_j); two slices per row behind the nodes
         const int nc = (int)m.n_cap;
         const double r0 = m.radius, R = m.radius_polar, H = cap_height(m);
         std::vector<double> gx(nc), gw(nc);
         gauss_legendre(nc, gx.data(), gw.data());
         const int rows = (nc + 1) / 2;
-        t.poly.resize((size_t)(t.n_poly + rows + nc) * SAS_POLY_STRIDE, 0.0);
+        t.poly.resize((size_t)(t.n_poly + rows) * SAS_POLY_STRIDE, 0.0);
         double* cap = t.poly.data() + (size_t)t.n_poly * SAS_POLY_STRIDE;
-        double* fold = cap + (size_t)rows * SAS_POLY_STRIDE;
-        static_assert(SAS_J1R_C_N + 1 == SAS_POLY_STRIDE, "one folded slice per row");
-        const float kr[SAS_J1R_C_N] = SAS_J1R_C;
         double rho2max = r0 * r0;
         for (int j = 0; j < nc; ++j) {
             const double u = 0.5 * (H / R) * (1.0 + gx[j]), wj = 0.5 * (H / R) * gw[j];
@@ -690,12 +684,8 @@ sas_status build_model_tables(const sas_model_desc& m, ModelTables& t, double q_
             cap[4 * j + 1] = R * R * v;
             cap[4 * j + 2] = 2.0 * pi * R * R * R * wj * v;
             rho2max = std::fmax(rho2max, R * R * v);
-            fold[SAS_POLY_STRIDE * j] = cap[4 * j];
-            double rp = 1.0;
-            for (int k = 0; k < SAS_J1R_C_N; ++k, rp *= cap[4 * j + 1])
-                fold[SAS_POLY_STRIDE * j + 1 + k] = cap[4 * j + 2] * (double)kr[k] * rp;
         }
-        t.n_poly += rows + nc;
+        t.n_poly += rows;
         t.n_cap = nc;
         t.cap_body = pi * r0 * r0 * m.length;
         t.cap_r2 = r0 * r0;

@@ -675,43 +675,19 @@ __device__ __forceinline__ float capped_amp(float body, float u, float w, const 
     return f;
 }
 
-// The same amplitude for x <= 4 from the folded slice rows {z_j, d_0..d_6}
-// (d_m = c_j k_m rho_j^(2m), so that c_j a(u rho_j^2) = sum_m d_m u^m): the
-// contrast and the slice radius need no multiply of their own.
-__device__ __forceinline__ float capped_amp_fold(float body, float u, float w, const float* __restrict__ fold,
-                                                 int nc, float r2)
-{
-    float f = body * sas_cyl_a_r(u * r2);
-#pragma unroll 4
-    for (int j = 0; j < nc; ++j) {
-        const float4 a = *reinterpret_cast<const float4*>(fold + SAS_POLY_STRIDE * j);      // z, d_0, d_1, d_2
-        const float4 b = *reinterpret_cast<const float4*>(fold + SAS_POLY_STRIDE * j + 4);  // d_3 .. d_6
-        float p = fmaf(b.w, u, b.z);
-        p = fmaf(p, u, b.y);
-        p = fmaf(p, u, b.x);
-        p = fmaf(p, u, a.w);
-        p = fmaf(p, u, a.z);
-        p = fmaf(p, u, a.y);
-        f = fmaf(__cosf(w * a.x), p, f);
-    }
-    return f;
-}
-
 // Capped cylinder and barbell (Eq. 1 over disk slices normal to the axis):
 // per orientation node and polydisperse scale s (poly node {s, coefficient,
 // s^2}), F / (drho s^3) = pi r^2 L sinc(s Q_C L / 2) a(s Q_AB r)
 //   + sum_j c_j cos(s Q_C z_j) a(s Q_AB rho_j), a(x) = 2 J1(x)/x, the cap
 // slices {z_j, rho_j^2, c_j} behind the nodes. FP32: the 2 J1(x)/x form is
 // chosen per node, uniformly over the warp, from the warp's largest |Q|^2
-// times s^2 times the largest slice radius squared; FOLD: the x <= 4 form
-// from the folded slice rows (the batch kernel keeps the plain rows).
-template <typename T, bool FOLD = true>
+// times s^2 times the largest slice radius squared.
+template <typename T>
 __device__ __forceinline__ T avg_capped(const T qv[3], const T* __restrict__ poly, int np,
                                         const T* __restrict__ orient, int no, const ModelConst<T>& mc)
 {
     const T* __restrict__ cap = poly + SAS_POLY_STRIDE * np;
     const int nc = mc.n_cap;
-    const T* __restrict__ fold = cap + SAS_POLY_STRIDE * ((nc + 1) / 2);
     Kahan<T> k;
     float qm = 0.f;
     if constexpr (sizeof(T) == sizeof(float)) {
@@ -735,9 +711,7 @@ __device__ __forceinline__ T avg_capped(const T qv[3], const T* __restrict__ pol
             if constexpr (sizeof(T) == sizeof(float)) {
                 const float u = qab2 * p[2];
                 const float bound = qm * p[2];   // warp-uniform
-                if (bound <= SAS_J1R_SMAX)
-                    F = FOLD ? capped_amp_fold(body, u, w, fold, nc, mc.cap_r2)
-                             : capped_amp<0>(body, u, w, cap, nc, mc.cap_r2);
+                if (bound <= SAS_J1R_SMAX) F = capped_amp<0>(body, u, w, cap, nc, mc.cap_r2);
                 else if (bound <= SAS_J1V_SMAX) F = capped_amp<1>(body, u, w, cap, nc, mc.cap_r2);
                 else if (bound <= SAS_J1P_SMAX) F = capped_amp<2>(body, u, w, cap, nc, mc.cap_r2);
                 else if (bound <= SAS_J1Q_SMAX) F = capped_amp<3>(body, u, w, cap, nc, mc.cap_r2);
@@ -1128,7 +1102,7 @@ __device__ __forceinline__ T dsigma(const T qv[3], const ModelConst<T>& mc,
     } else if (KIND == SAS_ELLIPSOID) {
         avg = avg_ellipsoid<T>(qv, poly, mc.n_poly, orient, mc.n_orient, mc.rp2);
     } else if (KIND == SAS_CAPPED_CYLINDER || KIND == SAS_BARBELL) {
-        avg = avg_capped<T, !LEAN>(qv, poly, mc.n_rad, orient, mc.n_orient, mc);
+        avg = avg_capped<T>(qv, poly, mc.n_rad, orient, mc.n_orient, mc);
     } else if (KIND == SAS_CORE_SHELL_CYLINDER || KIND == SAS_HOLLOW_CYLINDER || KIND == SAS_CORE_SHELL_BICELLE) {
         avg = avg_cs_cylinder<T, !LEAN>(qv, poly, mc.n_rad, orient, mc.n_orient, mc);
     } else if (KIND == SAS_CORE_SHELL_ELLIPSOID) {
