@@ -312,6 +312,19 @@ static double oracle_shape_independent(const oracle_model *m, double q)
         }
         break;
     }
+    case 13:    /* mass fractal (Mildner-Hall): spheres of radius f_p0, dimension f_p1, cutoff f_p2 */
+    case 14: {  /* fractal aggregate (Teixeira): spheres of radius f_p0, dimension f_p1, cutoff f_p2 */
+        double D = m->f_p1, y = q * m->f_p2, e = D - 1.0, P = oracle_sphere_f(q * m->f_p0);
+        /* transform of r^(D - 3) exp(-r / xi), normalised to 1 at Q = 0 */
+        double M = y < 1e-8 ? 1.0 : sin(e * atan(y)) / (e * y * pow(1.0 + y * y, 0.5 * e));
+        f = P * P * (m->function == 13 ? M : 1.0 + tgamma(D + 1.0) * pow(m->f_p2 / m->f_p0, D) * M);
+        break;
+    }
+    case 15: {  /* spinodal (Furukawa): Qmax = f_p0, exponent g = f_p1 */
+        double x = q / m->f_p0, g = m->f_p1;
+        f = (1.0 + g / 2.0) * x * x / (g / 2.0 + pow(x, 2.0 + g));
+        break;
+    }
     default: {  /* star polymer (Benoit): Rg = f_p0 of the star, f_p1 arms */
         double fa = m->f_p1, v = q2 * m->f_p0 * m->f_p0 * fa / (3.0 * fa - 2.0);
         double deb, g;

@@ -109,6 +109,14 @@ MUTATIONS = {
          [("/ (4.0 * math.pi * EPS0 * dielectric * K_B * temperature)", "/ (4.0 * math.pi * EPS0 * K_B * temperature)")]),
     34: ("MSA closure with h = 0 in the core instead of -1", "percus", "test_msa_oracle.py", MSA,
          [("    inner = -1.0\n", "    inner = 0.0\n")]),
+    35: ("fractal factor with D instead of D - 1 in the sine", "mass_fractal", "test_shape_independent_oracle.py",
+         C, [("sin(e * atan(y)) / (e * y * pow(1.0 + y * y, 0.5 * e))",
+              "sin(D * atan(y)) / (D * y * pow(1.0 + y * y, 0.5 * e))")]),
+    36: ("Teixeira's aggregate with Gamma(D) instead of Gamma(D + 1)", "fractal_aggregate",
+         "test_shape_independent_oracle.py", C,
+         [("1.0 + tgamma(D + 1.0) * pow(m->f_p2 / m->f_p0, D) * M", "1.0 + tgamma(D) * pow(m->f_p2 / m->f_p0, D) * M")]),
+    37: ("spinodal peak without its normalisation 1 + g/2", "spinodal", "test_shape_independent_oracle.py", C,
+         [("f = (1.0 + g / 2.0) * x * x / (g / 2.0 + pow(x, 2.0 + g));", "f = x * x / (g / 2.0 + pow(x, 2.0 + g));")]),
 }
 
 

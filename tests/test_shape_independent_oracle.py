@@ -10,7 +10,14 @@ dSigma/dOmega = f_scale f(|Q|).
   Lorentzian halves at Q = 1/xi; Teubner-Strey with c2 = 0 is a
   Lorentzian; the power law scales as 2^-m per octave; the Gaussian peak
   has its maximum at Q0 and its half width at half maximum sigma sqrt(2 ln 2);
-* every form depends on |Q| only.
+* every form depends on |Q| only;
+* the fractal factor of the mass fractal and of Teixeira's aggregate is
+  the normalised three-dimensional transform of r^(D - 3) exp(-r / xi),
+  integrated numerically (scipy's QAWF Fourier quadrature), times the
+  sphere factor (scipy's spherical Bessel j1); Teixeira's S(0) =
+  1 + Gamma(D + 1) (xi / R0)^D;
+* the spinodal peak has its maximum 1 at Qmax and slopes 2 and -g in
+  log-log below and above it.
 """
 import math
 
@@ -82,7 +89,9 @@ def test_power_law_and_gaussian_peak():
 
 
 @pytest.mark.parametrize("function,params", [(W.GUINIER, (30.0,)), (W.GAUSS_COIL, (30.0,)), (W.DAB, (20.0,)),
-                                             (W.TEUBNER_STREY, (1.0, -200.0, 2e4))])
+                                             (W.TEUBNER_STREY, (1.0, -200.0, 2e4)),
+                                             (W.MASS_FRACTAL, (12.0, 2.3, 150.0)),
+                                             (W.FRACTAL, (5.0, 2.1, 120.0)), (W.SPINODAL, (0.03, 3.0))])
 def test_isotropy(function, params):
     m = _m(function, **{f"f_p{i}": v for i, v in enumerate(params)})
     d = np.random.default_rng(4).normal(size=(30, 3))
@@ -224,3 +233,63 @@ def test_star_polymer_against_a_discrete_gaussian_star():
     qs = np.array([1e-3, 0.01, 0.05, 0.2])
     assert np.allclose(_p(two, qs), _p(coil, qs), rtol=1e-12)
     assert np.allclose(_p(one, qs), _p(coil, qs), rtol=1e-12)
+
+
+# ---- fractals (mass fractal, Teixeira's aggregate) and the spinodal peak
+
+def _fractal_transform(q, d, xi):
+    """(1 / Gamma(D) xi^D) int_0^inf r^(D-1) exp(-r / xi) sin(q r) / (q r) dr,
+    the normalised 3D transform of r^(D-3) exp(-r / xi), by QAWF."""
+    from scipy import integrate
+    # [0, xi] by plain adaptive quadrature (the integrand ~ q r^(D-1) at 0),
+    # the tail by the Fourier quadrature
+    head, _ = integrate.quad(lambda r: r ** (d - 2.0) * math.exp(-r / xi) * math.sin(q * r), 0.0, xi, limit=400,
+                             epsabs=0.0, epsrel=1e-10)
+    tail, _ = integrate.quad(lambda r: r ** (d - 2.0) * math.exp(-r / xi), xi, np.inf, weight="sin", wvar=q,
+                             limlst=200)
+    return (head + tail) / (q * math.gamma(d) * xi ** d)
+
+
+def _sphere_p(x):
+    from scipy.special import spherical_jn
+    return (3.0 * spherical_jn(1, x) / x) ** 2
+
+
+@pytest.mark.parametrize("d", [1.5, 2.0, 2.6, 3.0])
+def test_mass_fractal_is_the_transform_of_its_correlation(d):
+    xi = 37.0
+    pure = _m(W.MASS_FRACTAL, f_p0=0.0, f_p1=d, f_p2=xi, f_scale=1.0)
+    qs = np.array([0.3, 2.0, 15.0, 90.0]) / xi
+    got = _p(pure, qs)
+    ref = np.array([_fractal_transform(q, d, xi) for q in qs])
+    assert np.allclose(got, ref, rtol=1e-8, atol=0), (got, ref)
+    assert abs(_p(pure, 1e-9)[0] - 1.0) < 1e-12
+    r = 14.0                                                       # with building blocks of radius r
+    blocks = _m(W.MASS_FRACTAL, f_p0=r, f_p1=d, f_p2=xi, f_scale=1.0)
+    assert np.allclose(_p(blocks, qs), ref * _sphere_p(qs * r), rtol=1e-8, atol=0)
+
+
+@pytest.mark.parametrize("d,xi,r0", [(1.8, 90.0, 6.0), (2.5, 200.0, 12.0)])
+def test_fractal_aggregate_against_its_pair_correlation(d, xi, r0):
+    """S(Q) = 1 + (D / R0^D) int r^(D-1) exp(-r / xi) sin(Q r) / (Q r) dr
+    (Teixeira's pair correlation of the aggregate), times the sphere factor
+    of the building blocks."""
+    m = _m(W.FRACTAL, f_p0=r0, f_p1=d, f_p2=xi, f_scale=1.0)
+    qs = np.array([0.001, 0.01, 0.05, 0.2])
+    s_ref = 1.0 + d / r0 ** d * math.gamma(d) * xi ** d * np.array([_fractal_transform(q, d, xi) for q in qs])
+    assert np.allclose(_p(m, qs), s_ref * _sphere_p(qs * r0), rtol=1e-8, atol=0)
+    assert _p(m, 1e-9)[0] == pytest.approx(1.0 + math.gamma(d + 1.0) * (xi / r0) ** d, rel=1e-9)
+
+
+@pytest.mark.parametrize("g", [2.0, 3.0, 4.0])
+def test_spinodal_peak(g):
+    qmax = 0.031
+    m = _m(W.SPINODAL, f_p0=qmax, f_p1=g, f_scale=1.0)
+    assert abs(_p(m, qmax)[0] - 1.0) < 1e-14
+    grid = qmax * np.linspace(0.5, 1.5, 2001)
+    v = _p(m, grid)
+    assert abs(grid[np.argmax(v)] - qmax) <= qmax * 5e-4 and v.max() <= 1.0 + 1e-14
+    lo = _p(m, [1e-6 * qmax, 2e-6 * qmax])
+    assert lo[1] / lo[0] == pytest.approx(4.0, rel=1e-5)            # Q^2 below the peak
+    hi = _p(m, [1e4 * qmax, 2e4 * qmax])
+    assert math.log2(hi[0] / hi[1]) == pytest.approx(g, rel=1e-4)   # Q^-g above it
