@@ -71,7 +71,7 @@ enum { SAS_SPHERE = 0, SAS_CORE_SHELL = 1, SAS_CYLINDER = 2, SAS_ELLIPSOID = 3,
 enum { SAS_FN_GUINIER = 0, SAS_FN_GAUSS_COIL = 1, SAS_FN_LORENTZ = 2, SAS_FN_DAB = 3, SAS_FN_POWER_LAW = 4,
        SAS_FN_GAUSS_PEAK = 5, SAS_FN_TEUBNER_STREY = 6, SAS_FN_PEAK_LORENTZ = 7, SAS_FN_TWO_POWER_LAW = 8,
        SAS_FN_GUINIER_POROD = 9, SAS_FN_GAUSS_LORENTZ_GEL = 10, SAS_FN_POLY_GAUSS_COIL = 11,
-       SAS_FN_STAR_POLYMER = 12 };
+       SAS_FN_STAR_POLYMER = 12, SAS_FN_MASS_FRACTAL = 13, SAS_FN_FRACTAL = 14, SAS_FN_SPINODAL = 15 };
 /* largest Gauss-Legendre rule over an end cap */
 #define SAS_MAX_CAP_NODES 64
 enum { SAS_SQ_NONE = 0, SAS_SQ_HARD_SPHERE_PY = 1, SAS_SQ_HAYTER_MSA = 2 };
@@ -250,7 +250,19 @@ typedef struct sas_model_desc {
      *                                                              f_p0 = Rg > 0, f_p1 = U = Mw/Mn - 1 >= 0
      *   SAS_FN_STAR_POLYMER   star of f Gaussian arms: (D(v) + (f - 1) g(v)^2) / f, D Debye's
      *                         function, g(v) = (1 - exp(-v)) / v, v = (Q Rg)^2 f / (3f - 2)
-     *                                                              f_p0 = Rg (of the star) > 0, f_p1 = f >= 1 */
+     *                                                              f_p0 = Rg (of the star) > 0, f_p1 = f >= 1
+     *   SAS_FN_MASS_FRACTAL   spheres of radius R in a mass fractal of dimension D and cutoff xi:
+     *                         P(Q R) M(Q xi; D), P(x) = (3 (sin x - x cos x) / x^3)^2 (1 at R = 0),
+     *                         M(y; D) = sin((D - 1) atan y) / ((D - 1) y (1 + y^2)^((D - 1) / 2)),
+     *                         the transform of r^(D - 3) exp(-r / xi) normalised to M(0) = 1
+     *                                                              f_p0 = R >= 0, f_p1 = D in (1, 6),
+     *                                                              f_p2 = xi > 0
+     *   SAS_FN_FRACTAL        Teixeira's fractal aggregate of spheres of radius R0:
+     *                         P(Q R0) (1 + Gamma(D + 1) (xi / R0)^D M(Q xi; D))
+     *                                                              f_p0 = R0 > 0, f_p1 = D in (1, 6),
+     *                                                              f_p2 = xi > 0
+     *   SAS_FN_SPINODAL       Furukawa's spinodal peak: (1 + g/2) x^2 / (g/2 + x^(2 + g)),
+     *                         x = Q / Qmax (1 at Q = Qmax)         f_p0 = Qmax > 0, f_p1 = g > 0 */
     int64_t function;
     double f_scale;          /* >= 0 */
     double f_p0, f_p1, f_p2;

@@ -879,6 +879,14 @@ ModelConst<T> model_const(const sas_model_desc& m, const ModelTables& t)
             break;
         case SAS_FN_POLY_GAUSS_COIL: c.f_a = (T)(p0 * p0 / (1.0 + 2.0 * p1)); c.f_b = (T)p1; break;
         case SAS_FN_STAR_POLYMER: c.f_a = (T)(p0 * p0 * p1 / (3.0 * p1 - 2.0)); c.f_b = (T)p1; break;
+        case SAS_FN_MASS_FRACTAL: c.f_a = (T)p0; c.f_b = (T)(p1 - 1.0); c.f_c = (T)m.f_p2; break;
+        case SAS_FN_FRACTAL:   // f_d = Gamma(D + 1) (xi / R0)^D
+            c.f_a = (T)p0;
+            c.f_b = (T)(p1 - 1.0);
+            c.f_c = (T)m.f_p2;
+            c.f_d = (T)(std::tgamma(p1 + 1.0) * std::pow(m.f_p2 / p0, p1));
+            break;
+        case SAS_FN_SPINODAL: c.f_a = (T)(1.0 / p0); c.f_b = (T)p1; c.f_c = (T)(0.5 * p1); c.f_d = (T)(1.0 + 0.5 * p1); break;
         default: c.f_a = (T)m.f_p0; c.f_b = (T)m.f_p1; c.f_c = (T)m.f_p2; break;
         }
     }
@@ -958,7 +966,7 @@ sas_status validate_model(const sas_model_desc* m)
     if (!m) return fail(SAS_ERR_ARG, "model is NULL");
     if (m->kind < 0 || m->kind > 14) return fail(SAS_ERR_ARG, "unknown model kind");
     if (m->kind == SAS_SHAPE_INDEPENDENT) {
-        if (m->function < SAS_FN_GUINIER || m->function > SAS_FN_STAR_POLYMER)
+        if (m->function < SAS_FN_GUINIER || m->function > SAS_FN_SPINODAL)
             return fail(SAS_ERR_ARG, "unknown shape-independent function");
         if (!finite_all({m->f_scale, m->f_p0, m->f_p1, m->f_p2}) || m->f_scale < 0.0)
             return fail(SAS_ERR_ARG, "f_scale must be finite and >= 0, f_p0..f_p2 finite");
@@ -980,6 +988,15 @@ sas_status validate_model(const sas_model_desc* m)
             return fail(SAS_ERR_ARG, "polydisperse coil needs Rg > 0 and U = Mw/Mn - 1 >= 0");
         if (fn == SAS_FN_STAR_POLYMER && !(m->f_p0 > 0.0 && m->f_p1 >= 1.0))
             return fail(SAS_ERR_ARG, "star polymer needs Rg > 0 and at least one arm");
+        if ((fn == SAS_FN_MASS_FRACTAL || fn == SAS_FN_FRACTAL) &&
+            !((fn == SAS_FN_FRACTAL ? m->f_p0 > 0.0 : m->f_p0 >= 0.0) && m->f_p1 > 1.0 && m->f_p1 < 6.0 &&
+              m->f_p2 > 0.0))
+            return fail(SAS_ERR_ARG, "fractals need a sphere radius (> 0 for Teixeira's, >= 0 for the mass "
+                                     "fractal), 1 < D < 6 and a cutoff xi > 0");
+        if (fn == SAS_FN_FRACTAL && !std::isfinite(std::tgamma(m->f_p1 + 1.0) * std::pow(m->f_p2 / m->f_p0, m->f_p1)))
+            return fail(SAS_ERR_ARG, "fractal: Gamma(D + 1) (xi / R0)^D overflows");
+        if (fn == SAS_FN_SPINODAL && !(m->f_p0 > 0.0 && m->f_p1 > 0.0))
+            return fail(SAS_ERR_ARG, "spinodal needs Qmax > 0 and an exponent g > 0");
         if (m->sq_kind != SAS_SQ_NONE || m->sampling != SAS_QUADRATURE || m->self_attenuation != 0)
             return fail(SAS_ERR_ARG, "shape-independent laws take no S(Q), per-event sampling or self-attenuation");
     }

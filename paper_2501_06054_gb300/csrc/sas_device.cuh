@@ -1032,6 +1032,38 @@ __device__ __forceinline__ T y_minus_log1p(T y)
     return y - log1p(y);
 }
 
+// Sphere factor (3 (sin x - x cos x) / x^3)^2, x = q r (1 at r = 0): the
+// series to x^8 below x = 0.5 (truncation 2e-12 relative), CUDA's accurate
+// sincos above (one evaluation per history, so no special-function-unit form).
+template <typename T>
+__device__ __forceinline__ T si_sphere_p(T q, T r)
+{
+    const T x = q * r;
+    T g;
+    if (x < (T)0.5) {
+        const T t = x * x;
+        g = fma(t, fma(t, fma(t, fma(t, (T)(1.0 / 3991680.0), (T)(-1.0 / 45360.0)), (T)(1.0 / 840.0)),
+                       (T)(-1.0 / 30.0)), (T)(1.0 / 3.0));
+    } else {
+        T s, c;
+        sincos(x, &s, &c);
+        g = (s - x * c) / (x * x * x);
+    }
+    const T a = (T)3 * g;
+    return a * a;
+}
+
+// Fractal factor M(y; D) = sin(e atan y) / (e y (1 + y^2)^(e/2)), e = D - 1 > 0,
+// as (sin z / z)(atan y / y)(1 + y^2)^(-e/2) with z = e atan y (M(0) = 1).
+template <typename T>
+__device__ __forceinline__ T fractal_m(T y, T e)
+{
+    if (y < (T)1e-30) return (T)1;
+    const T th = atan(y);
+    const T z = e * th;
+    return (sin(z) / z) * (th / y) * pow(fma(y, y, (T)1), (T)-0.5 * e);
+}
+
 template <typename T>
 __device__ __forceinline__ T shape_independent(T q2, T q, const ModelConst<T>& mc)
 {
@@ -1069,6 +1101,14 @@ __device__ __forceinline__ T shape_independent(T q2, T q, const ModelConst<T>& m
         const T t = U > (T)0 ? log1p(y) / U : x;
         const T h = U > (T)0 ? y_minus_log1p<T>(y) / U : (T)0;
         return (t * t * debye_fn<T>(t) + (T)2 * h) / (((T)1 + U) * x * x);
+    }
+    case SAS_FN_MASS_FRACTAL:     // f_a = R, f_b = D - 1, f_c = xi
+        return si_sphere_p<T>(q, mc.f_a) * fractal_m<T>(q * mc.f_c, mc.f_b);
+    case SAS_FN_FRACTAL:          // f_a = R0, f_b = D - 1, f_c = xi, f_d = Gamma(D + 1) (xi / R0)^D
+        return si_sphere_p<T>(q, mc.f_a) * fma(mc.f_d, fractal_m<T>(q * mc.f_c, mc.f_b), (T)1);
+    case SAS_FN_SPINODAL: {       // f_a = 1 / Qmax, f_b = g, f_c = g / 2, f_d = 1 + g / 2
+        const T x = q * mc.f_a;
+        return mc.f_d * x * x / (mc.f_c + pow(x, (T)2 + mc.f_b));
     }
     default: {                    // star polymer: f_a = Rg^2 f / (3f - 2), f_b = f
         const T v = q2 * mc.f_a;

@@ -9,8 +9,12 @@ T1 alone (FP32 1e-5, FP64 1e-10): an absolute floor taken from their
 largest value would exceed most of the values themselves (the power law
 spans 14 decades from |Q| = 1e-4 to 1). The laws with a finite forward
 value whose tails fall below FP32's range (Guinier, Gaussian coil) or
-vanish away from a peak (Gaussian peak) keep T1's absolute part, 1e-7 of
-their forward (peak) value, the same rule as the form factors' 1e-7 P(0)."""
+vanish away from a peak (Gaussian peak), and the fractals whose building
+blocks' sphere factor has zeros on the grid, keep T1's absolute part, 1e-7
+of their forward (peak) value, the same rule as the form factors' 1e-7
+P(0). The fractals of 2 A blocks (no zero below |Q| = 1, five decades at
+most) and the spinodal peak (no zero for |Q| > 0) are held to the relative
+part."""
 import numpy as np
 import pytest
 
@@ -31,7 +35,8 @@ def _cuda():
 
 # laws held to the relative tolerance alone (no zeros, no underflow on the grid)
 RELATIVE_ONLY = {"lorentz", "dab", "power_law", "teubner_strey", "peak_lorentz", "two_power_law",
-                 "guinier_porod", "guinier_porod_rod", "gauss_lorentz_gel", "poly_coil", "star"}
+                 "guinier_porod", "guinier_porod_rod", "gauss_lorentz_gel", "poly_coil", "star",
+                 "mass_fractal", "fractal", "spinodal"}
 
 LAWS = {
     "guinier": (W.GUINIER, (40.0, 0.0, 0.0)),
@@ -48,6 +53,11 @@ LAWS = {
     "gauss_lorentz_gel": (W.GAUSS_LORENTZ_GEL, (80.0, 25.0, 0.3)),
     "poly_coil": (W.POLY_GAUSS_COIL, (50.0, 0.5, 0.0)),
     "star": (W.STAR_POLYMER, (40.0, 6.0, 0.0)),
+    # building blocks of 2 A: no zero of the sphere factor below |Q| = 1 (relative only)
+    "mass_fractal": (W.MASS_FRACTAL, (2.0, 2.0, 100.0)),
+    "mass_fractal_blocks": (W.MASS_FRACTAL, (25.0, 2.6, 300.0)),
+    "fractal": (W.FRACTAL, (2.0, 2.1, 120.0)),
+    "spinodal": (W.SPINODAL, (0.03, 3.0, 0.0)),
 }
 
 
@@ -93,7 +103,8 @@ def _records(e, first, n, seed):
 
 
 @pytest.mark.parametrize("name,precision", [("coil", W.FP32), ("dab", W.FP64), ("teubner_strey", W.FP32),
-                                            ("poly_coil", W.FP32), ("star", W.FP64), ("guinier_porod", W.FP32)])
+                                            ("poly_coil", W.FP32), ("star", W.FP64), ("guinier_porod", W.FP32),
+                                            ("fractal", W.FP32), ("spinodal", W.FP64)])
 def test_records_and_trace(name, precision):
     m = _m(name, precision)
     inst = W.instrument(nx=64, ny=64)
@@ -115,7 +126,10 @@ def test_records_and_trace(name, precision):
     e.close()
 
 
-@pytest.mark.parametrize("bad", [dict(function=13), dict(f_p0=0.0), dict(f_scale=-1.0),
+@pytest.mark.parametrize("bad", [dict(function=16), dict(f_p0=0.0), dict(f_scale=-1.0),
+                                 dict(function=W.MASS_FRACTAL, f_p0=10.0, f_p1=1.0, f_p2=50.0),
+                                 dict(function=W.FRACTAL, f_p0=0.0, f_p1=2.0, f_p2=50.0),
+                                 dict(function=W.SPINODAL, f_p0=0.03, f_p1=0.0),
                                  dict(sampling=W.PER_EVENT), dict(self_attenuation=1),
                                  dict(sq_kind=W.SQ_HARD_SPHERE_PY, sq_radius=10.0, sq_fraction=0.1)])
 def test_refusals(bad):
