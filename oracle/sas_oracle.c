@@ -248,6 +248,40 @@ double oracle_sq_py(double q, double radius, double phi)
 
 static double sphere_volume(double r) { return 4.0 / 3.0 * PI * r * r * r; }
 
+/* x^-a gamma(a, x) = x^-a int_0^x t^(a-1) e^-t dt, the scaled lower
+ * incomplete gamma function (a > 0, x > 0): the power series
+ * e^-x sum_n x^n / (a (a+1) ... (a+n)) (Abramowitz-Stegun 6.5.29) for
+ * x < a + 1; above, Gamma(a) x^-a - e^-x CF(a, x) with the continued
+ * fraction of Gamma(a, x) (A-S 6.5.31, even part) evaluated by Lentz's
+ * method. */
+static double oracle_scaled_lower_gamma(double a, double x)
+{
+    if (x < a + 1.0) {
+        double term = 1.0 / a, sum = term;
+        for (int n = 1; n < 1000 && term > 1e-18 * sum; ++n) {
+            term *= x / (a + n);
+            sum += term;
+        }
+        return exp(-x) * sum;
+    }
+    /* Gamma(a, x) = e^-x x^a / (x + 1 - a - 1 (1 - a) / (x + 3 - a - 2 (2 - a) / (x + 5 - a - ...))) */
+    const double tiny = 1e-300;
+    double b = x + 1.0 - a, f = 1.0 / b, C = 1.0 / tiny, D = 1.0 / b;
+    for (int i = 1; i < 1000; ++i) {
+        double an = -i * (i - a);
+        b += 2.0;
+        D = an * D + b;
+        if (fabs(D) < tiny) D = tiny;
+        C = b + an / C;
+        if (fabs(C) < tiny) C = tiny;
+        D = 1.0 / D;
+        double delta = C * D;
+        f *= delta;
+        if (fabs(delta - 1.0) < 1e-16) break;
+    }
+    return tgamma(a) * pow(x, -a) - exp(-x) * f;
+}
+
 /* Scattering cross section per unit volume dSigma/dOmega(Q) in 1/angstrom:
  * (phi / <V>) <|F|^2> S(Q), F = drho V f, averages over the polydispersity
  * nodes (and, for the uniaxial models, over the orientation nodes).      */
@@ -323,6 +357,15 @@ static double oracle_shape_independent(const oracle_model *m, double q)
     case 15: {  /* spinodal (Furukawa): Qmax = f_p0, exponent g = f_p1 */
         double x = q / m->f_p0, g = m->f_p1;
         f = (1.0 + g / 2.0) * x * x / (g / 2.0 + pow(x, 2.0 + g));
+        break;
+    }
+    case 16: {  /* polymer with excluded volume (Hammouda): Rg = f_p0, Porod exponent m = 1/nu = f_p1;
+                   P = 2 int_0^1 (1 - x) exp(-U x^(2 nu)) dx, U = Q^2 Rg^2 (2 nu + 1)(2 nu + 2) / 6,
+                   = m (U^(-m/2) gamma(m/2, U) - U^(-m) gamma(m, U)) */
+        double mp = m->f_p1, nu = 1.0 / mp;
+        double U = q2 * m->f_p0 * m->f_p0 * (2.0 * nu + 1.0) * (2.0 * nu + 2.0) / 6.0;
+        f = U < 1e-300 ? 1.0
+                       : mp * (oracle_scaled_lower_gamma(0.5 * mp, U) - oracle_scaled_lower_gamma(mp, U));
         break;
     }
     default: {  /* star polymer (Benoit): Rg = f_p0 of the star, f_p1 arms */

@@ -115,6 +115,10 @@ MUTATIONS = {
     36: ("Teixeira's aggregate with Gamma(D) instead of Gamma(D + 1)", "fractal_aggregate",
          "test_shape_independent_oracle.py", C,
          [("1.0 + tgamma(D + 1.0) * pow(m->f_p2 / m->f_p0, D) * M", "1.0 + tgamma(D) * pow(m->f_p2 / m->f_p0, D) * M")]),
+    38: ("excluded-volume chain with U = (Q Rg)^2 (the Rg factor dropped)", "excluded_volume",
+         "test_shape_independent_oracle.py", C,
+         [("double U = q2 * m->f_p0 * m->f_p0 * (2.0 * nu + 1.0) * (2.0 * nu + 2.0) / 6.0;",
+           "double U = q2 * m->f_p0 * m->f_p0;")]),
     37: ("spinodal peak without its normalisation 1 + g/2", "spinodal", "test_shape_independent_oracle.py", C,
          [("f = (1.0 + g / 2.0) * x * x / (g / 2.0 + pow(x, 2.0 + g));", "f = x * x / (g / 2.0 + pow(x, 2.0 + g));")]),
 }

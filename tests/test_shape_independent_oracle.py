@@ -17,7 +17,11 @@ dSigma/dOmega = f_scale f(|Q|).
   sphere factor (scipy's spherical Bessel j1); Teixeira's S(0) =
   1 + Gamma(D + 1) (xi / R0)^D;
 * the spinodal peak has its maximum 1 at Qmax and slopes 2 and -g in
-  log-log below and above it.
+  log-log below and above it;
+* the chain with excluded volume is Hammouda's integral
+  2 int_0^1 (1 - x) exp(-U x^(2 nu)) dx (scipy's adaptive quadrature), is
+  Debye's function at nu = 1/2, has the Guinier slope -Rg^2/3 and the
+  log-log slope -1/nu at large Q.
 """
 import math
 
@@ -293,3 +297,38 @@ def test_spinodal_peak(g):
     assert lo[1] / lo[0] == pytest.approx(4.0, rel=1e-5)            # Q^2 below the peak
     hi = _p(m, [1e4 * qmax, 2e4 * qmax])
     assert math.log2(hi[0] / hi[1]) == pytest.approx(g, rel=1e-4)   # Q^-g above it
+
+
+# ---- the chain with excluded volume (Hammouda)
+
+def _pev(rg, m, qs):
+    return _p(_m(W.POLYMER_EXCL_VOLUME, f_p0=rg, f_p1=m, f_scale=1.0), qs)
+
+
+@pytest.mark.parametrize("m", [5.0 / 3.0, 2.5, 3.0, 4.5])
+def test_excluded_volume_chain_is_hammoudas_integral(m):
+    from scipy import integrate
+    rg, nu = 40.0, 1.0 / m
+    qs = np.array([1e-4, 0.01, 0.05, 0.2, 1.0])
+    got = _pev(rg, m, qs)
+    for q, g in zip(qs, got):
+        u = q * q * rg * rg * (2 * nu + 1) * (2 * nu + 2) / 6.0
+        # x = y^p, p = 1 / (2 nu): the exponent becomes -u y, the layer where it
+        # falls has width 1/u in y
+        p = 0.5 / nu
+        pts = [c / u for c in (0.1, 1.0, 10.0, 100.0) if c / u < 1.0] or None
+        ref, _ = integrate.quad(lambda y: 2.0 * (1.0 - y ** p) * math.exp(-u * y) * p * y ** (p - 1.0), 0.0, 1.0,
+                                epsabs=0.0, epsrel=1e-13, limit=2000, points=pts)
+        assert g == pytest.approx(ref, rel=1e-10), (m, q)
+
+
+def test_excluded_volume_chain_limits():
+    rg = 35.0
+    qs = np.array([0.003, 0.02, 0.1, 0.4])
+    u = (qs * rg) ** 2                                              # nu = 1/2: Debye's function of (Q Rg)^2
+    assert np.allclose(_pev(rg, 2.0, qs), 2.0 * (np.exp(-u) - 1.0 + u) / u ** 2, rtol=1e-12, atol=0)
+    for m in (5.0 / 3.0, 3.0):
+        q = 1e-4                                                    # Guinier: 1 - Q^2 Rg^2 / 3
+        assert (1.0 - _pev(rg, m, q)[0]) / (q * q * rg * rg / 3.0) == pytest.approx(1.0, rel=1e-4)
+        hi = _pev(rg, m, [20.0, 40.0])                              # Q^-m far beyond 1/Rg, up to the
+        assert math.log2(hi[0] / hi[1]) == pytest.approx(m, rel=1e-4)   # second term's U^(-m/2) ~ 1e-5
