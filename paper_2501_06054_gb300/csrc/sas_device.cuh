@@ -838,28 +838,29 @@ __device__ __forceinline__ T avg_cs_cylinder(const T qv[3], const T* __restrict_
             k.add(c[3] * inner);
         }
         return k.s;
-    }
-    for (int o = 0; o < no; ++o) {
-        const T* c = orient + 4 * o;
-        const T qc = fma(qv[0], c[0], fma(qv[1], c[1], qv[2] * c[2]));
-        const T x0 = fma(qv[1], c[2], -qv[2] * c[1]);
-        const T x1 = fma(qv[2], c[0], -qv[0] * c[2]);
-        const T x2 = fma(qv[0], c[1], -qv[1] * c[0]);
-        const T qab2 = fma(x0, x0, fma(x1, x1, x2 * x2));
-        const T y1 = fabs(qc) * mc.half_length, y2 = fabs(qc) * mc.half_length_o;
-        const T s1 = M<T>::sinc(y1, M<T>::rcp(y1)), s2 = M<T>::sinc(y2, M<T>::rcp(y2));
-        T inner = 0;
-        const T qab = M<T>::sqrt_(qab2), iq = M<T>::rcp(qab);
-        for (int i = 0; i < np; ++i) {
-            const T* p = poly + SAS_POLY_STRIDE * i;
-            const T xa = qab * p[6], xb = qab * p[7];
-            const T F = fma(s1, p[2], s2 * p[3]) * M<T>::cyl_a(xa, iq / p[6], 0) +
-                        fma(s1, p[4], s2 * p[5]) * M<T>::cyl_a(xb, iq / p[7], 0);
-            inner = fma(F, F, inner);
+    } else {
+        for (int o = 0; o < no; ++o) {
+            const T* c = orient + 4 * o;
+            const T qc = fma(qv[0], c[0], fma(qv[1], c[1], qv[2] * c[2]));
+            const T x0 = fma(qv[1], c[2], -qv[2] * c[1]);
+            const T x1 = fma(qv[2], c[0], -qv[0] * c[2]);
+            const T x2 = fma(qv[0], c[1], -qv[1] * c[0]);
+            const T qab2 = fma(x0, x0, fma(x1, x1, x2 * x2));
+            const T y1 = fabs(qc) * mc.half_length, y2 = fabs(qc) * mc.half_length_o;
+            const T s1 = M<T>::sinc(y1, M<T>::rcp(y1)), s2 = M<T>::sinc(y2, M<T>::rcp(y2));
+            T inner = 0;
+            const T qab = M<T>::sqrt_(qab2), iq = M<T>::rcp(qab);
+            for (int i = 0; i < np; ++i) {
+                const T* p = poly + SAS_POLY_STRIDE * i;
+                const T xa = qab * p[6], xb = qab * p[7];
+                const T F = fma(s1, p[2], s2 * p[3]) * M<T>::cyl_a(xa, iq / p[6], 0) +
+                            fma(s1, p[4], s2 * p[5]) * M<T>::cyl_a(xb, iq / p[7], 0);
+                inner = fma(F, F, inner);
+            }
+            k.add(c[3] * inner);
         }
-        k.add(c[3] * inner);
+        return k.s;
     }
-    return k.s;
 }
 
 // Core-shell ellipsoid of revolution: per orientation node and radius node
@@ -1064,6 +1065,41 @@ __device__ __forceinline__ T fractal_m(T y, T e)
     return (sin(z) / z) * (th / y) * pow(fma(y, y, (T)1), (T)-0.5 * e);
 }
 
+// x^-a gamma(a, x), the scaled lower incomplete gamma function (a > 0,
+// x > 0; gamma_a = Gamma(a)): the power series e^-x sum_n x^n / (a (a+1)
+// ... (a+n)) below x = a + 1, above it Gamma(a) x^-a - e^-x CF with the
+// continued fraction of Gamma(a, x) by Lentz's method (Abramowitz-Stegun
+// 6.5.29 and 6.5.31). Both converge within 200 steps for a <= 6.
+template <typename T>
+__device__ __forceinline__ T scaled_lower_gamma(T a, T x, T gamma_a)
+{
+    constexpr bool fp32 = sizeof(T) == sizeof(float);
+    const T eps = fp32 ? (T)3e-8 : (T)1e-17;
+    if (x < a + (T)1) {
+        T term = (T)1 / a, sum = term;
+        for (int n = 1; n < 200 && term > eps * sum; ++n) {
+            term *= x / (a + (T)n);
+            sum += term;
+        }
+        return exp(-x) * sum;
+    }
+    const T tiny = fp32 ? (T)1e-30 : (T)1e-300;
+    T b = x + (T)1 - a, f = (T)1 / b, C = (T)1 / tiny, D = (T)1 / b;
+    for (int i = 1; i < 200; ++i) {
+        const T an = -(T)i * ((T)i - a);
+        b += (T)2;
+        D = fma(an, D, b);
+        if (fabs(D) < tiny) D = tiny;
+        C = b + an / C;
+        if (fabs(C) < tiny) C = tiny;
+        D = (T)1 / D;
+        const T delta = C * D;
+        f *= delta;
+        if (fabs(delta - (T)1) < eps) break;
+    }
+    return gamma_a * pow(x, -a) - exp(-x) * f;
+}
+
 template <typename T>
 __device__ __forceinline__ T shape_independent(T q2, T q, const ModelConst<T>& mc)
 {
@@ -1109,6 +1145,11 @@ __device__ __forceinline__ T shape_independent(T q2, T q, const ModelConst<T>& m
     case SAS_FN_SPINODAL: {       // f_a = 1 / Qmax, f_b = g, f_c = g / 2, f_d = 1 + g / 2
         const T x = q * mc.f_a;
         return mc.f_d * x * x / (mc.f_c + pow(x, (T)2 + mc.f_b));
+    }
+    case SAS_FN_POLYMER_EXCL_VOLUME: {   // f_a: U = Q^2 f_a; f_b = m = 1/nu, f_c = Gamma(m/2), f_d = Gamma(m)
+        const T U = q2 * mc.f_a;
+        if (U < (T)1e-30) return (T)1;
+        return mc.f_b * (scaled_lower_gamma<T>((T)0.5 * mc.f_b, U, mc.f_c) - scaled_lower_gamma<T>(mc.f_b, U, mc.f_d));
     }
     default: {                    // star polymer: f_a = Rg^2 f / (3f - 2), f_b = f
         const T v = q2 * mc.f_a;

@@ -36,7 +36,7 @@ def _cuda():
 # laws held to the relative tolerance alone (no zeros, no underflow on the grid)
 RELATIVE_ONLY = {"lorentz", "dab", "power_law", "teubner_strey", "peak_lorentz", "two_power_law",
                  "guinier_porod", "guinier_porod_rod", "gauss_lorentz_gel", "poly_coil", "star",
-                 "mass_fractal", "fractal", "spinodal"}
+                 "mass_fractal", "fractal", "spinodal", "excluded_volume", "excluded_volume_swollen"}
 
 LAWS = {
     "guinier": (W.GUINIER, (40.0, 0.0, 0.0)),
@@ -58,6 +58,8 @@ LAWS = {
     "mass_fractal_blocks": (W.MASS_FRACTAL, (25.0, 2.6, 300.0)),
     "fractal": (W.FRACTAL, (2.0, 2.1, 120.0)),
     "spinodal": (W.SPINODAL, (0.03, 3.0, 0.0)),
+    "excluded_volume": (W.POLYMER_EXCL_VOLUME, (40.0, 5.0 / 3.0, 0.0)),
+    "excluded_volume_swollen": (W.POLYMER_EXCL_VOLUME, (25.0, 4.5, 0.0)),
 }
 
 
@@ -104,7 +106,8 @@ def _records(e, first, n, seed):
 
 @pytest.mark.parametrize("name,precision", [("coil", W.FP32), ("dab", W.FP64), ("teubner_strey", W.FP32),
                                             ("poly_coil", W.FP32), ("star", W.FP64), ("guinier_porod", W.FP32),
-                                            ("fractal", W.FP32), ("spinodal", W.FP64)])
+                                            ("fractal", W.FP32), ("spinodal", W.FP64),
+                                            ("excluded_volume", W.FP32)])
 def test_records_and_trace(name, precision):
     m = _m(name, precision)
     inst = W.instrument(nx=64, ny=64)
@@ -130,6 +133,7 @@ def test_records_and_trace(name, precision):
                                  dict(function=W.MASS_FRACTAL, f_p0=10.0, f_p1=1.0, f_p2=50.0),
                                  dict(function=W.FRACTAL, f_p0=0.0, f_p1=2.0, f_p2=50.0),
                                  dict(function=W.SPINODAL, f_p0=0.03, f_p1=0.0),
+                                 dict(function=W.POLYMER_EXCL_VOLUME, f_p0=30.0, f_p1=1.0),
                                  dict(sampling=W.PER_EVENT), dict(self_attenuation=1),
                                  dict(sq_kind=W.SQ_HARD_SPHERE_PY, sq_radius=10.0, sq_fraction=0.1)])
 def test_refusals(bad):
