@@ -34,6 +34,29 @@ def weak_range(rank: int, n_per_rank: int):
     return rank * n_per_rank, n_per_rank
 
 
+def experiment_partition(costs, world: int):
+    """Split a batch of experiments over `world` ranks with no exchange:
+    every experiment's detector stays on the rank that traces it (its
+    histories are keyed by its own experiment id). Longest-processing-time
+    assignment: experiments in decreasing cost (histories x per-history
+    cost) go to the least-loaded rank, ties to the lowest rank, which keeps
+    the largest load within 4/3 of the optimum. Returns one ascending list
+    of experiment indices per rank."""
+    if world < 1:
+        raise ValueError("need world >= 1")
+    costs = [float(c) for c in costs]
+    if any(not c >= 0.0 for c in costs):
+        raise ValueError("costs must be >= 0")
+    order = sorted(range(len(costs)), key=lambda e: (-costs[e], e))
+    load = [0.0] * world
+    parts = [[] for _ in range(world)]
+    for e in order:
+        r = min(range(world), key=lambda k: (load[k], k))
+        parts[r].append(e)
+        load[r] += costs[e]
+    return [sorted(p) for p in parts]
+
+
 class _CudaArray:
     """__cuda_array_interface__ of a library-owned device array, so that
     torch can view it without a copy."""

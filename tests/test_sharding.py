@@ -78,3 +78,27 @@ def test_ranks_reproduce_single_run(tmp_path, world, n, mode, dst):
         assert np.allclose(red["sum_w"], full["sum_w"].ravel(), rtol=1e-12, atol=0)
         assert np.allclose(red["sum_w2"], full["sum_w2"].ravel(), rtol=1e-12, atol=0)
         assert red["trans"][0] == pytest.approx(full["trans"], rel=1e-12)
+
+
+def test_experiment_partition_balances_without_exchange():
+    """A batch splits over ranks by experiment: each experiment on exactly
+    one rank, the largest load within 4/3 of the lower bound max(mean load,
+    largest experiment) (the longest-processing-time guarantee), the split
+    deterministic."""
+    import sas_workloads as W
+    from paper_2501_06054_gb300 import flops as F
+    from paper_2501_06054_gb300 import shard
+    models, counts = W.batched_models(n_exp=512, seed=3)
+    costs = [F.flops_per_history(m.kind, m.n_poly, m.n_gamma * m.n_psi) * float(c) for m, c in zip(models, counts)]
+    for world in (1, 2, 3, 8):
+        parts = shard.experiment_partition(costs, world)
+        assert len(parts) == world
+        flat = sorted(e for p in parts for e in p)
+        assert flat == list(range(len(costs)))
+        loads = [sum(costs[e] for e in p) for p in parts]
+        bound = max(sum(costs) / world, max(costs))
+        assert max(loads) <= 4.0 / 3.0 * bound * (1 + 1e-12)
+        assert parts == shard.experiment_partition(costs, world)
+    assert shard.experiment_partition([], 2) == [[], []]
+    with pytest.raises(ValueError):
+        shard.experiment_partition([1.0, -1.0], 2)
