@@ -368,6 +368,18 @@ static double oracle_shape_independent(const oracle_model *m, double q)
                        : mp * (oracle_scaled_lower_gamma(0.5 * mp, U) - oracle_scaled_lower_gamma(mp, U));
         break;
     }
+    case 17: {  /* linear pearls: N = f_p2 spheres of radius R = f_p0 on a line, centres d = 2R + f_p1 apart;
+                   Debye's sum over the pairs, normalised to 1 at Q = 0 */
+        double R = m->f_p0, d = 2.0 * R + m->f_p1, P = oracle_sphere_f(q * R);
+        int64_t N = (int64_t)m->f_p2;
+        double pairs = (double)N;
+        for (int64_t k = 1; k < N; ++k) {
+            double y = q * k * d;
+            pairs += 2.0 * (double)(N - k) * (y < 1e-8 ? 1.0 : sin(y) / y);
+        }
+        f = P * P * pairs / ((double)N * (double)N);
+        break;
+    }
     default: {  /* star polymer (Benoit): Rg = f_p0 of the star, f_p1 arms */
         double fa = m->f_p1, v = q2 * m->f_p0 * m->f_p0 * fa / (3.0 * fa - 2.0);
         double deb, g;

@@ -42,7 +42,7 @@ ELLIPTICAL_CYLINDER, HOLLOW_RECTANGULAR_PRISM = 12, 13   # no symmetry axis, lik
 SHAPE_INDEPENDENT = 14                                    # dSigma/dOmega = f_scale f(|Q|), see `function`
 GUINIER, GAUSS_COIL, LORENTZ, DAB, POWER_LAW, GAUSS_PEAK, TEUBNER_STREY = range(7)
 PEAK_LORENTZ, TWO_POWER_LAW, GUINIER_POROD, GAUSS_LORENTZ_GEL, POLY_GAUSS_COIL, STAR_POLYMER = range(7, 13)
-MASS_FRACTAL, FRACTAL, SPINODAL, POLYMER_EXCL_VOLUME = 13, 14, 15, 16
+MASS_FRACTAL, FRACTAL, SPINODAL, POLYMER_EXCL_VOLUME, LINEAR_PEARLS = 13, 14, 15, 16, 17
 MODEL_NAMES = {SPHERE: "sphere", CORE_SHELL: "core_shell", CYLINDER: "cylinder",
                ELLIPSOID: "ellipsoid", TRIAXIAL_ELLIPSOID: "triaxial_ellipsoid",
                PARALLELEPIPED: "parallelepiped", CAPPED_CYLINDER: "capped_cylinder",
@@ -115,7 +115,7 @@ class Model:
     thickness_face: float = 0.0     # core-shell cylinder: shell on the end faces; core-shell ellipsoid:
                                     # shell along the axis (thickness: radial / equatorial shell)
     sld_face: float = 0.0           # core-shell bicelle: SLD of the face layers (sld_shell is the rim's)
-    function: int = GUINIER         # shape-independent: GUINIER .. POLYMER_EXCL_VOLUME
+    function: int = GUINIER         # shape-independent: GUINIER .. LINEAR_PEARLS
     f_scale: float = 0.0            # shape-independent: dSigma/dOmega = f_scale f(|Q|), 1/angstrom
     f_p0: float = 0.0               # shape-independent parameters (Rg, xi, m, Q0 / sigma, a2 / c1 / c2)
     f_p1: float = 0.0

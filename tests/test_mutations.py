@@ -119,6 +119,10 @@ MUTATIONS = {
          "test_shape_independent_oracle.py", C,
          [("double U = q2 * m->f_p0 * m->f_p0 * (2.0 * nu + 1.0) * (2.0 * nu + 2.0) / 6.0;",
            "double U = q2 * m->f_p0 * m->f_p0;")]),
+    39: ("linear pearls with N instead of N - k pairs at distance k d", "linear_pearls",
+         "test_shape_independent_oracle.py", C,
+         [("pairs += 2.0 * (double)(N - k) * (y < 1e-8 ? 1.0 : sin(y) / y);",
+           "pairs += 2.0 * (double)N * (y < 1e-8 ? 1.0 : sin(y) / y);")]),
     37: ("spinodal peak without its normalisation 1 + g/2", "spinodal", "test_shape_independent_oracle.py", C,
          [("f = (1.0 + g / 2.0) * x * x / (g / 2.0 + pow(x, 2.0 + g));", "f = x * x / (g / 2.0 + pow(x, 2.0 + g));")]),
 }

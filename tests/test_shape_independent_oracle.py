@@ -21,7 +21,10 @@ dSigma/dOmega = f_scale f(|Q|).
 * the chain with excluded volume is Hammouda's integral
   2 int_0^1 (1 - x) exp(-U x^(2 nu)) dx (scipy's adaptive quadrature), is
   Debye's function at nu = 1/2, has the Guinier slope -Rg^2/3 and the
-  log-log slope -1/nu at large Q.
+  log-log slope -1/nu at large Q;
+* linear pearls: the isotropic average of |sum_j exp(i Q.r_j)|^2 of the
+  chain by Gauss-Legendre quadrature over the angle to the chain's axis,
+  times the sphere factor; one pearl is the sphere.
 """
 import math
 
@@ -332,3 +335,26 @@ def test_excluded_volume_chain_limits():
         assert (1.0 - _pev(rg, m, q)[0]) / (q * q * rg * rg / 3.0) == pytest.approx(1.0, rel=1e-4)
         hi = _pev(rg, m, [20.0, 40.0])                              # Q^-m far beyond 1/Rg, up to the
         assert math.log2(hi[0] / hi[1]) == pytest.approx(m, rel=1e-4)   # second term's U^(-m/2) ~ 1e-5
+
+
+# ---- linear pearls
+
+@pytest.mark.parametrize("n,r,sep", [(2, 20.0, 0.0), (7, 15.0, 12.0), (30, 8.0, 3.0)])
+def test_linear_pearls_is_the_orientation_average_of_the_chain(n, r, sep):
+    d = 2 * r + sep
+    m = _m(W.LINEAR_PEARLS, f_p0=r, f_p1=sep, f_p2=float(n), f_scale=1.0)
+    qs = np.array([1e-3, 0.01, 0.03, 0.1, 0.3])
+    x, w = np.polynomial.legendre.leggauss(400)                 # cos of the angle between Q and the axis
+    z = d * np.arange(n)
+    ref = []
+    for q in qs:
+        amp = np.exp(1j * q * np.outer(x, z)).sum(axis=1)       # sum over the pearls at each angle
+        ref.append(0.5 * np.dot(w, np.abs(amp) ** 2) / n ** 2 * _sphere_p(q * r))
+    assert np.allclose(_p(m, qs), ref, rtol=1e-10, atol=0)
+    assert abs(_p(m, 1e-9)[0] - 1.0) < 1e-12
+
+
+def test_one_pearl_is_the_sphere():
+    m = _m(W.LINEAR_PEARLS, f_p0=25.0, f_p1=5.0, f_p2=1.0, f_scale=1.0)
+    qs = np.array([0.01, 0.1, 0.3])
+    assert np.allclose(_p(m, qs), _sphere_p(qs * 25.0), rtol=1e-12, atol=0)
