@@ -72,7 +72,7 @@ enum { SAS_FN_GUINIER = 0, SAS_FN_GAUSS_COIL = 1, SAS_FN_LORENTZ = 2, SAS_FN_DAB
        SAS_FN_GAUSS_PEAK = 5, SAS_FN_TEUBNER_STREY = 6, SAS_FN_PEAK_LORENTZ = 7, SAS_FN_TWO_POWER_LAW = 8,
        SAS_FN_GUINIER_POROD = 9, SAS_FN_GAUSS_LORENTZ_GEL = 10, SAS_FN_POLY_GAUSS_COIL = 11,
        SAS_FN_STAR_POLYMER = 12, SAS_FN_MASS_FRACTAL = 13, SAS_FN_FRACTAL = 14, SAS_FN_SPINODAL = 15,
-       SAS_FN_POLYMER_EXCL_VOLUME = 16 };
+       SAS_FN_POLYMER_EXCL_VOLUME = 16, SAS_FN_LINEAR_PEARLS = 17 };
 /* largest Gauss-Legendre rule over an end cap */
 #define SAS_MAX_CAP_NODES 64
 enum { SAS_SQ_NONE = 0, SAS_SQ_HARD_SPHERE_PY = 1, SAS_SQ_HAYTER_MSA = 2 };
@@ -266,7 +266,11 @@ typedef struct sas_model_desc {
      *                         x = Q / Qmax (1 at Q = Qmax)         f_p0 = Qmax > 0, f_p1 = g > 0
      *   SAS_FN_POLYMER_EXCL_VOLUME  Hammouda's chain with excluded volume, Flory exponent
      *                         nu = 1/m: 2 int_0^1 (1 - x) exp(-U x^(2 nu)) dx,
-     *                         U = (Q Rg)^2 (2 nu + 1)(2 nu + 2) / 6   f_p0 = Rg > 0, f_p1 = m in (1, 6) */
+     *                         U = (Q Rg)^2 (2 nu + 1)(2 nu + 2) / 6   f_p0 = Rg > 0, f_p1 = m in (1, 6)
+     *   SAS_FN_LINEAR_PEARLS  N spheres of radius R on a line, centres d = 2R + s apart:
+     *                         P(Q R) (N + 2 sum_k (N - k) sin(Q k d) / (Q k d)) / N^2
+     *                                                              f_p0 = R > 0, f_p1 = s >= 0,
+     *                                                              f_p2 = N (an integer, 1 .. 1000) */
     int64_t function;
     double f_scale;          /* >= 0 */
     double f_p0, f_p1, f_p2;

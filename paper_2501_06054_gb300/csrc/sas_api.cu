@@ -887,6 +887,12 @@ ModelConst<T> model_const(const sas_model_desc& m, const ModelTables& t)
             c.f_d = (T)(std::tgamma(p1 + 1.0) * std::pow(m.f_p2 / p0, p1));
             break;
         case SAS_FN_SPINODAL: c.f_a = (T)(1.0 / p0); c.f_b = (T)p1; c.f_c = (T)(0.5 * p1); c.f_d = (T)(1.0 + 0.5 * p1); break;
+        case SAS_FN_LINEAR_PEARLS:   // R, centre distance d, N, 1 / N^2
+            c.f_a = (T)p0;
+            c.f_b = (T)(2.0 * p0 + p1);
+            c.f_c = (T)m.f_p2;
+            c.f_d = (T)(1.0 / (m.f_p2 * m.f_p2));
+            break;
         case SAS_FN_POLYMER_EXCL_VOLUME: {   // U = Q^2 f_a; m, Gamma(m / 2), Gamma(m)
             const double nu = 1.0 / p1;
             c.f_a = (T)(p0 * p0 * (2.0 * nu + 1.0) * (2.0 * nu + 2.0) / 6.0);
@@ -974,7 +980,7 @@ sas_status validate_model(const sas_model_desc* m)
     if (!m) return fail(SAS_ERR_ARG, "model is NULL");
     if (m->kind < 0 || m->kind > 14) return fail(SAS_ERR_ARG, "unknown model kind");
     if (m->kind == SAS_SHAPE_INDEPENDENT) {
-        if (m->function < SAS_FN_GUINIER || m->function > SAS_FN_POLYMER_EXCL_VOLUME)
+        if (m->function < SAS_FN_GUINIER || m->function > SAS_FN_LINEAR_PEARLS)
             return fail(SAS_ERR_ARG, "unknown shape-independent function");
         if (!finite_all({m->f_scale, m->f_p0, m->f_p1, m->f_p2}) || m->f_scale < 0.0)
             return fail(SAS_ERR_ARG, "f_scale must be finite and >= 0, f_p0..f_p2 finite");
@@ -1005,6 +1011,9 @@ sas_status validate_model(const sas_model_desc* m)
             return fail(SAS_ERR_ARG, "fractal: Gamma(D + 1) (xi / R0)^D overflows");
         if (fn == SAS_FN_SPINODAL && !(m->f_p0 > 0.0 && m->f_p1 > 0.0))
             return fail(SAS_ERR_ARG, "spinodal needs Qmax > 0 and an exponent g > 0");
+        if (fn == SAS_FN_LINEAR_PEARLS &&
+            !(m->f_p0 > 0.0 && m->f_p1 >= 0.0 && m->f_p2 >= 1.0 && m->f_p2 <= 1000.0 && m->f_p2 == std::floor(m->f_p2)))
+            return fail(SAS_ERR_ARG, "linear pearls need R > 0, a separation s >= 0 and an integer N in [1, 1000]");
         if (fn == SAS_FN_POLYMER_EXCL_VOLUME && !(m->f_p0 > 0.0 && m->f_p1 > 1.0 && m->f_p1 < 6.0))
             return fail(SAS_ERR_ARG, "excluded-volume chain needs Rg > 0 and a Porod exponent 1 < m < 6");
         if (m->sq_kind != SAS_SQ_NONE || m->sampling != SAS_QUADRATURE || m->self_attenuation != 0)

@@ -1146,6 +1146,17 @@ __device__ __forceinline__ T shape_independent(T q2, T q, const ModelConst<T>& m
         const T x = q * mc.f_a;
         return mc.f_d * x * x / (mc.f_c + pow(x, (T)2 + mc.f_b));
     }
+    case SAS_FN_LINEAR_PEARLS: {  // f_a = R, f_b = d, f_c = N, f_d = 1 / N^2
+        if (q < (T)1e-30) return (T)1;
+        const int n = (int)mc.f_c;
+        const T y1 = q * mc.f_b;
+        T pairs = mc.f_c;
+        for (int k = 1; k < n; ++k) {
+            const T y = y1 * (T)k;
+            pairs = fma((T)2 * (T)(n - k), sin(y) / y, pairs);
+        }
+        return si_sphere_p<T>(q, mc.f_a) * pairs * mc.f_d;
+    }
     case SAS_FN_POLYMER_EXCL_VOLUME: {   // f_a: U = Q^2 f_a; f_b = m = 1/nu, f_c = Gamma(m/2), f_d = Gamma(m)
         const T U = q2 * mc.f_a;
         if (U < (T)1e-30) return (T)1;

@@ -60,6 +60,8 @@ LAWS = {
     "spinodal": (W.SPINODAL, (0.03, 3.0, 0.0)),
     "excluded_volume": (W.POLYMER_EXCL_VOLUME, (40.0, 5.0 / 3.0, 0.0)),
     "excluded_volume_swollen": (W.POLYMER_EXCL_VOLUME, (25.0, 4.5, 0.0)),
+    "linear_pearls": (W.LINEAR_PEARLS, (20.0, 10.0, 8.0)),
+    "linear_pearls_long": (W.LINEAR_PEARLS, (6.0, 4.0, 60.0)),
 }
 
 
@@ -107,7 +109,7 @@ def _records(e, first, n, seed):
 @pytest.mark.parametrize("name,precision", [("coil", W.FP32), ("dab", W.FP64), ("teubner_strey", W.FP32),
                                             ("poly_coil", W.FP32), ("star", W.FP64), ("guinier_porod", W.FP32),
                                             ("fractal", W.FP32), ("spinodal", W.FP64),
-                                            ("excluded_volume", W.FP32)])
+                                            ("excluded_volume", W.FP32), ("linear_pearls", W.FP32)])
 def test_records_and_trace(name, precision):
     m = _m(name, precision)
     inst = W.instrument(nx=64, ny=64)
@@ -134,6 +136,7 @@ def test_records_and_trace(name, precision):
                                  dict(function=W.FRACTAL, f_p0=0.0, f_p1=2.0, f_p2=50.0),
                                  dict(function=W.SPINODAL, f_p0=0.03, f_p1=0.0),
                                  dict(function=W.POLYMER_EXCL_VOLUME, f_p0=30.0, f_p1=1.0),
+                                 dict(function=W.LINEAR_PEARLS, f_p0=10.0, f_p1=2.0, f_p2=2.5),
                                  dict(sampling=W.PER_EVENT), dict(self_attenuation=1),
                                  dict(sq_kind=W.SQ_HARD_SPHERE_PY, sq_radius=10.0, sq_fraction=0.1)])
 def test_refusals(bad):
