@@ -84,7 +84,8 @@ class _Model(ctypes.Structure):
                 ("self_att", ctypes.c_int64), ("n_cap", ctypes.c_int64), ("thickness_face", ctypes.c_double),
                 ("sld_face", ctypes.c_double), ("function", ctypes.c_int64)] + \
                [(n, ctypes.c_double) for n in ("f_scale", "f_p0", "f_p1", "f_p2")] + \
-               [("sq_tab", _DP), ("sq_n", ctypes.c_int64), ("sq_dq", ctypes.c_double)]
+               [("sq_tab", _DP), ("sq_n", ctypes.c_int64), ("sq_dq", ctypes.c_double),
+                ("fuzz", ctypes.c_double)]
 
 
 def lib():
@@ -362,7 +363,8 @@ class Prepared:
                         sld_face=float(m.get("sld_face", 0.0)), function=int(m.get("function", 0)),
                         f_scale=float(m.get("f_scale", 0.0)), f_p0=float(m.get("f_p0", 0.0)),
                         f_p1=float(m.get("f_p1", 0.0)), f_p2=float(m.get("f_p2", 0.0)),
-                        sq_tab=self.sq_tab.ctypes.data_as(_DP), sq_n=sq_n, sq_dq=sq_dq)
+                        sq_tab=self.sq_tab.ctypes.data_as(_DP), sq_n=sq_n, sq_dq=sq_dq,
+                        fuzz=float(m.get("fuzziness", 0.0)))
 
 
 def _inst(instrument):

@@ -133,6 +133,8 @@ typedef struct {
     const double *sq_tab;
     int64_t sq_n;
     double sq_dq;
+    /* fuzzy sphere: width of the Gaussian the sphere's density is convolved with (0: sharp) */
+    double fuzz;
 } oracle_model;
 
 /* --------------------------------------------------------- model pieces */
@@ -403,11 +405,12 @@ double oracle_dsigma(const oracle_model *m, const double q[3])
     if (m->kind == 14) return oracle_shape_independent(m, qq);
     double sum = 0.0, vmean = 0.0;
     int64_t np = m->n_poly;
-    if (m->kind == 0) {              /* sphere */
-        double drho = m->sld - m->sld_solvent;
+    if (m->kind == 0) {              /* sphere; fuzzy: the amplitude of its density convolved with a
+                                        Gaussian of width fuzz, the product with exp(-(Q fuzz)^2 / 2) */
+        double drho = m->sld - m->sld_solvent, blur = exp(-0.5 * qq * qq * m->fuzz * m->fuzz);
         for (int64_t i = 0; i < np; ++i) {
             double r = m->poly_r[i], V = sphere_volume(r);
-            double F = drho * V * oracle_sphere_f(qq * r);
+            double F = drho * V * oracle_sphere_f(qq * r) * blur;
             sum += m->poly_w[i] * F * F;
             vmean += m->poly_w[i] * V;
         }

@@ -124,6 +124,7 @@ class Model:
     sq_temperature: float = 298.15  # K
     sq_salt: float = 0.0            # mol/L of 1:1 salt
     sq_dielectric: float = 78.4     # relative permittivity of the solvent
+    fuzziness: float = 0.0          # sphere: Gaussian interface width (fuzzy sphere), angstrom
 
     def as_dict(self):
         return asdict(self)

@@ -123,6 +123,9 @@ MUTATIONS = {
          "test_shape_independent_oracle.py", C,
          [("pairs += 2.0 * (double)(N - k) * (y < 1e-8 ? 1.0 : sin(y) / y);",
            "pairs += 2.0 * (double)N * (y < 1e-8 ? 1.0 : sin(y) / y);")]),
+    40: ("fuzzy sphere blurred by exp(-(Q sigma)^2) in the amplitude instead of its square root",
+         "fuzzy_sphere", "test_oracle_pins.py", C,
+         [("blur = exp(-0.5 * qq * qq * m->fuzz * m->fuzz);", "blur = exp(-qq * qq * m->fuzz * m->fuzz);")]),
     37: ("spinodal peak without its normalisation 1 + g/2", "spinodal", "test_shape_independent_oracle.py", C,
          [("f = (1.0 + g / 2.0) * x * x / (g / 2.0 + pow(x, 2.0 + g));", "f = x * x / (g / 2.0 + pow(x, 2.0 + g));")]),
 }

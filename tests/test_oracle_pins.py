@@ -229,6 +229,31 @@ def test_sphere_dsigma_closed_form():
     assert abs(got[0] / (phi * drho ** 2 * V) - 1.0) < 1e-14   # P(0) = 1
 
 
+def test_fuzzy_sphere_is_the_transform_of_the_blurred_ball():
+    """The fuzzy sphere's cross section against the three-dimensional
+    transform, by adaptive quadrature, of the ball's density convolved with
+    an isotropic Gaussian of width sigma (the convolution written out with
+    erf and the Gaussian tails); the transform at Q -> 0 is the ball's
+    volume."""
+    R, s, drho, phi = 40.0, 6.0, 2e-6, 0.01
+    m = _model(kind=W.SPHERE, radius=R, sld=drho, volume_fraction=phi, fuzziness=s)
+
+    def rho(r):
+        a, b = (R - r) / (math.sqrt(2) * s), (R + r) / (math.sqrt(2) * s)
+        return 0.5 * (math.erf(a) + math.erf(b)) + s / (r * math.sqrt(2 * math.pi)) * (
+            math.exp(-(R + r) ** 2 / (2 * s * s)) - math.exp(-(R - r) ** 2 / (2 * s * s)))
+
+    V = 4.0 / 3.0 * math.pi * R ** 3
+    mass, _ = si.quad(lambda r: 4 * math.pi * r * r * rho(r), 1e-9, R + 12 * s, limit=400)
+    assert mass == pytest.approx(V, rel=1e-12)
+    qs = np.array([0.01, 0.05, 0.1, 0.2])
+    got = oracle.dsigma(m, _q_along([0.1, 0.7, -0.4], qs))
+    for q, g in zip(qs, got):
+        ft, _ = si.quad(lambda r: 4 * math.pi * r * r * rho(r) * math.sin(q * r) / (q * r), 1e-9, R + 12 * s,
+                        limit=800, epsabs=0.0, epsrel=1e-12)
+        assert g == pytest.approx(phi * drho ** 2 * ft ** 2 / V, rel=1e-9)
+
+
 def test_sphere_guinier_limit():
     """Guinier law: 1 - P = Q^2 Rg^2 / 3 + O(Q^4) with Rg^2 = 3 R^2 / 5; for a
     sphere the next term is P - exp(-Q^2 Rg^2/3) = -(QR)^4 / 350 + O((QR)^6)."""
