@@ -300,6 +300,12 @@ typedef struct sas_model_desc {
     double sq_temperature;   /* K > 0 */
     double sq_salt;          /* mol/L >= 0 */
     double sq_dielectric;    /* relative permittivity of the solvent > 0 */
+    /* Fuzzy sphere (Table I, group F; SAS_SPHERE only, 0 elsewhere): the
+     * sphere's density convolved with an isotropic Gaussian of width sigma
+     * = fuzziness (angstrom, >= 0), so that every amplitude carries
+     * exp(-(Q sigma)^2 / 2) (convolution theorem) and dSigma/dOmega the
+     * factor exp(-(Q sigma)^2); 0 is the sharp sphere. */
+    double fuzziness;
 } sas_model_desc;
 
 typedef struct sas_experiment sas_experiment;   /* opaque, library-owned */

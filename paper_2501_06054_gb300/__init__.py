@@ -51,7 +51,7 @@ class sas_model_desc(ctypes.Structure):
                 ("thickness_face", ctypes.c_double), ("sld_face", ctypes.c_double),
                 ("function", ctypes.c_int64)] + \
                [(n, ctypes.c_double) for n in ("f_scale", "f_p0", "f_p1", "f_p2", "sq_charge",
-                                               "sq_temperature", "sq_salt", "sq_dielectric")]
+                                               "sq_temperature", "sq_salt", "sq_dielectric", "fuzziness")]
 
 
 class sas_launch_config(ctypes.Structure):

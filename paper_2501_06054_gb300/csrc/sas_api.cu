@@ -790,6 +790,7 @@ ModelConst<T> model_const(const sas_model_desc& m, const ModelTables& t)
     c.half_length = (T)t.half_length;
     c.shell = (T)m.thickness;
     c.rp2 = (T)t.rp2;
+    c.fuzz2 = (T)(m.kind == SAS_SPHERE ? m.fuzziness * m.fuzziness * 1.4426950408889634 : 0.0);   // log2(e)
     c.sq_2r = (T)t.sq_2r;
     c.sq_24phi = (T)t.sq_24phi;
     c.sq_alpha = (T)t.sq_alpha;
@@ -979,6 +980,8 @@ sas_status validate_model(const sas_model_desc* m)
 {
     if (!m) return fail(SAS_ERR_ARG, "model is NULL");
     if (m->kind < 0 || m->kind > 14) return fail(SAS_ERR_ARG, "unknown model kind");
+    if (!(m->fuzziness >= 0.0) || !std::isfinite(m->fuzziness) || (m->kind != SAS_SPHERE && m->fuzziness != 0.0))
+        return fail(SAS_ERR_ARG, "fuzziness must be finite, >= 0, and 0 for every kind but the sphere");
     if (m->kind == SAS_SHAPE_INDEPENDENT) {
         if (m->function < SAS_FN_GUINIER || m->function > SAS_FN_LINEAR_PEARLS)
             return fail(SAS_ERR_ARG, "unknown shape-independent function");

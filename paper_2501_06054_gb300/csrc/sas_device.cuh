@@ -457,6 +457,12 @@ __device__ __forceinline__ void dsigma_sorted(const float (&q2)[NV], const Model
 #pragma unroll
     for (int v = 0; v < NV; ++v)
         out[v] = q2[v] >= 0.f ? mc.scale * avg[v] * structure_factor<float>(qe[v], mc) : 0.f;
+    if constexpr (KIND == SAS_SPHERE) {   // fuzzy sphere: the Gaussian interface
+        if (mc.fuzz2 > 0.f) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) out[v] *= exp2f(-qe2[v] * mc.fuzz2);
+        }
+    }
 }
 
 // Kahan-compensated accumulation of the orientation sum.
@@ -1186,6 +1192,7 @@ __device__ __forceinline__ T dsigma(const T qv[3], const ModelConst<T>& mc,
     T avg;
     if (KIND == SAS_SPHERE) {
         avg = avg_sphere<T>(q, M<T>::rcp(q), poly, mc.n_poly);
+        if (mc.fuzz2 > (T)0) avg *= exp2(-q2 * mc.fuzz2);   // fuzzy sphere: the Gaussian interface
     } else if (KIND == SAS_CORE_SHELL) {
         avg = avg_core_shell<T>(q, M<T>::rcp(q), poly, mc.n_poly, mc.shell);
     } else if (KIND == SAS_CYLINDER) {
@@ -1308,6 +1315,7 @@ __device__ __forceinline__ T dsigma_event(const T qv[3], const ModelConst<T>& mc
         const T V = (T)(4.0 / 3.0) * pi * r * r * r;
         const T F = (T)3 * mc.ev_c1 * V * g;
         F2 = F * F;
+        if (mc.fuzz2 > (T)0) F2 *= exp2(-q2 * mc.fuzz2);
     } else if (KIND == SAS_CORE_SHELL) {
         const T ro = r + mc.shell;
         const T xc = q * r, xo = q * ro;

@@ -113,6 +113,7 @@ struct ModelConst {
     // the later laws as set in model_const)
     int function;
     T f_a, f_b, f_c, f_d, f_e;
+    T fuzz2;         // fuzzy sphere: sigma^2 log2(e) (dSigma/dOmega times 2^(-Q^2 fuzz2)); 0 otherwise
 };
 
 }  // namespace sas
